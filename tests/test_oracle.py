@@ -1,0 +1,280 @@
+"""Pins of the oracle against facts fixed by the paper and by mathematics (CPU only).
+
+- the paper's worked example (Figs. 1-3, Sec. 2.1.2, Sec. 2.2.2), from tests/golden/;
+- closed forms: tridiagonal, dense, arrowhead, k x k grid in natural order;
+- column structure against brute-force structural elimination (n <= 200);
+- numeric factor against dense Cholesky (a textbook library routine) on small
+  matrices, entries outside the pattern exactly zero, ||A - L L^T|| / ||A||;
+- solve: backward error, and the closed form x = b / d for a diagonal matrix;
+- nested dissection: hand-derived order on a 3 x 3 grid;
+- PR invariants: storage and flops unchanged, permutation only inside supernodes.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2409_13090_gb300 import inputs
+
+
+def _example(golden):
+    ents = [(i - 1, j - 1) for i, j in golden["A_strict_lower_pattern"]["entries"]]
+    return inputs.from_lower_pattern(golden["n"], ents, seed=3)
+
+
+def _seg(arr, ptr, k):
+    return arr[ptr[k]:ptr[k + 1]].tolist()
+
+
+# --------------------------------------------------------------------------- worked example
+
+def test_worked_example_symbolic(golden):
+    A = _example(golden)
+    s = oracle.Oracle(A, None, pr=False).symbolic()
+    assert s.perm.tolist() == list(range(9))  # postorder of Fig. 3's tree is the identity
+    sets = [list(range(s.sup_ptr[J] + 1, s.sup_ptr[J + 1] + 1)) for J in range(s.nsuper)]
+    assert sets == golden["supernodes"]["sets"]
+    assert [(p + 1) if p >= 0 else 0 for p in s.cparent] == golden["etree_parent"]["parent"]
+    assert [g + 1 for g in _seg(s.glbind, s.gl_ptr, 0)] == golden["glbind"]["J1"]
+    assert [g + 1 for g in _seg(s.glbind, s.gl_ptr, 1)] == golden["glbind"]["J2"]
+    assert [(p + 1) if p >= 0 else 0 for p in s.sup_parent] == golden["supernodal_parent"]["parent"]
+    assert _seg(s.relind, s.ri_ptr, 0) == golden["relind"]["J1_J3"]
+    assert _seg(s.relind, s.ri_ptr, 1) == golden["relind"]["J2_J3"]
+    for J, key in ((0, "J1"), (1, "J2")):
+        blocks = [list(range(f + 1, f + 1 + z)) for f, z in zip(_seg(s.blk_first, s.blk_ptr, J), _seg(s.blk_size, s.blk_ptr, J))]
+        assert blocks == golden["blocks"][key]
+    for J, key in ((0, "J1_J3"), (1, "J2_J3")):
+        q0, q1 = s.rb_pair_ptr[J], s.rb_pair_ptr[J + 1]
+        assert q1 - q0 == 1 and s.rb_pair_P[q0] == 2
+        assert s.rb_val[s.rb_val_ptr[q0]:s.rb_val_ptr[q0 + 1]].tolist() == golden["relindB"][key]
+    # the updates J1 -> J3 of Sec. 1: blocks {5,6} and {9}; B' = {9} lies below B = {5,6}
+    assert golden["rlb_updates_J1_to_J3"]["syrk"] == [[5, 6], [9]]
+    # pattern of L = A's pattern plus the fill of Fig. 1
+    cp, rows = oracle.Oracle(A, None, pr=False).columns()
+    pat = {(int(r) + 1, j + 1) for j in range(9) for r in rows[cp[j]:cp[j + 1]] if r != j}
+    want = {tuple(e) for e in golden["A_strict_lower_pattern"]["entries"]} | {tuple(e) for e in golden["fill"]["entries"]}
+    assert pat == want
+
+
+def test_worked_example_pr(golden):
+    A = _example(golden)
+    s = oracle.Oracle(A, None, pr=True).symbolic()
+    old_to_new = {int(k): v for k, v in golden["pr_relabel"]["old_to_new"].items()}
+    for new0, old0 in enumerate(s.perm.tolist()):
+        if old0 >= 4:
+            assert old_to_new[old0 + 1] == new0 + 1
+        else:
+            assert old0 == new0
+    assert s.blk_ptr[1] - s.blk_ptr[0] == golden["pr_blocks"]["J1"]
+    assert s.blk_ptr[2] - s.blk_ptr[1] == golden["pr_blocks"]["J2"]
+    # supernodes and storage carried over unchanged
+    assert s.sup_ptr.tolist() == [0, 2, 4, 9]
+    assert s.nnzL == oracle.Oracle(A, None, pr=False).symbolic().nnzL
+
+
+def test_worked_example_numeric(golden):
+    A = _example(golden)
+    for pr in (False, True):
+        o = oracle.Oracle(A, None, pr=pr)
+        assert o.factor() == 0
+        s = o.symbolic()
+        M = inputs.dense_from_lower(A)[np.ix_(s.perm, s.perm)]
+        Ld = np.linalg.cholesky(M)
+        Ls = _dense_L(o)
+        assert np.abs(Ls - Ld).max() <= 1e-13 * np.abs(Ld).max()
+
+
+# --------------------------------------------------------------------------- helpers
+
+def _dense_L(o):
+    cp, rows = o.columns()
+    lv = o.L_columns()
+    n = len(cp) - 1
+    L = np.zeros((n, n))
+    for j in range(n):
+        L[rows[cp[j]:cp[j + 1]], j] = lv[cp[j]:cp[j + 1]]
+    return L
+
+
+def _pattern_mask(o):
+    cp, rows = o.columns()
+    n = len(cp) - 1
+    m = np.zeros((n, n), bool)
+    for j in range(n):
+        m[rows[cp[j]:cp[j + 1]], j] = True
+    return m
+
+
+def _brute_force_pattern(M):
+    """Structural elimination on a dense boolean matrix (fill of Gaussian elimination)."""
+    n = M.shape[0]
+    S = (M != 0)
+    S = np.tril(S | S.T)
+    for j in range(n):
+        rows = np.nonzero(S[j + 1:, j])[0] + j + 1
+        for a in rows:
+            S[a, rows[rows <= a]] = True
+    return S
+
+
+# --------------------------------------------------------------------------- closed forms
+
+def test_tridiagonal_closed_form():
+    n = 50
+    A = inputs.from_lower_pattern(n, [(i + 1, i) for i in range(n - 1)])
+    o = oracle.Oracle(A, None, pr=False)
+    s = o.symbolic()
+    assert s.nnzL == 2 * n - 1
+    assert s.cparent.tolist() == list(range(1, n)) + [-1]
+    sizes = np.diff(s.sup_ptr).tolist()
+    assert sizes == [1] * (n - 2) + [2]
+
+
+def test_dense_closed_form():
+    n = 30
+    A = inputs.from_lower_pattern(n, [(i, j) for j in range(n) for i in range(j + 1, n)])
+    s = oracle.Oracle(A, None, pr=True).symbolic()
+    assert s.nsuper == 1 and s.nnzL == n * (n + 1) // 2
+    assert s.flops == sum(c * c for c in range(1, n + 1))
+
+
+def test_arrowhead_closed_form():
+    n = 40
+    A = inputs.from_lower_pattern(n, [(n - 1, j) for j in range(n - 1)])
+    s = oracle.Oracle(A, None, pr=False).symbolic()
+    assert s.nnzL == 2 * n - 1
+
+
+@pytest.mark.parametrize("k", [3, 5, 8, 12])
+def test_grid_natural_band_closed_form(k):
+    # In natural order the factor fills the row envelope: row i of a point with
+    # y >= 1 spans k+1 columns, the first grid row spans 2 (1 for the corner), so
+    # nnz(L) = (n - k)(k + 1) + 2(k - 1) + 1 = n(k + 1) - k^2 + k - 1.
+    A = inputs.laplacian_2d(k, k)
+    n = k * k
+    s = oracle.Oracle(A, None, pr=False).symbolic()
+    assert s.nnzL == n * (k + 1) - k * k + k - 1
+
+
+def test_nd_hand_order():
+    # 3x3 grid, leaf 1: split x at 1 -> left column {x=0}, right {x=2}, separator {x=1};
+    # each column box splits y at 1 -> (y=0), (y=2), separator (y=1).
+    assert oracle.nd_grid(3, 3, 1, leaf=1).tolist() == [0, 6, 3, 2, 8, 5, 1, 4, 7]
+
+
+def test_nd_is_permutation_and_top_separator():
+    perm = oracle.nd_grid(64, 64, 1, leaf=8)
+    assert sorted(perm.tolist()) == list(range(64 * 64))
+    top = perm[-64:]
+    assert set((top % 64).tolist()) == {32}  # the last 64 points are the plane x = 32
+    p3 = oracle.nd_grid(6, 5, 4, leaf=8)
+    assert sorted(p3.tolist()) == list(range(120))
+
+
+# --------------------------------------------------------------------------- brute force
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+@pytest.mark.parametrize("pr", [False, True])
+def test_structure_vs_brute_force(seed, pr):
+    n = 60 + 35 * seed
+    A = inputs.random_spd(n, 0.04, seed)
+    rng = np.random.default_rng(seed)
+    perm0 = rng.permutation(n).astype(np.int32)
+    o = oracle.Oracle(A, perm0, pr=pr)
+    s = o.symbolic()
+    M = inputs.dense_from_lower(A)[np.ix_(s.perm, s.perm)]
+    bf = _brute_force_pattern(M)
+    mask = _pattern_mask(o)
+    if not pr:
+        assert np.array_equal(mask, bf)
+    else:
+        assert not np.any(bf & ~mask)  # the true pattern lies inside the supernodal one
+        assert mask.sum() == oracle.Oracle(A, perm0, pr=False).symbolic().nnzL
+
+
+@pytest.mark.parametrize("case", ["rand", "grid2d", "grid3d", "st27"])
+@pytest.mark.parametrize("pr", [False, True])
+def test_numeric_vs_dense_cholesky(case, pr):
+    if case == "rand":
+        A = inputs.random_spd(150, 0.03, 11)
+        perm0 = None
+    elif case == "grid2d":
+        A = inputs.laplacian_2d(12, 13, shift=0.01)
+        perm0 = oracle.nd_grid(12, 13, 1, 4)
+    elif case == "grid3d":
+        A = inputs.diffusion_3d_7pt(5, 6, 5, seed=4, shift=1e-2)
+        perm0 = oracle.nd_grid(5, 6, 5, 8)
+    else:
+        A = inputs.stencil_3d_27pt(5, 5, 5, seed=5)
+        perm0 = oracle.nd_grid(5, 5, 5, 8)
+    o = oracle.Oracle(A, perm0, pr=pr)
+    assert o.factor() == 0
+    s = o.symbolic()
+    M = inputs.dense_from_lower(A)[np.ix_(s.perm, s.perm)]
+    Ld = np.linalg.cholesky(M)
+    Ls = _dense_L(o)
+    mask = _pattern_mask(o)
+    assert np.all(Ld[~mask] == 0.0) or np.abs(Ld[~mask]).max() <= 1e-15 * np.abs(Ld).max()
+    assert np.linalg.norm(Ls - Ld) <= 1e-12 * np.linalg.norm(Ld)
+    assert np.linalg.norm(M - Ls @ Ls.T) <= 1e-14 * np.linalg.norm(M)
+
+
+def test_solve_backward_error_and_diagonal_closed_form():
+    A = inputs.diffusion_3d_7pt(6, 6, 6, seed=9, shift=1e-3)
+    o = oracle.Oracle(A, oracle.nd_grid(6, 6, 6, 8), pr=True)
+    assert o.factor() == 0
+    B = inputs.rhs(A.n, 3, 1)
+    X = o.solve(B)
+    assert oracle.backward_error(A, B, X).max() <= 1e-14
+    # diagonal matrix: x = b / d exactly
+    n = 17
+    D = inputs.from_lower_pattern(n, [])
+    D.values[:] = np.arange(1, n + 1, dtype=float) ** 2
+    od = oracle.Oracle(D, None, pr=True)
+    assert od.factor() == 0
+    b = inputs.rhs(n, 2, 2)
+    x = od.solve(b)
+    # x = (b / d^(1/2)) / d^(1/2): two correctly rounded divisions, within 2 ulps of b / d
+    want = b / D.values[:, None]
+    assert np.all(np.abs(x - want) <= 2 * np.finfo(float).eps * np.abs(want))
+
+
+def test_not_positive_definite_reports_column():
+    A = inputs.laplacian_2d(6, 6)
+    o = oracle.Oracle(A, None, pr=False)
+    s = o.symbolic()
+    # make the diagonal of original column 20 very negative: the first non-positive
+    # pivot is met at that column's position in the final ordering, or before it
+    v = A.values.copy()
+    diag_pos = A.colptr[20]
+    v[diag_pos] = -100.0
+    info = o.factor(v)
+    assert info >= 1
+    new_pos = int(np.nonzero(s.perm == info - 1)[0][0])
+    assert new_pos <= int(np.nonzero(s.perm == 20)[0][0])
+
+
+def test_pr_invariants():
+    A = inputs.diffusion_3d_7pt(10, 9, 8, seed=1)
+    perm0 = oracle.nd_grid(10, 9, 8, 8)
+    s0 = oracle.Oracle(A, perm0, pr=False).symbolic()
+    s1 = oracle.Oracle(A, perm0, pr=True).symbolic()
+    assert s0.nnzL == s1.nnzL and s0.flops == s1.flops
+    assert np.array_equal(s0.sup_ptr, s1.sup_ptr) and np.array_equal(s0.gl_ptr, s1.gl_ptr)
+    for J in range(s0.nsuper):
+        a, b = s0.sup_ptr[J], s0.sup_ptr[J + 1]
+        assert sorted(s0.perm[a:b].tolist()) == sorted(s1.perm[a:b].tolist())
+    assert len(s1.blk_first) <= len(s0.blk_first)
+
+
+def test_relindB_is_distance_of_block_top_from_bottom():
+    """relindB(J, P) entry = m_P - 1 - position of the block's first row in glbind(P)."""
+    A = inputs.stencil_3d_27pt(6, 6, 6, seed=2)
+    s = oracle.Oracle(A, oracle.nd_grid(6, 6, 6, 8), pr=True).symbolic()
+    for J in range(s.nsuper):
+        firsts = _seg(s.blk_first, s.blk_ptr, J)
+        for q in range(s.rb_pair_ptr[J], s.rb_pair_ptr[J + 1]):
+            P = s.rb_pair_P[q]
+            g = _seg(s.glbind, s.gl_ptr, P)
+            sel = [f for f in firsts if f >= s.sup_ptr[P]]
+            vals = s.rb_val[s.rb_val_ptr[q]:s.rb_val_ptr[q + 1]].tolist()
+            assert vals == [len(g) - 1 - g.index(f) for f in sel]
