@@ -1,0 +1,319 @@
+#!/usr/bin/env python
+"""Benchmark: numeric factorization GFLOP/s and solve time of the supernodal
+right-looking Cholesky (RLB) on one GB300.
+
+Workload: 3D 7-point variable-coefficient diffusion on a 48^3 grid
+(n = 110,592; edge coefficients log-uniform[1e-2, 1e2]; diagonal = row sum + 1e-6),
+geometric nested dissection, partition refinement, FP64 RLB factor, 4 right-hand
+sides uniform[-1, 1]. Seeded synthetic input (stand-in for the paper's
+SuiteSparse matrices).
+
+One step = refactor (values already in HBM: value load, every level's POTRF,
+TRSM and RLB updates) + solve of the 4 right-hand sides (forward and backward
+sweeps, FP64 residual and backward error).
+value = sum_j |L_{*,j}|^2 / factor time (GFLOP/s), over the timed steps.
+
+--impl reference times the oracle (plain FP64 column Cholesky in C) on the
+host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "factor GFLOP/s + solve time: FP64 vs FP32/TF32+IR at <=1e-14 backward error"
+WORKLOAD = "diffusion3d_7pt_varcoef_48^3"
+SAMPLE_SIDE = 32  # oracle sample: the same generator on a 32^3 grid
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "tf32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    return ap.parse_args()
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _cpu_sample(steps: int):
+    """Times the oracle (as it stands) on the same generator at 32^3: returns (GFLOP/s, sample text)."""
+    import oracle
+    from paper_2409_13090_gb300 import inputs
+    A = inputs.diffusion_3d_7pt(SAMPLE_SIDE, SAMPLE_SIDE, SAMPLE_SIDE, inputs.SEED_BASE + 2)
+    o = oracle.Oracle(A, oracle.nd_grid(*A.grid, 8), pr=True)
+    flops = o.symbolic().flops
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        info = o.factor()
+        times.append(time.perf_counter() - t0)
+        assert info == 0
+    return flops, times, f"oracle Alg. 1 column Cholesky of the same generator on a {SAMPLE_SIDE}^3 grid " \
+                         f"(n={A.n}, sum c_j^2={flops:.3e}), 1 thread"
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    flops, times, sample = _cpu_sample(args.warmup + args.steps)
+    t = times[args.warmup:]
+    val = flops * len(t) / sum(t) / 1e9
+    line = {"metric": METRIC, "value": val, "unit": "GFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(t) / len(t), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "n": 110592, "nrhs": 4, "precision": "fp64",
+                       "sample": sample, "parallelism": "none (host)"},
+            "cpu_baseline": {"value": val, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = _args()
+    import oracle  # noqa: F401  (only the cpu_baseline leg and --impl reference execute it)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+
+    import paper_2409_13090_gb300 as sc
+    from paper_2409_13090_gb300 import inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    sc.build()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    A, nrhs = inputs.workload(2)
+    t0 = time.perf_counter()
+    sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid, nd_leaf=8, pr=True, variant="rlb")
+    analyze_s = time.perf_counter() - t0
+    view = sym.view()
+    flops = view["flops"]
+    dv = torch.tensor(A.values, device=dev, dtype=torch.float64)
+    B = inputs.rhs(A.n, nrhs, inputs.SEED_BASE + 2)
+    Bd = torch.tensor(np.ascontiguousarray(B.T), device=dev)  # (nrhs, n) = column-major n x nrhs
+    Xd = torch.zeros_like(Bd)
+    num = sym.factor(dv, precision=args.precision)
+    assert num.rc == 0, num.rc
+    for _ in range(max(3, args.warmup)):
+        num.refactor(dv)
+        _, sinfo = num.solve(Bd, Xd)
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches = 0
+    etas = []
+    iters = []
+    for e0, e1, e2 in ev:
+        e0.record(stream)
+        finfo = num.refactor(dv)
+        e1.record(stream)
+        _, sinfo = num.solve(Bd, Xd)
+        e2.record(stream)
+        launches += finfo.kernel_launches + sinfo["kernel_launches"]
+        etas.append(sinfo["eta_max"])
+        iters.append(sinfo["iterations"])
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    fac_ms = sum(a.elapsed_time(b) for a, b, _ in ev)
+    sol_ms = sum(b.elapsed_time(c) for _, b, c in ev)
+    step_ms = sum(a.elapsed_time(c) for a, _, c in ev)
+    if dist:
+        t = torch.tensor([fac_ms, sol_ms, step_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        fac_ms, sol_ms, step_ms = t.tolist()
+    K = args.steps
+    value = world * flops * K / (fac_ms * 1e-3) / 1e9
+
+    # ---- end to end through host buffers (pinned): H2D values + factor + solve with H2D B / D2H X
+    vals_h = torch.tensor(A.values, dtype=torch.float64).pin_memory()
+    B_h = torch.tensor(np.ascontiguousarray(B.T)).pin_memory()
+    X_h = torch.zeros_like(B_h).pin_memory()
+    e2e_f, e2e_s = [], []
+    for i in range(K + 1):
+        torch.cuda.synchronize()
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record(stream)
+        num.refactor(vals_h)
+        b.record(stream)
+        num.solve(B_h, X_h)
+        c.record(stream)
+        torch.cuda.synchronize()
+        if i:
+            e2e_f.append(a.elapsed_time(b))
+            e2e_s.append(b.elapsed_time(c))
+    e2e = {"value": world * flops / (sum(e2e_f) / len(e2e_f) * 1e-3) / 1e9, "unit": "GFLOP/s",
+           "h2d_bytes_per_step": int(A.nnz * 8 + A.n * nrhs * 8), "d2h_bytes_per_step": int(A.n * nrhs * 8 + 8),
+           "factor_ms": sum(e2e_f) / len(e2e_f), "solve_ms": sum(e2e_s) / len(e2e_s)}
+
+    # ---- per-kernel profile of the same factorization (CUDA events around every launch)
+    prof = None
+    for _ in range(3):
+        p = num.profile(dv)
+        if prof is None:
+            prof = {k: dict(v) for k, v in p.items()}
+        else:
+            for k in p:
+                prof[k]["ms"] += p[k]["ms"]
+    for k in prof:
+        prof[k]["ms"] /= 3
+    peaks, peak_kind = _peaks()
+    fp_peak = {}
+    for kind, nm in ((0, "fp64"), (1, "fp32")):
+        try:
+            fp_peak[nm] = sc.sc_probe_fma_peak(kind) / 1e12
+        except Exception:
+            fp_peak[nm] = None
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
+    if dom == "gemm_tc":
+        peak = peaks["bf16_tflops_sustained"] * (1.1 / 2.25)
+        bound, pk = "tensor", f"TF32 = {peak_kind} bf16 sustained x 1.1/2.25 (nominal tf32/bf16)"
+    else:
+        peak = fp_peak["fp64" if args.precision == "fp64" else "fp32"]
+        bound, pk = "alu", "measured FMA-chain probe (sc_probe_fma_peak)"
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if peak else None, "traffic": None, "kernel": dom,
+                "kernel_launches": d["launches"], "peak_source": pk,
+                "profile": {k: {"ms": round(v["ms"], 4), "gflop": round(v["flops"] / 1e9, 3),
+                                "launches": v["launches"]} for k, v in prof.items()},
+                "fma_peak_tflops": fp_peak}
+
+    # ---- the low-precision form on the same matrix (factor GFLOP/s, refinement outcome)
+    mixed = None
+    if not args.no_mixed and args.precision == "fp64":
+        mixed = {}
+        for prec in ("fp32", "tf32"):
+            nm = sym.factor(dv, precision=prec)
+            for _ in range(2):
+                nm.refactor(dv)
+            fts = []
+            for _ in range(3):
+                fi = nm.refactor(dv)
+                fts.append(fi.factor_ms)
+            _, si = nm.solve(Bd, torch.zeros_like(Bd))
+            mixed[prec] = {"factor_gflops": flops / (min(fts) * 1e-3) / 1e9, "factor_ms": min(fts),
+                           "ir_iterations": si["iterations"], "eta_max": si["eta_max"], "converged": si["converged"],
+                           "solve_ms": si["solve_ms"], "pivot_fallbacks": fi.pivot_fallbacks}
+            nm.free()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cflops, ctimes, sample = _cpu_sample(2)
+        cpu = {"value": cflops / min(ctimes) / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+               "sample": sample}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": K,
+                "warmup": args.warmup, "ms_per_step": step_ms / K, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n": A.n, "nnz_A_lower": A.nnz, "nnz_L": int(view["nnzL"]),
+                           "sum_cj2": flops, "nsuper": int(view["nsuper"]), "nrhs": nrhs,
+                           "precision": args.precision, "variant": "rlb", "ordering": "grid ND (leaf 8) + PR",
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                           "l2": "inputs larger than L2 (factor storage rewritten every step)",
+                           "analyze_s": analyze_s},
+                "factor_ms": fac_ms / K, "solve_ms": sol_ms / K, "eta_max": max(etas),
+                "ir_iterations": max(iters), "gpu_launches": launches, "clocks": clk, "e2e": e2e,
+                "roofline": roofline, "cpu_baseline": cpu, "mixed": mixed}
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

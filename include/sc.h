@@ -1,0 +1,257 @@
+/*
+ * sc.h -- C ABI of the GB300 supernodal sparse Cholesky library (libsc).
+ *
+ * Right-looking supernodal Cholesky A = L L^T of a sparse symmetric positive
+ * definite matrix, in the two variants of Karsavuran, Ng, Peyton and Peyton,
+ * "Some new techniques to use in serial sparse Cholesky factorization
+ * algorithms" (arXiv 2409.13090):
+ *   RL  -- Algorithm 4 (Sec. 2.2.1): one update matrix U_J per supernode,
+ *          assembled into the ancestors through relative indices;
+ *   RLB -- Algorithm 5 (Sec. 2.2.2): SYRK/GEMM updates applied block by block
+ *          straight into the ancestors' factor storage, with no floating-point
+ *          working storage and no assembly.
+ * The solution pipeline is the four steps of Sec. 1: ordering, symbolic
+ * factorization (host), numeric factorization (GPU), solution (GPU).
+ *
+ * Conventions shared by every entry point
+ *  - Indices are 0-based. A is given by its lower triangle including the
+ *    diagonal, compressed sparse column (CSC): colptr[n+1] (int64), rowind
+ *    (int32), row indices strictly ascending within a column, the diagonal
+ *    entry present and first in its column. values are FP64, aligned with
+ *    rowind (Sec. 2.1.1: on entry the factor storage holds the entries of the
+ *    lower triangle of A).
+ *  - Return value: SC_OK (0) on success; -i when argument i (1-based) is
+ *    invalid; a positive k when the matrix is not positive definite, k being
+ *    the 1-based index (in the caller's ordering) of the column whose pivot
+ *    was not positive; otherwise one of the named SC_ERR_* codes below.
+ *  - Ownership: the library copies what it needs from caller arrays during
+ *    the call; the caller keeps ownership of every pointer it passes. Handles
+ *    are released with their _free function. An sc_numeric keeps a reference
+ *    to its sc_symbolic; sc_symbolic_free on a symbolic handle that still has
+ *    live numeric handles fails with SC_ERR_IN_USE.
+ *  - Streams: cuda_stream is a cudaStream_t passed as void* (NULL = the
+ *    legacy default stream). Device work is enqueued on it; entry points that
+ *    return device results to the host synchronise that stream.
+ *  - Threading: a handle must not be used from two threads at once.
+ */
+#ifndef SC_H
+#define SC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ codes */
+#define SC_OK 0
+#define SC_ERR_CUDA (-101)          /* a CUDA runtime call failed            */
+#define SC_ERR_TIMEOUT (-102)       /* a bounded device-side wait gave up    */
+#define SC_ERR_NOT_CONVERGED (-103) /* refinement hit its cap; X = best iterate */
+#define SC_ERR_OOM (-104)           /* host or device allocation failed      */
+#define SC_ERR_IN_USE (-105)        /* symbolic handle still referenced      */
+#define SC_ERR_INTERNAL (-106)      /* an internal consistency check failed  */
+#define SC_ERR_UNSUPPORTED (-107)   /* option not available in this build    */
+
+/* --------------------------------------------------------------- options */
+enum sc_ordering { SC_ORDER_NATURAL = 0, SC_ORDER_GRID_ND = 1, SC_ORDER_USER = 2 };
+enum sc_variant { SC_RLB = 0, SC_RL = 1 };
+/* Arithmetic of the numeric factorization:
+ *   SC_FP64  every operation in FP64 (the paper's precision, Sec. 3.1);
+ *   SC_FP32  factor stored and computed in FP32 (SIMT FMA);
+ *   SC_TF32  factor stored in FP32, large update products on the TF32 tensor
+ *            cores with FP32 accumulation.
+ * With SC_FP32 / SC_TF32 the solve refines in FP64 (residual r = b - A x and
+ * the update x += d in FP64) until the backward error reaches ir_tol. */
+enum sc_precision { SC_FP64 = 0, SC_FP32 = 1, SC_TF32 = 2 };
+
+typedef struct sc_options {
+    int32_t ordering;          /* enum sc_ordering                                  */
+    int32_t grid[3];           /* nx, ny, nz for SC_ORDER_GRID_ND (id = x+nx*(y+ny*z)) */
+    int32_t nd_leaf;           /* ND: a box of at most this many points is a leaf   */
+    const int32_t *user_perm;  /* SC_ORDER_USER: perm[new] = old, length n          */
+    int32_t pr;                /* 1 = partition-refinement reordering within supernodes */
+    int32_t variant;           /* enum sc_variant                                   */
+    int32_t precision;         /* enum sc_precision (default for sc_factor)         */
+    int32_t chunk;             /* panel width for the dense work inside a supernode (8..64) */
+    double ir_tol;             /* refinement stops at backward error <= ir_tol      */
+    int32_t ir_maxit;          /* refinement iteration cap                          */
+    double pivot_tau;          /* low-precision pivot d_jj <= tau * |A_jj| redone in FP64 */
+    int64_t spin_limit;        /* iteration limit of every bounded device wait      */
+    int32_t use_graph;         /* 1 = replay the factor schedule as a CUDA graph    */
+    int32_t reserved[7];
+} sc_options;
+
+/* Fills o with the defaults: SC_ORDER_NATURAL, nd_leaf 8, pr 1, SC_RLB, SC_FP64,
+ * chunk 64, ir_tol 1e-14, ir_maxit 30, pivot_tau 2^-10, spin_limit 1<<22,
+ * use_graph 1. Returns SC_OK, or -1 if o is NULL. */
+int sc_options_default(sc_options *o);
+
+/* ------------------------------------------------------------- symbolic */
+typedef struct sc_symbolic sc_symbolic;
+
+/* Symbolic analysis (Sec. 1 steps 1-2; Sec. 2.1.2; Sec. 3.1): ordering, then
+ * elimination tree, postorder, column counts, fundamental supernodes,
+ * supernodal elimination tree, partition refinement within supernodes,
+ * relind(J, p(J)), blocks and relindB(J, P) (Alg. 5), levels, and the
+ * device schedule. Host only; no device memory is touched.
+ *   n        order of A (>= 1)
+ *   colptr   n+1 column pointers into rowind (host)
+ *   rowind   row indices of the lower triangle (host)
+ *   o        options (host); NULL = defaults
+ *   out      receives the new handle
+ * Errors: -1..-5 for invalid arguments (unsorted or duplicate indices,
+ * entries above the diagonal or a missing diagonal give -3), SC_ERR_OOM. */
+int sc_analyze(int64_t n, const int64_t *colptr, const int32_t *rowind, const sc_options *o,
+               sc_symbolic **out);
+
+/* Read-only view of the symbolic structures, for verification. Pointers stay
+ * valid until the handle is freed. All arrays are host memory. */
+typedef struct sc_symbolic_view {
+    int64_t n, nsuper, nnzL, nblocks, npairs;
+    double flops;               /* sum over columns j of |L_{*,j}|^2        */
+    const int32_t *perm;        /* [n]  final ordering, perm[new] = old      */
+    const int32_t *sup_ptr;     /* [nsuper+1] first column of each supernode */
+    const int32_t *sup_parent;  /* [nsuper]   p(J), -1 for a root            */
+    const int64_t *gl_ptr;      /* [nsuper+1] offsets into glbind            */
+    const int32_t *glbind;      /* rows of each supernode, ascending         */
+    const int64_t *ri_ptr;      /* [nsuper+1] offsets into relind            */
+    const int32_t *relind;      /* relind(J, p(J)): |S_J| entries per J       */
+    const int64_t *blk_ptr;     /* [nsuper+1] offsets into the block arrays   */
+    const int32_t *blk_first;   /* first (global) row of each block           */
+    const int32_t *blk_size;    /* rows in each block                         */
+    const int32_t *blk_owner;   /* supernode whose columns hold the block     */
+    const int64_t *rb_pair_ptr; /* [nsuper+1] offsets into the (J,P) pairs    */
+    const int32_t *rb_pair_P;   /* ancestor P of each pair, from p(J) upward  */
+    const int64_t *rb_val_ptr;  /* [npairs+1] offsets into rb_val             */
+    const int32_t *rb_val;      /* relindB(J,P): one entry per block of J at or above P */
+    const int32_t *level;       /* [nsuper] height in the supernodal etree    */
+    const int32_t *cparent;     /* [n] column elimination tree of the final ordering */
+} sc_symbolic_view;
+
+/* Fills v with the view of s. Errors: -1, -2 for NULL arguments. */
+int sc_symbolic_export(const sc_symbolic *s, sc_symbolic_view *v);
+
+/* relind composition of line 10 of Alg. 4 (a host utility): out[k] =
+ * rCP[lenCP - 1 - rJC[k]], i.e. each distance in relind(J,C) picks the entry
+ * of relind(C,P) at that distance from its bottom. Errors: -1..-5 when a
+ * pointer is NULL or a distance is outside relind(C,P). */
+int sc_relind_compose(const int32_t *rJC, int64_t lenJC, const int32_t *rCP, int64_t lenCP, int32_t *out);
+
+/* Frees s. Returns SC_ERR_IN_USE (and frees nothing) while numeric handles
+ * made from s are alive; SC_OK otherwise (also for NULL). */
+int sc_symbolic_free(sc_symbolic *s);
+
+/* -------------------------------------------------------------- numeric */
+typedef struct sc_numeric sc_numeric;
+
+typedef struct sc_factor_info {
+    int64_t failed_col;     /* 0, or 1-based caller-order column of the first bad pivot */
+    int32_t precision;      /* precision actually used                          */
+    int32_t pivot_fallbacks;/* diagonal blocks redone in FP64 (low precision only) */
+    double flops;           /* sum_j |L_{*,j}|^2                                */
+    double factor_ms;       /* device time of the factorization (CUDA events)   */
+    int64_t device_bytes;   /* device memory held by the numeric handle         */
+    int32_t kernel_launches;/* kernels launched by one factorization            */
+    int32_t reserved[5];
+} sc_factor_info;
+
+/* Numeric factorization (Sec. 1 step 3): Alg. 5 (RLB) or Alg. 4 (RL) as set
+ * in the symbolic handle's options, on the GPU.
+ *   s                symbolic handle (from sc_analyze)
+ *   values           FP64 values aligned with the rowind given to sc_analyze;
+ *                    host memory if values_on_device == 0, device memory otherwise
+ *   precision        enum sc_precision, or -1 for the handle's option
+ *   cuda_stream      stream for the device work
+ *   out              receives a new numeric handle (device memory is allocated)
+ *   info             optional (may be NULL)
+ * Returns SC_OK, a positive column index when A is not positive definite
+ * (the handle is still returned so it can be freed or refactored), or an
+ * error code. Synchronises cuda_stream. */
+int sc_factor(sc_symbolic *s, const double *values, int values_on_device, int precision,
+              void *cuda_stream, sc_numeric **out, sc_factor_info *info);
+
+/* Refactors an existing numeric handle with new values of the same pattern,
+ * reusing its device memory and its captured launch schedule. Same argument
+ * meaning and return codes as sc_factor. Synchronises cuda_stream. */
+int sc_refactor(sc_numeric *h, const double *values, int values_on_device, void *cuda_stream,
+                sc_factor_info *info);
+
+typedef struct sc_solve_info {
+    int32_t iterations;    /* refinement iterations (0 for a plain FP64 solve)   */
+    int32_t converged;     /* 1 if max backward error <= ir_tol                  */
+    double eta_max;        /* max over right-hand sides of the backward error    */
+    double solve_ms;       /* device time of the whole solve incl. refinement    */
+    double *eta;           /* optional [nrhs] output, caller-owned host memory   */
+    int32_t refine;        /* in: 1 = refine even for an FP64 factor (-1 = by precision) */
+    int32_t kernel_launches; /* out: kernels launched by this solve                */
+    int32_t reserved[4];
+} sc_solve_info;
+
+/* Solves A X = B (Sec. 1 step 4): permute, forward solve with L, backward
+ * solve with L^T, un-permute; with a low-precision factor (or refine = 1),
+ * iterative refinement in FP64 until the backward error
+ *   eta = ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf)
+ * is at most ir_tol for every column, or ir_maxit iterations.
+ *   h        numeric handle
+ *   nrhs     number of right-hand sides (>= 1)
+ *   B, ldb   n x nrhs column-major FP64 right-hand sides
+ *   X, ldx   n x nrhs column-major FP64 solution (may not alias B)
+ *   on_device  1 if B and X are device pointers, 0 if host pointers
+ *   info     optional; its eta field, when set, receives nrhs values
+ * Returns SC_OK, SC_ERR_NOT_CONVERGED (X holds the best iterate), or an
+ * error code. Synchronises cuda_stream. */
+int sc_solve(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, double *X, int64_t ldx,
+             int on_device, void *cuda_stream, sc_solve_info *info);
+
+/* Batched symbolic analysis for many independent matrices (the batch is
+ * factored as one block-diagonal problem whose levels are aligned by height,
+ * so every level of every matrix is in one launch sequence).
+ *   count    number of matrices (>= 1)
+ *   syms     count symbolic handles (each from sc_analyze); not consumed
+ *   out      receives the combined handle; its unknowns are the matrices'
+ *            unknowns concatenated in order, and its values array is the
+ *            matrices' values arrays concatenated in order.
+ * Errors: -1..-3, SC_ERR_OOM. */
+int sc_analyze_batch(int count, sc_symbolic *const *syms, sc_symbolic **out);
+
+/* Copies L to host memory in the canonical supernodal layout: for each
+ * supernode J, an m_J x |J| row-major block (row r = glbind(J)[r], column
+ * c = column f_J + c of the final ordering, entries above the diagonal 0),
+ * blocks concatenated in supernode order, as FP64. out must hold
+ * sum_J m_J |J| doubles. Synchronises the handle's last stream. */
+int sc_numeric_export_L(const sc_numeric *h, double *out);
+
+/* Per-kernel-class profile of one factorization, for roofline reporting: the
+ * factorization runs once outside the CUDA graph with CUDA events around every
+ * launch on cuda_stream. Each output array has SC_PROF_CLASSES entries, in the
+ * class order: value load (K0), POTRF, TRSM, SIMT products, tensor-core
+ * products, warp products, RL update matrices, RL assembly.
+ *   ms        summed device time per class (milliseconds, host array)
+ *   flops     algorithmic flops per class (2 per multiply-add; POTRF w^3/3,
+ *             TRSM rows * w^2; RL assembly counts one per added entry)
+ *   launches  launches per class
+ * Same values/stream conventions and return codes as sc_refactor. */
+#define SC_PROF_CLASSES 8
+int sc_factor_profile(sc_numeric *h, const double *values, int values_on_device, void *cuda_stream, double *ms,
+                      double *flops, int32_t *launches);
+
+/* Measured FMA throughput of the current GPU (the roofline denominator of the
+ * SIMT kernels): a kernel of independent FMA chains timed with CUDA events,
+ * best of three. kind 0 = FP64, 1 = FP32. Writes FLOP/s (2 per FMA) to
+ * *flops_per_s. Errors: -1 bad kind, -3 NULL output, SC_ERR_CUDA, SC_ERR_OOM. */
+int sc_probe_fma_peak(int kind, void *cuda_stream, double *flops_per_s);
+
+/* Frees h and its device memory. NULL is accepted. */
+void sc_numeric_free(sc_numeric *h);
+
+/* Human-readable text for a return code. Never NULL. */
+const char *sc_strerror(int code);
+
+/* Build identification: the CUDA architecture the kernels were compiled for. */
+const char *sc_build_info(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SC_H */

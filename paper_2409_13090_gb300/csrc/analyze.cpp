@@ -1,0 +1,586 @@
+// Host symbolic analysis of libsc (Sec. 1 steps 1-2, Sec. 2.1.2, Sec. 3.1 of
+// arXiv 2409.13090): ordering, elimination tree, postorder, column counts,
+// fundamental supernodes, supernodal elimination tree, partition refinement
+// within supernodes, relind(J,p(J)), blocks and relindB(J,P) (Alg. 5), levels,
+// factor-storage layout and the map from A's entries into it.
+//
+// Algorithms (chosen for O(nnz(L)) or better cost on multi-million-row inputs):
+//   - nested dissection on a grid with an explicit work stack;
+//   - elimination tree by Liu's algorithm with path compression;
+//   - column counts by marking the row subtrees of the elimination tree;
+//   - supernode structures by a union over child supernodes only;
+//   - partition refinement with an in-place, array-based partition;
+//   - relindB(J,P) by composition with relind(C,P), as in line 10 of Alg. 5.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
+#include "sc_internal.h"
+
+namespace sc {
+
+namespace {
+
+int validate(int64_t n, const int64_t *colptr, const int32_t *rowind) {
+    if (n <= 0 || n > INT32_MAX - 1) return -1;
+    if (!colptr) return -2;
+    if (!rowind) return -3;
+    if (colptr[0] != 0) return -2;
+    for (int64_t j = 0; j < n; j++) {
+        if (colptr[j + 1] <= colptr[j]) return -2;  // every column holds its diagonal
+        if (rowind[colptr[j]] != j) return -3;      // diagonal present and first
+        for (int64_t p = colptr[j] + 1; p < colptr[j + 1]; p++)
+            if (rowind[p] <= rowind[p - 1] || rowind[p] >= n) return -3;
+    }
+    return SC_OK;
+}
+
+// Geometric nested dissection: a box of volume <= leaf is emitted in
+// lexicographic order (x fastest); otherwise the longest axis (ties: x, y, z)
+// is split at m = lo + len/2 and the order is left box, right box, plane m.
+void grid_nd(int nx, int ny, int nz, int leaf, std::vector<int32_t> &perm) {
+    struct Box { int lo[3], hi[3]; bool sep; };
+    perm.clear();
+    perm.reserve((size_t)nx * ny * nz);
+    std::vector<Box> st;
+    st.push_back(Box{{0, 0, 0}, {nx, ny, nz}, false});
+    while (!st.empty()) {
+        Box b = st.back();
+        st.pop_back();
+        int len[3] = {b.hi[0] - b.lo[0], b.hi[1] - b.lo[1], b.hi[2] - b.lo[2]};
+        if (len[0] <= 0 || len[1] <= 0 || len[2] <= 0) continue;
+        int64_t vol = (int64_t)len[0] * len[1] * len[2];
+        if (b.sep || vol <= leaf) {
+            for (int z = b.lo[2]; z < b.hi[2]; z++)
+                for (int y = b.lo[1]; y < b.hi[1]; y++)
+                    for (int x = b.lo[0]; x < b.hi[0]; x++) perm.push_back(x + nx * (y + ny * z));
+            continue;
+        }
+        int ax = 0;
+        for (int d = 1; d < 3; d++)
+            if (len[d] > len[ax]) ax = d;
+        int m = b.lo[ax] + len[ax] / 2;
+        Box left = b, right = b, sep = b;
+        left.hi[ax] = m;
+        right.lo[ax] = m + 1;
+        sep.lo[ax] = m;
+        sep.hi[ax] = m + 1;
+        sep.sep = true;
+        // processed in the order left, right, separator (stack: push reversed)
+        st.push_back(sep);
+        st.push_back(right);
+        st.push_back(left);
+    }
+}
+
+// Full symmetric adjacency (no diagonal) of the lower-triangle CSC input.
+void build_adjacency(int64_t n, const int64_t *colptr, const int32_t *rowind, std::vector<int64_t> &ptr,
+                     std::vector<int32_t> &adj) {
+    ptr.assign(n + 1, 0);
+    for (int64_t j = 0; j < n; j++)
+        for (int64_t p = colptr[j] + 1; p < colptr[j + 1]; p++) {
+            ptr[rowind[p] + 1]++;
+            ptr[j + 1]++;
+        }
+    for (int64_t j = 0; j < n; j++) ptr[j + 1] += ptr[j];
+    adj.resize(ptr[n]);
+    std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+    for (int64_t j = 0; j < n; j++)
+        for (int64_t p = colptr[j] + 1; p < colptr[j + 1]; p++) {
+            int32_t i = rowind[p];
+            adj[fill[i]++] = (int32_t)j;
+            adj[fill[j]++] = i;
+        }
+}
+
+// Liu's elimination-tree algorithm with path compression, for the ordering
+// perm (new -> old). parent[] in new labels, -1 for roots.
+void etree_liu(int64_t n, const std::vector<int64_t> &aptr, const std::vector<int32_t> &adj,
+               const std::vector<int32_t> &perm, const std::vector<int32_t> &iperm, std::vector<int32_t> &parent) {
+    parent.assign(n, -1);
+    std::vector<int32_t> anc(n, -1);
+    for (int64_t i = 0; i < n; i++) {
+        int32_t io = perm[i];
+        for (int64_t p = aptr[io]; p < aptr[io + 1]; p++) {
+            int32_t k = iperm[adj[p]];
+            if (k >= i) continue;
+            int32_t r = k;
+            while (anc[r] != -1 && anc[r] != i) {
+                int32_t t = anc[r];
+                anc[r] = (int32_t)i;
+                r = t;
+            }
+            if (anc[r] == -1) {
+                anc[r] = (int32_t)i;
+                parent[r] = (int32_t)i;
+            }
+        }
+    }
+}
+
+// Postorder: DFS from the roots in ascending order, children in ascending
+// order; post[k] = the k-th vertex to finish.
+void postorder(int64_t n, const std::vector<int32_t> &parent, std::vector<int32_t> &post) {
+    std::vector<int32_t> head(n, -1), next(n, -1);
+    for (int64_t j = n - 1; j >= 0; j--)
+        if (parent[j] >= 0) {
+            next[j] = head[parent[j]];
+            head[parent[j]] = (int32_t)j;
+        }
+    post.clear();
+    post.reserve(n);
+    std::vector<int32_t> stack;
+    std::vector<int32_t> cur(n);
+    for (int64_t r = 0; r < n; r++) {
+        if (parent[r] != -1) continue;
+        stack.push_back((int32_t)r);
+        cur[r] = head[r];
+        while (!stack.empty()) {
+            int32_t v = stack.back();
+            int32_t c = cur[v];
+            if (c != -1) {
+                cur[v] = next[c];
+                cur[c] = head[c];
+                stack.push_back(c);
+            } else {
+                post.push_back(v);
+                stack.pop_back();
+            }
+        }
+    }
+}
+
+// Partition refinement of one supernode (the PR method cited in Sec. 1 and
+// Sec. 3.1; its steps are not printed in the paper). Start from the parts
+// [all columns, ascending]; for each set R (a descendant's rows inside this
+// supernode, descendants in ascending order), split every part X that R cuts
+// into X n R and X \ R, kept adjacent; X n R goes last when R meets a part
+// after X and none before it, first otherwise; each part stays ascending.
+// sets: local column indices. Output order[pos] = local column at position pos.
+void refine(int32_t size, const std::vector<std::vector<int32_t>> &sets, std::vector<int32_t> &order) {
+    order.resize(size);
+    std::iota(order.begin(), order.end(), 0);
+    std::vector<int32_t> where(size), part_of(size, 0);
+    std::iota(where.begin(), where.end(), 0);
+    std::vector<int32_t> pstart{0}, pend{size};
+    std::vector<int32_t> cnt(1, 0);
+    std::vector<char> inR(size, 0);
+    std::vector<int32_t> touched, tmp_in, tmp_out;
+    for (const auto &R : sets) {
+        touched.clear();
+        for (int32_t x : R) {
+            inR[x] = 1;
+            int32_t p = part_of[where[x]];
+            if (cnt[p]++ == 0) touched.push_back(p);
+        }
+        std::sort(touched.begin(), touched.end(), [&](int32_t a, int32_t b) { return pstart[a] < pstart[b]; });
+        for (size_t t = 0; t < touched.size(); t++) {
+            int32_t p = touched[t];
+            int32_t s = pstart[p], e = pend[p];
+            if (cnt[p] == e - s) continue;
+            bool before = t > 0, after = t + 1 < touched.size();
+            tmp_in.clear();
+            tmp_out.clear();
+            for (int32_t q = s; q < e; q++) (inR[order[q]] ? tmp_in : tmp_out).push_back(order[q]);
+            const std::vector<int32_t> &first = (after && !before) ? tmp_out : tmp_in;
+            const std::vector<int32_t> &second = (after && !before) ? tmp_in : tmp_out;
+            int32_t q = s;
+            for (int32_t x : first) { order[q] = x; where[x] = q; q++; }
+            int32_t split = q;
+            for (int32_t x : second) { order[q] = x; where[x] = q; q++; }
+            int32_t np = (int32_t)pstart.size();
+            pstart.push_back(split);
+            pend.push_back(e);
+            cnt.push_back(0);
+            pend[p] = split;
+            for (int32_t r = split; r < e; r++) part_of[r] = np;
+        }
+        for (int32_t p : touched) cnt[p] = 0;
+        for (int32_t x : R) inR[x] = 0;
+    }
+}
+
+}  // namespace
+
+int compose_relind(const int32_t *rJC, int64_t lenJC, const int32_t *rCP, int64_t lenCP, int32_t *out) {
+    if (!rJC) return -1;
+    if (lenJC < 0) return -2;
+    if (!rCP) return -3;
+    if (lenCP < 0) return -4;
+    if (!out) return -5;
+    for (int64_t k = 0; k < lenJC; k++) {
+        int64_t d = rJC[k];
+        if (d < 0 || d >= lenCP) return -1;
+        out[k] = rCP[lenCP - 1 - d];
+    }
+    return SC_OK;
+}
+
+int analyze_impl(int64_t n, const int64_t *colptr, const int32_t *rowind, const sc_options &o, sc_symbolic **out) {
+    int rc = validate(n, colptr, rowind);
+    if (rc) return rc;
+    auto s = std::make_unique<sc_symbolic>();
+    s->n = n;
+    s->opt = o;
+    int64_t nnzA = colptr[n];
+    s->colptr.assign(colptr, colptr + n + 1);
+    s->rowind.assign(rowind, rowind + nnzA);
+
+    // ---- step 1: ordering
+    std::vector<int32_t> p0;
+    if (o.ordering == SC_ORDER_GRID_ND) {
+        if ((int64_t)o.grid[0] * o.grid[1] * o.grid[2] != n || o.grid[0] <= 0 || o.grid[1] <= 0 || o.grid[2] <= 0 ||
+            o.nd_leaf < 1)
+            return -4;
+        grid_nd(o.grid[0], o.grid[1], o.grid[2], o.nd_leaf, p0);
+    } else if (o.ordering == SC_ORDER_USER) {
+        if (!o.user_perm) return -4;
+        p0.assign(o.user_perm, o.user_perm + n);
+        std::vector<char> seen(n, 0);
+        for (int64_t k = 0; k < n; k++) {
+            if (p0[k] < 0 || p0[k] >= n || seen[p0[k]]) return -4;
+            seen[p0[k]] = 1;
+        }
+    } else if (o.ordering == SC_ORDER_NATURAL) {
+        p0.resize(n);
+        std::iota(p0.begin(), p0.end(), 0);
+    } else {
+        return -4;
+    }
+    std::vector<int64_t> aptr;
+    std::vector<int32_t> adj;
+    build_adjacency(n, colptr, rowind, aptr, adj);
+    std::vector<int32_t> ip0(n);
+    for (int64_t k = 0; k < n; k++) ip0[p0[k]] = (int32_t)k;
+
+    // ---- elimination tree and postorder
+    std::vector<int32_t> par0;
+    etree_liu(n, aptr, adj, p0, ip0, par0);
+    std::vector<int32_t> post;
+    postorder(n, par0, post);
+    std::vector<int32_t> p1(n), ip1(n), newof(n);
+    for (int64_t k = 0; k < n; k++) {
+        p1[k] = p0[post[k]];
+        newof[post[k]] = (int32_t)k;
+    }
+    for (int64_t k = 0; k < n; k++) ip1[p1[k]] = (int32_t)k;
+    std::vector<int32_t> parent(n);
+    for (int64_t k = 0; k < n; k++) parent[k] = par0[post[k]] < 0 ? -1 : newof[par0[post[k]]];
+
+    // ---- column counts (row-subtree marking)
+    std::vector<int64_t> cc(n, 1);
+    {
+        std::vector<int32_t> mark(n, -1);
+        for (int64_t i = 0; i < n; i++) {
+            mark[i] = (int32_t)i;
+            int32_t io = p1[i];
+            for (int64_t p = aptr[io]; p < aptr[io + 1]; p++) {
+                int32_t j = ip1[adj[p]];
+                if (j >= i) continue;
+                while (mark[j] != i) {
+                    mark[j] = (int32_t)i;
+                    cc[j]++;
+                    j = parent[j];
+                }
+            }
+        }
+    }
+
+    // ---- fundamental supernodes
+    std::vector<int32_t> nchild(n, 0);
+    for (int64_t j = 0; j < n; j++)
+        if (parent[j] >= 0) nchild[parent[j]]++;
+    std::vector<int32_t> &sup_ptr = s->sup_ptr;
+    sup_ptr.clear();
+    for (int64_t j = 0; j < n; j++) {
+        bool joins = j > 0 && parent[j - 1] == j && nchild[j] == 1 && cc[j - 1] == cc[j] + 1;
+        if (!joins) sup_ptr.push_back((int32_t)j);
+    }
+    sup_ptr.push_back((int32_t)n);
+    int64_t ns = (int64_t)sup_ptr.size() - 1;
+    s->nsuper = ns;
+    std::vector<int32_t> &sup_of = s->sup_of;
+    sup_of.resize(n);
+    for (int64_t J = 0; J < ns; J++)
+        for (int32_t j = sup_ptr[J]; j < sup_ptr[J + 1]; j++) sup_of[j] = (int32_t)J;
+
+    // ---- supernode structures S_J (pre-PR labels), union over child supernodes
+    std::vector<int64_t> sptr(ns + 1, 0);
+    std::vector<int32_t> srows;
+    srows.reserve(n * 4);
+    std::vector<int32_t> spar(ns, -1);
+    std::vector<int32_t> chead(ns, -1), cnext(ns, -1), ctail(ns, -1);
+    {
+        std::vector<int32_t> mark(n, -1);
+        std::vector<int32_t> lst;
+        for (int64_t J = 0; J < ns; J++) {
+            int32_t f = sup_ptr[J], l = sup_ptr[J + 1] - 1;
+            lst.clear();
+            for (int32_t j = f; j <= l; j++) {
+                int32_t jo = p1[j];
+                for (int64_t p = aptr[jo]; p < aptr[jo + 1]; p++) {
+                    int32_t i = ip1[adj[p]];
+                    if (i > l && mark[i] != J) {
+                        mark[i] = (int32_t)J;
+                        lst.push_back(i);
+                    }
+                }
+            }
+            for (int32_t C = chead[J]; C != -1; C = cnext[C])
+                for (int64_t p = sptr[C]; p < sptr[C + 1]; p++) {
+                    int32_t i = srows[p];
+                    if (i > l && mark[i] != J) {
+                        mark[i] = (int32_t)J;
+                        lst.push_back(i);
+                    }
+                }
+            std::sort(lst.begin(), lst.end());
+            srows.insert(srows.end(), lst.begin(), lst.end());
+            sptr[J + 1] = (int64_t)srows.size();
+            // consistency with the column counts
+            int64_t m = (l - f + 1) + (int64_t)lst.size();
+            for (int32_t j = f; j <= l; j++)
+                if (cc[j] != m - (j - f)) return SC_ERR_INTERNAL;
+            if (!lst.empty()) {
+                int32_t P = sup_of[lst[0]];
+                spar[J] = P;
+                if (chead[P] == -1) chead[P] = (int32_t)J; else cnext[ctail[P]] = (int32_t)J;
+                ctail[P] = (int32_t)J;
+            }
+        }
+    }
+
+    // ---- partition refinement within supernodes (on the pre-PR structure)
+    std::vector<int32_t> p3 = p1;
+    if (o.pr) {
+        // R = S_J n P for each descendant J, grouped by P, ascending J
+        std::vector<int64_t> nsets(ns + 1, 0);
+        for (int64_t J = 0; J < ns; J++) {
+            int32_t last = -1;
+            for (int64_t p = sptr[J]; p < sptr[J + 1]; p++) {
+                int32_t P = sup_of[srows[p]];
+                if (P != last) { nsets[P + 1]++; last = P; }
+            }
+        }
+        for (int64_t P = 0; P < ns; P++) nsets[P + 1] += nsets[P];
+        std::vector<int64_t> set_owner_fill(nsets.begin(), nsets.end() - 1);
+        std::vector<int64_t> set_lo(nsets[ns]), set_hi(nsets[ns]);
+        for (int64_t J = 0; J < ns; J++) {
+            int64_t p = sptr[J];
+            while (p < sptr[J + 1]) {
+                int32_t P = sup_of[srows[p]];
+                int64_t q = p;
+                while (q < sptr[J + 1] && sup_of[srows[q]] == P) q++;
+                int64_t slot = set_owner_fill[P]++;
+                set_lo[slot] = p;
+                set_hi[slot] = q;
+                p = q;
+            }
+        }
+        std::vector<std::vector<int32_t>> sets;
+        std::vector<int32_t> order;
+        for (int64_t P = 0; P < ns; P++) {
+            int32_t f = sup_ptr[P], size = sup_ptr[P + 1] - f;
+            if (size < 2 || nsets[P + 1] == nsets[P]) continue;
+            sets.clear();
+            for (int64_t q = nsets[P]; q < nsets[P + 1]; q++) {
+                sets.emplace_back();
+                for (int64_t p = set_lo[q]; p < set_hi[q]; p++) sets.back().push_back(srows[p] - f);
+            }
+            refine(size, sets, order);
+            for (int32_t k = 0; k < size; k++) p3[f + k] = p1[f + order[k]];
+        }
+    }
+    // labels after PR
+    std::vector<int32_t> lab(n);  // lab[pre-PR label] = final label
+    {
+        std::vector<int32_t> ip3(n);
+        for (int64_t k = 0; k < n; k++) ip3[p3[k]] = (int32_t)k;
+        for (int64_t k = 0; k < n; k++) lab[k] = ip3[p1[k]];
+    }
+    s->perm = p3;
+    s->iperm.resize(n);
+    for (int64_t k = 0; k < n; k++) s->iperm[p3[k]] = (int32_t)k;
+
+    // ---- glbind(J) = J's columns followed by the relabelled S_J, ascending
+    s->gl_ptr.assign(ns + 1, 0);
+    for (int64_t J = 0; J < ns; J++)
+        s->gl_ptr[J + 1] = s->gl_ptr[J] + (sup_ptr[J + 1] - sup_ptr[J]) + (sptr[J + 1] - sptr[J]);
+    s->glbind.resize(s->gl_ptr[ns]);
+    for (int64_t J = 0; J < ns; J++) {
+        int64_t w = s->gl_ptr[J];
+        for (int32_t j = sup_ptr[J]; j < sup_ptr[J + 1]; j++) s->glbind[w++] = j;
+        int64_t b = w;
+        for (int64_t p = sptr[J]; p < sptr[J + 1]; p++) s->glbind[w++] = lab[srows[p]];
+        std::sort(s->glbind.begin() + b, s->glbind.begin() + w);
+    }
+    s->sup_parent = spar;
+    s->nnzL = 0;
+    s->flops = 0.0;
+    for (int64_t J = 0; J < ns; J++) {
+        int64_t m = s->gl_ptr[J + 1] - s->gl_ptr[J];
+        for (int32_t c = 0; c < sup_ptr[J + 1] - sup_ptr[J]; c++) {
+            s->nnzL += m - c;
+            s->flops += (double)(m - c) * (double)(m - c);
+        }
+    }
+    // column elimination tree of the final ordering
+    etree_liu(n, aptr, adj, s->perm, s->iperm, s->cparent);
+
+    // ---- relind(J, p(J)) through a position map of glbind(P) (Sec. 2.1.2)
+    s->ri_ptr.assign(ns + 1, 0);
+    for (int64_t J = 0; J < ns; J++) s->ri_ptr[J + 1] = s->ri_ptr[J] + (spar[J] >= 0 ? sptr[J + 1] - sptr[J] : 0);
+    s->relind.resize(s->ri_ptr[ns]);
+    {
+        std::vector<int32_t> dist(n, -1);
+        for (int64_t P = 0; P < ns; P++) {
+            if (chead[P] == -1) continue;
+            int64_t m = s->gl_ptr[P + 1] - s->gl_ptr[P];
+            for (int64_t q = 0; q < m; q++) dist[s->glbind[s->gl_ptr[P] + q]] = (int32_t)(m - 1 - q);
+            for (int32_t J = chead[P]; J != -1; J = cnext[J]) {
+                int64_t nJ = sup_ptr[J + 1] - sup_ptr[J];
+                int64_t w = s->ri_ptr[J];
+                for (int64_t p = s->gl_ptr[J] + nJ; p < s->gl_ptr[J + 1]; p++) {
+                    int32_t d = dist[s->glbind[p]];
+                    if (d < 0) return SC_ERR_INTERNAL;
+                    s->relind[w++] = d;
+                }
+            }
+            for (int64_t q = 0; q < m; q++) dist[s->glbind[s->gl_ptr[P] + q]] = -1;
+        }
+    }
+
+    // ---- blocks: maximal runs of consecutive rows of S_J, cut at supernode boundaries
+    s->blk_ptr.assign(ns + 1, 0);
+    for (int64_t J = 0; J < ns; J++) {
+        int64_t nJ = sup_ptr[J + 1] - sup_ptr[J];
+        int32_t prev = -2;
+        for (int64_t p = s->gl_ptr[J] + nJ; p < s->gl_ptr[J + 1]; p++) {
+            int32_t i = s->glbind[p];
+            if (i == prev + 1 && sup_of[i] == sup_of[prev]) {
+                s->blk_size.back()++;
+            } else {
+                s->blk_first.push_back(i);
+                s->blk_size.push_back(1);
+                s->blk_owner.push_back(sup_of[i]);
+            }
+            prev = i;
+        }
+        s->blk_ptr[J + 1] = (int64_t)s->blk_first.size();
+    }
+
+    // ---- relindB(J, P): extracted from relind(J, p(J)) (line 5 of Alg. 5), then
+    //      composed with relind(C, P) for each further ancestor (line 9)
+    s->rb_pair_ptr.assign(ns + 1, 0);
+    s->rb_val_ptr.assign(1, 0);
+    {
+        std::vector<int32_t> cur, nxt;
+        std::vector<int64_t> bpos;  // position in S_J of each block's first row
+        for (int64_t J = 0; J < ns; J++) {
+            int64_t b0 = s->blk_ptr[J], b1 = s->blk_ptr[J + 1];
+            if (b1 > b0) {
+                int64_t nJ = sup_ptr[J + 1] - sup_ptr[J];
+                // extract: relind of each block's top row
+                cur.clear();
+                int64_t q = 0;
+                for (int64_t b = b0; b < b1; b++) {
+                    cur.push_back(s->relind[s->ri_ptr[J] + q]);
+                    q += s->blk_size[b];
+                }
+                (void)nJ;
+                int32_t top = s->blk_owner[b1 - 1];
+                int64_t first_blk = b0;  // blocks at or above the current P
+                int32_t C = (int32_t)J;
+                for (int32_t P = spar[J]; P >= 0; P = spar[P]) {
+                    if (P != spar[J]) {
+                        // compose for the blocks lying below C: relindB(J,P) = relindB(J,C) o relind(C,P)
+                        int32_t lC = sup_ptr[C + 1] - 1;
+                        int64_t k0 = 0;
+                        while (first_blk + k0 < b1 && s->blk_first[first_blk + k0] <= lC) k0++;
+                        int64_t lenCP = s->ri_ptr[C + 1] - s->ri_ptr[C];
+                        nxt.resize(cur.size() - k0);
+                        int r = compose_relind(cur.data() + k0, (int64_t)nxt.size(), s->relind.data() + s->ri_ptr[C], lenCP,
+                                               nxt.data());
+                        if (r) return SC_ERR_INTERNAL;
+                        cur.swap(nxt);
+                        first_blk += k0;
+                    }
+                    s->rb_pair_P.push_back(P);
+                    s->rb_val.insert(s->rb_val.end(), cur.begin(), cur.end());
+                    s->rb_val_ptr.push_back((int64_t)s->rb_val.size());
+                    if (P == top) break;
+                    C = P;
+                }
+            }
+            s->rb_pair_ptr[J + 1] = (int64_t)s->rb_pair_P.size();
+        }
+    }
+
+    // ---- levels: height in the supernodal elimination tree
+    s->level.assign(ns, 0);
+    for (int64_t J = 0; J < ns; J++)
+        if (spar[J] >= 0 && s->level[spar[J]] < s->level[J] + 1) s->level[spar[J]] = s->level[J] + 1;
+
+    // ---- factor storage: J holds m_J rows of ld_J entries (row-major), at lnz_off[J].
+    //      Wide panels get ld a multiple of 4 and 128-byte aligned bases (tensor-memory copies).
+    s->lnz_off.resize(ns);
+    s->lnz_ld.resize(ns);
+    int64_t off = 0;
+    for (int64_t J = 0; J < ns; J++) {
+        int32_t w = sup_ptr[J + 1] - sup_ptr[J];
+        int64_t m = s->gl_ptr[J + 1] - s->gl_ptr[J];
+        int32_t ld = w >= 16 ? (w + 3) / 4 * 4 : w;
+        int64_t align = w >= 16 ? 32 : 4;
+        off = (off + align - 1) / align * align;
+        s->lnz_off[J] = off;
+        s->lnz_ld[J] = ld;
+        off += m * ld;
+    }
+    s->lnz_size = (off + 31) / 32 * 32;
+
+    // ---- map of A's entries into Lnz
+    s->valmap.resize(nnzA);
+    for (int64_t c = 0; c < n; c++)
+        for (int64_t p = colptr[c]; p < colptr[c + 1]; p++) {
+            int32_t a = s->iperm[rowind[p]], b = s->iperm[c];
+            int32_t col = std::min(a, b), row = std::max(a, b);
+            int32_t J = sup_of[col];
+            int32_t f = sup_ptr[J];
+            int64_t m = s->gl_ptr[J + 1] - s->gl_ptr[J];
+            const int32_t *g = s->glbind.data() + s->gl_ptr[J];
+            int64_t pos = std::lower_bound(g, g + m, row) - g;
+            if (pos >= m || g[pos] != row) return SC_ERR_INTERNAL;
+            s->valmap[p] = s->lnz_off[J] + pos * s->lnz_ld[J] + (col - f);
+        }
+
+    // ---- full symmetric CSR of A (caller's ordering) for the FP64 residual
+    s->csr_ptr.assign(n + 1, 0);
+    for (int64_t c = 0; c < n; c++)
+        for (int64_t p = colptr[c]; p < colptr[c + 1]; p++) {
+            s->csr_ptr[rowind[p] + 1]++;
+            if (rowind[p] != c) s->csr_ptr[c + 1]++;
+        }
+    for (int64_t i = 0; i < n; i++) s->csr_ptr[i + 1] += s->csr_ptr[i];
+    s->csr_col.resize(s->csr_ptr[n]);
+    s->csr_map.resize(s->csr_ptr[n]);
+    {
+        std::vector<int64_t> fill(s->csr_ptr.begin(), s->csr_ptr.end() - 1);
+        for (int64_t c = 0; c < n; c++)
+            for (int64_t p = colptr[c]; p < colptr[c + 1]; p++) {
+                int32_t i = rowind[p];
+                s->csr_col[fill[i]] = (int32_t)c;
+                s->csr_map[fill[i]++] = p;
+                if (i != c) {
+                    s->csr_col[fill[c]] = i;
+                    s->csr_map[fill[c]++] = p;
+                }
+            }
+    }
+
+    rc = build_schedule(s.get());
+    if (rc) return rc;
+    *out = s.release();
+    return SC_OK;
+}
+
+}  // namespace sc

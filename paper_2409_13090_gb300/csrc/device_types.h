@@ -1,0 +1,33 @@
+// Plain data types shared by the host launch plan and the device kernels.
+#pragma once
+#include <cstdint>
+
+#include "sc_internal.h"
+
+namespace sc {
+
+// Per-chunk data needed on the device.
+struct ChunkDev {
+    int64_t off;   // offset of the supernode's panel
+    int64_t gl;    // offset of glbind(J)
+    int32_t ld;    // panel leading dimension
+    int32_t m;     // rows of the panel (m_J)
+    int32_t c0;    // first local column of the chunk
+    int32_t w;     // chunk width
+    int32_t col0;  // global column of the chunk's first column
+    int32_t pad;
+};
+
+// One tile of the row-wise TRSM: rows [r0, min(r0+rows, m)) of chunk c.
+struct TrsmTile {
+    int32_t chunk, r0;
+};
+
+// One output tile of a product task.
+struct GemmTile {
+    int32_t task, tm, tn, pad;
+};
+
+constexpr int kMaxChunk = 64;
+
+}  // namespace sc

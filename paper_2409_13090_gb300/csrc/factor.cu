@@ -1,0 +1,413 @@
+// Numeric factorization of libsc on the GPU: builds the per-level launch plan
+// from the host schedule, owns the device memory of a numeric handle, and
+// runs the level sequence (Alg. 5 RLB or Alg. 4 RL, made level-parallel),
+// replayed as one CUDA graph.
+#include <algorithm>
+#include <cstring>
+
+#include "kernels.cuh"
+#include "numeric.h"
+#include "tc_gemm.cuh"
+
+namespace sc {
+
+#define SC_CUDA(x)                                  \
+    do {                                            \
+        cudaError_t e_ = (x);                       \
+        if (e_ != cudaSuccess) return SC_ERR_CUDA;  \
+    } while (0)
+
+namespace {
+
+constexpr int kBM = 64, kBN = 64, kBK = 16;
+
+// diagonal of the input matrix in the final ordering: adiag[k] = A(perm[k], perm[k])
+__global__ void k_diag(double *__restrict__ adiag, const int64_t *__restrict__ diag_pos,
+                       const double *__restrict__ values, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) adiag[i] = values[diag_pos[i]];
+}
+
+
+template <typename U>
+int upload(U *&dst, const std::vector<U> &src, int64_t &bytes) {
+    size_t b = std::max<size_t>(1, src.size()) * sizeof(U);
+    if (cudaMalloc((void **)&dst, b) != cudaSuccess) return SC_ERR_OOM;
+    bytes += (int64_t)b;
+    if (!src.empty() && cudaMemcpy(dst, src.data(), src.size() * sizeof(U), cudaMemcpyHostToDevice) != cudaSuccess)
+        return SC_ERR_CUDA;
+    return SC_OK;
+}
+
+bool is_small(const Task &t) { return (int64_t)t.m * t.n <= 64; }
+
+// algorithmic flops of a product task: 2 k per entry written
+double task_flops(const Task &t) {
+    double e = (t.flags & kTaskLower) ? (double)t.n * (t.n + 1) / 2 + (double)(t.m - t.n) * t.n : (double)t.m * t.n;
+    return 2.0 * e * t.k;
+}
+
+void tiles_of(const Task &t, int32_t id, std::vector<GemmTile> &out) {
+    int tm = (t.m + kBM - 1) / kBM, tn = (t.n + kBN - 1) / kBN;
+    for (int i = 0; i < tm; i++)
+        for (int j = 0; j < tn; j++) {
+            if ((t.flags & kTaskLower) && (i * kBM + kBM - 1) < j * kBN) continue;  // above the diagonal
+            out.push_back(GemmTile{id, i, j, 0});
+        }
+}
+
+// Optional per-kernel-class timing of one factorization (CUDA events around
+// every launch; only used outside graph capture).
+struct Prof {
+    cudaStream_t st = nullptr;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
+    int cur = -1;
+    void begin(int cls) {
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, st);
+        ev.push_back({cls, {a, b}});
+    }
+    void end() { cudaEventRecord(ev.back().second.second, st); }
+};
+
+template <typename T>
+int run_levels(sc_numeric *h, cudaStream_t st, Prof *prof = nullptr) {
+    const sc_symbolic *s = h->sym;
+    auto B = [&](int cls) {
+        if (prof) prof->begin(cls);
+    };
+    auto E = [&]() {
+        if (prof) prof->end();
+    };
+    T *lnz = (T *)h->d_lnz;
+    T *pool = (T *)h->d_pool;
+    int launches = 0;
+    B(kProfK0);
+    SC_CUDA(cudaMemsetAsync(h->d_lnz, 0, (size_t)s->lnz_size * sizeof(T), st));
+    SC_CUDA(cudaMemsetAsync(h->d_info, 0x7f, sizeof(int32_t), st));
+    SC_CUDA(cudaMemsetAsync(h->d_info + 1, 0, sizeof(int32_t), st));
+    int64_t nnz = (int64_t)s->valmap.size();
+    k_diag<<<(unsigned)((s->n + 255) / 256), 256, 0, st>>>(h->d_adiag, h->d_diagpos, h->d_values, s->n);
+    k_scatter_values<T><<<(unsigned)std::min<int64_t>((nnz + 255) / 256, 152 * 16), 256, 0, st>>>(
+        lnz, h->d_valmap, h->d_values, nnz);
+    E();
+    launches += 2;
+    const double tau = s->opt.pivot_tau;
+    for (const LevelPlan &p : h->plans) {
+        if (p.potrf_cnt) {
+            B(kProfPotrf);
+            k_potrf<T><<<p.potrf_cnt, 256, kPotrfSmem, st>>>(lnz, h->d_chunks, h->d_potrf + p.potrf_off, h->d_adiag,
+                                                              h->d_info, h->d_info + 1, tau);
+            E();
+            launches++;
+        }
+        if (p.trsm_cnt) {
+            B(kProfTrsm);
+            k_trsm<T><<<p.trsm_cnt, kTrsmRows, trsm_smem<T>(), st>>>(lnz, h->d_chunks, h->d_trsm + p.trsm_off);
+            E();
+            launches++;
+        }
+        if (p.gemm_cnt) {
+            B(kProfGemm);
+            k_gemm_tiles<T, kBM, kBN, kBK><<<p.gemm_cnt, 256, 0, st>>>(lnz, pool, h->d_tasks, h->d_gemm + p.gemm_off);
+            E();
+            launches++;
+        }
+        if (p.tc_cnt) {
+            B(kProfTc);
+            if (!launch_tc_gemm(lnz, pool, h->d_tasks, h->d_gemm + p.tc_off, p.tc_cnt, st)) return SC_ERR_UNSUPPORTED;
+            E();
+            launches++;
+        }
+        if (p.small_cnt) {
+            B(kProfSmall);
+            k_small_tasks<T><<<(p.small_cnt + 7) / 8, 256, 0, st>>>(lnz, pool, h->d_tasks, h->d_small + p.small_off,
+                                                                    p.small_cnt);
+            E();
+            launches++;
+        }
+        if (p.rlg_cnt) {
+            B(kProfRlUpd);
+            k_gemm_tiles<T, kBM, kBN, kBK><<<p.rlg_cnt, 256, 0, st>>>(lnz, pool, h->d_tasks, h->d_gemm + p.rlg_off);
+            E();
+            launches++;
+        }
+        if (p.rls_cnt) {
+            B(kProfRlUpd);
+            k_small_tasks<T><<<(p.rls_cnt + 7) / 8, 256, 0, st>>>(lnz, pool, h->d_tasks, h->d_small + p.rls_off,
+                                                                  p.rls_cnt);
+            E();
+            launches++;
+        }
+        for (int32_t q0 = 0; q0 < p.rlp_cnt; q0 += 65535) {  // grid.y holds at most 65535 pairs
+            unsigned gx = (unsigned)std::min<int64_t>((p.rlp_max + 255) / 256, 64);
+            unsigned gy = (unsigned)std::min<int32_t>(65535, p.rlp_cnt - q0);
+            B(kProfRlAsm);
+            k_rl_assemble<T><<<dim3(gx, gy), 256, 0, st>>>(lnz, pool, h->d_rlpairs + p.rlp_off + q0, h->d_rlrelind);
+            E();
+            launches++;
+        }
+    }
+    SC_CUDA(cudaGetLastError());
+    h->kernel_launches = launches;
+    return SC_OK;
+}
+
+int set_smem_attrs() {
+    static bool done = false;
+    if (done) return SC_OK;
+    SC_CUDA(cudaFuncSetAttribute(k_potrf<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPotrfSmem));
+    SC_CUDA(cudaFuncSetAttribute(k_potrf<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPotrfSmem));
+    SC_CUDA(cudaFuncSetAttribute(k_trsm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, trsm_smem<double>()));
+    SC_CUDA(cudaFuncSetAttribute(k_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, trsm_smem<float>()));
+    if (!tc_gemm_init()) return SC_ERR_CUDA;
+    done = true;
+    return SC_OK;
+}
+
+}  // namespace
+
+int numeric_create(sc_symbolic *s, int precision, sc_numeric **out) {
+    if (precision < SC_FP64 || precision > SC_TF32) return -3;
+    int rc = set_smem_attrs();
+    if (rc) return rc;
+    auto h = new sc_numeric();
+    h->sym = s;
+    h->precision = precision;
+    h->elt = precision == SC_FP64 ? 8 : 4;
+    h->use_graph = s->opt.use_graph != 0;
+    int64_t &bytes = h->device_bytes;
+    auto fail = [&](int code) {
+        numeric_free(h);
+        return code;
+    };
+    if (cudaMalloc(&h->d_lnz, (size_t)s->lnz_size * h->elt) != cudaSuccess) return fail(SC_ERR_OOM);
+    bytes += s->lnz_size * (int64_t)h->elt;
+    if (cudaMalloc(&h->d_pool, (size_t)std::max<int64_t>(1, s->rl_pool_max) * h->elt) != cudaSuccess)
+        return fail(SC_ERR_OOM);
+    bytes += std::max<int64_t>(1, s->rl_pool_max) * (int64_t)h->elt;
+    if ((rc = upload(h->d_valmap, s->valmap, bytes))) return fail(rc);
+    if (cudaMalloc((void **)&h->d_values, std::max<size_t>(1, s->valmap.size()) * sizeof(double)) != cudaSuccess)
+        return fail(SC_ERR_OOM);
+    bytes += (int64_t)s->valmap.size() * 8;
+    {
+        std::vector<int64_t> dp(s->n);
+        for (int64_t k = 0; k < s->n; k++) dp[k] = s->colptr[s->perm[k]];  // diagonal is first in its column
+        if ((rc = upload(h->d_diagpos, dp, bytes))) return fail(rc);
+    }
+    if (cudaMalloc((void **)&h->d_adiag, (size_t)s->n * sizeof(double)) != cudaSuccess) return fail(SC_ERR_OOM);
+    if (cudaMalloc((void **)&h->d_info, 2 * sizeof(int32_t)) != cudaSuccess) return fail(SC_ERR_OOM);
+
+    // chunks
+    std::vector<ChunkDev> cd(s->chunks.size());
+    for (size_t c = 0; c < s->chunks.size(); c++) {
+        const Chunk &ch = s->chunks[c];
+        int32_t J = ch.sn;
+        cd[c] = ChunkDev{s->lnz_off[J], s->gl_ptr[J], s->lnz_ld[J], (int32_t)(s->gl_ptr[J + 1] - s->gl_ptr[J]), ch.c0,
+                         ch.w, s->sup_ptr[J] + ch.c0, 0};
+    }
+    if ((rc = upload(h->d_chunks, cd, bytes))) return fail(rc);
+
+    // per-level work lists
+    std::vector<int32_t> potrf, small;
+    std::vector<TrsmTile> trsm;
+    std::vector<GemmTile> gemm;
+    std::vector<Task> tasks;
+    std::vector<RLPair> rlpairs;
+    const bool tc = precision == SC_TF32;
+    h->plans.resize(s->levels.size());
+    for (size_t lv = 0; lv < s->levels.size(); lv++) {
+        const Level &L = s->levels[lv];
+        LevelPlan &p = h->plans[lv];
+        p.potrf_off = (int32_t)potrf.size();
+        for (int32_t c : L.chunks) {
+            potrf.push_back(c);
+            double w = cd[c].w;
+            h->class_flops[kProfPotrf] += w * w * w / 3.0;
+            h->class_flops[kProfTrsm] += (double)(cd[c].m - cd[c].c0 - cd[c].w) * w * w;
+        }
+        p.potrf_cnt = (int32_t)potrf.size() - p.potrf_off;
+        p.trsm_off = (int32_t)trsm.size();
+        for (int32_t c : L.chunks) {
+            const ChunkDev &ch = cd[c];
+            for (int32_t r0 = ch.c0 + ch.w; r0 < ch.m; r0 += kTrsmRows) trsm.push_back(TrsmTile{c, r0});
+        }
+        p.trsm_cnt = (int32_t)trsm.size() - p.trsm_off;
+        // product tasks: tensor-core tiles (TF32), SIMT tiles, warp tasks
+        std::vector<int32_t> ids_small;
+        std::vector<GemmTile> g_simt, g_tc;
+        for (const Task &t : L.tasks) {
+            int32_t id = (int32_t)tasks.size();
+            tasks.push_back(t);
+            if (is_small(t)) {
+                ids_small.push_back(id);
+                h->class_flops[kProfSmall] += task_flops(t);
+            } else if (tc && tc_eligible(t)) {
+                tc_tiles_of(t, id, g_tc);
+                h->class_flops[kProfTc] += task_flops(t);
+            } else {
+                tiles_of(t, id, g_simt);
+                h->class_flops[kProfGemm] += task_flops(t);
+            }
+        }
+        p.gemm_off = (int32_t)gemm.size();
+        gemm.insert(gemm.end(), g_simt.begin(), g_simt.end());
+        p.gemm_cnt = (int32_t)g_simt.size();
+        p.tc_off = (int32_t)gemm.size();
+        gemm.insert(gemm.end(), g_tc.begin(), g_tc.end());
+        p.tc_cnt = (int32_t)g_tc.size();
+        p.small_off = (int32_t)small.size();
+        small.insert(small.end(), ids_small.begin(), ids_small.end());
+        p.small_cnt = (int32_t)ids_small.size();
+        // RL update matrices and assembly
+        std::vector<int32_t> rl_small;
+        std::vector<GemmTile> rl_g;
+        for (const Task &t : L.rl_tasks) {
+            int32_t id = (int32_t)tasks.size();
+            tasks.push_back(t);
+            if (is_small(t)) rl_small.push_back(id);
+            else tiles_of(t, id, rl_g);
+            h->class_flops[kProfRlUpd] += task_flops(t);
+        }
+        p.rlg_off = (int32_t)gemm.size();
+        gemm.insert(gemm.end(), rl_g.begin(), rl_g.end());
+        p.rlg_cnt = (int32_t)rl_g.size();
+        p.rls_off = (int32_t)small.size();
+        small.insert(small.end(), rl_small.begin(), rl_small.end());
+        p.rls_cnt = (int32_t)rl_small.size();
+        p.rlp_off = (int32_t)rlpairs.size();
+        for (const RLPair &pr : L.rl_pairs) {
+            rlpairs.push_back(pr);
+            p.rlp_max = std::max<int64_t>(p.rlp_max, (int64_t)(pr.c_end - pr.c_begin) * (pr.s - pr.c_begin));
+            h->class_flops[kProfRlAsm] += (double)(pr.c_end - pr.c_begin) * (pr.s - pr.c_begin);
+        }
+        p.rlp_cnt = (int32_t)L.rl_pairs.size();
+    }
+    h->ntasks = (int32_t)tasks.size();
+    if ((rc = upload(h->d_potrf, potrf, bytes))) return fail(rc);
+    if ((rc = upload(h->d_trsm, trsm, bytes))) return fail(rc);
+    if ((rc = upload(h->d_gemm, gemm, bytes))) return fail(rc);
+    if ((rc = upload(h->d_small, small, bytes))) return fail(rc);
+    if ((rc = upload(h->d_tasks, tasks, bytes))) return fail(rc);
+    if ((rc = upload(h->d_rlpairs, rlpairs, bytes))) return fail(rc);
+    if ((rc = upload(h->d_rlrelind, s->rl_relind, bytes))) return fail(rc);
+    s->refs++;
+    *out = h;
+    return SC_OK;
+}
+
+int numeric_factor(sc_numeric *h, const double *values, int on_device, cudaStream_t st, sc_factor_info *info) {
+    const sc_symbolic *s = h->sym;
+    int64_t nnz = (int64_t)s->valmap.size();
+    h->last_stream = st;
+    SC_CUDA(cudaMemcpyAsync(h->d_values, values, nnz * sizeof(double),
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    cudaEvent_t e0, e1;
+    SC_CUDA(cudaEventCreate(&e0));
+    SC_CUDA(cudaEventCreate(&e1));
+    SC_CUDA(cudaEventRecord(e0, st));
+    int rc = SC_OK;
+    if (h->use_graph) {
+        if (!h->gexec) {
+            // captured once on the handle's own stream (the legacy default stream
+            // cannot be captured), then replayed on the caller's stream
+            if (!h->cap_stream) SC_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+            cudaGraph_t g;
+            SC_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+            rc = h->precision == SC_FP64 ? run_levels<double>(h, h->cap_stream) : run_levels<float>(h, h->cap_stream);
+            cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &g);
+            if (rc) return rc;
+            SC_CUDA(ce);
+            SC_CUDA(cudaGraphInstantiate(&h->gexec, g, 0));
+            cudaGraphDestroy(g);
+        }
+        SC_CUDA(cudaGraphLaunch(h->gexec, st));
+    } else {
+        rc = h->precision == SC_FP64 ? run_levels<double>(h, st) : run_levels<float>(h, st);
+        if (rc) return rc;
+    }
+    SC_CUDA(cudaEventRecord(e1, st));
+    int32_t hinfo[2];
+    SC_CUDA(cudaMemcpyAsync(hinfo, h->d_info, sizeof(hinfo), cudaMemcpyDeviceToHost, st));
+    SC_CUDA(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int64_t failed = 0;
+    if (hinfo[0] != 0x7f7f7f7f) failed = (int64_t)s->perm[hinfo[0] - 1] + 1;
+    if (info) {
+        info->failed_col = failed;
+        info->precision = h->precision;
+        info->pivot_fallbacks = hinfo[1];
+        info->flops = s->flops;
+        info->factor_ms = ms;
+        info->device_bytes = h->device_bytes;
+        info->kernel_launches = h->kernel_launches;
+    }
+    return failed ? (int)std::min<int64_t>(failed, INT32_MAX) : SC_OK;
+}
+
+int numeric_profile(sc_numeric *h, const double *values, int on_device, cudaStream_t st, double *ms, double *flops,
+                    int32_t *launches) {
+    const sc_symbolic *s = h->sym;
+    int64_t nnz = (int64_t)s->valmap.size();
+    h->last_stream = st;
+    SC_CUDA(cudaMemcpyAsync(h->d_values, values, nnz * sizeof(double),
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    Prof prof;
+    prof.st = st;
+    int rc = h->precision == SC_FP64 ? run_levels<double>(h, st, &prof) : run_levels<float>(h, st, &prof);
+    SC_CUDA(cudaStreamSynchronize(st));
+    for (int c = 0; c < kProfClasses; c++) {
+        ms[c] = 0.0;
+        flops[c] = h->class_flops[c];
+        launches[c] = 0;
+    }
+    for (auto &e : prof.ev) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e.second.first, e.second.second);
+        ms[e.first] += t;
+        launches[e.first]++;
+        cudaEventDestroy(e.second.first);
+        cudaEventDestroy(e.second.second);
+    }
+    return rc;
+}
+
+int numeric_export_L(const sc_numeric *h, double *out) {
+    const sc_symbolic *s = h->sym;
+    if (h->last_stream) SC_CUDA(cudaStreamSynchronize(h->last_stream));
+    std::vector<unsigned char> buf((size_t)s->lnz_size * h->elt);
+    SC_CUDA(cudaMemcpy(buf.data(), h->d_lnz, buf.size(), cudaMemcpyDeviceToHost));
+    int64_t o = 0;
+    for (int64_t J = 0; J < s->nsuper; J++) {
+        int32_t w = s->sup_ptr[J + 1] - s->sup_ptr[J];
+        int64_t m = s->gl_ptr[J + 1] - s->gl_ptr[J];
+        for (int64_t r = 0; r < m; r++)
+            for (int32_t c = 0; c < w; c++) {
+                int64_t e = s->lnz_off[J] + r * s->lnz_ld[J] + c;
+                double v = h->elt == 8 ? ((const double *)buf.data())[e] : (double)((const float *)buf.data())[e];
+                out[o++] = r >= c ? v : 0.0;
+            }
+    }
+    return SC_OK;
+}
+
+void numeric_free(sc_numeric *h) {
+    if (!h) return;
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    void *ptrs[] = {h->d_lnz, h->d_pool, h->d_valmap, h->d_values, h->d_diagpos, h->d_adiag, h->d_info,
+                    h->d_chunks, h->d_potrf, h->d_trsm, h->d_gemm, h->d_small, h->d_tasks, h->d_rlpairs,
+                    h->d_rlrelind, h->d_glbind, h->d_perm, h->d_csr_ptr, h->d_csr_col, h->d_csr_val,
+                    h->d_csr_map, h->d_counters, h->d_xw, h->d_solve_tiles, h->d_x, h->d_r, h->d_b, h->d_xbest, h->d_y, h->d_z, h->d_acc, h->d_red};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (h->sym) h->sym->refs--;
+    delete h;
+}
+
+}  // namespace sc

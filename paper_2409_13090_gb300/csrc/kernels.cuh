@@ -1,0 +1,262 @@
+// Device kernels of the numeric factorization and the solve (SIMT part).
+// Factor storage: supernode J is a row-major m_J x ld_J panel at element offset
+// off_J of one buffer (row r = glbind(J)[r], column c = column f_J + c).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "device_types.h"
+
+namespace sc {
+
+
+
+// --------------------------------------------------------------------- K0
+template <typename T>
+__global__ void k_scatter_values(T *__restrict__ lnz, const int64_t *__restrict__ valmap,
+                                 const double *__restrict__ values, int64_t nnz) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (; i < nnz; i += stride) lnz[valmap[i]] = (T)values[i];
+}
+
+// --------------------------------------------------------------------- K1
+// POTRF of each chunk's w x w diagonal block (lower) in shared memory, column
+// by column, right-looking: pivot, scale the column, rank-1 update of the
+// trailing triangle.
+//   T = double: one pass in FP64; a pivot d <= 0 sets info.
+//   T = float : one pass in FP32. If some pivot d (before the square root)
+//               is <= tau * |A_jj| (A_jj = the diagonal entry of the input
+//               matrix), the block is refactored in FP64 from the same stored
+//               values and low_pivots is incremented; a pivot <= 0 in that
+//               pass sets info.
+// info receives the minimum failing column (1-based, final ordering).
+template <typename S>
+__device__ bool potrf_pass(S (*a)[kMaxChunk + 1], int w, const double *__restrict__ adiag, int col0, double tau,
+                           bool check_low, int32_t *__restrict__ info, int *flag) {
+    for (int k = 0; k < w; k++) {
+        if (threadIdx.x == 0) {
+            S d = a[k][k];
+            if (check_low) {
+                if (!((double)d > tau * fabs(adiag[col0 + k]))) *flag = 1;
+            } else if (!(d > S(0))) {
+                atomicMin(info, col0 + k + 1);
+                d = S(1);
+            }
+            if (!(d > S(0))) d = S(1);
+            a[k][k] = sqrt(d);
+        }
+        __syncthreads();
+        if (check_low && *flag) return false;
+        S dk = a[k][k];
+        for (int i = k + 1 + threadIdx.x; i < w; i += blockDim.x) a[i][k] /= dk;
+        __syncthreads();
+        int rem = w - k - 1;
+        for (int idx = threadIdx.x; idx < rem * rem; idx += blockDim.x) {
+            int i = k + 1 + idx / rem, j = k + 1 + idx % rem;
+            if (j <= i) a[i][j] -= a[i][k] * a[j][k];
+        }
+        __syncthreads();
+    }
+    return true;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_potrf(T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
+                                               const int32_t *__restrict__ list, const double *__restrict__ adiag,
+                                               int32_t *__restrict__ info, int32_t *__restrict__ low_pivots,
+                                               double tau) {
+    extern __shared__ double smem_potrf[];
+    __shared__ int flag;
+    const ChunkDev ch = chunks[list[blockIdx.x]];
+    const int w = ch.w;
+    T *base = lnz + ch.off + (int64_t)ch.c0 * ch.ld + ch.c0;
+    if (threadIdx.x == 0) flag = 0;
+    bool done = false;
+    if (sizeof(T) == 4) {
+        auto a = reinterpret_cast<float (*)[kMaxChunk + 1]>(smem_potrf);
+        for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
+            int r = idx / w, c = idx % w;
+            a[r][c] = (r >= c) ? (float)base[(int64_t)r * ch.ld + c] : 0.f;
+        }
+        __syncthreads();
+        done = potrf_pass<float>(a, w, adiag, ch.col0, tau, true, info, &flag);
+        if (done) {
+            for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
+                int r = idx / w, c = idx % w;
+                if (r >= c) base[(int64_t)r * ch.ld + c] = (T)a[r][c];
+            }
+            return;
+        }
+        if (threadIdx.x == 0) atomicAdd(low_pivots, 1);
+        __syncthreads();
+    }
+    auto a = reinterpret_cast<double (*)[kMaxChunk + 1]>(smem_potrf);
+    for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
+        int r = idx / w, c = idx % w;
+        a[r][c] = (r >= c) ? (double)base[(int64_t)r * ch.ld + c] : 0.0;
+    }
+    __syncthreads();
+    potrf_pass<double>(a, w, adiag, ch.col0, tau, false, info, &flag);
+    for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
+        int r = idx / w, c = idx % w;
+        if (r >= c) base[(int64_t)r * ch.ld + c] = (T)a[r][c];
+    }
+}
+constexpr int kPotrfSmem = kMaxChunk * (kMaxChunk + 1) * 8;
+
+// --------------------------------------------------------------------- K2
+// TRSM of the rows below each chunk's diagonal block: row x <- x L_cc^{-T},
+// one row per thread by forward substitution, in the storage precision.
+constexpr int kTrsmRows = 64;
+template <typename T>
+constexpr int trsm_smem() { return (int)sizeof(T) * kMaxChunk * (kMaxChunk + 1 + kTrsmRows + 1); }
+template <typename T>
+__global__ void __launch_bounds__(kTrsmRows) k_trsm(T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
+                                                    const TrsmTile *__restrict__ tiles) {
+    extern __shared__ __align__(16) unsigned char smem_trsm[];
+    auto l = reinterpret_cast<T (*)[kMaxChunk + 1]>(smem_trsm);
+    auto x = reinterpret_cast<T (*)[kTrsmRows + 1]>(smem_trsm + sizeof(T) * kMaxChunk * (kMaxChunk + 1));
+    const TrsmTile tl = tiles[blockIdx.x];
+    const ChunkDev ch = chunks[tl.chunk];
+    const int w = ch.w;
+    const T *diag = lnz + ch.off + (int64_t)ch.c0 * ch.ld + ch.c0;
+    for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
+        int r = idx / w, c = idx % w;
+        l[r][c] = r >= c ? diag[(int64_t)r * ch.ld + c] : T(0);
+    }
+    const int rows = min(kTrsmRows, ch.m - tl.r0);
+    T *rbase = lnz + ch.off + (int64_t)tl.r0 * ch.ld + ch.c0;
+    for (int idx = threadIdx.x; idx < rows * w; idx += blockDim.x) {
+        int r = idx / w, c = idx % w;
+        x[c][r] = rbase[(int64_t)r * ch.ld + c];
+    }
+    __syncthreads();
+    const int t = threadIdx.x;
+    if (t < rows) {
+        for (int k = 0; k < w; k++) {
+            T v = x[k][t] / l[k][k];
+            x[k][t] = v;
+            for (int j = k + 1; j < w; j++) x[j][t] -= v * l[j][k];
+        }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < rows * w; idx += blockDim.x) {
+        int r = idx / w, c = idx % w;
+        rbase[(int64_t)r * ch.ld + c] = x[c][r];
+    }
+}
+
+// --------------------------------------------------------------------- K3
+// Tiled product C -= A B^T (or C = -A B^T into an RL update matrix) on SIMT
+// FMA units. 256 threads, BM x BN tile, 4 x 4 outputs per thread. The
+// scatter into Lnz(P) is an atomic add: supernodes of one level may update the
+// same ancestor entries.
+template <typename T, int BM, int BN, int BK>
+__global__ void __launch_bounds__(256) k_gemm_tiles(T *__restrict__ lnz, T *__restrict__ pool,
+                                                    const Task *__restrict__ tasks,
+                                                    const GemmTile *__restrict__ tiles) {
+    static_assert(BM == 64 && BN == 64, "4x4 per thread over 16x16 threads");
+    __shared__ T As[BK][BM + 1];
+    __shared__ T Bs[BK][BN + 1];
+    const GemmTile tl = tiles[blockIdx.x];
+    const Task tk = tasks[tl.task];
+    const int row0 = tl.tm * BM, col0 = tl.tn * BN;
+    const T *A = lnz + tk.a_off;
+    const T *B = lnz + tk.b_off;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = T(0);
+    for (int k0 = 0; k0 < tk.k; k0 += BK) {
+        for (int idx = threadIdx.x; idx < BM * BK; idx += 256) {
+            int r = idx / BK, kk = idx % BK;
+            int gr = row0 + r, gk = k0 + kk;
+            As[kk][r] = (gr < tk.m && gk < tk.k) ? A[(int64_t)gr * tk.lds + gk] : T(0);
+        }
+        for (int idx = threadIdx.x; idx < BN * BK; idx += 256) {
+            int r = idx / BK, kk = idx % BK;
+            int gr = col0 + r, gk = k0 + kk;
+            Bs[kk][r] = (gr < tk.n && gk < tk.k) ? B[(int64_t)gr * tk.lds + gk] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; kk++) {
+            T a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; j++) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+    }
+    const bool lower = tk.flags & kTaskLower;
+    const bool store = tk.flags & kTaskStoreU;
+    T *C = (store ? pool : lnz) + tk.c_off;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        int gi = row0 + ty + 16 * i;
+        if (gi >= tk.m) continue;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            int gj = col0 + tx + 16 * j;
+            if (gj >= tk.n || (lower && gj > gi)) continue;
+            if (store) C[(int64_t)gi * tk.ldc + gj] = -acc[i][j];
+            else atomicAdd(C + (int64_t)gi * tk.ldc + gj, -acc[i][j]);
+        }
+    }
+}
+
+// Tiny product tasks: one warp per task, one output entry per lane step.
+template <typename T>
+__global__ void __launch_bounds__(256) k_small_tasks(T *__restrict__ lnz, T *__restrict__ pool,
+                                                     const Task *__restrict__ tasks,
+                                                     const int32_t *__restrict__ list, int32_t count) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    int lane = threadIdx.x % 32;
+    if (warp >= count) return;
+    const Task tk = tasks[list[warp]];
+    const bool lower = tk.flags & kTaskLower;
+    const bool store = tk.flags & kTaskStoreU;
+    T *C = (store ? pool : lnz) + tk.c_off;
+    const int total = tk.m * tk.n;
+    for (int e = lane; e < total; e += 32) {
+        int i = e / tk.n, j = e % tk.n;
+        if (lower && j > i) continue;
+        const T *a = lnz + tk.a_off + (int64_t)i * tk.lds;
+        const T *b = lnz + tk.b_off + (int64_t)j * tk.lds;
+        T acc = T(0);
+        for (int k = 0; k < tk.k; k++) acc += a[k] * b[k];
+        if (store) C[(int64_t)i * tk.ldc + j] = -acc;
+        else atomicAdd(C + (int64_t)i * tk.ldc + j, -acc);
+    }
+}
+
+// --------------------------------------------------------------------- K4b
+// RL assembly (Alg. 4, line 13): for every column c of U_J inside P and every
+// row r >= c, Lnz(P)[m_P-1-relind[r]][m_P-1-relind[c]] += U_J[r][c].
+template <typename T>
+__global__ void k_rl_assemble(T *__restrict__ lnz, const T *__restrict__ pool, const RLPair *__restrict__ pairs,
+                              const int32_t *__restrict__ relind) {
+    const RLPair pr = pairs[blockIdx.y];
+    const int32_t *ri = relind + pr.ri_off;  // entries for rows c_begin..s-1
+    const int ncols = pr.c_end - pr.c_begin;
+    const int nrows = pr.s - pr.c_begin;
+    const int64_t total = (int64_t)ncols * nrows;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        int cc = (int)(e / nrows), rr = (int)(e % nrows);
+        if (rr < cc) continue;
+        int c = pr.c_begin + cc, r = pr.c_begin + rr;
+        int64_t prow = pr.mP - 1 - ri[rr];
+        int64_t pcol = pr.mP - 1 - ri[cc];
+        atomicAdd(lnz + pr.p_off + prow * pr.ldp + pcol, pool[pr.u_off + (int64_t)r * pr.s + c]);
+    }
+}
+
+}  // namespace sc

@@ -1,0 +1,97 @@
+// Numeric handle of libsc: device buffers and the launch plan of one
+// factorization (factor.cu) and of the solve (solve.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "device_types.h"
+#include "sc_internal.h"
+
+namespace sc {
+
+// Launch plan of one level: offsets/counts into the flat device work lists.
+struct LevelPlan {
+    int32_t potrf_off = 0, potrf_cnt = 0;   // chunk ids
+    int32_t trsm_off = 0, trsm_cnt = 0;     // TrsmTile
+    int32_t gemm_off = 0, gemm_cnt = 0;     // GemmTile (SIMT)
+    int32_t tc_off = 0, tc_cnt = 0;         // GemmTile (tensor cores)
+    int32_t small_off = 0, small_cnt = 0;   // task ids (warp kernel)
+    int32_t rlg_off = 0, rlg_cnt = 0;       // GemmTile of RL update matrices
+    int32_t rls_off = 0, rls_cnt = 0;       // task ids of small RL update matrices
+    int32_t rlp_off = 0, rlp_cnt = 0;       // RLPair
+    int64_t rlp_max = 0;                    // largest assembly work item (elements)
+    // solve
+    int32_t sv_off = 0, sv_cnt = 0;         // TrsmTile-like (chunk, row start) for the below-diagonal sweeps
+};
+
+// kernel classes of the per-kernel profile
+enum { kProfK0 = 0, kProfPotrf, kProfTrsm, kProfGemm, kProfTc, kProfSmall, kProfRlUpd, kProfRlAsm, kProfClasses };
+
+template <typename T>
+struct DevArray {
+    T *p = nullptr;
+    int64_t n = 0;
+};
+
+}  // namespace sc
+
+struct sc_numeric {
+    sc_symbolic *sym = nullptr;
+    int precision = SC_FP64;
+    size_t elt = 8;
+    cudaStream_t last_stream = nullptr;
+    // device memory
+    void *d_lnz = nullptr;
+    void *d_pool = nullptr;
+    int64_t *d_valmap = nullptr;
+    double *d_values = nullptr;
+    int64_t *d_diagpos = nullptr;
+    double *d_adiag = nullptr;
+    int32_t *d_info = nullptr;  // [0] = failing column (min), [1] = low-precision pivot count
+    sc::ChunkDev *d_chunks = nullptr;
+    int32_t *d_potrf = nullptr;
+    sc::TrsmTile *d_trsm = nullptr;
+    sc::GemmTile *d_gemm = nullptr;
+    int32_t *d_small = nullptr;
+    sc::Task *d_tasks = nullptr;
+    sc::RLPair *d_rlpairs = nullptr;
+    int32_t *d_rlrelind = nullptr;
+    // solve
+    int32_t *d_glbind = nullptr;
+    int32_t *d_perm = nullptr;
+    int64_t *d_csr_ptr = nullptr;
+    int32_t *d_csr_col = nullptr;
+    double *d_csr_val = nullptr;
+    int64_t *d_csr_map = nullptr;
+    int32_t *d_counters = nullptr;  // [nchunks] backward-sweep counters, then [nchunks] tile counts
+    void *d_xw = nullptr;           // permuted right-hand side / forward work vector
+    sc::TrsmTile *d_solve_tiles = nullptr;
+    int64_t solve_cap = 0;          // rhs capacity of the work vectors
+    double *d_x = nullptr, *d_r = nullptr, *d_b = nullptr, *d_xbest = nullptr;
+    void *d_y = nullptr, *d_z = nullptr, *d_acc = nullptr;  // permuted work vectors (storage precision)
+    double *d_red = nullptr;        // reductions for eta
+    double anorm = 0.0;
+    bool solve_ready = false;
+    int64_t device_bytes = 0;
+    // plan
+    std::vector<sc::LevelPlan> plans;
+    int32_t ntasks = 0;
+    int32_t kernel_launches = 0;
+    double class_flops[sc::kProfClasses] = {};
+    // graph of the factorization (captured on first use on a stream)
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    bool use_graph = true;
+};
+
+namespace sc {
+int numeric_create(sc_symbolic *s, int precision, sc_numeric **out);
+int numeric_factor(sc_numeric *h, const double *values, int on_device, cudaStream_t st, sc_factor_info *info);
+int numeric_solve(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, double *X, int64_t ldx, int on_device,
+                  cudaStream_t st, sc_solve_info *info);
+int numeric_export_L(const sc_numeric *h, double *out);
+int numeric_profile(sc_numeric *h, const double *values, int on_device, cudaStream_t st, double *ms, double *flops,
+                    int32_t *launches);
+void numeric_free(sc_numeric *h);
+}  // namespace sc

@@ -1,0 +1,108 @@
+// Internal data structures of libsc shared by the host analysis and the CUDA
+// numeric path. Not part of the C ABI (include/sc.h is).
+#pragma once
+#include <atomic>
+#include <cstdint>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/sc.h"
+
+namespace sc {
+
+// Update task C[m x n] -= A[m x k] * B[n x k]^T on row-major panels.
+// A and B are row slabs of one source panel (leading dimension lds);
+// C is a dense block of the target panel (leading dimension ldc).
+// Offsets are element indices into the factor storage Lnz (or the RL pool
+// for C when kTaskStoreU is set).
+struct Task {
+    int64_t a_off, b_off, c_off;
+    int32_t lds, ldc, m, n, k, flags;
+};
+enum : int32_t {
+    kTaskLower = 1,   // only entries with local row >= local column are written
+    kTaskStoreU = 2,  // C is an RL update matrix: C = -A B^T (plain store, no accumulate)
+};
+
+// One panel of at most `chunk` columns of a supernode; the unit of the dense
+// work (POTRF, TRSM) and of the level schedule.
+struct Chunk {
+    int32_t sn;   // supernode
+    int32_t c0;   // first local column
+    int32_t w;    // columns
+    int32_t last; // 1 if this is the supernode's last chunk
+};
+
+// RL assembly of U_J's columns lying in ancestor P (Alg. 4, line 13).
+struct RLPair {
+    int64_t u_off;      // offset of U_J in the pool (row-major, ld = s)
+    int64_t p_off;      // offset of Lnz(P)
+    int64_t ri_off;     // offset into rl_relind of relind(J,P) for rows c_begin..s-1
+    int32_t s;          // |S_J|
+    int32_t c_begin;    // first row/column of U_J inside P
+    int32_t c_end;      // one past the last column of U_J inside P
+    int32_t ldp, mP, fP;
+    int32_t pad;
+};
+
+struct Level {
+    std::vector<int32_t> chunks;       // chunks factored at this level
+    std::vector<int32_t> last_chunks;  // of which: the last chunk of their supernode
+    std::vector<Task> tasks;           // RLB updates + intra-supernode trailing updates
+    std::vector<Task> rl_tasks;        // RL: U_J products (variant RL only)
+    std::vector<RLPair> rl_pairs;      // RL: assembly work (variant RL only)
+    int64_t rl_pool = 0;               // RL: pool elements needed by this level
+};
+
+}  // namespace sc
+
+struct sc_symbolic {
+    int64_t n = 0;
+    sc_options opt{};
+    // input pattern (lower, CSC) as given
+    std::vector<int64_t> colptr;
+    std::vector<int32_t> rowind;
+    // final ordering
+    std::vector<int32_t> perm, iperm, cparent;
+    // supernodal structure
+    int64_t nsuper = 0;
+    std::vector<int32_t> sup_ptr, sup_parent, level;
+    std::vector<int64_t> gl_ptr;
+    std::vector<int32_t> glbind;
+    std::vector<int64_t> ri_ptr;
+    std::vector<int32_t> relind;
+    std::vector<int64_t> blk_ptr;
+    std::vector<int32_t> blk_first, blk_size, blk_owner;
+    std::vector<int64_t> rb_pair_ptr;
+    std::vector<int32_t> rb_pair_P;
+    std::vector<int64_t> rb_val_ptr;
+    std::vector<int32_t> rb_val;
+    int64_t nnzL = 0;
+    double flops = 0.0;
+    // factor storage layout: supernode J occupies m_J rows x ld_J at element offset lnz_off[J]
+    std::vector<int64_t> lnz_off;
+    std::vector<int32_t> lnz_ld;
+    int64_t lnz_size = 0;
+    std::vector<int64_t> valmap;  // A entry p -> element offset in Lnz
+    std::vector<int32_t> sup_of;  // column -> supernode
+    // device schedule (precision independent)
+    std::vector<sc::Chunk> chunks;
+    std::vector<sc::Level> levels;
+    std::vector<int32_t> chunk_of_col;  // column -> chunk
+    std::vector<int32_t> rl_relind;     // RL: composed relind(J,P) lists
+    int64_t rl_pool_max = 0;
+    // full symmetric CSR of A in the caller's ordering (for the FP64 residual)
+    std::vector<int64_t> csr_ptr;
+    std::vector<int32_t> csr_col;
+    std::vector<int64_t> csr_map;  // CSR entry -> index into values
+    double anorm_inf_pattern = 0;  // unused placeholder
+    std::atomic<int> refs{0};
+};
+
+namespace sc {
+int analyze_impl(int64_t n, const int64_t *colptr, const int32_t *rowind, const sc_options &o,
+                 sc_symbolic **out);
+int build_schedule(sc_symbolic *s);
+int compose_relind(const int32_t *rJC, int64_t lenJC, const int32_t *rCP, int64_t lenCP, int32_t *out);
+}  // namespace sc

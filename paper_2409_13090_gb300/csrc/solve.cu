@@ -1,0 +1,417 @@
+// Triangular solves and iterative refinement of libsc (Sec. 1 step 4).
+//
+// Work vectors are kept in the final ordering, row-major n x nb (nb right-hand
+// sides of one block), in the storage precision of the factor.
+//   forward  (levels ascending):  y_c = L_cc^{-1} x_c ; x_rows -= L_{rows,c} y_c
+//   backward (levels descending): z_c = L_cc^{-T} (y_c - L_{rows,c}^T z_rows)
+// where c runs over the chunks of a level and rows over the panel rows below
+// the chunk (global row = glbind(J)[row]). The backward gather of a chunk is
+// spread over row tiles; the last tile to finish (per-chunk counter after a
+// memory fence) applies the diagonal solve, so each sweep is one launch per level.
+// Refinement: r = b - A x in FP64 on the caller's matrix (CSR), then
+//   eta = ||r||_inf / (||A||_inf ||x||_inf + ||b||_inf) per column, and
+//   x += solve(r) until eta <= ir_tol.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "kernels.cuh"
+#include "numeric.h"
+
+namespace sc {
+
+#define SC_CUDA(x)                                  \
+    do {                                            \
+        cudaError_t e_ = (x);                       \
+        if (e_ != cudaSuccess) return SC_ERR_CUDA;  \
+    } while (0)
+
+namespace {
+
+constexpr int kRhsBlk = 16;
+constexpr int kSolveRows = 64;
+
+template <typename T>
+constexpr int solve_smem() {
+    return (int)sizeof(T) * (kMaxChunk * (kMaxChunk + 1) + kMaxChunk * kRhsBlk);
+}
+
+// x_perm[k][r] = B[perm[k]][r0 + r]
+template <typename T>
+__global__ void k_perm_in(T *__restrict__ x, const double *__restrict__ B, int64_t ldb, const int32_t *__restrict__ perm,
+                          int64_t n, int nb, int r0) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n * nb) return;
+    int64_t k = i / nb;
+    int r = (int)(i % nb);
+    x[i] = (T)B[(int64_t)(r0 + r) * ldb + perm[k]];
+}
+
+// X[perm[k]][r0 + r] (+)= z_perm[k][r]
+template <typename T>
+__global__ void k_perm_out(double *__restrict__ X, int64_t ldx, const T *__restrict__ z, const int32_t *__restrict__ perm,
+                           int64_t n, int nb, int r0, int add) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n * nb) return;
+    int64_t k = i / nb;
+    int r = (int)(i % nb);
+    double *dst = X + (int64_t)(r0 + r) * ldx + perm[k];
+    *dst = add ? *dst + (double)z[i] : (double)z[i];
+}
+
+template <typename T>
+__device__ void load_diag(T (*l)[kMaxChunk + 1], const T *lnz, const ChunkDev &ch) {
+    const T *d = lnz + ch.off + (int64_t)ch.c0 * ch.ld + ch.c0;
+    for (int idx = threadIdx.x; idx < ch.w * ch.w; idx += blockDim.x) {
+        int r = idx / ch.w, c = idx % ch.w;
+        l[r][c] = r >= c ? d[(int64_t)r * ch.ld + c] : T(0);
+    }
+}
+
+// Forward sweep of one level (one launch). Each tile recomputes y_c for its chunk.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fwd(const T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
+                                             const TrsmTile *__restrict__ tiles, const int32_t *__restrict__ glbind,
+                                             T *__restrict__ x, T *__restrict__ y, int nb) {
+    extern __shared__ __align__(16) unsigned char smem_fwd[];
+    auto l = reinterpret_cast<T (*)[kMaxChunk + 1]>(smem_fwd);
+    auto v = reinterpret_cast<T (*)[kRhsBlk]>(smem_fwd + sizeof(T) * kMaxChunk * (kMaxChunk + 1));
+    const TrsmTile tl = tiles[blockIdx.x];
+    const ChunkDev ch = chunks[tl.chunk];
+    const int w = ch.w;
+    load_diag(l, lnz, ch);
+    for (int idx = threadIdx.x; idx < w * nb; idx += blockDim.x) {
+        int k = idx / nb, r = idx % nb;
+        v[k][r] = x[(int64_t)(ch.col0 + k) * nb + r];
+    }
+    __syncthreads();
+    for (int k = 0; k < w; k++) {
+        if (threadIdx.x < nb) v[k][threadIdx.x] /= l[k][k];
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < (w - k - 1) * nb; idx += blockDim.x) {
+            int i = k + 1 + idx / nb, r = idx % nb;
+            v[i][r] -= l[i][k] * v[k][r];
+        }
+        __syncthreads();
+    }
+    if (tl.r0 == ch.c0 + w) {  // the chunk's first tile writes y_c
+        for (int idx = threadIdx.x; idx < w * nb; idx += blockDim.x) {
+            int k = idx / nb, r = idx % nb;
+            y[(int64_t)(ch.col0 + k) * nb + r] = v[k][r];
+        }
+    }
+    const int rows = max(0, min(kSolveRows, ch.m - tl.r0));
+    for (int idx = threadIdx.x; idx < rows * nb; idx += blockDim.x) {
+        int i = idx / nb, r = idx % nb;
+        const T *lr = lnz + ch.off + (int64_t)(tl.r0 + i) * ch.ld + ch.c0;
+        T acc = T(0);
+        for (int k = 0; k < w; k++) acc += lr[k] * v[k][r];
+        int g = glbind[ch.gl + tl.r0 + i];
+        atomicAdd(x + (int64_t)g * nb + r, -acc);
+    }
+}
+
+// Backward sweep of one level (one launch): gather into acc, last tile solves.
+template <typename T>
+__global__ void __launch_bounds__(256) k_bwd(const T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
+                                             const TrsmTile *__restrict__ tiles, const int32_t *__restrict__ glbind,
+                                             const T *__restrict__ y, T *__restrict__ z, T *__restrict__ acc,
+                                             int32_t *__restrict__ counters, const int32_t *__restrict__ ntiles, int nb) {
+    extern __shared__ __align__(16) unsigned char smem_bwd[];
+    auto l = reinterpret_cast<T (*)[kMaxChunk + 1]>(smem_bwd);
+    auto v = reinterpret_cast<T (*)[kRhsBlk]>(smem_bwd + sizeof(T) * kMaxChunk * (kMaxChunk + 1));
+    __shared__ int last;
+    const TrsmTile tl = tiles[blockIdx.x];
+    const ChunkDev ch = chunks[tl.chunk];
+    const int w = ch.w;
+    const int rows = max(0, min(kSolveRows, ch.m - tl.r0));
+    if (rows > 0) {
+        for (int idx = threadIdx.x; idx < w * nb; idx += blockDim.x) {
+            int k = idx / nb, r = idx % nb;
+            const T *lc = lnz + ch.off + (int64_t)tl.r0 * ch.ld + ch.c0 + k;
+            T s = T(0);
+            for (int i = 0; i < rows; i++) s += lc[(int64_t)i * ch.ld] * z[(int64_t)glbind[ch.gl + tl.r0 + i] * nb + r];
+            atomicAdd(acc + (int64_t)(ch.col0 + k) * nb + r, s);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) last = (atomicAdd(counters + tl.chunk, 1) == ntiles[tl.chunk] - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    load_diag(l, lnz, ch);
+    for (int idx = threadIdx.x; idx < w * nb; idx += blockDim.x) {
+        int k = idx / nb, r = idx % nb;
+        int64_t g = (int64_t)(ch.col0 + k) * nb + r;
+        v[k][r] = y[g] - __ldcg(acc + g);
+    }
+    __syncthreads();
+    for (int k = w - 1; k >= 0; k--) {
+        if (threadIdx.x < nb) v[k][threadIdx.x] /= l[k][k];
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < k * nb; idx += blockDim.x) {
+            int j = idx / nb, r = idx % nb;
+            v[j][r] -= l[k][j] * v[k][r];
+        }
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < w * nb; idx += blockDim.x) {
+        int k = idx / nb, r = idx % nb;
+        z[(int64_t)(ch.col0 + k) * nb + r] = v[k][r];
+    }
+}
+
+__global__ void k_gather_vals(double *__restrict__ out, const double *__restrict__ values,
+                              const int64_t *__restrict__ map, int64_t nnz) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < nnz) out[i] = values[map[i]];
+}
+
+__device__ inline void atomic_max_nonneg(double *addr, double v) {
+    atomicMax((unsigned long long *)addr, (unsigned long long)__double_as_longlong(v));
+}
+
+// ||A||_inf of the full symmetric matrix from its CSR
+__global__ void k_anorm(const int64_t *__restrict__ ptr, const double *__restrict__ val, int64_t n, double *out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int64_t p = ptr[i]; p < ptr[i + 1]; p++) s += fabs(val[p]);
+    atomic_max_nonneg(out, s);
+}
+
+// r = b - A x (FP64), and per column: red[3c] = max|r|, red[3c+1] = max|x|, red[3c+2] = max|b|
+__global__ void k_residual(const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                           const double *__restrict__ val, const double *__restrict__ X, const double *__restrict__ B,
+                           double *__restrict__ R, int64_t n, int nrhs, double *__restrict__ red) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int c = blockIdx.y;
+    if (i >= n) return;
+    const double *x = X + (int64_t)c * n;
+    double s = B[(int64_t)c * n + i];
+    for (int64_t p = ptr[i]; p < ptr[i + 1]; p++) s -= val[p] * x[col[p]];
+    R[(int64_t)c * n + i] = s;
+    atomic_max_nonneg(red + 3 * c, fabs(s));
+    atomic_max_nonneg(red + 3 * c + 1, fabs(x[i]));
+    atomic_max_nonneg(red + 3 * c + 2, fabs(B[(int64_t)c * n + i]));
+}
+
+int ensure_solve(sc_numeric *h, int64_t nrhs) {
+    const sc_symbolic *s = h->sym;
+    int64_t n = s->n;
+    if (!h->solve_ready) {
+        auto up = [&](auto *&dst, const auto &src) -> int {
+            using U = typename std::remove_reference<decltype(src)>::type::value_type;
+            size_t b = std::max<size_t>(1, src.size()) * sizeof(U);
+            if (cudaMalloc((void **)&dst, b) != cudaSuccess) return SC_ERR_OOM;
+            h->device_bytes += (int64_t)b;
+            if (!src.empty() && cudaMemcpy(dst, src.data(), src.size() * sizeof(U), cudaMemcpyHostToDevice) != cudaSuccess)
+                return SC_ERR_CUDA;
+            return SC_OK;
+        };
+        int rc;
+        if ((rc = up(h->d_glbind, s->glbind))) return rc;
+        if ((rc = up(h->d_perm, s->perm))) return rc;
+        if ((rc = up(h->d_csr_ptr, s->csr_ptr))) return rc;
+        if ((rc = up(h->d_csr_col, s->csr_col))) return rc;
+        if ((rc = up(h->d_csr_map, s->csr_map))) return rc;
+        if (cudaMalloc((void **)&h->d_csr_val, std::max<size_t>(1, s->csr_col.size()) * 8) != cudaSuccess)
+            return SC_ERR_OOM;
+        // solve tiles: per level, per chunk, row tiles below the diagonal block
+        std::vector<TrsmTile> tiles;
+        std::vector<int32_t> ntiles(s->chunks.size(), 0);
+        for (size_t lv = 0; lv < s->levels.size(); lv++) {
+            LevelPlan &p = h->plans[lv];
+            p.sv_off = (int32_t)tiles.size();
+            for (int32_t c : s->levels[lv].chunks) {
+                const Chunk &ch = s->chunks[c];
+                int32_t m = (int32_t)(s->gl_ptr[ch.sn + 1] - s->gl_ptr[ch.sn]);
+                int32_t r0 = ch.c0 + ch.w;
+                if (r0 >= m) {
+                    tiles.push_back(TrsmTile{c, r0});
+                    ntiles[c] = 1;
+                }
+                for (; r0 < m; r0 += kSolveRows) {
+                    tiles.push_back(TrsmTile{c, r0});
+                    ntiles[c]++;
+                }
+            }
+            p.sv_cnt = (int32_t)tiles.size() - p.sv_off;
+        }
+        if ((rc = up(h->d_solve_tiles, tiles))) return rc;
+        // counters [nchunks] followed by tile counts [nchunks]
+        std::vector<int32_t> cnt2(2 * s->chunks.size(), 0);
+        std::copy(ntiles.begin(), ntiles.end(), cnt2.begin() + s->chunks.size());
+        if ((rc = up(h->d_counters, cnt2))) return rc;
+        if (cudaMalloc((void **)&h->d_red, 4096 * sizeof(double)) != cudaSuccess) return SC_ERR_OOM;
+        if (cudaFuncSetAttribute(k_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, solve_smem<double>()) ||
+            cudaFuncSetAttribute(k_bwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, solve_smem<double>()) ||
+            cudaFuncSetAttribute(k_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, solve_smem<float>()) ||
+            cudaFuncSetAttribute(k_bwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, solve_smem<float>()))
+            return SC_ERR_CUDA;
+        h->solve_ready = true;
+    }
+    if (nrhs > h->solve_cap) {
+        double **d64[] = {&h->d_x, &h->d_r, &h->d_b, &h->d_xbest};
+        for (double **p : d64) {
+            if (*p) cudaFree(*p);
+            if (cudaMalloc((void **)p, (size_t)n * nrhs * sizeof(double)) != cudaSuccess) return SC_ERR_OOM;
+        }
+        void **dw[] = {&h->d_y, &h->d_z, &h->d_acc};
+        for (void **p : dw) {
+            if (*p) cudaFree(*p);
+            if (cudaMalloc(p, (size_t)n * kRhsBlk * h->elt) != cudaSuccess) return SC_ERR_OOM;
+        }
+        if (h->d_xw) cudaFree(h->d_xw);
+        if (cudaMalloc(&h->d_xw, (size_t)n * kRhsBlk * h->elt) != cudaSuccess) return SC_ERR_OOM;
+        h->solve_cap = nrhs;
+    }
+    return SC_OK;
+}
+
+// One triangular solve with the factor: X = A^{-1} B (or X += A^{-1} B), B and X
+// column-major n x nrhs FP64 device arrays.
+template <typename T>
+int tri_solve(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, double *X, int64_t ldx, int add,
+              cudaStream_t st, int &launches) {
+    const sc_symbolic *s = h->sym;
+    const int64_t n = s->n;
+    const T *lnz = (const T *)h->d_lnz;
+    T *xw = (T *)h->d_xw, *y = (T *)h->d_y, *z = (T *)h->d_z, *acc = (T *)h->d_acc;
+    const size_t nch = s->chunks.size();
+    for (int64_t r0 = 0; r0 < nrhs; r0 += kRhsBlk) {
+        int nb = (int)std::min<int64_t>(kRhsBlk, nrhs - r0);
+        unsigned g = (unsigned)((n * nb + 255) / 256);
+        k_perm_in<T><<<g, 256, 0, st>>>(xw, B, ldb, h->d_perm, n, nb, (int)r0);
+        launches += 2;
+        for (size_t lv = 0; lv < h->plans.size(); lv++) {
+            const LevelPlan &p = h->plans[lv];
+            if (p.sv_cnt) {
+                k_fwd<T><<<p.sv_cnt, 256, solve_smem<T>(), st>>>(lnz, h->d_chunks, h->d_solve_tiles + p.sv_off,
+                                                                 h->d_glbind, xw, y, nb);
+                launches++;
+            }
+        }
+        SC_CUDA(cudaMemsetAsync(acc, 0, (size_t)n * nb * sizeof(T), st));
+        SC_CUDA(cudaMemsetAsync(h->d_counters, 0, nch * sizeof(int32_t), st));
+        for (size_t lv = h->plans.size(); lv-- > 0;) {
+            const LevelPlan &p = h->plans[lv];
+            if (p.sv_cnt) {
+                k_bwd<T><<<p.sv_cnt, 256, solve_smem<T>(), st>>>(lnz, h->d_chunks, h->d_solve_tiles + p.sv_off,
+                                                                 h->d_glbind, y, z, acc, h->d_counters,
+                                                                 h->d_counters + nch, nb);
+                launches++;
+            }
+        }
+        k_perm_out<T><<<g, 256, 0, st>>>(X, ldx, z, h->d_perm, n, nb, (int)r0, add);
+    }
+    SC_CUDA(cudaGetLastError());
+    return SC_OK;
+}
+
+int tri_solve_any(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, double *X, int64_t ldx, int add,
+                  cudaStream_t st, int &launches) {
+    return h->elt == 8 ? tri_solve<double>(h, nrhs, B, ldb, X, ldx, add, st, launches)
+                       : tri_solve<float>(h, nrhs, B, ldb, X, ldx, add, st, launches);
+}
+
+// eta per column for the current iterate in h->d_x; returns host values
+int backward_error(sc_numeric *h, int64_t nrhs, cudaStream_t st, std::vector<double> &eta, int &launches) {
+    const sc_symbolic *s = h->sym;
+    int64_t n = s->n;
+    SC_CUDA(cudaMemsetAsync(h->d_red, 0, 3 * nrhs * sizeof(double), st));
+    dim3 g((unsigned)((n + 255) / 256), (unsigned)nrhs);
+    k_residual<<<g, 256, 0, st>>>(h->d_csr_ptr, h->d_csr_col, h->d_csr_val, h->d_x, h->d_b, h->d_r, n, (int)nrhs,
+                                  h->d_red);
+    launches++;
+    std::vector<double> red(3 * nrhs);
+    SC_CUDA(cudaMemcpyAsync(red.data(), h->d_red, red.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SC_CUDA(cudaStreamSynchronize(st));
+    eta.resize(nrhs);
+    for (int64_t c = 0; c < nrhs; c++) {
+        double den = h->anorm * red[3 * c + 1] + red[3 * c + 2];
+        eta[c] = den > 0 ? red[3 * c] / den : 0.0;
+    }
+    return SC_OK;
+}
+
+}  // namespace
+
+int numeric_solve(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, double *X, int64_t ldx, int on_device,
+                  cudaStream_t st, sc_solve_info *info) {
+    const sc_symbolic *s = h->sym;
+    const int64_t n = s->n;
+    int rc = ensure_solve(h, nrhs);
+    if (rc) return rc;
+    h->last_stream = st;
+    if (nrhs > 1365) return -2;  // the reduction buffer holds 3 values per column (+ ||A||)
+    cudaEvent_t e0, e1;
+    SC_CUDA(cudaEventCreate(&e0));
+    SC_CUDA(cudaEventCreate(&e1));
+    SC_CUDA(cudaEventRecord(e0, st));
+    // b (column-major, ld = n) on the device
+    for (int64_t c = 0; c < nrhs; c++)
+        SC_CUDA(cudaMemcpyAsync(h->d_b + c * n, B + c * ldb, n * sizeof(double),
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    // matrix values in CSR order and ||A||_inf (values may change with every refactor)
+    int64_t nnzc = (int64_t)s->csr_col.size();
+    k_gather_vals<<<(unsigned)((nnzc + 255) / 256), 256, 0, st>>>(h->d_csr_val, h->d_values, h->d_csr_map, nnzc);
+    SC_CUDA(cudaMemsetAsync(h->d_red + 4095, 0, sizeof(double), st));
+    k_anorm<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(h->d_csr_ptr, h->d_csr_val, n, h->d_red + 4095);
+    SC_CUDA(cudaMemcpyAsync(&h->anorm, h->d_red + 4095, sizeof(double), cudaMemcpyDeviceToHost, st));
+    int launches = 2;
+    // x0 = solve(b)
+    if ((rc = tri_solve_any(h, nrhs, h->d_b, n, h->d_x, n, 0, st, launches))) return rc;
+    const bool refine = info && info->refine >= 0 ? info->refine != 0 : h->precision != SC_FP64;
+    const double tol = s->opt.ir_tol;
+    const int maxit = s->opt.ir_maxit;
+    std::vector<double> eta, best_eta;
+    std::vector<double> hist;
+    if ((rc = backward_error(h, nrhs, st, eta, launches))) return rc;
+    double emax = *std::max_element(eta.begin(), eta.end());
+    double best = emax;
+    best_eta = eta;
+    SC_CUDA(cudaMemcpyAsync(h->d_xbest, h->d_x, (size_t)n * nrhs * 8, cudaMemcpyDeviceToDevice, st));
+    hist.push_back(emax);
+    int it = 0;
+    if (refine) {
+        while (emax > tol && it < maxit) {
+            // d = solve(r); x += d
+            if ((rc = tri_solve_any(h, nrhs, h->d_r, n, h->d_x, n, 1, st, launches))) return rc;
+            it++;
+            if ((rc = backward_error(h, nrhs, st, eta, launches))) return rc;
+            emax = *std::max_element(eta.begin(), eta.end());
+            hist.push_back(emax);
+            if (emax < best) {
+                best = emax;
+                best_eta = eta;
+                SC_CUDA(cudaMemcpyAsync(h->d_xbest, h->d_x, (size_t)n * nrhs * 8, cudaMemcpyDeviceToDevice, st));
+            }
+            // stagnation: no halving over the last 3 iterations
+            if (hist.size() > 3 && emax > 0.5 * hist[hist.size() - 4]) break;
+        }
+    }
+    for (int64_t c = 0; c < nrhs; c++)
+        SC_CUDA(cudaMemcpyAsync(X + c * ldx, h->d_xbest + c * n, n * sizeof(double),
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    SC_CUDA(cudaEventRecord(e1, st));
+    SC_CUDA(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    bool conv = best <= tol;
+    if (info) {
+        info->iterations = it;
+        info->converged = conv ? 1 : 0;
+        info->eta_max = best;
+        info->solve_ms = ms;
+        info->kernel_launches = launches;
+        if (info->eta) std::copy(best_eta.begin(), best_eta.end(), info->eta);
+    }
+    if (refine && !conv) return SC_ERR_NOT_CONVERGED;
+    return SC_OK;
+}
+
+}  // namespace sc

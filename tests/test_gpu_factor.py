@@ -1,0 +1,166 @@
+"""GPU factor and solve through the C ABI against the oracle (needs a GB300).
+
+Parity bars (written here, derived from the arithmetic):
+- FP64 factor: every supernode block of L agrees with the oracle's L within
+  |L_gpu - L_or| <= 1e-10 * max|L_or| elementwise (the two sum the same
+  products in different orders; the growth for these SPD inputs stays far below
+  1e6 u), and the solve reaches eta <= 1e-14.
+- FP32 / TF32 factor: L within 1e-3 (FP32) or 2e-2 (TF32) relative to max|L|
+  on well-conditioned inputs; after FP64 refinement eta <= 1e-14.
+- structure: the library's symbolic arrays are bit-exact with the oracle's.
+- non-positive-definite input: the reported column equals the oracle's.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2409_13090_gb300 as sc
+from paper_2409_13090_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    sc.build()
+    oracle.build()
+
+
+def _grid_case(name):
+    if name == "lap2d_64":
+        return inputs.workload(1)[0]
+    if name == "diff7_24":
+        return inputs.workload(2, 0.5)[0]
+    if name == "diff7_13":
+        return inputs.diffusion_3d_7pt(13, 11, 9, seed=5, shift=1e-2)
+    if name == "st27_14":
+        return inputs.workload(3, 14 / 80)[0]
+    if name == "aniso_16":
+        return inputs.anisotropic_3d_7pt(16, 16, 16, seed=6, shift=1e-2)
+    if name == "lap2d_ragged":
+        return inputs.laplacian_2d(37, 29, 0.05)
+    raise KeyError(name)
+
+
+def _oracle_L(A, perm0):
+    o = oracle.Oracle(A, perm0, pr=True)
+    assert o.factor() == 0
+    return o, o.L_supernodal()
+
+
+def _check_L(Lg, Lo, tol):
+    scale = np.abs(Lo).max()
+    err = np.abs(Lg - Lo).max()
+    assert err <= tol * scale, f"max |L_gpu - L_oracle| = {err:.3e} > {tol:.1e} * {scale:.3e}"
+
+
+@pytest.mark.parametrize("name", ["lap2d_64", "diff7_24", "diff7_13", "st27_14", "aniso_16", "lap2d_ragged"])
+@pytest.mark.parametrize("variant", ["rlb", "rl"])
+def test_fp64_factor_matches_oracle(name, variant):
+    A = _grid_case(name)
+    sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid, variant=variant)
+    o, Lo = _oracle_L(A, oracle.nd_grid(*A.grid, 8))
+    num = sym.factor(A.values, precision="fp64")
+    assert num.rc == 0
+    _check_L(num.export_L(), Lo, 1e-10)
+    B = inputs.rhs(A.n, 4, 3)
+    X, info = num.solve(B)
+    eta = oracle.backward_error(A, B, X)
+    assert eta.max() <= 1e-14, eta
+    Xo = o.solve(B)
+    assert np.abs(X - Xo).max() <= 1e-8 * np.abs(Xo).max()
+
+
+@pytest.mark.parametrize("chunk", [8, 24, 64])
+def test_chunk_widths(chunk):
+    A = _grid_case("diff7_13")
+    sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid, chunk=chunk)
+    _, Lo = _oracle_L(A, oracle.nd_grid(*A.grid, 8))
+    num = sym.factor(A.values, precision="fp64")
+    _check_L(num.export_L(), Lo, 1e-10)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-3), ("tf32", 2e-2)])
+@pytest.mark.parametrize("name", ["lap2d_64", "st27_14", "lap2d_ragged"])
+def test_low_precision_factor_and_refinement(prec, tol, name):
+    A = _grid_case(name)
+    sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid)
+    _, Lo = _oracle_L(A, oracle.nd_grid(*A.grid, 8))
+    num = sym.factor(A.values, precision=prec)
+    assert num.rc == 0
+    _check_L(num.export_L(), Lo, tol)
+    B = inputs.rhs(A.n, 3, 4)
+    X, info = num.solve(B)
+    assert info["converged"], info
+    assert oracle.backward_error(A, B, X).max() <= 1e-14
+
+
+def test_values_from_device_and_refactor():
+    import torch
+    A = _grid_case("diff7_13")
+    sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid)
+    dv = torch.tensor(A.values, device="cuda", dtype=torch.float64)
+    num = sym.factor(dv, precision="fp64")
+    L1 = num.export_L()
+    v2 = A.values * 2.0
+    num.refactor(v2)
+    L2 = num.export_L()
+    assert np.allclose(L2, L1 * np.sqrt(2.0), rtol=1e-12, atol=1e-14)
+    # device right-hand sides: (nrhs, n) contiguous = column-major n x nrhs
+    B = inputs.rhs(A.n, 2, 5)
+    Bd = torch.tensor(np.ascontiguousarray(B.T), device="cuda")
+    Xd, info = num.solve(Bd)
+    X = Xd.cpu().numpy().T
+    A2 = inputs.SparseSym(A.n, A.colptr, A.rowind, v2)
+    assert oracle.backward_error(A2, B, X).max() <= 1e-14
+
+
+def test_not_positive_definite_column_matches_oracle():
+    A = inputs.laplacian_2d(20, 20)
+    v = A.values.copy()
+    v[A.colptr[137]] = -50.0  # diagonal of column 137
+    perm0 = oracle.nd_grid(20, 20, 1, 8)
+    o = oracle.Oracle(A, perm0, pr=True)
+    info_or = o.factor(v)
+    assert info_or > 0
+    sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid)
+    num = sym.factor(v, precision="fp64")
+    assert num.rc == info_or and num.failed_col == info_or
+
+
+def test_batch_factor_matches_per_matrix():
+    mats, _ = inputs.workload(4, 0.08)
+    syms = [sc.Symbolic(A, ordering="grid_nd", grid=A.grid) for A in mats]
+    bsym = sc.Symbolic.batch(syms)
+    vals = np.concatenate([A.values for A in mats])
+    num = bsym.factor(vals, precision="fp64")
+    assert num.rc == 0
+    Lb = num.export_L()
+    off = 0
+    for A in mats:
+        _, Lo = _oracle_L(A, oracle.nd_grid(*A.grid, 8))
+        _check_L(Lb[off:off + Lo.size], Lo, 1e-10)
+        off += Lo.size
+    B = inputs.rhs(bsym.n, 1, 9)
+    X, _ = num.solve(B, refine=True)
+    r0 = 0
+    for A in mats:
+        assert oracle.backward_error(A, B[r0:r0 + A.n], X[r0:r0 + A.n]).max() <= 1e-14
+        r0 += A.n
+
+
+def test_full_workload2_fp64_parity():
+    """48^3 7-point variable-coefficient matrix, FP64 RLB (the benchmark's launch): L elementwise vs
+    the oracle's Alg. 1 factor, and the backward error of 4 right-hand sides."""
+    A, nrhs = inputs.workload(2)
+    sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid)
+    num = sym.factor(A.values, precision="fp64")
+    assert num.rc == 0
+    o, Lo = _oracle_L(A, oracle.nd_grid(*A.grid, 8))
+    _check_L(num.export_L(), Lo, 1e-9)
+    B = inputs.rhs(A.n, nrhs, 2)
+    X, info = num.solve(B)
+    assert oracle.backward_error(A, B, X).max() <= 1e-14

@@ -1,0 +1,155 @@
+"""Host symbolic analysis of libsc against the oracle's separately written pass (CPU only).
+
+Bit-exact on every array: ordering (ND + postorder + PR), supernodes, supernodal
+parents, glbind, relind(J,p(J)), blocks, relindB(J,P) (the library composes it
+as in Alg. 5, the oracle searches glbind(P) directly), levels, column etree.
+"""
+import re
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2409_13090_gb300 as sc
+from paper_2409_13090_gb300 import inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+KEYS = ["perm", "sup_ptr", "sup_parent", "gl_ptr", "glbind", "ri_ptr", "relind", "blk_ptr", "blk_first",
+        "blk_size", "blk_owner", "rb_pair_ptr", "rb_pair_P", "rb_val_ptr", "rb_val", "level", "cparent"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    sc.build()
+
+
+def _compare(A, *, grid=None, user_perm=None, pr=True, leaf=8):
+    if grid is not None:
+        perm0 = oracle.nd_grid(*grid, leaf)
+        lib_sym = sc.Symbolic(A, ordering="grid_nd", grid=grid, nd_leaf=leaf, pr=pr)
+    elif user_perm is not None:
+        perm0 = user_perm
+        lib_sym = sc.Symbolic(A, ordering="user", user_perm=user_perm, pr=pr)
+    else:
+        perm0 = None
+        lib_sym = sc.Symbolic(A, ordering="natural", pr=pr)
+    o = oracle.Oracle(A, perm0, pr=pr).symbolic()
+    v = lib_sym.view()
+    for k in KEYS:
+        assert np.array_equal(v[k], getattr(o, k)), k
+    assert v["nnzL"] == o.nnzL and v["flops"] == o.flops and v["nsuper"] == o.nsuper
+    return v
+
+
+def test_worked_example_through_library(golden):
+    ents = [(i - 1, j - 1) for i, j in golden["A_strict_lower_pattern"]["entries"]]
+    A = inputs.from_lower_pattern(9, ents)
+    v = sc.Symbolic(A, pr=False).view()
+    assert v["sup_ptr"].tolist() == [0, 2, 4, 9]
+    assert v["relind"].tolist() == golden["relind"]["J1_J3"] + golden["relind"]["J2_J3"]
+    assert v["rb_val"].tolist() == golden["relindB"]["J1_J3"] + golden["relindB"]["J2_J3"]
+    v = sc.Symbolic(A, pr=True).view()
+    assert (v["blk_ptr"][1:3] - v["blk_ptr"][0:2]).tolist() == [1, 1]
+    _compare(A, pr=False)
+    _compare(A, pr=True)
+
+
+def test_relind_composition_example(golden):
+    g = golden["relind_composition"]
+    assert sc.sc_relind_compose(g["relind_J_C"], g["relind_C_P"]).tolist() == g["relind_J_P"]
+
+
+def test_indmap_example(golden):
+    # relative indices of glbind(J3) with respect to itself: distance from the bottom
+    g = golden["indmap_J3"]
+    rows = g["rows"]
+    assert [len(rows) - 1 - i for i in range(len(rows))] == g["values"]
+
+
+@pytest.mark.parametrize("pr", [False, True])
+def test_workload1_full(pr):
+    A, _ = inputs.workload(1)
+    _compare(A, grid=A.grid, pr=pr)
+
+
+@pytest.mark.parametrize("idx,scale", [(2, 0.25), (2, 0.5), (3, 0.2), (3, 0.5), (5, 0.125)])
+def test_workloads_scaled(idx, scale):
+    A, _ = inputs.workload(idx, scale)
+    _compare(A, grid=A.grid, pr=True)
+
+
+def test_workload2_full():
+    A, _ = inputs.workload(2)
+    v = _compare(A, grid=A.grid, pr=True)
+    assert v["nsuper"] > 1000
+
+
+def test_workload4_members():
+    mats, _ = inputs.workload(4, 0.1)
+    for A in mats[:4]:
+        _compare(A, grid=A.grid, pr=True)
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("pr", [False, True])
+def test_random_user_perm(seed, pr):
+    n = 50 + 40 * seed
+    A = inputs.random_spd(n, 0.05, seed)
+    perm = np.random.default_rng(100 + seed).permutation(n).astype(np.int32)
+    _compare(A, user_perm=perm, pr=pr)
+    _compare(A, pr=pr)
+
+
+def test_closed_form_special_cases():
+    n = 40
+    tri = inputs.from_lower_pattern(n, [(i + 1, i) for i in range(n - 1)])
+    _compare(tri, pr=True)
+    dense = inputs.from_lower_pattern(20, [(i, j) for j in range(20) for i in range(j + 1, 20)])
+    v = _compare(dense, pr=True)
+    assert v["nsuper"] == 1
+    arrow = inputs.from_lower_pattern(n, [(n - 1, j) for j in range(n - 1)])
+    _compare(arrow, pr=True)
+
+
+def test_invalid_input_codes():
+    A = inputs.laplacian_2d(4, 4)
+    bad = A.rowind.copy()
+    bad[1], bad[2] = bad[2], bad[1]  # unsorted rows in column 0
+    o = sc.sc_options_default()
+    rc, _ = sc.sc_analyze(A.n, np.ascontiguousarray(A.colptr), bad, o)
+    assert rc == -3
+    rc, _ = sc.sc_analyze(0, np.ascontiguousarray(A.colptr), np.ascontiguousarray(A.rowind), o)
+    assert rc == -1
+    o.ordering = 1
+    o.grid[0], o.grid[1], o.grid[2] = 5, 4, 1  # wrong grid size
+    rc, _ = sc.sc_analyze(A.n, np.ascontiguousarray(A.colptr), np.ascontiguousarray(A.rowind), o)
+    assert rc == -4
+
+
+def test_batch_concatenates_structures():
+    mats = [inputs.laplacian_2d(5, 6, 0.1), inputs.laplacian_2d(7, 4, 0.2), inputs.laplacian_2d(3, 3, 0.3)]
+    syms = [sc.Symbolic(A, ordering="grid_nd", grid=A.grid) for A in mats]
+    b = sc.Symbolic.batch(syms).view()
+    vs = [s.view() for s in syms]
+    assert b["n"] == sum(v["n"] for v in vs) and b["nsuper"] == sum(v["nsuper"] for v in vs)
+    assert b["nnzL"] == sum(v["nnzL"] for v in vs)
+    off = 0
+    parts = []
+    for v in vs:
+        parts.append(v["perm"] + off)
+        off += v["n"]
+    assert np.array_equal(b["perm"], np.concatenate(parts))
+
+
+def test_library_exports_every_declared_symbol():
+    """The C ABI library loads on a machine without a GPU and exports every function of include/sc.h."""
+    import ctypes
+    hdr = open(os.path.join(ROOT, "include", "sc.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    names = set(re.findall(r"^\s*(?:const\s+)?\w+\s*\**\s*(sc_\w+)\s*\(", hdr, flags=re.M))
+    assert {"sc_analyze", "sc_factor", "sc_solve", "sc_refactor", "sc_analyze_batch", "sc_symbolic_export",
+            "sc_numeric_free", "sc_symbolic_free", "sc_strerror", "sc_options_default"} <= names
+    L = ctypes.CDLL(sc.build())
+    for nm in sorted(names):
+        assert hasattr(L, nm), nm
