@@ -41,6 +41,7 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "tf32"])
+    ap.add_argument("--merge", type=float, default=0.125, help="supernode merging budget (Sec. 3.1); 0 = off")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     return ap.parse_args()
@@ -168,7 +169,7 @@ def main():
 
     A, nrhs = inputs.workload(2)
     t0 = time.perf_counter()
-    sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid, nd_leaf=8, pr=True, variant="rlb")
+    sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid, nd_leaf=8, pr=True, variant="rlb", merge=args.merge)
     analyze_s = time.perf_counter() - t0
     view = sym.view()
     flops = view["flops"]
@@ -304,6 +305,7 @@ def main():
                 "config": {"workload": WORKLOAD, "n": A.n, "nnz_A_lower": A.nnz, "nnz_L": int(view["nnzL"]),
                            "sum_cj2": flops, "nsuper": int(view["nsuper"]), "nrhs": nrhs,
                            "precision": args.precision, "variant": "rlb", "ordering": "grid ND (leaf 8) + PR",
+                           "merge_frac": args.merge,
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                            "l2": "inputs larger than L2 (factor storage rewritten every step)",
                            "analyze_s": analyze_s},

@@ -79,20 +79,24 @@ typedef struct sc_options {
     double pivot_tau;          /* low-precision pivot d_jj <= tau * |A_jj| redone in FP64 */
     int64_t spin_limit;        /* iteration limit of every bounded device wait      */
     int32_t use_graph;         /* 1 = replay the factor schedule as a CUDA graph    */
-    int32_t reserved[7];
+    double merge_frac;         /* supernode merging budget (Sec. 3.1): merge child-parent
+                                  pairs by least new fill while the added storage stays
+                                  <= merge_frac x the fundamental storage; 0 = off */
+    int32_t reserved[6];
 } sc_options;
 
 /* Fills o with the defaults: SC_ORDER_NATURAL, nd_leaf 8, pr 1, SC_RLB, SC_FP64,
  * chunk 64, ir_tol 1e-14, ir_maxit 30, pivot_tau 2^-10, spin_limit 1<<22,
- * use_graph 1. Returns SC_OK, or -1 if o is NULL. */
+ * use_graph 1, merge_frac 0 (fundamental supernodes). Returns SC_OK, or -1 if
+ * o is NULL. */
 int sc_options_default(sc_options *o);
 
 /* ------------------------------------------------------------- symbolic */
 typedef struct sc_symbolic sc_symbolic;
 
 /* Symbolic analysis (Sec. 1 steps 1-2; Sec. 2.1.2; Sec. 3.1): ordering, then
- * elimination tree, postorder, column counts, fundamental supernodes,
- * supernodal elimination tree, partition refinement within supernodes,
+ * elimination tree, postorder, column counts, fundamental supernodes, optional
+ * supernode merging, supernodal elimination tree, partition refinement within supernodes,
  * relind(J, p(J)), blocks and relindB(J, P) (Alg. 5), levels, and the
  * device schedule. Host only; no device memory is touched.
  *   n        order of A (>= 1)
@@ -108,8 +112,8 @@ int sc_analyze(int64_t n, const int64_t *colptr, const int32_t *rowind, const sc
 /* Read-only view of the symbolic structures, for verification. Pointers stay
  * valid until the handle is freed. All arrays are host memory. */
 typedef struct sc_symbolic_view {
-    int64_t n, nsuper, nnzL, nblocks, npairs;
-    double flops;               /* sum over columns j of |L_{*,j}|^2        */
+    int64_t n, nsuper, nnzL, nblocks, npairs;  /* nnzL: entries stored (incl. merged zeros) */
+    double flops;               /* sum over columns j of |L_{*,j}|^2, true (fundamental) structure */
     const int32_t *perm;        /* [n]  final ordering, perm[new] = old      */
     const int32_t *sup_ptr;     /* [nsuper+1] first column of each supernode */
     const int32_t *sup_parent;  /* [nsuper]   p(J), -1 for a root            */
@@ -225,14 +229,15 @@ int sc_numeric_export_L(const sc_numeric *h, double *out);
 /* Per-kernel-class profile of one factorization, for roofline reporting: the
  * factorization runs once outside the CUDA graph with CUDA events around every
  * launch on cuda_stream. Each output array has SC_PROF_CLASSES entries, in the
- * class order: value load (K0), POTRF, TRSM, SIMT products, tensor-core
- * products, warp products, RL update matrices, RL assembly.
+ * class order: value load (K0), POTRF, TRSM, SIMT tiled products,
+ * tensor-core tiled products, warp products, RL update matrices, RL assembly,
+ * device-side RLB loops.
  *   ms        summed device time per class (milliseconds, host array)
  *   flops     algorithmic flops per class (2 per multiply-add; POTRF w^3/3,
  *             TRSM rows * w^2; RL assembly counts one per added entry)
  *   launches  launches per class
  * Same values/stream conventions and return codes as sc_refactor. */
-#define SC_PROF_CLASSES 8
+#define SC_PROF_CLASSES 9
 int sc_factor_profile(sc_numeric *h, const double *values, int values_on_device, void *cuda_stream, double *ms,
                       double *flops, int32_t *launches);
 
@@ -241,6 +246,12 @@ int sc_factor_profile(sc_numeric *h, const double *values, int values_on_device,
  * best of three. kind 0 = FP64, 1 = FP32. Writes FLOP/s (2 per FMA) to
  * *flops_per_s. Errors: -1 bad kind, -3 NULL output, SC_ERR_CUDA, SC_ERR_OOM. */
 int sc_probe_fma_peak(int kind, void *cuda_stream, double *flops_per_s);
+
+/* Size of the launch plan a factorization in `precision` would use (host only,
+ * no device memory): out[0..nout) receives, in order, the chunk levels, chunks,
+ * product tasks, warp-sized tasks, tiled tasks, SIMT tiles, tensor-core tiles,
+ * TRSM tiles, RL assembly pairs and device-loop items. Errors: -1, -2, -3. */
+int sc_plan_stats(const sc_symbolic *s, int precision, int64_t *out, int nout);
 
 /* Frees h and its device memory. NULL is accepted. */
 void sc_numeric_free(sc_numeric *h);

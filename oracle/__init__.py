@@ -40,7 +40,7 @@ def lib():
         P = C.c_void_p
         i64, i32, dbl = C.c_int64, C.c_int32, C.c_double
         L.or_nd_grid.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, P]
-        L.or_analyze.argtypes = [i64, P, P, P, C.c_int, C.POINTER(P)]
+        L.or_analyze.argtypes = [i64, P, P, P, C.c_int, C.c_double, C.POINTER(P)]
         L.or_free.argtypes = [P]
         L.or_factor.argtypes = [P, P]
         L.or_factor.restype = i64
@@ -101,7 +101,7 @@ class Symbolic:
 class Oracle:
     """Handle around the C oracle: analyze (own symbolic pass), factor (Alg. 1), solve, eta."""
 
-    def __init__(self, A, perm0: np.ndarray | None = None, pr: bool = True):
+    def __init__(self, A, perm0: np.ndarray | None = None, pr: bool = True, merge: float = 0.0):
         self.A = A
         L = lib()
         h = C.c_void_p()
@@ -109,7 +109,7 @@ class Oracle:
         self._colptr = np.ascontiguousarray(A.colptr, dtype=np.int64)
         self._rowind = np.ascontiguousarray(A.rowind, dtype=np.int32)
         rc = L.or_analyze(A.n, _p(self._colptr), _p(self._rowind), None if p0 is None else _p(p0),
-                          1 if pr else 0, C.byref(h))
+                          1 if pr else 0, float(merge), C.byref(h))
         if rc != 0:
             raise RuntimeError(f"or_analyze failed: {rc}")
         self._h = h

@@ -366,11 +366,145 @@ static int analyze_with(or_sym *s, int64_t n, const int64_t *colptr, const int32
     return symbolic_union(n, s->acolptr, s->arowind, &s->ccolptr, &s->crows, &s->cparent);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Supernode merging (Sec. 3.1): repeatedly merge the child-parent pair whose
+ * merge adds the least new fill, stopping before the cumulative growth of the
+ * factor storage would exceed merge_frac of the fundamental storage.
+ * Readings (the paper does not spell these out):
+ *   - a pair (X, p(X)) is a candidate only when X's last column is the column
+ *     just before p(X)'s first one, so merged supernodes stay consecutive;
+ *   - storage of a supernode with w columns and m rows = w m - w (w - 1) / 2
+ *     (its lower trapezoid); merging X into P gives w = |X| + |P| and
+ *     m = |X| + m_P; new fill = storage(merged) - storage(X) - storage(P);
+ *   - ties in new fill go to the child with the smaller first column;
+ *   - a merge is allowed while (added fill so far + its fill) <= frac * S0,
+ *     S0 = storage of the fundamental partition.
+ * Uses a binary heap of (fill, first column, supernode, version) entries with
+ * lazy invalidation.                                                          */
+
+typedef struct { int64_t d; int32_t f, id, ver; } hent;
+
+static int hless(const hent *a, const hent *b) { return a->d < b->d || (a->d == b->d && a->f < b->f); }
+
+static void hpush(hent **h, int64_t *len, int64_t *cap, hent e) {
+    if (*len == *cap) { *cap = *cap ? 2 * *cap : 1024; *h = realloc(*h, *cap * sizeof(hent)); }
+    int64_t i = (*len)++;
+    (*h)[i] = e;
+    while (i > 0) {
+        int64_t p = (i - 1) / 2;
+        if (!hless(&(*h)[i], &(*h)[p])) break;
+        hent t = (*h)[i]; (*h)[i] = (*h)[p]; (*h)[p] = t;
+        i = p;
+    }
+}
+
+static hent hpop(hent *h, int64_t *len) {
+    hent top = h[0];
+    h[0] = h[--(*len)];
+    int64_t i = 0;
+    for (;;) {
+        int64_t l = 2 * i + 1, r = l + 1, m = i;
+        if (l < *len && hless(&h[l], &h[m])) m = l;
+        if (r < *len && hless(&h[r], &h[m])) m = r;
+        if (m == i) break;
+        hent t = h[i]; h[i] = h[m]; h[m] = t;
+        i = m;
+    }
+    return top;
+}
+
+static int64_t st_trap(int64_t w, int64_t m) { return w * m - w * (w - 1) / 2; }
+
+/* new fill of merging X into P */
+static int64_t merge_fill(int64_t wX, int64_t mX, int64_t wP, int64_t mP) {
+    return st_trap(wX + wP, wX + mP) - st_trap(wX, mX) - st_trap(wP, mP);
+}
+
+static int merge_supernodes(or_sym *s, double frac, int32_t **top_out) {
+    int64_t n = s->n, ns = s->nsuper;
+    int32_t *f = xmalloc(ns * sizeof(int32_t)), *l = xmalloc(ns * sizeof(int32_t));
+    int32_t *ftop = xmalloc(ns * sizeof(int32_t)), *minS = xmalloc(ns * sizeof(int32_t));
+    int32_t *ver = xcalloc(ns, sizeof(int32_t)), *own = xmalloc(n * sizeof(int32_t));
+    int64_t *m = xmalloc(ns * sizeof(int64_t));
+    char *alive = xmalloc(ns);
+    int64_t S0 = 0;
+    for (int64_t X = 0; X < ns; X++) {
+        f[X] = s->sup_ptr[X];
+        l[X] = s->sup_ptr[X + 1] - 1;
+        ftop[X] = f[X];
+        m[X] = s->ccolptr[f[X] + 1] - s->ccolptr[f[X]];
+        minS[X] = -1;
+        for (int64_t p = s->ccolptr[f[X]]; p < s->ccolptr[f[X] + 1]; p++)
+            if (s->crows[p] > l[X]) { minS[X] = s->crows[p]; break; }
+        alive[X] = 1;
+        for (int32_t j = f[X]; j <= l[X]; j++) own[j] = (int32_t)X;
+        S0 += st_trap(l[X] - f[X] + 1, m[X]);
+    }
+    hent *h = NULL;
+    int64_t hl = 0, hc = 0;
+    for (int64_t X = 0; X < ns; X++) {
+        if (minS[X] < 0) continue;
+        int32_t P = own[minS[X]];
+        if (l[X] + 1 != f[P]) continue;
+        hent e = {merge_fill(l[X] - f[X] + 1, m[X], l[P] - f[P] + 1, m[P]), f[X], (int32_t)X, ver[X]};
+        hpush(&h, &hl, &hc, e);
+    }
+    int64_t added = 0;
+    while (hl > 0) {
+        hent e = hpop(h, &hl);
+        int32_t X = e.id;
+        if (!alive[X] || e.ver != ver[X]) continue;
+        int32_t P = own[minS[X]];
+        if ((double)(added + e.d) > frac * (double)S0) break;
+        /* merge X into P: P keeps its id, its last column and its rows below */
+        added += e.d;
+        m[P] = (l[X] - f[X] + 1) + m[P];
+        for (int32_t j = f[X]; j <= l[X]; j++) own[j] = P;
+        f[P] = f[X];
+        alive[X] = 0;
+        ver[P]++;
+        /* P's own candidate with its parent */
+        if (minS[P] >= 0) {
+            int32_t Q = own[minS[P]];
+            if (l[P] + 1 == f[Q]) {
+                hent c = {merge_fill(l[P] - f[P] + 1, m[P], l[Q] - f[Q] + 1, m[Q]), f[P], P, ver[P]};
+                hpush(&h, &hl, &hc, c);
+            }
+        }
+        /* the child just before the merged supernode, if P is its parent */
+        if (f[P] > 0) {
+            int32_t C = own[f[P] - 1];
+            if (alive[C] && minS[C] >= 0 && own[minS[C]] == P) {
+                ver[C]++;
+                hent c = {merge_fill(l[C] - f[C] + 1, m[C], l[P] - f[P] + 1, m[P]), f[C], C, ver[C]};
+                hpush(&h, &hl, &hc, c);
+            }
+        }
+    }
+    /* surviving supernodes in column order */
+    int64_t nn = 0;
+    int32_t *top = xmalloc(ns * sizeof(int32_t));
+    for (int64_t X = 0; X < ns; X++) {
+        if (!alive[X]) continue;
+        s->sup_ptr[nn] = f[X];
+        top[nn] = ftop[X];
+        nn++;
+    }
+    s->sup_ptr[nn] = (int32_t)n;
+    s->nsuper = nn;
+    for (int64_t J = 0; J < nn; J++)
+        for (int32_t j = s->sup_ptr[J]; j < s->sup_ptr[J + 1]; j++) s->sup_of[j] = (int32_t)J;
+    free(f); free(l); free(ftop); free(minS); free(ver); free(own); free(m); free(alive); free(h);
+    *top_out = top;
+    return OR_OK;
+}
+
 /* The top-level symbolic analysis.
  *   perm0: ordering to start from (new -> old), or NULL for the natural order;
- *   do_pr: apply partition refinement within supernodes.                     */
+ *   do_pr: apply partition refinement within supernodes;
+ *   merge_frac: supernode merging budget (0 = fundamental supernodes only).   */
 int or_analyze(int64_t n, const int64_t *colptr, const int32_t *rowind, const int32_t *perm0,
-               int do_pr, or_sym **out) {
+               int do_pr, double merge_frac, or_sym **out) {
     if (n <= 0 || !colptr || !rowind || !out) return OR_ERR_ARG;
     or_sym *s = xcalloc(1, sizeof(or_sym));
     s->n = n;
@@ -425,17 +559,42 @@ int or_analyze(int64_t n, const int64_t *colptr, const int32_t *rowind, const in
     for (int64_t J = 0; J < ns; J++)
         for (int32_t j = s->sup_ptr[J]; j < s->sup_ptr[J + 1]; j++) s->sup_of[j] = (int32_t)J;
     free(start); free(nchild); free(post);
+    /* sum over columns of |L_{*,j}|^2 of the true (fundamental) structure */
+    s->flops = 0.0;
+    for (int64_t j = 0; j < n; j++) {
+        double c = (double)(s->ccolptr[j + 1] - s->ccolptr[j]);
+        s->flops += c * c;
+    }
+    /* optional supernode merging (Sec. 3.1); top[J] = the fundamental supernode
+       whose rows below the diagonal block are the merged supernode's rows     */
+    int32_t *top = NULL;
+    if (merge_frac > 0.0) {
+        rc = merge_supernodes(s, merge_frac, &top);
+        if (rc) return rc;
+        ns = s->nsuper;
+    } else {
+        top = xmalloc(ns * sizeof(int32_t));
+        for (int64_t J = 0; J < ns; J++) top[J] = s->sup_ptr[J];
+    }
 
-    /* glbind(J) of the pre-PR (postordered) matrix: the structure of column f_J */
+    /* glbind(J) of the pre-PR (postordered) matrix: J's columns followed by the
+       rows of column top[J]'s structure that lie below J's last column        */
     int64_t *gpre_ptr = xcalloc(ns + 1, sizeof(int64_t));
     for (int64_t J = 0; J < ns; J++) {
-        int32_t f = s->sup_ptr[J];
-        gpre_ptr[J + 1] = gpre_ptr[J] + (s->ccolptr[f + 1] - s->ccolptr[f]);
+        int32_t f = s->sup_ptr[J], l = s->sup_ptr[J + 1] - 1, t = top[J];
+        int64_t below = 0;
+        for (int64_t p = s->ccolptr[t]; p < s->ccolptr[t + 1]; p++) below += s->crows[p] > l;
+        gpre_ptr[J + 1] = gpre_ptr[J] + (l - f + 1) + below;
     }
     int32_t *gpre = xmalloc((gpre_ptr[ns] + 1) * sizeof(int32_t));
-    for (int64_t J = 0; J < ns; J++)
-        memcpy(gpre + gpre_ptr[J], s->crows + s->ccolptr[s->sup_ptr[J]],
-               (gpre_ptr[J + 1] - gpre_ptr[J]) * sizeof(int32_t));
+    for (int64_t J = 0; J < ns; J++) {
+        int32_t f = s->sup_ptr[J], l = s->sup_ptr[J + 1] - 1, t = top[J];
+        int64_t w = gpre_ptr[J];
+        for (int32_t j = f; j <= l; j++) gpre[w++] = j;
+        for (int64_t p = s->ccolptr[t]; p < s->ccolptr[t + 1]; p++)
+            if (s->crows[p] > l) gpre[w++] = s->crows[p];
+    }
+    free(top);
 
     /* partition refinement within each supernode, on the pre-PR structure */
     int32_t *p3 = xmalloc(n * sizeof(int32_t));
@@ -445,11 +604,10 @@ int or_analyze(int64_t n, const int64_t *colptr, const int32_t *rowind, const in
         int64_t *cnt = xcalloc(ns + 1, sizeof(int64_t));
         for (int64_t J = 0; J < ns; J++) {
             int32_t l = s->sup_ptr[J + 1] - 1;
-            int32_t f = s->sup_ptr[J];
-            int64_t p = s->ccolptr[f], e = s->ccolptr[f + 1];
+            int64_t p = gpre_ptr[J], e = gpre_ptr[J + 1];
             int32_t lastP = -1;
             for (; p < e; p++) {
-                int32_t i = s->crows[p];
+                int32_t i = gpre[p];
                 if (i <= l) continue;
                 int32_t P = s->sup_of[i];
                 if (P != lastP) { cnt[P + 1]++; lastP = P; }
@@ -465,11 +623,11 @@ int or_analyze(int64_t n, const int64_t *colptr, const int32_t *rowind, const in
         memcpy(fillp, sptr, (ns + 1) * sizeof(int64_t));
         int64_t *set_size = xcalloc(nsets + 1, sizeof(int64_t));
         for (int64_t J = 0; J < ns; J++) {
-            int32_t l = s->sup_ptr[J + 1] - 1, f = s->sup_ptr[J];
+            int32_t l = s->sup_ptr[J + 1] - 1;
             int32_t lastP = -1;
             int64_t cur = -1;
-            for (int64_t p = s->ccolptr[f]; p < s->ccolptr[f + 1]; p++) {
-                int32_t i = s->crows[p];
+            for (int64_t p = gpre_ptr[J]; p < gpre_ptr[J + 1]; p++) {
+                int32_t i = gpre[p];
                 if (i <= l) continue;
                 int32_t P = s->sup_of[i];
                 if (P != lastP) { cur = fillp[P]++; lastP = P; }
@@ -482,11 +640,11 @@ int or_analyze(int64_t n, const int64_t *colptr, const int32_t *rowind, const in
         int64_t *wpos = xmalloc((nsets + 1) * sizeof(int64_t));
         memcpy(wpos, set_ptr_all, (nsets + 1) * sizeof(int64_t));
         for (int64_t J = 0; J < ns; J++) {
-            int32_t l = s->sup_ptr[J + 1] - 1, f = s->sup_ptr[J];
+            int32_t l = s->sup_ptr[J + 1] - 1;
             int32_t lastP = -1;
             int64_t cur = -1;
-            for (int64_t p = s->ccolptr[f]; p < s->ccolptr[f + 1]; p++) {
-                int32_t i = s->crows[p];
+            for (int64_t p = gpre_ptr[J]; p < gpre_ptr[J + 1]; p++) {
+                int32_t i = gpre[p];
                 if (i <= l) continue;
                 int32_t P = s->sup_of[i];
                 if (P != lastP) { cur = fillp[P]++; lastP = P; }
@@ -551,12 +709,7 @@ int or_analyze(int64_t n, const int64_t *colptr, const int32_t *rowind, const in
     s->ccolptr = sccp;
     s->crows = scrows;
     s->nnzL = 0;
-    s->flops = 0.0;
-    for (int64_t j = 0; j < n; j++) {
-        double c = (double)(s->ccolptr[j + 1] - s->ccolptr[j]);
-        s->nnzL += (int64_t)c;
-        s->flops += c * c;
-    }
+    for (int64_t j = 0; j < n; j++) s->nnzL += s->ccolptr[j + 1] - s->ccolptr[j];
 
     /* supernodal parent (Sec. 2.1.2): the supernode holding min{i in glbind(J), i > l} */
     s->sup_parent = xmalloc(ns * sizeof(int32_t));

@@ -40,7 +40,7 @@ class Options(C.Structure):
                 ("user_perm", C.c_void_p), ("pr", C.c_int32), ("variant", C.c_int32),
                 ("precision", C.c_int32), ("chunk", C.c_int32), ("ir_tol", C.c_double),
                 ("ir_maxit", C.c_int32), ("pivot_tau", C.c_double), ("spin_limit", C.c_int64),
-                ("use_graph", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("use_graph", C.c_int32), ("merge_frac", C.c_double), ("reserved", C.c_int32 * 6)]
 
 
 class SymbolicView(C.Structure):
@@ -96,6 +96,7 @@ def lib():
             "sc_numeric_free": ([P], None),
             "sc_factor_profile": ([P, P, C.c_int, P, P, P, P], C.c_int),
             "sc_probe_fma_peak": ([C.c_int, P, P], C.c_int),
+            "sc_plan_stats": ([P, C.c_int, P, C.c_int], C.c_int),
             "sc_strerror": ([C.c_int], C.c_char_p),
             "sc_build_info": ([], C.c_char_p),
         }
@@ -229,7 +230,7 @@ class Symbolic:
 
     def __init__(self, A=None, *, ordering="natural", grid=None, nd_leaf=8, user_perm=None, pr=True,
                  variant="rlb", precision="fp64", chunk=64, ir_tol=1e-14, ir_maxit=30, use_graph=True,
-                 _handle=None, _parts=None):
+                 merge=0.0, _handle=None, _parts=None):
         self._parts = _parts
         if _handle is not None:
             self._h = _handle
@@ -252,6 +253,7 @@ class Symbolic:
         o.ir_tol = ir_tol
         o.ir_maxit = ir_maxit
         o.use_graph = 1 if use_graph else 0
+        o.merge_frac = float(merge)
         colptr = np.ascontiguousarray(A.colptr, np.int64)
         rowind = np.ascontiguousarray(A.rowind, np.int32)
         rc, h = sc_analyze(A.n, colptr, rowind, o)
@@ -283,6 +285,16 @@ class Symbolic:
         out["relind"] = _view_array(v.relind, np.int32, int(out["ri_ptr"][-1]))
         out["rb_val"] = _view_array(v.rb_val, np.int32, int(out["rb_val_ptr"][-1]))
         return out
+
+    PLAN_KEYS = ["levels", "chunks", "tasks", "warp_tasks", "tiled_tasks", "simt_tiles", "tc_tiles", "trsm_tiles",
+                 "rl_pairs", "loop_items"]
+
+    def plan_stats(self, precision="fp64") -> dict:
+        out = np.zeros(len(self.PLAN_KEYS), np.int64)
+        rc = lib().sc_plan_stats(self._h, PRECISION[precision], _ptr(out), len(out))
+        if rc:
+            raise SCError(rc, "sc_plan_stats")
+        return dict(zip(self.PLAN_KEYS, out.tolist()))
 
     def factor(self, values=None, precision=None, stream=None, A=None) -> "Numeric":
         return Numeric(self, values if values is not None else A.values, precision, stream)
@@ -333,9 +345,13 @@ class Numeric:
         return info
 
     def solve(self, B, X=None, refine=None, stream=None):
-        """Solves A X = B. B: n x nrhs (numpy host, or torch CUDA tensor, column-major)."""
-        dev = _is_device(B)
-        if not dev:
+        """Solves A X = B.
+
+        B as a numpy array: n x nrhs (host, column-major). B as a torch tensor
+        (CUDA, or pinned/host CPU): shape (nrhs, n) contiguous, i.e. column-major
+        n x nrhs; X likewise (allocated when None)."""
+        if isinstance(B, np.ndarray):
+            dev = False
             B = np.asfortranarray(B, np.float64)
             if B.ndim == 1:
                 B = B.reshape(-1, 1, order="F")
@@ -344,7 +360,9 @@ class Numeric:
                 X = np.zeros_like(B, order="F")
             ldx = X.shape[0]
         else:
-            # torch CUDA tensors given as (nrhs, n) contiguous = column-major n x nrhs
+            dev = bool(B.is_cuda)
+            if B.dim() == 1:
+                B = B.reshape(1, -1)
             nrhs, ldb = B.shape[0], B.shape[1]
             if X is None:
                 import torch
@@ -360,14 +378,16 @@ class Numeric:
         return X, {"iterations": info.iterations, "converged": bool(info.converged), "eta_max": info.eta_max,
                    "eta": eta, "solve_ms": info.solve_ms, "rc": rc, "kernel_launches": info.kernel_launches}
 
-    PROFILE_CLASSES = ["value_load", "potrf", "trsm", "gemm_simt", "gemm_tc", "gemm_warp", "rl_update", "rl_assemble"]
+    PROFILE_CLASSES = ["value_load", "potrf", "trsm", "gemm_simt", "gemm_tc", "gemm_warp", "rl_update", "rl_assemble",
+                       "rlb_loop"]
 
     def profile(self, values, stream=None) -> dict:
         """One factorization with CUDA events around every launch (sc_factor_profile)."""
         if isinstance(values, np.ndarray):
             values = np.ascontiguousarray(values, np.float64)
-        ms, fl = np.zeros(8), np.zeros(8)
-        ln = np.zeros(8, np.int32)
+        nc = len(self.PROFILE_CLASSES)
+        ms, fl = np.zeros(nc), np.zeros(nc)
+        ln = np.zeros(nc, np.int32)
         rc = lib().sc_factor_profile(self._h, _ptr(values), _is_device(values), _stream(stream), _ptr(ms),
                                      _ptr(fl), _ptr(ln))
         if rc < 0:

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cstring>
 #include <numeric>
+#include <set>
 
 #include "sc_internal.h"
 
@@ -200,6 +201,103 @@ void refine(int32_t size, const std::vector<std::vector<int32_t>> &sets, std::ve
     }
 }
 
+// Supernode merging (Sec. 3.1): merge, one pair at a time, the child-parent
+// pair adding the least new fill, while the total added fill stays within
+// frac x the fundamental storage. A pair (X, p(X)) qualifies when X ends on the
+// column just before p(X) starts (merged supernodes stay consecutive); the
+// storage of w columns with m rows is w m - w (w - 1) / 2; merging X into P
+// yields w = |X| + |P|, m = |X| + m_P; ties go to the smaller first column.
+// Candidates live in an ordered set keyed by (fill, first column) and are
+// re-keyed when a merge changes them. The merged supernode keeps P's rows
+// below its last column (S_X lies inside P's columns and S_P).
+void merge_supernodes(int64_t n, double frac, std::vector<int32_t> &sup_ptr, std::vector<int32_t> &sup_of,
+                      std::vector<int64_t> &sptr, std::vector<int32_t> &srows, std::vector<int32_t> &spar,
+                      std::vector<int32_t> &chead, std::vector<int32_t> &cnext, std::vector<int32_t> &ctail) {
+    const int64_t ns = (int64_t)sup_ptr.size() - 1;
+    auto trap = [](int64_t w, int64_t m) { return w * m - w * (w - 1) / 2; };
+    std::vector<int32_t> f(ns), l(ns), own(sup_of);
+    std::vector<int64_t> w(ns), m(ns);
+    std::vector<char> alive(ns, 1);
+    int64_t S0 = 0;
+    for (int64_t X = 0; X < ns; X++) {
+        f[X] = sup_ptr[X];
+        l[X] = sup_ptr[X + 1] - 1;
+        w[X] = l[X] - f[X] + 1;
+        m[X] = w[X] + (sptr[X + 1] - sptr[X]);
+        S0 += trap(w[X], m[X]);
+    }
+    auto minS = [&](int64_t X) -> int32_t { return sptr[X + 1] > sptr[X] ? srows[sptr[X]] : -1; };
+    auto parent_now = [&](int64_t X) -> int32_t {
+        int32_t r = minS(X);
+        return r < 0 ? -1 : own[r];
+    };
+    typedef std::pair<int64_t, int32_t> Key;  // (fill, first column)
+    std::set<std::pair<Key, int32_t>> cand;
+    std::vector<Key> key(ns, Key(-1, -1));
+    auto refresh = [&](int32_t X) {
+        if (key[X].first >= 0) cand.erase({key[X], X});
+        key[X] = Key(-1, -1);
+        if (!alive[X]) return;
+        int32_t P = parent_now(X);
+        if (P < 0 || l[X] + 1 != f[P]) return;
+        int64_t fill = trap(w[X] + w[P], w[X] + m[P]) - trap(w[X], m[X]) - trap(w[P], m[P]);
+        key[X] = Key(fill, f[X]);
+        cand.insert({key[X], X});
+    };
+    for (int32_t X = 0; X < ns; X++) refresh(X);
+    int64_t added = 0;
+    while (!cand.empty()) {
+        auto it = cand.begin();
+        int64_t fill = it->first.first;
+        int32_t X = it->second;
+        if ((double)(added + fill) > frac * (double)S0) break;
+        int32_t P = parent_now(X);
+        cand.erase(it);
+        key[X] = Key(-1, -1);
+        added += fill;
+        alive[X] = 0;
+        for (int32_t j = f[X]; j <= l[X]; j++) own[j] = P;
+        m[P] += w[X];
+        w[P] += w[X];
+        f[P] = f[X];
+        refresh(P);
+        if (f[P] > 0) {
+            int32_t C = own[f[P] - 1];
+            if (alive[C] && parent_now(C) == P) refresh(C);
+        }
+    }
+    // renumber the surviving supernodes in column order
+    std::vector<int32_t> newid(ns, -1);
+    std::vector<int32_t> nptr;
+    std::vector<int64_t> nsptr{0};
+    std::vector<int32_t> nsrows;
+    for (int32_t X = 0; X < ns; X++) {
+        if (!alive[X]) continue;
+        newid[X] = (int32_t)nptr.size();
+        nptr.push_back(f[X]);
+        nsrows.insert(nsrows.end(), srows.begin() + sptr[X], srows.begin() + sptr[X + 1]);
+        nsptr.push_back((int64_t)nsrows.size());
+    }
+    nptr.push_back((int32_t)n);
+    const int64_t nn = (int64_t)nptr.size() - 1;
+    for (int64_t J = 0; J < nn; J++)
+        for (int32_t j = nptr[J]; j < nptr[J + 1]; j++) sup_of[j] = (int32_t)J;
+    sup_ptr.swap(nptr);
+    sptr.swap(nsptr);
+    srows.swap(nsrows);
+    spar.assign(nn, -1);
+    chead.assign(nn, -1);
+    cnext.assign(nn, -1);
+    ctail.assign(nn, -1);
+    for (int64_t J = 0; J < nn; J++) {
+        if (sptr[J + 1] == sptr[J]) continue;
+        int32_t P = sup_of[srows[sptr[J]]];
+        spar[J] = P;
+        if (chead[P] == -1) chead[P] = (int32_t)J; else cnext[ctail[P]] = (int32_t)J;
+        ctail[P] = (int32_t)J;
+    }
+}
+
 }  // namespace
 
 int compose_relind(const int32_t *rJC, int64_t lenJC, const int32_t *rCP, int64_t lenCP, int32_t *out) {
@@ -350,6 +448,17 @@ int analyze_impl(int64_t n, const int64_t *colptr, const int32_t *rowind, const 
         }
     }
 
+    // sum over columns of |L_{*,j}|^2 of the true (fundamental) structure
+    s->flops = 0.0;
+    for (int64_t j = 0; j < n; j++) s->flops += (double)cc[j] * (double)cc[j];
+
+    // ---- optional supernode merging (Sec. 3.1), before the reordering within supernodes
+    if (o.merge_frac > 0.0) {
+        merge_supernodes(n, o.merge_frac, sup_ptr, sup_of, sptr, srows, spar, chead, cnext, ctail);
+        ns = (int64_t)sup_ptr.size() - 1;
+        s->nsuper = ns;
+    }
+
     // ---- partition refinement within supernodes (on the pre-PR structure)
     std::vector<int32_t> p3 = p1;
     if (o.pr) {
@@ -416,13 +525,9 @@ int analyze_impl(int64_t n, const int64_t *colptr, const int32_t *rowind, const 
     }
     s->sup_parent = spar;
     s->nnzL = 0;
-    s->flops = 0.0;
     for (int64_t J = 0; J < ns; J++) {
         int64_t m = s->gl_ptr[J + 1] - s->gl_ptr[J];
-        for (int32_t c = 0; c < sup_ptr[J + 1] - sup_ptr[J]; c++) {
-            s->nnzL += m - c;
-            s->flops += (double)(m - c) * (double)(m - c);
-        }
+        for (int32_t c = 0; c < sup_ptr[J + 1] - sup_ptr[J]; c++) s->nnzL += m - c;
     }
     // column elimination tree of the final ordering
     etree_liu(n, aptr, adj, s->perm, s->iperm, s->cparent);

@@ -25,6 +25,7 @@ int sc_options_default(sc_options *o) {
     o->pivot_tau = 1.0 / 1024.0;
     o->spin_limit = 1 << 22;
     o->use_graph = 1;
+    o->merge_frac = 0.0;
     return SC_OK;
 }
 
@@ -37,6 +38,7 @@ int sc_analyze(int64_t n, const int64_t *colptr, const int32_t *rowind, const sc
     if (opt.variant != SC_RLB && opt.variant != SC_RL) return -4;
     if (opt.precision < SC_FP64 || opt.precision > SC_TF32) return -4;
     if (opt.chunk < 1 || opt.chunk > 64) return -4;
+    if (!(opt.merge_frac >= 0.0)) return -4;
     try {
         return sc::analyze_impl(n, colptr, rowind, opt, out);
     } catch (const std::bad_alloc &) {
@@ -148,6 +150,13 @@ int sc_factor_profile(sc_numeric *h, const double *values, int values_on_device,
     if (!flops) return -6;
     if (!launches) return -7;
     return sc::numeric_profile(h, values, values_on_device, (cudaStream_t)cuda_stream, ms, flops, launches);
+}
+
+int sc_plan_stats(const sc_symbolic *s, int precision, int64_t *out, int nout) {
+    if (!s) return -1;
+    if (precision < SC_FP64 || precision > SC_TF32) return -2;
+    if (!out) return -3;
+    return sc::plan_stats(s, precision, out, nout);
 }
 
 void sc_numeric_free(sc_numeric *h) { sc::numeric_free(h); }

@@ -30,4 +30,26 @@ struct GemmTile {
 
 constexpr int kMaxChunk = 64;
 
+// Supernode descriptor for the device-side RLB loops.
+struct SnDev {
+    int64_t off;  // offset of Lnz(J)
+    int32_t ld;   // leading dimension of Lnz(J)
+    int32_t m;    // m_J = |glbind(J)|
+    int32_t f;    // first column
+    int32_t n;    // |J|
+    int32_t b1;   // one past J's last block
+    int32_t pad;
+};
+
+// Block descriptor (Sec. 1 / Alg. 5): rows pos..pos+size-1 of Lnz(J) hold the
+// global rows first..first+size-1, which are columns of supernode owner.
+// relindB(J, owner) starts at rb_val[rb] and covers J's blocks bs.. onward.
+struct BlkDev {
+    int32_t pos, size, first, owner;
+    int64_t rb;
+    int32_t bs, pad;
+};
+
+constexpr int kLoopSmemBytes = 48 * 1024;
+
 }  // namespace sc

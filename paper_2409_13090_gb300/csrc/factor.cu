@@ -88,6 +88,7 @@ int run_levels(sc_numeric *h, cudaStream_t st, Prof *prof = nullptr) {
     SC_CUDA(cudaMemsetAsync(h->d_lnz, 0, (size_t)s->lnz_size * sizeof(T), st));
     SC_CUDA(cudaMemsetAsync(h->d_info, 0x7f, sizeof(int32_t), st));
     SC_CUDA(cudaMemsetAsync(h->d_info + 1, 0, sizeof(int32_t), st));
+    SC_CUDA(cudaMemsetAsync(h->d_err, 0, sizeof(int32_t), st));
     int64_t nnz = (int64_t)s->valmap.size();
     k_diag<<<(unsigned)((s->n + 255) / 256), 256, 0, st>>>(h->d_adiag, h->d_diagpos, h->d_values, s->n);
     k_scatter_values<T><<<(unsigned)std::min<int64_t>((nnz + 255) / 256, 152 * 16), 256, 0, st>>>(
@@ -109,17 +110,27 @@ int run_levels(sc_numeric *h, cudaStream_t st, Prof *prof = nullptr) {
             E();
             launches++;
         }
+        if (p.loop_cnt) {
+            B(kProfLoop);
+            k_rlb_loop<T><<<p.loop_cnt, 256, p.loop_smem, st>>>(lnz, h->d_loops + p.loop_off, h->d_sn, h->d_blk,
+                                                                 h->d_rbval);
+            E();
+            launches++;
+        }
         if (p.gemm_cnt) {
             B(kProfGemm);
             k_gemm_tiles<T, kBM, kBN, kBK><<<p.gemm_cnt, 256, 0, st>>>(lnz, pool, h->d_tasks, h->d_gemm + p.gemm_off);
             E();
             launches++;
         }
-        if (p.tc_cnt) {
-            B(kProfTc);
-            if (!launch_tc_gemm(lnz, pool, h->d_tasks, h->d_gemm + p.tc_off, p.tc_cnt, st)) return SC_ERR_UNSUPPORTED;
-            E();
-            launches++;
+        if constexpr (sizeof(T) == 4) {
+            if (p.tc_cnt) {
+                B(kProfTc);
+                launch_tc_gemm((float *)lnz, h->d_tasks, h->d_gemm + p.tc_off, p.tc_cnt, h->d_tmaps, h->d_tmap_of_sn,
+                               h->d_err, (long long)s->opt.spin_limit, st);
+                E();
+                launches++;
+            }
         }
         if (p.small_cnt) {
             B(kProfSmall);
@@ -167,7 +178,135 @@ int set_smem_attrs() {
     return SC_OK;
 }
 
+// Host-only launch plan of one factorization for a precision: flat work lists
+// with per-level offsets (no device memory touched).
+struct Plan {
+    std::vector<ChunkDev> cd;
+    std::vector<int32_t> potrf, small;
+    std::vector<TrsmTile> trsm;
+    std::vector<GemmTile> gemm;
+    std::vector<Task> tasks;
+    std::vector<RLPair> rlpairs;
+    std::vector<LoopItem> loops;
+    std::vector<LevelPlan> levels;
+    double class_flops[kProfClasses] = {};
+};
+
+void build_plan(const sc_symbolic *s, int precision, Plan &P) {
+    P.cd.resize(s->chunks.size());
+    for (size_t c = 0; c < s->chunks.size(); c++) {
+        const Chunk &ch = s->chunks[c];
+        int32_t J = ch.sn;
+        P.cd[c] = ChunkDev{s->lnz_off[J], s->gl_ptr[J], s->lnz_ld[J], (int32_t)(s->gl_ptr[J + 1] - s->gl_ptr[J]), ch.c0,
+                           ch.w, s->sup_ptr[J] + ch.c0, 0};
+    }
+    const bool tc = precision == SC_TF32;
+    std::vector<int32_t> tmap_of_sn(s->nsuper, -1);
+    {
+        int32_t nm = 0;
+        for (int64_t J = 0; J < s->nsuper; J++)
+            if (s->sup_ptr[J + 1] - s->sup_ptr[J] >= 16) tmap_of_sn[J] = nm++;
+    }
+    P.levels.resize(s->levels.size());
+    for (size_t lv = 0; lv < s->levels.size(); lv++) {
+        const Level &L = s->levels[lv];
+        LevelPlan &p = P.levels[lv];
+        p.potrf_off = (int32_t)P.potrf.size();
+        for (int32_t c : L.chunks) {
+            P.potrf.push_back(c);
+            double w = P.cd[c].w;
+            P.class_flops[kProfPotrf] += w * w * w / 3.0;
+            P.class_flops[kProfTrsm] += (double)(P.cd[c].m - P.cd[c].c0 - P.cd[c].w) * w * w;
+        }
+        p.potrf_cnt = (int32_t)P.potrf.size() - p.potrf_off;
+        p.trsm_off = (int32_t)P.trsm.size();
+        for (int32_t c : L.chunks) {
+            const ChunkDev &ch = P.cd[c];
+            for (int32_t r0 = ch.c0 + ch.w; r0 < ch.m; r0 += kTrsmRows) P.trsm.push_back(TrsmTile{c, r0});
+        }
+        p.trsm_cnt = (int32_t)P.trsm.size() - p.trsm_off;
+        // product tasks: tensor-core tiles (TF32), SIMT tiles, warp tasks
+        std::vector<int32_t> ids_small;
+        std::vector<GemmTile> g_simt, g_tc;
+        for (const Task &t : L.tasks) {
+            int32_t id = (int32_t)P.tasks.size();
+            P.tasks.push_back(t);
+            if (is_small(t)) {
+                ids_small.push_back(id);
+                P.class_flops[kProfSmall] += task_flops(t);
+            } else if (tc && tc_eligible(t, tmap_of_sn)) {
+                tc_tiles_of(t, id, g_tc);
+                P.class_flops[kProfTc] += task_flops(t);
+            } else {
+                tiles_of(t, id, g_simt);
+                P.class_flops[kProfGemm] += task_flops(t);
+            }
+        }
+        p.gemm_off = (int32_t)P.gemm.size();
+        P.gemm.insert(P.gemm.end(), g_simt.begin(), g_simt.end());
+        p.gemm_cnt = (int32_t)g_simt.size();
+        p.tc_off = (int32_t)P.gemm.size();
+        P.gemm.insert(P.gemm.end(), g_tc.begin(), g_tc.end());
+        p.tc_cnt = (int32_t)g_tc.size();
+        p.small_off = (int32_t)P.small.size();
+        P.small.insert(P.small.end(), ids_small.begin(), ids_small.end());
+        p.small_cnt = (int32_t)ids_small.size();
+        // device-side RLB loops
+        p.loop_off = (int32_t)P.loops.size();
+        for (LoopItem it : L.loops) {
+            const int64_t mJ = s->gl_ptr[it.sn + 1] - s->gl_ptr[it.sn];
+            const int64_t nJ = s->sup_ptr[it.sn + 1] - s->sup_ptr[it.sn];
+            const int64_t bytes = mJ * (nJ + 1) * (precision == SC_FP64 ? 8 : 4);
+            it.smem = bytes <= kLoopSmemBytes ? 1 : 0;
+            if (it.smem) p.loop_smem = std::max<int32_t>(p.loop_smem, (int32_t)bytes);
+            P.loops.push_back(it);
+        }
+        p.loop_cnt = (int32_t)P.loops.size() - p.loop_off;
+        P.class_flops[kProfLoop] += L.loop_flops;
+        // RL update matrices and assembly
+        std::vector<int32_t> rl_small;
+        std::vector<GemmTile> rl_g;
+        for (const Task &t : L.rl_tasks) {
+            int32_t id = (int32_t)P.tasks.size();
+            P.tasks.push_back(t);
+            if (is_small(t)) rl_small.push_back(id);
+            else tiles_of(t, id, rl_g);
+            P.class_flops[kProfRlUpd] += task_flops(t);
+        }
+        p.rlg_off = (int32_t)P.gemm.size();
+        P.gemm.insert(P.gemm.end(), rl_g.begin(), rl_g.end());
+        p.rlg_cnt = (int32_t)rl_g.size();
+        p.rls_off = (int32_t)P.small.size();
+        P.small.insert(P.small.end(), rl_small.begin(), rl_small.end());
+        p.rls_cnt = (int32_t)rl_small.size();
+        p.rlp_off = (int32_t)P.rlpairs.size();
+        for (const RLPair &pr : L.rl_pairs) {
+            P.rlpairs.push_back(pr);
+            p.rlp_max = std::max<int64_t>(p.rlp_max, (int64_t)(pr.c_end - pr.c_begin) * (pr.s - pr.c_begin));
+            P.class_flops[kProfRlAsm] += (double)(pr.c_end - pr.c_begin) * (pr.s - pr.c_begin);
+        }
+        p.rlp_cnt = (int32_t)L.rl_pairs.size();
+    }
+}
+
 }  // namespace
+
+int plan_stats(const sc_symbolic *s, int precision, int64_t *out, int nout) {
+    Plan P;
+    build_plan(s, precision, P);
+    int64_t small_tasks = 0, tile_tasks = 0;
+    for (const LevelPlan &l : P.levels) small_tasks += l.small_cnt + l.rls_cnt;
+    tile_tasks = (int64_t)P.tasks.size() - small_tasks;
+    int64_t tc_tiles = 0, simt_tiles = 0;
+    for (const LevelPlan &l : P.levels) {
+        tc_tiles += l.tc_cnt;
+        simt_tiles += l.gemm_cnt + l.rlg_cnt;
+    }
+    int64_t v[] = {(int64_t)P.levels.size(), (int64_t)P.cd.size(), (int64_t)P.tasks.size(), small_tasks, tile_tasks,
+                   simt_tiles, tc_tiles, (int64_t)P.trsm.size(), (int64_t)P.rlpairs.size(), (int64_t)P.loops.size()};
+    for (int i = 0; i < nout && i < (int)(sizeof(v) / sizeof(v[0])); i++) out[i] = v[i];
+    return SC_OK;
+}
 
 int numeric_create(sc_symbolic *s, int precision, sc_numeric **out) {
     if (precision < SC_FP64 || precision > SC_TF32) return -3;
@@ -199,100 +338,54 @@ int numeric_create(sc_symbolic *s, int precision, sc_numeric **out) {
     }
     if (cudaMalloc((void **)&h->d_adiag, (size_t)s->n * sizeof(double)) != cudaSuccess) return fail(SC_ERR_OOM);
     if (cudaMalloc((void **)&h->d_info, 2 * sizeof(int32_t)) != cudaSuccess) return fail(SC_ERR_OOM);
-
-    // chunks
-    std::vector<ChunkDev> cd(s->chunks.size());
-    for (size_t c = 0; c < s->chunks.size(); c++) {
-        const Chunk &ch = s->chunks[c];
-        int32_t J = ch.sn;
-        cd[c] = ChunkDev{s->lnz_off[J], s->gl_ptr[J], s->lnz_ld[J], (int32_t)(s->gl_ptr[J + 1] - s->gl_ptr[J]), ch.c0,
-                         ch.w, s->sup_ptr[J] + ch.c0, 0};
+    if (cudaMalloc((void **)&h->d_err, sizeof(int32_t)) != cudaSuccess) return fail(SC_ERR_OOM);
+    if (precision == SC_TF32) {
+        std::vector<CUtensorMap> maps;
+        std::vector<int32_t> tmap_of_sn;
+        if ((rc = tc_encode_maps(s, (float *)h->d_lnz, maps, tmap_of_sn))) return fail(rc);
+        if ((rc = upload(h->d_tmaps, maps, bytes))) return fail(rc);
+        if ((rc = upload(h->d_tmap_of_sn, tmap_of_sn, bytes))) return fail(rc);
     }
-    if ((rc = upload(h->d_chunks, cd, bytes))) return fail(rc);
-
-    // per-level work lists
-    std::vector<int32_t> potrf, small;
-    std::vector<TrsmTile> trsm;
-    std::vector<GemmTile> gemm;
-    std::vector<Task> tasks;
-    std::vector<RLPair> rlpairs;
-    const bool tc = precision == SC_TF32;
-    h->plans.resize(s->levels.size());
-    for (size_t lv = 0; lv < s->levels.size(); lv++) {
-        const Level &L = s->levels[lv];
-        LevelPlan &p = h->plans[lv];
-        p.potrf_off = (int32_t)potrf.size();
-        for (int32_t c : L.chunks) {
-            potrf.push_back(c);
-            double w = cd[c].w;
-            h->class_flops[kProfPotrf] += w * w * w / 3.0;
-            h->class_flops[kProfTrsm] += (double)(cd[c].m - cd[c].c0 - cd[c].w) * w * w;
-        }
-        p.potrf_cnt = (int32_t)potrf.size() - p.potrf_off;
-        p.trsm_off = (int32_t)trsm.size();
-        for (int32_t c : L.chunks) {
-            const ChunkDev &ch = cd[c];
-            for (int32_t r0 = ch.c0 + ch.w; r0 < ch.m; r0 += kTrsmRows) trsm.push_back(TrsmTile{c, r0});
-        }
-        p.trsm_cnt = (int32_t)trsm.size() - p.trsm_off;
-        // product tasks: tensor-core tiles (TF32), SIMT tiles, warp tasks
-        std::vector<int32_t> ids_small;
-        std::vector<GemmTile> g_simt, g_tc;
-        for (const Task &t : L.tasks) {
-            int32_t id = (int32_t)tasks.size();
-            tasks.push_back(t);
-            if (is_small(t)) {
-                ids_small.push_back(id);
-                h->class_flops[kProfSmall] += task_flops(t);
-            } else if (tc && tc_eligible(t)) {
-                tc_tiles_of(t, id, g_tc);
-                h->class_flops[kProfTc] += task_flops(t);
-            } else {
-                tiles_of(t, id, g_simt);
-                h->class_flops[kProfGemm] += task_flops(t);
+    Plan P;
+    build_plan(s, precision, P);
+    std::copy(P.class_flops, P.class_flops + kProfClasses, h->class_flops);
+    h->plans = P.levels;
+    h->ntasks = (int32_t)P.tasks.size();
+    if ((rc = upload(h->d_chunks, P.cd, bytes))) return fail(rc);
+    if ((rc = upload(h->d_potrf, P.potrf, bytes))) return fail(rc);
+    if ((rc = upload(h->d_trsm, P.trsm, bytes))) return fail(rc);
+    if ((rc = upload(h->d_gemm, P.gemm, bytes))) return fail(rc);
+    if ((rc = upload(h->d_small, P.small, bytes))) return fail(rc);
+    if ((rc = upload(h->d_tasks, P.tasks, bytes))) return fail(rc);
+    if ((rc = upload(h->d_rlpairs, P.rlpairs, bytes))) return fail(rc);
+    if ((rc = upload(h->d_rlrelind, s->rl_relind, bytes))) return fail(rc);
+    if ((rc = upload(h->d_loops, P.loops, bytes))) return fail(rc);
+    {
+        std::vector<SnDev> snd(s->nsuper);
+        for (int64_t J = 0; J < s->nsuper; J++)
+            snd[J] = SnDev{s->lnz_off[J], s->lnz_ld[J], (int32_t)(s->gl_ptr[J + 1] - s->gl_ptr[J]), s->sup_ptr[J],
+                           s->sup_ptr[J + 1] - s->sup_ptr[J], (int32_t)s->blk_ptr[J + 1], 0};
+        std::vector<BlkDev> bd(s->blk_first.size());
+        for (int64_t J = 0; J < s->nsuper; J++) {
+            int64_t b0 = s->blk_ptr[J], b1 = s->blk_ptr[J + 1];
+            int32_t q = s->sup_ptr[J + 1] - s->sup_ptr[J];
+            for (int64_t b = b0; b < b1; b++) {
+                bd[b] = BlkDev{q, s->blk_size[b], s->blk_first[b], s->blk_owner[b], 0, 0, 0};
+                q += s->blk_size[b];
+            }
+            for (int64_t pq = s->rb_pair_ptr[J]; pq < s->rb_pair_ptr[J + 1]; pq++) {
+                int64_t cnt = s->rb_val_ptr[pq + 1] - s->rb_val_ptr[pq];
+                int64_t bs = b1 - cnt;
+                for (int64_t b = bs; b < b1 && s->blk_owner[b] == s->rb_pair_P[pq]; b++) {
+                    bd[b].rb = s->rb_val_ptr[pq];
+                    bd[b].bs = (int32_t)bs;
+                }
             }
         }
-        p.gemm_off = (int32_t)gemm.size();
-        gemm.insert(gemm.end(), g_simt.begin(), g_simt.end());
-        p.gemm_cnt = (int32_t)g_simt.size();
-        p.tc_off = (int32_t)gemm.size();
-        gemm.insert(gemm.end(), g_tc.begin(), g_tc.end());
-        p.tc_cnt = (int32_t)g_tc.size();
-        p.small_off = (int32_t)small.size();
-        small.insert(small.end(), ids_small.begin(), ids_small.end());
-        p.small_cnt = (int32_t)ids_small.size();
-        // RL update matrices and assembly
-        std::vector<int32_t> rl_small;
-        std::vector<GemmTile> rl_g;
-        for (const Task &t : L.rl_tasks) {
-            int32_t id = (int32_t)tasks.size();
-            tasks.push_back(t);
-            if (is_small(t)) rl_small.push_back(id);
-            else tiles_of(t, id, rl_g);
-            h->class_flops[kProfRlUpd] += task_flops(t);
-        }
-        p.rlg_off = (int32_t)gemm.size();
-        gemm.insert(gemm.end(), rl_g.begin(), rl_g.end());
-        p.rlg_cnt = (int32_t)rl_g.size();
-        p.rls_off = (int32_t)small.size();
-        small.insert(small.end(), rl_small.begin(), rl_small.end());
-        p.rls_cnt = (int32_t)rl_small.size();
-        p.rlp_off = (int32_t)rlpairs.size();
-        for (const RLPair &pr : L.rl_pairs) {
-            rlpairs.push_back(pr);
-            p.rlp_max = std::max<int64_t>(p.rlp_max, (int64_t)(pr.c_end - pr.c_begin) * (pr.s - pr.c_begin));
-            h->class_flops[kProfRlAsm] += (double)(pr.c_end - pr.c_begin) * (pr.s - pr.c_begin);
-        }
-        p.rlp_cnt = (int32_t)L.rl_pairs.size();
+        if ((rc = upload(h->d_sn, snd, bytes))) return fail(rc);
+        if ((rc = upload(h->d_blk, bd, bytes))) return fail(rc);
+        if ((rc = upload(h->d_rbval, s->rb_val, bytes))) return fail(rc);
     }
-    h->ntasks = (int32_t)tasks.size();
-    if ((rc = upload(h->d_potrf, potrf, bytes))) return fail(rc);
-    if ((rc = upload(h->d_trsm, trsm, bytes))) return fail(rc);
-    if ((rc = upload(h->d_gemm, gemm, bytes))) return fail(rc);
-    if ((rc = upload(h->d_small, small, bytes))) return fail(rc);
-    if ((rc = upload(h->d_tasks, tasks, bytes))) return fail(rc);
-    if ((rc = upload(h->d_rlpairs, rlpairs, bytes))) return fail(rc);
-    if ((rc = upload(h->d_rlrelind, s->rl_relind, bytes))) return fail(rc);
     s->refs++;
     *out = h;
     return SC_OK;
@@ -329,9 +422,11 @@ int numeric_factor(sc_numeric *h, const double *values, int on_device, cudaStrea
         if (rc) return rc;
     }
     SC_CUDA(cudaEventRecord(e1, st));
-    int32_t hinfo[2];
+    int32_t hinfo[2], herr = 0;
     SC_CUDA(cudaMemcpyAsync(hinfo, h->d_info, sizeof(hinfo), cudaMemcpyDeviceToHost, st));
+    SC_CUDA(cudaMemcpyAsync(&herr, h->d_err, sizeof(herr), cudaMemcpyDeviceToHost, st));
     SC_CUDA(cudaStreamSynchronize(st));
+    if (herr) return SC_ERR_TIMEOUT;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
@@ -403,7 +498,8 @@ void numeric_free(sc_numeric *h) {
     void *ptrs[] = {h->d_lnz, h->d_pool, h->d_valmap, h->d_values, h->d_diagpos, h->d_adiag, h->d_info,
                     h->d_chunks, h->d_potrf, h->d_trsm, h->d_gemm, h->d_small, h->d_tasks, h->d_rlpairs,
                     h->d_rlrelind, h->d_glbind, h->d_perm, h->d_csr_ptr, h->d_csr_col, h->d_csr_val,
-                    h->d_csr_map, h->d_counters, h->d_xw, h->d_solve_tiles, h->d_x, h->d_r, h->d_b, h->d_xbest, h->d_y, h->d_z, h->d_acc, h->d_red};
+                    h->d_csr_map, h->d_counters, h->d_xw, h->d_solve_tiles, h->d_sn, h->d_blk, h->d_rbval,
+                    h->d_loops, h->d_tmaps, h->d_tmap_of_sn, h->d_err, h->d_x, h->d_r, h->d_b, h->d_xbest, h->d_y, h->d_z, h->d_acc, h->d_red};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->sym) h->sym->refs--;

@@ -198,6 +198,7 @@ __global__ void __launch_bounds__(256) k_gemm_tiles(T *__restrict__ lnz, T *__re
     }
     const bool lower = tk.flags & kTaskLower;
     const bool store = tk.flags & kTaskStoreU;
+    const bool excl = tk.flags & kTaskExclusive;
     T *C = (store ? pool : lnz) + tk.c_off;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
@@ -207,8 +208,10 @@ __global__ void __launch_bounds__(256) k_gemm_tiles(T *__restrict__ lnz, T *__re
         for (int j = 0; j < 4; j++) {
             int gj = col0 + tx + 16 * j;
             if (gj >= tk.n || (lower && gj > gi)) continue;
-            if (store) C[(int64_t)gi * tk.ldc + gj] = -acc[i][j];
-            else atomicAdd(C + (int64_t)gi * tk.ldc + gj, -acc[i][j]);
+            T *c = C + (int64_t)gi * tk.ldc + gj;
+            if (store) *c = -acc[i][j];
+            else if (excl) *c -= acc[i][j];
+            else atomicAdd(c, -acc[i][j]);
         }
     }
 }
@@ -235,6 +238,85 @@ __global__ void __launch_bounds__(256) k_small_tasks(T *__restrict__ lnz, T *__r
         for (int k = 0; k < tk.k; k++) acc += a[k] * b[k];
         if (store) C[(int64_t)i * tk.ldc + j] = -acc;
         else atomicAdd(C + (int64_t)i * tk.ldc + j, -acc);
+    }
+}
+
+// --------------------------------------------------------------------- K3 (device loops)
+// Alg. 5 lines 10-16 for a range of J's blocks, in one CTA: for each block B
+// (inside ancestor P): SYRK L_{B,B} -= L_{B,J} L_{B,J}^T, then for each maximal
+// run B' of blocks below B: GEMM L_{B',B} -= L_{B',J} L_{B,J}^T, both straight
+// into Lnz(P) at the rows given by relindB(J,P). Products that tile_task()
+// routes to the tiled kernels are skipped here. J's panel is staged in shared
+// memory when it fits. Entries are added atomically (other supernodes of the
+// level may update the same ancestor entries).
+__device__ inline int tri_row(int e) {
+    int i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+    while ((i + 1) * (i + 2) / 2 <= e) i++;
+    while (i * (i + 1) / 2 > e) i--;
+    return i;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_rlb_loop(T *__restrict__ lnz, const LoopItem *__restrict__ items,
+                                                  const SnDev *__restrict__ sn, const BlkDev *__restrict__ blk,
+                                                  const int32_t *__restrict__ rb_val) {
+    extern __shared__ __align__(16) unsigned char smem_loop[];
+    const LoopItem it = items[blockIdx.x];
+    const SnDev J = sn[it.sn];
+    const int K = J.n;
+    const T *src = lnz + J.off;
+    T *panel = reinterpret_cast<T *>(smem_loop);
+    const int ldp = K + 1;
+    if (it.smem) {
+        for (int idx = threadIdx.x; idx < J.m * K; idx += blockDim.x) {
+            int r = idx / K, c = idx % K;
+            panel[r * ldp + c] = src[(int64_t)r * J.ld + c];
+        }
+        __syncthreads();
+    }
+    const T *base = it.smem ? panel : src;
+    const int ldb = it.smem ? ldp : J.ld;
+    for (int b = it.b_lo; b < it.b_hi; b++) {
+        const BlkDev B = blk[b];
+        const SnDev P = sn[B.owner];
+        const int colB = B.first - P.f;
+        const int nb = B.size;
+        const long long tri = (long long)nb * (nb + 1) / 2;
+        if (!tile_task(tri, K)) {
+            T *C = lnz + P.off + (int64_t)colB * P.ld + colB;
+            for (int e = threadIdx.x; e < (int)tri; e += blockDim.x) {
+                int i = tri_row(e), j = e - i * (i + 1) / 2;
+                const T *a = base + (int64_t)(B.pos + i) * ldb;
+                const T *bb = base + (int64_t)(B.pos + j) * ldb;
+                T acc = T(0);
+                for (int k = 0; k < K; k++) acc += a[k] * bb[k];
+                atomicAdd(C + (int64_t)i * P.ld + j, -acc);
+            }
+        }
+        int r = b + 1;
+        while (r < J.b1) {
+            int e = r;
+            int rows = blk[r].size;
+            while (e + 1 < J.b1 && blk[e + 1].first == blk[e].first + blk[e].size) {
+                e++;
+                rows += blk[e].size;
+            }
+            if (!tile_task((long long)rows * nb, K)) {
+                const int rowP = P.m - 1 - rb_val[B.rb + (r - B.bs)];
+                T *C = lnz + P.off + (int64_t)rowP * P.ld + colB;
+                const int apos = blk[r].pos;
+                const int tot = rows * nb;
+                for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+                    int i = q / nb, j = q % nb;
+                    const T *a = base + (int64_t)(apos + i) * ldb;
+                    const T *bb = base + (int64_t)(B.pos + j) * ldb;
+                    T acc = T(0);
+                    for (int k = 0; k < K; k++) acc += a[k] * bb[k];
+                    atomicAdd(C + (int64_t)i * P.ld + j, -acc);
+                }
+            }
+            r = e + 1;
+        }
     }
 }
 

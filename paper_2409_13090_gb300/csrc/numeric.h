@@ -1,6 +1,7 @@
 // Numeric handle of libsc: device buffers and the launch plan of one
 // factorization (factor.cu) and of the solve (solve.cu).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -19,6 +20,8 @@ struct LevelPlan {
     int32_t small_off = 0, small_cnt = 0;   // task ids (warp kernel)
     int32_t rlg_off = 0, rlg_cnt = 0;       // GemmTile of RL update matrices
     int32_t rls_off = 0, rls_cnt = 0;       // task ids of small RL update matrices
+    int32_t loop_off = 0, loop_cnt = 0;     // LoopItem (device-side RLB loops)
+    int32_t loop_smem = 0;                  // dynamic shared memory of the loop launch
     int32_t rlp_off = 0, rlp_cnt = 0;       // RLPair
     int64_t rlp_max = 0;                    // largest assembly work item (elements)
     // solve
@@ -26,7 +29,7 @@ struct LevelPlan {
 };
 
 // kernel classes of the per-kernel profile
-enum { kProfK0 = 0, kProfPotrf, kProfTrsm, kProfGemm, kProfTc, kProfSmall, kProfRlUpd, kProfRlAsm, kProfClasses };
+enum { kProfK0 = 0, kProfPotrf, kProfTrsm, kProfGemm, kProfTc, kProfSmall, kProfRlUpd, kProfRlAsm, kProfLoop, kProfClasses };
 
 template <typename T>
 struct DevArray {
@@ -56,6 +59,13 @@ struct sc_numeric {
     int32_t *d_small = nullptr;
     sc::Task *d_tasks = nullptr;
     sc::RLPair *d_rlpairs = nullptr;
+    sc::SnDev *d_sn = nullptr;
+    sc::BlkDev *d_blk = nullptr;
+    int32_t *d_rbval = nullptr;
+    sc::LoopItem *d_loops = nullptr;
+    CUtensorMap *d_tmaps = nullptr;   // one per panel of width >= 16 (SC_TF32)
+    int32_t *d_tmap_of_sn = nullptr;
+    int32_t *d_err = nullptr;         // nonzero after a bounded device wait gave up
     int32_t *d_rlrelind = nullptr;
     // solve
     int32_t *d_glbind = nullptr;
@@ -91,6 +101,7 @@ int numeric_factor(sc_numeric *h, const double *values, int on_device, cudaStrea
 int numeric_solve(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, double *X, int64_t ldx, int on_device,
                   cudaStream_t st, sc_solve_info *info);
 int numeric_export_L(const sc_numeric *h, double *out);
+int plan_stats(const sc_symbolic *s, int precision, int64_t *out, int nout);
 int numeric_profile(sc_numeric *h, const double *values, int on_device, cudaStream_t st, double *ms, double *flops,
                     int32_t *launches);
 void numeric_free(sc_numeric *h);

@@ -19,10 +19,36 @@ namespace sc {
 struct Task {
     int64_t a_off, b_off, c_off;
     int32_t lds, ldc, m, n, k, flags;
+    int32_t src;    // source supernode J
+    int32_t a_row;  // first row of A in Lnz(J)
+    int32_t b_row;  // first row of B in Lnz(J)
+    int32_t kx0;    // first column of A and B in Lnz(J)
 };
 enum : int32_t {
-    kTaskLower = 1,   // only entries with local row >= local column are written
-    kTaskStoreU = 2,  // C is an RL update matrix: C = -A B^T (plain store, no accumulate)
+    kTaskLower = 1,      // only entries with local row >= local column are written
+    kTaskStoreU = 2,     // C is an RL update matrix: C = -A B^T (plain store, no accumulate)
+    kTaskExclusive = 4,  // no other task of the level writes C: plain read-modify-write
+};
+
+#ifdef __CUDACC__
+#define SC_HD __host__ __device__
+#else
+#define SC_HD
+#endif
+
+// Which RLB products run as tiled GEMMs (the rest run inside the device loop
+// over J's blocks). entries = outputs of the product, k = inner dimension.
+SC_HD inline bool tile_task(long long entries, int k) {
+    return (entries >= 1024 && k >= 16) || entries >= 8192;
+}
+
+// A range of blocks B of supernode J whose Alg. 5 loops (SYRK on B, GEMM for
+// each maximal B' below B) run on the device in one CTA.
+struct LoopItem {
+    int32_t sn;    // J
+    int32_t b_lo;  // first block (global block index)
+    int32_t b_hi;  // one past the last block
+    int32_t smem;  // set by the launch plan: 1 = J's panel is staged in shared memory
 };
 
 // One panel of at most `chunk` columns of a supernode; the unit of the dense
@@ -49,10 +75,12 @@ struct RLPair {
 struct Level {
     std::vector<int32_t> chunks;       // chunks factored at this level
     std::vector<int32_t> last_chunks;  // of which: the last chunk of their supernode
-    std::vector<Task> tasks;           // RLB updates + intra-supernode trailing updates
+    std::vector<Task> tasks;           // tiled products: large RLB updates + intra-supernode trailing updates
+    std::vector<LoopItem> loops;       // device-side RLB loops (the remaining products)
     std::vector<Task> rl_tasks;        // RL: U_J products (variant RL only)
     std::vector<RLPair> rl_pairs;      // RL: assembly work (variant RL only)
     int64_t rl_pool = 0;               // RL: pool elements needed by this level
+    double loop_flops = 0;             // algorithmic flops of the device loops
 };
 
 }  // namespace sc

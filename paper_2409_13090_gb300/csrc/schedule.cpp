@@ -83,7 +83,10 @@ int build_schedule(sc_symbolic *s) {
                 t.m = (int32_t)(mJ - r0);
                 t.n = nJ - r0;
                 t.k = ch.w;
-                t.flags = kTaskLower;
+                t.flags = kTaskLower | kTaskExclusive;
+                t.src = J;
+                t.a_row = t.b_row = r0;
+                t.kx0 = ch.c0;
                 L.tasks.push_back(t);
                 continue;
             }
@@ -99,6 +102,11 @@ int build_schedule(sc_symbolic *s) {
                 }
             }
             if (!rl) {
+                // Alg. 5 lines 7-17 for J: large (B, B') products become tiled tasks;
+                // the rest run in device loops over ranges of J's blocks.
+                const int64_t kLoopBudget = 1 << 17;
+                LoopItem cur_item{(int32_t)J, (int32_t)b0, (int32_t)b0, 0};
+                int64_t cost = 0;
                 for (int64_t q = s->rb_pair_ptr[J]; q < s->rb_pair_ptr[J + 1]; q++) {
                     int32_t P = s->rb_pair_P[q];
                     const int32_t *rb = s->rb_val.data() + s->rb_val_ptr[q];
@@ -112,16 +120,27 @@ int build_schedule(sc_symbolic *s) {
                         int64_t posB = mP - 1 - rb[b - bs];
                         int32_t colB = s->blk_first[b] - fP;
                         if (posB != colB) return SC_ERR_INTERNAL;
-                        Task t;
-                        t.a_off = offJ + bpos[b - b0] * ldJ;
-                        t.b_off = t.a_off;
-                        t.c_off = offP + posB * ldP + colB;
-                        t.lds = ldJ;
-                        t.ldc = ldP;
-                        t.m = t.n = s->blk_size[b];
-                        t.k = nJ;
-                        t.flags = kTaskLower;
-                        L.tasks.push_back(t);
+                        int32_t nb = s->blk_size[b];
+                        int64_t bcost = 0;
+                        long long tri = (long long)nb * (nb + 1) / 2;
+                        if (tile_task(tri, nJ)) {
+                            Task t;
+                            t.a_off = offJ + bpos[b - b0] * ldJ;
+                            t.b_off = t.a_off;
+                            t.c_off = offP + posB * ldP + colB;
+                            t.lds = ldJ;
+                            t.ldc = ldP;
+                            t.m = t.n = nb;
+                            t.k = nJ;
+                            t.flags = kTaskLower;
+                            t.src = J;
+                            t.a_row = t.b_row = (int32_t)bpos[b - b0];
+                            t.kx0 = 0;
+                            L.tasks.push_back(t);
+                        } else {
+                            bcost += tri * (nJ + 4);
+                            L.loop_flops += 2.0 * (double)tri * nJ;
+                        }
                         // maximal blocks B' below B: runs of blocks whose rows abut
                         int64_t r = b + 1;
                         while (r < b1) {
@@ -131,21 +150,41 @@ int build_schedule(sc_symbolic *s) {
                                 e++;
                                 rows += s->blk_size[e];
                             }
-                            Task g;
-                            g.a_off = offJ + bpos[r - b0] * ldJ;
-                            g.b_off = offJ + bpos[b - b0] * ldJ;
-                            g.c_off = offP + (mP - 1 - rb[r - bs]) * ldP + colB;
-                            g.lds = ldJ;
-                            g.ldc = ldP;
-                            g.m = rows;
-                            g.n = s->blk_size[b];
-                            g.k = nJ;
-                            g.flags = 0;
-                            L.tasks.push_back(g);
+                            if (tile_task((long long)rows * nb, nJ)) {
+                                Task g;
+                                g.a_off = offJ + bpos[r - b0] * ldJ;
+                                g.b_off = offJ + bpos[b - b0] * ldJ;
+                                g.c_off = offP + (mP - 1 - rb[r - bs]) * ldP + colB;
+                                g.lds = ldJ;
+                                g.ldc = ldP;
+                                g.m = rows;
+                                g.n = nb;
+                                g.k = nJ;
+                                g.flags = 0;
+                                g.src = J;
+                                g.a_row = (int32_t)bpos[r - b0];
+                                g.b_row = (int32_t)bpos[b - b0];
+                                g.kx0 = 0;
+                                L.tasks.push_back(g);
+                            } else {
+                                bcost += (int64_t)rows * nb * (nJ + 4);
+                                L.loop_flops += 2.0 * (double)rows * nb * nJ;
+                            }
                             r = e + 1;
+                        }
+                        // blocks are visited in ascending order: extend the current loop item
+                        if (bcost > 0) {
+                            if (cur_item.b_hi != b || cost >= kLoopBudget) {
+                                if (cur_item.b_hi > cur_item.b_lo) L.loops.push_back(cur_item);
+                                cur_item = LoopItem{(int32_t)J, (int32_t)b, (int32_t)b, 0};
+                                cost = 0;
+                            }
+                            cur_item.b_hi = (int32_t)b + 1;
+                            cost += bcost;
                         }
                     }
                 }
+                if (cur_item.b_hi > cur_item.b_lo) L.loops.push_back(cur_item);
             } else {
                 // RL: U_J = -L_{S,J} L_{S,J}^T into the level's pool
                 int32_t sJ = (int32_t)(mJ - nJ);
@@ -158,6 +197,9 @@ int build_schedule(sc_symbolic *s) {
                 t.m = t.n = sJ;
                 t.k = nJ;
                 t.flags = kTaskLower | kTaskStoreU;
+                t.src = J;
+                t.a_row = t.b_row = nJ;
+                t.kx0 = 0;
                 L.rl_tasks.push_back(t);
                 int64_t u_off = L.rl_pool;
                 L.rl_pool += (int64_t)sJ * sJ;

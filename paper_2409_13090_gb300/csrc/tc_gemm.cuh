@@ -1,12 +1,292 @@
-// Tensor-core (tcgen05, TF32) product tiles for SC_TF32. Placeholder until the
-// tcgen05 kernel lands: no task is routed here, so SC_TF32 runs the SIMT FP32 path.
+// Tensor-core product tiles for SC_TF32 (sm_103a): C[128 x 128 tile] -= A B^T
+// with A, B row slabs of one FP32 supernode panel, TF32 inputs, FP32 accumulate.
+//
+//   TMA (cp.async.bulk.tensor, 128-byte swizzle, one tensor map per source
+//   panel held in global memory) -> 4-stage shared-memory ring guarded by
+//   mbarriers -> tcgen05.mma.cta_group::1.kind::tf32 (M=128, N=128, K=8) issued
+//   by one thread into a 128-column TMEM accumulator -> tcgen05.ld by the four
+//   warps (each owns 32 TMEM lanes = 32 output rows) -> subtract into the
+//   target block of Lnz(P) (plain read-modify-write for an exclusive target,
+//   atomic add otherwise).
+// Operands are K-major: a panel row is contiguous along the supernode's
+// columns, which is the inner (K) dimension of every update product.
+// Every wait is bounded by spin_limit iterations; on expiry the kernel sets
+// *err, stops issuing, waits (bounded) for what it issued, frees TMEM and
+// returns without writing its tile.
 #pragma once
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <vector>
+
 #include "kernels.cuh"
 
 namespace sc {
-inline bool tc_gemm_init() { return true; }
-inline bool tc_eligible(const Task &) { return false; }
-inline void tc_tiles_of(const Task &, int32_t, std::vector<GemmTile> &) {}
-template <typename T>
-inline bool launch_tc_gemm(T *, T *, const Task *, const GemmTile *, int32_t, cudaStream_t) { return false; }
+namespace tc {
+
+constexpr int BM = 128, BN = 128, BK = 32;  // BK fp32 = 128 bytes = one swizzle row
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * BK * 4;
+constexpr int B_BYTES = BN * BK * 4;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*alignment*/ + 256 /*barriers*/;
+constexpr int TMEM_COLS = 128;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait: false (and *err set) when spin_limit polls pass without completion
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long spin_limit, int32_t *err,
+                                          int code) {
+    for (long long i = 0; i < spin_limit; i++)
+        if (mbar_try_wait(bar, parity)) return true;
+    atomicExch(err, code);
+    return false;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            dst),
+        "l"(map), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);  // start address
+    d |= (uint64_t)1 << 16;                  // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;                  // descriptor version
+    d |= (uint64_t)2 << 61;                  // swizzle mode: 128 B
+    return d;
+}
+// instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major, M = 128, N = 128
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accum)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(128, 1)
+    k_tc_gemm(float *__restrict__ lnz, const Task *__restrict__ tasks, const GemmTile *__restrict__ tiles,
+              const CUtensorMap *__restrict__ tmaps, const int32_t *__restrict__ tmap_of_sn, int32_t *__restrict__ err,
+              long long spin_limit) {
+    extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);  // full[S], empty[S], done
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 1);
+    __shared__ int abort_flag;
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const GemmTile tl = tiles[blockIdx.x];
+    const Task tk = tasks[tl.task];
+    const CUtensorMap *map = tmaps + tmap_of_sn[tk.src];
+    const int nk = (tk.k + BK - 1) / BK;
+    const int ay = tk.a_row + tl.tm * BM, by = tk.b_row + tl.tn * BN;
+
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < 2 * STAGES + 1; s++) mbar_init(smem_u32(bars + s), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(map) : "memory");
+    }
+    __syncwarp();  // thread 0 rejoins warp 0 before the warp-collective allocation
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_holder;
+
+    int issued = 0;  // stages loaded by the producer (for the bounded drain on abort)
+    if (warp == 0 && lane == 0) {
+        // producer: TMA loads of A and B k-blocks into the ring
+        for (int kb = 0; kb < nk; kb++) {
+            const int s = kb % STAGES;
+            const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+            if (kb >= STAGES && !mbar_wait(smem_u32(bars + STAGES + s), ph ^ 1u, spin_limit, err, 1)) {
+                abort_flag = 1;
+                break;
+            }
+            if (abort_flag) break;
+            const uint32_t full = smem_u32(bars + s);
+            mbar_expect_tx(full, STAGE_BYTES);
+            const int x = tk.kx0 + kb * BK;
+            tma_load_2d(smem_u32(smem + s * A_BYTES), map, x, ay, full);
+            tma_load_2d(smem_u32(smem + STAGES * A_BYTES + s * B_BYTES), map, x, by, full);
+            issued = kb + 1;
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        for (int kb = 0; kb < nk; kb++) {
+            const int s = kb % STAGES;
+            const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+            if (!mbar_wait(smem_u32(bars + s), ph, spin_limit, err, 2)) {
+                abort_flag = 1;
+                break;
+            }
+            fence_after();
+            const uint32_t a0 = smem_u32(smem + s * A_BYTES);
+            const uint32_t b0 = smem_u32(smem + STAGES * A_BYTES + s * B_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < BK / 8; kk++) {
+                // advance 8 tf32 = 32 bytes along K inside the swizzle row
+                mma_tf32(tmem, umma_desc_sw128(a0 + kk * 32), umma_desc_sw128(b0 + kk * 32), (kb > 0 || kk > 0) ? 1u : 0u);
+            }
+            mma_commit(smem_u32(bars + STAGES + s));  // frees stage s when these MMAs finish
+        }
+        mma_commit(smem_u32(bars + 2 * STAGES));  // accumulator complete
+    }
+    __syncwarp();
+
+    // epilogue: every warp waits for the accumulator, reads its 32 lanes
+    const bool ok = mbar_wait(smem_u32(bars + 2 * STAGES), 0, spin_limit, err, 3);
+    fence_after();
+    // the collective tcgen05.ld below needs a warp-uniform decision
+    if (__all_sync(0xffffffffu, ok && !abort_flag)) {
+        const int row = warp * 32 + lane;
+        const int gi = tl.tm * BM + row;
+        const bool lower = tk.flags & kTaskLower;
+        const bool excl = tk.flags & kTaskExclusive;
+        float *crow = lnz + tk.c_off + (int64_t)gi * tk.ldc;
+#pragma unroll 1
+        for (int cc = 0; cc < BN / 32; cc++) {
+            float v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), v);
+            if (gi < tk.m) {
+#pragma unroll
+                for (int j = 0; j < 32; j++) {
+                    const int gj = tl.tn * BN + cc * 32 + j;
+                    if (gj < tk.n && (!lower || gj <= gi)) {
+                        if (excl) crow[gj] -= v[j];
+                        else atomicAdd(crow + gj, -v[j]);
+                    }
+                }
+            }
+        }
+    }
+    // drain: on an abort, wait (bounded) for every TMA load the producer issued
+    if (warp == 0 && lane == 0 && abort_flag) {
+        for (int kb = 0; kb < issued; kb++) {
+            if (kb + STAGES < issued) continue;  // later loads to the same stage implied completion
+            mbar_wait(smem_u32(bars + kb % STAGES), (uint32_t)(kb / STAGES) & 1u, spin_limit, err, 4);
+        }
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+}  // namespace tc
+
+// ---------------------------------------------------------------- host side
+inline bool tc_gemm_init() {
+    return cudaFuncSetAttribute(tc::k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES) ==
+           cudaSuccess;
+}
+
+// A product goes to the tensor cores when its source panel has a tensor map
+// (|J| >= 16: 16-byte row stride, 128-byte aligned base) and it fills a good
+// part of a 128 x 128 tile with K >= 32.
+inline bool tc_eligible(const Task &t, const std::vector<int32_t> &tmap_of_sn) {
+    return tmap_of_sn[t.src] >= 0 && t.k >= 32 && t.m >= 64 && t.n >= 32 && !(t.flags & kTaskStoreU);
+}
+
+inline void tc_tiles_of(const Task &t, int32_t id, std::vector<GemmTile> &out) {
+    int tm = (t.m + tc::BM - 1) / tc::BM, tn = (t.n + tc::BN - 1) / tc::BN;
+    for (int i = 0; i < tm; i++)
+        for (int j = 0; j < tn; j++) {
+            if ((t.flags & kTaskLower) && (i * tc::BM + tc::BM - 1) < j * tc::BN) continue;
+            out.push_back(GemmTile{id, i, j, 0});
+        }
+}
+
+// Encodes one 2D tensor map per panel of width >= 16 (dims {ld_J, m_J}, box
+// {32, 128}, 128-byte swizzle, zero fill outside the panel).
+inline int tc_encode_maps(const sc_symbolic *s, float *d_lnz, std::vector<CUtensorMap> &maps,
+                          std::vector<int32_t> &tmap_of_sn) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return SC_ERR_CUDA;
+        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    tmap_of_sn.assign(s->nsuper, -1);
+    maps.clear();
+    for (int64_t J = 0; J < s->nsuper; J++) {
+        int32_t w = s->sup_ptr[J + 1] - s->sup_ptr[J];
+        if (w < 16) continue;
+        int64_t m = s->gl_ptr[J + 1] - s->gl_ptr[J];
+        CUtensorMap map;
+        cuuint64_t dims[2] = {(cuuint64_t)s->lnz_ld[J], (cuuint64_t)m};
+        cuuint64_t strides[1] = {(cuuint64_t)s->lnz_ld[J] * 4};
+        cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)tc::BM};
+        cuuint32_t estr[2] = {1, 1};
+        CUresult r = encode(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)(d_lnz + s->lnz_off[J]), dims, strides,
+                            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return SC_ERR_CUDA;
+        tmap_of_sn[J] = (int32_t)maps.size();
+        maps.push_back(map);
+    }
+    return SC_OK;
+}
+
+inline void launch_tc_gemm(float *lnz, const Task *tasks, const GemmTile *tiles, int32_t count,
+                           const CUtensorMap *maps, const int32_t *tmap_of_sn, int32_t *err, long long spin_limit,
+                           cudaStream_t st) {
+    tc::k_tc_gemm<<<count, 128, tc::SMEM_BYTES, st>>>(lnz, tasks, tiles, maps, tmap_of_sn, err, spin_limit);
+}
+
 }  // namespace sc

@@ -74,6 +74,20 @@ def test_fp64_factor_matches_oracle(name, variant):
     assert np.abs(X - Xo).max() <= 1e-8 * np.abs(Xo).max()
 
 
+@pytest.mark.parametrize("merge", [0.125, 0.4])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("tf32", 2e-2)])
+def test_merged_supernodes_factor(merge, prec, tol):
+    A = _grid_case("st27_14")
+    sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid, merge=merge)
+    o = oracle.Oracle(A, oracle.nd_grid(*A.grid, 8), pr=True, merge=merge)
+    assert o.factor() == 0
+    num = sym.factor(A.values, precision=prec)
+    _check_L(num.export_L(), o.L_supernodal(), tol)
+    B = inputs.rhs(A.n, 2, 8)
+    X, info = num.solve(B)
+    assert oracle.backward_error(A, B, X).max() <= 1e-14
+
+
 @pytest.mark.parametrize("chunk", [8, 24, 64])
 def test_chunk_widths(chunk):
     A = _grid_case("diff7_13")
@@ -152,14 +166,17 @@ def test_batch_factor_matches_per_matrix():
         r0 += A.n
 
 
-def test_full_workload2_fp64_parity():
-    """48^3 7-point variable-coefficient matrix, FP64 RLB (the benchmark's launch): L elementwise vs
-    the oracle's Alg. 1 factor, and the backward error of 4 right-hand sides."""
+@pytest.mark.parametrize("merge", [0.0, 0.125])
+def test_full_workload2_fp64_parity(merge):
+    """48^3 7-point variable-coefficient matrix, FP64 RLB (the benchmark's launch uses merge 0.125):
+    L elementwise vs the oracle's Alg. 1 factor, and the backward error of 4 right-hand sides."""
     A, nrhs = inputs.workload(2)
-    sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid)
+    sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid, merge=merge)
     num = sym.factor(A.values, precision="fp64")
     assert num.rc == 0
-    o, Lo = _oracle_L(A, oracle.nd_grid(*A.grid, 8))
+    o = oracle.Oracle(A, oracle.nd_grid(*A.grid, 8), pr=True, merge=merge)
+    assert o.factor() == 0
+    Lo = o.L_supernodal()
     _check_L(num.export_L(), Lo, 1e-9)
     B = inputs.rhs(A.n, nrhs, 2)
     X, info = num.solve(B)

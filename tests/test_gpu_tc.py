@@ -1,0 +1,70 @@
+"""TF32 tensor-core (tcgen05) product tiles against the oracle (needs a GB300).
+
+Cases are chosen so that the launch plan routes products to the tensor-core
+kernel (asserted through sc_plan_stats): a dense matrix (one wide supernode,
+trailing updates with K = 64 across many chunks) and 3D stencils whose
+separators are wide (cross-supernode updates with K = |J| >= 32). The factor
+is compared with the oracle's FP64 L within the TF32 bound used for the other
+low-precision tests, and refinement must reach eta <= 1e-14.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2409_13090_gb300 as sc
+from paper_2409_13090_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    sc.build()
+    oracle.build()
+
+
+def _dense(n, seed):
+    rng = np.random.default_rng(seed)
+    ents = [(i, j) for j in range(n) for i in range(j + 1, n)]
+    A = inputs.from_lower_pattern(n, ents, seed=seed)
+    A.values[:] = np.where(A.rowind == np.repeat(np.arange(n), np.diff(A.colptr)), A.values, rng.uniform(-1, 1, A.nnz))
+    # diagonal dominance for a well-conditioned SPD matrix
+    rows = np.repeat(np.arange(n), np.diff(A.colptr))
+    off = A.rowind != rows
+    s = np.zeros(n)
+    np.add.at(s, A.rowind[off], np.abs(A.values[off]))
+    np.add.at(s, rows[off], np.abs(A.values[off]))
+    A.values[~off] = s + 1.0
+    return A
+
+
+@pytest.mark.parametrize("case", ["dense_700", "st27_16", "diff7_20"])
+def test_tf32_tensor_core_tiles_match_oracle(case):
+    if case == "dense_700":
+        A, perm0, kw = _dense(700, 1), None, dict(ordering="natural")
+    elif case == "st27_16":
+        A = inputs.stencil_3d_27pt(16, 16, 16, seed=3)
+        perm0, kw = oracle.nd_grid(16, 16, 16, 8), dict(ordering="grid_nd", grid=A.grid)
+    else:
+        A = inputs.diffusion_3d_7pt(20, 20, 20, seed=4, shift=1e-1)
+        perm0, kw = oracle.nd_grid(20, 20, 20, 8), dict(ordering="grid_nd", grid=A.grid)
+    sym = sc.Symbolic(A, **kw)
+    assert sym.plan_stats("tf32")["tc_tiles"] > 0
+    o = oracle.Oracle(A, perm0, pr=True)
+    assert o.factor() == 0
+    Lo = o.L_supernodal()
+    num = sym.factor(A.values, precision="tf32")
+    assert num.rc == 0
+    Lg = num.export_L()
+    err = np.abs(Lg - Lo).max() / np.abs(Lo).max()
+    assert err <= 2e-2, err
+    # the same handle in FP32 SIMT agrees with TF32 to TF32 accuracy
+    num32 = sym.factor(A.values, precision="fp32")
+    assert np.abs(num32.export_L() - Lg).max() / np.abs(Lo).max() <= 2e-2
+    B = inputs.rhs(A.n, 2, 7)
+    X, info = num.solve(B)
+    assert info["converged"], info
+    assert oracle.backward_error(A, B, X).max() <= 1e-14

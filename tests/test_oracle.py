@@ -278,3 +278,50 @@ def test_relindB_is_distance_of_block_top_from_bottom():
             sel = [f for f in firsts if f >= s.sup_ptr[P]]
             vals = s.rb_val[s.rb_val_ptr[q]:s.rb_val_ptr[q + 1]].tolist()
             assert vals == [len(g) - 1 - g.index(f) for f in sel]
+
+
+# --------------------------------------------------------------------------- supernode merging (Sec. 3.1)
+
+def test_merge_worked_example_by_hand(golden):
+    """At a 12.5 % budget: S0 = 9 + 9 + 15 = 33, budget 4.125. J1 is not adjacent to J3;
+    J2 -> J3 adds 7*7 - 21 - 9 - 15 = 4 <= 4.125 and merges; J1 -> (J2 u J3) would then
+    add 9*9 - 36 - 9 - 28 = 8, past the budget."""
+    ents = [(i - 1, j - 1) for i, j in golden["A_strict_lower_pattern"]["entries"]]
+    A = inputs.from_lower_pattern(9, ents)
+    s = oracle.Oracle(A, None, pr=False, merge=0.125).symbolic()
+    assert s.sup_ptr.tolist() == [0, 2, 9]
+    assert s.nnzL == 33 + 4
+    assert s.flops == oracle.Oracle(A, None, pr=False).symbolic().flops  # metric stays fundamental
+    s = oracle.Oracle(A, None, pr=False, merge=4.0 / 33.0 - 1e-9).symbolic()  # budget just below 4
+    assert s.sup_ptr.tolist() == [0, 2, 4, 9]
+
+
+def test_merge_chain_by_hand():
+    """Tridiagonal n = 8: fundamental supernodes {0}..{5},{6,7}, storage 15, budget 1.875.
+    Every adjacent pair adds exactly 1; the tie goes to the smallest first column, so
+    {0} merges into {1}; the next merge would reach 2 > 1.875."""
+    n = 8
+    A = inputs.from_lower_pattern(n, [(i + 1, i) for i in range(n - 1)])
+    s = oracle.Oracle(A, None, pr=False, merge=0.125).symbolic()
+    assert s.sup_ptr.tolist() == [0, 2, 3, 4, 5, 6, 8]
+    s = oracle.Oracle(A, None, pr=False, merge=10.0).symbolic()
+    assert s.nsuper == 1 and s.nnzL == n * (n + 1) // 2
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_merge_invariants_and_numeric(seed):
+    A = inputs.diffusion_3d_7pt(7, 6, 5, seed=seed, shift=1e-2)
+    perm0 = oracle.nd_grid(7, 6, 5, 8)
+    f = oracle.Oracle(A, perm0, pr=True).symbolic()
+    o = oracle.Oracle(A, perm0, pr=True, merge=0.125)
+    m = o.symbolic()
+    assert m.nsuper < f.nsuper and m.flops == f.flops
+    assert f.nnzL <= m.nnzL <= f.nnzL * 1.125
+    # merged partition coarsens the fundamental one (same postorder, up to PR inside supernodes)
+    assert set(m.sup_ptr.tolist()) <= set(f.sup_ptr.tolist())
+    assert o.factor() == 0
+    M = inputs.dense_from_lower(A)[np.ix_(m.perm, m.perm)]
+    Ld = np.linalg.cholesky(M)
+    Ls = _dense_L(o)
+    assert np.linalg.norm(Ls - Ld) <= 1e-12 * np.linalg.norm(Ld)
+    assert not np.any(_brute_force_pattern(M) & ~_pattern_mask(o))

@@ -24,17 +24,17 @@ def built():
     sc.build()
 
 
-def _compare(A, *, grid=None, user_perm=None, pr=True, leaf=8):
+def _compare(A, *, grid=None, user_perm=None, pr=True, leaf=8, merge=0.0):
     if grid is not None:
         perm0 = oracle.nd_grid(*grid, leaf)
-        lib_sym = sc.Symbolic(A, ordering="grid_nd", grid=grid, nd_leaf=leaf, pr=pr)
+        lib_sym = sc.Symbolic(A, ordering="grid_nd", grid=grid, nd_leaf=leaf, pr=pr, merge=merge)
     elif user_perm is not None:
         perm0 = user_perm
-        lib_sym = sc.Symbolic(A, ordering="user", user_perm=user_perm, pr=pr)
+        lib_sym = sc.Symbolic(A, ordering="user", user_perm=user_perm, pr=pr, merge=merge)
     else:
         perm0 = None
-        lib_sym = sc.Symbolic(A, ordering="natural", pr=pr)
-    o = oracle.Oracle(A, perm0, pr=pr).symbolic()
+        lib_sym = sc.Symbolic(A, ordering="natural", pr=pr, merge=merge)
+    o = oracle.Oracle(A, perm0, pr=pr, merge=merge).symbolic()
     v = lib_sym.view()
     for k in KEYS:
         assert np.array_equal(v[k], getattr(o, k)), k
@@ -79,10 +79,27 @@ def test_workloads_scaled(idx, scale):
     _compare(A, grid=A.grid, pr=True)
 
 
-def test_workload2_full():
+@pytest.mark.parametrize("merge", [0.0, 0.125])
+def test_workload2_full(merge):
     A, _ = inputs.workload(2)
-    v = _compare(A, grid=A.grid, pr=True)
+    v = _compare(A, grid=A.grid, pr=True, merge=merge)
     assert v["nsuper"] > 1000
+
+
+@pytest.mark.parametrize("idx,scale", [(1, 1.0), (2, 0.5), (3, 0.3), (5, 0.15)])
+@pytest.mark.parametrize("merge", [0.05, 0.125, 0.5])
+def test_merged_supernodes_bit_exact(idx, scale, merge):
+    A, _ = inputs.workload(idx, scale)
+    _compare(A, grid=A.grid, pr=True, merge=merge)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_merged_random_bit_exact(seed):
+    n = 80 + 50 * seed
+    A = inputs.random_spd(n, 0.04, seed)
+    perm = np.random.default_rng(7 + seed).permutation(n).astype(np.int32)
+    _compare(A, user_perm=perm, pr=True, merge=0.125)
+    _compare(A, pr=False, merge=0.3)
 
 
 def test_workload4_members():
