@@ -253,6 +253,36 @@ int sc_probe_fma_peak(int kind, void *cuda_stream, double *flops_per_s);
  * TRSM tiles, RL assembly pairs and device-loop items. Errors: -1, -2, -3. */
 int sc_plan_stats(const sc_symbolic *s, int precision, int64_t *out, int nout);
 
+/* Allocation-free residual and backward error. The paper has no counterpart:
+ * this entry point exists for callers that cannot let a library allocate
+ * device memory during a call -- applications that give all device memory to
+ * their own pool up front, or latency-critical loops where a cudaMalloc (which
+ * can synchronise the whole device) is not acceptable. It computes, for each
+ * column c of X,
+ *   R_c = B_c - A X_c  and  eta_c = ||R_c||_inf / (||A||_inf ||X_c||_inf + ||B_c||_inf),
+ * the same check sc_solve reports, and calls no allocation routine.
+ *   n                 order of A (>= 1)
+ *   row_ptr, col, val A as a full symmetric CSR (both triangles): row_ptr[n+1]
+ *                     int64, col int32, val FP64 -- device memory
+ *   nrhs              columns of B, X, R: 1..SC_NOALLOC_MAX_RHS
+ *   B, ldb / X, ldx   column-major FP64 inputs (device memory), ld >= n
+ *   R, ldr            column-major FP64 output (device memory), ld >= n
+ *   eta               nrhs FP64 outputs (device memory)
+ *   cuda_stream       stream for the work; the call returns without waiting
+ * Working memory is one fixed array of 3 * SC_NOALLOC_MAX_RHS + 1 doubles
+ * (about 24 KB) built into the library; every GPU that loads the library
+ * holds it until the process exits. The first call on a device looks up that
+ * array's device address (with the device current) and keeps it; make that
+ * first call before any stream capture. All calls share the array and each
+ * call clears it first, so calls whose work overlaps on the GPU (other
+ * streams, other threads) race and must be serialised by the caller.
+ * Errors: -1..-12 for the arguments in order (-5: nrhs outside 1..max),
+ * SC_ERR_CUDA. */
+#define SC_NOALLOC_MAX_RHS 1024
+int sc_residual_eta_noalloc(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val, int64_t nrhs,
+                            const double *B, int64_t ldb, const double *X, int64_t ldx, double *R, int64_t ldr,
+                            double *eta, void *cuda_stream);
+
 /* Frees h and its device memory. NULL is accepted. */
 void sc_numeric_free(sc_numeric *h);
 
