@@ -42,6 +42,9 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "tf32"])
     ap.add_argument("--merge", type=float, default=0.125, help="supernode merging budget (Sec. 3.1); 0 = off")
+    ap.add_argument("--workload", type=int, default=2, choices=[2, 3],
+                    help="2: the benchmark matrix (48^3 7-point); 3: 80^3 27-point (for profiling the TF32 path)")
+    ap.add_argument("--scale", type=float, default=1.0, help="grid-side scale of the workload (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     return ap.parse_args()
@@ -167,7 +170,7 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
 
-    A, nrhs = inputs.workload(2)
+    A, nrhs = inputs.workload(args.workload, args.scale)
     t0 = time.perf_counter()
     sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid, nd_leaf=8, pr=True, variant="rlb", merge=args.merge)
     analyze_s = time.perf_counter() - t0
@@ -302,7 +305,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": step_ms / K, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD, "n": A.n, "nnz_A_lower": A.nnz, "nnz_L": int(view["nnzL"]),
+                "config": {"workload": WORKLOAD if (args.workload == 2 and args.scale == 1.0) else A.name, "n": A.n, "nnz_A_lower": A.nnz, "nnz_L": int(view["nnzL"]),
                            "sum_cj2": flops, "nsuper": int(view["nsuper"]), "nrhs": nrhs,
                            "precision": args.precision, "variant": "rlb", "ordering": "grid ND (leaf 8) + PR",
                            "merge_frac": args.merge,

@@ -106,13 +106,13 @@ int run_levels(sc_numeric *h, cudaStream_t st, Prof *prof = nullptr) {
         }
         if (p.trsm_cnt) {
             B(kProfTrsm);
-            k_trsm<T><<<p.trsm_cnt, kTrsmRows, trsm_smem<T>(), st>>>(lnz, h->d_chunks, h->d_trsm + p.trsm_off);
+            k_trsm<T><<<p.trsm_cnt, kTrsmRows, 0, st>>>(lnz, h->d_chunks, h->d_trsm + p.trsm_off);
             E();
             launches++;
         }
         if (p.loop_cnt) {
             B(kProfLoop);
-            k_rlb_loop<T><<<p.loop_cnt, 256, p.loop_smem, st>>>(lnz, h->d_loops + p.loop_off, h->d_sn, h->d_blk,
+            k_rlb_loop<T><<<p.loop_cnt, 256, 0, st>>>(lnz, h->d_loops + p.loop_off, h->d_sn, h->d_blk,
                                                                  h->d_rbval);
             E();
             launches++;
@@ -171,8 +171,6 @@ int set_smem_attrs() {
     if (done) return SC_OK;
     SC_CUDA(cudaFuncSetAttribute(k_potrf<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPotrfSmem));
     SC_CUDA(cudaFuncSetAttribute(k_potrf<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPotrfSmem));
-    SC_CUDA(cudaFuncSetAttribute(k_trsm<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, trsm_smem<double>()));
-    SC_CUDA(cudaFuncSetAttribute(k_trsm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, trsm_smem<float>()));
     if (!tc_gemm_init()) return SC_ERR_CUDA;
     done = true;
     return SC_OK;
@@ -253,14 +251,7 @@ void build_plan(const sc_symbolic *s, int precision, Plan &P) {
         p.small_cnt = (int32_t)ids_small.size();
         // device-side RLB loops
         p.loop_off = (int32_t)P.loops.size();
-        for (LoopItem it : L.loops) {
-            const int64_t mJ = s->gl_ptr[it.sn + 1] - s->gl_ptr[it.sn];
-            const int64_t nJ = s->sup_ptr[it.sn + 1] - s->sup_ptr[it.sn];
-            const int64_t bytes = mJ * (nJ + 1) * (precision == SC_FP64 ? 8 : 4);
-            it.smem = bytes <= kLoopSmemBytes ? 1 : 0;
-            if (it.smem) p.loop_smem = std::max<int32_t>(p.loop_smem, (int32_t)bytes);
-            P.loops.push_back(it);
-        }
+        for (const LoopItem &it : L.loops) P.loops.push_back(it);
         p.loop_cnt = (int32_t)P.loops.size() - p.loop_off;
         P.class_flops[kProfLoop] += L.loop_flops;
         // RL update matrices and assembly

@@ -22,8 +22,9 @@ __global__ void k_scatter_values(T *__restrict__ lnz, const int64_t *__restrict_
 
 // --------------------------------------------------------------------- K1
 // POTRF of each chunk's w x w diagonal block (lower) in shared memory, column
-// by column, right-looking: pivot, scale the column, rank-1 update of the
-// trailing triangle.
+// by column, right-looking (pivot, scale the column, rank-1 update of the
+// trailing triangle); a 16 x 16 thread grid updates the trailing triangle and
+// pivots are applied as one reciprocal per column.
 //   T = double: one pass in FP64; a pivot d <= 0 sets info.
 //   T = float : one pass in FP32. If some pivot d (before the square root)
 //               is <= tau * |A_jj| (A_jj = the diagonal entry of the input
@@ -33,7 +34,8 @@ __global__ void k_scatter_values(T *__restrict__ lnz, const int64_t *__restrict_
 // info receives the minimum failing column (1-based, final ordering).
 template <typename S>
 __device__ bool potrf_pass(S (*a)[kMaxChunk + 1], int w, const double *__restrict__ adiag, int col0, double tau,
-                           bool check_low, int32_t *__restrict__ info, int *flag) {
+                           bool check_low, int32_t *__restrict__ info, int *flag, S *rcp) {
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // 16 x 16 threads
     for (int k = 0; k < w; k++) {
         if (threadIdx.x == 0) {
             S d = a[k][k];
@@ -44,17 +46,19 @@ __device__ bool potrf_pass(S (*a)[kMaxChunk + 1], int w, const double *__restric
                 d = S(1);
             }
             if (!(d > S(0))) d = S(1);
-            a[k][k] = sqrt(d);
+            S r = sqrt(d);
+            a[k][k] = r;
+            *rcp = S(1) / r;
         }
         __syncthreads();
         if (check_low && *flag) return false;
-        S dk = a[k][k];
-        for (int i = k + 1 + threadIdx.x; i < w; i += blockDim.x) a[i][k] /= dk;
+        const S rk = *rcp;
+        for (int i = k + 1 + threadIdx.x; i < w; i += blockDim.x) a[i][k] *= rk;
         __syncthreads();
-        int rem = w - k - 1;
-        for (int idx = threadIdx.x; idx < rem * rem; idx += blockDim.x) {
-            int i = k + 1 + idx / rem, j = k + 1 + idx % rem;
-            if (j <= i) a[i][j] -= a[i][k] * a[j][k];
+        // trailing update of the lower triangle: rows i = k+1+ty+16a, columns j = k+1+tx+16b, j <= i
+        for (int i = k + 1 + ty; i < w; i += 16) {
+            const S aik = a[i][k];
+            for (int j = k + 1 + tx; j <= i; j += 16) a[i][j] -= aik * a[j][k];
         }
         __syncthreads();
     }
@@ -68,11 +72,12 @@ __global__ void __launch_bounds__(256) k_potrf(T *__restrict__ lnz, const ChunkD
                                                double tau) {
     extern __shared__ double smem_potrf[];
     __shared__ int flag;
+    __shared__ double rcp64;
+    __shared__ float rcp32;
     const ChunkDev ch = chunks[list[blockIdx.x]];
     const int w = ch.w;
     T *base = lnz + ch.off + (int64_t)ch.c0 * ch.ld + ch.c0;
     if (threadIdx.x == 0) flag = 0;
-    bool done = false;
     if (sizeof(T) == 4) {
         auto a = reinterpret_cast<float (*)[kMaxChunk + 1]>(smem_potrf);
         for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
@@ -80,8 +85,7 @@ __global__ void __launch_bounds__(256) k_potrf(T *__restrict__ lnz, const ChunkD
             a[r][c] = (r >= c) ? (float)base[(int64_t)r * ch.ld + c] : 0.f;
         }
         __syncthreads();
-        done = potrf_pass<float>(a, w, adiag, ch.col0, tau, true, info, &flag);
-        if (done) {
+        if (potrf_pass<float>(a, w, adiag, ch.col0, tau, true, info, &flag, &rcp32)) {
             for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
                 int r = idx / w, c = idx % w;
                 if (r >= c) base[(int64_t)r * ch.ld + c] = (T)a[r][c];
@@ -91,13 +95,14 @@ __global__ void __launch_bounds__(256) k_potrf(T *__restrict__ lnz, const ChunkD
         if (threadIdx.x == 0) atomicAdd(low_pivots, 1);
         __syncthreads();
     }
+    // FP64 factorization (the FP64 path, or the fallback of a low pivot)
     auto a = reinterpret_cast<double (*)[kMaxChunk + 1]>(smem_potrf);
     for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
         int r = idx / w, c = idx % w;
         a[r][c] = (r >= c) ? (double)base[(int64_t)r * ch.ld + c] : 0.0;
     }
     __syncthreads();
-    potrf_pass<double>(a, w, adiag, ch.col0, tau, false, info, &flag);
+    potrf_pass<double>(a, w, adiag, ch.col0, tau, false, info, &flag, &rcp64);
     for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
         int r = idx / w, c = idx % w;
         if (r >= c) base[(int64_t)r * ch.ld + c] = (T)a[r][c];
@@ -106,45 +111,43 @@ __global__ void __launch_bounds__(256) k_potrf(T *__restrict__ lnz, const ChunkD
 constexpr int kPotrfSmem = kMaxChunk * (kMaxChunk + 1) * 8;
 
 // --------------------------------------------------------------------- K2
-// TRSM of the rows below each chunk's diagonal block: row x <- x L_cc^{-T},
-// one row per thread by forward substitution, in the storage precision.
-constexpr int kTrsmRows = 64;
-template <typename T>
-constexpr int trsm_smem() { return (int)sizeof(T) * kMaxChunk * (kMaxChunk + 1 + kTrsmRows + 1); }
+// TRSM of the rows below each chunk's diagonal block: row x <- x L_cc^{-T} by
+// forward substitution, one row per thread held in registers (the chunk is
+// zero-padded to 64 columns so the substitution unrolls fully), pivots applied
+// as reciprocals, L_cc broadcast from shared memory. Storage precision.
+constexpr int kTrsmRows = 128;
 template <typename T>
 __global__ void __launch_bounds__(kTrsmRows) k_trsm(T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
                                                     const TrsmTile *__restrict__ tiles) {
-    extern __shared__ __align__(16) unsigned char smem_trsm[];
-    auto l = reinterpret_cast<T (*)[kMaxChunk + 1]>(smem_trsm);
-    auto x = reinterpret_cast<T (*)[kTrsmRows + 1]>(smem_trsm + sizeof(T) * kMaxChunk * (kMaxChunk + 1));
+    __shared__ T l[kMaxChunk][kMaxChunk + 1];
+    __shared__ T rinv[kMaxChunk];
     const TrsmTile tl = tiles[blockIdx.x];
     const ChunkDev ch = chunks[tl.chunk];
     const int w = ch.w;
     const T *diag = lnz + ch.off + (int64_t)ch.c0 * ch.ld + ch.c0;
-    for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
-        int r = idx / w, c = idx % w;
-        l[r][c] = r >= c ? diag[(int64_t)r * ch.ld + c] : T(0);
-    }
-    const int rows = min(kTrsmRows, ch.m - tl.r0);
-    T *rbase = lnz + ch.off + (int64_t)tl.r0 * ch.ld + ch.c0;
-    for (int idx = threadIdx.x; idx < rows * w; idx += blockDim.x) {
-        int r = idx / w, c = idx % w;
-        x[c][r] = rbase[(int64_t)r * ch.ld + c];
+    for (int idx = threadIdx.x; idx < kMaxChunk * kMaxChunk; idx += blockDim.x) {
+        int r = idx / kMaxChunk, c = idx % kMaxChunk;
+        l[r][c] = (r < w && c < w && r >= c) ? diag[(int64_t)r * ch.ld + c] : T(0);
     }
     __syncthreads();
-    const int t = threadIdx.x;
-    if (t < rows) {
-        for (int k = 0; k < w; k++) {
-            T v = x[k][t] / l[k][k];
-            x[k][t] = v;
-            for (int j = k + 1; j < w; j++) x[j][t] -= v * l[j][k];
-        }
-    }
+    if (threadIdx.x < kMaxChunk) rinv[threadIdx.x] = threadIdx.x < w ? T(1) / l[threadIdx.x][threadIdx.x] : T(0);
     __syncthreads();
-    for (int idx = threadIdx.x; idx < rows * w; idx += blockDim.x) {
-        int r = idx / w, c = idx % w;
-        rbase[(int64_t)r * ch.ld + c] = x[c][r];
+    const int row = tl.r0 + threadIdx.x;
+    if (row >= ch.m) return;
+    T *xr = lnz + ch.off + (int64_t)row * ch.ld + ch.c0;
+    T x[kMaxChunk];
+#pragma unroll
+    for (int k = 0; k < kMaxChunk; k++) x[k] = k < w ? xr[k] : T(0);
+#pragma unroll
+    for (int k = 0; k < kMaxChunk; k++) {
+        const T v = x[k] * rinv[k];
+        x[k] = v;
+#pragma unroll
+        for (int j = k + 1; j < kMaxChunk; j++) x[j] -= v * l[j][k];
     }
+#pragma unroll
+    for (int k = 0; k < kMaxChunk; k++)
+        if (k < w) xr[k] = x[k];
 }
 
 // --------------------------------------------------------------------- K3
@@ -260,63 +263,55 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_rlb_loop(T *__restrict__ lnz, const LoopItem *__restrict__ items,
                                                   const SnDev *__restrict__ sn, const BlkDev *__restrict__ blk,
                                                   const int32_t *__restrict__ rb_val) {
-    extern __shared__ __align__(16) unsigned char smem_loop[];
     const LoopItem it = items[blockIdx.x];
     const SnDev J = sn[it.sn];
     const int K = J.n;
     const T *src = lnz + J.off;
-    T *panel = reinterpret_cast<T *>(smem_loop);
-    const int ldp = K + 1;
-    if (it.smem) {
-        for (int idx = threadIdx.x; idx < J.m * K; idx += blockDim.x) {
-            int r = idx / K, c = idx % K;
-            panel[r * ldp + c] = src[(int64_t)r * J.ld + c];
-        }
-        __syncthreads();
-    }
-    const T *base = it.smem ? panel : src;
-    const int ldb = it.smem ? ldp : J.ld;
-    for (int b = it.b_lo; b < it.b_hi; b++) {
-        const BlkDev B = blk[b];
-        const SnDev P = sn[B.owner];
-        const int colB = B.first - P.f;
-        const int nb = B.size;
-        const long long tri = (long long)nb * (nb + 1) / 2;
-        if (!tile_task(tri, K)) {
+    const BlkDev B = blk[it.b];
+    const SnDev P = sn[B.owner];
+    const int colB = B.first - P.f;
+    const int nb = B.size;
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nwarps = blockDim.x / 32;
+    // task 0 = SYRK on B (when r_lo == b), tasks 1.. = runs B' below B; one warp per task
+    int task = 0;
+    if (it.r_lo == it.b) {
+        if (warp == 0) {
+            const int tri = nb * (nb + 1) / 2;
             T *C = lnz + P.off + (int64_t)colB * P.ld + colB;
-            for (int e = threadIdx.x; e < (int)tri; e += blockDim.x) {
+            for (int e = lane; e < tri; e += 32) {
                 int i = tri_row(e), j = e - i * (i + 1) / 2;
-                const T *a = base + (int64_t)(B.pos + i) * ldb;
-                const T *bb = base + (int64_t)(B.pos + j) * ldb;
+                const T *a = src + (int64_t)(B.pos + i) * J.ld;
+                const T *bb = src + (int64_t)(B.pos + j) * J.ld;
                 T acc = T(0);
                 for (int k = 0; k < K; k++) acc += a[k] * bb[k];
                 atomicAdd(C + (int64_t)i * P.ld + j, -acc);
             }
         }
-        int r = b + 1;
-        while (r < J.b1) {
-            int e = r;
-            int rows = blk[r].size;
-            while (e + 1 < J.b1 && blk[e + 1].first == blk[e].first + blk[e].size) {
-                e++;
-                rows += blk[e].size;
-            }
-            if (!tile_task((long long)rows * nb, K)) {
-                const int rowP = P.m - 1 - rb_val[B.rb + (r - B.bs)];
-                T *C = lnz + P.off + (int64_t)rowP * P.ld + colB;
-                const int apos = blk[r].pos;
-                const int tot = rows * nb;
-                for (int q = threadIdx.x; q < tot; q += blockDim.x) {
-                    int i = q / nb, j = q % nb;
-                    const T *a = base + (int64_t)(apos + i) * ldb;
-                    const T *bb = base + (int64_t)(B.pos + j) * ldb;
-                    T acc = T(0);
-                    for (int k = 0; k < K; k++) acc += a[k] * bb[k];
-                    atomicAdd(C + (int64_t)i * P.ld + j, -acc);
-                }
-            }
-            r = e + 1;
+        task = 1;
+    }
+    int r = it.r_lo == it.b ? it.b + 1 : it.r_lo;
+    while (r < it.r_hi) {
+        int e = r;
+        int rows = blk[r].size;
+        while (e + 1 < J.b1 && blk[e + 1].first == blk[e].first + blk[e].size) {
+            e++;
+            rows += blk[e].size;
         }
+        if ((task++ % nwarps) == warp) {
+            const int rowP = P.m - 1 - rb_val[B.rb + (r - B.bs)];
+            T *C = lnz + P.off + (int64_t)rowP * P.ld + colB;
+            const int apos = blk[r].pos;
+            const int tot = rows * nb;
+            for (int q = lane; q < tot; q += 32) {
+                int i = q / nb, j = q % nb;
+                const T *a = src + (int64_t)(apos + i) * J.ld;
+                const T *bb = src + (int64_t)(B.pos + j) * J.ld;
+                T acc = T(0);
+                for (int k = 0; k < K; k++) acc += a[k] * bb[k];
+                atomicAdd(C + (int64_t)i * P.ld + j, -acc);
+            }
+        }
+        r = e + 1;
     }
 }
 

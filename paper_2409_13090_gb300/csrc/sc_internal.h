@@ -42,13 +42,14 @@ SC_HD inline bool tile_task(long long entries, int k) {
     return (entries >= 1024 && k >= 16) || entries >= 8192;
 }
 
-// A range of blocks B of supernode J whose Alg. 5 loops (SYRK on B, GEMM for
-// each maximal B' below B) run on the device in one CTA.
+// Part of Alg. 5's inner loops for one block B of supernode J, run on the
+// device by one CTA: the SYRK on B when r_lo == b, then the GEMMs of the
+// maximal runs B' below B that start at block indices in [max(r_lo, b+1), r_hi).
 struct LoopItem {
     int32_t sn;    // J
-    int32_t b_lo;  // first block (global block index)
-    int32_t b_hi;  // one past the last block
-    int32_t smem;  // set by the launch plan: 1 = J's panel is staged in shared memory
+    int32_t b;     // block B (global block index)
+    int32_t r_lo;  // b: include the SYRK on B; otherwise the first run start
+    int32_t r_hi;  // runs starting at block indices below r_hi
 };
 
 // One panel of at most `chunk` columns of a supernode; the unit of the dense

@@ -7,8 +7,10 @@
 //
 // Per level:
 //   - cdiv of each chunk: POTRF of its diagonal block, TRSM of the rows below;
-//   - for a chunk that is not the last of J: the trailing update of J's
-//     remaining columns (one lower-trapezoidal product, K = chunk width);
+//   - for a chunk that is not the last of J: trailing updates inside J,
+//     deferred to macro panels of 256 columns (a chunk updates the rest of its
+//     macro panel, K = chunk width; the macro panel's last chunk updates all
+//     later columns at once, K = 256);
 //   - for J's last chunk (all of L_{*,J} is final):
 //       RLB (Alg. 5): for every ancestor P, every block B of J inside P:
 //         SYRK  L_{B,B}  -= L_{B,J} L_{B,J}^T            (line 12)
@@ -72,22 +74,45 @@ int build_schedule(sc_symbolic *s) {
             int32_t ldJ = s->lnz_ld[J];
             int64_t offJ = s->lnz_off[J];
             if (!ch.last) {
-                // trailing update of J's columns after this chunk (dense, inside Lnz(J))
-                int32_t r0 = ch.c0 + ch.w;
-                Task t;
-                t.a_off = offJ + (int64_t)r0 * ldJ + ch.c0;
-                t.b_off = t.a_off;
-                t.c_off = offJ + (int64_t)r0 * ldJ + r0;
-                t.lds = ldJ;
-                t.ldc = ldJ;
-                t.m = (int32_t)(mJ - r0);
-                t.n = nJ - r0;
-                t.k = ch.w;
-                t.flags = kTaskLower | kTaskExclusive;
-                t.src = J;
-                t.a_row = t.b_row = r0;
-                t.kx0 = ch.c0;
-                L.tasks.push_back(t);
+                // trailing updates inside J, deferred to macro panels of Wm columns:
+                // a chunk updates the rest of its macro panel (K = chunk width); the
+                // macro panel's last chunk updates every column after the macro
+                // panel at once (K = macro width). Targets lie in Lnz(J) only.
+                const int32_t Wm = W * std::max(1, 256 / W);
+                const int32_t mstart = ch.c0 / Wm * Wm;
+                const int32_t mend = std::min(mstart + Wm, nJ);
+                const int32_t r0 = ch.c0 + ch.w;
+                if (r0 < mend) {
+                    Task t;
+                    t.a_off = offJ + (int64_t)r0 * ldJ + ch.c0;
+                    t.b_off = t.a_off;
+                    t.c_off = offJ + (int64_t)r0 * ldJ + r0;
+                    t.lds = ldJ;
+                    t.ldc = ldJ;
+                    t.m = (int32_t)(mJ - r0);
+                    t.n = mend - r0;
+                    t.k = ch.w;
+                    t.flags = kTaskLower | kTaskExclusive;
+                    t.src = J;
+                    t.a_row = t.b_row = r0;
+                    t.kx0 = ch.c0;
+                    L.tasks.push_back(t);
+                } else {
+                    Task t;
+                    t.a_off = offJ + (int64_t)mend * ldJ + mstart;
+                    t.b_off = t.a_off;
+                    t.c_off = offJ + (int64_t)mend * ldJ + mend;
+                    t.lds = ldJ;
+                    t.ldc = ldJ;
+                    t.m = (int32_t)(mJ - mend);
+                    t.n = nJ - mend;
+                    t.k = mend - mstart;
+                    t.flags = kTaskLower | kTaskExclusive;
+                    t.src = J;
+                    t.a_row = t.b_row = mend;
+                    t.kx0 = mstart;
+                    L.tasks.push_back(t);
+                }
                 continue;
             }
             int64_t b0 = s->blk_ptr[J], b1 = s->blk_ptr[J + 1];
@@ -103,10 +128,9 @@ int build_schedule(sc_symbolic *s) {
             }
             if (!rl) {
                 // Alg. 5 lines 7-17 for J: large (B, B') products become tiled tasks;
-                // the rest run in device loops over ranges of J's blocks.
-                const int64_t kLoopBudget = 1 << 17;
-                LoopItem cur_item{(int32_t)J, (int32_t)b0, (int32_t)b0, 0};
-                int64_t cost = 0;
+                // the rest run on the device in items of bounded cost, each item
+                // one block B and a range of the runs B' below it.
+                const int64_t kLoopBudget = 1 << 15;
                 for (int64_t q = s->rb_pair_ptr[J]; q < s->rb_pair_ptr[J + 1]; q++) {
                     int32_t P = s->rb_pair_P[q];
                     const int32_t *rb = s->rb_val.data() + s->rb_val_ptr[q];
@@ -121,7 +145,9 @@ int build_schedule(sc_symbolic *s) {
                         int32_t colB = s->blk_first[b] - fP;
                         if (posB != colB) return SC_ERR_INTERNAL;
                         int32_t nb = s->blk_size[b];
-                        int64_t bcost = 0;
+                        LoopItem item{(int32_t)J, (int32_t)b, (int32_t)b, (int32_t)b};
+                        int64_t cost = 0;
+                        bool open = false;  // item holds work
                         long long tri = (long long)nb * (nb + 1) / 2;
                         if (tile_task(tri, nJ)) {
                             Task t;
@@ -137,8 +163,10 @@ int build_schedule(sc_symbolic *s) {
                             t.a_row = t.b_row = (int32_t)bpos[b - b0];
                             t.kx0 = 0;
                             L.tasks.push_back(t);
+                            item.r_lo = (int32_t)b + 1;  // no SYRK in the device loop
                         } else {
-                            bcost += tri * (nJ + 4);
+                            cost += tri * (nJ + 4);
+                            open = true;
                             L.loop_flops += 2.0 * (double)tri * nJ;
                         }
                         // maximal blocks B' below B: runs of blocks whose rows abut
@@ -166,25 +194,34 @@ int build_schedule(sc_symbolic *s) {
                                 g.b_row = (int32_t)bpos[b - b0];
                                 g.kx0 = 0;
                                 L.tasks.push_back(g);
+                                // a tiled run ends the current item; the next item starts after it
+                                if (open) {
+                                    item.r_hi = (int32_t)r;
+                                    L.loops.push_back(item);
+                                }
+                                item = LoopItem{(int32_t)J, (int32_t)b, (int32_t)(e + 1), (int32_t)(e + 1)};
+                                cost = 0;
+                                open = false;
                             } else {
-                                bcost += (int64_t)rows * nb * (nJ + 4);
+                                int64_t c = (int64_t)rows * nb * (nJ + 4);
+                                if (open && cost + c > kLoopBudget) {
+                                    item.r_hi = (int32_t)r;
+                                    L.loops.push_back(item);
+                                    item = LoopItem{(int32_t)J, (int32_t)b, (int32_t)r, (int32_t)r};
+                                    cost = 0;
+                                }
+                                cost += c;
+                                open = true;
                                 L.loop_flops += 2.0 * (double)rows * nb * nJ;
                             }
                             r = e + 1;
                         }
-                        // blocks are visited in ascending order: extend the current loop item
-                        if (bcost > 0) {
-                            if (cur_item.b_hi != b || cost >= kLoopBudget) {
-                                if (cur_item.b_hi > cur_item.b_lo) L.loops.push_back(cur_item);
-                                cur_item = LoopItem{(int32_t)J, (int32_t)b, (int32_t)b, 0};
-                                cost = 0;
-                            }
-                            cur_item.b_hi = (int32_t)b + 1;
-                            cost += bcost;
+                        if (open) {
+                            item.r_hi = (int32_t)b1;
+                            L.loops.push_back(item);
                         }
                     }
                 }
-                if (cur_item.b_hi > cur_item.b_lo) L.loops.push_back(cur_item);
             } else {
                 // RL: U_J = -L_{S,J} L_{S,J}^T into the level's pool
                 int32_t sJ = (int32_t)(mJ - nJ);

@@ -33,7 +33,7 @@ constexpr int kSolveRows = 64;
 
 template <typename T>
 constexpr int solve_smem() {
-    return (int)sizeof(T) * (kMaxChunk * (kMaxChunk + 1) + kMaxChunk * kRhsBlk);
+    return (int)sizeof(T) * (kMaxChunk * (kMaxChunk + 1) + kMaxChunk * kRhsBlk + kMaxChunk);
 }
 
 // x_perm[k][r] = B[perm[k]][r0 + r]
@@ -60,15 +60,50 @@ __global__ void k_perm_out(double *__restrict__ X, int64_t ldx, const T *__restr
 }
 
 template <typename T>
-__device__ void load_diag(T (*l)[kMaxChunk + 1], const T *lnz, const ChunkDev &ch) {
+__device__ void load_diag(T (*l)[kMaxChunk + 1], T *rinv, const T *lnz, const ChunkDev &ch) {
     const T *d = lnz + ch.off + (int64_t)ch.c0 * ch.ld + ch.c0;
     for (int idx = threadIdx.x; idx < ch.w * ch.w; idx += blockDim.x) {
         int r = idx / ch.w, c = idx % ch.w;
         l[r][c] = r >= c ? d[(int64_t)r * ch.ld + c] : T(0);
     }
+    __syncthreads();
+    if (threadIdx.x < ch.w) rinv[threadIdx.x] = T(1) / l[threadIdx.x][threadIdx.x];
+    __syncthreads();
 }
 
-// Forward sweep of one level (one launch). Each tile recomputes y_c for its chunk.
+// v[0..w) of one right-hand side held by a warp (lane i: entries i and i+32).
+// Forward substitution with L_cc: for k: v_k *= 1/L_kk; v_j -= L_jk v_k (j > k).
+template <typename T>
+__device__ void warp_lower_solve(const T (*l)[kMaxChunk + 1], const T *rinv, int w, T &x0, T &x1) {
+    const int lane = threadIdx.x % 32;
+    for (int k = 0; k < w; k++) {
+        const T mine = k < 32 ? x0 : x1;
+        const T v = __shfl_sync(0xffffffffu, mine, k & 31) * rinv[k];
+        if (lane == (k & 31)) {
+            if (k < 32) x0 = v; else x1 = v;
+        }
+        if (lane > k) x0 -= l[lane][k] * v;
+        if (lane + 32 > k && lane + 32 < w) x1 -= l[lane + 32][k] * v;
+    }
+}
+
+// Backward substitution with L_cc^T: for k = w-1..0: v_k *= 1/L_kk; v_j -= L_kj v_k (j < k).
+template <typename T>
+__device__ void warp_upper_solve(const T (*l)[kMaxChunk + 1], const T *rinv, int w, T &x0, T &x1) {
+    const int lane = threadIdx.x % 32;
+    for (int k = w - 1; k >= 0; k--) {
+        const T mine = k < 32 ? x0 : x1;
+        const T v = __shfl_sync(0xffffffffu, mine, k & 31) * rinv[k];
+        if (lane == (k & 31)) {
+            if (k < 32) x0 = v; else x1 = v;
+        }
+        if (lane < k) x0 -= l[k][lane] * v;
+        if (lane + 32 < k) x1 -= l[k][lane + 32] * v;
+    }
+}
+
+// Forward sweep of one level (one launch). Each tile solves its chunk's diagonal
+// block (one warp per right-hand side), then updates its rows below.
 template <typename T>
 __global__ void __launch_bounds__(256) k_fwd(const T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
                                              const TrsmTile *__restrict__ tiles, const int32_t *__restrict__ glbind,
@@ -76,30 +111,25 @@ __global__ void __launch_bounds__(256) k_fwd(const T *__restrict__ lnz, const Ch
     extern __shared__ __align__(16) unsigned char smem_fwd[];
     auto l = reinterpret_cast<T (*)[kMaxChunk + 1]>(smem_fwd);
     auto v = reinterpret_cast<T (*)[kRhsBlk]>(smem_fwd + sizeof(T) * kMaxChunk * (kMaxChunk + 1));
+    T *rinv = reinterpret_cast<T *>(smem_fwd + sizeof(T) * (kMaxChunk * (kMaxChunk + 1) + kMaxChunk * kRhsBlk));
     const TrsmTile tl = tiles[blockIdx.x];
     const ChunkDev ch = chunks[tl.chunk];
     const int w = ch.w;
-    load_diag(l, lnz, ch);
-    for (int idx = threadIdx.x; idx < w * nb; idx += blockDim.x) {
-        int k = idx / nb, r = idx % nb;
-        v[k][r] = x[(int64_t)(ch.col0 + k) * nb + r];
+    load_diag(l, rinv, lnz, ch);
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+    const bool first = tl.r0 == ch.c0 + w;  // the chunk's first tile writes y_c
+    for (int r = warp; r < nb; r += blockDim.x / 32) {
+        T x0 = lane < w ? x[(int64_t)(ch.col0 + lane) * nb + r] : T(0);
+        T x1 = lane + 32 < w ? x[(int64_t)(ch.col0 + lane + 32) * nb + r] : T(0);
+        warp_lower_solve(l, rinv, w, x0, x1);
+        if (lane < w) v[lane][r] = x0;
+        if (lane + 32 < w) v[lane + 32][r] = x1;
+        if (first) {
+            if (lane < w) y[(int64_t)(ch.col0 + lane) * nb + r] = x0;
+            if (lane + 32 < w) y[(int64_t)(ch.col0 + lane + 32) * nb + r] = x1;
+        }
     }
     __syncthreads();
-    for (int k = 0; k < w; k++) {
-        if (threadIdx.x < nb) v[k][threadIdx.x] /= l[k][k];
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < (w - k - 1) * nb; idx += blockDim.x) {
-            int i = k + 1 + idx / nb, r = idx % nb;
-            v[i][r] -= l[i][k] * v[k][r];
-        }
-        __syncthreads();
-    }
-    if (tl.r0 == ch.c0 + w) {  // the chunk's first tile writes y_c
-        for (int idx = threadIdx.x; idx < w * nb; idx += blockDim.x) {
-            int k = idx / nb, r = idx % nb;
-            y[(int64_t)(ch.col0 + k) * nb + r] = v[k][r];
-        }
-    }
     const int rows = max(0, min(kSolveRows, ch.m - tl.r0));
     for (int idx = threadIdx.x; idx < rows * nb; idx += blockDim.x) {
         int i = idx / nb, r = idx % nb;
@@ -119,18 +149,29 @@ __global__ void __launch_bounds__(256) k_bwd(const T *__restrict__ lnz, const Ch
                                              int32_t *__restrict__ counters, const int32_t *__restrict__ ntiles, int nb) {
     extern __shared__ __align__(16) unsigned char smem_bwd[];
     auto l = reinterpret_cast<T (*)[kMaxChunk + 1]>(smem_bwd);
-    auto v = reinterpret_cast<T (*)[kRhsBlk]>(smem_bwd + sizeof(T) * kMaxChunk * (kMaxChunk + 1));
+    T *rinv = reinterpret_cast<T *>(smem_bwd + sizeof(T) * (kMaxChunk * (kMaxChunk + 1) + kMaxChunk * kRhsBlk));
     __shared__ int last;
     const TrsmTile tl = tiles[blockIdx.x];
     const ChunkDev ch = chunks[tl.chunk];
     const int w = ch.w;
     const int rows = max(0, min(kSolveRows, ch.m - tl.r0));
     if (rows > 0) {
+        // stage the tile's rows of L (coalesced row reads) and the matching z rows
+        auto lt = reinterpret_cast<T (*)[kMaxChunk + 1]>(smem_bwd);  // [rows][w]
+        auto zt = reinterpret_cast<T (*)[kRhsBlk]>(smem_bwd + sizeof(T) * kMaxChunk * (kMaxChunk + 1));
+        for (int idx = threadIdx.x; idx < rows * w; idx += blockDim.x) {
+            int i = idx / w, k = idx % w;
+            lt[i][k] = lnz[ch.off + (int64_t)(tl.r0 + i) * ch.ld + ch.c0 + k];
+        }
+        for (int idx = threadIdx.x; idx < rows * nb; idx += blockDim.x) {
+            int i = idx / nb, r = idx % nb;
+            zt[i][r] = z[(int64_t)glbind[ch.gl + tl.r0 + i] * nb + r];
+        }
+        __syncthreads();
         for (int idx = threadIdx.x; idx < w * nb; idx += blockDim.x) {
             int k = idx / nb, r = idx % nb;
-            const T *lc = lnz + ch.off + (int64_t)tl.r0 * ch.ld + ch.c0 + k;
             T s = T(0);
-            for (int i = 0; i < rows; i++) s += lc[(int64_t)i * ch.ld] * z[(int64_t)glbind[ch.gl + tl.r0 + i] * nb + r];
+            for (int i = 0; i < rows; i++) s += lt[i][k] * zt[i][r];
             atomicAdd(acc + (int64_t)(ch.col0 + k) * nb + r, s);
         }
         __threadfence();
@@ -140,25 +181,15 @@ __global__ void __launch_bounds__(256) k_bwd(const T *__restrict__ lnz, const Ch
     __syncthreads();
     if (!last) return;
     __threadfence();
-    load_diag(l, lnz, ch);
-    for (int idx = threadIdx.x; idx < w * nb; idx += blockDim.x) {
-        int k = idx / nb, r = idx % nb;
-        int64_t g = (int64_t)(ch.col0 + k) * nb + r;
-        v[k][r] = y[g] - __ldcg(acc + g);
-    }
-    __syncthreads();
-    for (int k = w - 1; k >= 0; k--) {
-        if (threadIdx.x < nb) v[k][threadIdx.x] /= l[k][k];
-        __syncthreads();
-        for (int idx = threadIdx.x; idx < k * nb; idx += blockDim.x) {
-            int j = idx / nb, r = idx % nb;
-            v[j][r] -= l[k][j] * v[k][r];
-        }
-        __syncthreads();
-    }
-    for (int idx = threadIdx.x; idx < w * nb; idx += blockDim.x) {
-        int k = idx / nb, r = idx % nb;
-        z[(int64_t)(ch.col0 + k) * nb + r] = v[k][r];
+    load_diag(l, rinv, lnz, ch);
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+    for (int r = warp; r < nb; r += blockDim.x / 32) {
+        const int64_t g0 = (int64_t)(ch.col0 + lane) * nb + r, g1 = (int64_t)(ch.col0 + lane + 32) * nb + r;
+        T x0 = lane < w ? y[g0] - __ldcg(acc + g0) : T(0);
+        T x1 = lane + 32 < w ? y[g1] - __ldcg(acc + g1) : T(0);
+        warp_upper_solve(l, rinv, w, x0, x1);
+        if (lane < w) z[g0] = x0;
+        if (lane + 32 < w) z[g1] = x1;
     }
 }
 

@@ -325,3 +325,11 @@ def test_merge_invariants_and_numeric(seed):
     Ls = _dense_L(o)
     assert np.linalg.norm(Ls - Ld) <= 1e-12 * np.linalg.norm(Ld)
     assert not np.any(_brute_force_pattern(M) & ~_pattern_mask(o))
+
+
+def test_backward_error_hand_example():
+    """A = [[4,1],[1,3]], b = [1,2], x = [0.1,0.6]: r = [0, 0.1], ||A||_inf = 5,
+    eta = 0.1 / (5 * 0.6 + 2) = 0.02."""
+    A = inputs.SparseSym(2, np.array([0, 2, 3], np.int64), np.array([0, 1, 1], np.int32), np.array([4.0, 1.0, 3.0]))
+    eta = oracle.backward_error(A, np.array([[1.0], [2.0]]), np.array([[0.1], [0.6]]))
+    assert abs(eta[0] - 0.02) <= 1e-15
