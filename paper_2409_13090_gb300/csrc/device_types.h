@@ -10,6 +10,7 @@ namespace sc {
 struct ChunkDev {
     int64_t off;   // offset of the supernode's panel
     int64_t gl;    // offset of glbind(J)
+    int64_t inv;   // offset of the chunk's w x w diagonal-block inverse (FP32 / TF32 factors)
     int32_t ld;    // panel leading dimension
     int32_t m;     // rows of the panel (m_J)
     int32_t c0;    // first local column of the chunk

@@ -100,13 +100,13 @@ int run_levels(sc_numeric *h, cudaStream_t st, Prof *prof = nullptr) {
         if (p.potrf_cnt) {
             B(kProfPotrf);
             k_potrf<T><<<p.potrf_cnt, 256, kPotrfSmem, st>>>(lnz, h->d_chunks, h->d_potrf + p.potrf_off, h->d_adiag,
-                                                              h->d_info, h->d_info + 1, tau);
+                                                              h->d_info, h->d_info + 1, tau, (float *)h->d_inv);
             E();
             launches++;
         }
         if (p.trsm_cnt) {
             B(kProfTrsm);
-            k_trsm<T><<<p.trsm_cnt, kTrsmRows, 0, st>>>(lnz, h->d_chunks, h->d_trsm + p.trsm_off);
+            k_trsm<T><<<p.trsm_cnt, kTrsmThreads, 0, st>>>(lnz, h->d_chunks, h->d_trsm + p.trsm_off);
             E();
             launches++;
         }
@@ -187,17 +187,21 @@ struct Plan {
     std::vector<RLPair> rlpairs;
     std::vector<LoopItem> loops;
     std::vector<LevelPlan> levels;
+    int64_t inv_size = 0;  // elements of the diagonal-block inverses
     double class_flops[kProfClasses] = {};
 };
 
 void build_plan(const sc_symbolic *s, int precision, Plan &P) {
     P.cd.resize(s->chunks.size());
+    int64_t inv = 0;
     for (size_t c = 0; c < s->chunks.size(); c++) {
         const Chunk &ch = s->chunks[c];
         int32_t J = ch.sn;
-        P.cd[c] = ChunkDev{s->lnz_off[J], s->gl_ptr[J], s->lnz_ld[J], (int32_t)(s->gl_ptr[J + 1] - s->gl_ptr[J]), ch.c0,
-                           ch.w, s->sup_ptr[J] + ch.c0, 0};
+        P.cd[c] = ChunkDev{s->lnz_off[J], s->gl_ptr[J], inv, s->lnz_ld[J], (int32_t)(s->gl_ptr[J + 1] - s->gl_ptr[J]),
+                           ch.c0, ch.w, s->sup_ptr[J] + ch.c0, 0};
+        inv += (int64_t)ch.w * ch.w;
     }
+    P.inv_size = inv;
     const bool tc = precision == SC_TF32;
     std::vector<int32_t> tmap_of_sn(s->nsuper, -1);
     {
@@ -339,6 +343,11 @@ int numeric_create(sc_symbolic *s, int precision, sc_numeric **out) {
     }
     Plan P;
     build_plan(s, precision, P);
+    if (precision != SC_FP64) {
+        if (cudaMalloc(&h->d_inv, (size_t)std::max<int64_t>(1, P.inv_size) * sizeof(float)) != cudaSuccess)
+            return fail(SC_ERR_OOM);
+        bytes += P.inv_size * 4;
+    }
     std::copy(P.class_flops, P.class_flops + kProfClasses, h->class_flops);
     h->plans = P.levels;
     h->ntasks = (int32_t)P.tasks.size();
@@ -485,12 +494,14 @@ int numeric_export_L(const sc_numeric *h, double *out) {
 void numeric_free(sc_numeric *h) {
     if (!h) return;
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    for (auto &g : h->sg)
+        if (g) cudaGraphExecDestroy(g);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     void *ptrs[] = {h->d_lnz, h->d_pool, h->d_valmap, h->d_values, h->d_diagpos, h->d_adiag, h->d_info,
                     h->d_chunks, h->d_potrf, h->d_trsm, h->d_gemm, h->d_small, h->d_tasks, h->d_rlpairs,
                     h->d_rlrelind, h->d_glbind, h->d_perm, h->d_csr_ptr, h->d_csr_col, h->d_csr_val,
                     h->d_csr_map, h->d_counters, h->d_xw, h->d_solve_tiles, h->d_sn, h->d_blk, h->d_rbval,
-                    h->d_loops, h->d_tmaps, h->d_tmap_of_sn, h->d_err, h->d_x, h->d_r, h->d_b, h->d_xbest, h->d_y, h->d_z, h->d_acc, h->d_red};
+                    h->d_loops, h->d_tmaps, h->d_tmap_of_sn, h->d_err, h->d_inv, h->d_x, h->d_r, h->d_b, h->d_xbest, h->d_y, h->d_z, h->d_acc, h->d_red};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->sym) h->sym->refs--;

@@ -21,10 +21,11 @@ __global__ void k_scatter_values(T *__restrict__ lnz, const int64_t *__restrict_
 }
 
 // --------------------------------------------------------------------- K1
-// POTRF of each chunk's w x w diagonal block (lower) in shared memory, column
-// by column, right-looking (pivot, scale the column, rank-1 update of the
-// trailing triangle); a 16 x 16 thread grid updates the trailing triangle and
-// pivots are applied as one reciprocal per column.
+// POTRF of each chunk's w x w diagonal block (lower) in shared memory,
+// right-looking by panels of 8 columns: one warp factors a panel column by
+// column (pivot, reciprocal, scale, update of the panel's later columns) with
+// warp-level synchronisation, then all 256 threads apply the panel's rank-8
+// update to the trailing triangle.
 //   T = double: one pass in FP64; a pivot d <= 0 sets info.
 //   T = float : one pass in FP32. If some pivot d (before the square root)
 //               is <= tau * |A_jj| (A_jj = the diagonal entry of the input
@@ -34,46 +35,89 @@ __global__ void k_scatter_values(T *__restrict__ lnz, const int64_t *__restrict_
 // info receives the minimum failing column (1-based, final ordering).
 template <typename S>
 __device__ bool potrf_pass(S (*a)[kMaxChunk + 1], int w, const double *__restrict__ adiag, int col0, double tau,
-                           bool check_low, int32_t *__restrict__ info, int *flag, S *rcp) {
+                           bool check_low, int32_t *__restrict__ info, int *flag) {
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // 16 x 16 threads
-    for (int k = 0; k < w; k++) {
-        if (threadIdx.x == 0) {
-            S d = a[k][k];
-            if (check_low) {
-                if (!((double)d > tau * fabs(adiag[col0 + k]))) *flag = 1;
-            } else if (!(d > S(0))) {
-                atomicMin(info, col0 + k + 1);
-                d = S(1);
+    constexpr int PW = 8;                                    // panel width
+    for (int p0 = 0; p0 < w; p0 += PW) {
+        const int p1 = min(p0 + PW, w);
+        if (warp == 0) {
+            // panel p0..p1-1: columns one by one, warp-synchronous
+            for (int k = p0; k < p1; k++) {
+                S d = a[k][k];
+                if (check_low) {
+                    if (!((double)d > tau * fabs(adiag[col0 + k]))) {  // the same value in every lane
+                        if (lane == 0) *flag = 1;
+                        break;
+                    }
+                } else if (!(d > S(0))) {
+                    if (lane == 0) atomicMin(info, col0 + k + 1);
+                    d = S(1);
+                }
+                if (!(d > S(0))) d = S(1);
+                const S r = sqrt(d), rk = S(1) / r;
+                __syncwarp();
+                if (lane == 0) a[k][k] = r;
+                for (int i = k + 1 + lane; i < w; i += 32) a[i][k] *= rk;
+                __syncwarp();
+                for (int i = k + 1 + lane; i < w; i += 32) {
+                    const S aik = a[i][k];
+                    const int jend = min(p1 - 1, i);
+                    for (int j = k + 1; j <= jend; j++) a[i][j] -= aik * a[j][k];
+                }
+                __syncwarp();
             }
-            if (!(d > S(0))) d = S(1);
-            S r = sqrt(d);
-            a[k][k] = r;
-            *rcp = S(1) / r;
         }
         __syncthreads();
         if (check_low && *flag) return false;
-        const S rk = *rcp;
-        for (int i = k + 1 + threadIdx.x; i < w; i += blockDim.x) a[i][k] *= rk;
-        __syncthreads();
-        // trailing update of the lower triangle: rows i = k+1+ty+16a, columns j = k+1+tx+16b, j <= i
-        for (int i = k + 1 + ty; i < w; i += 16) {
-            const S aik = a[i][k];
-            for (int j = k + 1 + tx; j <= i; j += 16) a[i][j] -= aik * a[j][k];
+        // rank-(p1-p0) update of the trailing lower triangle
+        for (int i = p1 + ty; i < w; i += 16) {
+            S ai[PW];
+#pragma unroll
+            for (int t = 0; t < PW; t++) ai[t] = p0 + t < p1 ? a[i][p0 + t] : S(0);
+            for (int j = p1 + tx; j <= i; j += 16) {
+                S acc = S(0);
+#pragma unroll
+                for (int t = 0; t < PW; t++) acc += ai[t] * (p0 + t < p1 ? a[j][p0 + t] : S(0));
+                a[i][j] -= acc;
+            }
         }
         __syncthreads();
     }
     return true;
 }
 
+// dynamic shared memory of k_potrf: the block (FP64 or FP32), then the inverse buffer (FP32)
+constexpr int kPotrfInvOff = kMaxChunk * (kMaxChunk + 1);  // in doubles: after the FP64 block
+constexpr int kPotrfSmem = kMaxChunk * (kMaxChunk + 1) * 8 + kMaxChunk * (kMaxChunk + 1) * 4;
+
+// Inverse of the factored w x w lower-triangular block held in shared memory,
+// stored row-major (ld = w) in FP32 for the solve sweeps of FP32 / TF32
+// factors. Thread j builds column j by forward substitution in FP32, keeping
+// the column in the shared buffer iv (each thread reads only its own column).
+template <typename S>
+__device__ void tri_inverse(const S (*a)[kMaxChunk + 1], int w, float (*iv)[kMaxChunk + 1],
+                            float *__restrict__ out) {
+    const int j = threadIdx.x;
+    if (j < w) {
+        for (int i = 0; i < j; i++) iv[i][j] = 0.f;
+        for (int i = j; i < w; i++) {
+            float acc = i == j ? 1.f : 0.f;
+            for (int t = j; t < i; t++) acc -= (float)a[i][t] * iv[t][j];
+            iv[i][j] = acc / (float)a[i][i];
+        }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) out[idx] = iv[idx / w][idx % w];
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_potrf(T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
                                                const int32_t *__restrict__ list, const double *__restrict__ adiag,
                                                int32_t *__restrict__ info, int32_t *__restrict__ low_pivots,
-                                               double tau) {
+                                               double tau, float *__restrict__ inv) {
     extern __shared__ double smem_potrf[];
     __shared__ int flag;
-    __shared__ double rcp64;
-    __shared__ float rcp32;
     const ChunkDev ch = chunks[list[blockIdx.x]];
     const int w = ch.w;
     T *base = lnz + ch.off + (int64_t)ch.c0 * ch.ld + ch.c0;
@@ -85,11 +129,12 @@ __global__ void __launch_bounds__(256) k_potrf(T *__restrict__ lnz, const ChunkD
             a[r][c] = (r >= c) ? (float)base[(int64_t)r * ch.ld + c] : 0.f;
         }
         __syncthreads();
-        if (potrf_pass<float>(a, w, adiag, ch.col0, tau, true, info, &flag, &rcp32)) {
+        if (potrf_pass<float>(a, w, adiag, ch.col0, tau, true, info, &flag)) {
             for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
                 int r = idx / w, c = idx % w;
                 if (r >= c) base[(int64_t)r * ch.ld + c] = (T)a[r][c];
             }
+            tri_inverse<float>(a, w, reinterpret_cast<float (*)[kMaxChunk + 1]>(smem_potrf + kPotrfInvOff), inv + ch.inv);
             return;
         }
         if (threadIdx.x == 0) atomicAdd(low_pivots, 1);
@@ -102,23 +147,29 @@ __global__ void __launch_bounds__(256) k_potrf(T *__restrict__ lnz, const ChunkD
         a[r][c] = (r >= c) ? (double)base[(int64_t)r * ch.ld + c] : 0.0;
     }
     __syncthreads();
-    potrf_pass<double>(a, w, adiag, ch.col0, tau, false, info, &flag, &rcp64);
+    potrf_pass<double>(a, w, adiag, ch.col0, tau, false, info, &flag);
     for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
         int r = idx / w, c = idx % w;
         if (r >= c) base[(int64_t)r * ch.ld + c] = (T)a[r][c];
     }
+    if (sizeof(T) == 4) {
+        __syncthreads();
+        tri_inverse<double>(a, w, reinterpret_cast<float (*)[kMaxChunk + 1]>(smem_potrf + kPotrfInvOff), inv + ch.inv);
+    }
 }
-constexpr int kPotrfSmem = kMaxChunk * (kMaxChunk + 1) * 8;
 
 // --------------------------------------------------------------------- K2
 // TRSM of the rows below each chunk's diagonal block: row x <- x L_cc^{-T} by
-// forward substitution, one row per thread held in registers (the chunk is
-// zero-padded to 64 columns so the substitution unrolls fully), pivots applied
-// as reciprocals, L_cc broadcast from shared memory. Storage precision.
-constexpr int kTrsmRows = 128;
+// forward substitution. Four threads share a row (thread q of the row holds
+// columns q, q+4, ... in registers; the chunk is zero-padded to 64 columns so
+// the substitution unrolls fully); each pivot value is broadcast from its
+// owner with a width-4 shuffle; pivots are applied as reciprocals; L_cc is
+// read from shared memory. Storage precision.
+constexpr int kTrsmRows = 32;
+constexpr int kTrsmThreads = kTrsmRows * 4;
 template <typename T>
-__global__ void __launch_bounds__(kTrsmRows) k_trsm(T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
-                                                    const TrsmTile *__restrict__ tiles) {
+__global__ void __launch_bounds__(kTrsmThreads) k_trsm(T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
+                                                       const TrsmTile *__restrict__ tiles) {
     __shared__ T l[kMaxChunk][kMaxChunk + 1];
     __shared__ T rinv[kMaxChunk];
     const TrsmTile tl = tiles[blockIdx.x];
@@ -130,24 +181,36 @@ __global__ void __launch_bounds__(kTrsmRows) k_trsm(T *__restrict__ lnz, const C
         l[r][c] = (r < w && c < w && r >= c) ? diag[(int64_t)r * ch.ld + c] : T(0);
     }
     __syncthreads();
-    if (threadIdx.x < kMaxChunk) rinv[threadIdx.x] = threadIdx.x < w ? T(1) / l[threadIdx.x][threadIdx.x] : T(0);
+    for (int k = threadIdx.x; k < kMaxChunk; k += blockDim.x) rinv[k] = k < w ? T(1) / l[k][k] : T(0);
     __syncthreads();
-    const int row = tl.r0 + threadIdx.x;
-    if (row >= ch.m) return;
-    T *xr = lnz + ch.off + (int64_t)row * ch.ld + ch.c0;
-    T x[kMaxChunk];
+    const int q = threadIdx.x % 4;
+    const int row = tl.r0 + threadIdx.x / 4;
+    const bool live = row < ch.m;
+    T *xr = lnz + ch.off + (int64_t)(live ? row : tl.r0) * ch.ld + ch.c0;
+    T x[kMaxChunk / 4];
 #pragma unroll
-    for (int k = 0; k < kMaxChunk; k++) x[k] = k < w ? xr[k] : T(0);
-#pragma unroll
-    for (int k = 0; k < kMaxChunk; k++) {
-        const T v = x[k] * rinv[k];
-        x[k] = v;
-#pragma unroll
-        for (int j = k + 1; j < kMaxChunk; j++) x[j] -= v * l[j][k];
+    for (int jj = 0; jj < kMaxChunk / 4; jj++) {
+        const int j = q + 4 * jj;
+        x[jj] = (live && j < w) ? xr[j] : T(0);
     }
 #pragma unroll
-    for (int k = 0; k < kMaxChunk; k++)
-        if (k < w) xr[k] = x[k];
+    for (int k = 0; k < kMaxChunk; k++) {
+        T v = (q == (k & 3)) ? x[k >> 2] * rinv[k] : T(0);
+        v = __shfl_sync(0xffffffffu, v, k & 3, 4);
+        if (q == (k & 3)) x[k >> 2] = v;
+#pragma unroll
+        for (int jj = 0; jj < kMaxChunk / 4; jj++) {
+            const int j = q + 4 * jj;
+            if (j > k) x[jj] -= v * l[j][k];
+        }
+    }
+    if (live) {
+#pragma unroll
+        for (int jj = 0; jj < kMaxChunk / 4; jj++) {
+            const int j = q + 4 * jj;
+            if (j < w) xr[j] = x[jj];
+        }
+    }
 }
 
 // --------------------------------------------------------------------- K3

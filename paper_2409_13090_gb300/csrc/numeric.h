@@ -66,6 +66,7 @@ struct sc_numeric {
     CUtensorMap *d_tmaps = nullptr;   // one per panel of width >= 16 (SC_TF32)
     int32_t *d_tmap_of_sn = nullptr;
     int32_t *d_err = nullptr;         // nonzero after a bounded device wait gave up
+    void *d_inv = nullptr;            // FP32 inverses of the chunks' diagonal blocks (FP32 / TF32 factors)
     int32_t *d_rlrelind = nullptr;
     // solve
     int32_t *d_glbind = nullptr;
@@ -83,6 +84,11 @@ struct sc_numeric {
     double *d_red = nullptr;        // reductions for eta
     double anorm = 0.0;
     bool solve_ready = false;
+    // solve graphs for sg_nrhs right-hand sides: [0] x = solve(b) + residual,
+    // [1] x += solve(r) + residual
+    int64_t sg_nrhs = -1;
+    cudaGraphExec_t sg[2] = {nullptr, nullptr};
+    int32_t sg_launches[2] = {0, 0};
     int64_t device_bytes = 0;
     // plan
     std::vector<sc::LevelPlan> plans;

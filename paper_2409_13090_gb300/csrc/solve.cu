@@ -31,9 +31,11 @@ namespace {
 constexpr int kRhsBlk = 16;
 constexpr int kSolveRows = 64;
 
+// shared memory of a sweep CTA: the diagonal block (or its inverse), the chunk's
+// right-hand-side values in and out, reciprocal pivots
 template <typename T>
 constexpr int solve_smem() {
-    return (int)sizeof(T) * (kMaxChunk * (kMaxChunk + 1) + kMaxChunk * kRhsBlk + kMaxChunk);
+    return (int)sizeof(T) * (kMaxChunk * (kMaxChunk + 1) + 2 * kMaxChunk * kRhsBlk + kMaxChunk);
 }
 
 // x_perm[k][r] = B[perm[k]][r0 + r]
@@ -107,26 +109,46 @@ __device__ void warp_upper_solve(const T (*l)[kMaxChunk + 1], const T *rinv, int
 template <typename T>
 __global__ void __launch_bounds__(256) k_fwd(const T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
                                              const TrsmTile *__restrict__ tiles, const int32_t *__restrict__ glbind,
-                                             T *__restrict__ x, T *__restrict__ y, int nb) {
+                                             T *__restrict__ x, T *__restrict__ y, int nb,
+                                             const float *__restrict__ inv) {
     extern __shared__ __align__(16) unsigned char smem_fwd[];
     auto l = reinterpret_cast<T (*)[kMaxChunk + 1]>(smem_fwd);
     auto v = reinterpret_cast<T (*)[kRhsBlk]>(smem_fwd + sizeof(T) * kMaxChunk * (kMaxChunk + 1));
-    T *rinv = reinterpret_cast<T *>(smem_fwd + sizeof(T) * (kMaxChunk * (kMaxChunk + 1) + kMaxChunk * kRhsBlk));
+    auto xin = reinterpret_cast<T (*)[kRhsBlk]>(smem_fwd + sizeof(T) * (kMaxChunk * (kMaxChunk + 1) + kMaxChunk * kRhsBlk));
+    T *rinv = reinterpret_cast<T *>(smem_fwd + sizeof(T) * (kMaxChunk * (kMaxChunk + 1) + 2 * kMaxChunk * kRhsBlk));
     const TrsmTile tl = tiles[blockIdx.x];
     const ChunkDev ch = chunks[tl.chunk];
     const int w = ch.w;
-    load_diag(l, rinv, lnz, ch);
-    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
     const bool first = tl.r0 == ch.c0 + w;  // the chunk's first tile writes y_c
-    for (int r = warp; r < nb; r += blockDim.x / 32) {
-        T x0 = lane < w ? x[(int64_t)(ch.col0 + lane) * nb + r] : T(0);
-        T x1 = lane + 32 < w ? x[(int64_t)(ch.col0 + lane + 32) * nb + r] : T(0);
-        warp_lower_solve(l, rinv, w, x0, x1);
-        if (lane < w) v[lane][r] = x0;
-        if (lane + 32 < w) v[lane + 32][r] = x1;
-        if (first) {
-            if (lane < w) y[(int64_t)(ch.col0 + lane) * nb + r] = x0;
-            if (lane + 32 < w) y[(int64_t)(ch.col0 + lane + 32) * nb + r] = x1;
+    if constexpr (sizeof(T) == 4) {
+        // y_c = inv(L_cc) x_c: the block's stored inverse, a parallel product
+        const float *ib = inv + ch.inv;
+        for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) l[idx / w][idx % w] = ib[idx];
+        for (int idx = threadIdx.x; idx < w * nb; idx += blockDim.x) {
+            int k = idx / nb, r = idx % nb;
+            xin[k][r] = x[(int64_t)(ch.col0 + k) * nb + r];
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < w * nb; idx += blockDim.x) {
+            int k = idx / nb, r = idx % nb;
+            T acc = T(0);
+            for (int t = 0; t <= k; t++) acc += l[k][t] * xin[t][r];
+            v[k][r] = acc;
+            if (first) y[(int64_t)(ch.col0 + k) * nb + r] = acc;
+        }
+    } else {
+        load_diag(l, rinv, lnz, ch);
+        const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+        for (int r = warp; r < nb; r += blockDim.x / 32) {
+            T x0 = lane < w ? x[(int64_t)(ch.col0 + lane) * nb + r] : T(0);
+            T x1 = lane + 32 < w ? x[(int64_t)(ch.col0 + lane + 32) * nb + r] : T(0);
+            warp_lower_solve(l, rinv, w, x0, x1);
+            if (lane < w) v[lane][r] = x0;
+            if (lane + 32 < w) v[lane + 32][r] = x1;
+            if (first) {
+                if (lane < w) y[(int64_t)(ch.col0 + lane) * nb + r] = x0;
+                if (lane + 32 < w) y[(int64_t)(ch.col0 + lane + 32) * nb + r] = x1;
+            }
         }
     }
     __syncthreads();
@@ -146,10 +168,12 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_bwd(const T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
                                              const TrsmTile *__restrict__ tiles, const int32_t *__restrict__ glbind,
                                              const T *__restrict__ y, T *__restrict__ z, T *__restrict__ acc,
-                                             int32_t *__restrict__ counters, const int32_t *__restrict__ ntiles, int nb) {
+                                             int32_t *__restrict__ counters, const int32_t *__restrict__ ntiles, int nb,
+                                             const float *__restrict__ inv) {
     extern __shared__ __align__(16) unsigned char smem_bwd[];
     auto l = reinterpret_cast<T (*)[kMaxChunk + 1]>(smem_bwd);
-    T *rinv = reinterpret_cast<T *>(smem_bwd + sizeof(T) * (kMaxChunk * (kMaxChunk + 1) + kMaxChunk * kRhsBlk));
+    auto vin = reinterpret_cast<T (*)[kRhsBlk]>(smem_bwd + sizeof(T) * kMaxChunk * (kMaxChunk + 1));
+    T *rinv = reinterpret_cast<T *>(smem_bwd + sizeof(T) * (kMaxChunk * (kMaxChunk + 1) + 2 * kMaxChunk * kRhsBlk));
     __shared__ int last;
     const TrsmTile tl = tiles[blockIdx.x];
     const ChunkDev ch = chunks[tl.chunk];
@@ -181,6 +205,24 @@ __global__ void __launch_bounds__(256) k_bwd(const T *__restrict__ lnz, const Ch
     __syncthreads();
     if (!last) return;
     __threadfence();
+    if constexpr (sizeof(T) == 4) {
+        // z_c = inv(L_cc)^T (y_c - acc_c) with the block's stored inverse
+        const float *ib = inv + ch.inv;
+        for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) l[idx / w][idx % w] = ib[idx];
+        for (int idx = threadIdx.x; idx < w * nb; idx += blockDim.x) {
+            int k = idx / nb, r = idx % nb;
+            int64_t g = (int64_t)(ch.col0 + k) * nb + r;
+            vin[k][r] = y[g] - __ldcg(acc + g);
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < w * nb; idx += blockDim.x) {
+            int k = idx / nb, r = idx % nb;
+            T sum = T(0);
+            for (int t = k; t < w; t++) sum += l[t][k] * vin[t][r];
+            z[(int64_t)(ch.col0 + k) * nb + r] = sum;
+        }
+        return;
+    }
     load_diag(l, rinv, lnz, ch);
     const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
     for (int r = warp; r < nb; r += blockDim.x / 32) {
@@ -218,14 +260,29 @@ __global__ void k_residual(const int64_t *__restrict__ ptr, const int32_t *__res
                            double *__restrict__ R, int64_t n, int nrhs, double *__restrict__ red) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int c = blockIdx.y;
-    if (i >= n) return;
+    const bool live = i < n;  // every lane stays for the warp-wide reduction below
     const double *x = X + (int64_t)c * n;
-    double s = B[(int64_t)c * n + i];
-    for (int64_t p = ptr[i]; p < ptr[i + 1]; p++) s -= val[p] * x[col[p]];
-    R[(int64_t)c * n + i] = s;
-    atomic_max_nonneg(red + 3 * c, fabs(s));
-    atomic_max_nonneg(red + 3 * c + 1, fabs(x[i]));
-    atomic_max_nonneg(red + 3 * c + 2, fabs(B[(int64_t)c * n + i]));
+    double m0 = 0.0, m1 = 0.0, m2 = 0.0;
+    if (live) {
+        const double b = B[(int64_t)c * n + i];
+        double s = b;
+        for (int64_t p = ptr[i]; p < ptr[i + 1]; p++) s -= val[p] * x[col[p]];
+        R[(int64_t)c * n + i] = s;
+        m0 = fabs(s);
+        m1 = fabs(x[i]);
+        m2 = fabs(b);
+    }
+    // warp-level maxima first: one atomic per warp instead of one per row
+    for (int o = 16; o > 0; o >>= 1) {
+        m0 = fmax(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+        m1 = fmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+        m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomic_max_nonneg(red + 3 * c, m0);
+        atomic_max_nonneg(red + 3 * c + 1, m1);
+        atomic_max_nonneg(red + 3 * c + 2, m2);
+    }
 }
 
 int ensure_solve(sc_numeric *h, int64_t nrhs) {
@@ -284,6 +341,12 @@ int ensure_solve(sc_numeric *h, int64_t nrhs) {
         h->solve_ready = true;
     }
     if (nrhs > h->solve_cap) {
+        for (auto &g : h->sg)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+        h->sg_nrhs = -1;
         double **d64[] = {&h->d_x, &h->d_r, &h->d_b, &h->d_xbest};
         for (double **p : d64) {
             if (*p) cudaFree(*p);
@@ -320,7 +383,7 @@ int tri_solve(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, double 
             const LevelPlan &p = h->plans[lv];
             if (p.sv_cnt) {
                 k_fwd<T><<<p.sv_cnt, 256, solve_smem<T>(), st>>>(lnz, h->d_chunks, h->d_solve_tiles + p.sv_off,
-                                                                 h->d_glbind, xw, y, nb);
+                                                                 h->d_glbind, xw, y, nb, (const float *)h->d_inv);
                 launches++;
             }
         }
@@ -331,7 +394,7 @@ int tri_solve(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, double 
             if (p.sv_cnt) {
                 k_bwd<T><<<p.sv_cnt, 256, solve_smem<T>(), st>>>(lnz, h->d_chunks, h->d_solve_tiles + p.sv_off,
                                                                  h->d_glbind, y, z, acc, h->d_counters,
-                                                                 h->d_counters + nch, nb);
+                                                                 h->d_counters + nch, nb, (const float *)h->d_inv);
                 launches++;
             }
         }
@@ -348,14 +411,57 @@ int tri_solve_any(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, dou
 }
 
 // eta per column for the current iterate in h->d_x; returns host values
-int backward_error(sc_numeric *h, int64_t nrhs, cudaStream_t st, std::vector<double> &eta, int &launches) {
-    const sc_symbolic *s = h->sym;
-    int64_t n = s->n;
+// enqueues the residual r = b - A x and the per-column maxima for eta
+int enqueue_residual(sc_numeric *h, int64_t nrhs, cudaStream_t st, int &launches) {
+    const int64_t n = h->sym->n;
     SC_CUDA(cudaMemsetAsync(h->d_red, 0, 3 * nrhs * sizeof(double), st));
     dim3 g((unsigned)((n + 255) / 256), (unsigned)nrhs);
     k_residual<<<g, 256, 0, st>>>(h->d_csr_ptr, h->d_csr_col, h->d_csr_val, h->d_x, h->d_b, h->d_r, n, (int)nrhs,
                                   h->d_red);
     launches++;
+    return SC_OK;
+}
+
+// one refinement step on the device: step 0: x = solve(b); step 1: x += solve(r); then the residual
+int enqueue_step(sc_numeric *h, int64_t nrhs, int step, cudaStream_t st, int &launches) {
+    const int64_t n = h->sym->n;
+    int rc = step == 0 ? tri_solve_any(h, nrhs, h->d_b, n, h->d_x, n, 0, st, launches)
+                       : tri_solve_any(h, nrhs, h->d_r, n, h->d_x, n, 1, st, launches);
+    if (rc) return rc;
+    return enqueue_residual(h, nrhs, st, launches);
+}
+
+// runs a step, replaying a CUDA graph of it when the handle uses graphs
+int run_step(sc_numeric *h, int64_t nrhs, int step, cudaStream_t st, int &launches) {
+    if (!h->use_graph) return enqueue_step(h, nrhs, step, st, launches);
+    if (h->sg_nrhs != nrhs) {
+        for (auto &g : h->sg)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+        h->sg_nrhs = nrhs;
+    }
+    if (!h->sg[step]) {
+        if (!h->cap_stream) SC_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+        cudaGraph_t g;
+        int cnt = 0;
+        SC_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue_step(h, nrhs, step, h->cap_stream, cnt);
+        cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &g);
+        if (rc) return rc;
+        SC_CUDA(ce);
+        SC_CUDA(cudaGraphInstantiate(&h->sg[step], g, 0));
+        cudaGraphDestroy(g);
+        h->sg_launches[step] = cnt;
+    }
+    SC_CUDA(cudaGraphLaunch(h->sg[step], st));
+    launches += h->sg_launches[step];
+    return SC_OK;
+}
+
+// eta per column from the maxima of the last residual
+int read_eta(sc_numeric *h, int64_t nrhs, cudaStream_t st, std::vector<double> &eta) {
     std::vector<double> red(3 * nrhs);
     SC_CUDA(cudaMemcpyAsync(red.data(), h->d_red, red.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     SC_CUDA(cudaStreamSynchronize(st));
@@ -392,14 +498,14 @@ int numeric_solve(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, dou
     k_anorm<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(h->d_csr_ptr, h->d_csr_val, n, h->d_red + 4095);
     SC_CUDA(cudaMemcpyAsync(&h->anorm, h->d_red + 4095, sizeof(double), cudaMemcpyDeviceToHost, st));
     int launches = 2;
-    // x0 = solve(b)
-    if ((rc = tri_solve_any(h, nrhs, h->d_b, n, h->d_x, n, 0, st, launches))) return rc;
+    // x0 = solve(b), then its residual
+    if ((rc = run_step(h, nrhs, 0, st, launches))) return rc;
     const bool refine = info && info->refine >= 0 ? info->refine != 0 : h->precision != SC_FP64;
     const double tol = s->opt.ir_tol;
     const int maxit = s->opt.ir_maxit;
     std::vector<double> eta, best_eta;
     std::vector<double> hist;
-    if ((rc = backward_error(h, nrhs, st, eta, launches))) return rc;
+    if ((rc = read_eta(h, nrhs, st, eta))) return rc;
     double emax = *std::max_element(eta.begin(), eta.end());
     double best = emax;
     best_eta = eta;
@@ -408,10 +514,10 @@ int numeric_solve(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, dou
     int it = 0;
     if (refine) {
         while (emax > tol && it < maxit) {
-            // d = solve(r); x += d
-            if ((rc = tri_solve_any(h, nrhs, h->d_r, n, h->d_x, n, 1, st, launches))) return rc;
+            // d = solve(r); x += d; new residual
+            if ((rc = run_step(h, nrhs, 1, st, launches))) return rc;
             it++;
-            if ((rc = backward_error(h, nrhs, st, eta, launches))) return rc;
+            if ((rc = read_eta(h, nrhs, st, eta))) return rc;
             emax = *std::max_element(eta.begin(), eta.end());
             hist.push_back(emax);
             if (emax < best) {
