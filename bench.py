@@ -47,6 +47,8 @@ def _args():
     ap.add_argument("--scale", type=float, default=1.0, help="grid-side scale of the workload (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the TF32+refinement vs FP64 comparison on the 80^3 27-point matrix")
     return ap.parse_args()
 
 
@@ -294,6 +296,41 @@ def main():
                            "solve_ms": si["solve_ms"], "pivot_fallbacks": fi.pivot_fallbacks}
             nm.free()
 
+    # ---- the chosen form vs the plain form where refinement converges: 80^3 27-point stencil
+    #      (kappa ~ 1e2), 16 right-hand sides, TF32 factor + FP64 refinement vs FP64 factor + solve
+    compare = None
+    if not args.no_compare and args.workload == 2 and args.scale == 1.0:
+        A3, nrhs3 = inputs.workload(3)
+        sym3 = sc.Symbolic(A3, ordering="grid_nd", grid=A3.grid, nd_leaf=8, pr=True, variant="rlb", merge=args.merge)
+        f3 = sym3.view()["flops"]
+        dv3 = torch.tensor(A3.values, device=dev, dtype=torch.float64)
+        B3 = inputs.rhs(A3.n, nrhs3, inputs.SEED_BASE + 3)
+        B3d = torch.tensor(np.ascontiguousarray(B3.T), device=dev)
+        X3d = torch.zeros_like(B3d)
+        compare = {"workload": A3.name, "n": A3.n, "sum_cj2": f3, "nrhs": nrhs3}
+        for prec, reps in (("tf32", 3), ("fp64", 2)):
+            nm = sym3.factor(dv3, precision=prec)
+            nm.solve(B3d, X3d)
+            best = None
+            for _ in range(reps):
+                a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                a.record(stream)
+                nm.refactor(dv3)
+                b.record(stream)
+                _, si = nm.solve(B3d, X3d)
+                c.record(stream)
+                torch.cuda.synchronize()
+                t = (a.elapsed_time(b), b.elapsed_time(c))
+                if best is None or sum(t) < sum(best[0]):
+                    best = (t, si)
+            (fm, sm_), si = best
+            compare[prec] = {"factor_ms": fm, "factor_gflops": f3 / (fm * 1e-3) / 1e9, "solve_ms": sm_,
+                             "total_ms": fm + sm_, "eta_max": si["eta_max"], "ir_iterations": si["iterations"],
+                             "converged": si["converged"]}
+            nm.free()
+        compare["speedup_total"] = compare["fp64"]["total_ms"] / compare["tf32"]["total_ms"]
+        del dv3, B3d, X3d
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cflops, ctimes, sample = _cpu_sample(2)
@@ -314,7 +351,7 @@ def main():
                            "analyze_s": analyze_s},
                 "factor_ms": fac_ms / K, "solve_ms": sol_ms / K, "eta_max": max(etas),
                 "ir_iterations": max(iters), "gpu_launches": launches, "clocks": clk, "e2e": e2e,
-                "roofline": roofline, "cpu_baseline": cpu, "mixed": mixed}
+                "roofline": roofline, "cpu_baseline": cpu, "mixed": mixed, "tf32_ir_vs_fp64_stencil27_80": compare}
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

@@ -35,7 +35,27 @@ constexpr int kSolveRows = 64;
 // right-hand-side values in and out, reciprocal pivots
 template <typename T>
 constexpr int solve_smem() {
-    return (int)sizeof(T) * (kMaxChunk * (kMaxChunk + 1) + 2 * kMaxChunk * kRhsBlk + kMaxChunk);
+    return (int)sizeof(T) * (2 * kMaxChunk * (kMaxChunk + 1) + 2 * kMaxChunk * kRhsBlk + kMaxChunk);
+}
+
+// Loads a rows x w block (row stride ld) into shared memory dst[r][c] with a
+// fixed trip count per thread, so every thread keeps all of its loads in flight.
+template <typename T>
+__device__ __forceinline__ void stage_block(T (*dst)[kMaxChunk + 1], const T *__restrict__ src, int64_t ld, int rows,
+                                            int w) {
+    constexpr int kIters = kMaxChunk * kMaxChunk / 256;
+    T tmp[kIters];
+#pragma unroll
+    for (int it = 0; it < kIters; it++) {
+        const int idx = threadIdx.x + it * 256;
+        const int r = idx / kMaxChunk, c = idx % kMaxChunk;
+        tmp[it] = (r < rows && c < w) ? src[(int64_t)r * ld + c] : T(0);
+    }
+#pragma unroll
+    for (int it = 0; it < kIters; it++) {
+        const int idx = threadIdx.x + it * 256;
+        dst[idx / kMaxChunk][idx % kMaxChunk] = tmp[it];
+    }
 }
 
 // x_perm[k][r] = B[perm[k]][r0 + r]
@@ -63,11 +83,7 @@ __global__ void k_perm_out(double *__restrict__ X, int64_t ldx, const T *__restr
 
 template <typename T>
 __device__ void load_diag(T (*l)[kMaxChunk + 1], T *rinv, const T *lnz, const ChunkDev &ch) {
-    const T *d = lnz + ch.off + (int64_t)ch.c0 * ch.ld + ch.c0;
-    for (int idx = threadIdx.x; idx < ch.w * ch.w; idx += blockDim.x) {
-        int r = idx / ch.w, c = idx % ch.w;
-        l[r][c] = r >= c ? d[(int64_t)r * ch.ld + c] : T(0);
-    }
+    stage_block(l, lnz + ch.off + (int64_t)ch.c0 * ch.ld + ch.c0, ch.ld, ch.w, ch.w);
     __syncthreads();
     if (threadIdx.x < ch.w) rinv[threadIdx.x] = T(1) / l[threadIdx.x][threadIdx.x];
     __syncthreads();
@@ -116,17 +132,21 @@ __global__ void __launch_bounds__(256) k_fwd(const T *__restrict__ lnz, const Ch
     auto v = reinterpret_cast<T (*)[kRhsBlk]>(smem_fwd + sizeof(T) * kMaxChunk * (kMaxChunk + 1));
     auto xin = reinterpret_cast<T (*)[kRhsBlk]>(smem_fwd + sizeof(T) * (kMaxChunk * (kMaxChunk + 1) + kMaxChunk * kRhsBlk));
     T *rinv = reinterpret_cast<T *>(smem_fwd + sizeof(T) * (kMaxChunk * (kMaxChunk + 1) + 2 * kMaxChunk * kRhsBlk));
+    auto lr = reinterpret_cast<T (*)[kMaxChunk + 1]>(smem_fwd + sizeof(T) * (kMaxChunk * (kMaxChunk + 1) + 2 * kMaxChunk * kRhsBlk + kMaxChunk));
     const TrsmTile tl = tiles[blockIdx.x];
     const ChunkDev ch = chunks[tl.chunk];
     const int w = ch.w;
     const bool first = tl.r0 == ch.c0 + w;  // the chunk's first tile writes y_c
+    const int rows = max(0, min(kSolveRows, ch.m - tl.r0));
+    // the tile's rows of L, staged early so their loads overlap the diagonal solve
+    stage_block(lr, lnz + ch.off + (int64_t)tl.r0 * ch.ld + ch.c0, ch.ld, rows, w);
     if constexpr (sizeof(T) == 4) {
         // y_c = inv(L_cc) x_c: the block's stored inverse, a parallel product
-        const float *ib = inv + ch.inv;
-        for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) l[idx / w][idx % w] = ib[idx];
-        for (int idx = threadIdx.x; idx < w * nb; idx += blockDim.x) {
-            int k = idx / nb, r = idx % nb;
-            xin[k][r] = x[(int64_t)(ch.col0 + k) * nb + r];
+        stage_block(l, (const T *)(inv + ch.inv), w, w, w);
+#pragma unroll
+        for (int it = 0; it < kMaxChunk * kRhsBlk / 256; it++) {
+            const int idx = threadIdx.x + it * 256, k = idx / nb, r = idx % nb;
+            if (idx < w * nb) xin[k][r] = x[(int64_t)(ch.col0 + k) * nb + r];
         }
         __syncthreads();
         for (int idx = threadIdx.x; idx < w * nb; idx += blockDim.x) {
@@ -152,12 +172,10 @@ __global__ void __launch_bounds__(256) k_fwd(const T *__restrict__ lnz, const Ch
         }
     }
     __syncthreads();
-    const int rows = max(0, min(kSolveRows, ch.m - tl.r0));
     for (int idx = threadIdx.x; idx < rows * nb; idx += blockDim.x) {
         int i = idx / nb, r = idx % nb;
-        const T *lr = lnz + ch.off + (int64_t)(tl.r0 + i) * ch.ld + ch.c0;
         T acc = T(0);
-        for (int k = 0; k < w; k++) acc += lr[k] * v[k][r];
+        for (int k = 0; k < w; k++) acc += lr[i][k] * v[k][r];
         int g = glbind[ch.gl + tl.r0 + i];
         atomicAdd(x + (int64_t)g * nb + r, -acc);
     }
@@ -183,13 +201,14 @@ __global__ void __launch_bounds__(256) k_bwd(const T *__restrict__ lnz, const Ch
         // stage the tile's rows of L (coalesced row reads) and the matching z rows
         auto lt = reinterpret_cast<T (*)[kMaxChunk + 1]>(smem_bwd);  // [rows][w]
         auto zt = reinterpret_cast<T (*)[kRhsBlk]>(smem_bwd + sizeof(T) * kMaxChunk * (kMaxChunk + 1));
-        for (int idx = threadIdx.x; idx < rows * w; idx += blockDim.x) {
-            int i = idx / w, k = idx % w;
-            lt[i][k] = lnz[ch.off + (int64_t)(tl.r0 + i) * ch.ld + ch.c0 + k];
-        }
-        for (int idx = threadIdx.x; idx < rows * nb; idx += blockDim.x) {
-            int i = idx / nb, r = idx % nb;
-            zt[i][r] = z[(int64_t)glbind[ch.gl + tl.r0 + i] * nb + r];
+        __shared__ int32_t grow[kSolveRows];
+        if (threadIdx.x < rows) grow[threadIdx.x] = glbind[ch.gl + tl.r0 + threadIdx.x];
+        stage_block(lt, lnz + ch.off + (int64_t)tl.r0 * ch.ld + ch.c0, ch.ld, rows, w);
+        __syncthreads();
+#pragma unroll
+        for (int it = 0; it < kSolveRows * kRhsBlk / 256; it++) {
+            const int idx = threadIdx.x + it * 256, i = idx / nb, r = idx % nb;
+            if (idx < rows * nb) zt[i][r] = z[(int64_t)grow[i] * nb + r];
         }
         __syncthreads();
         for (int idx = threadIdx.x; idx < w * nb; idx += blockDim.x) {
@@ -207,12 +226,14 @@ __global__ void __launch_bounds__(256) k_bwd(const T *__restrict__ lnz, const Ch
     __threadfence();
     if constexpr (sizeof(T) == 4) {
         // z_c = inv(L_cc)^T (y_c - acc_c) with the block's stored inverse
-        const float *ib = inv + ch.inv;
-        for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) l[idx / w][idx % w] = ib[idx];
-        for (int idx = threadIdx.x; idx < w * nb; idx += blockDim.x) {
-            int k = idx / nb, r = idx % nb;
-            int64_t g = (int64_t)(ch.col0 + k) * nb + r;
-            vin[k][r] = y[g] - __ldcg(acc + g);
+        stage_block(l, (const T *)(inv + ch.inv), w, w, w);
+#pragma unroll
+        for (int it = 0; it < kMaxChunk * kRhsBlk / 256; it++) {
+            const int idx = threadIdx.x + it * 256, k = idx / nb, r = idx % nb;
+            if (idx < w * nb) {
+                int64_t g = (int64_t)(ch.col0 + k) * nb + r;
+                vin[k][r] = y[g] - __ldcg(acc + g);
+            }
         }
         __syncthreads();
         for (int idx = threadIdx.x; idx < w * nb; idx += blockDim.x) {
