@@ -87,6 +87,25 @@ __device__ bool potrf_pass(S (*a)[kMaxChunk + 1], int w, const double *__restric
     return true;
 }
 
+// Loads the lower triangle of a w x w block (row stride ld) into shared memory
+// (upper part zero) with a fixed trip count per thread (256 threads), so each
+// thread keeps all of its loads in flight.
+template <typename S, typename T>
+__device__ __forceinline__ void load_block(S (*a)[kMaxChunk + 1], const T *__restrict__ src, int64_t ld, int w) {
+    constexpr int kIters = kMaxChunk * kMaxChunk / 256;
+    T tmp[kIters];
+#pragma unroll
+    for (int it = 0; it < kIters; it++) {
+        const int idx = threadIdx.x + it * 256, r = idx / kMaxChunk, c = idx % kMaxChunk;
+        tmp[it] = (r < w && c <= r) ? src[(int64_t)r * ld + c] : T(0);
+    }
+#pragma unroll
+    for (int it = 0; it < kIters; it++) {
+        const int idx = threadIdx.x + it * 256;
+        a[idx / kMaxChunk][idx % kMaxChunk] = (S)tmp[it];
+    }
+}
+
 // dynamic shared memory of k_potrf: the block (FP64 or FP32), then the inverse buffer (FP32)
 constexpr int kPotrfInvOff = kMaxChunk * (kMaxChunk + 1);  // in doubles: after the FP64 block
 constexpr int kPotrfSmem = kMaxChunk * (kMaxChunk + 1) * 8 + kMaxChunk * (kMaxChunk + 1) * 4;
@@ -124,10 +143,7 @@ __global__ void __launch_bounds__(256) k_potrf(T *__restrict__ lnz, const ChunkD
     if (threadIdx.x == 0) flag = 0;
     if (sizeof(T) == 4) {
         auto a = reinterpret_cast<float (*)[kMaxChunk + 1]>(smem_potrf);
-        for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
-            int r = idx / w, c = idx % w;
-            a[r][c] = (r >= c) ? (float)base[(int64_t)r * ch.ld + c] : 0.f;
-        }
+        load_block(a, base, ch.ld, w);
         __syncthreads();
         if (potrf_pass<float>(a, w, adiag, ch.col0, tau, true, info, &flag)) {
             for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
@@ -142,10 +158,7 @@ __global__ void __launch_bounds__(256) k_potrf(T *__restrict__ lnz, const ChunkD
     }
     // FP64 factorization (the FP64 path, or the fallback of a low pivot)
     auto a = reinterpret_cast<double (*)[kMaxChunk + 1]>(smem_potrf);
-    for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
-        int r = idx / w, c = idx % w;
-        a[r][c] = (r >= c) ? (double)base[(int64_t)r * ch.ld + c] : 0.0;
-    }
+    load_block(a, base, ch.ld, w);
     __syncthreads();
     potrf_pass<double>(a, w, adiag, ch.col0, tau, false, info, &flag);
     for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
@@ -176,9 +189,19 @@ __global__ void __launch_bounds__(kTrsmThreads) k_trsm(T *__restrict__ lnz, cons
     const ChunkDev ch = chunks[tl.chunk];
     const int w = ch.w;
     const T *diag = lnz + ch.off + (int64_t)ch.c0 * ch.ld + ch.c0;
-    for (int idx = threadIdx.x; idx < kMaxChunk * kMaxChunk; idx += blockDim.x) {
-        int r = idx / kMaxChunk, c = idx % kMaxChunk;
-        l[r][c] = (r < w && c < w && r >= c) ? diag[(int64_t)r * ch.ld + c] : T(0);
+    {
+        constexpr int kIters = kMaxChunk * kMaxChunk / kTrsmThreads;
+        T tmp[kIters];
+#pragma unroll
+        for (int it = 0; it < kIters; it++) {
+            const int idx = threadIdx.x + it * kTrsmThreads, r = idx / kMaxChunk, c = idx % kMaxChunk;
+            tmp[it] = (r < w && c <= r) ? diag[(int64_t)r * ch.ld + c] : T(0);
+        }
+#pragma unroll
+        for (int it = 0; it < kIters; it++) {
+            const int idx = threadIdx.x + it * kTrsmThreads;
+            l[idx / kMaxChunk][idx % kMaxChunk] = tmp[it];
+        }
     }
     __syncthreads();
     for (int k = threadIdx.x; k < kMaxChunk; k += blockDim.x) rinv[k] = k < w ? T(1) / l[k][k] : T(0);
@@ -346,6 +369,7 @@ __global__ void __launch_bounds__(256) k_rlb_loop(T *__restrict__ lnz, const Loo
                 const T *a = src + (int64_t)(B.pos + i) * J.ld;
                 const T *bb = src + (int64_t)(B.pos + j) * J.ld;
                 T acc = T(0);
+#pragma unroll 8
                 for (int k = 0; k < K; k++) acc += a[k] * bb[k];
                 atomicAdd(C + (int64_t)i * P.ld + j, -acc);
             }
@@ -370,6 +394,7 @@ __global__ void __launch_bounds__(256) k_rlb_loop(T *__restrict__ lnz, const Loo
                 const T *a = src + (int64_t)(apos + i) * J.ld;
                 const T *bb = src + (int64_t)(B.pos + j) * J.ld;
                 T acc = T(0);
+#pragma unroll 8
                 for (int k = 0; k < K; k++) acc += a[k] * bb[k];
                 atomicAdd(C + (int64_t)i * P.ld + j, -acc);
             }
