@@ -73,7 +73,9 @@ struct Prof {
 };
 
 template <typename T>
-int run_levels(sc_numeric *h, cudaStream_t st, Prof *prof = nullptr) {
+// st2 (optional, graph capture only): a second stream on which each level's
+// device RLB loops run concurrently with the level's tiled products.
+int run_levels(sc_numeric *h, cudaStream_t st, Prof *prof = nullptr, cudaStream_t st2 = nullptr) {
     const sc_symbolic *s = h->sym;
     auto B = [&](int cls) {
         if (prof) prof->begin(cls);
@@ -110,10 +112,18 @@ int run_levels(sc_numeric *h, cudaStream_t st, Prof *prof = nullptr) {
             E();
             launches++;
         }
+        bool join = false;
         if (p.loop_cnt) {
             B(kProfLoop);
-            k_rlb_loop<T><<<p.loop_cnt, 256, 0, st>>>(lnz, h->d_loops + p.loop_off, h->d_sn, h->d_blk,
-                                                                 h->d_rbval);
+            cudaStream_t ls = st;
+            if (st2 && (p.gemm_cnt || p.tc_cnt)) {  // fork: loops and tiled products are independent
+                SC_CUDA(cudaEventRecord(h->ev_fork, st));
+                SC_CUDA(cudaStreamWaitEvent(st2, h->ev_fork, 0));
+                ls = st2;
+                join = true;
+            }
+            k_rlb_loop<T><<<p.loop_cnt, 256, 0, ls>>>(lnz, h->d_loops + p.loop_off, h->d_sn, h->d_blk, h->d_rbval);
+            if (join) SC_CUDA(cudaEventRecord(h->ev_join, st2));
             E();
             launches++;
         }
@@ -152,6 +162,7 @@ int run_levels(sc_numeric *h, cudaStream_t st, Prof *prof = nullptr) {
             E();
             launches++;
         }
+        if (join) SC_CUDA(cudaStreamWaitEvent(st, h->ev_join, 0));
         for (int32_t q0 = 0; q0 < p.rlp_cnt; q0 += 65535) {  // grid.y holds at most 65535 pairs
             unsigned gx = (unsigned)std::min<int64_t>((p.rlp_max + 255) / 256, 64);
             unsigned gy = (unsigned)std::min<int32_t>(65535, p.rlp_cnt - q0);
@@ -407,9 +418,13 @@ int numeric_factor(sc_numeric *h, const double *values, int on_device, cudaStrea
             // captured once on the handle's own stream (the legacy default stream
             // cannot be captured), then replayed on the caller's stream
             if (!h->cap_stream) SC_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+            if (!h->cap_stream2) SC_CUDA(cudaStreamCreateWithFlags(&h->cap_stream2, cudaStreamNonBlocking));
+            if (!h->ev_fork) SC_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+            if (!h->ev_join) SC_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
             cudaGraph_t g;
             SC_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-            rc = h->precision == SC_FP64 ? run_levels<double>(h, h->cap_stream) : run_levels<float>(h, h->cap_stream);
+            rc = h->precision == SC_FP64 ? run_levels<double>(h, h->cap_stream, nullptr, h->cap_stream2)
+                                         : run_levels<float>(h, h->cap_stream, nullptr, h->cap_stream2);
             cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &g);
             if (rc) return rc;
             SC_CUDA(ce);
@@ -497,6 +512,9 @@ void numeric_free(sc_numeric *h) {
     for (auto &g : h->sg)
         if (g) cudaGraphExecDestroy(g);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->cap_stream2) cudaStreamDestroy(h->cap_stream2);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     void *ptrs[] = {h->d_lnz, h->d_pool, h->d_valmap, h->d_values, h->d_diagpos, h->d_adiag, h->d_info,
                     h->d_chunks, h->d_potrf, h->d_trsm, h->d_gemm, h->d_small, h->d_tasks, h->d_rlpairs,
                     h->d_rlrelind, h->d_glbind, h->d_perm, h->d_csr_ptr, h->d_csr_col, h->d_csr_val,

@@ -98,6 +98,8 @@ struct sc_numeric {
     // graph of the factorization (captured on first use on a stream)
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t cap_stream2 = nullptr;  // side branch of the captured factor graph
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool use_graph = true;
 };
 
