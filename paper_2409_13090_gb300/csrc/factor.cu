@@ -116,7 +116,7 @@ int run_levels(sc_numeric *h, cudaStream_t st, Prof *prof = nullptr, cudaStream_
         if (p.loop_cnt) {
             B(kProfLoop);
             cudaStream_t ls = st;
-            if (st2 && (p.gemm_cnt || p.tc_cnt)) {  // fork: loops and tiled products are independent
+            if (st2 && (p.gemm_cnt || p.tc_cnt || p.tc64_cnt)) {  // fork: loops and tiled products are independent
                 SC_CUDA(cudaEventRecord(h->ev_fork, st));
                 SC_CUDA(cudaStreamWaitEvent(st2, h->ev_fork, 0));
                 ls = st2;
@@ -136,8 +136,15 @@ int run_levels(sc_numeric *h, cudaStream_t st, Prof *prof = nullptr, cudaStream_
         if constexpr (sizeof(T) == 4) {
             if (p.tc_cnt) {
                 B(kProfTc);
-                launch_tc_gemm((float *)lnz, h->d_tasks, h->d_gemm + p.tc_off, p.tc_cnt, h->d_tmaps, h->d_tmap_of_sn,
-                               h->d_err, (long long)s->opt.spin_limit, st);
+                launch_tc_gemm(128, (float *)lnz, h->d_tasks, h->d_gemm + p.tc_off, p.tc_cnt, h->d_tmaps,
+                               h->d_tmap_of_sn, h->d_err, (long long)s->opt.spin_limit, h->num_sms, st);
+                E();
+                launches++;
+            }
+            if (p.tc64_cnt) {
+                B(kProfTc);
+                launch_tc_gemm(64, (float *)lnz, h->d_tasks, h->d_gemm + p.tc64_off, p.tc64_cnt, h->d_tmaps,
+                               h->d_tmap_of_sn, h->d_err, (long long)s->opt.spin_limit, h->num_sms, st);
                 E();
                 launches++;
             }
@@ -240,15 +247,16 @@ void build_plan(const sc_symbolic *s, int precision, Plan &P) {
         p.trsm_cnt = (int32_t)P.trsm.size() - p.trsm_off;
         // product tasks: tensor-core tiles (TF32), SIMT tiles, warp tasks
         std::vector<int32_t> ids_small;
-        std::vector<GemmTile> g_simt, g_tc;
+        std::vector<GemmTile> g_simt, g_tc, g_tc64;
         for (const Task &t : L.tasks) {
             int32_t id = (int32_t)P.tasks.size();
             P.tasks.push_back(t);
+            const int bn = tc ? tc_width(t, tmap_of_sn) : 0;
             if (is_small(t)) {
                 ids_small.push_back(id);
                 P.class_flops[kProfSmall] += task_flops(t);
-            } else if (tc && tc_eligible(t, tmap_of_sn)) {
-                tc_tiles_of(t, id, g_tc);
+            } else if (bn) {
+                tc_tiles_of(t, id, bn, bn == 128 ? g_tc : g_tc64);
                 P.class_flops[kProfTc] += task_flops(t);
             } else {
                 tiles_of(t, id, g_simt);
@@ -261,6 +269,9 @@ void build_plan(const sc_symbolic *s, int precision, Plan &P) {
         p.tc_off = (int32_t)P.gemm.size();
         P.gemm.insert(P.gemm.end(), g_tc.begin(), g_tc.end());
         p.tc_cnt = (int32_t)g_tc.size();
+        p.tc64_off = (int32_t)P.gemm.size();
+        P.gemm.insert(P.gemm.end(), g_tc64.begin(), g_tc64.end());
+        p.tc64_cnt = (int32_t)g_tc64.size();
         p.small_off = (int32_t)P.small.size();
         P.small.insert(P.small.end(), ids_small.begin(), ids_small.end());
         p.small_cnt = (int32_t)ids_small.size();
@@ -305,7 +316,7 @@ int plan_stats(const sc_symbolic *s, int precision, int64_t *out, int nout) {
     tile_tasks = (int64_t)P.tasks.size() - small_tasks;
     int64_t tc_tiles = 0, simt_tiles = 0;
     for (const LevelPlan &l : P.levels) {
-        tc_tiles += l.tc_cnt;
+        tc_tiles += l.tc_cnt + l.tc64_cnt;
         simt_tiles += l.gemm_cnt + l.rlg_cnt;
     }
     int64_t v[] = {(int64_t)P.levels.size(), (int64_t)P.cd.size(), (int64_t)P.tasks.size(), small_tasks, tile_tasks,
@@ -323,6 +334,11 @@ int numeric_create(sc_symbolic *s, int precision, sc_numeric **out) {
     h->precision = precision;
     h->elt = precision == SC_FP64 ? 8 : 4;
     h->use_graph = s->opt.use_graph != 0;
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (h->num_sms < 1) h->num_sms = 1;
+    }
     int64_t &bytes = h->device_bytes;
     auto fail = [&](int code) {
         numeric_free(h);

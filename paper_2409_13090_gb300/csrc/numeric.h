@@ -16,7 +16,8 @@ struct LevelPlan {
     int32_t potrf_off = 0, potrf_cnt = 0;   // chunk ids
     int32_t trsm_off = 0, trsm_cnt = 0;     // TrsmTile
     int32_t gemm_off = 0, gemm_cnt = 0;     // GemmTile (SIMT)
-    int32_t tc_off = 0, tc_cnt = 0;         // GemmTile (tensor cores)
+    int32_t tc_off = 0, tc_cnt = 0;         // GemmTile (tensor cores, 128-column tiles)
+    int32_t tc64_off = 0, tc64_cnt = 0;     // GemmTile (tensor cores, 64-column tiles)
     int32_t small_off = 0, small_cnt = 0;   // task ids (warp kernel)
     int32_t rlg_off = 0, rlg_cnt = 0;       // GemmTile of RL update matrices
     int32_t rls_off = 0, rls_cnt = 0;       // task ids of small RL update matrices
@@ -101,6 +102,7 @@ struct sc_numeric {
     cudaStream_t cap_stream2 = nullptr;  // side branch of the captured factor graph
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool use_graph = true;
+    int num_sms = 152;
 };
 
 namespace sc {

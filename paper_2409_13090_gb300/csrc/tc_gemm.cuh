@@ -1,18 +1,22 @@
-// Tensor-core product tiles for SC_TF32 (sm_103a): C[128 x 128 tile] -= A B^T
+// Tensor-core product tiles for SC_TF32 (sm_103a): C[128 x BN tile] -= A B^T
 // with A, B row slabs of one FP32 supernode panel, TF32 inputs, FP32 accumulate.
 //
-//   TMA (cp.async.bulk.tensor, 128-byte swizzle, one tensor map per source
-//   panel held in global memory) -> 4-stage shared-memory ring guarded by
-//   mbarriers -> tcgen05.mma.cta_group::1.kind::tf32 (M=128, N=128, K=8) issued
-//   by one thread into a 128-column TMEM accumulator -> tcgen05.ld by the four
-//   warps (each owns 32 TMEM lanes = 32 output rows) -> subtract into the
-//   target block of Lnz(P) (plain read-modify-write for an exclusive target,
-//   atomic add otherwise).
+// Persistent, warp-specialised kernel (one or two CTAs per SM, looping over the
+// level's tiles):
+//   warp 0  producer: TMA loads (cp.async.bulk.tensor, 128-byte swizzle, tensor
+//           maps per source panel held in global memory) into a 4-stage ring;
+//   warp 1  MMA issuer: tcgen05.mma.cta_group::1.kind::tf32 (M = 128, N = BN,
+//           K = 8) into one of two TMEM accumulators; tcgen05.commit frees ring
+//           stages and hands finished accumulators to the epilogue;
+//   warps 2-5 epilogue: tcgen05.ld of 32 lanes each, subtract into the target
+//           block of Lnz(P) (plain read-modify-write for an exclusive target,
+//           atomic add otherwise; 16-byte vectors when aligned), then release
+//           the accumulator -- so one tile's epilogue overlaps the next tile's
+//           loads and MMAs.
 // Operands are K-major: a panel row is contiguous along the supernode's
-// columns, which is the inner (K) dimension of every update product.
-// Every wait is bounded by spin_limit iterations; on expiry the kernel sets
-// *err, stops issuing, waits (bounded) for what it issued, frees TMEM and
-// returns without writing its tile.
+// columns, the inner (K) dimension of every update product.
+// Every wait is bounded by spin_limit polls; on expiry the kernel sets *err and
+// the roles stop; TMEM is freed before the CTA exits.
 #pragma once
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -24,13 +28,21 @@
 namespace sc {
 namespace tc {
 
-constexpr int BM = 128, BN = 128, BK = 32;  // BK fp32 = 128 bytes = one swizzle row
+constexpr int BM = 128, BK = 32;  // BK fp32 = 128 bytes = one swizzle row
 constexpr int STAGES = 4;
 constexpr int A_BYTES = BM * BK * 4;
-constexpr int B_BYTES = BN * BK * 4;
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*alignment*/ + 256 /*barriers*/;
-constexpr int TMEM_COLS = 128;
+
+template <int BN>
+struct Cfg {
+    static constexpr int B_BYTES = BN * BK * 4;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*alignment*/ + 256 /*barriers*/;
+    static constexpr int TMEM_COLS = 2 * BN;  // two accumulators
+    static constexpr int CTAS_PER_SM = BN == 64 ? 2 : 1;
+    // instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major, M = 128, N = BN
+    static constexpr uint32_t IDESC =
+        (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -39,6 +51,9 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 }
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     uint32_t ok;
@@ -76,15 +91,13 @@ __device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t addr) {
     d |= (uint64_t)2 << 61;                  // swizzle mode: 128 B
     return d;
 }
-// instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major, M = 128, N = 128
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-
-__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accum) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accum)
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
         : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -108,34 +121,67 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
 }
 
-__global__ void __launch_bounds__(128, 1)
-    k_tc_gemm(float *__restrict__ lnz, const Task *__restrict__ tasks, const GemmTile *__restrict__ tiles,
+// C row segment -= v[0..32) for columns gj0..gj0+31 of row gi (masked at n, and
+// to j <= gi for a lower task).
+__device__ __forceinline__ void epilogue_row(float *__restrict__ crow, const float (&v)[32], int gi, int gj0, int n,
+                                             bool lower, bool excl, bool vec) {
+    const bool full = gj0 + 32 <= n && (!lower || gj0 + 31 <= gi);
+    if (vec && full) {
+        float4 *c4 = reinterpret_cast<float4 *>(crow + gj0);
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const float4 d = make_float4(-v[4 * q], -v[4 * q + 1], -v[4 * q + 2], -v[4 * q + 3]);
+            if (excl) {
+                float4 c = c4[q];
+                c.x += d.x;
+                c.y += d.y;
+                c.z += d.z;
+                c.w += d.w;
+                c4[q] = c;
+            } else {
+                atomicAdd(c4 + q, d);
+            }
+        }
+        return;
+    }
+#pragma unroll
+    for (int j = 0; j < 32; j++) {
+        const int gj = gj0 + j;
+        if (gj < n && (!lower || gj <= gi)) {
+            if (excl) crow[gj] -= v[j];
+            else atomicAdd(crow + gj, -v[j]);
+        }
+    }
+}
+
+template <int BN>
+__global__ void __launch_bounds__(192, 1)
+    k_tc_gemm(float *__restrict__ lnz, const Task *__restrict__ tasks, const GemmTile *__restrict__ tiles, int ntiles,
               const CUtensorMap *__restrict__ tmaps, const int32_t *__restrict__ tmap_of_sn, int32_t *__restrict__ err,
               long long spin_limit) {
+    using C = Cfg<BN>;
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);  // full[S], empty[S], done
-    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 1);
-    __shared__ int abort_flag;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * C::STAGE_BYTES);
+    uint64_t *full = bars, *empty = bars + STAGES, *accf = bars + 2 * STAGES, *acce = bars + 2 * STAGES + 2;
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 4);
+    __shared__ volatile int abort_flag;
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const GemmTile tl = tiles[blockIdx.x];
-    const Task tk = tasks[tl.task];
-    const CUtensorMap *map = tmaps + tmap_of_sn[tk.src];
-    const int nk = (tk.k + BK - 1) / BK;
-    const int ay = tk.a_row + tl.tm * BM, by = tk.b_row + tl.tn * BN;
-
     if (threadIdx.x == 0) {
         abort_flag = 0;
-        for (int s = 0; s < 2 * STAGES + 1; s++) mbar_init(smem_u32(bars + s), 1);
+        for (int s = 0; s < 2 * STAGES; s++) mbar_init(smem_u32(bars + s), 1);
+        for (int a = 0; a < 2; a++) {
+            mbar_init(smem_u32(accf + a), 1);  // one tcgen05.commit per tile
+            mbar_init(smem_u32(acce + a), 4);  // one arrival per epilogue warp
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(map) : "memory");
     }
     __syncwarp();  // thread 0 rejoins warp 0 before the warp-collective allocation
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
-                     "r"(TMEM_COLS)
+                     "r"(C::TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -144,112 +190,134 @@ __global__ void __launch_bounds__(128, 1)
     fence_after();
     const uint32_t tmem = *tmem_holder;
 
-    int issued = 0;  // stages loaded by the producer (for the bounded drain on abort)
-    if (warp == 0 && lane == 0) {
-        // producer: TMA loads of A and B k-blocks into the ring
-        for (int kb = 0; kb < nk; kb++) {
-            const int s = kb % STAGES;
-            const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-            if (kb >= STAGES && !mbar_wait(smem_u32(bars + STAGES + s), ph ^ 1u, spin_limit, err, 1)) {
-                abort_flag = 1;
-                break;
-            }
-            if (abort_flag) break;
-            const uint32_t full = smem_u32(bars + s);
-            mbar_expect_tx(full, STAGE_BYTES);
-            const int x = tk.kx0 + kb * BK;
-            tma_load_2d(smem_u32(smem + s * A_BYTES), map, x, ay, full);
-            tma_load_2d(smem_u32(smem + STAGES * A_BYTES + s * B_BYTES), map, x, by, full);
-            issued = kb + 1;
-        }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        for (int kb = 0; kb < nk; kb++) {
-            const int s = kb % STAGES;
-            const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-            if (!mbar_wait(smem_u32(bars + s), ph, spin_limit, err, 2)) {
-                abort_flag = 1;
-                break;
-            }
-            fence_after();
-            const uint32_t a0 = smem_u32(smem + s * A_BYTES);
-            const uint32_t b0 = smem_u32(smem + STAGES * A_BYTES + s * B_BYTES);
-#pragma unroll
-            for (int kk = 0; kk < BK / 8; kk++) {
-                // advance 8 tf32 = 32 bytes along K inside the swizzle row
-                mma_tf32(tmem, umma_desc_sw128(a0 + kk * 32), umma_desc_sw128(b0 + kk * 32), (kb > 0 || kk > 0) ? 1u : 0u);
-            }
-            mma_commit(smem_u32(bars + STAGES + s));  // frees stage s when these MMAs finish
-        }
-        mma_commit(smem_u32(bars + 2 * STAGES));  // accumulator complete
-    }
-    __syncwarp();
-
-    // epilogue: every warp waits for the accumulator, reads its 32 lanes
-    const bool ok = mbar_wait(smem_u32(bars + 2 * STAGES), 0, spin_limit, err, 3);
-    fence_after();
-    // the collective tcgen05.ld below needs a warp-uniform decision
-    if (__all_sync(0xffffffffu, ok && !abort_flag)) {
-        const int row = warp * 32 + lane;
-        const int gi = tl.tm * BM + row;
-        const bool lower = tk.flags & kTaskLower;
-        const bool excl = tk.flags & kTaskExclusive;
-        float *crow = lnz + tk.c_off + (int64_t)gi * tk.ldc;
-#pragma unroll 1
-        for (int cc = 0; cc < BN / 32; cc++) {
-            float v[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), v);
-            if (gi < tk.m) {
-#pragma unroll
-                for (int j = 0; j < 32; j++) {
-                    const int gj = tl.tn * BN + cc * 32 + j;
-                    if (gj < tk.n && (!lower || gj <= gi)) {
-                        if (excl) crow[gj] -= v[j];
-                        else atomicAdd(crow + gj, -v[j]);
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer
+            uint32_t g = 0;
+            for (int t = blockIdx.x; t < ntiles && !abort_flag; t += gridDim.x) {
+                const GemmTile tl = tiles[t];
+                const Task tk = tasks[tl.task];
+                const int mi = tmap_of_sn[tk.src];
+                const CUtensorMap *amap = tmaps + 2 * mi;
+                const CUtensorMap *bmap = tmaps + 2 * mi + (BN == BM ? 0 : 1);
+                const int nk = (tk.k + BK - 1) / BK;
+                const int ay = tk.a_row + tl.tm * BM, by = tk.b_row + tl.tn * BN;
+                for (int kb = 0; kb < nk; kb++, g++) {
+                    const int s = g % STAGES;
+                    const uint32_t ph = (g / STAGES) & 1u;
+                    if (g >= STAGES && !mbar_wait(smem_u32(empty + s), ph ^ 1u, spin_limit, err, 1)) {
+                        abort_flag = 1;
+                        break;
                     }
+                    const uint32_t fb = smem_u32(full + s);
+                    mbar_expect_tx(fb, C::STAGE_BYTES);
+                    const int x = tk.kx0 + kb * BK;
+                    tma_load_2d(smem_u32(smem + s * A_BYTES), amap, x, ay, fb);
+                    tma_load_2d(smem_u32(smem + STAGES * A_BYTES + s * C::B_BYTES), bmap, x, by, fb);
                 }
             }
         }
-    }
-    // drain: on an abort, wait (bounded) for every TMA load the producer issued
-    if (warp == 0 && lane == 0 && abort_flag) {
-        for (int kb = 0; kb < issued; kb++) {
-            if (kb + STAGES < issued) continue;  // later loads to the same stage implied completion
-            mbar_wait(smem_u32(bars + kb % STAGES), (uint32_t)(kb / STAGES) & 1u, spin_limit, err, 4);
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer
+            uint32_t g = 0;
+            int i = 0;
+            for (int t = blockIdx.x; t < ntiles && !abort_flag; t += gridDim.x, i++) {
+                const Task tk = tasks[tiles[t].task];
+                const int nk = (tk.k + BK - 1) / BK;
+                const int a = i & 1, u = i >> 1;
+                if (u > 0 && !mbar_wait(smem_u32(acce + a), (uint32_t)(u - 1) & 1u, spin_limit, err, 2)) {
+                    abort_flag = 1;
+                    break;
+                }
+                fence_after();
+                const uint32_t td = tmem + (uint32_t)(a * BN);
+                for (int kb = 0; kb < nk; kb++, g++) {
+                    const int s = g % STAGES;
+                    const uint32_t ph = (g / STAGES) & 1u;
+                    if (!mbar_wait(smem_u32(full + s), ph, spin_limit, err, 3)) {
+                        abort_flag = 1;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t a0 = smem_u32(smem + s * A_BYTES);
+                    const uint32_t b0 = smem_u32(smem + STAGES * A_BYTES + s * C::B_BYTES);
+#pragma unroll
+                    for (int kk = 0; kk < BK / 8; kk++)  // 8 tf32 = 32 bytes along K inside the swizzle row
+                        mma_tf32(td, umma_desc_sw128(a0 + kk * 32), umma_desc_sw128(b0 + kk * 32), C::IDESC,
+                                 (kb > 0 || kk > 0) ? 1u : 0u);
+                    mma_commit(smem_u32(empty + s));  // frees ring stage s when these MMAs finish
+                }
+                mma_commit(smem_u32(accf + a));  // accumulator a complete
+            }
+        }
+    } else {
+        // epilogue warps 2..5: TMEM lanes 32*(warp % 4) .. +31
+        const int quarter = warp % 4;
+        int i = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, i++) {
+            const int a = i & 1, u = i >> 1;
+            const bool ok = mbar_wait(smem_u32(accf + a), (uint32_t)u & 1u, spin_limit, err, 4);
+            if (!__all_sync(0xffffffffu, ok && !abort_flag)) break;
+            fence_after();
+            const GemmTile tl = tiles[t];
+            const Task tk = tasks[tl.task];
+            const int gi = tl.tm * BM + quarter * 32 + lane;
+            const bool lower = tk.flags & kTaskLower;
+            const bool excl = tk.flags & kTaskExclusive;
+            const bool vec = (tk.ldc % 4 == 0) && (tk.c_off % 4 == 0);
+            float *crow = lnz + tk.c_off + (int64_t)gi * tk.ldc;
+#pragma unroll 1
+            for (int cc = 0; cc < BN / 32; cc++) {
+                float v[32];
+                tmem_ld32(tmem + (uint32_t)(a * BN) + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cc * 32), v);
+                if (gi < tk.m) epilogue_row(crow, v, gi, tl.tn * BN + cc * 32, tk.n, lower, excl, vec);
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(acce + a));
         }
     }
+    __syncwarp();
     fence_before();
     __syncthreads();
     fence_after();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
 }
 
 }  // namespace tc
 
 // ---------------------------------------------------------------- host side
 inline bool tc_gemm_init() {
-    return cudaFuncSetAttribute(tc::k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES) ==
-           cudaSuccess;
+    return cudaFuncSetAttribute(tc::k_tc_gemm<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::Cfg<128>::SMEM) ==
+               cudaSuccess &&
+           cudaFuncSetAttribute(tc::k_tc_gemm<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::Cfg<64>::SMEM) ==
+               cudaSuccess;
 }
 
-// A product goes to the tensor cores when its source panel has a tensor map
-// (|J| >= 16: 16-byte row stride, 128-byte aligned base) and it fills a good
-// part of a 128 x 128 tile with K >= 32.
-inline bool tc_eligible(const Task &t, const std::vector<int32_t> &tmap_of_sn) {
-    return tmap_of_sn[t.src] >= 0 && t.k >= 32 && t.m >= 64 && t.n >= 32 && !(t.flags & kTaskStoreU);
+// Tile width for a product on the tensor cores: 128 or 64 columns, or 0 when the
+// product stays on the SIMT units. Needs a tensor map for the source panel
+// (|J| >= 16: 16-byte row stride, 128-byte aligned base), K >= 32 and m >= 64.
+inline int tc_width(const Task &t, const std::vector<int32_t> &tmap_of_sn) {
+    if (tmap_of_sn[t.src] < 0 || t.k < 32 || t.m < 64 || (t.flags & kTaskStoreU)) return 0;
+    if (t.n >= 96) return 128;
+    if (t.n >= 16) return 64;
+    return 0;
 }
 
-inline void tc_tiles_of(const Task &t, int32_t id, std::vector<GemmTile> &out) {
-    int tm = (t.m + tc::BM - 1) / tc::BM, tn = (t.n + tc::BN - 1) / tc::BN;
+inline void tc_tiles_of(const Task &t, int32_t id, int bn, std::vector<GemmTile> &out) {
+    int tm = (t.m + tc::BM - 1) / tc::BM, tn = (t.n + bn - 1) / bn;
     for (int i = 0; i < tm; i++)
         for (int j = 0; j < tn; j++) {
-            if ((t.flags & kTaskLower) && (i * tc::BM + tc::BM - 1) < j * tc::BN) continue;
+            if ((t.flags & kTaskLower) && (i * tc::BM + tc::BM - 1) < j * bn) continue;
             out.push_back(GemmTile{id, i, j, 0});
         }
 }
 
-// Encodes one 2D tensor map per panel of width >= 16 (dims {ld_J, m_J}, box
-// {32, 128}, 128-byte swizzle, zero fill outside the panel).
+// Encodes two 2D tensor maps per panel of width >= 16 (dims {ld_J, m_J}, boxes
+// {32, 128} and {32, 64}, 128-byte swizzle, zero fill outside the panel):
+// maps[2 * tmap_of_sn[J]] and maps[2 * tmap_of_sn[J] + 1].
 inline int tc_encode_maps(const sc_symbolic *s, float *d_lnz, std::vector<CUtensorMap> &maps,
                           std::vector<int32_t> &tmap_of_sn) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -268,25 +336,36 @@ inline int tc_encode_maps(const sc_symbolic *s, float *d_lnz, std::vector<CUtens
         int32_t w = s->sup_ptr[J + 1] - s->sup_ptr[J];
         if (w < 16) continue;
         int64_t m = s->gl_ptr[J + 1] - s->gl_ptr[J];
-        CUtensorMap map;
-        cuuint64_t dims[2] = {(cuuint64_t)s->lnz_ld[J], (cuuint64_t)m};
-        cuuint64_t strides[1] = {(cuuint64_t)s->lnz_ld[J] * 4};
-        cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)tc::BM};
-        cuuint32_t estr[2] = {1, 1};
-        CUresult r = encode(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)(d_lnz + s->lnz_off[J]), dims, strides,
-                            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return SC_ERR_CUDA;
-        tmap_of_sn[J] = (int32_t)maps.size();
-        maps.push_back(map);
+        tmap_of_sn[J] = (int32_t)(maps.size() / 2);
+        for (int rows : {tc::BM, 64}) {
+            CUtensorMap map;
+            cuuint64_t dims[2] = {(cuuint64_t)s->lnz_ld[J], (cuuint64_t)m};
+            cuuint64_t strides[1] = {(cuuint64_t)s->lnz_ld[J] * 4};
+            cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)rows};
+            cuuint32_t estr[2] = {1, 1};
+            CUresult r = encode(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)(d_lnz + s->lnz_off[J]), dims,
+                                strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return SC_ERR_CUDA;
+            maps.push_back(map);
+        }
     }
     return SC_OK;
 }
 
-inline void launch_tc_gemm(float *lnz, const Task *tasks, const GemmTile *tiles, int32_t count,
+// Launches the persistent kernel over `count` tiles of width bn.
+inline void launch_tc_gemm(int bn, float *lnz, const Task *tasks, const GemmTile *tiles, int32_t count,
                            const CUtensorMap *maps, const int32_t *tmap_of_sn, int32_t *err, long long spin_limit,
-                           cudaStream_t st) {
-    tc::k_tc_gemm<<<count, 128, tc::SMEM_BYTES, st>>>(lnz, tasks, tiles, maps, tmap_of_sn, err, spin_limit);
+                           int num_sms, cudaStream_t st) {
+    if (bn == 128) {
+        const int grid = std::min<int>(count, num_sms * tc::Cfg<128>::CTAS_PER_SM);
+        tc::k_tc_gemm<128><<<grid, 192, tc::Cfg<128>::SMEM, st>>>(lnz, tasks, tiles, count, maps, tmap_of_sn, err,
+                                                                   spin_limit);
+    } else {
+        const int grid = std::min<int>(count, num_sms * tc::Cfg<64>::CTAS_PER_SM);
+        tc::k_tc_gemm<64><<<grid, 192, tc::Cfg<64>::SMEM, st>>>(lnz, tasks, tiles, count, maps, tmap_of_sn, err,
+                                                                 spin_limit);
+    }
 }
 
 }  // namespace sc
