@@ -8,7 +8,7 @@
 //   warp 1  MMA issuer: tcgen05.mma.cta_group::1.kind::tf32 (M = 128, N = BN,
 //           K = 8) into one of two TMEM accumulators; tcgen05.commit frees ring
 //           stages and hands finished accumulators to the epilogue;
-//   warps 2-5 epilogue: tcgen05.ld of 32 lanes each, subtract into the target
+//   warps 2-9 epilogue: tcgen05.ld of 32 lanes x half the columns each, subtract into the target
 //           block of Lnz(P) (plain read-modify-write for an exclusive target,
 //           atomic add otherwise; 16-byte vectors when aligned), then release
 //           the accumulator -- so one tile's epilogue overlaps the next tile's
@@ -31,6 +31,9 @@ namespace tc {
 constexpr int BM = 128, BK = 32;  // BK fp32 = 128 bytes = one swizzle row
 constexpr int STAGES = 4;
 constexpr int A_BYTES = BM * BK * 4;
+
+constexpr int kEpiWarps = 8;                 // two per TMEM lane quarter, each half of the columns
+constexpr int kThreads = 32 * (2 + kEpiWarps);  // producer warp, MMA warp, epilogue warps
 
 template <int BN>
 struct Cfg {
@@ -122,24 +125,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 }
 
 // C row segment -= v[0..32) for columns gj0..gj0+31 of row gi (masked at n, and
-// to j <= gi for a lower task).
-__device__ __forceinline__ void epilogue_row(float *__restrict__ crow, const float (&v)[32], int gi, int gj0, int n,
-                                             bool lower, bool excl, bool vec) {
-    const bool full = gj0 + 32 <= n && (!lower || gj0 + 31 <= gi);
-    if (vec && full) {
+// to j <= gi for a lower task). For an exclusive target with an aligned full
+// segment, the caller has already loaded the old values into c (prefetch).
+__device__ __forceinline__ bool seg_vec(int gi, int gj0, int n, bool lower, bool vec) {
+    return vec && gj0 + 32 <= n && (!lower || gj0 + 31 <= gi);
+}
+__device__ __forceinline__ void epilogue_row(float *__restrict__ crow, const float (&v)[32], const float4 (&c)[8],
+                                             int gi, int gj0, int n, bool lower, bool excl, bool vec) {
+    if (seg_vec(gi, gj0, n, lower, vec)) {
         float4 *c4 = reinterpret_cast<float4 *>(crow + gj0);
 #pragma unroll
         for (int q = 0; q < 8; q++) {
-            const float4 d = make_float4(-v[4 * q], -v[4 * q + 1], -v[4 * q + 2], -v[4 * q + 3]);
             if (excl) {
-                float4 c = c4[q];
-                c.x += d.x;
-                c.y += d.y;
-                c.z += d.z;
-                c.w += d.w;
-                c4[q] = c;
+                c4[q] = make_float4(c[q].x - v[4 * q], c[q].y - v[4 * q + 1], c[q].z - v[4 * q + 2],
+                                    c[q].w - v[4 * q + 3]);
             } else {
-                atomicAdd(c4 + q, d);
+                atomicAdd(c4 + q, make_float4(-v[4 * q], -v[4 * q + 1], -v[4 * q + 2], -v[4 * q + 3]));
             }
         }
         return;
@@ -155,7 +156,7 @@ __device__ __forceinline__ void epilogue_row(float *__restrict__ crow, const flo
 }
 
 template <int BN>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(kThreads, Cfg<BN>::CTAS_PER_SM)
     k_tc_gemm(float *__restrict__ lnz, const Task *__restrict__ tasks, const GemmTile *__restrict__ tiles, int ntiles,
               const CUtensorMap *__restrict__ tmaps, const int32_t *__restrict__ tmap_of_sn, int32_t *__restrict__ err,
               long long spin_limit) {
@@ -173,7 +174,7 @@ __global__ void __launch_bounds__(192, 1)
         for (int s = 0; s < 2 * STAGES; s++) mbar_init(smem_u32(bars + s), 1);
         for (int a = 0; a < 2; a++) {
             mbar_init(smem_u32(accf + a), 1);  // one tcgen05.commit per tile
-            mbar_init(smem_u32(acce + a), 4);  // one arrival per epilogue warp
+            mbar_init(smem_u32(acce + a), kEpiWarps);  // one arrival per epilogue warp
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -252,14 +253,10 @@ __global__ void __launch_bounds__(192, 1)
             }
         }
     } else {
-        // epilogue warps 2..5: TMEM lanes 32*(warp % 4) .. +31
-        const int quarter = warp % 4;
+        // epilogue warps 2..9: TMEM lanes 32*(warp % 4) .. +31, column half (warp - 2) / 4
+        const int quarter = warp % 4, half = (warp - 2) / 4;
         int i = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, i++) {
-            const int a = i & 1, u = i >> 1;
-            const bool ok = mbar_wait(smem_u32(accf + a), (uint32_t)u & 1u, spin_limit, err, 4);
-            if (!__all_sync(0xffffffffu, ok && !abort_flag)) break;
-            fence_after();
             const GemmTile tl = tiles[t];
             const Task tk = tasks[tl.task];
             const int gi = tl.tm * BM + quarter * 32 + lane;
@@ -267,11 +264,24 @@ __global__ void __launch_bounds__(192, 1)
             const bool excl = tk.flags & kTaskExclusive;
             const bool vec = (tk.ldc % 4 == 0) && (tk.c_off % 4 == 0);
             float *crow = lnz + tk.c_off + (int64_t)gi * tk.ldc;
+            const int a = i & 1, u = i >> 1;
+            const bool ok = mbar_wait(smem_u32(accf + a), (uint32_t)u & 1u, spin_limit, err, 4);
+            if (!__all_sync(0xffffffffu, ok && !abort_flag)) break;
+            fence_after();
 #pragma unroll 1
-            for (int cc = 0; cc < BN / 32; cc++) {
+            for (int cc = half * (BN / 64); cc < (half + 1) * (BN / 64); cc++) {
+                const int gj0 = tl.tn * BN + cc * 32;
+                // issue the target's loads before the accumulator read so their latencies overlap
+                float4 c[8];
+                const bool pre = excl && gi < tk.m && seg_vec(gi, gj0, tk.n, lower, vec);
+                if (pre) {
+                    const float4 *c4 = reinterpret_cast<const float4 *>(crow + gj0);
+#pragma unroll
+                    for (int q = 0; q < 8; q++) c[q] = c4[q];
+                }
                 float v[32];
                 tmem_ld32(tmem + (uint32_t)(a * BN) + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cc * 32), v);
-                if (gi < tk.m) epilogue_row(crow, v, gi, tl.tn * BN + cc * 32, tk.n, lower, excl, vec);
+                if (gi < tk.m) epilogue_row(crow, v, c, gi, gj0, tk.n, lower, excl, vec);
             }
             fence_before();
             __syncwarp();
@@ -359,12 +369,12 @@ inline void launch_tc_gemm(int bn, float *lnz, const Task *tasks, const GemmTile
                            int num_sms, cudaStream_t st) {
     if (bn == 128) {
         const int grid = std::min<int>(count, num_sms * tc::Cfg<128>::CTAS_PER_SM);
-        tc::k_tc_gemm<128><<<grid, 192, tc::Cfg<128>::SMEM, st>>>(lnz, tasks, tiles, count, maps, tmap_of_sn, err,
-                                                                   spin_limit);
+        tc::k_tc_gemm<128><<<grid, tc::kThreads, tc::Cfg<128>::SMEM, st>>>(lnz, tasks, tiles, count, maps, tmap_of_sn,
+                                                                            err, spin_limit);
     } else {
         const int grid = std::min<int>(count, num_sms * tc::Cfg<64>::CTAS_PER_SM);
-        tc::k_tc_gemm<64><<<grid, 192, tc::Cfg<64>::SMEM, st>>>(lnz, tasks, tiles, count, maps, tmap_of_sn, err,
-                                                                 spin_limit);
+        tc::k_tc_gemm<64><<<grid, tc::kThreads, tc::Cfg<64>::SMEM, st>>>(lnz, tasks, tiles, count, maps, tmap_of_sn,
+                                                                          err, spin_limit);
     }
 }
 
