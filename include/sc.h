@@ -283,6 +283,18 @@ int sc_residual_eta_noalloc(int64_t n, const int64_t *row_ptr, const int32_t *co
                             const double *B, int64_t ldb, const double *X, int64_t ldx, double *R, int64_t ldr,
                             double *eta, void *cuda_stream);
 
+/* Test hook for the failure path of the solve's bounded waits (no counterpart
+ * in the paper). The next sc_solve on h runs with the forward sweep expecting
+ * one arrival more at chunk `chunk` (0-based, in the order of the level
+ * schedule; nchunks - 1 is the root's last chunk) than the sweep delivers, so
+ * the waits at that chunk give up after spin_limit polls and sc_solve returns
+ * SC_ERR_TIMEOUT; every other wait sees the error and stops. The expected
+ * count is restored afterwards, so later solves on h run normally. Nothing
+ * faults: the wait ends by its iteration limit.
+ * Errors: -1 (h NULL), -2 (chunk < 0; a chunk beyond the last makes the next
+ * sc_solve return -1). */
+int sc_test_stall_solve(sc_numeric *h, int64_t chunk);
+
 /* Frees h and its device memory. NULL is accepted. */
 void sc_numeric_free(sc_numeric *h);
 

@@ -97,6 +97,7 @@ def lib():
             "sc_factor_profile": ([P, P, C.c_int, P, P, P, P], C.c_int),
             "sc_probe_fma_peak": ([C.c_int, P, P], C.c_int),
             "sc_plan_stats": ([P, C.c_int, P, C.c_int], C.c_int),
+            "sc_test_stall_solve": ([P, i64], C.c_int),
             "sc_strerror": ([C.c_int], C.c_char_p),
             "sc_build_info": ([], C.c_char_p),
         }
@@ -230,7 +231,7 @@ class Symbolic:
 
     def __init__(self, A=None, *, ordering="natural", grid=None, nd_leaf=8, user_perm=None, pr=True,
                  variant="rlb", precision="fp64", chunk=64, ir_tol=1e-14, ir_maxit=30, use_graph=True,
-                 merge=0.0, _handle=None, _parts=None):
+                 merge=0.0, spin_limit=None, _handle=None, _parts=None):
         self._parts = _parts
         if _handle is not None:
             self._h = _handle
@@ -254,6 +255,8 @@ class Symbolic:
         o.ir_maxit = ir_maxit
         o.use_graph = 1 if use_graph else 0
         o.merge_frac = float(merge)
+        if spin_limit is not None:
+            o.spin_limit = int(spin_limit)
         colptr = np.ascontiguousarray(A.colptr, np.int64)
         rowind = np.ascontiguousarray(A.rowind, np.int32)
         rc, h = sc_analyze(A.n, colptr, rowind, o)
@@ -377,6 +380,14 @@ class Numeric:
             raise SCError(rc, "sc_solve")
         return X, {"iterations": info.iterations, "converged": bool(info.converged), "eta_max": info.eta_max,
                    "eta": eta, "solve_ms": info.solve_ms, "rc": rc, "kernel_launches": info.kernel_launches}
+
+    def stall_next_solve(self, chunk: int):
+        """Test hook (sc_test_stall_solve): the next solve's forward sweep waits at
+        `chunk` for an arrival that never comes; its bounded waits give up and the
+        solve raises SCError(SC_ERR_TIMEOUT)."""
+        rc = lib().sc_test_stall_solve(self._h, int(chunk))
+        if rc:
+            raise SCError(rc, "sc_test_stall_solve")
 
     PROFILE_CLASSES = ["value_load", "potrf", "trsm", "gemm_simt", "gemm_tc", "gemm_warp", "rl_update", "rl_assemble",
                        "rlb_loop"]

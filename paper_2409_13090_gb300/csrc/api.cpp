@@ -159,6 +159,13 @@ int sc_plan_stats(const sc_symbolic *s, int precision, int64_t *out, int nout) {
     return sc::plan_stats(s, precision, out, nout);
 }
 
+int sc_test_stall_solve(sc_numeric *h, int64_t chunk) {
+    if (!h) return -1;
+    if (chunk < 0 || chunk > INT32_MAX) return -2;
+    h->stall_chunk = (int32_t)chunk;
+    return SC_OK;
+}
+
 void sc_numeric_free(sc_numeric *h) { sc::numeric_free(h); }
 
 const char *sc_strerror(int code) {

@@ -56,6 +56,21 @@ void tiles_of(const Task &t, int32_t id, std::vector<GemmTile> &out) {
         }
 }
 
+// FP32 inverses of the factored diagonal blocks of all chunks, for the solve
+// sweeps of FP32 / TF32 factors (one launch after the last level, off the
+// factorization's critical path).
+__global__ void __launch_bounds__(256) k_inverse(const float *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
+                                                 const int32_t *__restrict__ list, float *__restrict__ inv) {
+    extern __shared__ double smem_potrf[];
+    const ChunkDev ch = chunks[list[blockIdx.x]];
+    auto a = reinterpret_cast<float (*)[kMaxChunk + 1]>(smem_potrf);
+    auto iv = a + kMaxChunk;
+    load_block(a, lnz + ch.off + (int64_t)ch.c0 * ch.ld + ch.c0, ch.ld, ch.w);
+    __syncthreads();
+    tri_inverse<float>(a, ch.w, iv, inv + ch.inv);
+}
+
+
 // Optional per-kernel-class timing of one factorization (CUDA events around
 // every launch; only used outside graph capture).
 struct Prof {
@@ -102,7 +117,7 @@ int run_levels(sc_numeric *h, cudaStream_t st, Prof *prof = nullptr, cudaStream_
         if (p.potrf_cnt) {
             B(kProfPotrf);
             k_potrf<T><<<p.potrf_cnt, 256, kPotrfSmem, st>>>(lnz, h->d_chunks, h->d_potrf + p.potrf_off, h->d_adiag,
-                                                              h->d_info, h->d_info + 1, tau, (float *)h->d_inv);
+                                                              h->d_info, h->d_info + 1, tau);
             E();
             launches++;
         }
@@ -179,6 +194,16 @@ int run_levels(sc_numeric *h, cudaStream_t st, Prof *prof = nullptr, cudaStream_
             launches++;
         }
     }
+    if constexpr (sizeof(T) == 4) {
+        // diagonal-block inverses for the solve, all chunks in one launch
+        const int32_t nch = (int32_t)s->chunks.size();
+        if (nch) {
+            B(kProfPotrf);
+            k_inverse<<<nch, 256, kPotrfSmem, st>>>((const float *)lnz, h->d_chunks, h->d_potrf, (float *)h->d_inv);
+            E();
+            launches++;
+        }
+    }
     SC_CUDA(cudaGetLastError());
     h->kernel_launches = launches;
     return SC_OK;
@@ -189,6 +214,7 @@ int set_smem_attrs() {
     if (done) return SC_OK;
     SC_CUDA(cudaFuncSetAttribute(k_potrf<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPotrfSmem));
     SC_CUDA(cudaFuncSetAttribute(k_potrf<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPotrfSmem));
+    SC_CUDA(cudaFuncSetAttribute(k_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, kPotrfSmem));
     if (!tc_gemm_init()) return SC_ERR_CUDA;
     done = true;
     return SC_OK;
@@ -535,7 +561,8 @@ void numeric_free(sc_numeric *h) {
                     h->d_chunks, h->d_potrf, h->d_trsm, h->d_gemm, h->d_small, h->d_tasks, h->d_rlpairs,
                     h->d_rlrelind, h->d_glbind, h->d_perm, h->d_csr_ptr, h->d_csr_col, h->d_csr_val,
                     h->d_csr_map, h->d_counters, h->d_xw, h->d_solve_tiles, h->d_sn, h->d_blk, h->d_rbval,
-                    h->d_loops, h->d_tmaps, h->d_tmap_of_sn, h->d_err, h->d_inv, h->d_x, h->d_r, h->d_b, h->d_xbest, h->d_y, h->d_z, h->d_acc, h->d_red};
+                    h->d_loops, h->d_tmaps, h->d_tmap_of_sn, h->d_err, h->d_inv, h->d_x, h->d_r, h->d_b, h->d_xbest, h->d_y, h->d_z, h->d_acc, h->d_red,
+                    h->d_dep_ptr, h->d_dep, h->d_sync, h->d_serr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->sym) h->sym->refs--;

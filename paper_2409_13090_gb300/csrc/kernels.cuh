@@ -32,10 +32,11 @@ __global__ void k_scatter_values(T *__restrict__ lnz, const int64_t *__restrict_
 //               matrix), the block is refactored in FP64 from the same stored
 //               values and low_pivots is incremented; a pivot <= 0 in that
 //               pass sets info.
-// info receives the minimum failing column (1-based, final ordering).
+// info receives the minimum failing column (1-based, final ordering). dk[k] =
+// |A_jj| of the block's column k, staged in shared memory.
 template <typename S>
-__device__ bool potrf_pass(S (*a)[kMaxChunk + 1], int w, const double *__restrict__ adiag, int col0, double tau,
-                           bool check_low, int32_t *__restrict__ info, int *flag) {
+__device__ bool potrf_pass(S (*a)[kMaxChunk + 1], int w, const double *dk, int col0, double tau, bool check_low,
+                           int32_t *__restrict__ info, int *flag) {
     const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // 16 x 16 threads
     constexpr int PW = 8;                                    // panel width
@@ -46,7 +47,7 @@ __device__ bool potrf_pass(S (*a)[kMaxChunk + 1], int w, const double *__restric
             for (int k = p0; k < p1; k++) {
                 S d = a[k][k];
                 if (check_low) {
-                    if (!((double)d > tau * fabs(adiag[col0 + k]))) {  // the same value in every lane
+                    if (!((double)d > tau * dk[k])) {  // the same value in every lane
                         if (lane == 0) *flag = 1;
                         break;
                     }
@@ -106,9 +107,9 @@ __device__ __forceinline__ void load_block(S (*a)[kMaxChunk + 1], const T *__res
     }
 }
 
-// dynamic shared memory of k_potrf: the block (FP64 or FP32), then the inverse buffer (FP32)
-constexpr int kPotrfInvOff = kMaxChunk * (kMaxChunk + 1);  // in doubles: after the FP64 block
-constexpr int kPotrfSmem = kMaxChunk * (kMaxChunk + 1) * 8 + kMaxChunk * (kMaxChunk + 1) * 4;
+// dynamic shared memory of k_potrf (the block, FP64 or FP32) and of k_inverse
+// (the FP32 block, then the FP32 inverse)
+constexpr int kPotrfSmem = kMaxChunk * (kMaxChunk + 1) * 8;
 
 // Inverse of the factored w x w lower-triangular block held in shared memory,
 // stored row-major (ld = w) in FP32 for the solve sweeps of FP32 / TF32
@@ -134,23 +135,24 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_potrf(T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
                                                const int32_t *__restrict__ list, const double *__restrict__ adiag,
                                                int32_t *__restrict__ info, int32_t *__restrict__ low_pivots,
-                                               double tau, float *__restrict__ inv) {
+                                               double tau) {
     extern __shared__ double smem_potrf[];
     __shared__ int flag;
+    __shared__ double dk[kMaxChunk];
     const ChunkDev ch = chunks[list[blockIdx.x]];
     const int w = ch.w;
     T *base = lnz + ch.off + (int64_t)ch.c0 * ch.ld + ch.c0;
     if (threadIdx.x == 0) flag = 0;
+    if (threadIdx.x < w) dk[threadIdx.x] = fabs(adiag[ch.col0 + threadIdx.x]);
     if (sizeof(T) == 4) {
         auto a = reinterpret_cast<float (*)[kMaxChunk + 1]>(smem_potrf);
         load_block(a, base, ch.ld, w);
         __syncthreads();
-        if (potrf_pass<float>(a, w, adiag, ch.col0, tau, true, info, &flag)) {
+        if (potrf_pass<float>(a, w, dk, ch.col0, tau, true, info, &flag)) {
             for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
                 int r = idx / w, c = idx % w;
                 if (r >= c) base[(int64_t)r * ch.ld + c] = (T)a[r][c];
             }
-            tri_inverse<float>(a, w, reinterpret_cast<float (*)[kMaxChunk + 1]>(smem_potrf + kPotrfInvOff), inv + ch.inv);
             return;
         }
         if (threadIdx.x == 0) atomicAdd(low_pivots, 1);
@@ -160,14 +162,10 @@ __global__ void __launch_bounds__(256) k_potrf(T *__restrict__ lnz, const ChunkD
     auto a = reinterpret_cast<double (*)[kMaxChunk + 1]>(smem_potrf);
     load_block(a, base, ch.ld, w);
     __syncthreads();
-    potrf_pass<double>(a, w, adiag, ch.col0, tau, false, info, &flag);
+    potrf_pass<double>(a, w, dk, ch.col0, tau, false, info, &flag);
     for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
         int r = idx / w, c = idx % w;
         if (r >= c) base[(int64_t)r * ch.ld + c] = (T)a[r][c];
-    }
-    if (sizeof(T) == 4) {
-        __syncthreads();
-        tri_inverse<double>(a, w, reinterpret_cast<float (*)[kMaxChunk + 1]>(smem_potrf + kPotrfInvOff), inv + ch.inv);
     }
 }
 

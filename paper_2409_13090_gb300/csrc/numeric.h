@@ -26,7 +26,6 @@ struct LevelPlan {
     int32_t rlp_off = 0, rlp_cnt = 0;       // RLPair
     int64_t rlp_max = 0;                    // largest assembly work item (elements)
     // solve
-    int32_t sv_off = 0, sv_cnt = 0;         // TrsmTile-like (chunk, row start) for the below-diagonal sweeps
 };
 
 // kernel classes of the per-kernel profile
@@ -76,7 +75,14 @@ struct sc_numeric {
     int32_t *d_csr_col = nullptr;
     double *d_csr_val = nullptr;
     int64_t *d_csr_map = nullptr;
-    int32_t *d_counters = nullptr;  // [nchunks] backward-sweep counters, then [nchunks] tile counts
+    int32_t *d_counters = nullptr;  // [nchunks] solve tiles per chunk, then [nchunks] expected forward arrivals
+    int32_t *d_dep_ptr = nullptr;   // per solve tile: range in d_dep
+    int32_t *d_dep = nullptr;       // distinct chunks the tile's rows fall in
+    int32_t *d_sync = nullptr;      // per sweep: arrivals, backward counters, done flags, work counters
+    int32_t *d_serr = nullptr;      // nonzero after a bounded wait of a solve sweep gave up
+    int32_t solve_tiles = 0;        // tiles of one sweep
+    int32_t solve_grid = 1;         // CTAs of a persistent sweep
+    int32_t stall_chunk = -1;       // test hook: chunk whose expected arrivals are raised by one
     void *d_xw = nullptr;           // permuted right-hand side / forward work vector
     sc::TrsmTile *d_solve_tiles = nullptr;
     int64_t solve_cap = 0;          // rhs capacity of the work vectors

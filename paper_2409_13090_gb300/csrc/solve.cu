@@ -5,9 +5,11 @@
 //   forward  (levels ascending):  y_c = L_cc^{-1} x_c ; x_rows -= L_{rows,c} y_c
 //   backward (levels descending): z_c = L_cc^{-T} (y_c - L_{rows,c}^T z_rows)
 // where c runs over the chunks of a level and rows over the panel rows below
-// the chunk (global row = glbind(J)[row]). The backward gather of a chunk is
-// spread over row tiles; the last tile to finish (per-chunk counter after a
-// memory fence) applies the diagonal solve, so each sweep is one launch per level.
+// the chunk (global row = glbind(J)[row]). Each sweep is one persistent launch:
+// CTAs take row tiles in level order (reverse order backward) and wait on
+// per-chunk counters instead of a barrier per level. The backward gather of a
+// chunk is spread over row tiles; the last tile to finish (per-chunk counter
+// after a memory fence) applies the diagonal solve and marks the chunk done.
 // Refinement: r = b - A x in FP64 on the caller's matrix (CSR), then
 //   eta = ||r||_inf / (||A||_inf ||x||_inf + ||b||_inf) per column, and
 //   x += solve(r) until eta <= ir_tol.
@@ -120,139 +122,255 @@ __device__ void warp_upper_solve(const T (*l)[kMaxChunk + 1], const T *rinv, int
     }
 }
 
-// Forward sweep of one level (one launch). Each tile solves its chunk's diagonal
-// block (one warp per right-hand side), then updates its rows below.
+// FP32 block products of the sweeps, register-blocked over right-hand sides:
+// thread (i = tid % 64, g = tid / 64) forms o[j] = sum_k a(i, k) b[k][4g + j],
+// j < 4, with a(i, k) = a[i][k] (or a[k][i] when kTrans). Lanes of a warp read
+// a at 32 consecutive banks and b as one broadcast 16-byte word, so each k
+// costs two shared-memory wavefronts for four FMAs per lane.
+template <bool kTrans>
+__device__ __forceinline__ void rhs4_product(const float (*a)[kMaxChunk + 1], const float (*b)[kRhsBlk], int i, int g,
+                                             int K, float (&o)[4]) {
+    o[0] = o[1] = o[2] = o[3] = 0.f;
+#pragma unroll 8
+    for (int k = 0; k < K; k++) {
+        const float av = kTrans ? a[k][i] : a[i][k];
+        const float4 bv = *reinterpret_cast<const float4 *>(&b[k][4 * g]);
+        o[0] += av * bv.x;
+        o[1] += av * bv.y;
+        o[2] += av * bv.z;
+        o[3] += av * bv.w;
+    }
+}
+
+// Bounded wait until *flag >= target (acquire at GPU scope). Gives up, setting
+// *err to `code`, after spin_limit polls, or at once when another CTA has
+// already given up.
+__device__ bool wait_flag(const int32_t *flag, int32_t target, int32_t *err, long long spin_limit, int code) {
+    for (long long i = 0; i < spin_limit; i++) {
+        int32_t v;
+        asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
+        if (v >= target) return true;
+        if (*(volatile int32_t *)err) return false;
+        __nanosleep(32);
+    }
+    atomicCAS(err, 0, code);
+    return false;
+}
+
+// next tile index of a sweep for this CTA (broadcast through shared memory);
+// `total` once the sweep is done or a wait has given up
+__device__ __forceinline__ int grab_tile(int32_t *work, int total, int32_t *err, int *slot) {
+    if (threadIdx.x == 0) *slot = *(volatile int32_t *)err ? total : atomicAdd(work, 1);
+    __syncthreads();
+    return *slot;
+}
+
+// Forward sweep: one persistent launch over all tiles in level order. A CTA
+// takes the next tile, stages its rows of L and the chunk's diagonal block (or
+// its inverse), waits until every tile that updates the chunk's rows of x has
+// arrived, solves y_c = L_cc^{-1} x_c and subtracts L_{rows,c} y_c from x. Then
+// it counts one arrival at every chunk its rows fall in. A tile only waits for
+// tiles of lower levels, which were taken earlier by running CTAs, so the
+// sweep needs no co-residency guarantee.
 template <typename T>
 __global__ void __launch_bounds__(256) k_fwd(const T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
-                                             const TrsmTile *__restrict__ tiles, const int32_t *__restrict__ glbind,
-                                             T *__restrict__ x, T *__restrict__ y, int nb,
-                                             const float *__restrict__ inv) {
+                                             const TrsmTile *__restrict__ tiles, int total,
+                                             const int32_t *__restrict__ dep_ptr, const int32_t *__restrict__ dep,
+                                             const int32_t *__restrict__ need, const int32_t *__restrict__ glbind,
+                                             T *__restrict__ x, T *__restrict__ y, int nb, const float *__restrict__ inv,
+                                             int32_t *__restrict__ arrive, int32_t *__restrict__ work,
+                                             int32_t *__restrict__ err, long long spin_limit) {
     extern __shared__ __align__(16) unsigned char smem_fwd[];
     auto l = reinterpret_cast<T (*)[kMaxChunk + 1]>(smem_fwd);
     auto v = reinterpret_cast<T (*)[kRhsBlk]>(smem_fwd + sizeof(T) * kMaxChunk * (kMaxChunk + 1));
     auto xin = reinterpret_cast<T (*)[kRhsBlk]>(smem_fwd + sizeof(T) * (kMaxChunk * (kMaxChunk + 1) + kMaxChunk * kRhsBlk));
     T *rinv = reinterpret_cast<T *>(smem_fwd + sizeof(T) * (kMaxChunk * (kMaxChunk + 1) + 2 * kMaxChunk * kRhsBlk));
     auto lr = reinterpret_cast<T (*)[kMaxChunk + 1]>(smem_fwd + sizeof(T) * (kMaxChunk * (kMaxChunk + 1) + 2 * kMaxChunk * kRhsBlk + kMaxChunk));
-    const TrsmTile tl = tiles[blockIdx.x];
-    const ChunkDev ch = chunks[tl.chunk];
-    const int w = ch.w;
-    const bool first = tl.r0 == ch.c0 + w;  // the chunk's first tile writes y_c
-    const int rows = max(0, min(kSolveRows, ch.m - tl.r0));
-    // the tile's rows of L, staged early so their loads overlap the diagonal solve
-    stage_block(lr, lnz + ch.off + (int64_t)tl.r0 * ch.ld + ch.c0, ch.ld, rows, w);
-    if constexpr (sizeof(T) == 4) {
-        // y_c = inv(L_cc) x_c: the block's stored inverse, a parallel product
-        stage_block(l, (const T *)(inv + ch.inv), w, w, w);
-#pragma unroll
-        for (int it = 0; it < kMaxChunk * kRhsBlk / 256; it++) {
-            const int idx = threadIdx.x + it * 256, k = idx / nb, r = idx % nb;
-            if (idx < w * nb) xin[k][r] = x[(int64_t)(ch.col0 + k) * nb + r];
-        }
+    __shared__ int s_t, s_ok;
+    for (;;) {
+        const int t = grab_tile(work, total, err, &s_t);
+        if (t >= total) break;
+        const TrsmTile tl = tiles[t];
+        const ChunkDev ch = chunks[tl.chunk];
+        const int w = ch.w;
+        const bool first = tl.r0 == ch.c0 + w;  // the chunk's first tile writes y_c
+        const int rows = max(0, min(kSolveRows, ch.m - tl.r0));
+        // loads that need no other tile: the tile's rows of L and the diagonal block
+        stage_block(lr, lnz + ch.off + (int64_t)tl.r0 * ch.ld + ch.c0, ch.ld, rows, w);
+        if constexpr (sizeof(T) == 4) stage_block(l, (const T *)(inv + ch.inv), w, w, w);
+        else load_diag(l, rinv, lnz, ch);
+        if (threadIdx.x == 0) s_ok = wait_flag(arrive + tl.chunk, need[tl.chunk], err, spin_limit, 5);
         __syncthreads();
-        for (int idx = threadIdx.x; idx < w * nb; idx += blockDim.x) {
-            int k = idx / nb, r = idx % nb;
-            T acc = T(0);
-            for (int t = 0; t <= k; t++) acc += l[k][t] * xin[t][r];
-            v[k][r] = acc;
-            if (first) y[(int64_t)(ch.col0 + k) * nb + r] = acc;
-        }
-    } else {
-        load_diag(l, rinv, lnz, ch);
-        const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
-        for (int r = warp; r < nb; r += blockDim.x / 32) {
-            T x0 = lane < w ? x[(int64_t)(ch.col0 + lane) * nb + r] : T(0);
-            T x1 = lane + 32 < w ? x[(int64_t)(ch.col0 + lane + 32) * nb + r] : T(0);
-            warp_lower_solve(l, rinv, w, x0, x1);
-            if (lane < w) v[lane][r] = x0;
-            if (lane + 32 < w) v[lane + 32][r] = x1;
-            if (first) {
-                if (lane < w) y[(int64_t)(ch.col0 + lane) * nb + r] = x0;
-                if (lane + 32 < w) y[(int64_t)(ch.col0 + lane + 32) * nb + r] = x1;
+        if (!s_ok) break;
+        if constexpr (sizeof(T) == 4) {
+            // y_c = inv(L_cc) x_c: the block's stored inverse, a parallel product
+#pragma unroll
+            for (int it = 0; it < kMaxChunk * kRhsBlk / 256; it++) {
+                const int idx = threadIdx.x + it * 256, k = idx / nb, r = idx % nb;
+                if (idx < w * nb) xin[k][r] = __ldcg(x + (int64_t)(ch.col0 + k) * nb + r);
+            }
+            __syncthreads();
+            // the stored inverse is zero above its diagonal: full-width rows
+            const int k = threadIdx.x % kMaxChunk, g = threadIdx.x / kMaxChunk;
+            if (k < w && 4 * g < nb) {
+                float o[4];
+                rhs4_product<false>(l, xin, k, g, w, o);
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const int r = 4 * g + j;
+                    if (r < nb) {
+                        v[k][r] = o[j];
+                        if (first) y[(int64_t)(ch.col0 + k) * nb + r] = o[j];
+                    }
+                }
+            }
+        } else {
+            const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+            for (int r = warp; r < nb; r += blockDim.x / 32) {
+                T x0 = lane < w ? __ldcg(x + (int64_t)(ch.col0 + lane) * nb + r) : T(0);
+                T x1 = lane + 32 < w ? __ldcg(x + (int64_t)(ch.col0 + lane + 32) * nb + r) : T(0);
+                warp_lower_solve(l, rinv, w, x0, x1);
+                if (lane < w) v[lane][r] = x0;
+                if (lane + 32 < w) v[lane + 32][r] = x1;
+                if (first) {
+                    if (lane < w) y[(int64_t)(ch.col0 + lane) * nb + r] = x0;
+                    if (lane + 32 < w) y[(int64_t)(ch.col0 + lane + 32) * nb + r] = x1;
+                }
             }
         }
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < rows * nb; idx += blockDim.x) {
-        int i = idx / nb, r = idx % nb;
-        T acc = T(0);
-        for (int k = 0; k < w; k++) acc += lr[i][k] * v[k][r];
-        int g = glbind[ch.gl + tl.r0 + i];
-        atomicAdd(x + (int64_t)g * nb + r, -acc);
+        __syncthreads();
+        if constexpr (sizeof(T) == 4) {
+            const int i = threadIdx.x % kSolveRows, g = threadIdx.x / kSolveRows;
+            if (i < rows && 4 * g < nb) {
+                float o[4];
+                rhs4_product<false>(lr, v, i, g, w, o);
+                T *xr = x + (int64_t)glbind[ch.gl + tl.r0 + i] * nb;
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+                    if (4 * g + j < nb) atomicAdd(xr + 4 * g + j, -o[j]);
+            }
+        } else {
+            for (int idx = threadIdx.x; idx < rows * nb; idx += blockDim.x) {
+                int i = idx / nb, r = idx % nb;
+                T acc = T(0);
+                for (int k = 0; k < w; k++) acc += lr[i][k] * v[k][r];
+                int g = glbind[ch.gl + tl.r0 + i];
+                atomicAdd(x + (int64_t)g * nb + r, -acc);
+            }
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int p = dep_ptr[t]; p < dep_ptr[t + 1]; p++) atomicAdd(arrive + dep[p], 1);
     }
 }
 
-// Backward sweep of one level (one launch): gather into acc, last tile solves.
+// Backward sweep: one persistent launch over all tiles in reverse level order.
+// A tile stages its rows of L, waits until z is final in every chunk its rows
+// fall in, and adds L_{rows,c}^T z_rows into acc_c; the chunk's last tile to
+// finish solves z_c = L_cc^{-T} (y_c - acc_c) and marks the chunk done.
 template <typename T>
 __global__ void __launch_bounds__(256) k_bwd(const T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
-                                             const TrsmTile *__restrict__ tiles, const int32_t *__restrict__ glbind,
-                                             const T *__restrict__ y, T *__restrict__ z, T *__restrict__ acc,
-                                             int32_t *__restrict__ counters, const int32_t *__restrict__ ntiles, int nb,
-                                             const float *__restrict__ inv) {
+                                             const TrsmTile *__restrict__ tiles, int total,
+                                             const int32_t *__restrict__ dep_ptr, const int32_t *__restrict__ dep,
+                                             const int32_t *__restrict__ ntiles, const int32_t *__restrict__ glbind,
+                                             const T *__restrict__ y, T *__restrict__ z, T *__restrict__ acc, int nb,
+                                             const float *__restrict__ inv, int32_t *__restrict__ cnt,
+                                             int32_t *__restrict__ done, int32_t *__restrict__ work,
+                                             int32_t *__restrict__ err, long long spin_limit) {
     extern __shared__ __align__(16) unsigned char smem_bwd[];
     auto l = reinterpret_cast<T (*)[kMaxChunk + 1]>(smem_bwd);
     auto vin = reinterpret_cast<T (*)[kRhsBlk]>(smem_bwd + sizeof(T) * kMaxChunk * (kMaxChunk + 1));
     T *rinv = reinterpret_cast<T *>(smem_bwd + sizeof(T) * (kMaxChunk * (kMaxChunk + 1) + 2 * kMaxChunk * kRhsBlk));
-    __shared__ int last;
-    const TrsmTile tl = tiles[blockIdx.x];
-    const ChunkDev ch = chunks[tl.chunk];
-    const int w = ch.w;
-    const int rows = max(0, min(kSolveRows, ch.m - tl.r0));
-    if (rows > 0) {
-        // stage the tile's rows of L (coalesced row reads) and the matching z rows
-        auto lt = reinterpret_cast<T (*)[kMaxChunk + 1]>(smem_bwd);  // [rows][w]
-        auto zt = reinterpret_cast<T (*)[kRhsBlk]>(smem_bwd + sizeof(T) * kMaxChunk * (kMaxChunk + 1));
-        __shared__ int32_t grow[kSolveRows];
-        if (threadIdx.x < rows) grow[threadIdx.x] = glbind[ch.gl + tl.r0 + threadIdx.x];
-        stage_block(lt, lnz + ch.off + (int64_t)tl.r0 * ch.ld + ch.c0, ch.ld, rows, w);
-        __syncthreads();
+    auto lt = reinterpret_cast<T (*)[kMaxChunk + 1]>(smem_bwd);  // [rows][w]
+    auto zt = reinterpret_cast<T (*)[kRhsBlk]>(smem_bwd + sizeof(T) * kMaxChunk * (kMaxChunk + 1));
+    __shared__ int32_t grow[kSolveRows];
+    __shared__ int s_t, s_ok, s_last;
+    for (;;) {
+        const int tr = grab_tile(work, total, err, &s_t);
+        if (tr >= total) break;
+        const int t = total - 1 - tr;
+        const TrsmTile tl = tiles[t];
+        const ChunkDev ch = chunks[tl.chunk];
+        const int w = ch.w;
+        const int rows = max(0, min(kSolveRows, ch.m - tl.r0));
+        if (rows > 0) {
+            if (threadIdx.x < rows) grow[threadIdx.x] = glbind[ch.gl + tl.r0 + threadIdx.x];
+            stage_block(lt, lnz + ch.off + (int64_t)tl.r0 * ch.ld + ch.c0, ch.ld, rows, w);
+            if (threadIdx.x == 0) {
+                bool ok = true;
+                for (int p = dep_ptr[t]; p < dep_ptr[t + 1] && ok; p++) ok = wait_flag(done + dep[p], 1, err, spin_limit, 6);
+                s_ok = ok;
+            }
+            __syncthreads();
+            if (!s_ok) break;
 #pragma unroll
-        for (int it = 0; it < kSolveRows * kRhsBlk / 256; it++) {
-            const int idx = threadIdx.x + it * 256, i = idx / nb, r = idx % nb;
-            if (idx < rows * nb) zt[i][r] = z[(int64_t)grow[i] * nb + r];
+            for (int it = 0; it < kSolveRows * kRhsBlk / 256; it++) {
+                const int idx = threadIdx.x + it * 256, i = idx / nb, r = idx % nb;
+                if (idx < rows * nb) zt[i][r] = __ldcg(z + (int64_t)grow[i] * nb + r);
+            }
+            __syncthreads();
+            if constexpr (sizeof(T) == 4) {
+                const int k = threadIdx.x % kMaxChunk, g = threadIdx.x / kMaxChunk;
+                if (k < w && 4 * g < nb) {
+                    float o[4];
+                    rhs4_product<true>(lt, zt, k, g, rows, o);
+                    T *ar = acc + (int64_t)(ch.col0 + k) * nb;
+#pragma unroll
+                    for (int j = 0; j < 4; j++)
+                        if (4 * g + j < nb) atomicAdd(ar + 4 * g + j, o[j]);
+                }
+            } else {
+                for (int idx = threadIdx.x; idx < w * nb; idx += blockDim.x) {
+                    int k = idx / nb, r = idx % nb;
+                    T s = T(0);
+                    for (int i = 0; i < rows; i++) s += lt[i][k] * zt[i][r];
+                    atomicAdd(acc + (int64_t)(ch.col0 + k) * nb + r, s);
+                }
+            }
+            __threadfence();
         }
         __syncthreads();
-        for (int idx = threadIdx.x; idx < w * nb; idx += blockDim.x) {
-            int k = idx / nb, r = idx % nb;
-            T s = T(0);
-            for (int i = 0; i < rows; i++) s += lt[i][k] * zt[i][r];
-            atomicAdd(acc + (int64_t)(ch.col0 + k) * nb + r, s);
-        }
+        if (threadIdx.x == 0) s_last = (atomicAdd(cnt + tl.chunk, 1) == ntiles[tl.chunk] - 1);
+        __syncthreads();
+        if (!s_last) continue;
         __threadfence();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) last = (atomicAdd(counters + tl.chunk, 1) == ntiles[tl.chunk] - 1);
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    if constexpr (sizeof(T) == 4) {
-        // z_c = inv(L_cc)^T (y_c - acc_c) with the block's stored inverse
-        stage_block(l, (const T *)(inv + ch.inv), w, w, w);
+        if constexpr (sizeof(T) == 4) {
+            // z_c = inv(L_cc)^T (y_c - acc_c) with the block's stored inverse
+            stage_block(l, (const T *)(inv + ch.inv), w, w, w);
 #pragma unroll
-        for (int it = 0; it < kMaxChunk * kRhsBlk / 256; it++) {
-            const int idx = threadIdx.x + it * 256, k = idx / nb, r = idx % nb;
-            if (idx < w * nb) {
-                int64_t g = (int64_t)(ch.col0 + k) * nb + r;
-                vin[k][r] = y[g] - __ldcg(acc + g);
+            for (int it = 0; it < kMaxChunk * kRhsBlk / 256; it++) {
+                const int idx = threadIdx.x + it * 256, k = idx / nb, r = idx % nb;
+                if (idx < w * nb) {
+                    int64_t g = (int64_t)(ch.col0 + k) * nb + r;
+                    vin[k][r] = y[g] - __ldcg(acc + g);
+                }
+            }
+            __syncthreads();
+            // inv(L_cc)^T: column k of the inverse, zero above the diagonal
+            const int k = threadIdx.x % kMaxChunk, g = threadIdx.x / kMaxChunk;
+            if (k < w && 4 * g < nb) {
+                float o[4];
+                rhs4_product<true>(l, vin, k, g, w, o);
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+                    if (4 * g + j < nb) z[(int64_t)(ch.col0 + k) * nb + 4 * g + j] = o[j];
+            }
+        } else {
+            load_diag(l, rinv, lnz, ch);
+            const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+            for (int r = warp; r < nb; r += blockDim.x / 32) {
+                const int64_t g0 = (int64_t)(ch.col0 + lane) * nb + r, g1 = (int64_t)(ch.col0 + lane + 32) * nb + r;
+                T x0 = lane < w ? y[g0] - __ldcg(acc + g0) : T(0);
+                T x1 = lane + 32 < w ? y[g1] - __ldcg(acc + g1) : T(0);
+                warp_upper_solve(l, rinv, w, x0, x1);
+                if (lane < w) z[g0] = x0;
+                if (lane + 32 < w) z[g1] = x1;
             }
         }
+        __threadfence();
         __syncthreads();
-        for (int idx = threadIdx.x; idx < w * nb; idx += blockDim.x) {
-            int k = idx / nb, r = idx % nb;
-            T sum = T(0);
-            for (int t = k; t < w; t++) sum += l[t][k] * vin[t][r];
-            z[(int64_t)(ch.col0 + k) * nb + r] = sum;
-        }
-        return;
-    }
-    load_diag(l, rinv, lnz, ch);
-    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
-    for (int r = warp; r < nb; r += blockDim.x / 32) {
-        const int64_t g0 = (int64_t)(ch.col0 + lane) * nb + r, g1 = (int64_t)(ch.col0 + lane + 32) * nb + r;
-        T x0 = lane < w ? y[g0] - __ldcg(acc + g0) : T(0);
-        T x1 = lane + 32 < w ? y[g1] - __ldcg(acc + g1) : T(0);
-        warp_upper_solve(l, rinv, w, x0, x1);
-        if (lane < w) z[g0] = x0;
-        if (lane + 32 < w) z[g1] = x1;
+        if (threadIdx.x == 0) atomicExch(done + tl.chunk, 1);
     }
 }
 
@@ -327,12 +445,10 @@ int ensure_solve(sc_numeric *h, int64_t nrhs) {
         if ((rc = up(h->d_csr_map, s->csr_map))) return rc;
         if (cudaMalloc((void **)&h->d_csr_val, std::max<size_t>(1, s->csr_col.size()) * 8) != cudaSuccess)
             return SC_ERR_OOM;
-        // solve tiles: per level, per chunk, row tiles below the diagonal block
+        // solve tiles in level order: per chunk, row tiles below the diagonal block
         std::vector<TrsmTile> tiles;
         std::vector<int32_t> ntiles(s->chunks.size(), 0);
         for (size_t lv = 0; lv < s->levels.size(); lv++) {
-            LevelPlan &p = h->plans[lv];
-            p.sv_off = (int32_t)tiles.size();
             for (int32_t c : s->levels[lv].chunks) {
                 const Chunk &ch = s->chunks[c];
                 int32_t m = (int32_t)(s->gl_ptr[ch.sn + 1] - s->gl_ptr[ch.sn]);
@@ -346,19 +462,60 @@ int ensure_solve(sc_numeric *h, int64_t nrhs) {
                     ntiles[c]++;
                 }
             }
-            p.sv_cnt = (int32_t)tiles.size() - p.sv_off;
         }
+        // per tile the distinct chunks its rows fall in (glbind is ascending and
+        // chunk_of_col monotone, so a change of chunk along the rows starts a new
+        // one); per chunk the number of tiles whose rows fall in it
+        std::vector<int32_t> dep_ptr(tiles.size() + 1, 0), dep, need(s->chunks.size(), 0);
+        for (size_t t = 0; t < tiles.size(); t++) {
+            const Chunk &ch = s->chunks[tiles[t].chunk];
+            const int64_t gl = s->gl_ptr[ch.sn];
+            const int32_t m = (int32_t)(s->gl_ptr[ch.sn + 1] - gl);
+            int32_t prev = -1;
+            for (int32_t r = tiles[t].r0; r < std::min(m, tiles[t].r0 + kSolveRows); r++) {
+                int32_t c = s->chunk_of_col[s->glbind[gl + r]];
+                if (c != prev) {
+                    dep.push_back(c);
+                    need[c]++;
+                    prev = c;
+                }
+            }
+            dep_ptr[t + 1] = (int32_t)dep.size();
+        }
+        h->solve_tiles = (int32_t)tiles.size();
         if ((rc = up(h->d_solve_tiles, tiles))) return rc;
-        // counters [nchunks] followed by tile counts [nchunks]
+        if ((rc = up(h->d_dep_ptr, dep_ptr))) return rc;
+        if ((rc = up(h->d_dep, dep))) return rc;
+        // constants: tile counts [nchunks], then expected forward arrivals [nchunks]
         std::vector<int32_t> cnt2(2 * s->chunks.size(), 0);
-        std::copy(ntiles.begin(), ntiles.end(), cnt2.begin() + s->chunks.size());
+        std::copy(ntiles.begin(), ntiles.end(), cnt2.begin());
+        std::copy(need.begin(), need.end(), cnt2.begin() + s->chunks.size());
         if ((rc = up(h->d_counters, cnt2))) return rc;
+        // per-sweep synchronisation words, zeroed before every right-hand-side block:
+        // arrivals, backward counters, done flags [nchunks each], two work counters
+        if (cudaMalloc((void **)&h->d_sync, (3 * s->chunks.size() + 2) * sizeof(int32_t)) != cudaSuccess)
+            return SC_ERR_OOM;
+        if (cudaMalloc((void **)&h->d_serr, sizeof(int32_t)) != cudaSuccess) return SC_ERR_OOM;
         if (cudaMalloc((void **)&h->d_red, 4096 * sizeof(double)) != cudaSuccess) return SC_ERR_OOM;
         if (cudaFuncSetAttribute(k_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, solve_smem<double>()) ||
             cudaFuncSetAttribute(k_bwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, solve_smem<double>()) ||
             cudaFuncSetAttribute(k_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, solve_smem<float>()) ||
             cudaFuncSetAttribute(k_bwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, solve_smem<float>()))
             return SC_ERR_CUDA;
+        // persistent sweeps: as many CTAs as fit on the device at once
+        int per_sm = 1;
+        if (h->elt == 8) {
+            int a = 1, b = 1;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_fwd<double>, 256, solve_smem<double>());
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bwd<double>, 256, solve_smem<double>());
+            per_sm = std::max(1, std::min(a, b));
+        } else {
+            int a = 1, b = 1;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_fwd<float>, 256, solve_smem<float>());
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bwd<float>, 256, solve_smem<float>());
+            per_sm = std::max(1, std::min(a, b));
+        }
+        h->solve_grid = std::max(1, std::min<int>(h->solve_tiles, per_sm * h->num_sms));
         h->solve_ready = true;
     }
     if (nrhs > h->solve_cap) {
@@ -399,26 +556,19 @@ int tri_solve(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, double 
         int nb = (int)std::min<int64_t>(kRhsBlk, nrhs - r0);
         unsigned g = (unsigned)((n * nb + 255) / 256);
         k_perm_in<T><<<g, 256, 0, st>>>(xw, B, ldb, h->d_perm, n, nb, (int)r0);
-        launches += 2;
-        for (size_t lv = 0; lv < h->plans.size(); lv++) {
-            const LevelPlan &p = h->plans[lv];
-            if (p.sv_cnt) {
-                k_fwd<T><<<p.sv_cnt, 256, solve_smem<T>(), st>>>(lnz, h->d_chunks, h->d_solve_tiles + p.sv_off,
-                                                                 h->d_glbind, xw, y, nb, (const float *)h->d_inv);
-                launches++;
-            }
-        }
+        SC_CUDA(cudaMemsetAsync(h->d_sync, 0, (3 * nch + 2) * sizeof(int32_t), st));
         SC_CUDA(cudaMemsetAsync(acc, 0, (size_t)n * nb * sizeof(T), st));
-        SC_CUDA(cudaMemsetAsync(h->d_counters, 0, nch * sizeof(int32_t), st));
-        for (size_t lv = h->plans.size(); lv-- > 0;) {
-            const LevelPlan &p = h->plans[lv];
-            if (p.sv_cnt) {
-                k_bwd<T><<<p.sv_cnt, 256, solve_smem<T>(), st>>>(lnz, h->d_chunks, h->d_solve_tiles + p.sv_off,
-                                                                 h->d_glbind, y, z, acc, h->d_counters,
-                                                                 h->d_counters + nch, nb, (const float *)h->d_inv);
-                launches++;
-            }
-        }
+        int32_t *arrive = h->d_sync, *cnt = h->d_sync + nch, *done = h->d_sync + 2 * nch, *work = h->d_sync + 3 * nch;
+        const long long spin = (long long)s->opt.spin_limit;
+        k_fwd<T><<<h->solve_grid, 256, solve_smem<T>(), st>>>(lnz, h->d_chunks, h->d_solve_tiles, h->solve_tiles,
+                                                              h->d_dep_ptr, h->d_dep, h->d_counters + nch, h->d_glbind,
+                                                              xw, y, nb, (const float *)h->d_inv, arrive, work,
+                                                              h->d_serr, spin);
+        k_bwd<T><<<h->solve_grid, 256, solve_smem<T>(), st>>>(lnz, h->d_chunks, h->d_solve_tiles, h->solve_tiles,
+                                                              h->d_dep_ptr, h->d_dep, h->d_counters, h->d_glbind, y, z,
+                                                              acc, nb, (const float *)h->d_inv, cnt, done, work + 1,
+                                                              h->d_serr, spin);
+        launches += 4;
         k_perm_out<T><<<g, 256, 0, st>>>(X, ldx, z, h->d_perm, n, nb, (int)r0, add);
     }
     SC_CUDA(cudaGetLastError());
@@ -484,8 +634,11 @@ int run_step(sc_numeric *h, int64_t nrhs, int step, cudaStream_t st, int &launch
 // eta per column from the maxima of the last residual
 int read_eta(sc_numeric *h, int64_t nrhs, cudaStream_t st, std::vector<double> &eta) {
     std::vector<double> red(3 * nrhs);
+    int32_t werr = 0;
     SC_CUDA(cudaMemcpyAsync(red.data(), h->d_red, red.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SC_CUDA(cudaMemcpyAsync(&werr, h->d_serr, sizeof(werr), cudaMemcpyDeviceToHost, st));
     SC_CUDA(cudaStreamSynchronize(st));
+    if (werr) return SC_ERR_TIMEOUT;
     eta.resize(nrhs);
     for (int64_t c = 0; c < nrhs; c++) {
         double den = h->anorm * red[3 * c + 1] + red[3 * c + 2];
@@ -497,6 +650,33 @@ int read_eta(sc_numeric *h, int64_t nrhs, cudaStream_t st, std::vector<double> &
 }  // namespace
 
 int numeric_solve(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, double *X, int64_t ldx, int on_device,
+                  cudaStream_t st, sc_solve_info *info);
+
+namespace {
+// Test hook: one solve in which the forward sweep expects one arrival more at
+// chunk h->stall_chunk than it will receive, so that chunk's bounded waits give
+// up and the solve returns SC_ERR_TIMEOUT. The expected count is restored and
+// the hook cleared afterwards.
+int solve_with_stall(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, double *X, int64_t ldx, int on_device,
+                     cudaStream_t st, sc_solve_info *info) {
+    const int32_t c = h->stall_chunk;
+    h->stall_chunk = -1;
+    const size_t nch = h->sym->chunks.size();
+    if (c >= (int32_t)nch) return -1;
+    int rc0 = ensure_solve(h, nrhs);
+    if (rc0) return rc0;
+    int32_t *slot = h->d_counters + nch + c, need = 0;
+    SC_CUDA(cudaMemcpy(&need, slot, sizeof(need), cudaMemcpyDeviceToHost));
+    const int32_t raised = need + 1;
+    SC_CUDA(cudaMemcpy(slot, &raised, sizeof(raised), cudaMemcpyHostToDevice));
+    int rc = numeric_solve(h, nrhs, B, ldb, X, ldx, on_device, st, info);
+    cudaStreamSynchronize(st);
+    if (cudaMemcpy(slot, &need, sizeof(need), cudaMemcpyHostToDevice) != cudaSuccess) return SC_ERR_CUDA;
+    return rc;
+}
+}  // namespace
+
+int numeric_solve(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, double *X, int64_t ldx, int on_device,
                   cudaStream_t st, sc_solve_info *info) {
     const sc_symbolic *s = h->sym;
     const int64_t n = s->n;
@@ -504,9 +684,17 @@ int numeric_solve(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, dou
     if (rc) return rc;
     h->last_stream = st;
     if (nrhs > 1365) return -2;  // the reduction buffer holds 3 values per column (+ ||A||)
-    cudaEvent_t e0, e1;
-    SC_CUDA(cudaEventCreate(&e0));
-    SC_CUDA(cudaEventCreate(&e1));
+    if (h->stall_chunk >= 0) return solve_with_stall(h, nrhs, B, ldb, X, ldx, on_device, st, info);
+    struct Events {  // destroyed on every return path
+        cudaEvent_t e[2] = {nullptr, nullptr};
+        ~Events() {
+            for (cudaEvent_t x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } ev;
+    SC_CUDA(cudaEventCreate(&ev.e[0]));
+    SC_CUDA(cudaEventCreate(&ev.e[1]));
+    cudaEvent_t e0 = ev.e[0], e1 = ev.e[1];
     SC_CUDA(cudaEventRecord(e0, st));
     // b (column-major, ld = n) on the device
     for (int64_t c = 0; c < nrhs; c++)
@@ -518,6 +706,7 @@ int numeric_solve(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, dou
     SC_CUDA(cudaMemsetAsync(h->d_red + 4095, 0, sizeof(double), st));
     k_anorm<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(h->d_csr_ptr, h->d_csr_val, n, h->d_red + 4095);
     SC_CUDA(cudaMemcpyAsync(&h->anorm, h->d_red + 4095, sizeof(double), cudaMemcpyDeviceToHost, st));
+    SC_CUDA(cudaMemsetAsync(h->d_serr, 0, sizeof(int32_t), st));
     int launches = 2;
     // x0 = solve(b), then its residual
     if ((rc = run_step(h, nrhs, 0, st, launches))) return rc;
@@ -557,8 +746,6 @@ int numeric_solve(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, dou
     SC_CUDA(cudaStreamSynchronize(st));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     bool conv = best <= tol;
     if (info) {
         info->iterations = it;

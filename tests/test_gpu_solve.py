@@ -1,0 +1,58 @@
+"""Solve sweeps on the GPU (needs a GB300): the bounded waits of the persistent
+forward / backward sweeps.
+
+Each sweep is one launch whose CTAs wait on per-chunk counters. Every wait is
+bounded: after spin_limit polls it sets an error word, every other wait sees
+the word and stops, and sc_solve returns SC_ERR_TIMEOUT. The test makes one
+chunk expect an arrival that never comes (sc_test_stall_solve), checks the
+status, and then checks that the same handle solves correctly again, i.e. the
+CUDA context survived and the expected count was restored.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2409_13090_gb300 as sc
+from paper_2409_13090_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    sc.build()
+    oracle.build()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("where", ["root", "leaf"])
+def test_stalled_chunk_times_out_and_handle_recovers(prec, where):
+    A = inputs.diffusion_3d_7pt(13, 11, 9, seed=5, shift=1e-2)
+    sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid, spin_limit=1 << 16)
+    num = sym.factor(A.values, precision=prec)
+    assert num.rc == 0
+    B = inputs.rhs(A.n, 3, 11)
+    X0, info0 = num.solve(B)
+    assert oracle.backward_error(A, B, X0).max() <= 1e-14
+    nchunks = sym.plan_stats(prec)["chunks"]
+    num.stall_next_solve(nchunks - 1 if where == "root" else 0)
+    with pytest.raises(sc.SCError) as e:
+        num.solve(B)
+    assert e.value.code == sc.SC_ERR_TIMEOUT
+    X1, info1 = num.solve(B)
+    assert oracle.backward_error(A, B, X1).max() <= 1e-14
+    assert np.abs(X1 - X0).max() <= 1e-10 * np.abs(X0).max()
+
+
+def test_many_right_hand_sides_several_blocks():
+    """40 right-hand sides: three blocks of the sweep (16 + 16 + 8), each with
+    freshly zeroed counters."""
+    A = inputs.workload(2, 0.25)[0]
+    sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid)
+    num = sym.factor(A.values, precision="fp64")
+    B = inputs.rhs(A.n, 40, 12)
+    X, info = num.solve(B)
+    assert oracle.backward_error(A, B, X).max() <= 1e-14
