@@ -24,10 +24,13 @@ struct TrsmTile {
     int32_t chunk, r0;
 };
 
-// One output tile of a product task.
+// One output tile of a product task. ks < 0: the whole inner dimension;
+// ks >= 0: only its slice [ks * kSplitK, (ks + 1) * kSplitK), added atomically
+// (SIMT tiles of tasks with few tiles and a long inner dimension).
 struct GemmTile {
-    int32_t task, tm, tn, pad;
+    int32_t task, tm, tn, ks;
 };
+constexpr int kSplitK = 256;
 
 constexpr int kMaxChunk = 64;
 

@@ -49,10 +49,15 @@ double task_flops(const Task &t) {
 
 void tiles_of(const Task &t, int32_t id, std::vector<GemmTile> &out) {
     int tm = (t.m + kBM - 1) / kBM, tn = (t.n + kBN - 1) / kBN;
+    // a task of few tiles with a long inner dimension is split along it, so its
+    // tiles do not serialise a level (an RL update matrix is stored, not added:
+    // never split)
+    const int slices = (tm * tn <= 8 && t.k > 2 * kSplitK && !(t.flags & kTaskStoreU)) ? (t.k + kSplitK - 1) / kSplitK : 0;
     for (int i = 0; i < tm; i++)
         for (int j = 0; j < tn; j++) {
             if ((t.flags & kTaskLower) && (i * kBM + kBM - 1) < j * kBN) continue;  // above the diagonal
-            out.push_back(GemmTile{id, i, j, 0});
+            if (!slices) out.push_back(GemmTile{id, i, j, -1});
+            for (int q = 0; q < slices; q++) out.push_back(GemmTile{id, i, j, q});
         }
 }
 

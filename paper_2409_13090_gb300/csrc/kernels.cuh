@@ -22,55 +22,80 @@ __global__ void k_scatter_values(T *__restrict__ lnz, const int64_t *__restrict_
 
 // --------------------------------------------------------------------- K1
 // POTRF of each chunk's w x w diagonal block (lower) in shared memory,
-// right-looking by panels of 8 columns: one warp factors a panel column by
-// column (pivot, reciprocal, scale, update of the panel's later columns) with
-// warp-level synchronisation, then all 256 threads apply the panel's rank-8
-// update to the trailing triangle.
+// right-looking by panels of 8 columns. Per panel:
+//   1. warp 0 factors the panel's 8 x 8 diagonal block in registers (lane i
+//      holds row i; pivots and column entries are broadcast by shuffles);
+//   2. every row below it is solved against that block, one thread per row
+//      (x <- x L_d^{-T}, reciprocal pivots);
+//   3. all 256 threads apply the panel's rank-8 update to the trailing triangle.
 //   T = double: one pass in FP64; a pivot d <= 0 sets info.
 //   T = float : one pass in FP32. If some pivot d (before the square root)
 //               is <= tau * |A_jj| (A_jj = the diagonal entry of the input
 //               matrix), the block is refactored in FP64 from the same stored
 //               values and low_pivots is incremented; a pivot <= 0 in that
 //               pass sets info.
-// info receives the minimum failing column (1-based, final ordering). dk[k] =
-// |A_jj| of the block's column k, staged in shared memory.
+// info receives the minimum failing column (1-based, final ordering). thr[k] =
+// tau * |A_jj| of the block's column k, staged in shared memory.
 template <typename S>
-__device__ bool potrf_pass(S (*a)[kMaxChunk + 1], int w, const double *dk, int col0, double tau, bool check_low,
+__device__ bool potrf_pass(S (*a)[kMaxChunk + 1], int w, const double *thr, int col0, bool check_low,
                            int32_t *__restrict__ info, int *flag) {
+    constexpr int PW = 8;  // panel width
+    __shared__ S rpiv[PW];
     const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // 16 x 16 threads
-    constexpr int PW = 8;                                    // panel width
     for (int p0 = 0; p0 < w; p0 += PW) {
-        const int p1 = min(p0 + PW, w);
+        const int pw = min(PW, w - p0), p1 = p0 + pw;
         if (warp == 0) {
-            // panel p0..p1-1: columns one by one, warp-synchronous
-            for (int k = p0; k < p1; k++) {
-                S d = a[k][k];
-                if (check_low) {
-                    if (!((double)d > tau * dk[k])) {  // the same value in every lane
-                        if (lane == 0) *flag = 1;
-                        break;
+            S r[PW];
+#pragma unroll
+            for (int j = 0; j < PW; j++) r[j] = (lane < pw && j <= lane) ? a[p0 + lane][p0 + j] : S(0);
+            bool low = false;
+#pragma unroll
+            for (int k = 0; k < PW; k++) {
+                if (k < pw) {
+                    S d = __shfl_sync(0xffffffffu, r[k], k);  // the same value in every lane
+                    if (check_low) {
+                        if (!((double)d > thr[p0 + k])) low = true;
+                    } else if (!(d > S(0))) {
+                        if (lane == 0) atomicMin(info, col0 + p0 + k + 1);
                     }
-                } else if (!(d > S(0))) {
-                    if (lane == 0) atomicMin(info, col0 + k + 1);
-                    d = S(1);
+                    if (!(d > S(0))) d = S(1);
+                    const S sq = sqrt(d), rk = S(1) / sq;
+                    if (lane == k) r[k] = sq;
+                    else if (lane > k) r[k] *= rk;
+                    if (lane == 0) rpiv[k] = rk;
+#pragma unroll
+                    for (int j = k + 1; j < PW; j++) {
+                        const S ljk = __shfl_sync(0xffffffffu, r[k], j);
+                        if (lane >= j) r[j] -= r[k] * ljk;
+                    }
                 }
-                if (!(d > S(0))) d = S(1);
-                const S r = sqrt(d), rk = S(1) / r;
-                __syncwarp();
-                if (lane == 0) a[k][k] = r;
-                for (int i = k + 1 + lane; i < w; i += 32) a[i][k] *= rk;
-                __syncwarp();
-                for (int i = k + 1 + lane; i < w; i += 32) {
-                    const S aik = a[i][k];
-                    const int jend = min(p1 - 1, i);
-                    for (int j = k + 1; j <= jend; j++) a[i][j] -= aik * a[j][k];
-                }
-                __syncwarp();
             }
+            if (lane < pw) {
+#pragma unroll
+                for (int j = 0; j < PW; j++)
+                    if (j <= lane) a[p0 + lane][p0 + j] = r[j];
+            }
+            if (lane == 0 && low) *flag = 1;
         }
         __syncthreads();
         if (check_low && *flag) return false;
+        // rows below the diagonal block: x <- x L_d^{-T}
+        for (int i = p1 + threadIdx.x; i < w; i += blockDim.x) {
+            S x[PW];
+#pragma unroll
+            for (int j = 0; j < PW; j++) x[j] = j < pw ? a[i][p0 + j] : S(0);
+#pragma unroll
+            for (int k = 0; k < PW; k++) {
+                x[k] *= rpiv[k];
+#pragma unroll
+                for (int j = k + 1; j < PW; j++) x[j] -= x[k] * a[p0 + j][p0 + k];
+            }
+#pragma unroll
+            for (int j = 0; j < PW; j++)
+                if (j < pw) a[i][p0 + j] = x[j];
+        }
+        __syncthreads();
         // rank-(p1-p0) update of the trailing lower triangle
         for (int i = p1 + ty; i < w; i += 16) {
             S ai[PW];
@@ -138,17 +163,17 @@ __global__ void __launch_bounds__(256) k_potrf(T *__restrict__ lnz, const ChunkD
                                                double tau) {
     extern __shared__ double smem_potrf[];
     __shared__ int flag;
-    __shared__ double dk[kMaxChunk];
+    __shared__ double thr[kMaxChunk];
     const ChunkDev ch = chunks[list[blockIdx.x]];
     const int w = ch.w;
     T *base = lnz + ch.off + (int64_t)ch.c0 * ch.ld + ch.c0;
     if (threadIdx.x == 0) flag = 0;
-    if (threadIdx.x < w) dk[threadIdx.x] = fabs(adiag[ch.col0 + threadIdx.x]);
+    if (threadIdx.x < w) thr[threadIdx.x] = tau * fabs(adiag[ch.col0 + threadIdx.x]);
     if (sizeof(T) == 4) {
         auto a = reinterpret_cast<float (*)[kMaxChunk + 1]>(smem_potrf);
         load_block(a, base, ch.ld, w);
         __syncthreads();
-        if (potrf_pass<float>(a, w, dk, ch.col0, tau, true, info, &flag)) {
+        if (potrf_pass<float>(a, w, thr, ch.col0, true, info, &flag)) {
             for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
                 int r = idx / w, c = idx % w;
                 if (r >= c) base[(int64_t)r * ch.ld + c] = (T)a[r][c];
@@ -162,7 +187,7 @@ __global__ void __launch_bounds__(256) k_potrf(T *__restrict__ lnz, const ChunkD
     auto a = reinterpret_cast<double (*)[kMaxChunk + 1]>(smem_potrf);
     load_block(a, base, ch.ld, w);
     __syncthreads();
-    potrf_pass<double>(a, w, dk, ch.col0, tau, false, info, &flag);
+    potrf_pass<double>(a, w, thr, ch.col0, false, info, &flag);
     for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
         int r = idx / w, c = idx % w;
         if (r >= c) base[(int64_t)r * ch.ld + c] = (T)a[r][c];
@@ -236,14 +261,19 @@ __global__ void __launch_bounds__(kTrsmThreads) k_trsm(T *__restrict__ lnz, cons
 
 // --------------------------------------------------------------------- K3
 // Tiled product C -= A B^T (or C = -A B^T into an RL update matrix) on SIMT
-// FMA units. 256 threads, BM x BN tile, 4 x 4 outputs per thread. The
-// scatter into Lnz(P) is an atomic add: supernodes of one level may update the
-// same ancestor entries.
+// FMA units. 256 threads, 64 x 64 tile; warp w owns the 16 x 32 sub-tile
+// (rows 16 (w / 2), columns 32 (w % 2)) and each lane a 4 x 4 strided micro-tile
+// of it. A warp whose sub-tile lies outside m x n, or wholly above the diagonal
+// of a lower task, skips its multiply-adds (it still helps stage the operands),
+// and the last K slice runs only its valid columns, so ragged tiles do not
+// spend FMA-pipe cycles on padding. The scatter into Lnz(P) is an atomic add
+// unless the task is the only writer of its target: supernodes of one level
+// may update the same ancestor entries.
 template <typename T, int BM, int BN, int BK>
 __global__ void __launch_bounds__(256) k_gemm_tiles(T *__restrict__ lnz, T *__restrict__ pool,
                                                     const Task *__restrict__ tasks,
                                                     const GemmTile *__restrict__ tiles) {
-    static_assert(BM == 64 && BN == 64, "4x4 per thread over 16x16 threads");
+    static_assert(BM == 64 && BN == 64, "8 warps of 16 x 32 sub-tiles");
     __shared__ T As[BK][BM + 1];
     __shared__ T Bs[BK][BN + 1];
     const GemmTile tl = tiles[blockIdx.x];
@@ -251,49 +281,72 @@ __global__ void __launch_bounds__(256) k_gemm_tiles(T *__restrict__ lnz, T *__re
     const int row0 = tl.tm * BM, col0 = tl.tn * BN;
     const T *A = lnz + tk.a_off;
     const T *B = lnz + tk.b_off;
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int r0 = (warp / 2) * 16 + lane / 8;  // rows r0 + 4 i
+    const int c0 = (warp % 2) * 32 + lane % 8;  // columns c0 + 8 j
+    const bool lower = tk.flags & kTaskLower;
+    // warp-uniform: does the sub-tile hold any entry that is written?
+    const int sr = row0 + (warp / 2) * 16, sc = col0 + (warp % 2) * 32;
+    const bool active = sr < tk.m && sc < tk.n && !(lower && min(sr + 15, tk.m - 1) < sc);
     T acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; i++)
 #pragma unroll
         for (int j = 0; j < 4; j++) acc[i][j] = T(0);
-    for (int k0 = 0; k0 < tk.k; k0 += BK) {
-        for (int idx = threadIdx.x; idx < BM * BK; idx += 256) {
-            int r = idx / BK, kk = idx % BK;
-            int gr = row0 + r, gk = k0 + kk;
-            As[kk][r] = (gr < tk.m && gk < tk.k) ? A[(int64_t)gr * tk.lds + gk] : T(0);
+    const bool split = tl.ks >= 0;
+    const int kb = split ? tl.ks * kSplitK : 0, ke = split ? min(tk.k, kb + kSplitK) : tk.k;
+    // operands of the next K slice are fetched into registers while the
+    // current one is multiplied
+    constexpr int kLd = BM * BK / 256;
+    T pa[kLd], pb[kLd];
+    auto fetch = [&](int k0) {
+#pragma unroll
+        for (int it = 0; it < kLd; it++) {
+            const int idx = threadIdx.x + it * 256, r = idx / BK, gk = k0 + idx % BK;
+            pa[it] = (row0 + r < tk.m && gk < ke) ? A[(int64_t)(row0 + r) * tk.lds + gk] : T(0);
+            pb[it] = (col0 + r < tk.n && gk < ke) ? B[(int64_t)(col0 + r) * tk.lds + gk] : T(0);
         }
-        for (int idx = threadIdx.x; idx < BN * BK; idx += 256) {
-            int r = idx / BK, kk = idx % BK;
-            int gr = col0 + r, gk = k0 + kk;
-            Bs[kk][r] = (gr < tk.n && gk < tk.k) ? B[(int64_t)gr * tk.lds + gk] : T(0);
+    };
+    fetch(kb);
+    for (int k0 = kb; k0 < ke; k0 += BK) {
+#pragma unroll
+        for (int it = 0; it < kLd; it++) {
+            const int idx = threadIdx.x + it * 256;
+            As[idx % BK][idx / BK] = pa[it];
+            Bs[idx % BK][idx / BK] = pb[it];
         }
         __syncthreads();
+        if (k0 + BK < ke) fetch(k0 + BK);
+        if (active) {
+            const int kn = min(BK, ke - k0);
 #pragma unroll
-        for (int kk = 0; kk < BK; kk++) {
-            T a[4], b[4];
+            for (int kk = 0; kk < BK; kk++) {
+                if (kk < kn) {
+                    T a[4], b[4];
 #pragma unroll
-            for (int i = 0; i < 4; i++) a[i] = As[kk][ty + 16 * i];
+                    for (int i = 0; i < 4; i++) a[i] = As[kk][r0 + 4 * i];
 #pragma unroll
-            for (int j = 0; j < 4; j++) b[j] = Bs[kk][tx + 16 * j];
+                    for (int j = 0; j < 4; j++) b[j] = Bs[kk][c0 + 8 * j];
 #pragma unroll
-            for (int i = 0; i < 4; i++)
+                    for (int i = 0; i < 4; i++)
 #pragma unroll
-                for (int j = 0; j < 4; j++) acc[i][j] += a[i] * b[j];
+                        for (int j = 0; j < 4; j++) acc[i][j] += a[i] * b[j];
+                }
+            }
         }
         __syncthreads();
     }
-    const bool lower = tk.flags & kTaskLower;
+    if (!active) return;
     const bool store = tk.flags & kTaskStoreU;
-    const bool excl = tk.flags & kTaskExclusive;
+    const bool excl = (tk.flags & kTaskExclusive) && !split;
     T *C = (store ? pool : lnz) + tk.c_off;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
-        int gi = row0 + ty + 16 * i;
+        int gi = row0 + r0 + 4 * i;
         if (gi >= tk.m) continue;
 #pragma unroll
         for (int j = 0; j < 4; j++) {
-            int gj = col0 + tx + 16 * j;
+            int gj = col0 + c0 + 8 * j;
             if (gj >= tk.n || (lower && gj > gi)) continue;
             T *c = C + (int64_t)gi * tk.ldc + gj;
             if (store) *c = -acc[i][j];

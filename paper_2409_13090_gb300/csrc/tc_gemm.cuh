@@ -321,7 +321,7 @@ inline void tc_tiles_of(const Task &t, int32_t id, int bn, std::vector<GemmTile>
     for (int i = 0; i < tm; i++)
         for (int j = 0; j < tn; j++) {
             if ((t.flags & kTaskLower) && (i * tc::BM + tc::BM - 1) < j * bn) continue;
-            out.push_back(GemmTile{id, i, j, 0});
+            out.push_back(GemmTile{id, i, j, -1});
         }
 }
 
