@@ -34,6 +34,14 @@ WORKLOAD = "diffusion3d_7pt_varcoef_48^3"
 SAMPLE_SIDE = 32  # oracle sample: the same generator on a 32^3 grid
 
 
+# DRAM bytes (read + write) of every launch of a kernel class in one
+# factorization, measured with ncu on the current kernel code (recorded with
+# its command in profiles/k_gemm_tiles_fp64_diffusion48.md). Key: (class,
+# precision, workload, scale, merge). Classes without a capture of the current
+# code report null.
+TRAFFIC = {("gemm_simt", "fp64", 2, 1.0, 0.125): 2173629184}
+
+
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -272,7 +280,10 @@ def main():
         peak = fp_peak["fp64" if args.precision == "fp64" else "fp32"]
         bound, pk = "alu", "measured FMA-chain probe (sc_probe_fma_peak)"
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if peak else None, "traffic": None, "kernel": dom,
+                "frac": (achieved / peak) if peak else None,
+                "traffic": TRAFFIC.get((dom, args.precision, args.workload, args.scale, args.merge)),
+                "traffic_scope": "DRAM bytes of all launches of the class in one factorization (ncu)",
+                "kernel": dom,
                 "kernel_launches": d["launches"], "peak_source": pk,
                 "profile": {k: {"ms": round(v["ms"], 4), "gflop": round(v["flops"] / 1e9, 3),
                                 "launches": v["launches"]} for k, v in prof.items()},
