@@ -61,9 +61,15 @@ enum sc_variant { SC_RLB = 0, SC_RL = 1 };
  *   SC_FP32  factor stored and computed in FP32 (SIMT FMA);
  *   SC_TF32  factor stored in FP32, large update products on the TF32 tensor
  *            cores with FP32 accumulation.
- * With SC_FP32 / SC_TF32 the solve refines in FP64 (residual r = b - A x and
- * the update x += d in FP64) until the backward error reaches ir_tol. */
-enum sc_precision { SC_FP64 = 0, SC_FP32 = 1, SC_TF32 = 2 };
+ *   SC_TF32X3  as SC_TF32, but each large product is formed from split
+ *            operands x = hi + lo (hi = TF32 rounding of x, lo = TF32 rounding
+ *            of x - hi) as hi*hi' + hi*lo' + lo*hi' on the tensor cores: close
+ *            to FP32 accuracy at tensor-core rate, so fewer refinement steps.
+ *            Holds two extra FP32 copies of the factor storage.
+ * With SC_FP32 / SC_TF32 / SC_TF32X3 the solve refines in FP64 (residual
+ * r = b - A x and the update x += d in FP64) until the backward error reaches
+ * ir_tol. */
+enum sc_precision { SC_FP64 = 0, SC_FP32 = 1, SC_TF32 = 2, SC_TF32X3 = 3 };
 
 typedef struct sc_options {
     int32_t ordering;          /* enum sc_ordering                                  */

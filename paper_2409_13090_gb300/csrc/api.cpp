@@ -36,7 +36,7 @@ int sc_analyze(int64_t n, const int64_t *colptr, const int32_t *rowind, const sc
     sc_options_default(&def);
     const sc_options &opt = o ? *o : def;
     if (opt.variant != SC_RLB && opt.variant != SC_RL) return -4;
-    if (opt.precision < SC_FP64 || opt.precision > SC_TF32) return -4;
+    if (opt.precision < SC_FP64 || opt.precision > SC_TF32X3) return -4;
     if (opt.chunk < 1 || opt.chunk > 64) return -4;
     if (!(opt.merge_frac >= 0.0)) return -4;
     try {
@@ -92,7 +92,7 @@ int sc_factor(sc_symbolic *s, const double *values, int values_on_device, int pr
     if (!values) return -2;
     if (values_on_device != 0 && values_on_device != 1) return -3;
     if (precision == -1) precision = s->opt.precision;
-    if (precision < SC_FP64 || precision > SC_TF32) return -4;
+    if (precision < SC_FP64 || precision > SC_TF32X3) return -4;
     if (!out) return -6;
     *out = nullptr;
     sc_numeric *h = nullptr;
@@ -154,7 +154,7 @@ int sc_factor_profile(sc_numeric *h, const double *values, int values_on_device,
 
 int sc_plan_stats(const sc_symbolic *s, int precision, int64_t *out, int nout) {
     if (!s) return -1;
-    if (precision < SC_FP64 || precision > SC_TF32) return -2;
+    if (precision < SC_FP64 || precision > SC_TF32X3) return -2;
     if (!out) return -3;
     return sc::plan_stats(s, precision, out, nout);
 }

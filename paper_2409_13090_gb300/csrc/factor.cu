@@ -122,13 +122,14 @@ int run_levels(sc_numeric *h, cudaStream_t st, Prof *prof = nullptr, cudaStream_
         if (p.potrf_cnt) {
             B(kProfPotrf);
             k_potrf<T><<<p.potrf_cnt, 256, kPotrfSmem, st>>>(lnz, h->d_chunks, h->d_potrf + p.potrf_off, h->d_adiag,
-                                                              h->d_info, h->d_info + 1, tau);
+                                                              h->d_info, h->d_info + 1, tau, h->d_hi, h->d_lo);
             E();
             launches++;
         }
         if (p.trsm_cnt) {
             B(kProfTrsm);
-            k_trsm<T><<<p.trsm_cnt, kTrsmThreads, 0, st>>>(lnz, h->d_chunks, h->d_trsm + p.trsm_off);
+            k_trsm<T><<<p.trsm_cnt, kTrsmThreads, 0, st>>>(lnz, h->d_chunks, h->d_trsm + p.trsm_off, h->d_hi,
+                                                           h->d_lo);
             E();
             launches++;
         }
@@ -156,15 +157,17 @@ int run_levels(sc_numeric *h, cudaStream_t st, Prof *prof = nullptr, cudaStream_
         if constexpr (sizeof(T) == 4) {
             if (p.tc_cnt) {
                 B(kProfTc);
-                launch_tc_gemm(128, (float *)lnz, h->d_tasks, h->d_gemm + p.tc_off, p.tc_cnt, h->d_tmaps,
-                               h->d_tmap_of_sn, h->d_err, (long long)s->opt.spin_limit, h->num_sms, st);
+                launch_tc_gemm(128, h->precision == SC_TF32X3, (float *)lnz, h->d_tasks, h->d_gemm + p.tc_off,
+                               p.tc_cnt, h->d_tmaps, h->nmaps, h->d_tmap_of_sn, h->d_err,
+                               (long long)s->opt.spin_limit, h->num_sms, st);
                 E();
                 launches++;
             }
             if (p.tc64_cnt) {
                 B(kProfTc);
-                launch_tc_gemm(64, (float *)lnz, h->d_tasks, h->d_gemm + p.tc64_off, p.tc64_cnt, h->d_tmaps,
-                               h->d_tmap_of_sn, h->d_err, (long long)s->opt.spin_limit, h->num_sms, st);
+                launch_tc_gemm(64, h->precision == SC_TF32X3, (float *)lnz, h->d_tasks, h->d_gemm + p.tc64_off,
+                               p.tc64_cnt, h->d_tmaps, h->nmaps, h->d_tmap_of_sn, h->d_err,
+                               (long long)s->opt.spin_limit, h->num_sms, st);
                 E();
                 launches++;
             }
@@ -251,7 +254,7 @@ void build_plan(const sc_symbolic *s, int precision, Plan &P) {
         inv += (int64_t)ch.w * ch.w;
     }
     P.inv_size = inv;
-    const bool tc = precision == SC_TF32;
+    const bool tc = precision == SC_TF32 || precision == SC_TF32X3;
     std::vector<int32_t> tmap_of_sn(s->nsuper, -1);
     {
         int32_t nm = 0;
@@ -357,7 +360,7 @@ int plan_stats(const sc_symbolic *s, int precision, int64_t *out, int nout) {
 }
 
 int numeric_create(sc_symbolic *s, int precision, sc_numeric **out) {
-    if (precision < SC_FP64 || precision > SC_TF32) return -3;
+    if (precision < SC_FP64 || precision > SC_TF32X3) return -3;
     int rc = set_smem_attrs();
     if (rc) return rc;
     auto h = new sc_numeric();
@@ -392,10 +395,25 @@ int numeric_create(sc_symbolic *s, int precision, sc_numeric **out) {
     if (cudaMalloc((void **)&h->d_adiag, (size_t)s->n * sizeof(double)) != cudaSuccess) return fail(SC_ERR_OOM);
     if (cudaMalloc((void **)&h->d_info, 2 * sizeof(int32_t)) != cudaSuccess) return fail(SC_ERR_OOM);
     if (cudaMalloc((void **)&h->d_err, sizeof(int32_t)) != cudaSuccess) return fail(SC_ERR_OOM);
-    if (precision == SC_TF32) {
-        std::vector<CUtensorMap> maps;
+    if (precision == SC_TF32X3) {
+        // split copies of the factor: zero once, so padding columns stay zero
+        for (float **p : {&h->d_hi, &h->d_lo}) {
+            if (cudaMalloc((void **)p, (size_t)s->lnz_size * sizeof(float)) != cudaSuccess) return fail(SC_ERR_OOM);
+            if (cudaMemset(*p, 0, (size_t)s->lnz_size * sizeof(float)) != cudaSuccess) return fail(SC_ERR_CUDA);
+            bytes += s->lnz_size * 4;
+        }
+    }
+    if (precision == SC_TF32 || precision == SC_TF32X3) {
+        // TF32: maps over the factor; TF32x3: maps over hi, then maps over lo
+        std::vector<CUtensorMap> maps, maps_lo;
         std::vector<int32_t> tmap_of_sn;
-        if ((rc = tc_encode_maps(s, (float *)h->d_lnz, maps, tmap_of_sn))) return fail(rc);
+        if ((rc = tc_encode_maps(s, precision == SC_TF32 ? (float *)h->d_lnz : h->d_hi, maps, tmap_of_sn)))
+            return fail(rc);
+        h->nmaps = (int32_t)(maps.size() / 2);
+        if (precision == SC_TF32X3) {
+            if ((rc = tc_encode_maps(s, h->d_lo, maps_lo, tmap_of_sn))) return fail(rc);
+            maps.insert(maps.end(), maps_lo.begin(), maps_lo.end());
+        }
         if ((rc = upload(h->d_tmaps, maps, bytes))) return fail(rc);
         if ((rc = upload(h->d_tmap_of_sn, tmap_of_sn, bytes))) return fail(rc);
     }
@@ -567,7 +585,7 @@ void numeric_free(sc_numeric *h) {
                     h->d_rlrelind, h->d_glbind, h->d_perm, h->d_csr_ptr, h->d_csr_col, h->d_csr_val,
                     h->d_csr_map, h->d_counters, h->d_xw, h->d_solve_tiles, h->d_sn, h->d_blk, h->d_rbval,
                     h->d_loops, h->d_tmaps, h->d_tmap_of_sn, h->d_err, h->d_inv, h->d_x, h->d_r, h->d_b, h->d_xbest, h->d_y, h->d_z, h->d_acc, h->d_red,
-                    h->d_dep_ptr, h->d_dep, h->d_sync, h->d_serr};
+                    h->d_dep_ptr, h->d_dep, h->d_sync, h->d_serr, h->d_hi, h->d_lo};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->sym) h->sym->refs--;

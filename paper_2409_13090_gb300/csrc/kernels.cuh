@@ -11,6 +11,22 @@ namespace sc {
 
 
 
+// TF32 rounding (round to nearest, ties away from zero; the low 13 mantissa
+// bits of the result are zero).
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+// Split of a final factor entry for the three-product TF32 form: hi = tf32(x),
+// lo = tf32(x - hi) (x - hi is exact in FP32), written at the same element
+// offset of the hi and lo copies of the factor storage.
+__device__ __forceinline__ void store_split(float *__restrict__ hi, float *__restrict__ lo, int64_t e, float x) {
+    const float h = tf32_rna(x);
+    hi[e] = h;
+    lo[e] = tf32_rna(x - h);
+}
+
 // --------------------------------------------------------------------- K0
 template <typename T>
 __global__ void k_scatter_values(T *__restrict__ lnz, const int64_t *__restrict__ valmap,
@@ -160,7 +176,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_potrf(T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
                                                const int32_t *__restrict__ list, const double *__restrict__ adiag,
                                                int32_t *__restrict__ info, int32_t *__restrict__ low_pivots,
-                                               double tau) {
+                                               double tau, float *__restrict__ hi, float *__restrict__ lo) {
     extern __shared__ double smem_potrf[];
     __shared__ int flag;
     __shared__ double thr[kMaxChunk];
@@ -176,7 +192,10 @@ __global__ void __launch_bounds__(256) k_potrf(T *__restrict__ lnz, const ChunkD
         if (potrf_pass<float>(a, w, thr, ch.col0, true, info, &flag)) {
             for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
                 int r = idx / w, c = idx % w;
-                if (r >= c) base[(int64_t)r * ch.ld + c] = (T)a[r][c];
+                if (r >= c) {
+                    base[(int64_t)r * ch.ld + c] = (T)a[r][c];
+                    if (hi) store_split(hi, lo, (base - lnz) + (int64_t)r * ch.ld + c, a[r][c]);
+                }
             }
             return;
         }
@@ -190,7 +209,10 @@ __global__ void __launch_bounds__(256) k_potrf(T *__restrict__ lnz, const ChunkD
     potrf_pass<double>(a, w, thr, ch.col0, false, info, &flag);
     for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
         int r = idx / w, c = idx % w;
-        if (r >= c) base[(int64_t)r * ch.ld + c] = (T)a[r][c];
+        if (r >= c) {
+            base[(int64_t)r * ch.ld + c] = (T)a[r][c];
+            if (sizeof(T) == 4 && hi) store_split(hi, lo, (base - lnz) + (int64_t)r * ch.ld + c, (float)a[r][c]);
+        }
     }
 }
 
@@ -205,7 +227,8 @@ constexpr int kTrsmRows = 32;
 constexpr int kTrsmThreads = kTrsmRows * 4;
 template <typename T>
 __global__ void __launch_bounds__(kTrsmThreads) k_trsm(T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
-                                                       const TrsmTile *__restrict__ tiles) {
+                                                       const TrsmTile *__restrict__ tiles, float *__restrict__ hi,
+                                                       float *__restrict__ lo) {
     __shared__ T l[kMaxChunk][kMaxChunk + 1];
     __shared__ T rinv[kMaxChunk];
     const TrsmTile tl = tiles[blockIdx.x];
@@ -254,7 +277,10 @@ __global__ void __launch_bounds__(kTrsmThreads) k_trsm(T *__restrict__ lnz, cons
 #pragma unroll
         for (int jj = 0; jj < kMaxChunk / 4; jj++) {
             const int j = q + 4 * jj;
-            if (j < w) xr[j] = x[jj];
+            if (j < w) {
+                xr[j] = x[jj];
+                if (sizeof(T) == 4 && hi) store_split(hi, lo, (xr - lnz) + j, (float)x[jj]);
+            }
         }
     }
 }

@@ -67,6 +67,9 @@ struct sc_numeric {
     int32_t *d_tmap_of_sn = nullptr;
     int32_t *d_err = nullptr;         // nonzero after a bounded device wait gave up
     void *d_inv = nullptr;            // FP32 inverses of the chunks' diagonal blocks (FP32 / TF32 factors)
+    float *d_hi = nullptr;            // SC_TF32X3: tf32(x) of every final factor entry (same layout as Lnz)
+    float *d_lo = nullptr;            // SC_TF32X3: tf32(x - hi)
+    int32_t nmaps = 0;                // panels with tensor maps (lo maps follow hi maps for SC_TF32X3)
     int32_t *d_rlrelind = nullptr;
     // solve
     int32_t *d_glbind = nullptr;

@@ -29,19 +29,23 @@ namespace sc {
 namespace tc {
 
 constexpr int BM = 128, BK = 32;  // BK fp32 = 128 bytes = one swizzle row
-constexpr int STAGES = 4;
 constexpr int A_BYTES = BM * BK * 4;
 
 constexpr int kEpiWarps = 8;                 // two per TMEM lane quarter, each half of the columns
 constexpr int kThreads = 32 * (2 + kEpiWarps);  // producer warp, MMA warp, epilogue warps
 
-template <int BN>
+// X3: the three-product split form (SC_TF32X3): a stage holds hi and lo tiles
+// of A and B (A_hi, A_lo, B_hi, B_lo), and each K step issues hi*hi, hi*lo,
+// lo*hi into the same accumulator.
+template <int BN, bool X3>
 struct Cfg {
     static constexpr int B_BYTES = BN * BK * 4;
-    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr int NSPLIT = X3 ? 2 : 1;
+    static constexpr int STAGES = X3 ? 3 : 4;
+    static constexpr int STAGE_BYTES = NSPLIT * (A_BYTES + B_BYTES);
     static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*alignment*/ + 256 /*barriers*/;
     static constexpr int TMEM_COLS = 2 * BN;  // two accumulators
-    static constexpr int CTAS_PER_SM = BN == 64 ? 2 : 1;
+    static constexpr int CTAS_PER_SM = (BN == 64 && !X3) ? 2 : 1;
     // instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major, M = 128, N = BN
     static constexpr uint32_t IDESC =
         (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
@@ -155,12 +159,25 @@ __device__ __forceinline__ void epilogue_row(float *__restrict__ crow, const flo
     }
 }
 
-template <int BN>
-__global__ void __launch_bounds__(kThreads, Cfg<BN>::CTAS_PER_SM)
+// Shared memory of stage s: A tiles (hi, then lo for X3) of all stages first,
+// then B tiles; every tile starts on a 1024-byte boundary (the swizzle atom).
+template <int BN, bool X3>
+__device__ __forceinline__ uint32_t a_tile(const unsigned char *smem, int s, int part) {
+    return smem_u32(smem + (s * Cfg<BN, X3>::NSPLIT + part) * A_BYTES);
+}
+template <int BN, bool X3>
+__device__ __forceinline__ uint32_t b_tile(const unsigned char *smem, int s, int part) {
+    using C = Cfg<BN, X3>;
+    return smem_u32(smem + C::STAGES * C::NSPLIT * A_BYTES + (s * C::NSPLIT + part) * C::B_BYTES);
+}
+
+template <int BN, bool X3>
+__global__ void __launch_bounds__(kThreads, (Cfg<BN, X3>::CTAS_PER_SM))
     k_tc_gemm(float *__restrict__ lnz, const Task *__restrict__ tasks, const GemmTile *__restrict__ tiles, int ntiles,
-              const CUtensorMap *__restrict__ tmaps, const int32_t *__restrict__ tmap_of_sn, int32_t *__restrict__ err,
-              long long spin_limit) {
-    using C = Cfg<BN>;
+              const CUtensorMap *__restrict__ tmaps, int lo_maps, const int32_t *__restrict__ tmap_of_sn,
+              int32_t *__restrict__ err, long long spin_limit) {
+    using C = Cfg<BN, X3>;
+    constexpr int STAGES = C::STAGES;
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * C::STAGE_BYTES);
@@ -213,8 +230,12 @@ __global__ void __launch_bounds__(kThreads, Cfg<BN>::CTAS_PER_SM)
                     const uint32_t fb = smem_u32(full + s);
                     mbar_expect_tx(fb, C::STAGE_BYTES);
                     const int x = tk.kx0 + kb * BK;
-                    tma_load_2d(smem_u32(smem + s * A_BYTES), amap, x, ay, fb);
-                    tma_load_2d(smem_u32(smem + STAGES * A_BYTES + s * C::B_BYTES), bmap, x, by, fb);
+                    tma_load_2d(a_tile<BN, X3>(smem, s, 0), amap, x, ay, fb);
+                    tma_load_2d(b_tile<BN, X3>(smem, s, 0), bmap, x, by, fb);
+                    if constexpr (X3) {
+                        tma_load_2d(a_tile<BN, X3>(smem, s, 1), amap + 2 * lo_maps, x, ay, fb);
+                        tma_load_2d(b_tile<BN, X3>(smem, s, 1), bmap + 2 * lo_maps, x, by, fb);
+                    }
                 }
             }
         }
@@ -241,12 +262,21 @@ __global__ void __launch_bounds__(kThreads, Cfg<BN>::CTAS_PER_SM)
                         break;
                     }
                     fence_after();
-                    const uint32_t a0 = smem_u32(smem + s * A_BYTES);
-                    const uint32_t b0 = smem_u32(smem + STAGES * A_BYTES + s * C::B_BYTES);
+                    const uint32_t a0 = a_tile<BN, X3>(smem, s, 0), b0 = b_tile<BN, X3>(smem, s, 0);
 #pragma unroll
-                    for (int kk = 0; kk < BK / 8; kk++)  // 8 tf32 = 32 bytes along K inside the swizzle row
-                        mma_tf32(td, umma_desc_sw128(a0 + kk * 32), umma_desc_sw128(b0 + kk * 32), C::IDESC,
-                                 (kb > 0 || kk > 0) ? 1u : 0u);
+                    for (int kk = 0; kk < BK / 8; kk++) {  // 8 tf32 = 32 bytes along K inside the swizzle row
+                        if constexpr (X3) {
+                            // small terms first: lo*hi, hi*lo, then hi*hi
+                            const uint32_t a1 = a_tile<BN, X3>(smem, s, 1), b1 = b_tile<BN, X3>(smem, s, 1);
+                            mma_tf32(td, umma_desc_sw128(a1 + kk * 32), umma_desc_sw128(b0 + kk * 32), C::IDESC,
+                                     (kb > 0 || kk > 0) ? 1u : 0u);
+                            mma_tf32(td, umma_desc_sw128(a0 + kk * 32), umma_desc_sw128(b1 + kk * 32), C::IDESC, 1u);
+                            mma_tf32(td, umma_desc_sw128(a0 + kk * 32), umma_desc_sw128(b0 + kk * 32), C::IDESC, 1u);
+                        } else {
+                            mma_tf32(td, umma_desc_sw128(a0 + kk * 32), umma_desc_sw128(b0 + kk * 32), C::IDESC,
+                                     (kb > 0 || kk > 0) ? 1u : 0u);
+                        }
+                    }
                     mma_commit(smem_u32(empty + s));  // frees ring stage s when these MMAs finish
                 }
                 mma_commit(smem_u32(accf + a));  // accumulator a complete
@@ -300,10 +330,15 @@ __global__ void __launch_bounds__(kThreads, Cfg<BN>::CTAS_PER_SM)
 
 // ---------------------------------------------------------------- host side
 inline bool tc_gemm_init() {
-    return cudaFuncSetAttribute(tc::k_tc_gemm<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::Cfg<128>::SMEM) ==
-               cudaSuccess &&
-           cudaFuncSetAttribute(tc::k_tc_gemm<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::Cfg<64>::SMEM) ==
-               cudaSuccess;
+    using namespace tc;
+    return cudaFuncSetAttribute(k_tc_gemm<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                Cfg<128, false>::SMEM) == cudaSuccess &&
+           cudaFuncSetAttribute(k_tc_gemm<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                Cfg<64, false>::SMEM) == cudaSuccess &&
+           cudaFuncSetAttribute(k_tc_gemm<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                Cfg<128, true>::SMEM) == cudaSuccess &&
+           cudaFuncSetAttribute(k_tc_gemm<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                Cfg<64, true>::SMEM) == cudaSuccess;
 }
 
 // Tile width for a product on the tensor cores: 128 or 64 columns, or 0 when the
@@ -363,18 +398,26 @@ inline int tc_encode_maps(const sc_symbolic *s, float *d_lnz, std::vector<CUtens
     return SC_OK;
 }
 
-// Launches the persistent kernel over `count` tiles of width bn.
-inline void launch_tc_gemm(int bn, float *lnz, const Task *tasks, const GemmTile *tiles, int32_t count,
-                           const CUtensorMap *maps, const int32_t *tmap_of_sn, int32_t *err, long long spin_limit,
-                           int num_sms, cudaStream_t st) {
+// Launches the persistent kernel over `count` tiles of width bn; x3 selects
+// the three-product split form (maps[2 * nmaps ...] are then the lo maps).
+template <int BN, bool X3>
+inline void launch_tc(float *lnz, const Task *tasks, const GemmTile *tiles, int32_t count, const CUtensorMap *maps,
+                      int nmaps, const int32_t *tmap_of_sn, int32_t *err, long long spin_limit, int num_sms,
+                      cudaStream_t st) {
+    using C = tc::Cfg<BN, X3>;
+    const int grid = std::min<int>(count, num_sms * C::CTAS_PER_SM);
+    tc::k_tc_gemm<BN, X3><<<grid, tc::kThreads, C::SMEM, st>>>(lnz, tasks, tiles, count, maps, nmaps, tmap_of_sn, err,
+                                                               spin_limit);
+}
+inline void launch_tc_gemm(int bn, bool x3, float *lnz, const Task *tasks, const GemmTile *tiles, int32_t count,
+                           const CUtensorMap *maps, int nmaps, const int32_t *tmap_of_sn, int32_t *err,
+                           long long spin_limit, int num_sms, cudaStream_t st) {
     if (bn == 128) {
-        const int grid = std::min<int>(count, num_sms * tc::Cfg<128>::CTAS_PER_SM);
-        tc::k_tc_gemm<128><<<grid, tc::kThreads, tc::Cfg<128>::SMEM, st>>>(lnz, tasks, tiles, count, maps, tmap_of_sn,
-                                                                            err, spin_limit);
+        if (x3) launch_tc<128, true>(lnz, tasks, tiles, count, maps, nmaps, tmap_of_sn, err, spin_limit, num_sms, st);
+        else launch_tc<128, false>(lnz, tasks, tiles, count, maps, nmaps, tmap_of_sn, err, spin_limit, num_sms, st);
     } else {
-        const int grid = std::min<int>(count, num_sms * tc::Cfg<64>::CTAS_PER_SM);
-        tc::k_tc_gemm<64><<<grid, tc::kThreads, tc::Cfg<64>::SMEM, st>>>(lnz, tasks, tiles, count, maps, tmap_of_sn,
-                                                                          err, spin_limit);
+        if (x3) launch_tc<64, true>(lnz, tasks, tiles, count, maps, nmaps, tmap_of_sn, err, spin_limit, num_sms, st);
+        else launch_tc<64, false>(lnz, tasks, tiles, count, maps, nmaps, tmap_of_sn, err, spin_limit, num_sms, st);
     }
 }
 

@@ -5,7 +5,7 @@ Parity bars (written here, derived from the arithmetic):
   |L_gpu - L_or| <= 1e-10 * max|L_or| elementwise (the two sum the same
   products in different orders; the growth for these SPD inputs stays far below
   1e6 u), and the solve reaches eta <= 1e-14.
-- FP32 / TF32 factor: L within 1e-3 (FP32) or 2e-2 (TF32) relative to max|L|
+- FP32 / TF32 / TF32x3 factor: L within 1e-3 (FP32, TF32x3) or 2e-2 (TF32) relative to max|L|
   on well-conditioned inputs; after FP64 refinement eta <= 1e-14.
 - structure: the library's symbolic arrays are bit-exact with the oracle's.
 - non-positive-definite input: the reported column equals the oracle's.
@@ -97,7 +97,7 @@ def test_chunk_widths(chunk):
     _check_L(num.export_L(), Lo, 1e-10)
 
 
-@pytest.mark.parametrize("prec,tol", [("fp32", 1e-3), ("tf32", 2e-2)])
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-3), ("tf32", 2e-2), ("tf32x3", 1e-3)])
 @pytest.mark.parametrize("name", ["lap2d_64", "st27_14", "lap2d_ragged"])
 def test_low_precision_factor_and_refinement(prec, tol, name):
     A = _grid_case(name)

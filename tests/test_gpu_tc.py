@@ -68,3 +68,39 @@ def test_tf32_tensor_core_tiles_match_oracle(case):
     X, info = num.solve(B)
     assert info["converged"], info
     assert oracle.backward_error(A, B, X).max() <= 1e-14
+
+
+@pytest.mark.parametrize("case", ["dense_700", "st27_16"])
+def test_tf32x3_split_products_reach_fp32_accuracy(case):
+    """The three-product split form (x = hi + lo, hi*hi' + hi*lo' + lo*hi') on the
+    tensor cores: L within the FP32 bound of the oracle's FP64 L and as close
+    to it as the FP32 SIMT factor (within 2x), or 16x closer than the plain
+    TF32 factor where TF32 rounding of the products dominates; refinement to
+    eta <= 1e-14 in no more steps than the plain TF32 factor."""
+    if case == "dense_700":
+        A, perm0, kw = _dense(700, 1), None, dict(ordering="natural")
+    else:
+        A = inputs.stencil_3d_27pt(16, 16, 16, seed=3)
+        perm0, kw = oracle.nd_grid(16, 16, 16, 8), dict(ordering="grid_nd", grid=A.grid)
+    sym = sc.Symbolic(A, **kw)
+    assert sym.plan_stats("tf32x3")["tc_tiles"] > 0
+    o = oracle.Oracle(A, perm0, pr=True)
+    assert o.factor() == 0
+    Lo = o.L_supernodal()
+    scale = np.abs(Lo).max()
+    errs = {}
+    nums = {}
+    for prec in ("tf32", "tf32x3", "fp32"):
+        nums[prec] = sym.factor(A.values, precision=prec)
+        assert nums[prec].rc == 0
+        errs[prec] = np.abs(nums[prec].export_L() - Lo).max() / scale
+    assert errs["tf32x3"] <= 1e-3, errs
+    assert errs["tf32x3"] <= max(2 * errs["fp32"], errs["tf32"] / 16), errs
+    B = inputs.rhs(A.n, 2, 7)
+    its = {}
+    for prec in ("tf32", "tf32x3"):
+        X, info = nums[prec].solve(B)
+        assert info["converged"], info
+        assert oracle.backward_error(A, B, X).max() <= 1e-14
+        its[prec] = info["iterations"]
+    assert its["tf32x3"] <= its["tf32"], its
