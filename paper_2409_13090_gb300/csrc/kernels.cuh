@@ -408,22 +408,105 @@ __global__ void __launch_bounds__(256) k_small_tasks(T *__restrict__ lnz, T *__r
 }
 
 // --------------------------------------------------------------------- K3 (device loops)
+// One warp forms a block of up to NI x NJ = 32 outputs C[i][j] = sum_k A_i[k]
+// B_j[k] of two row slabs of a panel (row stride ld, K columns): the lanes walk
+// K (coalesced loads of NI A rows and NJ B rows per step, 32 FMAs per lane),
+// then a transpose-reduction (31 shuffles) leaves output (l / NJ, l % NJ) in
+// lane l, which subtracts it from C (row stride ldc) atomically where it is
+// inside the block (ni x nj) and, for a lower block, on or below the diagonal
+// (row i0 + i >= column j0 + j).
+template <typename T, int NI>
+__device__ __forceinline__ void warp_block(const T *__restrict__ A, const T *__restrict__ Bm, int64_t ld, int K,
+                                           int ni, int nj, T *__restrict__ C, int64_t ldc, bool lower, int i0,
+                                           int j0) {
+    constexpr int NJ = 32 / NI;
+    const int lane = threadIdx.x % 32;
+    T v[32];
+#pragma unroll
+    for (int q = 0; q < 32; q++) v[q] = T(0);
+#pragma unroll(sizeof(T) == 4 ? 2 : 1)
+    for (int k = lane; k < K; k += 32) {
+        T a[NI], b[NJ];
+#pragma unroll
+        for (int i = 0; i < NI; i++) a[i] = i < ni ? A[(int64_t)i * ld + k] : T(0);
+#pragma unroll
+        for (int j = 0; j < NJ; j++) b[j] = j < nj ? Bm[(int64_t)j * ld + k] : T(0);
+#pragma unroll
+        for (int i = 0; i < NI; i++)
+#pragma unroll
+            for (int j = 0; j < NJ; j++) v[i * NJ + j] += a[i] * b[j];
+    }
+    // recursive halving: at offset o a lane keeps the half of its values whose
+    // index bit o matches its own lane bit, and adds the partner's copy of it
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const bool up = lane & o;
+#pragma unroll
+        for (int q = 0; q < o; q++) {
+            const T send = up ? v[q] : v[q + o];
+            const T keep = up ? v[q + o] : v[q];
+            v[q] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    const int i = lane / NJ, j = lane % NJ;
+    if (i < ni && j < nj && (!lower || i0 + i >= j0 + j)) atomicAdd(C + (int64_t)i * ldc + j, -v[0]);
+}
+
+// Rows x nb product C -= A B^T cut into NI x NJ warp blocks, dealt round-robin
+// to the CTA's warps; `task` counts blocks across the CTA's products.
+template <typename T, int NI>
+__device__ __forceinline__ void warp_blocks(const T *A, const T *Bm, int64_t ld, int K, int rows, int nb, T *C,
+                                            int64_t ldc, bool lower, int &task) {
+    constexpr int NJ = 32 / NI;
+    const int warp = threadIdx.x / 32, nwarps = blockDim.x / 32;
+    for (int i0 = 0; i0 < rows; i0 += NI)
+        for (int j0 = 0; j0 < nb && (!lower || j0 <= i0 + NI - 1); j0 += NJ) {
+            if ((task++ % nwarps) != warp) continue;
+            warp_block<T, NI>(A + (int64_t)i0 * ld, Bm + (int64_t)j0 * ld, ld, K, min(NI, rows - i0),
+                              min(NJ, nb - j0), C + (int64_t)i0 * ldc + j0, ldc, lower, i0, j0);
+        }
+}
+
+// Block shape for a rows x nb product: the NI in {ni_min, ..., 8} (powers of
+// two) with the fewest warp blocks, ties to the smaller NI + 32 / NI (fewer
+// loads per step). FP64 starts at 2 (a 1 x 32 block's operands and
+// accumulators do not fit the register budget in FP64).
+__device__ __forceinline__ int block_rows(int rows, int nb, int ni_min) {
+    int best = ni_min, bestn = 1 << 30;
+    for (int ni = ni_min; ni <= 8; ni *= 2) {
+        const int nj = 32 / ni;
+        const int cnt = ((rows + ni - 1) / ni) * ((nb + nj - 1) / nj);
+        if (cnt < bestn || (cnt == bestn && ni + nj < best + 32 / best)) {
+            best = ni;
+            bestn = cnt;
+        }
+    }
+    return best;
+}
+
+template <typename T>
+__device__ __forceinline__ void product_blocks(const T *A, const T *Bm, int64_t ld, int K, int rows, int nb, T *C,
+                                               int64_t ldc, bool lower, int &task) {
+    switch (lower ? 4 : block_rows(rows, nb, sizeof(T) == 8 ? 2 : 1)) {
+        case 1:
+            if constexpr (sizeof(T) == 4) warp_blocks<T, 1>(A, Bm, ld, K, rows, nb, C, ldc, lower, task);
+            break;
+        case 2: warp_blocks<T, 2>(A, Bm, ld, K, rows, nb, C, ldc, lower, task); break;
+        case 4: warp_blocks<T, 4>(A, Bm, ld, K, rows, nb, C, ldc, lower, task); break;
+        default: warp_blocks<T, 8>(A, Bm, ld, K, rows, nb, C, ldc, lower, task); break;
+    }
+}
+
 // Alg. 5 lines 10-16 for a range of J's blocks, in one CTA: for each block B
 // (inside ancestor P): SYRK L_{B,B} -= L_{B,J} L_{B,J}^T, then for each maximal
 // run B' of blocks below B: GEMM L_{B',B} -= L_{B',J} L_{B,J}^T, both straight
 // into Lnz(P) at the rows given by relindB(J,P). Products that tile_task()
-// routes to the tiled kernels are skipped here. J's panel is staged in shared
-// memory when it fits. Entries are added atomically (other supernodes of the
-// level may update the same ancestor entries).
-__device__ inline int tri_row(int e) {
-    int i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
-    while ((i + 1) * (i + 2) / 2 <= e) i++;
-    while (i * (i + 1) / 2 > e) i--;
-    return i;
-}
-
+// routes to the tiled kernels are skipped here. The products are cut into
+// 32-output warp blocks (warp_block) dealt round-robin to the CTA's warps.
+// Entries are added atomically (other supernodes of the level may update the
+// same ancestor entries).
 template <typename T>
-__global__ void __launch_bounds__(256) k_rlb_loop(T *__restrict__ lnz, const LoopItem *__restrict__ items,
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_rlb_loop(T *__restrict__ lnz, const LoopItem *__restrict__ items,
                                                   const SnDev *__restrict__ sn, const BlkDev *__restrict__ blk,
                                                   const int32_t *__restrict__ rb_val) {
     const LoopItem it = items[blockIdx.x];
@@ -434,25 +517,10 @@ __global__ void __launch_bounds__(256) k_rlb_loop(T *__restrict__ lnz, const Loo
     const SnDev P = sn[B.owner];
     const int colB = B.first - P.f;
     const int nb = B.size;
-    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nwarps = blockDim.x / 32;
-    // task 0 = SYRK on B (when r_lo == b), tasks 1.. = runs B' below B; one warp per task
+    const T *rowsB = src + (int64_t)B.pos * J.ld;
     int task = 0;
-    if (it.r_lo == it.b) {
-        if (warp == 0) {
-            const int tri = nb * (nb + 1) / 2;
-            T *C = lnz + P.off + (int64_t)colB * P.ld + colB;
-            for (int e = lane; e < tri; e += 32) {
-                int i = tri_row(e), j = e - i * (i + 1) / 2;
-                const T *a = src + (int64_t)(B.pos + i) * J.ld;
-                const T *bb = src + (int64_t)(B.pos + j) * J.ld;
-                T acc = T(0);
-#pragma unroll 8
-                for (int k = 0; k < K; k++) acc += a[k] * bb[k];
-                atomicAdd(C + (int64_t)i * P.ld + j, -acc);
-            }
-        }
-        task = 1;
-    }
+    if (it.r_lo == it.b)  // SYRK on B: lower-triangular blocks of L_{B,B}
+        product_blocks(rowsB, rowsB, J.ld, K, nb, nb, lnz + P.off + (int64_t)colB * P.ld + colB, P.ld, true, task);
     int r = it.r_lo == it.b ? it.b + 1 : it.r_lo;
     while (r < it.r_hi) {
         int e = r;
@@ -461,21 +529,9 @@ __global__ void __launch_bounds__(256) k_rlb_loop(T *__restrict__ lnz, const Loo
             e++;
             rows += blk[e].size;
         }
-        if ((task++ % nwarps) == warp) {
-            const int rowP = P.m - 1 - rb_val[B.rb + (r - B.bs)];
-            T *C = lnz + P.off + (int64_t)rowP * P.ld + colB;
-            const int apos = blk[r].pos;
-            const int tot = rows * nb;
-            for (int q = lane; q < tot; q += 32) {
-                int i = q / nb, j = q % nb;
-                const T *a = src + (int64_t)(apos + i) * J.ld;
-                const T *bb = src + (int64_t)(B.pos + j) * J.ld;
-                T acc = T(0);
-#pragma unroll 8
-                for (int k = 0; k < K; k++) acc += a[k] * bb[k];
-                atomicAdd(C + (int64_t)i * P.ld + j, -acc);
-            }
-        }
+        const int rowP = P.m - 1 - rb_val[B.rb + (r - B.bs)];
+        product_blocks(src + (int64_t)blk[r].pos * J.ld, rowsB, J.ld, K, rows, nb,
+                       lnz + P.off + (int64_t)rowP * P.ld + colB, P.ld, false, task);
         r = e + 1;
     }
 }
