@@ -32,6 +32,30 @@ struct GemmTile {
 };
 constexpr int kSplitK = 256;
 
+// Work of one CTA of the thin-product kernel: warp blocks blk0 .. blk0 + 3 of
+// a task (blocks numbered row-major over the task's NI x NJ block grid).
+struct ThinUnit {
+    int32_t task, blk0;
+};
+constexpr int kThinWarps = 4;
+
+// Warp-block shape for a rows x nb product: the NI in {ni_min, ..., 8}
+// (powers of two; NJ = 32 / NI) with the fewest blocks, ties to the smaller
+// NI + NJ (fewer loads per step). Lower (triangular) products use 4 x 8.
+SC_HD inline int block_rows(int rows, int nb, int ni_min, bool lower) {
+    if (lower) return 4;
+    int best = ni_min, bestn = 1 << 30;
+    for (int ni = ni_min; ni <= 8; ni *= 2) {
+        const int nj = 32 / ni;
+        const int cnt = ((rows + ni - 1) / ni) * ((nb + nj - 1) / nj);
+        if (cnt < bestn || (cnt == bestn && ni + nj < best + 32 / best)) {
+            best = ni;
+            bestn = cnt;
+        }
+    }
+    return best;
+}
+
 constexpr int kMaxChunk = 64;
 
 // Supernode descriptor for the device-side RLB loops.

@@ -172,6 +172,12 @@ int run_levels(sc_numeric *h, cudaStream_t st, Prof *prof = nullptr, cudaStream_
                 launches++;
             }
         }
+        if (p.thin_cnt) {
+            B(kProfGemm);
+            k_thin_tasks<T><<<p.thin_cnt, kThinWarps * 32, 0, st>>>(lnz, h->d_tasks, h->d_thin + p.thin_off);
+            E();
+            launches++;
+        }
         if (p.small_cnt) {
             B(kProfSmall);
             k_small_tasks<T><<<(p.small_cnt + 7) / 8, 256, 0, st>>>(lnz, pool, h->d_tasks, h->d_small + p.small_off,
@@ -233,6 +239,7 @@ int set_smem_attrs() {
 struct Plan {
     std::vector<ChunkDev> cd;
     std::vector<int32_t> potrf, small;
+    std::vector<ThinUnit> thin;
     std::vector<TrsmTile> trsm;
     std::vector<GemmTile> gemm;
     std::vector<Task> tasks;
@@ -281,6 +288,7 @@ void build_plan(const sc_symbolic *s, int precision, Plan &P) {
         p.trsm_cnt = (int32_t)P.trsm.size() - p.trsm_off;
         // product tasks: tensor-core tiles (TF32), SIMT tiles, warp tasks
         std::vector<int32_t> ids_small;
+        std::vector<ThinUnit> units_thin;
         std::vector<GemmTile> g_simt, g_tc, g_tc64;
         for (const Task &t : L.tasks) {
             int32_t id = (int32_t)P.tasks.size();
@@ -292,6 +300,12 @@ void build_plan(const sc_symbolic *s, int precision, Plan &P) {
             } else if (bn) {
                 tc_tiles_of(t, id, bn, bn == 128 ? g_tc : g_tc64);
                 P.class_flops[kProfTc] += task_flops(t);
+            } else if (std::min(t.m, t.n) <= kThinDim && !(t.flags & kTaskStoreU)) {
+                // a 64 x 64 tile would be mostly padding: warp blocks, kThinWarps per CTA
+                const int ni = block_rows(t.m, t.n, precision == SC_FP64 ? 2 : 1, (t.flags & kTaskLower) != 0);
+                const int nblk = ((t.m + ni - 1) / ni) * ((t.n + 32 / ni - 1) / (32 / ni));
+                for (int b0 = 0; b0 < nblk; b0 += kThinWarps) units_thin.push_back(ThinUnit{id, b0});
+                P.class_flops[kProfGemm] += task_flops(t);
             } else {
                 tiles_of(t, id, g_simt);
                 P.class_flops[kProfGemm] += task_flops(t);
@@ -309,6 +323,9 @@ void build_plan(const sc_symbolic *s, int precision, Plan &P) {
         p.small_off = (int32_t)P.small.size();
         P.small.insert(P.small.end(), ids_small.begin(), ids_small.end());
         p.small_cnt = (int32_t)ids_small.size();
+        p.thin_off = (int32_t)P.thin.size();
+        P.thin.insert(P.thin.end(), units_thin.begin(), units_thin.end());
+        p.thin_cnt = (int32_t)units_thin.size();
         // device-side RLB loops
         p.loop_off = (int32_t)P.loops.size();
         for (const LoopItem &it : L.loops) P.loops.push_back(it);
@@ -432,6 +449,7 @@ int numeric_create(sc_symbolic *s, int precision, sc_numeric **out) {
     if ((rc = upload(h->d_trsm, P.trsm, bytes))) return fail(rc);
     if ((rc = upload(h->d_gemm, P.gemm, bytes))) return fail(rc);
     if ((rc = upload(h->d_small, P.small, bytes))) return fail(rc);
+    if ((rc = upload(h->d_thin, P.thin, bytes))) return fail(rc);
     if ((rc = upload(h->d_tasks, P.tasks, bytes))) return fail(rc);
     if ((rc = upload(h->d_rlpairs, P.rlpairs, bytes))) return fail(rc);
     if ((rc = upload(h->d_rlrelind, s->rl_relind, bytes))) return fail(rc);
@@ -585,7 +603,7 @@ void numeric_free(sc_numeric *h) {
                     h->d_rlrelind, h->d_glbind, h->d_perm, h->d_csr_ptr, h->d_csr_col, h->d_csr_val,
                     h->d_csr_map, h->d_counters, h->d_xw, h->d_solve_tiles, h->d_sn, h->d_blk, h->d_rbval,
                     h->d_loops, h->d_tmaps, h->d_tmap_of_sn, h->d_err, h->d_inv, h->d_x, h->d_r, h->d_b, h->d_xbest, h->d_y, h->d_z, h->d_acc, h->d_red,
-                    h->d_dep_ptr, h->d_dep, h->d_sync, h->d_serr, h->d_hi, h->d_lo};
+                    h->d_dep_ptr, h->d_dep, h->d_sync, h->d_serr, h->d_hi, h->d_lo, h->d_thin};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->sym) h->sym->refs--;

@@ -467,33 +467,47 @@ __device__ __forceinline__ void warp_blocks(const T *A, const T *Bm, int64_t ld,
         }
 }
 
-// Block shape for a rows x nb product: the NI in {ni_min, ..., 8} (powers of
-// two) with the fewest warp blocks, ties to the smaller NI + 32 / NI (fewer
-// loads per step). FP64 starts at 2 (a 1 x 32 block's operands and
-// accumulators do not fit the register budget in FP64).
-__device__ __forceinline__ int block_rows(int rows, int nb, int ni_min) {
-    int best = ni_min, bestn = 1 << 30;
-    for (int ni = ni_min; ni <= 8; ni *= 2) {
-        const int nj = 32 / ni;
-        const int cnt = ((rows + ni - 1) / ni) * ((nb + nj - 1) / nj);
-        if (cnt < bestn || (cnt == bestn && ni + nj < best + 32 / best)) {
-            best = ni;
-            bestn = cnt;
-        }
-    }
-    return best;
-}
-
 template <typename T>
 __device__ __forceinline__ void product_blocks(const T *A, const T *Bm, int64_t ld, int K, int rows, int nb, T *C,
                                                int64_t ldc, bool lower, int &task) {
-    switch (lower ? 4 : block_rows(rows, nb, sizeof(T) == 8 ? 2 : 1)) {
+    switch (block_rows(rows, nb, sizeof(T) == 8 ? 2 : 1, lower)) {
         case 1:
             if constexpr (sizeof(T) == 4) warp_blocks<T, 1>(A, Bm, ld, K, rows, nb, C, ldc, lower, task);
             break;
         case 2: warp_blocks<T, 2>(A, Bm, ld, K, rows, nb, C, ldc, lower, task); break;
         case 4: warp_blocks<T, 4>(A, Bm, ld, K, rows, nb, C, ldc, lower, task); break;
         default: warp_blocks<T, 8>(A, Bm, ld, K, rows, nb, C, ldc, lower, task); break;
+    }
+}
+
+// Product tasks with one dimension <= kThinDim (a block B or a run B' of a few
+// rows against a long panel): each CTA takes kThinWarps consecutive warp
+// blocks of one task (ThinUnit), one per warp, so a long thin product spreads
+// over many SMs.
+constexpr int kThinDim = 8;
+template <typename T>
+__global__ void __launch_bounds__(kThinWarps * 32) k_thin_tasks(T *__restrict__ lnz, const Task *__restrict__ tasks,
+                                                                const ThinUnit *__restrict__ units) {
+    const ThinUnit u = units[blockIdx.x];
+    const Task tk = tasks[u.task];
+    const bool lower = (tk.flags & kTaskLower) != 0;
+    const int ni_min = sizeof(T) == 8 ? 2 : 1;
+    const int NI = block_rows(tk.m, tk.n, ni_min, lower), NJ = 32 / NI;
+    const int nbj = (tk.n + NJ - 1) / NJ, nblk = ((tk.m + NI - 1) / NI) * nbj;
+    const int b = u.blk0 + threadIdx.x / 32;
+    if (b >= nblk) return;
+    const int i0 = (b / nbj) * NI, j0 = (b % nbj) * NJ;
+    if (lower && j0 > i0 + NI - 1) return;  // wholly above the diagonal
+    const T *A = lnz + tk.a_off + (int64_t)i0 * tk.lds, *Bm = lnz + tk.b_off + (int64_t)j0 * tk.lds;
+    T *C = lnz + tk.c_off + (int64_t)i0 * tk.ldc + j0;
+    const int ni = min(NI, tk.m - i0), nj = min(NJ, tk.n - j0);
+    switch (NI) {
+        case 1:
+            if constexpr (sizeof(T) == 4) warp_block<T, 1>(A, Bm, tk.lds, tk.k, ni, nj, C, tk.ldc, lower, i0, j0);
+            break;
+        case 2: warp_block<T, 2>(A, Bm, tk.lds, tk.k, ni, nj, C, tk.ldc, lower, i0, j0); break;
+        case 4: warp_block<T, 4>(A, Bm, tk.lds, tk.k, ni, nj, C, tk.ldc, lower, i0, j0); break;
+        default: warp_block<T, 8>(A, Bm, tk.lds, tk.k, ni, nj, C, tk.ldc, lower, i0, j0); break;
     }
 }
 

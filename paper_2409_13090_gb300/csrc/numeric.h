@@ -19,6 +19,7 @@ struct LevelPlan {
     int32_t tc_off = 0, tc_cnt = 0;         // GemmTile (tensor cores, 128-column tiles)
     int32_t tc64_off = 0, tc64_cnt = 0;     // GemmTile (tensor cores, 64-column tiles)
     int32_t small_off = 0, small_cnt = 0;   // task ids (warp kernel)
+    int32_t thin_off = 0, thin_cnt = 0;     // ThinUnits of tasks with min(m, n) <= 8 (warp-block kernel)
     int32_t rlg_off = 0, rlg_cnt = 0;       // GemmTile of RL update matrices
     int32_t rls_off = 0, rls_cnt = 0;       // task ids of small RL update matrices
     int32_t loop_off = 0, loop_cnt = 0;     // LoopItem (device-side RLB loops)
@@ -57,6 +58,7 @@ struct sc_numeric {
     sc::TrsmTile *d_trsm = nullptr;
     sc::GemmTile *d_gemm = nullptr;
     int32_t *d_small = nullptr;
+    sc::ThinUnit *d_thin = nullptr;
     sc::Task *d_tasks = nullptr;
     sc::RLPair *d_rlpairs = nullptr;
     sc::SnDev *d_sn = nullptr;
