@@ -305,6 +305,13 @@ def main():
             mixed[prec] = {"factor_gflops": flops / (min(fts) * 1e-3) / 1e9, "factor_ms": min(fts),
                            "ir_iterations": si["iterations"], "eta_max": si["eta_max"], "converged": si["converged"],
                            "solve_ms": si["solve_ms"], "pivot_fallbacks": fi.pivot_fallbacks}
+            # conjugate gradients preconditioned by the same factor (classical refinement cannot
+            # converge here: kappa x unit roundoff of the factor exceeds 1)
+            nm.solve(Bd, torch.zeros_like(Bd), method="cg", max_iterations=400)
+            _, sc_ = nm.solve(Bd, torch.zeros_like(Bd), method="cg", max_iterations=400)
+            mixed[prec]["cg"] = {"iterations": sc_["iterations"], "eta_max": sc_["eta_max"],
+                                 "converged": sc_["converged"], "solve_ms": sc_["solve_ms"],
+                                 "total_ms": min(fts) + sc_["solve_ms"]}
             nm.free()
 
     # ---- the chosen form vs the plain form where refinement converges: 80^3 27-point stencil

@@ -195,7 +195,13 @@ typedef struct sc_solve_info {
     double *eta;           /* optional [nrhs] output, caller-owned host memory   */
     int32_t refine;        /* in: 1 = refine even for an FP64 factor (-1 = by precision) */
     int32_t kernel_launches; /* out: kernels launched by this solve                */
-    int32_t reserved[4];
+    int32_t method;        /* in: 0 = classical refinement x += solve(b - A x);
+                              1 = conjugate gradients on A x = b preconditioned by
+                              the factor (FP64 vectors), for matrices whose
+                              condition number times the factor's unit roundoff
+                              is too large for classical refinement to converge */
+    int32_t max_iterations; /* in: iteration cap of this solve (0 = ir_maxit)    */
+    int32_t reserved[2];
 } sc_solve_info;
 
 /* Solves A X = B (Sec. 1 step 4): permute, forward solve with L, backward

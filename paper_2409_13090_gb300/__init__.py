@@ -60,7 +60,8 @@ class FactorInfo(C.Structure):
 class SolveInfo(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("eta_max", C.c_double),
                 ("solve_ms", C.c_double), ("eta", C.c_void_p), ("refine", C.c_int32),
-                ("kernel_launches", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("kernel_launches", C.c_int32), ("method", C.c_int32), ("max_iterations", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
 
 
 class SCError(RuntimeError):
@@ -347,12 +348,14 @@ class Numeric:
             raise SCError(rc, "sc_refactor")
         return info
 
-    def solve(self, B, X=None, refine=None, stream=None):
+    def solve(self, B, X=None, refine=None, stream=None, method="ir", max_iterations=0):
         """Solves A X = B.
 
         B as a numpy array: n x nrhs (host, column-major). B as a torch tensor
         (CUDA, or pinned/host CPU): shape (nrhs, n) contiguous, i.e. column-major
-        n x nrhs; X likewise (allocated when None)."""
+        n x nrhs; X likewise (allocated when None). method "ir": classical
+        refinement; "cg": conjugate gradients preconditioned by the factor.
+        max_iterations caps the iterations of this solve (0: the options' cap)."""
         if isinstance(B, np.ndarray):
             dev = False
             B = np.asfortranarray(B, np.float64)
@@ -375,6 +378,8 @@ class Numeric:
         eta = np.zeros(nrhs)
         info.eta = eta.ctypes.data
         info.refine = -1 if refine is None else int(bool(refine))
+        info.method = {"ir": 0, "cg": 1}[method]
+        info.max_iterations = int(max_iterations)
         rc = sc_solve(self._h, nrhs, B, ldb, X, ldx, dev, _stream(stream), info)
         if rc not in (0, SC_ERR_NOT_CONVERGED):
             raise SCError(rc, "sc_solve")

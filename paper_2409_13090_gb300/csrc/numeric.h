@@ -94,6 +94,9 @@ struct sc_numeric {
     double *d_x = nullptr, *d_r = nullptr, *d_b = nullptr, *d_xbest = nullptr;
     void *d_y = nullptr, *d_z = nullptr, *d_acc = nullptr;  // permuted work vectors (storage precision)
     double *d_red = nullptr;        // reductions for eta
+    double *d_cgz = nullptr, *d_cgp = nullptr, *d_cgq = nullptr;  // preconditioned CG vectors (FP64)
+    double *d_cgs = nullptr;        // CG scalars: r.z (two), p.Ap, per column
+    int64_t cg_cap = 0;             // rhs capacity of the CG vectors
     double anorm = 0.0;
     bool solve_ready = false;
     // solve graphs for sg_nrhs right-hand sides: [0] x = solve(b) + residual,

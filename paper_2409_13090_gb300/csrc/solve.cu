@@ -424,6 +424,81 @@ __global__ void k_residual(const int64_t *__restrict__ ptr, const int32_t *__res
     }
 }
 
+// ---- conjugate gradients preconditioned by the factor (M = L L^T in the
+// factor's precision, FP64 vectors), all right-hand sides at once; per-column
+// scalars live on the device.
+__device__ inline double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Q = A P and pq[c] += P(:,c) . Q(:,c)
+__global__ void k_spmv_dot(const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                           const double *__restrict__ val, const double *__restrict__ P, double *__restrict__ Q,
+                           int64_t n, double *__restrict__ pq) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    double d = 0.0;
+    if (i < n) {
+        const double *p = P + (int64_t)c * n;
+        double s = 0.0;
+        for (int64_t e = ptr[i]; e < ptr[i + 1]; e++) s += val[e] * p[col[e]];
+        Q[(int64_t)c * n + i] = s;
+        d = p[i] * s;
+    }
+    d = warp_sum(d);
+    if ((threadIdx.x & 31) == 0) atomicAdd(pq + c, d);
+}
+
+// out[c] += X(:,c) . Y(:,c)
+__global__ void k_dot(const double *__restrict__ X, const double *__restrict__ Y, int64_t n, double *__restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    double d = i < n ? X[(int64_t)c * n + i] * Y[(int64_t)c * n + i] : 0.0;
+    d = warp_sum(d);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out + c, d);
+}
+
+// alpha = rz / pq; x += alpha p; r -= alpha q; maxima of |r|, |x|, |b| for eta
+__global__ void k_cg_step(double *__restrict__ X, double *__restrict__ R, const double *__restrict__ P,
+                          const double *__restrict__ Q, const double *__restrict__ B, const double *__restrict__ rz,
+                          const double *__restrict__ pq, int64_t n, double *__restrict__ red) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    double m0 = 0.0, m1 = 0.0, m2 = 0.0;
+    if (i < n) {
+        const double a = pq[c] != 0.0 ? rz[c] / pq[c] : 0.0;
+        const int64_t g = (int64_t)c * n + i;
+        const double x = X[g] + a * P[g], r = R[g] - a * Q[g];
+        X[g] = x;
+        R[g] = r;
+        m0 = fabs(r);
+        m1 = fabs(x);
+        m2 = fabs(B[g]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        m0 = fmax(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+        m1 = fmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+        m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomic_max_nonneg(red + 3 * c, m0);
+        atomic_max_nonneg(red + 3 * c + 1, m1);
+        atomic_max_nonneg(red + 3 * c + 2, m2);
+    }
+}
+
+// p = z + (rz_new / rz_old) p  (p = z when rz_old is 0)
+__global__ void k_cg_dir(double *__restrict__ P, const double *__restrict__ Z, const double *__restrict__ rz_new,
+                         const double *__restrict__ rz_old, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (i >= n) return;
+    const double b = rz_old[c] != 0.0 ? rz_new[c] / rz_old[c] : 0.0;
+    const int64_t g = (int64_t)c * n + i;
+    P[g] = Z[g] + b * P[g];
+}
+
 int ensure_solve(sc_numeric *h, int64_t nrhs) {
     const sc_symbolic *s = h->sym;
     int64_t n = s->n;
@@ -676,6 +751,88 @@ int solve_with_stall(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, 
 }
 }  // namespace
 
+namespace {
+// Conjugate gradients on A x = b preconditioned by the factor, started from the
+// iterate in h->d_x whose residual is in h->d_r (step 0 of the solve). Each
+// iteration reads the per-column eta of the recursively updated residual; when
+// it reaches tol, the true residual b - A x is formed and checked, and CG
+// restarts from it if it is not yet below tol. h->d_xbest receives the best
+// iterate by the true residual; best / best_eta its eta.
+int pcg(sc_numeric *h, int64_t nrhs, cudaStream_t st, double tol, int maxit, double emax0, double &best,
+        std::vector<double> &best_eta, int &it, int &launches) {
+    const int64_t n = h->sym->n;
+    if (h->cg_cap < nrhs) {
+        double **arr[] = {&h->d_cgz, &h->d_cgp, &h->d_cgq};
+        for (double **p : arr) {
+            if (*p) cudaFree(*p);
+            if (cudaMalloc((void **)p, (size_t)n * nrhs * sizeof(double)) != cudaSuccess) return SC_ERR_OOM;
+        }
+        if (h->d_cgs) cudaFree(h->d_cgs);
+        if (cudaMalloc((void **)&h->d_cgs, 3 * nrhs * sizeof(double)) != cudaSuccess) return SC_ERR_OOM;
+        h->cg_cap = nrhs;
+    }
+    const dim3 g((unsigned)((n + 255) / 256), (unsigned)nrhs);
+    double *rz = h->d_cgs, *rz2 = h->d_cgs + nrhs, *pq = h->d_cgs + 2 * nrhs;
+    int rc;
+    // z = M^-1 r, p = z, rz = r . z
+    auto restart = [&]() -> int {
+        int r2 = tri_solve_any(h, nrhs, h->d_r, n, h->d_cgz, n, 0, st, launches);
+        if (r2) return r2;
+        SC_CUDA(cudaMemcpyAsync(h->d_cgp, h->d_cgz, (size_t)n * nrhs * 8, cudaMemcpyDeviceToDevice, st));
+        SC_CUDA(cudaMemsetAsync(rz, 0, nrhs * sizeof(double), st));
+        k_dot<<<g, 256, 0, st>>>(h->d_r, h->d_cgz, n, rz);
+        launches++;
+        return SC_OK;
+    };
+    if ((rc = restart())) return rc;
+    std::vector<double> eta;
+    double emax = emax0;
+    while (it < maxit) {
+        SC_CUDA(cudaMemsetAsync(pq, 0, nrhs * sizeof(double), st));
+        k_spmv_dot<<<g, 256, 0, st>>>(h->d_csr_ptr, h->d_csr_col, h->d_csr_val, h->d_cgp, h->d_cgq, n, pq);
+        SC_CUDA(cudaMemsetAsync(h->d_red, 0, 3 * nrhs * sizeof(double), st));
+        k_cg_step<<<g, 256, 0, st>>>(h->d_x, h->d_r, h->d_cgp, h->d_cgq, h->d_b, rz, pq, n, h->d_red);
+        launches += 2;
+        it++;
+        if ((rc = read_eta(h, nrhs, st, eta))) return rc;
+        emax = *std::max_element(eta.begin(), eta.end());
+        if (emax <= tol) {
+            // the true residual decides
+            if ((rc = enqueue_residual(h, nrhs, st, launches))) return rc;
+            if ((rc = read_eta(h, nrhs, st, eta))) return rc;
+            emax = *std::max_element(eta.begin(), eta.end());
+            if (emax < best) {
+                best = emax;
+                best_eta = eta;
+                SC_CUDA(cudaMemcpyAsync(h->d_xbest, h->d_x, (size_t)n * nrhs * 8, cudaMemcpyDeviceToDevice, st));
+            }
+            if (emax <= tol) break;
+            if ((rc = restart())) return rc;
+            continue;
+        }
+        // z = M^-1 r; rz2 = r . z; p = z + (rz2 / rz) p
+        if ((rc = tri_solve_any(h, nrhs, h->d_r, n, h->d_cgz, n, 0, st, launches))) return rc;
+        SC_CUDA(cudaMemsetAsync(rz2, 0, nrhs * sizeof(double), st));
+        k_dot<<<g, 256, 0, st>>>(h->d_r, h->d_cgz, n, rz2);
+        k_cg_dir<<<g, 256, 0, st>>>(h->d_cgp, h->d_cgz, rz2, rz, n);
+        launches += 2;
+        std::swap(rz, rz2);
+    }
+    if (emax > tol) {
+        // cap reached: keep the better of the last iterate and the best so far, by the true residual
+        if ((rc = enqueue_residual(h, nrhs, st, launches))) return rc;
+        if ((rc = read_eta(h, nrhs, st, eta))) return rc;
+        emax = *std::max_element(eta.begin(), eta.end());
+        if (emax < best) {
+            best = emax;
+            best_eta = eta;
+            SC_CUDA(cudaMemcpyAsync(h->d_xbest, h->d_x, (size_t)n * nrhs * 8, cudaMemcpyDeviceToDevice, st));
+        }
+    }
+    return SC_OK;
+}
+}  // namespace
+
 int numeric_solve(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, double *X, int64_t ldx, int on_device,
                   cudaStream_t st, sc_solve_info *info) {
     const sc_symbolic *s = h->sym;
@@ -722,7 +879,12 @@ int numeric_solve(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, dou
     SC_CUDA(cudaMemcpyAsync(h->d_xbest, h->d_x, (size_t)n * nrhs * 8, cudaMemcpyDeviceToDevice, st));
     hist.push_back(emax);
     int it = 0;
-    if (refine) {
+    const bool cg = info && info->method == 1;
+    if (refine && cg && emax > tol) {
+        if ((rc = pcg(h, nrhs, st, tol, info->max_iterations > 0 ? info->max_iterations : maxit, emax, best, best_eta,
+                      it, launches)))
+            return rc;
+    } else if (refine) {
         while (emax > tol && it < maxit) {
             // d = solve(r); x += d; new residual
             if ((rc = run_step(h, nrhs, 1, st, launches))) return rc;

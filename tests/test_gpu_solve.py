@@ -56,3 +56,18 @@ def test_many_right_hand_sides_several_blocks():
     B = inputs.rhs(A.n, 40, 12)
     X, info = num.solve(B)
     assert oracle.backward_error(A, B, X).max() <= 1e-14
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "tf32x3"])
+def test_cg_with_low_precision_factor_reaches_fp64_backward_error(prec):
+    """The 7-point variable-coefficient matrix (diagonal = row sum + 1e-6, so
+    kappa is large) at 24^3: conjugate gradients preconditioned by the
+    low-precision factor reaches eta <= 1e-14 (checked with the oracle's eta)."""
+    A = inputs.workload(2, 0.5)[0]
+    sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid, merge=0.125)
+    num = sym.factor(A.values, precision=prec)
+    assert num.rc == 0
+    B = inputs.rhs(A.n, 4, 13)
+    X, info = num.solve(B, method="cg", max_iterations=400)
+    assert info["converged"], info
+    assert oracle.backward_error(A, B, X).max() <= 1e-14
