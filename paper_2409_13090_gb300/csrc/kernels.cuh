@@ -76,7 +76,16 @@ __device__ bool potrf_pass(S (*a)[kMaxChunk + 1], int w, const double *thr, int 
                         if (lane == 0) atomicMin(info, col0 + p0 + k + 1);
                     }
                     if (!(d > S(0))) d = S(1);
-                    const S sq = sqrt(d), rk = S(1) / sq;
+                    // FP64: one reciprocal square root (the FP64 pipe is narrow and this chain is
+                    // serial); FP32: IEEE square root and division
+                    S sq, rk;
+                    if constexpr (sizeof(S) == 8) {
+                        rk = rsqrt(d);
+                        sq = d * rk;
+                    } else {
+                        sq = sqrt(d);
+                        rk = S(1) / sq;
+                    }
                     if (lane == k) r[k] = sq;
                     else if (lane > k) r[k] *= rk;
                     if (lane == 0) rpiv[k] = rk;
@@ -269,8 +278,10 @@ __global__ void __launch_bounds__(kTrsmThreads) k_trsm(T *__restrict__ lnz, cons
         if (q == (k & 3)) x[k >> 2] = v;
 #pragma unroll
         for (int jj = 0; jj < kMaxChunk / 4; jj++) {
-            const int j = q + 4 * jj;
-            if (j > k) x[jj] -= v * l[j][k];
+            if (4 * jj + 3 > k) {  // resolved at compile time: some lane of the quad has j > k
+                const int j = q + 4 * jj;
+                if (j > k) x[jj] -= v * l[j][k];
+            }
         }
     }
     if (live) {
