@@ -32,6 +32,9 @@ namespace {
 
 constexpr int kRhsBlk = 16;
 constexpr int kSolveRows = 64;
+// one synchronisation word per 128-byte line: the CTAs that poll one chunk's
+// word do not contend with arrivals at its neighbours
+constexpr int kSyncStride = 32;
 
 // shared memory of a sweep CTA: the diagonal block (or its inverse), the chunk's
 // right-hand-side values in and out, reciprocal pivots
@@ -151,7 +154,7 @@ __device__ bool wait_flag(const int32_t *flag, int32_t target, int32_t *err, lon
         asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
         if (v >= target) return true;
         if (*(volatile int32_t *)err) return false;
-        __nanosleep(32);
+        if (i > 64) __nanosleep(32);
     }
     atomicCAS(err, 0, code);
     return false;
@@ -199,7 +202,7 @@ __global__ void __launch_bounds__(256) k_fwd(const T *__restrict__ lnz, const Ch
         stage_block(lr, lnz + ch.off + (int64_t)tl.r0 * ch.ld + ch.c0, ch.ld, rows, w);
         if constexpr (sizeof(T) == 4) stage_block(l, (const T *)(inv + ch.inv), w, w, w);
         else load_diag(l, rinv, lnz, ch);
-        if (threadIdx.x == 0) s_ok = wait_flag(arrive + tl.chunk, need[tl.chunk], err, spin_limit, 5);
+        if (threadIdx.x == 0) s_ok = wait_flag(arrive + (int64_t)tl.chunk * kSyncStride, need[tl.chunk], err, spin_limit, 5);
         __syncthreads();
         if (!s_ok) break;
         if constexpr (sizeof(T) == 4) {
@@ -258,10 +261,12 @@ __global__ void __launch_bounds__(256) k_fwd(const T *__restrict__ lnz, const Ch
                 atomicAdd(x + (int64_t)g * nb + r, -acc);
             }
         }
-        __threadfence();
+        // release: the barrier orders every thread's updates before thread 0's fence
         __syncthreads();
-        if (threadIdx.x == 0)
-            for (int p = dep_ptr[t]; p < dep_ptr[t + 1]; p++) atomicAdd(arrive + dep[p], 1);
+        if (threadIdx.x == 0) {
+            __threadfence();
+            for (int p = dep_ptr[t]; p < dep_ptr[t + 1]; p++) atomicAdd(arrive + (int64_t)dep[p] * kSyncStride, 1);
+        }
     }
 }
 
@@ -299,7 +304,7 @@ __global__ void __launch_bounds__(256) k_bwd(const T *__restrict__ lnz, const Ch
             stage_block(lt, lnz + ch.off + (int64_t)tl.r0 * ch.ld + ch.c0, ch.ld, rows, w);
             if (threadIdx.x == 0) {
                 bool ok = true;
-                for (int p = dep_ptr[t]; p < dep_ptr[t + 1] && ok; p++) ok = wait_flag(done + dep[p], 1, err, spin_limit, 6);
+                for (int p = dep_ptr[t]; p < dep_ptr[t + 1] && ok; p++) ok = wait_flag(done + (int64_t)dep[p] * kSyncStride, 1, err, spin_limit, 6);
                 s_ok = ok;
             }
             __syncthreads();
@@ -328,13 +333,15 @@ __global__ void __launch_bounds__(256) k_bwd(const T *__restrict__ lnz, const Ch
                     atomicAdd(acc + (int64_t)(ch.col0 + k) * nb + r, s);
                 }
             }
-            __threadfence();
         }
         __syncthreads();
-        if (threadIdx.x == 0) s_last = (atomicAdd(cnt + tl.chunk, 1) == ntiles[tl.chunk] - 1);
+        if (threadIdx.x == 0) {
+            __threadfence();  // release this tile's contributions
+            s_last = (atomicAdd(cnt + (int64_t)tl.chunk * kSyncStride, 1) == ntiles[tl.chunk] - 1);
+            if (s_last) __threadfence();  // acquire the other tiles' contributions
+        }
         __syncthreads();
         if (!s_last) continue;
-        __threadfence();
         if constexpr (sizeof(T) == 4) {
             // z_c = inv(L_cc)^T (y_c - acc_c) with the block's stored inverse
             stage_block(l, (const T *)(inv + ch.inv), w, w, w);
@@ -368,9 +375,11 @@ __global__ void __launch_bounds__(256) k_bwd(const T *__restrict__ lnz, const Ch
                 if (lane + 32 < w) z[g1] = x1;
             }
         }
-        __threadfence();
         __syncthreads();
-        if (threadIdx.x == 0) atomicExch(done + tl.chunk, 1);
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicExch(done + (int64_t)tl.chunk * kSyncStride, 1);
+        }
     }
 }
 
@@ -567,8 +576,9 @@ int ensure_solve(sc_numeric *h, int64_t nrhs) {
         std::copy(need.begin(), need.end(), cnt2.begin() + s->chunks.size());
         if ((rc = up(h->d_counters, cnt2))) return rc;
         // per-sweep synchronisation words, zeroed before every right-hand-side block:
-        // arrivals, backward counters, done flags [nchunks each], two work counters
-        if (cudaMalloc((void **)&h->d_sync, (3 * s->chunks.size() + 2) * sizeof(int32_t)) != cudaSuccess)
+        // arrivals, backward counters, done flags (nchunks words each, kSyncStride
+        // apart), then the two work counters
+        if (cudaMalloc((void **)&h->d_sync, (3 * s->chunks.size() * kSyncStride + 2) * sizeof(int32_t)) != cudaSuccess)
             return SC_ERR_OOM;
         if (cudaMalloc((void **)&h->d_serr, sizeof(int32_t)) != cudaSuccess) return SC_ERR_OOM;
         if (cudaMalloc((void **)&h->d_red, 4096 * sizeof(double)) != cudaSuccess) return SC_ERR_OOM;
@@ -631,9 +641,10 @@ int tri_solve(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, double 
         int nb = (int)std::min<int64_t>(kRhsBlk, nrhs - r0);
         unsigned g = (unsigned)((n * nb + 255) / 256);
         k_perm_in<T><<<g, 256, 0, st>>>(xw, B, ldb, h->d_perm, n, nb, (int)r0);
-        SC_CUDA(cudaMemsetAsync(h->d_sync, 0, (3 * nch + 2) * sizeof(int32_t), st));
+        SC_CUDA(cudaMemsetAsync(h->d_sync, 0, (3 * nch * kSyncStride + 2) * sizeof(int32_t), st));
         SC_CUDA(cudaMemsetAsync(acc, 0, (size_t)n * nb * sizeof(T), st));
-        int32_t *arrive = h->d_sync, *cnt = h->d_sync + nch, *done = h->d_sync + 2 * nch, *work = h->d_sync + 3 * nch;
+        int32_t *arrive = h->d_sync, *cnt = h->d_sync + nch * kSyncStride, *done = h->d_sync + 2 * nch * kSyncStride,
+                *work = h->d_sync + 3 * nch * kSyncStride;
         const long long spin = (long long)s->opt.spin_limit;
         k_fwd<T><<<h->solve_grid, 256, solve_smem<T>(), st>>>(lnz, h->d_chunks, h->d_solve_tiles, h->solve_tiles,
                                                               h->d_dep_ptr, h->d_dep, h->d_counters + nch, h->d_glbind,
