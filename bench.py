@@ -42,6 +42,23 @@ SAMPLE_SIDE = 32  # oracle sample: the same generator on a 32^3 grid
 TRAFFIC = {("gemm_simt", "fp64", 2, 1.0, 0.125): 2173148928}
 
 
+def reduce_max_over_ranks(dist, values, device):
+    """Max over ranks of per-rank timings (replicas: the job takes as long as
+    its slowest rank). dist None: single process, values unchanged."""
+    if dist is None:
+        return list(values)
+    import torch
+    t = torch.tensor(list(values), device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def whole_job_rate(world, flops, steps, max_ms):
+    """GFLOP/s of the whole job: every rank factors its own copy (weak scaling),
+    so the job does world x flops x steps in the slowest rank's time."""
+    return world * flops * steps / (max_ms * 1e-3) / 1e9
+
+
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -224,12 +241,9 @@ def main():
     fac_ms = sum(a.elapsed_time(b) for a, b, _ in ev)
     sol_ms = sum(b.elapsed_time(c) for _, b, c in ev)
     step_ms = sum(a.elapsed_time(c) for a, _, c in ev)
-    if dist:
-        t = torch.tensor([fac_ms, sol_ms, step_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        fac_ms, sol_ms, step_ms = t.tolist()
+    fac_ms, sol_ms, step_ms = reduce_max_over_ranks(dist, [fac_ms, sol_ms, step_ms], dev)
     K = args.steps
-    value = world * flops * K / (fac_ms * 1e-3) / 1e9
+    value = whole_job_rate(world, flops, K, fac_ms)
 
     # ---- end to end through host buffers (pinned): H2D values + factor + solve with H2D B / D2H X
     vals_h = torch.tensor(A.values, dtype=torch.float64).pin_memory()
