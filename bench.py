@@ -59,6 +59,112 @@ def whole_job_rate(world, flops, steps, max_ms):
     return world * flops * steps / (max_ms * 1e-3) / 1e9
 
 
+def _time_factor_solve(num, dv, Bd, Xd, stream, reps, **solve_kw):
+    """Best of reps (refactor, solve) pairs timed with CUDA events on the stream."""
+    import torch
+    num.solve(Bd, Xd, **solve_kw)
+    best = None
+    for _ in range(reps):
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record(stream)
+        num.refactor(dv)
+        b.record(stream)
+        _, si = num.solve(Bd, Xd, **solve_kw)
+        c.record(stream)
+        torch.cuda.synchronize()
+        t = (a.elapsed_time(b), b.elapsed_time(c))
+        if best is None or sum(t) < sum(best[0]):
+            best = (t, si)
+    return best
+
+
+def _other_workloads(args, sc, inputs, torch, np, dev, stream):
+    """The other workloads of the benchmark's configuration list, each measured
+    once: the 64^2 Laplacian (RL vs RLB in FP64), the batch of 256 2D Laplacians
+    (batched low-precision factor + refinement vs per-matrix FP64) and the
+    anisotropic 3D matrix (FP64 vs TF32x3 + preconditioned CG, PR on vs off)."""
+    out = {}
+    # 64^2 2D Laplacian, FP64, RL (Alg. 4) and RLB (Alg. 5), fundamental supernodes
+    A1, n1 = inputs.workload(1)
+    dv1 = torch.tensor(A1.values, device=dev, dtype=torch.float64)
+    B1 = torch.tensor(np.ascontiguousarray(inputs.rhs(A1.n, n1, inputs.SEED_BASE + 1).T), device=dev)
+    r = {"workload": A1.name, "n": A1.n}
+    for var in ("rl", "rlb"):
+        sy = sc.Symbolic(A1, ordering="grid_nd", grid=A1.grid, variant=var, merge=args.merge)
+        nm = sy.factor(dv1, precision="fp64")
+        (fm, sm_), si = _time_factor_solve(nm, dv1, B1, torch.zeros_like(B1), stream, 5)
+        fl = sy.view()["flops"]
+        r[var] = {"factor_ms": fm, "factor_gflops": fl / (fm * 1e-3) / 1e9, "solve_ms": sm_, "eta_max": si["eta_max"]}
+        nm.free()
+    out["rl_vs_rlb_lap2d_64"] = r
+    # 256 2D Laplacians: one batched factorization vs a loop of per-matrix FP64 factorizations
+    mats, n4 = inputs.workload(4)
+    syms = [sc.Symbolic(A, ordering="grid_nd", grid=A.grid, merge=args.merge) for A in mats]
+    bsym = sc.Symbolic.batch(syms)
+    vals = torch.tensor(np.concatenate([A.values for A in mats]), device=dev, dtype=torch.float64)
+    ntot = sum(A.n for A in mats)
+    Bb = torch.tensor(np.ascontiguousarray(inputs.rhs(ntot, n4, inputs.SEED_BASE + 4).T), device=dev)
+    flb = sum(sy.view()["flops"] for sy in syms)
+    r = {"matrices": len(mats), "n_total": ntot, "sum_cj2": flb}
+    for prec in ("fp32", "tf32x3"):
+        nm = bsym.factor(vals, precision=prec)
+        (fm, sm_), si = _time_factor_solve(nm, vals, Bb, torch.zeros_like(Bb), stream, 3)
+        r["batched_" + prec] = {"factor_ms": fm, "factor_gflops": flb / (fm * 1e-3) / 1e9, "solve_ms": sm_,
+                                "total_ms": fm + sm_, "eta_max": si["eta_max"], "ir_iterations": si["iterations"],
+                                "converged": si["converged"]}
+        nm.free()
+    nums, parts = [], []
+    off = row = 0
+    for A, sy in zip(mats, syms):
+        v = vals[off:off + A.nnz]
+        nums.append(sy.factor(v, precision="fp64"))
+        parts.append((v, Bb[:, row:row + A.n].contiguous()))
+        off += A.nnz
+        row += A.n
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    worst = 0.0
+    for nm, (v, Bi) in zip(nums, parts):
+        nm.refactor(v)
+        _, si = nm.solve(Bi, torch.zeros_like(Bi))
+        worst = max(worst, si["eta_max"])
+    b.record(stream)
+    torch.cuda.synchronize()
+    r["per_matrix_fp64"] = {"total_ms": a.elapsed_time(b), "eta_max": worst}
+    for nm in nums:
+        nm.free()
+    r["speedup_total"] = r["per_matrix_fp64"]["total_ms"] / min(r["batched_fp32"]["total_ms"],
+                                                             r["batched_tf32x3"]["total_ms"])
+    out["batch_lap2d_256"] = r
+    del vals, Bb
+    # anisotropic 3D 7-point (1:1:100 x log-uniform, shift 1e-8): PR on vs off, FP64 vs TF32x3 + CG
+    A5, n5 = inputs.workload(5, args.aniso_scale)
+    dv5 = torch.tensor(A5.values, device=dev, dtype=torch.float64)
+    B5 = torch.tensor(np.ascontiguousarray(inputs.rhs(A5.n, n5, inputs.SEED_BASE + 5).T), device=dev)
+    r = {"workload": A5.name, "n": A5.n, "nrhs": n5}
+    for pr in (True, False):
+        sy = sc.Symbolic(A5, ordering="grid_nd", grid=A5.grid, pr=pr, merge=args.merge)
+        vw = sy.view()
+        key = "pr_on" if pr else "pr_off"
+        r[key] = {"blocks": int(len(vw["blk_first"])), "sum_cj2": vw["flops"]}
+        nm = sy.factor(dv5, precision="tf32x3")
+        (fm, sm_), si = _time_factor_solve(nm, dv5, B5, torch.zeros_like(B5), stream, 2, method="cg",
+                                           max_iterations=1000)
+        r[key]["tf32x3_cg"] = {"factor_ms": fm, "factor_gflops": vw["flops"] / (fm * 1e-3) / 1e9,
+                               "solve_ms": sm_, "total_ms": fm + sm_, "eta_max": si["eta_max"],
+                               "iterations": si["iterations"], "converged": si["converged"]}
+        nm.free()
+        if pr:
+            nm = sy.factor(dv5, precision="fp64")
+            (fm, sm_), si = _time_factor_solve(nm, dv5, B5, torch.zeros_like(B5), stream, 1)
+            r[key]["fp64"] = {"factor_ms": fm, "factor_gflops": vw["flops"] / (fm * 1e-3) / 1e9,
+                              "solve_ms": sm_, "total_ms": fm + sm_, "eta_max": si["eta_max"]}
+            nm.free()
+    out["aniso_3d"] = r
+    return out
+
+
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -66,6 +172,9 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "tf32", "tf32x3"])
+    ap.add_argument("--no-others", action="store_true", help="skip the other workloads' measurements")
+    ap.add_argument("--aniso-scale", type=float, default=0.5,
+                    help="grid scale of the anisotropic 3D workload (1.0 = 128^3)")
     ap.add_argument("--merge", type=float, default=0.125, help="supernode merging budget (Sec. 3.1); 0 = off")
     ap.add_argument("--workload", type=int, default=2, choices=[2, 3],
                     help="2: the benchmark matrix (48^3 7-point); 3: 80^3 27-point (for profiling the TF32 path)")
@@ -364,6 +473,10 @@ def main():
                                                                      compare["tf32x3"]["total_ms"])
         del dv3, B3d, X3d
 
+    others = None
+    if not args.no_others and args.workload == 2 and args.scale == 1.0 and rank == 0:
+        others = _other_workloads(args, sc, inputs, torch, np, dev, stream)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cflops, ctimes, sample = _cpu_sample(2)
@@ -384,7 +497,8 @@ def main():
                            "analyze_s": analyze_s},
                 "factor_ms": fac_ms / K, "solve_ms": sol_ms / K, "eta_max": max(etas),
                 "ir_iterations": max(iters), "gpu_launches": launches, "clocks": clk, "e2e": e2e,
-                "roofline": roofline, "cpu_baseline": cpu, "mixed": mixed, "tf32_ir_vs_fp64_stencil27_80": compare}
+                "roofline": roofline, "cpu_baseline": cpu, "mixed": mixed, "tf32_ir_vs_fp64_stencil27_80": compare,
+                "other_workloads": others}
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

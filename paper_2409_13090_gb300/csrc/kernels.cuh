@@ -234,6 +234,44 @@ __global__ void __launch_bounds__(256) k_potrf(T *__restrict__ lnz, const ChunkD
 // read from shared memory. Storage precision.
 constexpr int kTrsmRows = 32;
 constexpr int kTrsmThreads = kTrsmRows * 4;
+
+// Substitution of one row for a chunk of width <= W (W in {8, 16, 32, 64}): the
+// loops unroll to W, so narrow chunks do not spend FMA-pipe cycles on padding.
+template <typename T, int W>
+__device__ __forceinline__ void trsm_row(const T (*l)[kMaxChunk + 1], const T *rinv, T *xr, bool live, int w, int q,
+                                         T *lnz, float *hi, float *lo) {
+    constexpr int NJ = W / 4;
+    T x[NJ];
+#pragma unroll
+    for (int jj = 0; jj < NJ; jj++) {
+        const int j = q + 4 * jj;
+        x[jj] = (live && j < w) ? xr[j] : T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < W; k++) {
+        T v = (q == (k & 3)) ? x[k >> 2] * rinv[k] : T(0);
+        v = __shfl_sync(0xffffffffu, v, k & 3, 4);
+        if (q == (k & 3)) x[k >> 2] = v;
+#pragma unroll
+        for (int jj = 0; jj < NJ; jj++) {
+            if (4 * jj + 3 > k) {  // resolved at compile time: some lane of the quad has j > k
+                const int j = q + 4 * jj;
+                if (j > k) x[jj] -= v * l[j][k];
+            }
+        }
+    }
+    if (live) {
+#pragma unroll
+        for (int jj = 0; jj < NJ; jj++) {
+            const int j = q + 4 * jj;
+            if (j < w) {
+                xr[j] = x[jj];
+                if (sizeof(T) == 4 && hi) store_split(hi, lo, (xr - lnz) + j, (float)x[jj]);
+            }
+        }
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kTrsmThreads) k_trsm(T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
                                                        const TrsmTile *__restrict__ tiles, float *__restrict__ hi,
@@ -265,35 +303,10 @@ __global__ void __launch_bounds__(kTrsmThreads) k_trsm(T *__restrict__ lnz, cons
     const int row = tl.r0 + threadIdx.x / 4;
     const bool live = row < ch.m;
     T *xr = lnz + ch.off + (int64_t)(live ? row : tl.r0) * ch.ld + ch.c0;
-    T x[kMaxChunk / 4];
-#pragma unroll
-    for (int jj = 0; jj < kMaxChunk / 4; jj++) {
-        const int j = q + 4 * jj;
-        x[jj] = (live && j < w) ? xr[j] : T(0);
-    }
-#pragma unroll
-    for (int k = 0; k < kMaxChunk; k++) {
-        T v = (q == (k & 3)) ? x[k >> 2] * rinv[k] : T(0);
-        v = __shfl_sync(0xffffffffu, v, k & 3, 4);
-        if (q == (k & 3)) x[k >> 2] = v;
-#pragma unroll
-        for (int jj = 0; jj < kMaxChunk / 4; jj++) {
-            if (4 * jj + 3 > k) {  // resolved at compile time: some lane of the quad has j > k
-                const int j = q + 4 * jj;
-                if (j > k) x[jj] -= v * l[j][k];
-            }
-        }
-    }
-    if (live) {
-#pragma unroll
-        for (int jj = 0; jj < kMaxChunk / 4; jj++) {
-            const int j = q + 4 * jj;
-            if (j < w) {
-                xr[j] = x[jj];
-                if (sizeof(T) == 4 && hi) store_split(hi, lo, (xr - lnz) + j, (float)x[jj]);
-            }
-        }
-    }
+    if (w <= 8) trsm_row<T, 8>(l, rinv, xr, live, w, q, lnz, hi, lo);
+    else if (w <= 16) trsm_row<T, 16>(l, rinv, xr, live, w, q, lnz, hi, lo);
+    else if (w <= 32) trsm_row<T, 32>(l, rinv, xr, live, w, q, lnz, hi, lo);
+    else trsm_row<T, 64>(l, rinv, xr, live, w, q, lnz, hi, lo);
 }
 
 // --------------------------------------------------------------------- K3
@@ -478,9 +491,29 @@ __device__ __forceinline__ void warp_blocks(const T *A, const T *Bm, int64_t ld,
         }
 }
 
+// Short inner dimension (K < 32, where most lanes of a warp block would idle):
+// one output per thread, K-loop in registers, outputs dealt over the CTA.
+template <typename T>
+__device__ __forceinline__ void thread_outputs(const T *A, const T *Bm, int64_t ld, int K, int rows, int nb, T *C,
+                                               int64_t ldc, bool lower) {
+    const int total = rows * nb;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int i = e / nb, j = e % nb;
+        if (lower && j > i) continue;
+        const T *a = A + (int64_t)i * ld, *b = Bm + (int64_t)j * ld;
+        T acc = T(0);
+        for (int k = 0; k < K; k++) acc += a[k] * b[k];
+        atomicAdd(C + (int64_t)i * ldc + j, -acc);
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void product_blocks(const T *A, const T *Bm, int64_t ld, int K, int rows, int nb, T *C,
                                                int64_t ldc, bool lower, int &task) {
+    if (K < 32) {
+        thread_outputs(A, Bm, ld, K, rows, nb, C, ldc, lower);
+        return;
+    }
     switch (block_rows(rows, nb, sizeof(T) == 8 ? 2 : 1, lower)) {
         case 1:
             if constexpr (sizeof(T) == 4) warp_blocks<T, 1>(A, Bm, ld, K, rows, nb, C, ldc, lower, task);
