@@ -134,19 +134,27 @@ int run_levels(sc_numeric *h, cudaStream_t st, Prof *prof = nullptr, cudaStream_
             launches++;
         }
         bool join = false;
-        if (p.loop_cnt) {
+        if (p.loop_cnt || p.loopw_cnt) {
             B(kProfLoop);
             cudaStream_t ls = st;
-            if (st2 && (p.gemm_cnt || p.tc_cnt || p.tc64_cnt)) {  // fork: loops and tiled products are independent
-                SC_CUDA(cudaEventRecord(h->ev_fork, st));
+            if (st2 && (p.gemm_cnt || p.tc_cnt || p.tc64_cnt || p.thin_cnt)) {  // fork: loops and tiled products
+                SC_CUDA(cudaEventRecord(h->ev_fork, st));                       // are independent
                 SC_CUDA(cudaStreamWaitEvent(st2, h->ev_fork, 0));
                 ls = st2;
                 join = true;
             }
-            k_rlb_loop<T><<<p.loop_cnt, 256, 0, ls>>>(lnz, h->d_loops + p.loop_off, h->d_sn, h->d_blk, h->d_rbval);
+            if (p.loop_cnt) {
+                k_rlb_loop<T><<<p.loop_cnt, 256, 0, ls>>>(lnz, h->d_loops + p.loop_off, h->d_sn, h->d_blk,
+                                                          h->d_rbval);
+                launches++;
+            }
+            if (p.loopw_cnt) {
+                k_rlb_loop_warp<T><<<(p.loopw_cnt + 7) / 8, 256, 0, ls>>>(lnz, h->d_loops + p.loopw_off, p.loopw_cnt,
+                                                                          h->d_sn, h->d_blk, h->d_rbval);
+                launches++;
+            }
             if (join) SC_CUDA(cudaEventRecord(h->ev_join, st2));
             E();
-            launches++;
         }
         if (p.gemm_cnt) {
             B(kProfGemm);
@@ -327,9 +335,15 @@ void build_plan(const sc_symbolic *s, int precision, Plan &P) {
         P.thin.insert(P.thin.end(), units_thin.begin(), units_thin.end());
         p.thin_cnt = (int32_t)units_thin.size();
         // device-side RLB loops
+        // (items of supernodes narrower than 32 columns: one warp each)
         p.loop_off = (int32_t)P.loops.size();
-        for (const LoopItem &it : L.loops) P.loops.push_back(it);
+        for (const LoopItem &it : L.loops)
+            if (s->sup_ptr[it.sn + 1] - s->sup_ptr[it.sn] >= 32) P.loops.push_back(it);
         p.loop_cnt = (int32_t)P.loops.size() - p.loop_off;
+        p.loopw_off = (int32_t)P.loops.size();
+        for (const LoopItem &it : L.loops)
+            if (s->sup_ptr[it.sn + 1] - s->sup_ptr[it.sn] < 32) P.loops.push_back(it);
+        p.loopw_cnt = (int32_t)P.loops.size() - p.loopw_off;
         P.class_flops[kProfLoop] += L.loop_flops;
         // RL update matrices and assembly
         std::vector<int32_t> rl_small;

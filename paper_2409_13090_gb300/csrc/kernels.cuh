@@ -563,11 +563,12 @@ __global__ void __launch_bounds__(kThinWarps * 32) k_thin_tasks(T *__restrict__ 
 // 32-output warp blocks (warp_block) dealt round-robin to the CTA's warps.
 // Entries are added atomically (other supernodes of the level may update the
 // same ancestor entries).
-template <typename T>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_rlb_loop(T *__restrict__ lnz, const LoopItem *__restrict__ items,
-                                                  const SnDev *__restrict__ sn, const BlkDev *__restrict__ blk,
-                                                  const int32_t *__restrict__ rb_val) {
-    const LoopItem it = items[blockIdx.x];
+// Calls f(A, B, ld, K, rows, nb, C, ldc, lower) for every product of one loop
+// item: the SYRK on B when the item starts at B, then the GEMM of each
+// maximal run B' below B in the item's range.
+template <typename T, typename F>
+__device__ __forceinline__ void item_products(T *lnz, const LoopItem &it, const SnDev *sn, const BlkDev *blk,
+                                              const int32_t *rb_val, F &&f) {
     const SnDev J = sn[it.sn];
     const int K = J.n;
     const T *src = lnz + J.off;
@@ -576,9 +577,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_rlb_loop(T *_
     const int colB = B.first - P.f;
     const int nb = B.size;
     const T *rowsB = src + (int64_t)B.pos * J.ld;
-    int task = 0;
-    if (it.r_lo == it.b)  // SYRK on B: lower-triangular blocks of L_{B,B}
-        product_blocks(rowsB, rowsB, J.ld, K, nb, nb, lnz + P.off + (int64_t)colB * P.ld + colB, P.ld, true, task);
+    if (it.r_lo == it.b)  // SYRK on B: lower triangle of L_{B,B}
+        f(rowsB, rowsB, (int64_t)J.ld, K, nb, nb, lnz + P.off + (int64_t)colB * P.ld + colB, (int64_t)P.ld, true);
     int r = it.r_lo == it.b ? it.b + 1 : it.r_lo;
     while (r < it.r_hi) {
         int e = r;
@@ -588,10 +588,45 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_rlb_loop(T *_
             rows += blk[e].size;
         }
         const int rowP = P.m - 1 - rb_val[B.rb + (r - B.bs)];
-        product_blocks(src + (int64_t)blk[r].pos * J.ld, rowsB, J.ld, K, rows, nb,
-                       lnz + P.off + (int64_t)rowP * P.ld + colB, P.ld, false, task);
+        f(src + (int64_t)blk[r].pos * J.ld, rowsB, (int64_t)J.ld, K, rows, nb,
+          lnz + P.off + (int64_t)rowP * P.ld + colB, (int64_t)P.ld, false);
         r = e + 1;
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_rlb_loop(T *__restrict__ lnz,
+                                                                         const LoopItem *__restrict__ items,
+                                                                         const SnDev *__restrict__ sn,
+                                                                         const BlkDev *__restrict__ blk,
+                                                                         const int32_t *__restrict__ rb_val) {
+    int task = 0;
+    item_products(lnz, items[blockIdx.x], sn, blk, rb_val,
+                  [&](const T *A, const T *Bm, int64_t ld, int K, int rows, int nb, T *C, int64_t ldc, bool lower) {
+                      product_blocks(A, Bm, ld, K, rows, nb, C, ldc, lower, task);
+                  });
+}
+
+// Loop items of a supernode narrower than 32 columns: one warp per item (eight
+// per CTA), one output per lane with the K-loop in registers.
+template <typename T>
+__global__ void __launch_bounds__(256) k_rlb_loop_warp(T *__restrict__ lnz, const LoopItem *__restrict__ items,
+                                                       int count, const SnDev *__restrict__ sn,
+                                                       const BlkDev *__restrict__ blk,
+                                                       const int32_t *__restrict__ rb_val) {
+    const int idx = blockIdx.x * 8 + threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (idx >= count) return;
+    item_products(lnz, items[idx], sn, blk, rb_val,
+                  [&](const T *A, const T *Bm, int64_t ld, int K, int rows, int nb, T *C, int64_t ldc, bool lower) {
+                      for (int e = lane; e < rows * nb; e += 32) {
+                          const int i = e / nb, j = e % nb;
+                          if (lower && j > i) continue;
+                          const T *a = A + (int64_t)i * ld, *b = Bm + (int64_t)j * ld;
+                          T acc = T(0);
+                          for (int k = 0; k < K; k++) acc += a[k] * b[k];
+                          atomicAdd(C + (int64_t)i * ldc + j, -acc);
+                      }
+                  });
 }
 
 // --------------------------------------------------------------------- K4b
