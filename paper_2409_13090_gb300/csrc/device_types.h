@@ -24,6 +24,12 @@ struct TrsmTile {
     int32_t chunk, r0;
 };
 
+// What a CTA of a persistent solve sweep takes at once: tile t0 alone (cnt 0),
+// or narrow tiles t0 .. t0 + cnt - 1, one per warp (cnt 1..8).
+struct SolveUnit {
+    int32_t t0, cnt;
+};
+
 // One output tile of a product task. ks < 0: the whole inner dimension;
 // ks >= 0: only its slice [ks * kSplitK, (ks + 1) * kSplitK), added atomically
 // (SIMT tiles of tasks with few tiles and a long inner dimension).

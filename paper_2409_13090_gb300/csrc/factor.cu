@@ -618,7 +618,7 @@ void numeric_free(sc_numeric *h) {
                     h->d_csr_map, h->d_counters, h->d_xw, h->d_solve_tiles, h->d_sn, h->d_blk, h->d_rbval,
                     h->d_loops, h->d_tmaps, h->d_tmap_of_sn, h->d_err, h->d_inv, h->d_x, h->d_r, h->d_b, h->d_xbest, h->d_y, h->d_z, h->d_acc, h->d_red,
                     h->d_dep_ptr, h->d_dep, h->d_sync, h->d_serr, h->d_hi, h->d_lo, h->d_thin,
-                    h->d_cgz, h->d_cgp, h->d_cgq, h->d_cgs};
+                    h->d_cgz, h->d_cgp, h->d_cgq, h->d_cgs, h->d_solve_units};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->sym) h->sym->refs--;

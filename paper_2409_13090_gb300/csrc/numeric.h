@@ -86,11 +86,12 @@ struct sc_numeric {
     int32_t *d_dep = nullptr;       // distinct chunks the tile's rows fall in
     int32_t *d_sync = nullptr;      // per sweep: arrivals, backward counters, done flags, work counters
     int32_t *d_serr = nullptr;      // nonzero after a bounded wait of a solve sweep gave up
-    int32_t solve_tiles = 0;        // tiles of one sweep
+    int32_t solve_tiles = 0;        // grab units of one sweep
     int32_t solve_grid = 1;         // CTAs of a persistent sweep
     int32_t stall_chunk = -1;       // test hook: chunk whose expected arrivals are raised by one
     void *d_xw = nullptr;           // permuted right-hand side / forward work vector
     sc::TrsmTile *d_solve_tiles = nullptr;
+    sc::SolveUnit *d_solve_units = nullptr;
     int64_t solve_cap = 0;          // rhs capacity of the work vectors
     double *d_x = nullptr, *d_r = nullptr, *d_b = nullptr, *d_xbest = nullptr;
     void *d_y = nullptr, *d_z = nullptr, *d_acc = nullptr;  // permuted work vectors (storage precision)

@@ -168,6 +168,135 @@ __device__ __forceinline__ int grab_tile(int32_t *work, int total, int32_t *err,
     return *slot;
 }
 
+// ---- tiles of narrow chunks (w <= kSmallW): one warp per tile, eight per CTA
+// (a SolveUnit with cnt > 0). v / z of the diagonal step are kept in a
+// per-warp shared-memory slice of kSmallW x kRhsBlk values.
+constexpr int kSmallW = 16;
+
+// Forward step of one narrow tile by one warp: wait for the chunk's arrivals,
+// v = L_cc^{-1} x_c (stored FP32 inverse, or substitution per right-hand side
+// in FP64), subtract L_{rows,c} v from x, count the arrivals. false when a wait
+// gave up.
+template <typename T>
+__device__ bool fwd_tile_warp(const T *__restrict__ lnz, const ChunkDev &ch, const TrsmTile &tl, int t,
+                              const int32_t *__restrict__ dep_ptr, const int32_t *__restrict__ dep,
+                              const int32_t *__restrict__ need, const int32_t *__restrict__ glbind, T *__restrict__ x,
+                              T *__restrict__ y, int nb, const float *__restrict__ inv, int32_t *__restrict__ arrive,
+                              int32_t *__restrict__ err, long long spin_limit, T (*vw)[kRhsBlk]) {
+    const int lane = threadIdx.x % 32, w = ch.w;
+    const bool first = tl.r0 == ch.c0 + w;
+    const int rows = max(0, min(kSolveRows, ch.m - tl.r0));
+    int ok = 1;
+    if (lane == 0) ok = wait_flag(arrive + (int64_t)tl.chunk * kSyncStride, need[tl.chunk], err, spin_limit, 5);
+    if (!__shfl_sync(0xffffffffu, ok, 0)) return false;
+    const T *dg = lnz + ch.off + (int64_t)ch.c0 * ch.ld + ch.c0;
+    if constexpr (sizeof(T) == 4) {
+        const float *iv = inv + ch.inv;
+        for (int e = lane; e < w * nb; e += 32) {
+            const int k = e / nb, r = e % nb;
+            T acc = T(0);
+            for (int q = 0; q <= k; q++) acc += iv[k * w + q] * __ldcg(x + (int64_t)(ch.col0 + q) * nb + r);
+            vw[k][r] = acc;
+            if (first) y[(int64_t)(ch.col0 + k) * nb + r] = acc;
+        }
+    } else {
+        if (lane < nb) {
+            const int r = lane;
+            for (int k = 0; k < w; k++) {
+                T sum = __ldcg(x + (int64_t)(ch.col0 + k) * nb + r);
+                for (int q = 0; q < k; q++) sum -= dg[(int64_t)k * ch.ld + q] * vw[q][r];
+                vw[k][r] = sum / dg[(int64_t)k * ch.ld + k];
+                if (first) y[(int64_t)(ch.col0 + k) * nb + r] = vw[k][r];
+            }
+        }
+    }
+    __syncwarp();
+    for (int e = lane; e < rows * nb; e += 32) {
+        const int i = e / nb, r = e % nb;
+        const T *lr = lnz + ch.off + (int64_t)(tl.r0 + i) * ch.ld + ch.c0;
+        T acc = T(0);
+        for (int k = 0; k < w; k++) acc += lr[k] * vw[k][r];
+        atomicAdd(x + (int64_t)glbind[ch.gl + tl.r0 + i] * nb + r, -acc);
+    }
+    __syncwarp();
+    if (lane == 0) {
+        __threadfence();
+        for (int p = dep_ptr[t]; p < dep_ptr[t + 1]; p++) atomicAdd(arrive + (int64_t)dep[p] * kSyncStride, 1);
+    }
+    __syncwarp();
+    return true;
+}
+
+// Backward step of one narrow tile by one warp: wait until z is final in the
+// chunks its rows fall in, add L_{rows,c}^T z_rows into acc_c, and when it is
+// the chunk's last tile, z_c = L_cc^{-T} (y_c - acc_c) and mark the chunk done.
+template <typename T>
+__device__ bool bwd_tile_warp(const T *__restrict__ lnz, const ChunkDev &ch, const TrsmTile &tl, int t,
+                              const int32_t *__restrict__ dep_ptr, const int32_t *__restrict__ dep,
+                              const int32_t *__restrict__ ntiles, const int32_t *__restrict__ glbind,
+                              const T *__restrict__ y, T *__restrict__ z, T *__restrict__ acc, int nb,
+                              const float *__restrict__ inv, int32_t *__restrict__ cnt, int32_t *__restrict__ done,
+                              int32_t *__restrict__ err, long long spin_limit, T (*vw)[kRhsBlk]) {
+    const int lane = threadIdx.x % 32, w = ch.w;
+    const int rows = max(0, min(kSolveRows, ch.m - tl.r0));
+    if (rows > 0) {
+        int ok = 1;
+        if (lane == 0)
+            for (int p = dep_ptr[t]; p < dep_ptr[t + 1] && ok; p++)
+                ok = wait_flag(done + (int64_t)dep[p] * kSyncStride, 1, err, spin_limit, 6);
+        if (!__shfl_sync(0xffffffffu, ok, 0)) return false;
+        for (int e = lane; e < w * nb; e += 32) {
+            const int k = e / nb, r = e % nb;
+            T sum = T(0);
+            for (int i = 0; i < rows; i++)
+                sum += lnz[ch.off + (int64_t)(tl.r0 + i) * ch.ld + ch.c0 + k] *
+                       __ldcg(z + (int64_t)glbind[ch.gl + tl.r0 + i] * nb + r);
+            atomicAdd(acc + (int64_t)(ch.col0 + k) * nb + r, sum);
+        }
+    }
+    __syncwarp();
+    int last = 0;
+    if (lane == 0) {
+        __threadfence();
+        last = atomicAdd(cnt + (int64_t)tl.chunk * kSyncStride, 1) == ntiles[tl.chunk] - 1;
+        if (last) __threadfence();
+    }
+    if (!__shfl_sync(0xffffffffu, last, 0)) return true;
+    const T *dg = lnz + ch.off + (int64_t)ch.c0 * ch.ld + ch.c0;
+    for (int e = lane; e < w * nb; e += 32) {
+        const int k = e / nb, r = e % nb;
+        const int64_t g = (int64_t)(ch.col0 + k) * nb + r;
+        vw[k][r] = y[g] - __ldcg(acc + g);
+    }
+    __syncwarp();
+    if constexpr (sizeof(T) == 4) {
+        const float *iv = inv + ch.inv;
+        for (int e = lane; e < w * nb; e += 32) {
+            const int k = e / nb, r = e % nb;
+            T sum = T(0);
+            for (int q = k; q < w; q++) sum += iv[q * w + k] * vw[q][r];
+            z[(int64_t)(ch.col0 + k) * nb + r] = sum;
+        }
+    } else {
+        if (lane < nb) {
+            const int r = lane;
+            for (int k = w - 1; k >= 0; k--) {
+                T sum = vw[k][r];
+                for (int q = k + 1; q < w; q++) sum -= dg[(int64_t)q * ch.ld + k] * vw[q][r];
+                vw[k][r] = sum / dg[(int64_t)k * ch.ld + k];
+                z[(int64_t)(ch.col0 + k) * nb + r] = vw[k][r];
+            }
+        }
+    }
+    __syncwarp();
+    if (lane == 0) {
+        __threadfence();
+        atomicExch(done + (int64_t)tl.chunk * kSyncStride, 1);
+    }
+    __syncwarp();
+    return true;
+}
+
 // Forward sweep: one persistent launch over all tiles in level order. A CTA
 // takes the next tile, stages its rows of L and the chunk's diagonal block (or
 // its inverse), waits until every tile that updates the chunk's rows of x has
@@ -177,9 +306,10 @@ __device__ __forceinline__ int grab_tile(int32_t *work, int total, int32_t *err,
 // sweep needs no co-residency guarantee.
 template <typename T>
 __global__ void __launch_bounds__(256) k_fwd(const T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
-                                             const TrsmTile *__restrict__ tiles, int total,
-                                             const int32_t *__restrict__ dep_ptr, const int32_t *__restrict__ dep,
-                                             const int32_t *__restrict__ need, const int32_t *__restrict__ glbind,
+                                             const TrsmTile *__restrict__ tiles, const SolveUnit *__restrict__ units,
+                                             int total, const int32_t *__restrict__ dep_ptr,
+                                             const int32_t *__restrict__ dep, const int32_t *__restrict__ need,
+                                             const int32_t *__restrict__ glbind,
                                              T *__restrict__ x, T *__restrict__ y, int nb, const float *__restrict__ inv,
                                              int32_t *__restrict__ arrive, int32_t *__restrict__ work,
                                              int32_t *__restrict__ err, long long spin_limit) {
@@ -191,8 +321,22 @@ __global__ void __launch_bounds__(256) k_fwd(const T *__restrict__ lnz, const Ch
     auto lr = reinterpret_cast<T (*)[kMaxChunk + 1]>(smem_fwd + sizeof(T) * (kMaxChunk * (kMaxChunk + 1) + 2 * kMaxChunk * kRhsBlk + kMaxChunk));
     __shared__ int s_t, s_ok;
     for (;;) {
-        const int t = grab_tile(work, total, err, &s_t);
-        if (t >= total) break;
+        const int u = grab_tile(work, total, err, &s_t);
+        if (u >= total) break;
+        const SolveUnit su = units[u];
+        if (su.cnt > 0) {  // narrow tiles, one per warp
+            const int wp = threadIdx.x / 32;
+            if (wp < su.cnt) {
+                const int t = su.t0 + wp;
+                const TrsmTile tl = tiles[t];
+                const ChunkDev ch = chunks[tl.chunk];
+                fwd_tile_warp(lnz, ch, tl, t, dep_ptr, dep, need, glbind, x, y, nb, inv, arrive, err, spin_limit,
+                              reinterpret_cast<T (*)[kRhsBlk]>(smem_fwd) + wp * kSmallW);
+            }
+            __syncthreads();
+            continue;
+        }
+        const int t = su.t0;
         const TrsmTile tl = tiles[t];
         const ChunkDev ch = chunks[tl.chunk];
         const int w = ch.w;
@@ -276,9 +420,10 @@ __global__ void __launch_bounds__(256) k_fwd(const T *__restrict__ lnz, const Ch
 // finish solves z_c = L_cc^{-T} (y_c - acc_c) and marks the chunk done.
 template <typename T>
 __global__ void __launch_bounds__(256) k_bwd(const T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
-                                             const TrsmTile *__restrict__ tiles, int total,
-                                             const int32_t *__restrict__ dep_ptr, const int32_t *__restrict__ dep,
-                                             const int32_t *__restrict__ ntiles, const int32_t *__restrict__ glbind,
+                                             const TrsmTile *__restrict__ tiles, const SolveUnit *__restrict__ units,
+                                             int total, const int32_t *__restrict__ dep_ptr,
+                                             const int32_t *__restrict__ dep, const int32_t *__restrict__ ntiles,
+                                             const int32_t *__restrict__ glbind,
                                              const T *__restrict__ y, T *__restrict__ z, T *__restrict__ acc, int nb,
                                              const float *__restrict__ inv, int32_t *__restrict__ cnt,
                                              int32_t *__restrict__ done, int32_t *__restrict__ work,
@@ -294,7 +439,20 @@ __global__ void __launch_bounds__(256) k_bwd(const T *__restrict__ lnz, const Ch
     for (;;) {
         const int tr = grab_tile(work, total, err, &s_t);
         if (tr >= total) break;
-        const int t = total - 1 - tr;
+        const SolveUnit su = units[total - 1 - tr];
+        if (su.cnt > 0) {  // narrow tiles, one per warp
+            const int wp = threadIdx.x / 32;
+            if (wp < su.cnt) {
+                const int t = su.t0 + wp;
+                const TrsmTile tl = tiles[t];
+                const ChunkDev ch = chunks[tl.chunk];
+                bwd_tile_warp(lnz, ch, tl, t, dep_ptr, dep, ntiles, glbind, y, z, acc, nb, inv, cnt, done, err,
+                              spin_limit, reinterpret_cast<T (*)[kRhsBlk]>(smem_bwd) + wp * kSmallW);
+            }
+            __syncthreads();
+            continue;
+        }
+        const int t = su.t0;
         const TrsmTile tl = tiles[t];
         const ChunkDev ch = chunks[tl.chunk];
         const int w = ch.w;
@@ -566,8 +724,30 @@ int ensure_solve(sc_numeric *h, int64_t nrhs) {
             }
             dep_ptr[t + 1] = (int32_t)dep.size();
         }
-        h->solve_tiles = (int32_t)tiles.size();
+        // grab units in level order: a tile of a chunk wider than kSmallW alone (one
+        // CTA), else up to eight consecutive narrow tiles of one level (a warp each)
+        std::vector<SolveUnit> units;
+        {
+            size_t t = 0;
+            for (size_t lv = 0; lv < s->levels.size(); lv++) {
+                size_t tend = t;
+                for (int32_t c : s->levels[lv].chunks) tend += ntiles[c];
+                while (t < tend) {
+                    if (s->chunks[tiles[t].chunk].w > kSmallW) {
+                        units.push_back(SolveUnit{(int32_t)t, 0});
+                        t++;
+                        continue;
+                    }
+                    size_t e = t;
+                    while (e < tend && e - t < 8 && s->chunks[tiles[e].chunk].w <= kSmallW) e++;
+                    units.push_back(SolveUnit{(int32_t)t, (int32_t)(e - t)});
+                    t = e;
+                }
+            }
+        }
+        h->solve_tiles = (int32_t)units.size();
         if ((rc = up(h->d_solve_tiles, tiles))) return rc;
+        if ((rc = up(h->d_solve_units, units))) return rc;
         if ((rc = up(h->d_dep_ptr, dep_ptr))) return rc;
         if ((rc = up(h->d_dep, dep))) return rc;
         // constants: tile counts [nchunks], then expected forward arrivals [nchunks]
@@ -646,11 +826,13 @@ int tri_solve(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, double 
         int32_t *arrive = h->d_sync, *cnt = h->d_sync + nch * kSyncStride, *done = h->d_sync + 2 * nch * kSyncStride,
                 *work = h->d_sync + 3 * nch * kSyncStride;
         const long long spin = (long long)s->opt.spin_limit;
-        k_fwd<T><<<h->solve_grid, 256, solve_smem<T>(), st>>>(lnz, h->d_chunks, h->d_solve_tiles, h->solve_tiles,
+        k_fwd<T><<<h->solve_grid, 256, solve_smem<T>(), st>>>(lnz, h->d_chunks, h->d_solve_tiles, h->d_solve_units,
+                                                              h->solve_tiles,
                                                               h->d_dep_ptr, h->d_dep, h->d_counters + nch, h->d_glbind,
                                                               xw, y, nb, (const float *)h->d_inv, arrive, work,
                                                               h->d_serr, spin);
-        k_bwd<T><<<h->solve_grid, 256, solve_smem<T>(), st>>>(lnz, h->d_chunks, h->d_solve_tiles, h->solve_tiles,
+        k_bwd<T><<<h->solve_grid, 256, solve_smem<T>(), st>>>(lnz, h->d_chunks, h->d_solve_tiles, h->d_solve_units,
+                                                              h->solve_tiles,
                                                               h->d_dep_ptr, h->d_dep, h->d_counters, h->d_glbind, y, z,
                                                               acc, nb, (const float *)h->d_inv, cnt, done, work + 1,
                                                               h->d_serr, spin);
