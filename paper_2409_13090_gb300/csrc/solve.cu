@@ -305,14 +305,15 @@ __device__ bool bwd_tile_warp(const T *__restrict__ lnz, const ChunkDev &ch, con
 // tiles of lower levels, which were taken earlier by running CTAs, so the
 // sweep needs no co-residency guarantee.
 template <typename T>
-__global__ void __launch_bounds__(256) k_fwd(const T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
+__global__ void __launch_bounds__(256, 4) k_fwd(const T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
                                              const TrsmTile *__restrict__ tiles, const SolveUnit *__restrict__ units,
                                              int total, const int32_t *__restrict__ dep_ptr,
                                              const int32_t *__restrict__ dep, const int32_t *__restrict__ need,
                                              const int32_t *__restrict__ glbind,
-                                             T *__restrict__ x, T *__restrict__ y, int nb, const float *__restrict__ inv,
-                                             int32_t *__restrict__ arrive, int32_t *__restrict__ work,
-                                             int32_t *__restrict__ err, long long spin_limit) {
+                                             T *__restrict__ x0, T *__restrict__ y0, int nrhs, int64_t vstride,
+                                             const float *__restrict__ inv, int32_t *__restrict__ arrive0,
+                                             int64_t sstride, int32_t *__restrict__ work, int32_t *__restrict__ err,
+                                             long long spin_limit) {
     extern __shared__ __align__(16) unsigned char smem_fwd[];
     auto l = reinterpret_cast<T (*)[kMaxChunk + 1]>(smem_fwd);
     auto v = reinterpret_cast<T (*)[kRhsBlk]>(smem_fwd + sizeof(T) * kMaxChunk * (kMaxChunk + 1));
@@ -321,9 +322,14 @@ __global__ void __launch_bounds__(256) k_fwd(const T *__restrict__ lnz, const Ch
     auto lr = reinterpret_cast<T (*)[kMaxChunk + 1]>(smem_fwd + sizeof(T) * (kMaxChunk * (kMaxChunk + 1) + 2 * kMaxChunk * kRhsBlk + kMaxChunk));
     __shared__ int s_t, s_ok;
     for (;;) {
-        const int u = grab_tile(work, total, err, &s_t);
-        if (u >= total) break;
-        const SolveUnit su = units[u];
+        const int ug = grab_tile(work, total, err, &s_t);
+        if (ug >= total) break;
+        // unit-major over the right-hand-side blocks: each block keeps its own order
+        const int nblk = (nrhs + kRhsBlk - 1) / kRhsBlk, bk = ug % nblk;
+        const SolveUnit su = units[ug / nblk];
+        const int nb = min(kRhsBlk, nrhs - bk * kRhsBlk);
+        T *x = x0 + bk * vstride, *y = y0 + bk * vstride;
+        int32_t *arrive = arrive0 + bk * sstride;
         if (su.cnt > 0) {  // narrow tiles, one per warp
             const int wp = threadIdx.x / 32;
             if (wp < su.cnt) {
@@ -419,15 +425,16 @@ __global__ void __launch_bounds__(256) k_fwd(const T *__restrict__ lnz, const Ch
 // fall in, and adds L_{rows,c}^T z_rows into acc_c; the chunk's last tile to
 // finish solves z_c = L_cc^{-T} (y_c - acc_c) and marks the chunk done.
 template <typename T>
-__global__ void __launch_bounds__(256) k_bwd(const T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
+__global__ void __launch_bounds__(256, 4) k_bwd(const T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
                                              const TrsmTile *__restrict__ tiles, const SolveUnit *__restrict__ units,
                                              int total, const int32_t *__restrict__ dep_ptr,
                                              const int32_t *__restrict__ dep, const int32_t *__restrict__ ntiles,
                                              const int32_t *__restrict__ glbind,
-                                             const T *__restrict__ y, T *__restrict__ z, T *__restrict__ acc, int nb,
-                                             const float *__restrict__ inv, int32_t *__restrict__ cnt,
-                                             int32_t *__restrict__ done, int32_t *__restrict__ work,
-                                             int32_t *__restrict__ err, long long spin_limit) {
+                                             const T *__restrict__ y0, T *__restrict__ z0, T *__restrict__ acc0,
+                                             int nrhs, int64_t vstride, const float *__restrict__ inv,
+                                             int32_t *__restrict__ cnt0, int32_t *__restrict__ done0, int64_t sstride,
+                                             int32_t *__restrict__ work, int32_t *__restrict__ err,
+                                             long long spin_limit) {
     extern __shared__ __align__(16) unsigned char smem_bwd[];
     auto l = reinterpret_cast<T (*)[kMaxChunk + 1]>(smem_bwd);
     auto vin = reinterpret_cast<T (*)[kRhsBlk]>(smem_bwd + sizeof(T) * kMaxChunk * (kMaxChunk + 1));
@@ -439,7 +446,13 @@ __global__ void __launch_bounds__(256) k_bwd(const T *__restrict__ lnz, const Ch
     for (;;) {
         const int tr = grab_tile(work, total, err, &s_t);
         if (tr >= total) break;
-        const SolveUnit su = units[total - 1 - tr];
+        const int ug = total - 1 - tr;
+        const int nblk = (nrhs + kRhsBlk - 1) / kRhsBlk, bk = ug % nblk;
+        const SolveUnit su = units[ug / nblk];
+        const int nb = min(kRhsBlk, nrhs - bk * kRhsBlk);
+        const T *y = y0 + bk * vstride;
+        T *z = z0 + bk * vstride, *acc = acc0 + bk * vstride;
+        int32_t *cnt = cnt0 + bk * sstride, *done = done0 + bk * sstride;
         if (su.cnt > 0) {  // narrow tiles, one per warp
             const int wp = threadIdx.x / 32;
             if (wp < su.cnt) {
@@ -755,11 +768,10 @@ int ensure_solve(sc_numeric *h, int64_t nrhs) {
         std::copy(ntiles.begin(), ntiles.end(), cnt2.begin());
         std::copy(need.begin(), need.end(), cnt2.begin() + s->chunks.size());
         if ((rc = up(h->d_counters, cnt2))) return rc;
-        // per-sweep synchronisation words, zeroed before every right-hand-side block:
-        // arrivals, backward counters, done flags (nchunks words each, kSyncStride
-        // apart), then the two work counters
-        if (cudaMalloc((void **)&h->d_sync, (3 * s->chunks.size() * kSyncStride + 2) * sizeof(int32_t)) != cudaSuccess)
-            return SC_ERR_OOM;
+        // per-sweep synchronisation words (allocated with the work vectors, zeroed
+        // before every solve): per block of right-hand sides, arrivals, backward
+        // counters and done flags (nchunks words each, kSyncStride apart); then
+        // the two work counters
         if (cudaMalloc((void **)&h->d_serr, sizeof(int32_t)) != cudaSuccess) return SC_ERR_OOM;
         if (cudaMalloc((void **)&h->d_red, 4096 * sizeof(double)) != cudaSuccess) return SC_ERR_OOM;
         if (cudaFuncSetAttribute(k_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, solve_smem<double>()) ||
@@ -780,7 +792,7 @@ int ensure_solve(sc_numeric *h, int64_t nrhs) {
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bwd<float>, 256, solve_smem<float>());
             per_sm = std::max(1, std::min(a, b));
         }
-        h->solve_grid = std::max(1, std::min<int>(h->solve_tiles, per_sm * h->num_sms));
+        h->solve_grid = std::max(1, per_sm * h->num_sms);  // CTAs resident at once; a launch takes fewer if it has less work
         h->solve_ready = true;
     }
     if (nrhs > h->solve_cap) {
@@ -795,13 +807,16 @@ int ensure_solve(sc_numeric *h, int64_t nrhs) {
             if (*p) cudaFree(*p);
             if (cudaMalloc((void **)p, (size_t)n * nrhs * sizeof(double)) != cudaSuccess) return SC_ERR_OOM;
         }
-        void **dw[] = {&h->d_y, &h->d_z, &h->d_acc};
+        const int64_t nblk = (nrhs + kRhsBlk - 1) / kRhsBlk;
+        void **dw[] = {&h->d_y, &h->d_z, &h->d_acc, &h->d_xw};
         for (void **p : dw) {
             if (*p) cudaFree(*p);
-            if (cudaMalloc(p, (size_t)n * kRhsBlk * h->elt) != cudaSuccess) return SC_ERR_OOM;
+            if (cudaMalloc(p, (size_t)n * kRhsBlk * nblk * h->elt) != cudaSuccess) return SC_ERR_OOM;
         }
-        if (h->d_xw) cudaFree(h->d_xw);
-        if (cudaMalloc(&h->d_xw, (size_t)n * kRhsBlk * h->elt) != cudaSuccess) return SC_ERR_OOM;
+        if (h->d_sync) cudaFree(h->d_sync);
+        if (cudaMalloc((void **)&h->d_sync, (3 * s->chunks.size() * kSyncStride * nblk + 2) * sizeof(int32_t)) !=
+            cudaSuccess)
+            return SC_ERR_OOM;
         h->solve_cap = nrhs;
     }
     return SC_OK;
@@ -817,27 +832,37 @@ int tri_solve(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, double 
     const T *lnz = (const T *)h->d_lnz;
     T *xw = (T *)h->d_xw, *y = (T *)h->d_y, *z = (T *)h->d_z, *acc = (T *)h->d_acc;
     const size_t nch = s->chunks.size();
-    for (int64_t r0 = 0; r0 < nrhs; r0 += kRhsBlk) {
-        int nb = (int)std::min<int64_t>(kRhsBlk, nrhs - r0);
-        unsigned g = (unsigned)((n * nb + 255) / 256);
-        k_perm_in<T><<<g, 256, 0, st>>>(xw, B, ldb, h->d_perm, n, nb, (int)r0);
-        SC_CUDA(cudaMemsetAsync(h->d_sync, 0, (3 * nch * kSyncStride + 2) * sizeof(int32_t), st));
-        SC_CUDA(cudaMemsetAsync(acc, 0, (size_t)n * nb * sizeof(T), st));
-        int32_t *arrive = h->d_sync, *cnt = h->d_sync + nch * kSyncStride, *done = h->d_sync + 2 * nch * kSyncStride,
-                *work = h->d_sync + 3 * nch * kSyncStride;
-        const long long spin = (long long)s->opt.spin_limit;
-        k_fwd<T><<<h->solve_grid, 256, solve_smem<T>(), st>>>(lnz, h->d_chunks, h->d_solve_tiles, h->d_solve_units,
-                                                              h->solve_tiles,
-                                                              h->d_dep_ptr, h->d_dep, h->d_counters + nch, h->d_glbind,
-                                                              xw, y, nb, (const float *)h->d_inv, arrive, work,
-                                                              h->d_serr, spin);
-        k_bwd<T><<<h->solve_grid, 256, solve_smem<T>(), st>>>(lnz, h->d_chunks, h->d_solve_tiles, h->d_solve_units,
-                                                              h->solve_tiles,
-                                                              h->d_dep_ptr, h->d_dep, h->d_counters, h->d_glbind, y, z,
-                                                              acc, nb, (const float *)h->d_inv, cnt, done, work + 1,
-                                                              h->d_serr, spin);
-        launches += 4;
-        k_perm_out<T><<<g, 256, 0, st>>>(X, ldx, z, h->d_perm, n, nb, (int)r0, add);
+    // every block of kRhsBlk right-hand sides has its own work vectors and
+    // synchronisation words; one persistent launch per sweep serves them all
+    const int nblk = (int)((nrhs + kRhsBlk - 1) / kRhsBlk);
+    const int64_t vs = n * kRhsBlk, ss = 3 * (int64_t)nch * kSyncStride;
+    for (int bk = 0; bk < nblk; bk++) {
+        const int nb = (int)std::min<int64_t>(kRhsBlk, nrhs - bk * kRhsBlk);
+        const unsigned g = (unsigned)((n * nb + 255) / 256);
+        k_perm_in<T><<<g, 256, 0, st>>>(xw + bk * vs, B, ldb, h->d_perm, n, nb, bk * kRhsBlk);
+        launches++;
+    }
+    SC_CUDA(cudaMemsetAsync(h->d_sync, 0, (nblk * ss + 2) * sizeof(int32_t), st));
+    SC_CUDA(cudaMemsetAsync(acc, 0, (size_t)nblk * vs * sizeof(T), st));
+    int32_t *arrive = h->d_sync, *cnt = h->d_sync + nch * kSyncStride, *done = h->d_sync + 2 * nch * kSyncStride,
+            *work = h->d_sync + nblk * ss;
+    const long long spin = (long long)s->opt.spin_limit;
+    const int total = h->solve_tiles * nblk;
+    const int grid = std::max(1, std::min(total, h->solve_grid));
+    k_fwd<T><<<grid, 256, solve_smem<T>(), st>>>(lnz, h->d_chunks, h->d_solve_tiles, h->d_solve_units, total,
+                                                 h->d_dep_ptr, h->d_dep, h->d_counters + nch, h->d_glbind, xw, y,
+                                                 (int)nrhs, vs, (const float *)h->d_inv, arrive, ss, work, h->d_serr,
+                                                 spin);
+    k_bwd<T><<<grid, 256, solve_smem<T>(), st>>>(lnz, h->d_chunks, h->d_solve_tiles, h->d_solve_units, total,
+                                                 h->d_dep_ptr, h->d_dep, h->d_counters, h->d_glbind, y, z, acc,
+                                                 (int)nrhs, vs, (const float *)h->d_inv, cnt, done, ss, work + 1,
+                                                 h->d_serr, spin);
+    launches += 2;
+    for (int bk = 0; bk < nblk; bk++) {
+        const int nb = (int)std::min<int64_t>(kRhsBlk, nrhs - bk * kRhsBlk);
+        const unsigned g = (unsigned)((n * nb + 255) / 256);
+        k_perm_out<T><<<g, 256, 0, st>>>(X, ldx, z + bk * vs, h->d_perm, n, nb, bk * kRhsBlk, add);
+        launches++;
     }
     SC_CUDA(cudaGetLastError());
     return SC_OK;
