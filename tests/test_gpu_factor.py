@@ -181,3 +181,27 @@ def test_full_workload2_fp64_parity(merge):
     B = inputs.rhs(A.n, nrhs, 2)
     X, info = num.solve(B)
     assert oracle.backward_error(A, B, X).max() <= 1e-14
+
+
+def test_anisotropic_near_singular_fp64_parity_and_cg():
+    """The anisotropic 7-point matrix with the 1e-8 shift (1:1:100 coupling x
+    log-uniform[0.1, 10]; kappa ~ 1e10 at 16^3): FP64 L against the oracle's L,
+    PR on and off, and conjugate gradients preconditioned by the TF32x3 factor
+    reaching eta <= 1e-14 (classical refinement cannot: kappa x u > 1)."""
+    A, nrhs = inputs.workload(5, 0.125)
+    perm0 = oracle.nd_grid(*A.grid, 8)
+    B = inputs.rhs(A.n, 4, 17)
+    for pr in (True, False):
+        sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid, pr=pr)
+        o = oracle.Oracle(A, perm0, pr=pr)
+        assert o.factor() == 0
+        num = sym.factor(A.values, precision="fp64")
+        assert num.rc == 0
+        _check_L(num.export_L(), o.L_supernodal(), 1e-9)
+        X, _ = num.solve(B, refine=True)
+        assert oracle.backward_error(A, B, X).max() <= 1e-14
+    sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid, merge=0.125)
+    num = sym.factor(A.values, precision="tf32x3")
+    X, info = num.solve(B, method="cg", max_iterations=500)
+    assert info["converged"], info
+    assert oracle.backward_error(A, B, X).max() <= 1e-14
