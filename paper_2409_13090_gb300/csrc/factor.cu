@@ -128,7 +128,7 @@ int run_levels(sc_numeric *h, cudaStream_t st, Prof *prof = nullptr, cudaStream_
         }
         if (p.trsm_cnt) {
             B(kProfTrsm);
-            k_trsm<T><<<p.trsm_cnt, kTrsmThreads, 0, st>>>(lnz, h->d_chunks, h->d_trsm + p.trsm_off, h->d_hi,
+            k_trsm<T><<<p.trsm_cnt, trsm_rows<T>() * 4, 0, st>>>(lnz, h->d_chunks, h->d_trsm + p.trsm_off, h->d_hi,
                                                            h->d_lo);
             E();
             launches++;
@@ -291,7 +291,8 @@ void build_plan(const sc_symbolic *s, int precision, Plan &P) {
         p.trsm_off = (int32_t)P.trsm.size();
         for (int32_t c : L.chunks) {
             const ChunkDev &ch = P.cd[c];
-            for (int32_t r0 = ch.c0 + ch.w; r0 < ch.m; r0 += kTrsmRows) P.trsm.push_back(TrsmTile{c, r0});
+            const int32_t rows = precision == SC_FP64 ? trsm_rows<double>() : trsm_rows<float>();
+            for (int32_t r0 = ch.c0 + ch.w; r0 < ch.m; r0 += rows) P.trsm.push_back(TrsmTile{c, r0});
         }
         p.trsm_cnt = (int32_t)P.trsm.size() - p.trsm_off;
         // product tasks: tensor-core tiles (TF32), SIMT tiles, warp tasks

@@ -232,8 +232,12 @@ __global__ void __launch_bounds__(256) k_potrf(T *__restrict__ lnz, const ChunkD
 // the substitution unrolls fully); each pivot value is broadcast from its
 // owner with a width-4 shuffle; pivots are applied as reciprocals; L_cc is
 // read from shared memory. Storage precision.
-constexpr int kTrsmRows = 32;
-constexpr int kTrsmThreads = kTrsmRows * 4;
+// Rows per TRSM tile: 32 in FP32; 16 in FP64, so a wide chunk's rows spread
+// over twice as many SMs (the FP64 pipe of one SM is narrow).
+template <typename T>
+__host__ __device__ constexpr int trsm_rows() {
+    return sizeof(T) == 8 ? 16 : 32;
+}
 
 // Substitution of one row for a chunk of width <= W (W in {8, 16, 32, 64}): the
 // loops unroll to W, so narrow chunks do not spend FMA-pipe cycles on padding.
@@ -273,7 +277,7 @@ __device__ __forceinline__ void trsm_row(const T (*l)[kMaxChunk + 1], const T *r
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kTrsmThreads) k_trsm(T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
+__global__ void __launch_bounds__(trsm_rows<T>() * 4) k_trsm(T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
                                                        const TrsmTile *__restrict__ tiles, float *__restrict__ hi,
                                                        float *__restrict__ lo) {
     __shared__ T l[kMaxChunk][kMaxChunk + 1];
@@ -283,17 +287,21 @@ __global__ void __launch_bounds__(kTrsmThreads) k_trsm(T *__restrict__ lnz, cons
     const int w = ch.w;
     const T *diag = lnz + ch.off + (int64_t)ch.c0 * ch.ld + ch.c0;
     {
-        constexpr int kIters = kMaxChunk * kMaxChunk / kTrsmThreads;
-        T tmp[kIters];
+        // fixed-trip staging through registers, 16 loads in flight per thread
+        constexpr int kThreads = trsm_rows<T>() * 4;
+        constexpr int kIters = kMaxChunk * kMaxChunk / kThreads;
+        for (int it0 = 0; it0 < kIters; it0 += 16) {
+            T tmp[16];
 #pragma unroll
-        for (int it = 0; it < kIters; it++) {
-            const int idx = threadIdx.x + it * kTrsmThreads, r = idx / kMaxChunk, c = idx % kMaxChunk;
-            tmp[it] = (r < w && c <= r) ? diag[(int64_t)r * ch.ld + c] : T(0);
-        }
+            for (int it = 0; it < 16; it++) {
+                const int idx = threadIdx.x + (it0 + it) * kThreads, r = idx / kMaxChunk, c = idx % kMaxChunk;
+                tmp[it] = (r < w && c <= r) ? diag[(int64_t)r * ch.ld + c] : T(0);
+            }
 #pragma unroll
-        for (int it = 0; it < kIters; it++) {
-            const int idx = threadIdx.x + it * kTrsmThreads;
-            l[idx / kMaxChunk][idx % kMaxChunk] = tmp[it];
+            for (int it = 0; it < 16; it++) {
+                const int idx = threadIdx.x + (it0 + it) * kThreads;
+                l[idx / kMaxChunk][idx % kMaxChunk] = tmp[it];
+            }
         }
     }
     __syncthreads();
