@@ -86,43 +86,50 @@ __global__ void k_perm_out(double *__restrict__ X, int64_t ldx, const T *__restr
     *dst = add ? *dst + (double)z[i] : (double)z[i];
 }
 
+// Stages the chunk's diagonal block L_cc and its reciprocal pivots, then scales
+// it for division-free substitution: scale_cols: l[j][k] = L_jk / L_kk (j > k,
+// forward); otherwise l[k][j] = L_kj / L_kk (j < k, backward).
 template <typename T>
-__device__ void load_diag(T (*l)[kMaxChunk + 1], T *rinv, const T *lnz, const ChunkDev &ch) {
+__device__ void load_diag(T (*l)[kMaxChunk + 1], T *rinv, const T *lnz, const ChunkDev &ch, bool scale_cols) {
     stage_block(l, lnz + ch.off + (int64_t)ch.c0 * ch.ld + ch.c0, ch.ld, ch.w, ch.w);
     __syncthreads();
     if (threadIdx.x < ch.w) rinv[threadIdx.x] = T(1) / l[threadIdx.x][threadIdx.x];
     __syncthreads();
+    for (int idx = threadIdx.x; idx < ch.w * ch.w; idx += blockDim.x) {
+        const int r = idx / ch.w, c = idx % ch.w;
+        if (r > c) l[r][c] *= scale_cols ? rinv[c] : rinv[r];
+    }
+    __syncthreads();
 }
 
 // v[0..w) of one right-hand side held by a warp (lane i: entries i and i+32).
-// Forward substitution with L_cc: for k: v_k *= 1/L_kk; v_j -= L_jk v_k (j > k).
+// Forward substitution on the numerators u_k = x_k - sum_{q<k} L_kq v_q with
+// the column-scaled block M_jk = L_jk / L_kk: u_j -= M_jk u_k; then v = u / L_kk.
+// Each step's critical path is one shuffle and one FMA.
 template <typename T>
-__device__ void warp_lower_solve(const T (*l)[kMaxChunk + 1], const T *rinv, int w, T &x0, T &x1) {
+__device__ void warp_lower_solve(const T (*m)[kMaxChunk + 1], const T *rinv, int w, T &x0, T &x1) {
     const int lane = threadIdx.x % 32;
     for (int k = 0; k < w; k++) {
-        const T mine = k < 32 ? x0 : x1;
-        const T v = __shfl_sync(0xffffffffu, mine, k & 31) * rinv[k];
-        if (lane == (k & 31)) {
-            if (k < 32) x0 = v; else x1 = v;
-        }
-        if (lane > k) x0 -= l[lane][k] * v;
-        if (lane + 32 > k && lane + 32 < w) x1 -= l[lane + 32][k] * v;
+        const T uk = __shfl_sync(0xffffffffu, k < 32 ? x0 : x1, k & 31);
+        if (lane > k) x0 -= m[lane][k] * uk;
+        if (lane + 32 > k && lane + 32 < w) x1 -= m[lane + 32][k] * uk;
     }
+    if (lane < w) x0 *= rinv[lane];
+    if (lane + 32 < w) x1 *= rinv[lane + 32];
 }
 
-// Backward substitution with L_cc^T: for k = w-1..0: v_k *= 1/L_kk; v_j -= L_kj v_k (j < k).
+// Backward substitution with L_cc^T on numerators, row-scaled block
+// M_kj = L_kj / L_kk: for k = w-1..0: t_j -= M_kj t_k (j < k); then z = t / L_kk.
 template <typename T>
-__device__ void warp_upper_solve(const T (*l)[kMaxChunk + 1], const T *rinv, int w, T &x0, T &x1) {
+__device__ void warp_upper_solve(const T (*m)[kMaxChunk + 1], const T *rinv, int w, T &x0, T &x1) {
     const int lane = threadIdx.x % 32;
     for (int k = w - 1; k >= 0; k--) {
-        const T mine = k < 32 ? x0 : x1;
-        const T v = __shfl_sync(0xffffffffu, mine, k & 31) * rinv[k];
-        if (lane == (k & 31)) {
-            if (k < 32) x0 = v; else x1 = v;
-        }
-        if (lane < k) x0 -= l[k][lane] * v;
-        if (lane + 32 < k) x1 -= l[k][lane + 32] * v;
+        const T tk = __shfl_sync(0xffffffffu, k < 32 ? x0 : x1, k & 31);
+        if (lane < k) x0 -= m[k][lane] * tk;
+        if (lane + 32 < k) x1 -= m[k][lane + 32] * tk;
     }
+    if (lane < w) x0 *= rinv[lane];
+    if (lane + 32 < w) x1 *= rinv[lane + 32];
 }
 
 // FP32 block products of the sweeps, register-blocked over right-hand sides:
@@ -351,7 +358,7 @@ __global__ void __launch_bounds__(256, 4) k_fwd(const T *__restrict__ lnz, const
         // loads that need no other tile: the tile's rows of L and the diagonal block
         stage_block(lr, lnz + ch.off + (int64_t)tl.r0 * ch.ld + ch.c0, ch.ld, rows, w);
         if constexpr (sizeof(T) == 4) stage_block(l, (const T *)(inv + ch.inv), w, w, w);
-        else load_diag(l, rinv, lnz, ch);
+        else load_diag(l, rinv, lnz, ch, true);
         if (threadIdx.x == 0) s_ok = wait_flag(arrive + (int64_t)tl.chunk * kSyncStride, need[tl.chunk], err, spin_limit, 5);
         __syncthreads();
         if (!s_ok) break;
@@ -535,7 +542,7 @@ __global__ void __launch_bounds__(256, 4) k_bwd(const T *__restrict__ lnz, const
                     if (4 * g + j < nb) z[(int64_t)(ch.col0 + k) * nb + 4 * g + j] = o[j];
             }
         } else {
-            load_diag(l, rinv, lnz, ch);
+            load_diag(l, rinv, lnz, ch, false);
             const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
             for (int r = warp; r < nb; r += blockDim.x / 32) {
                 const int64_t g0 = (int64_t)(ch.col0 + lane) * nb + r, g1 = (int64_t)(ch.col0 + lane + 32) * nb + r;
