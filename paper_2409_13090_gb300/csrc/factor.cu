@@ -95,7 +95,8 @@ struct Prof {
 template <typename T>
 // st2 (optional, graph capture only): a second stream on which each level's
 // device RLB loops run concurrently with the level's tiled products.
-int run_levels(sc_numeric *h, cudaStream_t st, Prof *prof = nullptr, cudaStream_t st2 = nullptr) {
+int run_levels(sc_numeric *h, cudaStream_t st, Prof *prof = nullptr, cudaStream_t st2 = nullptr,
+               cudaStream_t st3 = nullptr) {
     const sc_symbolic *s = h->sym;
     auto B = [&](int cls) {
         if (prof) prof->begin(cls);
@@ -118,7 +119,44 @@ int run_levels(sc_numeric *h, cudaStream_t st, Prof *prof = nullptr, cudaStream_
     E();
     launches += 2;
     const double tau = s->opt.pivot_tau;
-    for (const LevelPlan &p : h->plans) {
+    // tiled products of one dependency class on stream ps
+    auto products = [&](const ProdLists &pl, cudaStream_t ps) -> int {
+        if (pl.gemm_cnt) {
+            B(kProfGemm);
+            k_gemm_tiles<T, kBM, kBN, kBK><<<pl.gemm_cnt, 256, 0, ps>>>(lnz, pool, h->d_tasks,
+                                                                        h->d_gemm + pl.gemm_off);
+            E();
+            launches++;
+        }
+        if constexpr (sizeof(T) == 4) {
+            if (pl.tc_cnt) {
+                B(kProfTc);
+                launch_tc_gemm(128, h->precision == SC_TF32X3, (float *)lnz, h->d_tasks, h->d_gemm + pl.tc_off,
+                               pl.tc_cnt, h->d_tmaps, h->nmaps, h->d_tmap_of_sn, h->d_err,
+                               (long long)s->opt.spin_limit, h->num_sms, ps);
+                E();
+                launches++;
+            }
+            if (pl.tc64_cnt) {
+                B(kProfTc);
+                launch_tc_gemm(64, h->precision == SC_TF32X3, (float *)lnz, h->d_tasks, h->d_gemm + pl.tc64_off,
+                               pl.tc64_cnt, h->d_tmaps, h->nmaps, h->d_tmap_of_sn, h->d_err,
+                               (long long)s->opt.spin_limit, h->num_sms, ps);
+                E();
+                launches++;
+            }
+        }
+        if (pl.thin_cnt) {
+            B(kProfGemm);
+            k_thin_tasks<T><<<pl.thin_cnt, kThinWarps * 32, 0, ps>>>(lnz, h->d_tasks, h->d_thin + pl.thin_off);
+            E();
+            launches++;
+        }
+        return SC_OK;
+    };
+    const size_t nlev = h->plans.size();
+    for (size_t lv = 0; lv < nlev; lv++) {
+        const LevelPlan &p = h->plans[lv];
         if (p.potrf_cnt) {
             B(kProfPotrf);
             k_potrf<T><<<p.potrf_cnt, 256, kPotrfSmem, st>>>(lnz, h->d_chunks, h->d_potrf + p.potrf_off, h->d_adiag,
@@ -133,12 +171,24 @@ int run_levels(sc_numeric *h, cudaStream_t st, Prof *prof = nullptr, cudaStream_
             E();
             launches++;
         }
+        // Lookahead: level lv's products into chunks two or more levels up run on
+        // st3, overlapping level lv+1's POTRF, TRSM and device loops; level lv+1's
+        // own products wait for them, so no target is written by two streams at
+        // once (rest(lv) and crit(lv) have disjoint targets, and so have rest(lv)
+        // and the device loops, which never target a supernode being factored).
+        if (st3) {
+            SC_CUDA(cudaEventRecord(h->ev_trsm, st));
+            SC_CUDA(cudaStreamWaitEvent(st3, h->ev_trsm, 0));
+            int rc = products(p.rest, st3);
+            if (rc) return rc;
+            SC_CUDA(cudaEventRecord(h->ev_rest[lv % 2], st3));
+        }
         bool join = false;
         if (p.loop_cnt || p.loopw_cnt) {
             B(kProfLoop);
             cudaStream_t ls = st;
-            if (st2 && (p.gemm_cnt || p.tc_cnt || p.tc64_cnt || p.thin_cnt)) {  // fork: loops and tiled products
-                SC_CUDA(cudaEventRecord(h->ev_fork, st));                       // are independent
+            if (st2 && (p.crit.any() || p.small_cnt)) {  // fork: loops and tiled products are independent
+                SC_CUDA(cudaEventRecord(h->ev_fork, st));
                 SC_CUDA(cudaStreamWaitEvent(st2, h->ev_fork, 0));
                 ls = st2;
                 join = true;
@@ -156,35 +206,11 @@ int run_levels(sc_numeric *h, cudaStream_t st, Prof *prof = nullptr, cudaStream_
             if (join) SC_CUDA(cudaEventRecord(h->ev_join, st2));
             E();
         }
-        if (p.gemm_cnt) {
-            B(kProfGemm);
-            k_gemm_tiles<T, kBM, kBN, kBK><<<p.gemm_cnt, 256, 0, st>>>(lnz, pool, h->d_tasks, h->d_gemm + p.gemm_off);
-            E();
-            launches++;
-        }
-        if constexpr (sizeof(T) == 4) {
-            if (p.tc_cnt) {
-                B(kProfTc);
-                launch_tc_gemm(128, h->precision == SC_TF32X3, (float *)lnz, h->d_tasks, h->d_gemm + p.tc_off,
-                               p.tc_cnt, h->d_tmaps, h->nmaps, h->d_tmap_of_sn, h->d_err,
-                               (long long)s->opt.spin_limit, h->num_sms, st);
-                E();
-                launches++;
-            }
-            if (p.tc64_cnt) {
-                B(kProfTc);
-                launch_tc_gemm(64, h->precision == SC_TF32X3, (float *)lnz, h->d_tasks, h->d_gemm + p.tc64_off,
-                               p.tc64_cnt, h->d_tmaps, h->nmaps, h->d_tmap_of_sn, h->d_err,
-                               (long long)s->opt.spin_limit, h->num_sms, st);
-                E();
-                launches++;
-            }
-        }
-        if (p.thin_cnt) {
-            B(kProfGemm);
-            k_thin_tasks<T><<<p.thin_cnt, kThinWarps * 32, 0, st>>>(lnz, h->d_tasks, h->d_thin + p.thin_off);
-            E();
-            launches++;
+        {
+            if (st3 && lv >= 1) SC_CUDA(cudaStreamWaitEvent(st, h->ev_rest[(lv - 1) % 2], 0));
+            int rc = products(p.crit, st);
+            if (rc) return rc;
+            if (!st3 && (rc = products(p.rest, st))) return rc;
         }
         if (p.small_cnt) {
             B(kProfSmall);
@@ -216,6 +242,7 @@ int run_levels(sc_numeric *h, cudaStream_t st, Prof *prof = nullptr, cudaStream_
             launches++;
         }
     }
+    if (st3 && nlev) SC_CUDA(cudaStreamWaitEvent(st, h->ev_rest[(nlev - 1) % 2], 0));  // join the lookahead branch
     if constexpr (sizeof(T) == 4) {
         // diagonal-block inverses for the solve, all chunks in one launch
         const int32_t nch = (int32_t)s->chunks.size();
@@ -258,7 +285,9 @@ struct Plan {
     double class_flops[kProfClasses] = {};
 };
 
-void build_plan(const sc_symbolic *s, int precision, Plan &P) {
+// lookahead: split each level's tiled products into those that target chunks
+// of the next level (crit) and the rest (targets two or more levels up).
+void build_plan(const sc_symbolic *s, int precision, Plan &P, bool lookahead) {
     P.cd.resize(s->chunks.size());
     int64_t inv = 0;
     for (size_t c = 0; c < s->chunks.size(); c++) {
@@ -297,44 +326,48 @@ void build_plan(const sc_symbolic *s, int precision, Plan &P) {
         p.trsm_cnt = (int32_t)P.trsm.size() - p.trsm_off;
         // product tasks: tensor-core tiles (TF32), SIMT tiles, warp tasks
         std::vector<int32_t> ids_small;
-        std::vector<ThinUnit> units_thin;
-        std::vector<GemmTile> g_simt, g_tc, g_tc64;
-        for (const Task &t : L.tasks) {
+        std::vector<ThinUnit> units_thin[2];
+        std::vector<GemmTile> g_simt[2], g_tc[2], g_tc64[2];
+        for (Task t : L.tasks) {
             int32_t id = (int32_t)P.tasks.size();
+            const int cls = lookahead && !(t.flags & kTaskCrit) ? 1 : 0;  // 0 crit, 1 rest
             P.tasks.push_back(t);
             const int bn = tc ? tc_width(t, tmap_of_sn) : 0;
             if (is_small(t)) {
                 ids_small.push_back(id);
                 P.class_flops[kProfSmall] += task_flops(t);
             } else if (bn) {
-                tc_tiles_of(t, id, bn, bn == 128 ? g_tc : g_tc64);
+                tc_tiles_of(t, id, bn, bn == 128 ? g_tc[cls] : g_tc64[cls]);
                 P.class_flops[kProfTc] += task_flops(t);
             } else if (std::min(t.m, t.n) <= kThinDim && !(t.flags & kTaskStoreU)) {
                 // a 64 x 64 tile would be mostly padding: warp blocks, kThinWarps per CTA
                 const int ni = block_rows(t.m, t.n, precision == SC_FP64 ? 2 : 1, (t.flags & kTaskLower) != 0);
                 const int nblk = ((t.m + ni - 1) / ni) * ((t.n + 32 / ni - 1) / (32 / ni));
-                for (int b0 = 0; b0 < nblk; b0 += kThinWarps) units_thin.push_back(ThinUnit{id, b0});
+                for (int b0 = 0; b0 < nblk; b0 += kThinWarps) units_thin[cls].push_back(ThinUnit{id, b0});
                 P.class_flops[kProfGemm] += task_flops(t);
             } else {
-                tiles_of(t, id, g_simt);
+                tiles_of(t, id, g_simt[cls]);
                 P.class_flops[kProfGemm] += task_flops(t);
             }
         }
-        p.gemm_off = (int32_t)P.gemm.size();
-        P.gemm.insert(P.gemm.end(), g_simt.begin(), g_simt.end());
-        p.gemm_cnt = (int32_t)g_simt.size();
-        p.tc_off = (int32_t)P.gemm.size();
-        P.gemm.insert(P.gemm.end(), g_tc.begin(), g_tc.end());
-        p.tc_cnt = (int32_t)g_tc.size();
-        p.tc64_off = (int32_t)P.gemm.size();
-        P.gemm.insert(P.gemm.end(), g_tc64.begin(), g_tc64.end());
-        p.tc64_cnt = (int32_t)g_tc64.size();
+        for (int cls = 0; cls < 2; cls++) {
+            ProdLists &pl = cls == 0 ? p.crit : p.rest;
+            pl.gemm_off = (int32_t)P.gemm.size();
+            P.gemm.insert(P.gemm.end(), g_simt[cls].begin(), g_simt[cls].end());
+            pl.gemm_cnt = (int32_t)g_simt[cls].size();
+            pl.tc_off = (int32_t)P.gemm.size();
+            P.gemm.insert(P.gemm.end(), g_tc[cls].begin(), g_tc[cls].end());
+            pl.tc_cnt = (int32_t)g_tc[cls].size();
+            pl.tc64_off = (int32_t)P.gemm.size();
+            P.gemm.insert(P.gemm.end(), g_tc64[cls].begin(), g_tc64[cls].end());
+            pl.tc64_cnt = (int32_t)g_tc64[cls].size();
+            pl.thin_off = (int32_t)P.thin.size();
+            P.thin.insert(P.thin.end(), units_thin[cls].begin(), units_thin[cls].end());
+            pl.thin_cnt = (int32_t)units_thin[cls].size();
+        }
         p.small_off = (int32_t)P.small.size();
         P.small.insert(P.small.end(), ids_small.begin(), ids_small.end());
         p.small_cnt = (int32_t)ids_small.size();
-        p.thin_off = (int32_t)P.thin.size();
-        P.thin.insert(P.thin.end(), units_thin.begin(), units_thin.end());
-        p.thin_cnt = (int32_t)units_thin.size();
         // device-side RLB loops
         // (items of supernodes narrower than 32 columns: one warp each)
         p.loop_off = (int32_t)P.loops.size();
@@ -376,14 +409,14 @@ void build_plan(const sc_symbolic *s, int precision, Plan &P) {
 
 int plan_stats(const sc_symbolic *s, int precision, int64_t *out, int nout) {
     Plan P;
-    build_plan(s, precision, P);
+    build_plan(s, precision, P, false);
     int64_t small_tasks = 0, tile_tasks = 0;
     for (const LevelPlan &l : P.levels) small_tasks += l.small_cnt + l.rls_cnt;
     tile_tasks = (int64_t)P.tasks.size() - small_tasks;
     int64_t tc_tiles = 0, simt_tiles = 0;
     for (const LevelPlan &l : P.levels) {
-        tc_tiles += l.tc_cnt + l.tc64_cnt;
-        simt_tiles += l.gemm_cnt + l.rlg_cnt;
+        tc_tiles += l.crit.tc_cnt + l.crit.tc64_cnt + l.rest.tc_cnt + l.rest.tc64_cnt;
+        simt_tiles += l.crit.gemm_cnt + l.rest.gemm_cnt + l.rlg_cnt;
     }
     int64_t v[] = {(int64_t)P.levels.size(), (int64_t)P.cd.size(), (int64_t)P.tasks.size(), small_tasks, tile_tasks,
                    simt_tiles, tc_tiles, (int64_t)P.trsm.size(), (int64_t)P.rlpairs.size(), (int64_t)P.loops.size()};
@@ -450,7 +483,12 @@ int numeric_create(sc_symbolic *s, int precision, sc_numeric **out) {
         if ((rc = upload(h->d_tmap_of_sn, tmap_of_sn, bytes))) return fail(rc);
     }
     Plan P;
-    build_plan(s, precision, P);
+    // lookahead needs the captured graph's concurrent branches (RLB schedule);
+    // it pays for FP32-storage factors, whose POTRF / TRSM latency is large next
+    // to their products, not for FP64 (DFMA-bound products, where splitting a
+    // level's products into two launches leaves SMs idle)
+    h->lookahead = h->use_graph && s->opt.variant == SC_RLB && precision != SC_FP64;
+    build_plan(s, precision, P, h->lookahead);
     if (precision != SC_FP64) {
         if (cudaMalloc(&h->d_inv, (size_t)std::max<int64_t>(1, P.inv_size) * sizeof(float)) != cudaSuccess)
             return fail(SC_ERR_OOM);
@@ -519,10 +557,18 @@ int numeric_factor(sc_numeric *h, const double *values, int on_device, cudaStrea
             if (!h->cap_stream2) SC_CUDA(cudaStreamCreateWithFlags(&h->cap_stream2, cudaStreamNonBlocking));
             if (!h->ev_fork) SC_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
             if (!h->ev_join) SC_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+            cudaStream_t st3 = nullptr;
+            if (h->lookahead) {
+                if (!h->cap_stream3) SC_CUDA(cudaStreamCreateWithFlags(&h->cap_stream3, cudaStreamNonBlocking));
+                if (!h->ev_trsm) SC_CUDA(cudaEventCreateWithFlags(&h->ev_trsm, cudaEventDisableTiming));
+                for (auto &e : h->ev_rest)
+                    if (!e) SC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+                st3 = h->cap_stream3;
+            }
             cudaGraph_t g;
             SC_CUDA(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-            rc = h->precision == SC_FP64 ? run_levels<double>(h, h->cap_stream, nullptr, h->cap_stream2)
-                                         : run_levels<float>(h, h->cap_stream, nullptr, h->cap_stream2);
+            rc = h->precision == SC_FP64 ? run_levels<double>(h, h->cap_stream, nullptr, h->cap_stream2, st3)
+                                         : run_levels<float>(h, h->cap_stream, nullptr, h->cap_stream2, st3);
             cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &g);
             if (rc) return rc;
             SC_CUDA(ce);
@@ -611,8 +657,9 @@ void numeric_free(sc_numeric *h) {
         if (g) cudaGraphExecDestroy(g);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->cap_stream2) cudaStreamDestroy(h->cap_stream2);
-    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
-    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->cap_stream3) cudaStreamDestroy(h->cap_stream3);
+    for (cudaEvent_t e : {h->ev_fork, h->ev_join, h->ev_trsm, h->ev_rest[0], h->ev_rest[1]})
+        if (e) cudaEventDestroy(e);
     void *ptrs[] = {h->d_lnz, h->d_pool, h->d_valmap, h->d_values, h->d_diagpos, h->d_adiag, h->d_info,
                     h->d_chunks, h->d_potrf, h->d_trsm, h->d_gemm, h->d_small, h->d_tasks, h->d_rlpairs,
                     h->d_rlrelind, h->d_glbind, h->d_perm, h->d_csr_ptr, h->d_csr_col, h->d_csr_val,

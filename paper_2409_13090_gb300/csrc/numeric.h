@@ -11,15 +11,23 @@
 
 namespace sc {
 
-// Launch plan of one level: offsets/counts into the flat device work lists.
-struct LevelPlan {
-    int32_t potrf_off = 0, potrf_cnt = 0;   // chunk ids
-    int32_t trsm_off = 0, trsm_cnt = 0;     // TrsmTile
+// The product launches of one level that share a dependency class.
+struct ProdLists {
     int32_t gemm_off = 0, gemm_cnt = 0;     // GemmTile (SIMT)
     int32_t tc_off = 0, tc_cnt = 0;         // GemmTile (tensor cores, 128-column tiles)
     int32_t tc64_off = 0, tc64_cnt = 0;     // GemmTile (tensor cores, 64-column tiles)
-    int32_t small_off = 0, small_cnt = 0;   // task ids (warp kernel)
     int32_t thin_off = 0, thin_cnt = 0;     // ThinUnits of tasks with min(m, n) <= 8 (warp-block kernel)
+    bool any() const { return gemm_cnt || tc_cnt || tc64_cnt || thin_cnt; }
+};
+
+// Launch plan of one level: offsets/counts into the flat device work lists.
+// With lookahead, `crit` holds the products into chunks of the next level and
+// `rest` the others, which may run concurrently with the next level.
+struct LevelPlan {
+    int32_t potrf_off = 0, potrf_cnt = 0;   // chunk ids
+    int32_t trsm_off = 0, trsm_cnt = 0;     // TrsmTile
+    ProdLists crit, rest;
+    int32_t small_off = 0, small_cnt = 0;   // task ids (warp kernel)
     int32_t rlg_off = 0, rlg_cnt = 0;       // GemmTile of RL update matrices
     int32_t rls_off = 0, rls_cnt = 0;       // task ids of small RL update matrices
     int32_t loop_off = 0, loop_cnt = 0;     // LoopItem (device-side RLB loops), one CTA per item
@@ -115,8 +123,11 @@ struct sc_numeric {
     // graph of the factorization (captured on first use on a stream)
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t cap_stream = nullptr;
-    cudaStream_t cap_stream2 = nullptr;  // side branch of the captured factor graph
+    cudaStream_t cap_stream2 = nullptr;  // side branch of the captured factor graph (device loops)
+    cudaStream_t cap_stream3 = nullptr;  // lookahead branch (products not needed by the next level)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_trsm = nullptr, ev_rest[2] = {nullptr, nullptr};
+    bool lookahead = false;              // plan split into crit / rest products
     bool use_graph = true;
     int num_sms = 152;
 };

@@ -23,11 +23,13 @@ struct Task {
     int32_t a_row;  // first row of A in Lnz(J)
     int32_t b_row;  // first row of B in Lnz(J)
     int32_t kx0;    // first column of A and B in Lnz(J)
+    int32_t tcol;   // global column of C's first column (its chunk decides kTaskCrit)
 };
 enum : int32_t {
     kTaskLower = 1,      // only entries with local row >= local column are written
     kTaskStoreU = 2,     // C is an RL update matrix: C = -A B^T (plain store, no accumulate)
     kTaskExclusive = 4,  // no other task of the level writes C: plain read-modify-write
+    kTaskCrit = 8,       // C lies in a chunk of the next level: must finish before that level
 };
 
 #ifdef __CUDACC__

@@ -82,37 +82,32 @@ int build_schedule(sc_symbolic *s) {
                 const int32_t mstart = ch.c0 / Wm * Wm;
                 const int32_t mend = std::min(mstart + Wm, nJ);
                 const int32_t r0 = ch.c0 + ch.w;
-                if (r0 < mend) {
-                    Task t;
-                    t.a_off = offJ + (int64_t)r0 * ldJ + ch.c0;
-                    t.b_off = t.a_off;
-                    t.c_off = offJ + (int64_t)r0 * ldJ + r0;
-                    t.lds = ldJ;
-                    t.ldc = ldJ;
-                    t.m = (int32_t)(mJ - r0);
-                    t.n = mend - r0;
-                    t.k = ch.w;
-                    t.flags = kTaskLower | kTaskExclusive;
-                    t.src = J;
-                    t.a_row = t.b_row = r0;
-                    t.kx0 = ch.c0;
-                    L.tasks.push_back(t);
-                } else {
-                    Task t;
-                    t.a_off = offJ + (int64_t)mend * ldJ + mstart;
-                    t.b_off = t.a_off;
-                    t.c_off = offJ + (int64_t)mend * ldJ + mend;
-                    t.lds = ldJ;
-                    t.ldc = ldJ;
-                    t.m = (int32_t)(mJ - mend);
-                    t.n = nJ - mend;
-                    t.k = mend - mstart;
-                    t.flags = kTaskLower | kTaskExclusive;
-                    t.src = J;
-                    t.a_row = t.b_row = mend;
-                    t.kx0 = mstart;
-                    L.tasks.push_back(t);
-                }
+                // the update of the next chunk's columns is split off, so the next
+                // level's POTRF waits only for it (kTaskCrit, set below)
+                auto lower_update = [&](int32_t c_first, int32_t c_end, int32_t kx0, int32_t K) {
+                    const int32_t split = std::min(c_end, r0 + std::min(W, nJ - r0));
+                    for (int32_t part = 0; part < 2; part++) {
+                        const int32_t a = part == 0 ? c_first : split, e = part == 0 ? split : c_end;
+                        if (a >= e) continue;
+                        Task t;
+                        t.a_off = offJ + (int64_t)a * ldJ + kx0;
+                        t.b_off = t.a_off;
+                        t.c_off = offJ + (int64_t)a * ldJ + a;
+                        t.lds = ldJ;
+                        t.ldc = ldJ;
+                        t.m = (int32_t)(mJ - a);
+                        t.n = e - a;
+                        t.k = K;
+                        t.flags = kTaskLower | kTaskExclusive;
+                        t.src = J;
+                        t.a_row = t.b_row = a;
+                        t.kx0 = kx0;
+                        t.tcol = s->sup_ptr[J] + a;
+                        L.tasks.push_back(t);
+                    }
+                };
+                if (r0 < mend) lower_update(r0, mend, ch.c0, ch.w);
+                else lower_update(mend, nJ, mstart, mend - mstart);
                 continue;
             }
             int64_t b0 = s->blk_ptr[J], b1 = s->blk_ptr[J + 1];
@@ -162,6 +157,7 @@ int build_schedule(sc_symbolic *s) {
                             t.src = J;
                             t.a_row = t.b_row = (int32_t)bpos[b - b0];
                             t.kx0 = 0;
+                            t.tcol = fP + colB;
                             L.tasks.push_back(t);
                             item.r_lo = (int32_t)b + 1;  // no SYRK in the device loop
                         } else {
@@ -193,6 +189,7 @@ int build_schedule(sc_symbolic *s) {
                                 g.a_row = (int32_t)bpos[r - b0];
                                 g.b_row = (int32_t)bpos[b - b0];
                                 g.kx0 = 0;
+                                g.tcol = fP + colB;
                                 L.tasks.push_back(g);
                                 // a tiled run ends the current item; the next item starts after it
                                 if (open) {
@@ -237,6 +234,7 @@ int build_schedule(sc_symbolic *s) {
                 t.src = J;
                 t.a_row = t.b_row = nJ;
                 t.kx0 = 0;
+                t.tcol = 0;
                 L.rl_tasks.push_back(t);
                 int64_t u_off = L.rl_pool;
                 L.rl_pool += (int64_t)sJ * sJ;
@@ -284,6 +282,10 @@ int build_schedule(sc_symbolic *s) {
         }
         s->rl_pool_max = std::max(s->rl_pool_max, L.rl_pool);
     }
+    // a product is critical when its target lies in a chunk of the next level
+    for (int32_t lv = 0; lv < nlev; lv++)
+        for (Task &t : s->levels[lv].tasks)
+            if (clevel[s->chunk_of_col[t.tcol]] == lv + 1) t.flags |= kTaskCrit;
     return SC_OK;
 }
 
