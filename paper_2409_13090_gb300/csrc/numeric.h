@@ -32,7 +32,6 @@ struct LevelPlan {
     int32_t rls_off = 0, rls_cnt = 0;       // task ids of small RL update matrices
     int32_t loop_off = 0, loop_cnt = 0;     // LoopItem (device-side RLB loops), one CTA per item
     int32_t loopw_off = 0, loopw_cnt = 0;   // LoopItem of supernodes narrower than 32 columns, one warp per item
-    int32_t loop_smem = 0;                  // dynamic shared memory of the loop launch
     int32_t rlp_off = 0, rlp_cnt = 0;       // RLPair
     int64_t rlp_max = 0;                    // largest assembly work item (elements)
     // solve
