@@ -232,7 +232,7 @@ class Symbolic:
 
     def __init__(self, A=None, *, ordering="natural", grid=None, nd_leaf=8, user_perm=None, pr=True,
                  variant="rlb", precision="fp64", chunk=64, ir_tol=1e-14, ir_maxit=30, use_graph=True,
-                 merge=0.0, spin_limit=None, _handle=None, _parts=None):
+                 merge=0.0, spin_limit=None, pivot_tau=None, _handle=None, _parts=None):
         self._parts = _parts
         if _handle is not None:
             self._h = _handle
@@ -258,6 +258,8 @@ class Symbolic:
         o.merge_frac = float(merge)
         if spin_limit is not None:
             o.spin_limit = int(spin_limit)
+        if pivot_tau is not None:
+            o.pivot_tau = float(pivot_tau)
         colptr = np.ascontiguousarray(A.colptr, np.int64)
         rowind = np.ascontiguousarray(A.rowind, np.int32)
         rc, h = sc_analyze(A.n, colptr, rowind, o)

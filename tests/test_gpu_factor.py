@@ -205,3 +205,35 @@ def test_anisotropic_near_singular_fp64_parity_and_cg():
     X, info = num.solve(B, method="cg", max_iterations=500)
     assert info["converged"], info
     assert oracle.backward_error(A, B, X).max() <= 1e-14
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+def test_low_pivot_blocks_redone_in_fp64(prec):
+    """The low-precision pivot rule: a diagonal block whose FP32 pivot d falls to
+    tau * |A_jj| or below is refactored in FP64 from the same stored values, and
+    the count is reported. With tau = 0.5 many blocks qualify (pivots drop below
+    half the input diagonal as elimination proceeds); with the default 2^-10
+    none do on this well-conditioned matrix. Either way L matches the oracle to
+    FP32 accuracy and refinement reaches eta <= 1e-14; the redone blocks are
+    FP64-accurate, so the factor with tau = 0.5 is no further from the oracle
+    (within a factor 2 for the FP32 rounding of the rest)."""
+    A = _grid_case("diff7_13")
+    _, Lo = _oracle_L(A, oracle.nd_grid(*A.grid, 8))
+    scale = np.abs(Lo).max()
+    B = inputs.rhs(A.n, 2, 19)
+    errs = {}
+    for tau in (2.0 ** -10, 0.5):
+        sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid, pivot_tau=tau)
+        num = sym.factor(A.values, precision=prec)
+        assert num.rc == 0
+        fb = num.info.pivot_fallbacks
+        if tau == 0.5:
+            assert fb > 0
+        else:
+            assert fb == 0
+        errs[tau] = np.abs(num.export_L() - Lo).max() / scale
+        assert errs[tau] <= 1e-3
+        X, info = num.solve(B)
+        assert info["converged"], info
+        assert oracle.backward_error(A, B, X).max() <= 1e-14
+    assert errs[0.5] <= errs[2.0 ** -10] * 2 + 1e-12
