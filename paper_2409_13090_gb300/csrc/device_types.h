@@ -31,12 +31,14 @@ struct SolveUnit {
 };
 
 // One output tile of a product task. ks < 0: the whole inner dimension;
-// ks >= 0: only its slice [ks * kSplitK, (ks + 1) * kSplitK), added atomically
-// (SIMT tiles of tasks with few tiles and a long inner dimension).
+// ks >= 0: only its slice [ks * S, (ks + 1) * S), added atomically, with
+// S = kSplitKCrit for a critical task and kSplitK otherwise (SIMT tiles of
+// critical tasks, and of tasks with few tiles and a long inner dimension).
 struct GemmTile {
     int32_t task, tm, tn, ks;
 };
 constexpr int kSplitK = 256;
+constexpr int kSplitKCrit = 32;  // slice width of split critical tasks (kTaskCrit)
 
 // Work of one CTA of the thin-product kernel: warp blocks blk0 .. blk0 + 3 of
 // a task (blocks numbered row-major over the task's NI x NJ block grid).

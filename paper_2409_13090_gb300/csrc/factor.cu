@@ -50,9 +50,14 @@ double task_flops(const Task &t) {
 void tiles_of(const Task &t, int32_t id, std::vector<GemmTile> &out) {
     int tm = (t.m + kBM - 1) / kBM, tn = (t.n + kBN - 1) / kBN;
     // a task of few tiles with a long inner dimension is split along it, so its
-    // tiles do not serialise a level (an RL update matrix is stored, not added:
-    // never split)
-    const int slices = (tm * tn <= 8 && t.k > 2 * kSplitK && !(t.flags & kTaskStoreU)) ? (t.k + kSplitK - 1) / kSplitK : 0;
+    // tiles do not serialise a level; a critical task (the next level waits for
+    // it) is split into slices of kSplitKCrit so its latency is short (an RL
+    // update matrix is stored, not added: never split)
+    int slices = 0;
+    if (!(t.flags & kTaskStoreU)) {
+        if ((t.flags & kTaskCrit) && t.k >= 2 * kSplitKCrit) slices = (t.k + kSplitKCrit - 1) / kSplitKCrit;
+        else if (tm * tn <= 8 && t.k > 2 * kSplitK) slices = (t.k + kSplitK - 1) / kSplitK;
+    }
     for (int i = 0; i < tm; i++)
         for (int j = 0; j < tn; j++) {
             if ((t.flags & kTaskLower) && (i * kBM + kBM - 1) < j * kBN) continue;  // above the diagonal
@@ -328,9 +333,10 @@ void build_plan(const sc_symbolic *s, int precision, Plan &P, bool lookahead) {
         std::vector<int32_t> ids_small;
         std::vector<ThinUnit> units_thin[2];
         std::vector<GemmTile> g_simt[2], g_tc[2], g_tc64[2];
+        const bool split = lookahead;
         for (Task t : L.tasks) {
             int32_t id = (int32_t)P.tasks.size();
-            const int cls = lookahead && !(t.flags & kTaskCrit) ? 1 : 0;  // 0 crit, 1 rest
+            const int cls = split && !(t.flags & kTaskCrit) ? 1 : 0;  // 0 crit, 1 rest
             P.tasks.push_back(t);
             const int bn = tc ? tc_width(t, tmap_of_sn) : 0;
             if (is_small(t)) {
@@ -483,11 +489,8 @@ int numeric_create(sc_symbolic *s, int precision, sc_numeric **out) {
         if ((rc = upload(h->d_tmap_of_sn, tmap_of_sn, bytes))) return fail(rc);
     }
     Plan P;
-    // lookahead needs the captured graph's concurrent branches (RLB schedule);
-    // it pays for FP32-storage factors, whose POTRF / TRSM latency is large next
-    // to their products, not for FP64 (DFMA-bound products, where splitting a
-    // level's products into two launches leaves SMs idle)
-    h->lookahead = h->use_graph && s->opt.variant == SC_RLB && precision != SC_FP64;
+    // lookahead needs the captured graph's concurrent branches (RLB schedule)
+    h->lookahead = h->use_graph && s->opt.variant == SC_RLB;
     build_plan(s, precision, P, h->lookahead);
     if (precision != SC_FP64) {
         if (cudaMalloc(&h->d_inv, (size_t)std::max<int64_t>(1, P.inv_size) * sizeof(float)) != cudaSuccess)

@@ -352,7 +352,8 @@ __global__ void __launch_bounds__(256) k_gemm_tiles(T *__restrict__ lnz, T *__re
 #pragma unroll
         for (int j = 0; j < 4; j++) acc[i][j] = T(0);
     const bool split = tl.ks >= 0;
-    const int kb = split ? tl.ks * kSplitK : 0, ke = split ? min(tk.k, kb + kSplitK) : tk.k;
+    const int ksz = (tk.flags & kTaskCrit) ? kSplitKCrit : kSplitK;
+    const int kb = split ? tl.ks * ksz : 0, ke = split ? min(tk.k, kb + ksz) : tk.k;
     // operands of the next K slice are fetched into registers while the
     // current one is multiplied
     constexpr int kLd = BM * BK / 256;
