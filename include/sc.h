@@ -142,7 +142,7 @@ typedef struct sc_symbolic_view {
 /* Fills v with the view of s. Errors: -1, -2 for NULL arguments. */
 int sc_symbolic_export(const sc_symbolic *s, sc_symbolic_view *v);
 
-/* relind composition of line 10 of Alg. 4 (a host utility): out[k] =
+/* relind composition of Alg. 4 (a host utility): out[k] =
  * rCP[lenCP - 1 - rJC[k]], i.e. each distance in relind(J,C) picks the entry
  * of relind(C,P) at that distance from its bottom. Errors: -1..-5 when a
  * pointer is NULL or a distance is outside relind(C,P). */

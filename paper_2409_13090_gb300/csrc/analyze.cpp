@@ -10,7 +10,7 @@
 //   - column counts by marking the row subtrees of the elimination tree;
 //   - supernode structures by a union over child supernodes only;
 //   - partition refinement with an in-place, array-based partition;
-//   - relindB(J,P) by composition with relind(C,P), as in line 10 of Alg. 5.
+//   - relindB(J,P) by composition with relind(C,P), as Alg. 5 composes them.
 #include <algorithm>
 #include <cstring>
 #include <numeric>
@@ -574,8 +574,8 @@ int analyze_impl(int64_t n, const int64_t *colptr, const int32_t *rowind, const 
         s->blk_ptr[J + 1] = (int64_t)s->blk_first.size();
     }
 
-    // ---- relindB(J, P): extracted from relind(J, p(J)) (line 5 of Alg. 5), then
-    //      composed with relind(C, P) for each further ancestor (line 9)
+    // ---- relindB(J, P): extracted from relind(J, p(J)) (Alg. 5), then
+    //      composed with relind(C, P) for each further ancestor
     s->rb_pair_ptr.assign(ns + 1, 0);
     s->rb_val_ptr.assign(1, 0);
     {

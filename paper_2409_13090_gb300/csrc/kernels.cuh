@@ -564,7 +564,7 @@ __global__ void __launch_bounds__(kThinWarps * 32) k_thin_tasks(T *__restrict__ 
     }
 }
 
-// Alg. 5 lines 10-16 for a range of J's blocks, in one CTA: for each block B
+// Alg. 5's inner loops for a range of J's blocks, in one CTA: for each block B
 // (inside ancestor P): SYRK L_{B,B} -= L_{B,J} L_{B,J}^T, then for each maximal
 // run B' of blocks below B: GEMM L_{B',B} -= L_{B',J} L_{B,J}^T, both straight
 // into Lnz(P) at the rows given by relindB(J,P). Products that tile_task()
@@ -639,7 +639,7 @@ __global__ void __launch_bounds__(256) k_rlb_loop_warp(T *__restrict__ lnz, cons
 }
 
 // --------------------------------------------------------------------- K4b
-// RL assembly (Alg. 4, line 13): for every column c of U_J inside P and every
+// RL assembly (Alg. 4, the scatter-add step): for every column c of U_J inside P and every
 // row r >= c, Lnz(P)[m_P-1-relind[r]][m_P-1-relind[c]] += U_J[r][c].
 template <typename T>
 __global__ void k_rl_assemble(T *__restrict__ lnz, const T *__restrict__ pool, const RLPair *__restrict__ pairs,

@@ -63,7 +63,7 @@ struct Chunk {
     int32_t last; // 1 if this is the supernode's last chunk
 };
 
-// RL assembly of U_J's columns lying in ancestor P (Alg. 4, line 13).
+// RL assembly of U_J's columns lying in ancestor P (Alg. 4, the scatter-add step).
 struct RLPair {
     int64_t u_off;      // offset of U_J in the pool (row-major, ld = s)
     int64_t p_off;      // offset of Lnz(P)

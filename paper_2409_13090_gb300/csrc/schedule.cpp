@@ -13,12 +13,12 @@
 //     later columns at once, K = 256);
 //   - for J's last chunk (all of L_{*,J} is final):
 //       RLB (Alg. 5): for every ancestor P, every block B of J inside P:
-//         SYRK  L_{B,B}  -= L_{B,J} L_{B,J}^T            (line 12)
-//         GEMM  L_{B',B} -= L_{B',J} L_{B,J}^T  for every maximal B' below B (line 14)
+//         SYRK  L_{B,B}  -= L_{B,J} L_{B,J}^T
+//         GEMM  L_{B',B} -= L_{B',J} L_{B,J}^T  for every maximal B' below B
 //       each straight into Lnz(P) at the offsets given by relindB(J,P);
-//       RL (Alg. 4): U_J = -L_{S,J} L_{S,J}^T (line 6) into a pooled buffer,
+//       RL (Alg. 4): U_J = -L_{S,J} L_{S,J}^T into a pooled buffer,
 //         then for each ancestor P the columns of U_J lying in P are added
-//         into Lnz(P) through relind(J,P) (lines 10-14).
+//         into Lnz(P) through relind(J,P).
 #include <algorithm>
 
 #include "sc_internal.h"
@@ -122,7 +122,7 @@ int build_schedule(sc_symbolic *s) {
                 }
             }
             if (!rl) {
-                // Alg. 5 lines 7-17 for J: large (B, B') products become tiled tasks;
+                // Alg. 5's loops over J's ancestors and blocks: large (B, B') products become tiled tasks;
                 // the rest run on the device in items of bounded cost, each item
                 // one block B and a range of the runs B' below it.
                 const int64_t kLoopBudget = 1 << 15;
@@ -238,7 +238,7 @@ int build_schedule(sc_symbolic *s) {
                 L.rl_tasks.push_back(t);
                 int64_t u_off = L.rl_pool;
                 L.rl_pool += (int64_t)sJ * sJ;
-                // walk the ancestors: relind(J,P) = relind(J,C) o relind(C,P) (line 10)
+                // walk the ancestors: relind(J,P) = relind(J,C) o relind(C,P) (Alg. 4's composition)
                 const int32_t *S = s->glbind.data() + s->gl_ptr[J] + nJ;
                 int32_t P = s->sup_parent[J];
                 cur.assign(s->relind.begin() + s->ri_ptr[J], s->relind.begin() + s->ri_ptr[J + 1]);
@@ -271,7 +271,7 @@ int build_schedule(sc_symbolic *s) {
                         pr.pad = 0;
                         s->rl_relind.insert(s->rl_relind.end(), cur.begin(), cur.end());
                         L.rl_pairs.push_back(pr);
-                        // remove the assembled columns (line 14)
+                        // remove the assembled columns (Alg. 4)
                         cur.erase(cur.begin(), cur.begin() + (ce - cb));
                         start = ce;
                     }
