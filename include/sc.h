@@ -51,7 +51,7 @@ extern "C" {
 #define SC_ERR_OOM (-104)           /* host or device allocation failed      */
 #define SC_ERR_IN_USE (-105)        /* symbolic handle still referenced      */
 #define SC_ERR_INTERNAL (-106)      /* an internal consistency check failed  */
-#define SC_ERR_UNSUPPORTED (-107)   /* option not available in this build    */
+#define SC_ERR_UNSUPPORTED (-107)   /* option not available in this library  */
 
 /* --------------------------------------------------------------- options */
 enum sc_ordering { SC_ORDER_NATURAL = 0, SC_ORDER_GRID_ND = 1, SC_ORDER_USER = 2 };
