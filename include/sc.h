@@ -231,6 +231,30 @@ int sc_solve(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, double *
  * Errors: -1..-3, SC_ERR_OOM. */
 int sc_analyze_batch(int count, sc_symbolic *const *syms, sc_symbolic **out);
 
+/* Batched numeric factorization of many independent matrices in one launch
+ * sequence (a convenience over sc_analyze_batch + sc_factor): the values of
+ * matrix i (FP64, aligned with the rowind of syms[i]) are gathered into the
+ * batch handle's concatenated values array, and the block-diagonal problem is
+ * factored at once.
+ *   count      number of matrices (>= 1)
+ *   syms       count symbolic handles (each from sc_analyze); not consumed
+ *   values     count pointers; values[i] holds nnz(A_i) doubles
+ *   values_on_device  1 if every values[i] is a device pointer, 0 if host
+ *   precision  enum sc_precision
+ *   batch_sym  receives the combined symbolic handle (free it with
+ *              sc_symbolic_free after the numeric handle)
+ *   out        receives the numeric handle of the batch; solve with sc_solve
+ *              on right-hand sides whose rows are the matrices' unknowns
+ *              concatenated in order
+ *   info       optional, as for sc_factor
+ * Returns as sc_factor (a positive value: the failing column of the batch's
+ * concatenated ordering), -i for an invalid argument i (count, syms or a NULL
+ * syms[i] / values[i], values, values_on_device, precision, batch_sym, out),
+ * SC_ERR_OOM or SC_ERR_CUDA. */
+int sc_factor_batch(int count, sc_symbolic *const *syms, const double *const *values, int values_on_device,
+                    int precision, void *cuda_stream, sc_symbolic **batch_sym, sc_numeric **out,
+                    sc_factor_info *info);
+
 /* Copies L to host memory in the canonical supernodal layout: for each
  * supernode J, an m_J x |J| row-major block (row r = glbind(J)[r], column
  * c = column f_J + c of the final ordering, entries above the diagonal 0),

@@ -99,6 +99,7 @@ def lib():
             "sc_probe_fma_peak": ([C.c_int, P, P], C.c_int),
             "sc_plan_stats": ([P, C.c_int, P, C.c_int], C.c_int),
             "sc_test_stall_solve": ([P, i64], C.c_int),
+            "sc_factor_batch": ([C.c_int, P, P, C.c_int, C.c_int, P, C.POINTER(P), C.POINTER(P), P], C.c_int),
             "sc_strerror": ([C.c_int], C.c_char_p),
             "sc_build_info": ([], C.c_char_p),
         }
@@ -268,6 +269,27 @@ class Symbolic:
         self._h = h
         self.n = A.n
         self.precision = precision
+
+    @staticmethod
+    def factor_batch(syms, values_list, precision="fp64", stream=None):
+        """sc_factor_batch: one factorization of many matrices; returns (batch
+        Symbolic, Numeric). values_list: one FP64 array per matrix (all numpy,
+        or all CUDA tensors)."""
+        count = len(syms)
+        dev = not isinstance(values_list[0], np.ndarray)
+        keep = [v if dev else np.ascontiguousarray(v, np.float64) for v in values_list]
+        hs = (C.c_void_p * count)(*[s._h for s in syms])
+        vs = (C.c_void_p * count)(*[_ptr(v) for v in keep])
+        bsym, h = C.c_void_p(), C.c_void_p()
+        info = FactorInfo()
+        rc = lib().sc_factor_batch(count, hs, vs, int(dev), PRECISION[precision], _stream(stream), C.byref(bsym),
+                                   C.byref(h), C.byref(info))
+        if rc < 0:
+            raise SCError(rc, "sc_factor_batch")
+        b = Symbolic(_handle=bsym, _parts=list(syms))
+        num = Numeric.__new__(Numeric)
+        num.sym, num._h, num.info, num.rc, num._vals_keep = b, h, info, rc, keep
+        return b, num
 
     @classmethod
     def batch(cls, syms):

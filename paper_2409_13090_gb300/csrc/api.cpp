@@ -2,6 +2,7 @@
 // ownership and error codes around the host analysis and the CUDA path.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <new>
 
@@ -109,6 +110,51 @@ int sc_factor(sc_symbolic *s, const double *values, int values_on_device, int pr
         return rc;
     }
     *out = h;
+    return rc;
+}
+
+int sc_factor_batch(int count, sc_symbolic *const *syms, const double *const *values, int values_on_device,
+                    int precision, void *cuda_stream, sc_symbolic **batch_sym, sc_numeric **out,
+                    sc_factor_info *info) {
+    if (count < 1) return -1;
+    if (!syms) return -2;
+    if (!values) return -3;
+    if (values_on_device != 0 && values_on_device != 1) return -4;
+    if (precision < SC_FP64 || precision > SC_TF32X3) return -5;
+    if (!batch_sym) return -7;
+    if (!out) return -8;
+    *batch_sym = nullptr;
+    *out = nullptr;
+    for (int i = 0; i < count; i++)
+        if (!syms[i] || !values[i]) return -2;
+    sc_symbolic *b = nullptr;
+    int rc = sc_analyze_batch(count, syms, &b);
+    if (rc) return rc;
+    // the batch's values: the matrices' values concatenated in order
+    int64_t total = 0;
+    for (int i = 0; i < count; i++) total += (int64_t)syms[i]->valmap.size();
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    double *d_vals = nullptr;
+    if (cudaMalloc((void **)&d_vals, (size_t)std::max<int64_t>(1, total) * sizeof(double)) != cudaSuccess) {
+        sc_symbolic_free(b);
+        return SC_ERR_OOM;
+    }
+    int64_t off = 0;
+    for (int i = 0; i < count && rc == SC_OK; i++) {
+        const int64_t nnz = (int64_t)syms[i]->valmap.size();
+        if (cudaMemcpyAsync(d_vals + off, values[i], nnz * sizeof(double),
+                            values_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st) != cudaSuccess)
+            rc = SC_ERR_CUDA;
+        off += nnz;
+    }
+    if (rc == SC_OK) rc = sc_factor(b, d_vals, 1, precision, cuda_stream, out, info);
+    cudaStreamSynchronize(st);
+    cudaFree(d_vals);
+    if (rc < 0) {
+        sc_symbolic_free(b);
+        return rc;
+    }
+    *batch_sym = b;
     return rc;
 }
 

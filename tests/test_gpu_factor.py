@@ -237,3 +237,28 @@ def test_low_pivot_blocks_redone_in_fp64(prec):
         assert info["converged"], info
         assert oracle.backward_error(A, B, X).max() <= 1e-14
     assert errs[0.5] <= errs[2.0 ** -10] * 2 + 1e-12
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_factor_batch_entry_point(prec):
+    """sc_factor_batch: the values of each matrix gathered into one batched
+    factorization; L of every member matches its oracle factor (FP64 bound, or
+    the FP32 bound), and the batch solve reaches eta <= 1e-14 per matrix."""
+    import torch
+    mats, _ = inputs.workload(4, 0.06)
+    syms = [sc.Symbolic(A, ordering="grid_nd", grid=A.grid) for A in mats]
+    vals = [torch.tensor(A.values, device="cuda", dtype=torch.float64) for A in mats]
+    bsym, num = sc.Symbolic.factor_batch(syms, vals, precision=prec)
+    assert num.rc == 0
+    Lb = num.export_L()
+    off = 0
+    for A in mats:
+        _, Lo = _oracle_L(A, oracle.nd_grid(*A.grid, 8))
+        _check_L(Lb[off:off + Lo.size], Lo, 1e-10 if prec == "fp64" else 1e-3)
+        off += Lo.size
+    B = inputs.rhs(bsym.n, 1, 23)
+    X, info = num.solve(B)
+    r0 = 0
+    for A in mats:
+        assert oracle.backward_error(A, B[r0:r0 + A.n], X[r0:r0 + A.n]).max() <= 1e-14
+        r0 += A.n
