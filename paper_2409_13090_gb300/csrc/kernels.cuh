@@ -318,13 +318,36 @@ __global__ void __launch_bounds__(trsm_rows<T>() * 4) k_trsm(T *__restrict__ lnz
 }
 
 // --------------------------------------------------------------------- K3
+// The multiply-adds of one staged K slice for a warp whose micro-tiles reach
+// NI row groups and NJ column groups inside the task.
+template <typename T, int NI, int NJ, int BK>
+__device__ __forceinline__ void tile_fma(const T (*As)[64 + 1], const T (*Bs)[64 + 1], int r0, int c0, int kn,
+                                         T (&acc)[4][4]) {
+#pragma unroll
+    for (int kk = 0; kk < BK; kk++) {
+        if (kk < kn) {
+            T a[NI], b[NJ];
+#pragma unroll
+            for (int i = 0; i < NI; i++) a[i] = As[kk][r0 + 4 * i];
+#pragma unroll
+            for (int j = 0; j < NJ; j++) b[j] = Bs[kk][c0 + 8 * j];
+#pragma unroll
+            for (int i = 0; i < NI; i++)
+#pragma unroll
+                for (int j = 0; j < NJ; j++) acc[i][j] += a[i] * b[j];
+        }
+    }
+}
+
 // Tiled product C -= A B^T (or C = -A B^T into an RL update matrix) on SIMT
 // FMA units. 256 threads, 64 x 64 tile; warp w owns the 16 x 32 sub-tile
 // (rows 16 (w / 2), columns 32 (w % 2)) and each lane a 4 x 4 strided micro-tile
 // of it. A warp whose sub-tile lies outside m x n, or wholly above the diagonal
-// of a lower task, skips its multiply-adds (it still helps stage the operands),
-// and the last K slice runs only its valid columns, so ragged tiles do not
-// spend FMA-pipe cycles on padding. The scatter into Lnz(P) is an atomic add
+// of a lower task, skips its multiply-adds (it still helps stage the operands);
+// a warp at the ragged edge runs only the row groups (4 rows apart) and column
+// groups (8 columns apart) that reach inside the task, and the last K slice
+// runs only its valid columns, so ragged tiles spend few FMA-pipe cycles on
+// padding. The scatter into Lnz(P) is an atomic add
 // unless the task is the only writer of its target: supernodes of one level
 // may update the same ancestor entries.
 template <typename T, int BM, int BN, int BK>
@@ -346,6 +369,9 @@ __global__ void __launch_bounds__(256) k_gemm_tiles(T *__restrict__ lnz, T *__re
     // warp-uniform: does the sub-tile hold any entry that is written?
     const int sr = row0 + (warp / 2) * 16, sc = col0 + (warp % 2) * 32;
     const bool active = sr < tk.m && sc < tk.n && !(lower && min(sr + 15, tk.m - 1) < sc);
+    // row groups (4 rows apart) and column groups (8 columns apart) of the
+    // warp's micro-tiles that reach inside the task: the others skip their FMAs
+    const int shape = min(4, (tk.m - sr + 3) / 4) * 5 + min(4, (tk.n - sc + 7) / 8);
     T acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; i++)
@@ -378,19 +404,15 @@ __global__ void __launch_bounds__(256) k_gemm_tiles(T *__restrict__ lnz, T *__re
         if (k0 + BK < ke) fetch(k0 + BK);
         if (active) {
             const int kn = min(BK, ke - k0);
-#pragma unroll
-            for (int kk = 0; kk < BK; kk++) {
-                if (kk < kn) {
-                    T a[4], b[4];
-#pragma unroll
-                    for (int i = 0; i < 4; i++) a[i] = As[kk][r0 + 4 * i];
-#pragma unroll
-                    for (int j = 0; j < 4; j++) b[j] = Bs[kk][c0 + 8 * j];
-#pragma unroll
-                    for (int i = 0; i < 4; i++)
-#pragma unroll
-                        for (int j = 0; j < 4; j++) acc[i][j] += a[i] * b[j];
-                }
+            switch (shape) {  // warp-uniform: only the row / column groups inside the task
+#define SC_TILE_CASE(NI, NJ)                                                                      \
+    case NI * 5 + NJ: tile_fma<T, NI, NJ, BK>(As, Bs, r0, c0, kn, acc); break;
+                SC_TILE_CASE(1, 1) SC_TILE_CASE(1, 2) SC_TILE_CASE(1, 3) SC_TILE_CASE(1, 4)
+                SC_TILE_CASE(2, 1) SC_TILE_CASE(2, 2) SC_TILE_CASE(2, 3) SC_TILE_CASE(2, 4)
+                SC_TILE_CASE(3, 1) SC_TILE_CASE(3, 2) SC_TILE_CASE(3, 3) SC_TILE_CASE(3, 4)
+                SC_TILE_CASE(4, 1) SC_TILE_CASE(4, 2) SC_TILE_CASE(4, 3)
+                default: tile_fma<T, 4, 4, BK>(As, Bs, r0, c0, kn, acc); break;
+#undef SC_TILE_CASE
             }
         }
         __syncthreads();
