@@ -39,7 +39,7 @@ SAMPLE_SIDE = 32  # oracle sample: the same generator on a 32^3 grid
 # its command in profiles/k_gemm_tiles_fp64_diffusion48.md). Key: (class,
 # precision, workload, scale, merge). Classes without a capture of the current
 # code report null.
-TRAFFIC = {("gemm_simt", "fp64", 2, 1.0, 0.125): 2529188864}
+TRAFFIC = {("gemm_simt", "fp64", 2, 1.0, 0.125): 2544617984}
 
 
 def reduce_max_over_ranks(dist, values, device):
