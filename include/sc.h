@@ -54,7 +54,11 @@ extern "C" {
 #define SC_ERR_UNSUPPORTED (-107)   /* option not available in this library  */
 
 /* --------------------------------------------------------------- options */
-enum sc_ordering { SC_ORDER_NATURAL = 0, SC_ORDER_GRID_ND = 1, SC_ORDER_USER = 2 };
+/* SC_ORDER_GRID_ND: geometric nested dissection of an nx x ny x nz grid
+ * (grid[] and nd_leaf); SC_ORDER_GRAPH_ND: nested dissection of the matrix
+ * graph by breadth-first level structures (nd_leaf), for inputs without a
+ * grid; both stand in for the paper's METIS ordering (Sec. 3.1). */
+enum sc_ordering { SC_ORDER_NATURAL = 0, SC_ORDER_GRID_ND = 1, SC_ORDER_USER = 2, SC_ORDER_GRAPH_ND = 3 };
 enum sc_variant { SC_RLB = 0, SC_RL = 1 };
 /* Arithmetic of the numeric factorization:
  *   SC_FP64  every operation in FP64 (the paper's precision, Sec. 3.1);

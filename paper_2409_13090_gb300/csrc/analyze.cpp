@@ -75,6 +75,117 @@ void grid_nd(int nx, int ny, int nz, int leaf, std::vector<int32_t> &perm) {
 }
 
 // Full symmetric adjacency (no diagonal) of the lower-triangle CSC input.
+// Nested dissection of a general graph (no coordinates), a stand-in for the
+// paper's METIS ordering on inputs without a grid. For a vertex set S (sorted):
+// |S| <= leaf: emit S ascending. Otherwise split S into the connected
+// components of G[S] (found from their smallest vertex, in that order) and
+// order each alone; a connected S is split by a breadth-first level structure
+// from a pseudo-peripheral root (start at min S; up to 8 times move to the
+// vertex of the last level with the fewest neighbours in S, ties to the smaller
+// index, while that raises the eccentricity): the first level k with
+// 2 |L_0 .. L_k| >= |S| is the separator, and the order is ND(levels < k),
+// ND(levels > k), then level k ascending. Neighbours are visited ascending.
+class GraphND {
+  public:
+    GraphND(int64_t n, const std::vector<int64_t> &ptr, const std::vector<int32_t> &adj, int leaf,
+            std::vector<int32_t> &out)
+        : ptr_(ptr), adj_(adj), leaf_(leaf), out_(out), inset_(n, 0), seen_(n, 0) {}
+
+    void order(std::vector<int32_t> S) {
+        if ((int64_t)S.size() <= leaf_) {
+            out_.insert(out_.end(), S.begin(), S.end());
+            return;
+        }
+        const int32_t st = ++set_stamp_;
+        for (int32_t v : S) inset_[v] = st;
+        // connected components of G[S]
+        std::vector<std::vector<int32_t>> comps;
+        const int32_t cs = ++seen_stamp_;
+        for (int32_t v : S) {
+            if (seen_[v] == cs) continue;
+            std::vector<int32_t> comp{v};
+            seen_[v] = cs;
+            for (size_t h = 0; h < comp.size(); h++)
+                for (int64_t p = ptr_[comp[h]]; p < ptr_[comp[h] + 1]; p++) {
+                    const int32_t u = adj_[p];
+                    if (inset_[u] == st && seen_[u] != cs) {
+                        seen_[u] = cs;
+                        comp.push_back(u);
+                    }
+                }
+            std::sort(comp.begin(), comp.end());
+            comps.push_back(std::move(comp));
+        }
+        if (comps.size() > 1) {
+            for (auto &c : comps) order(std::move(c));
+            return;
+        }
+        // pseudo-peripheral root and its level structure
+        int32_t r = S[0];
+        std::vector<std::vector<int32_t>> L = levels(r, st);
+        for (int it = 0; it < 8; it++) {
+            int32_t cand = -1, cdeg = 0;
+            for (int32_t v : L.back()) {
+                int32_t d = 0;
+                for (int64_t p = ptr_[v]; p < ptr_[v + 1]; p++) d += inset_[adj_[p]] == st;
+                if (cand < 0 || d < cdeg || (d == cdeg && v < cand)) {
+                    cand = v;
+                    cdeg = d;
+                }
+            }
+            std::vector<std::vector<int32_t>> Lc = levels(cand, st);
+            if (Lc.size() <= L.size()) break;
+            r = cand;
+            L = std::move(Lc);
+        }
+        size_t k = 0;
+        int64_t cum = 0;
+        for (; k < L.size(); k++) {
+            cum += (int64_t)L[k].size();
+            if (2 * cum >= (int64_t)S.size()) break;
+        }
+        std::vector<int32_t> left, right, sep = L[k];
+        for (size_t q = 0; q < L.size(); q++)
+            if (q < k) left.insert(left.end(), L[q].begin(), L[q].end());
+            else if (q > k) right.insert(right.end(), L[q].begin(), L[q].end());
+        std::sort(left.begin(), left.end());
+        std::sort(right.begin(), right.end());
+        std::sort(sep.begin(), sep.end());
+        order(std::move(left));
+        order(std::move(right));
+        out_.insert(out_.end(), sep.begin(), sep.end());
+    }
+
+  private:
+    // breadth-first levels of G[S] (S = vertices stamped st) from root
+    std::vector<std::vector<int32_t>> levels(int32_t root, int32_t st) {
+        const int32_t bs = ++seen_stamp_;
+        std::vector<std::vector<int32_t>> L{{root}};
+        seen_[root] = bs;
+        while (true) {
+            std::vector<int32_t> next;
+            for (int32_t v : L.back())
+                for (int64_t p = ptr_[v]; p < ptr_[v + 1]; p++) {
+                    const int32_t u = adj_[p];
+                    if (inset_[u] == st && seen_[u] != bs) {
+                        seen_[u] = bs;
+                        next.push_back(u);
+                    }
+                }
+            if (next.empty()) break;
+            L.push_back(std::move(next));
+        }
+        return L;
+    }
+
+    const std::vector<int64_t> &ptr_;
+    const std::vector<int32_t> &adj_;
+    int64_t leaf_;
+    std::vector<int32_t> &out_;
+    std::vector<int32_t> inset_, seen_;
+    int32_t set_stamp_ = 0, seen_stamp_ = 0;
+};
+
 void build_adjacency(int64_t n, const int64_t *colptr, const int32_t *rowind, std::vector<int64_t> &ptr,
                      std::vector<int32_t> &adj) {
     ptr.assign(n + 1, 0);
@@ -342,12 +453,21 @@ int analyze_impl(int64_t n, const int64_t *colptr, const int32_t *rowind, const 
     } else if (o.ordering == SC_ORDER_NATURAL) {
         p0.resize(n);
         std::iota(p0.begin(), p0.end(), 0);
-    } else {
+    } else if (o.ordering != SC_ORDER_GRAPH_ND) {
         return -4;
     }
     std::vector<int64_t> aptr;
     std::vector<int32_t> adj;
     build_adjacency(n, colptr, rowind, aptr, adj);
+    if (o.ordering == SC_ORDER_GRAPH_ND) {
+        if (o.nd_leaf < 1) return -4;
+        p0.clear();
+        p0.reserve(n);
+        std::vector<int32_t> all(n);
+        std::iota(all.begin(), all.end(), 0);
+        GraphND(n, aptr, adj, o.nd_leaf, p0).order(std::move(all));
+        if ((int64_t)p0.size() != n) return SC_ERR_INTERNAL;
+    }
     std::vector<int32_t> ip0(n);
     for (int64_t k = 0; k < n; k++) ip0[p0[k]] = (int32_t)k;
 

@@ -262,3 +262,25 @@ def test_factor_batch_entry_point(prec):
     for A in mats:
         assert oracle.backward_error(A, B[r0:r0 + A.n], X[r0:r0 + A.n]).max() <= 1e-14
         r0 += A.n
+
+
+@pytest.mark.parametrize("case", ["rand", "diff7_14_no_grid"])
+@pytest.mark.parametrize("variant", ["rlb", "rl"])
+def test_graph_nd_ordering_factor(case, variant):
+    """Inputs without grid coordinates ordered by the general-graph nested
+    dissection: the FP64 factor matches the oracle's under the oracle's own
+    restatement of that ordering, and the solve reaches eta <= 1e-14."""
+    if case == "rand":
+        A = inputs.random_spd(2000, 0.003, 21)
+    else:
+        A = inputs.diffusion_3d_7pt(14, 14, 14, seed=2)
+    A.grid = None
+    sym = sc.Symbolic(A, ordering="graph_nd", variant=variant)
+    o, Lo = _oracle_L(A, oracle.nd_graph(A, 8))
+    num = sym.factor(A.values, precision="fp64")
+    assert num.rc == 0
+    _check_L(num.export_L(), Lo, 1e-10)
+    B = inputs.rhs(A.n, 3, 5)
+    X, info = num.solve(B)
+    assert info["converged"], info
+    assert oracle.backward_error(A, B, X).max() <= 1e-14

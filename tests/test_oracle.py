@@ -333,3 +333,51 @@ def test_backward_error_hand_example():
     A = inputs.SparseSym(2, np.array([0, 2, 3], np.int64), np.array([0, 1, 1], np.int32), np.array([4.0, 1.0, 3.0]))
     eta = oracle.backward_error(A, np.array([[1.0], [2.0]]), np.array([[0.1], [0.6]]))
     assert abs(eta[0] - 0.02) <= 1e-15
+
+
+# --------------------------------------------------------------------------- general-graph ND
+
+def test_nd_graph_hand_orders():
+    # path 0-1-...-6, leaf 1: levels from 0 are singletons (from 6 no more levels),
+    # the separator is the first level with 2*4 >= 7, i.e. vertex 3; each half of
+    # three splits at its middle vertex.
+    path = inputs.from_lower_pattern(7, [(i + 1, i) for i in range(6)])
+    assert oracle.nd_graph(path, leaf=1).tolist() == [0, 2, 1, 4, 6, 5, 3]
+    # star with centre 0, leaf 1: levels from 0 are {0},{1..6}; from leaf 1 they are
+    # {1},{0},{2..6} (deeper, so the root moves to 1); from 2 no deeper. Separator:
+    # 2*1 < 7, 2*2 < 7, 2*7 >= 7 -> {2..6}; the rest {0,1} splits at 0.
+    star = inputs.from_lower_pattern(7, [(i, 0) for i in range(1, 7)])
+    assert oracle.nd_graph(star, leaf=1).tolist() == [1, 0, 2, 3, 4, 5, 6]
+    # two disjoint paths 0-2-4 and 1-3-5, leaf 1: components taken by smallest vertex
+    two = inputs.from_lower_pattern(6, [(2, 0), (4, 2), (3, 1), (5, 3)])
+    assert oracle.nd_graph(two, leaf=1).tolist() == [0, 4, 2, 1, 5, 3]
+    # a leaf at least n keeps the natural order
+    assert oracle.nd_graph(star, leaf=7).tolist() == list(range(7))
+
+
+def test_nd_graph_is_a_dissection():
+    # each separator splits: eliminating in ND order never creates fill between
+    # vertices of the two sides, so on a 2D grid the fill is far below the
+    # natural (banded) order and of the order of the geometric ND.
+    A = inputs.laplacian_2d(24, 24)
+    perm = oracle.nd_graph(A, leaf=8)
+    assert sorted(perm.tolist()) == list(range(A.n))
+    nnz_nd = oracle.Oracle(A, perm, pr=False).symbolic().nnzL
+    nnz_nat = oracle.Oracle(A, None, pr=False).symbolic().nnzL
+    nnz_geo = oracle.Oracle(A, oracle.nd_grid(24, 24, 1, 8), pr=False).symbolic().nnzL
+    assert nnz_nd < 0.75 * nnz_nat, (nnz_nd, nnz_nat)
+    assert nnz_nd < 1.6 * nnz_geo, (nnz_nd, nnz_geo)
+    # the last vertices form a separator: removing them disconnects the grid
+    D = inputs.dense_from_lower(A) != 0
+    top = perm[-24:]
+    keep = np.setdiff1d(np.arange(A.n), top)
+    sub = D[np.ix_(keep, keep)]
+    seen = {0}
+    stack = [0]
+    while stack:
+        v = stack.pop()
+        for u in np.nonzero(sub[v])[0].tolist():
+            if u not in seen:
+                seen.add(u)
+                stack.append(u)
+    assert len(seen) < len(keep)

@@ -24,8 +24,11 @@ def built():
     sc.build()
 
 
-def _compare(A, *, grid=None, user_perm=None, pr=True, leaf=8, merge=0.0):
-    if grid is not None:
+def _compare(A, *, grid=None, user_perm=None, pr=True, leaf=8, merge=0.0, graph_nd=False):
+    if graph_nd:
+        perm0 = oracle.nd_graph(A, leaf)
+        lib_sym = sc.Symbolic(A, ordering="graph_nd", nd_leaf=leaf, pr=pr, merge=merge)
+    elif grid is not None:
         perm0 = oracle.nd_grid(*grid, leaf)
         lib_sym = sc.Symbolic(A, ordering="grid_nd", grid=grid, nd_leaf=leaf, pr=pr, merge=merge)
     elif user_perm is not None:
@@ -170,3 +173,51 @@ def test_library_exports_every_declared_symbol():
     L = ctypes.CDLL(sc.build())
     for nm in sorted(names):
         assert hasattr(L, nm), nm
+
+
+@pytest.mark.parametrize("case", ["rand", "grid2d", "grid3d", "st27", "disconnected", "path"])
+@pytest.mark.parametrize("leaf", [1, 8, 32])
+def test_graph_nd_ordering_bit_exact(case, leaf):
+    """The general-graph nested dissection (no grid coordinates) gives the same
+    permutation as the oracle's set-based restatement, and every symbolic array
+    that follows from it agrees bit for bit."""
+    if case == "rand":
+        A = inputs.random_spd(300, 0.02, 5)
+    elif case == "grid2d":
+        A = inputs.laplacian_2d(23, 17)
+    elif case == "grid3d":
+        A = inputs.diffusion_3d_7pt(9, 8, 7, seed=1)
+    elif case == "st27":
+        A = inputs.stencil_3d_27pt(7, 7, 7, seed=2)
+    elif case == "path":
+        A = inputs.from_lower_pattern(200, [(i + 1, i) for i in range(199)])
+    else:
+        # three components: a 2D grid, a path and isolated vertices, interleaved labels
+        rng = np.random.default_rng(9)
+        lab = rng.permutation(150)
+        ents = []
+        for y in range(8):
+            for x in range(8):
+                v = x + 8 * y
+                if x + 1 < 8:
+                    ents.append((v, v + 1))
+                if y + 1 < 8:
+                    ents.append((v, v + 8))
+        ents += [(64 + i, 65 + i) for i in range(70)]
+        ents = [(max(lab[a], lab[b]), min(lab[a], lab[b])) for a, b in ents]
+        A = inputs.from_lower_pattern(150, ents, seed=3)
+    A.grid = None
+    v = _compare(A, graph_nd=True, leaf=leaf, pr=True)
+    assert np.array_equal(v["perm"][np.argsort(v["perm"])], np.arange(A.n))
+
+
+def test_graph_nd_fill_close_to_geometric_nd():
+    """On a 3D grid given without coordinates the graph ordering's fill stays
+    within a small factor of the geometric ND and well below the natural order."""
+    A = inputs.diffusion_3d_7pt(16, 16, 16, seed=1)
+    nnz = {}
+    for name, kw in [("graph", dict(ordering="graph_nd")), ("grid", dict(ordering="grid_nd", grid=(16, 16, 16))),
+                     ("natural", dict(ordering="natural"))]:
+        nnz[name] = sc.Symbolic(A, pr=False, **kw).view()["nnzL"]
+    assert nnz["graph"] < 2.0 * nnz["grid"], nnz
+    assert nnz["graph"] < 0.5 * nnz["natural"], nnz
