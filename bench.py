@@ -181,6 +181,7 @@ def _args():
     ap.add_argument("--scale", type=float, default=1.0, help="grid-side scale of the workload (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the launch-plan autotuner's measurement")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the TF32+refinement vs FP64 comparison on the 80^3 27-point matrix")
     return ap.parse_args()
@@ -424,6 +425,41 @@ def main():
                       "bytes_per_solve": int(solve_bytes), "peak_source": f"{peak_kind} HBM copy",
                       "note": "the sweeps are bound by the chain of dependent chunk steps, not by HBM"}
 
+    # ---- the launch-plan autotuner (sc_tune) on the same matrix: the headline above
+    #      uses the default plan; here the tuned plan's factor is timed the same way
+    tune = None
+    if not args.no_tune:
+        try:
+            sym_t = sc.Symbolic(A, ordering="grid_nd", grid=A.grid, nd_leaf=8, pr=True, variant="rlb",
+                                merge=args.merge)
+            t0 = time.perf_counter()
+            table = sym_t.tune(dv, precision=args.precision, reps=3)
+            tune_s = time.perf_counter() - t0
+            num_t = sym_t.factor(dv, precision=args.precision)
+            for _ in range(3):
+                num_t.refactor(dv)
+
+            def _factor_ms(h):
+                evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                       for _ in range(K)]
+                torch.cuda.synchronize()
+                for a, b in evs:
+                    a.record(stream)
+                    h.refactor(dv)
+                    b.record(stream)
+                torch.cuda.synchronize()
+                return sum(a.elapsed_time(b) for a, b in evs) / K
+
+            ms_tuned, ms_default = _factor_ms(num_t), _factor_ms(num)
+            tune = {"table": {k: table[k] for k in sc.TUNE_FIELDS}, "settings_timed": table["tried"],
+                    "tune_s": tune_s, "factor_ms_default": ms_default, "factor_ms_tuned": ms_tuned,
+                    "gflops_default": flops / (ms_default * 1e-3) / 1e9,
+                    "gflops_tuned": flops / (ms_tuned * 1e-3) / 1e9,
+                    "note": "0 = library default; the headline value uses the default plan"}
+            num_t.free()
+        except Exception as ex:  # reported, not fatal: the headline is already measured
+            tune = {"error": str(ex)}
+
     # ---- the low-precision form on the same matrix (factor GFLOP/s, refinement outcome)
     mixed = None
     if not args.no_mixed and args.precision == "fp64":
@@ -509,7 +545,8 @@ def main():
                            "analyze_s": analyze_s},
                 "factor_ms": fac_ms / K, "solve_ms": sol_ms / K, "eta_max": max(etas),
                 "ir_iterations": max(iters), "gpu_launches": launches, "clocks": clk, "e2e": e2e,
-                "roofline": roofline, "solve_roofline": solve_roofline, "cpu_baseline": cpu, "mixed": mixed,
+                "roofline": roofline, "solve_roofline": solve_roofline, "tune": tune, "cpu_baseline": cpu,
+                "mixed": mixed,
                 "tf32_ir_vs_fp64_stencil27_80": compare,
                 "other_workloads": others}
         print(json.dumps(line))

@@ -75,6 +75,37 @@ enum sc_variant { SC_RLB = 0, SC_RL = 1 };
  * ir_tol. */
 enum sc_precision { SC_FP64 = 0, SC_FP32 = 1, SC_TF32 = 2, SC_TF32X3 = 3 };
 
+/* Launch-plan settings (host-side choices only: every setting runs the same
+ * kernels on the same data, so the factor agrees with the default plan up to
+ * the rounding order of the update sums). A zero field means the library
+ * default, given in brackets. sc_tune picks them by timing; a caller may also
+ * pass a table through sc_options.tune.
+ *   tile_min_entries  an Alg. 5 product (B, B') becomes a tiled task when it
+ *                     has >= this many outputs and K >= tile_min_k, or >= 8x
+ *                     this many outputs; smaller ones run in the device loops [1024]
+ *   tile_min_k        see tile_min_entries [16]
+ *   loop_budget       work bound of one device-loop item, in outputs x (K + 4) [32768]
+ *   lookahead         1 = products into the next level's chunks run first and
+ *                     the rest overlap the next level (RLB with graph replay
+ *                     only), -1 = off [1]
+ *   tc_min_k          tensor-core tiles only for K >= tc_min_k (>= 32) [32]
+ *   tc_wide_n         128-column tensor-core tiles for products at least this
+ *                     wide, 64-column tiles below (>= 16) [96]
+ *   thin_dim          products with min(m, n) <= thin_dim (1..8) go to the
+ *                     warp-block kernel, -1 = none [8]
+ *   factor_ms         out (sc_tune): median factor time of this setting */
+typedef struct sc_tune_table {
+    int32_t tile_min_entries;
+    int32_t tile_min_k;
+    int32_t loop_budget;
+    int32_t lookahead;
+    int32_t tc_min_k;
+    int32_t tc_wide_n;
+    int32_t thin_dim;
+    int32_t reserved[7];
+    double factor_ms;
+} sc_tune_table;
+
 typedef struct sc_options {
     int32_t ordering;          /* enum sc_ordering                                  */
     int32_t grid[3];           /* nx, ny, nz for SC_ORDER_GRID_ND (id = x+nx*(y+ny*z)) */
@@ -92,13 +123,14 @@ typedef struct sc_options {
     double merge_frac;         /* supernode merging budget (Sec. 3.1): merge child-parent
                                   pairs by least new fill while the added storage stays
                                   <= merge_frac x the fundamental storage; 0 = off */
-    int32_t reserved[6];
+    const sc_tune_table *tune; /* launch-plan settings (copied), NULL = defaults     */
+    int32_t reserved[4];
 } sc_options;
 
 /* Fills o with the defaults: SC_ORDER_NATURAL, nd_leaf 8, pr 1, SC_RLB, SC_FP64,
  * chunk 64, ir_tol 1e-14, ir_maxit 30, pivot_tau 2^-10, spin_limit 1<<22,
- * use_graph 1, merge_frac 0 (fundamental supernodes). Returns SC_OK, or -1 if
- * o is NULL. */
+ * use_graph 1, merge_frac 0 (fundamental supernodes), tune NULL. Returns
+ * SC_OK, or -1 if o is NULL. */
 int sc_options_default(sc_options *o);
 
 /* ------------------------------------------------------------- symbolic */
@@ -290,8 +322,32 @@ int sc_probe_fma_peak(int kind, void *cuda_stream, double *flops_per_s);
 /* Size of the launch plan a factorization in `precision` would use (host only,
  * no device memory): out[0..nout) receives, in order, the chunk levels, chunks,
  * product tasks, warp-sized tasks, tiled tasks, SIMT tiles, tensor-core tiles,
- * TRSM tiles, RL assembly pairs and device-loop items. Errors: -1, -2, -3. */
+ * TRSM tiles, RL assembly pairs, device-loop items and warp-block units.
+ * Errors: -1, -2, -3. */
 int sc_plan_stats(const sc_symbolic *s, int precision, int64_t *out, int nout);
+
+/* Launch-plan autotuner for one matrix (the level schedule and the product
+ * routing of Alg. 4/5 are fixed by the structure; the thresholds that cut
+ * products into tiled tasks, device-loop items, tensor-core or warp-block
+ * work, and the lookahead split, are chosen here). Starting from s's current
+ * table, it visits the fields of sc_tune_table one at a time (coordinate
+ * descent, one pass), factors the matrix under each candidate value (one
+ * untimed factorization, then `reps` timed ones; CUDA events) and keeps a
+ * value when its median time is below 0.98x the best so far. The winner is
+ * stored in s (every later sc_factor of s uses it) and written to *best with
+ * its time.
+ *   s            symbolic handle with no live numeric handles
+ *   values       FP64 values as for sc_factor (host or device)
+ *   precision    enum sc_precision, or -1 for the handle's option
+ *   reps         timed factorizations per candidate (1..15)
+ *   cuda_stream  stream for the device work (synchronised)
+ *   best         out: the chosen table, factor_ms set
+ *   tried        optional out: settings timed (incl. the starting one)
+ * Errors: -1..-8 for invalid arguments, SC_ERR_IN_USE when numeric handles of
+ * s are alive, a positive column when A is not positive definite, and the
+ * codes of sc_factor. On error s keeps its previous table. */
+int sc_tune(sc_symbolic *s, const double *values, int values_on_device, int precision, int reps, void *cuda_stream,
+            sc_tune_table *best, int32_t *tried);
 
 /* Allocation-free residual and backward error. The paper has no counterpart:
  * this entry point exists for callers that cannot let a library allocate

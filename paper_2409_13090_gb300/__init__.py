@@ -40,7 +40,28 @@ class Options(C.Structure):
                 ("user_perm", C.c_void_p), ("pr", C.c_int32), ("variant", C.c_int32),
                 ("precision", C.c_int32), ("chunk", C.c_int32), ("ir_tol", C.c_double),
                 ("ir_maxit", C.c_int32), ("pivot_tau", C.c_double), ("spin_limit", C.c_int64),
-                ("use_graph", C.c_int32), ("merge_frac", C.c_double), ("reserved", C.c_int32 * 6)]
+                ("use_graph", C.c_int32), ("merge_frac", C.c_double), ("tune", C.c_void_p),
+                ("reserved", C.c_int32 * 4)]
+
+
+TUNE_FIELDS = ["tile_min_entries", "tile_min_k", "loop_budget", "lookahead", "tc_min_k", "tc_wide_n", "thin_dim"]
+
+
+class TuneTable(C.Structure):
+    """sc_tune_table: launch-plan settings (0 = library default)."""
+    _fields_ = [(f, C.c_int32) for f in TUNE_FIELDS] + [("reserved", C.c_int32 * 7), ("factor_ms", C.c_double)]
+
+    def to_dict(self) -> dict:
+        d = {f: getattr(self, f) for f in TUNE_FIELDS}
+        d["factor_ms"] = self.factor_ms
+        return d
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "TuneTable":
+        t = cls()
+        for f in TUNE_FIELDS:
+            setattr(t, f, int(d.get(f, 0)))
+        return t
 
 
 class SymbolicView(C.Structure):
@@ -100,6 +121,7 @@ def lib():
             "sc_plan_stats": ([P, C.c_int, P, C.c_int], C.c_int),
             "sc_test_stall_solve": ([P, i64], C.c_int),
             "sc_factor_batch": ([C.c_int, P, P, C.c_int, C.c_int, P, C.POINTER(P), C.POINTER(P), P], C.c_int),
+            "sc_tune": ([P, P, C.c_int, C.c_int, C.c_int, P, P, P], C.c_int),
             "sc_strerror": ([C.c_int], C.c_char_p),
             "sc_build_info": ([], C.c_char_p),
         }
@@ -233,7 +255,7 @@ class Symbolic:
 
     def __init__(self, A=None, *, ordering="natural", grid=None, nd_leaf=8, user_perm=None, pr=True,
                  variant="rlb", precision="fp64", chunk=64, ir_tol=1e-14, ir_maxit=30, use_graph=True,
-                 merge=0.0, spin_limit=None, pivot_tau=None, _handle=None, _parts=None):
+                 merge=0.0, spin_limit=None, pivot_tau=None, tune=None, _handle=None, _parts=None):
         self._parts = _parts
         if _handle is not None:
             self._h = _handle
@@ -261,6 +283,10 @@ class Symbolic:
             o.spin_limit = int(spin_limit)
         if pivot_tau is not None:
             o.pivot_tau = float(pivot_tau)
+        self._tune_keep = None
+        if tune is not None:
+            self._tune_keep = TuneTable.from_dict(tune)
+            o.tune = C.addressof(self._tune_keep)
         colptr = np.ascontiguousarray(A.colptr, np.int64)
         rowind = np.ascontiguousarray(A.rowind, np.int32)
         rc, h = sc_analyze(A.n, colptr, rowind, o)
@@ -315,7 +341,24 @@ class Symbolic:
         return out
 
     PLAN_KEYS = ["levels", "chunks", "tasks", "warp_tasks", "tiled_tasks", "simt_tiles", "tc_tiles", "trsm_tiles",
-                 "rl_pairs", "loop_items"]
+                 "rl_pairs", "loop_items", "thin_units"]
+
+    def tune(self, values, precision=None, reps=3, stream=None) -> dict:
+        """sc_tune: time candidate launch-plan settings on this matrix and keep
+        the fastest in the handle. Returns the table (fields of TUNE_FIELDS,
+        factor_ms) and the number of settings timed ("tried")."""
+        dev = not isinstance(values, np.ndarray)
+        vals = values if dev else np.ascontiguousarray(values, np.float64)
+        best = TuneTable()
+        tried = C.c_int32(0)
+        prec = -1 if precision is None else PRECISION[precision]
+        rc = lib().sc_tune(self._h, _ptr(vals), int(dev), prec, int(reps), _stream(stream), C.byref(best),
+                           C.byref(tried))
+        if rc != 0:
+            raise SCError(rc, "sc_tune")
+        d = best.to_dict()
+        d["tried"] = tried.value
+        return d
 
     def plan_stats(self, precision="fp64") -> dict:
         out = np.zeros(len(self.PLAN_KEYS), np.int64)

@@ -431,6 +431,8 @@ int analyze_impl(int64_t n, const int64_t *colptr, const int32_t *rowind, const 
     auto s = std::make_unique<sc_symbolic>();
     s->n = n;
     s->opt = o;
+    s->opt.tune = nullptr;
+    if (o.tune) s->tune = *o.tune;
     int64_t nnzA = colptr[n];
     s->colptr.assign(colptr, colptr + n + 1);
     s->rowind.assign(rowind, rowind + nnzA);

@@ -25,6 +25,7 @@ extern "C" int sc_analyze_batch(int count, sc_symbolic *const *syms, sc_symbolic
     try {
         auto b = new sc_symbolic();
         b->opt = syms[0]->opt;
+        b->tune = syms[0]->tune;
         int64_t n0 = 0, ns0 = 0, nnz0 = 0, gl0 = 0, ri0 = 0, blk0 = 0, pair0 = 0, val0 = 0;
         b->colptr.push_back(0);
         b->sup_ptr.push_back(0);

@@ -293,6 +293,7 @@ struct Plan {
 // lookahead: split each level's tiled products into those that target chunks
 // of the next level (crit) and the rest (targets two or more levels up).
 void build_plan(const sc_symbolic *s, int precision, Plan &P, bool lookahead) {
+    const Knobs kn = knobs_of(s->tune);
     P.cd.resize(s->chunks.size());
     int64_t inv = 0;
     for (size_t c = 0; c < s->chunks.size(); c++) {
@@ -338,14 +339,14 @@ void build_plan(const sc_symbolic *s, int precision, Plan &P, bool lookahead) {
             int32_t id = (int32_t)P.tasks.size();
             const int cls = split && !(t.flags & kTaskCrit) ? 1 : 0;  // 0 crit, 1 rest
             P.tasks.push_back(t);
-            const int bn = tc ? tc_width(t, tmap_of_sn) : 0;
+            const int bn = tc ? tc_width(t, tmap_of_sn, kn.tc_min_k, kn.tc_wide_n) : 0;
             if (is_small(t)) {
                 ids_small.push_back(id);
                 P.class_flops[kProfSmall] += task_flops(t);
             } else if (bn) {
                 tc_tiles_of(t, id, bn, bn == 128 ? g_tc[cls] : g_tc64[cls]);
                 P.class_flops[kProfTc] += task_flops(t);
-            } else if (std::min(t.m, t.n) <= kThinDim && !(t.flags & kTaskStoreU)) {
+            } else if (std::min(t.m, t.n) <= std::min(kn.thin_dim, kThinDim) && !(t.flags & kTaskStoreU)) {
                 // a 64 x 64 tile would be mostly padding: warp blocks, kThinWarps per CTA
                 const int ni = block_rows(t.m, t.n, precision == SC_FP64 ? 2 : 1, (t.flags & kTaskLower) != 0);
                 const int nblk = ((t.m + ni - 1) / ni) * ((t.n + 32 / ni - 1) / (32 / ni));
@@ -425,7 +426,8 @@ int plan_stats(const sc_symbolic *s, int precision, int64_t *out, int nout) {
         simt_tiles += l.crit.gemm_cnt + l.rest.gemm_cnt + l.rlg_cnt;
     }
     int64_t v[] = {(int64_t)P.levels.size(), (int64_t)P.cd.size(), (int64_t)P.tasks.size(), small_tasks, tile_tasks,
-                   simt_tiles, tc_tiles, (int64_t)P.trsm.size(), (int64_t)P.rlpairs.size(), (int64_t)P.loops.size()};
+                   simt_tiles, tc_tiles, (int64_t)P.trsm.size(), (int64_t)P.rlpairs.size(), (int64_t)P.loops.size(),
+                   (int64_t)P.thin.size()};
     for (int i = 0; i < nout && i < (int)(sizeof(v) / sizeof(v[0])); i++) out[i] = v[i];
     return SC_OK;
 }
@@ -436,6 +438,7 @@ int numeric_create(sc_symbolic *s, int precision, sc_numeric **out) {
     if (rc) return rc;
     auto h = new sc_numeric();
     h->sym = s;
+    s->refs++;  // released by numeric_free, also on the error paths below
     h->precision = precision;
     h->elt = precision == SC_FP64 ? 8 : 4;
     h->use_graph = s->opt.use_graph != 0;
@@ -490,7 +493,7 @@ int numeric_create(sc_symbolic *s, int precision, sc_numeric **out) {
     }
     Plan P;
     // lookahead needs the captured graph's concurrent branches (RLB schedule)
-    h->lookahead = h->use_graph && s->opt.variant == SC_RLB;
+    h->lookahead = h->use_graph && s->opt.variant == SC_RLB && knobs_of(s->tune).lookahead;
     build_plan(s, precision, P, h->lookahead);
     if (precision != SC_FP64) {
         if (cudaMalloc(&h->d_inv, (size_t)std::max<int64_t>(1, P.inv_size) * sizeof(float)) != cudaSuccess)
@@ -536,7 +539,6 @@ int numeric_create(sc_symbolic *s, int precision, sc_numeric **out) {
         if ((rc = upload(h->d_blk, bd, bytes))) return fail(rc);
         if ((rc = upload(h->d_rbval, s->rb_val, bytes))) return fail(rc);
     }
-    s->refs++;
     *out = h;
     return SC_OK;
 }

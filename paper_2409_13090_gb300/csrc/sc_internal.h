@@ -40,8 +40,33 @@ enum : int32_t {
 
 // Which RLB products run as tiled GEMMs (the rest run inside the device loop
 // over J's blocks). entries = outputs of the product, k = inner dimension.
-SC_HD inline bool tile_task(long long entries, int k) {
-    return (entries >= 1024 && k >= 16) || entries >= 8192;
+SC_HD inline bool tile_task(long long entries, int k, int min_entries, int min_k) {
+    return (entries >= min_entries && k >= min_k) || entries >= 8LL * min_entries;
+}
+
+// Launch-plan settings of sc_tune_table with the defaults filled in.
+struct Knobs {
+    int tile_min_entries = 1024, tile_min_k = 16, loop_budget = 1 << 15;
+    bool lookahead = true;
+    int tc_min_k = 32, tc_wide_n = 96, thin_dim = 8;
+};
+inline Knobs knobs_of(const sc_tune_table &t) {
+    Knobs k;
+    if (t.tile_min_entries) k.tile_min_entries = t.tile_min_entries;
+    if (t.tile_min_k) k.tile_min_k = t.tile_min_k;
+    if (t.loop_budget) k.loop_budget = t.loop_budget;
+    if (t.lookahead) k.lookahead = t.lookahead > 0;
+    if (t.tc_min_k) k.tc_min_k = t.tc_min_k;
+    if (t.tc_wide_n) k.tc_wide_n = t.tc_wide_n;
+    if (t.thin_dim) k.thin_dim = t.thin_dim < 0 ? 0 : t.thin_dim;
+    return k;
+}
+// Field ranges of sc_tune_table (0 = default everywhere).
+inline bool tune_valid(const sc_tune_table &t) {
+    auto in = [](int32_t v, int32_t lo, int32_t hi) { return v == 0 || (v >= lo && v <= hi); };
+    return in(t.tile_min_entries, 1, 1 << 24) && in(t.tile_min_k, 1, 1 << 16) && in(t.loop_budget, 256, 1 << 28) &&
+           (t.lookahead >= -1 && t.lookahead <= 1) && in(t.tc_min_k, 32, 1 << 16) && in(t.tc_wide_n, 16, 1 << 16) &&
+           (t.thin_dim == -1 || in(t.thin_dim, 1, 8));
 }
 
 // Part of Alg. 5's inner loops for one block B of supernode J, run on the
@@ -90,7 +115,8 @@ struct Level {
 
 struct sc_symbolic {
     int64_t n = 0;
-    sc_options opt{};
+    sc_options opt{};      // opt.tune is not kept (NULL); the table is copied into `tune`
+    sc_tune_table tune{};  // launch-plan settings (zero fields = defaults)
     // input pattern (lower, CSC) as given
     std::vector<int64_t> colptr;
     std::vector<int32_t> rowind;

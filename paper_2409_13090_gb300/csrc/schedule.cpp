@@ -27,6 +27,7 @@ namespace sc {
 
 int build_schedule(sc_symbolic *s) {
     const int64_t ns = s->nsuper;
+    const Knobs kn = knobs_of(s->tune);
     int32_t W = s->opt.chunk;
     if (W < 1) W = 64;
     if (W > 64) W = 64;
@@ -125,7 +126,7 @@ int build_schedule(sc_symbolic *s) {
                 // Alg. 5's loops over J's ancestors and blocks: large (B, B') products become tiled tasks;
                 // the rest run on the device in items of bounded cost, each item
                 // one block B and a range of the runs B' below it.
-                const int64_t kLoopBudget = 1 << 15;
+                const int64_t kLoopBudget = kn.loop_budget;
                 for (int64_t q = s->rb_pair_ptr[J]; q < s->rb_pair_ptr[J + 1]; q++) {
                     int32_t P = s->rb_pair_P[q];
                     const int32_t *rb = s->rb_val.data() + s->rb_val_ptr[q];
@@ -144,7 +145,7 @@ int build_schedule(sc_symbolic *s) {
                         int64_t cost = 0;
                         bool open = false;  // item holds work
                         long long tri = (long long)nb * (nb + 1) / 2;
-                        if (tile_task(tri, nJ)) {
+                        if (tile_task(tri, nJ, kn.tile_min_entries, kn.tile_min_k)) {
                             Task t;
                             t.a_off = offJ + bpos[b - b0] * ldJ;
                             t.b_off = t.a_off;
@@ -174,7 +175,7 @@ int build_schedule(sc_symbolic *s) {
                                 e++;
                                 rows += s->blk_size[e];
                             }
-                            if (tile_task((long long)rows * nb, nJ)) {
+                            if (tile_task((long long)rows * nb, nJ, kn.tile_min_entries, kn.tile_min_k)) {
                                 Task g;
                                 g.a_off = offJ + bpos[r - b0] * ldJ;
                                 g.b_off = offJ + bpos[b - b0] * ldJ;

@@ -343,10 +343,11 @@ inline bool tc_gemm_init() {
 
 // Tile width for a product on the tensor cores: 128 or 64 columns, or 0 when the
 // product stays on the SIMT units. Needs a tensor map for the source panel
-// (|J| >= 16: 16-byte row stride, 128-byte aligned base), K >= 32 and m >= 64.
-inline int tc_width(const Task &t, const std::vector<int32_t> &tmap_of_sn) {
-    if (tmap_of_sn[t.src] < 0 || t.k < 32 || t.m < 64 || (t.flags & kTaskStoreU)) return 0;
-    if (t.n >= 96) return 128;
+// (|J| >= 16: 16-byte row stride, 128-byte aligned base), K >= 32 and m >= 64;
+// min_k (>= 32) and wide_n (>= 16) are the plan's thresholds.
+inline int tc_width(const Task &t, const std::vector<int32_t> &tmap_of_sn, int min_k, int wide_n) {
+    if (tmap_of_sn[t.src] < 0 || t.k < 32 || t.k < min_k || t.m < 64 || (t.flags & kTaskStoreU)) return 0;
+    if (t.n >= wide_n && t.n >= 16) return 128;
     if (t.n >= 16) return 64;
     return 0;
 }

@@ -284,3 +284,48 @@ def test_graph_nd_ordering_factor(case, variant):
     X, info = num.solve(B)
     assert info["converged"], info
     assert oracle.backward_error(A, B, X).max() <= 1e-14
+
+
+PLAN_TABLES = [
+    dict(tile_min_entries=64, tile_min_k=1),
+    dict(tile_min_entries=64, tile_min_k=1, thin_dim=-1, loop_budget=256),
+    dict(tile_min_entries=1 << 20, loop_budget=1 << 17),
+    dict(lookahead=-1, thin_dim=4),
+    dict(tc_min_k=128, tc_wide_n=16),
+    dict(tc_wide_n=128, tile_min_entries=512, tile_min_k=32),
+]
+
+
+@pytest.mark.parametrize("table", range(len(PLAN_TABLES)))
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("tf32", 2e-2)])
+def test_launch_plan_settings_keep_parity(table, prec, tol):
+    """Every launch-plan setting the tuner may pick (and extreme ones) gives
+    the same factor: products only move between kernels."""
+    A = _grid_case("st27_14")
+    sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid, tune=PLAN_TABLES[table])
+    o, Lo = _oracle_L(A, oracle.nd_grid(*A.grid, 8))
+    num = sym.factor(A.values, precision=prec)
+    assert num.rc == 0
+    _check_L(num.export_L(), Lo, tol)
+    B = inputs.rhs(A.n, 2, 3)
+    X, info = num.solve(B)
+    assert info["converged"], info
+    assert oracle.backward_error(A, B, X).max() <= 1e-14
+
+
+@pytest.mark.parametrize("name,prec,tol", [("diff7_24", "fp64", 1e-10), ("st27_14", "tf32", 2e-2)])
+def test_tuner_keeps_the_fastest_setting(name, prec, tol):
+    A = _grid_case(name)
+    sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid)
+    t = sym.tune(A.values, precision=prec, reps=1)
+    assert t["tried"] >= 5 and t["factor_ms"] > 0, t
+    # the table is a valid option set; the tuned handle factors correctly
+    sc.Symbolic(A, ordering="grid_nd", grid=A.grid, tune={k: t[k] for k in sc.TUNE_FIELDS})
+    o, Lo = _oracle_L(A, oracle.nd_grid(*A.grid, 8))
+    num = sym.factor(A.values, precision=prec)
+    assert num.rc == 0
+    _check_L(num.export_L(), Lo, tol)
+    # a live numeric handle blocks retuning
+    with pytest.raises(sc.SCError) as e:
+        sym.tune(A.values, precision=prec, reps=1)
+    assert e.value.code == sc.SC_ERR_IN_USE

@@ -221,3 +221,55 @@ def test_graph_nd_fill_close_to_geometric_nd():
         nnz[name] = sc.Symbolic(A, pr=False, **kw).view()["nnzL"]
     assert nnz["graph"] < 2.0 * nnz["grid"], nnz
     assert nnz["graph"] < 0.5 * nnz["natural"], nnz
+
+
+def test_tune_table_changes_only_the_launch_plan():
+    """The launch-plan settings move products between tiled tasks, device
+    loops, tensor-core tiles and warp blocks (seen in the host-side plan), and
+    leave every symbolic array bit-exact with the oracle."""
+    A = inputs.diffusion_3d_7pt(14, 14, 14, seed=1)
+    o = oracle.Oracle(A, oracle.nd_grid(*A.grid, 8), pr=True).symbolic()
+
+    def plan(**t):
+        sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid, tune=t or None)
+        v = sym.view()
+        for k in KEYS:
+            assert np.array_equal(v[k], getattr(o, k)), (t, k)
+        return sym.plan_stats("fp64"), sym.plan_stats("tf32")
+
+    b64, btf = plan()
+    assert btf["tc_tiles"] > 0 and b64["loop_items"] > 0
+    # smaller tiling thresholds: more tiled tasks, among them thin ones
+    f64, _ = plan(tile_min_entries=64, tile_min_k=1)
+    assert f64["tiled_tasks"] > b64["tiled_tasks"] and f64["thin_units"] > 0
+    n64, _ = plan(tile_min_entries=64, tile_min_k=1, thin_dim=-1)
+    assert n64["thin_units"] == 0 and n64["simt_tiles"] > f64["simt_tiles"]
+    h64, _ = plan(tile_min_entries=64, tile_min_k=1, thin_dim=4)
+    assert 0 < h64["thin_units"] < f64["thin_units"]
+    # larger thresholds: the Alg. 5 products stay in the device loops
+    l64, _ = plan(tile_min_entries=1 << 20)
+    assert l64["tiled_tasks"] < b64["tiled_tasks"]
+    s64, _ = plan(loop_budget=256)
+    assert s64["loop_items"] > b64["loop_items"] and s64["tiled_tasks"] == b64["tiled_tasks"]
+    _, ttf = plan(tc_min_k=1 << 16)
+    assert ttf["tc_tiles"] == 0 and ttf["simt_tiles"] > btf["simt_tiles"]
+    _, wtf = plan(tc_wide_n=16, lookahead=-1)
+    assert 0 < wtf["tc_tiles"] <= btf["tc_tiles"]
+
+
+@pytest.mark.parametrize("bad", [dict(lookahead=2), dict(tc_min_k=16), dict(tc_wide_n=8), dict(thin_dim=9),
+                                 dict(thin_dim=-2), dict(loop_budget=100), dict(tile_min_entries=-1)])
+def test_tune_table_ranges(bad):
+    A = inputs.laplacian_2d(8, 8)
+    with pytest.raises(sc.SCError) as e:
+        sc.Symbolic(A, tune=bad)
+    assert e.value.code == -4
+
+
+def test_tune_argument_checks_before_device_work():
+    A = inputs.laplacian_2d(8, 8)
+    sym = sc.Symbolic(A)
+    for kw, code in [(dict(reps=0), -5), (dict(reps=16), -5), (dict(precision="fp64", reps=0), -5)]:
+        with pytest.raises(sc.SCError) as e:
+            sym.tune(A.values, **kw)
+        assert e.value.code == code
