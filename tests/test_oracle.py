@@ -381,3 +381,27 @@ def test_nd_graph_is_a_dissection():
                 seen.add(u)
                 stack.append(u)
     assert len(seen) < len(keep)
+
+
+@pytest.mark.parametrize("case", ["grid3d", "rand"])
+def test_llt_probe_on_the_oracle_factor(case):
+    """The size-independent check used on full-size GPU factors: the oracle's
+    FP64 factor gives rounding-level residuals, and one wrong entry of L (a
+    planted mistake) is seen."""
+    from tests.factor_props import llt_probe
+    if case == "grid3d":
+        A = inputs.diffusion_3d_7pt(12, 11, 10, seed=4)
+        perm0 = oracle.nd_grid(12, 11, 10, 8)
+    else:
+        A = inputs.random_spd(400, 0.02, 8)
+        perm0 = None
+    o = oracle.Oracle(A, perm0, pr=True, merge=0.125)
+    assert o.factor() == 0
+    s = o.symbolic()
+    view = {"perm": s.perm, "sup_ptr": s.sup_ptr, "gl_ptr": s.gl_ptr, "glbind": s.glbind}
+    L = o.L_supernodal()
+    assert llt_probe(A, view, L) <= 1e-14
+    bad = L.copy()
+    k = int(np.argmax(np.abs(bad)))
+    bad[k] *= 1.01
+    assert llt_probe(A, view, bad) > 1e-4
