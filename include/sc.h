@@ -326,6 +326,36 @@ int sc_probe_fma_peak(int kind, void *cuda_stream, double *flops_per_s);
  * Errors: -1, -2, -3. */
 int sc_plan_stats(const sc_symbolic *s, int precision, int64_t *out, int nout);
 
+/* Host-side check of the device schedule of s (no device work): recomputes,
+ * from the symbolic structures alone, every address range the factor kernels
+ * derive from a product task, a device-loop item (Alg. 5's SYRK on B and GEMMs
+ * of the runs B' through relindB) or an RL assembly pair (Alg. 4, relind), and
+ * checks that each lies inside its source panel / target panel, in the lower
+ * trapezoid of the target, that the target is the source's own panel (in-panel
+ * updates, the only plain non-atomic writes) or an ancestor's, that a run B'
+ * maps to consecutive rows of P, that the columns read are factored at the
+ * product's level or before and the columns written after it, and that the
+ * critical-product flag matches the target's chunk level. Where each entry
+ * lands is checked against its definition: the target row and column are the
+ * positions in glbind(P) of the source rows (the relind maps are not used).
+ *   out[0..nout): products checked, loop products checked, RL assembly entries
+ *   checked, level of the first violation (-1 if none), its kind (0 if none:
+ *   1 source range, 2 target range, 3 trapezoid, 4 not an ancestor, 5 level
+ *   order, 6 critical flag, 7 run mapping, 8 RL pool, 9 RL relind, 10 plain
+ *   write outside the own panel, 11 an entry not landing at its row's and
+ *   column's positions in glbind(P)).
+ * Returns SC_OK, SC_ERR_INTERNAL when a violation is found, -1 / -2 for NULL
+ * arguments. */
+int sc_check_schedule(const sc_symbolic *s, int64_t *out, int nout);
+
+/* Test hook: plants one mistake of the given kind (1 a GEMM target one row
+ * too high, 2 a critical product marked as other, 3 an in-panel update reading
+ * one column too many, 4 a loop item reaching past its blocks) in s's schedule
+ * so that a test can see sc_check_schedule find it. s can no longer be factored
+ * (sc_factor returns SC_ERR_INTERNAL). Returns SC_OK, -1, -2 for a bad kind,
+ * or SC_ERR_UNSUPPORTED when the schedule has no entry of that kind. */
+int sc_test_perturb_schedule(sc_symbolic *s, int kind);
+
 /* Launch-plan autotuner for one matrix (the level schedule and the product
  * routing of Alg. 4/5 are fixed by the structure; the thresholds that cut
  * products into tiled tasks, device-loop items, tensor-core or warp-block

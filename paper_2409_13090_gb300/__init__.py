@@ -122,6 +122,8 @@ def lib():
             "sc_test_stall_solve": ([P, i64], C.c_int),
             "sc_factor_batch": ([C.c_int, P, P, C.c_int, C.c_int, P, C.POINTER(P), C.POINTER(P), P], C.c_int),
             "sc_tune": ([P, P, C.c_int, C.c_int, C.c_int, P, P, P], C.c_int),
+            "sc_check_schedule": ([P, P, C.c_int], C.c_int),
+            "sc_test_perturb_schedule": ([P, C.c_int], C.c_int),
             "sc_strerror": ([C.c_int], C.c_char_p),
             "sc_build_info": ([], C.c_char_p),
         }
@@ -342,6 +344,22 @@ class Symbolic:
 
     PLAN_KEYS = ["levels", "chunks", "tasks", "warp_tasks", "tiled_tasks", "simt_tiles", "tc_tiles", "trsm_tiles",
                  "rl_pairs", "loop_items", "thin_units"]
+
+    CHECK_KINDS = {0: "ok", 1: "source range", 2: "target range", 3: "trapezoid", 4: "not an ancestor",
+                   5: "level order", 6: "critical flag", 7: "run mapping", 8: "RL pool", 9: "RL relind",
+                   10: "plain write outside the own panel", 11: "entry mapping"}
+
+    def check_schedule(self) -> dict:
+        """sc_check_schedule: host-side bounds / order check of the device schedule."""
+        out = np.zeros(5, np.int64)
+        rc = lib().sc_check_schedule(self._h, _ptr(out), len(out))
+        if rc not in (0, SC_ERR_INTERNAL):
+            raise SCError(rc, "sc_check_schedule")
+        return {"ok": rc == 0, "tasks": int(out[0]), "loop_products": int(out[1]), "rl_entries": int(out[2]),
+                "bad_level": int(out[3]), "kind": self.CHECK_KINDS.get(int(out[4]), str(out[4]))}
+
+    def _perturb_schedule(self, kind: int) -> int:
+        return lib().sc_test_perturb_schedule(self._h, int(kind))
 
     def tune(self, values, precision=None, reps=3, stream=None) -> dict:
         """sc_tune: time candidate launch-plan settings on this matrix and keep

@@ -434,6 +434,7 @@ int plan_stats(const sc_symbolic *s, int precision, int64_t *out, int nout) {
 
 int numeric_create(sc_symbolic *s, int precision, sc_numeric **out) {
     if (precision < SC_FP64 || precision > SC_TF32X3) return -3;
+    if (s->poisoned) return SC_ERR_INTERNAL;
     int rc = set_smem_attrs();
     if (rc) return rc;
     auto h = new sc_numeric();

@@ -155,6 +155,7 @@ struct sc_symbolic {
     std::vector<int64_t> csr_map;  // CSR entry -> index into values
     double anorm_inf_pattern = 0;  // unused placeholder
     std::atomic<int> refs{0};
+    bool poisoned = false;  // a test hook altered the schedule: never factored
 };
 
 namespace sc {
