@@ -61,7 +61,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 print(out)
     if force or jobs or not os.path.exists(LIB):
         tmp = LIB + f".{os.getpid()}.tmp"
-        run([nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static"])
+        run([nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static", "-ldl"])
         os.replace(tmp, LIB)
     return LIB
 

@@ -31,6 +31,7 @@ int sc_options_default(sc_options *o) {
 }
 
 int sc_analyze(int64_t n, const int64_t *colptr, const int32_t *rowind, const sc_options *o, sc_symbolic **out) {
+    sc::NvtxRange range("sc_analyze");
     if (!out) return -5;
     *out = nullptr;
     sc_options def;
@@ -90,6 +91,7 @@ int sc_symbolic_free(sc_symbolic *s) {
 
 int sc_factor(sc_symbolic *s, const double *values, int values_on_device, int precision, void *cuda_stream,
               sc_numeric **out, sc_factor_info *info) {
+    sc::NvtxRange range("sc_factor");
     if (!s) return -1;
     if (!values) return -2;
     if (values_on_device != 0 && values_on_device != 1) return -3;
@@ -117,6 +119,7 @@ int sc_factor(sc_symbolic *s, const double *values, int values_on_device, int pr
 int sc_factor_batch(int count, sc_symbolic *const *syms, const double *const *values, int values_on_device,
                     int precision, void *cuda_stream, sc_symbolic **batch_sym, sc_numeric **out,
                     sc_factor_info *info) {
+    sc::NvtxRange range("sc_factor_batch");
     if (count < 1) return -1;
     if (!syms) return -2;
     if (!values) return -3;
@@ -160,6 +163,7 @@ int sc_factor_batch(int count, sc_symbolic *const *syms, const double *const *va
 }
 
 int sc_refactor(sc_numeric *h, const double *values, int values_on_device, void *cuda_stream, sc_factor_info *info) {
+    sc::NvtxRange range("sc_refactor");
     if (!h) return -1;
     if (!values) return -2;
     if (values_on_device != 0 && values_on_device != 1) return -3;
@@ -168,6 +172,7 @@ int sc_refactor(sc_numeric *h, const double *values, int values_on_device, void 
 
 int sc_solve(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, double *X, int64_t ldx, int on_device,
              void *cuda_stream, sc_solve_info *info) {
+    sc::NvtxRange range("sc_solve");
     if (!h) return -1;
     if (nrhs < 1) return -2;
     if (!B) return -3;

@@ -16,6 +16,7 @@ void append_shift(std::vector<T> &dst, const std::vector<T> &src, T shift, bool 
 }  // namespace
 
 extern "C" int sc_analyze_batch(int count, sc_symbolic *const *syms, sc_symbolic **out) {
+    sc::NvtxRange range("sc_analyze_batch");
     if (count < 1) return -1;
     if (!syms) return -2;
     if (!out) return -3;

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/sc.h"
+#include <nvtx3/nvToolsExt.h>
 
 namespace sc {
 
@@ -159,6 +160,14 @@ struct sc_symbolic {
 };
 
 namespace sc {
+// NVTX range over one library call: the phases show up in a profiler's
+// timeline; without a tool attached the calls do nothing.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 int analyze_impl(int64_t n, const int64_t *colptr, const int32_t *rowind, const sc_options &o,
                  sc_symbolic **out);
 int build_schedule(sc_symbolic *s);

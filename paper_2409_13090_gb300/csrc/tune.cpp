@@ -61,6 +61,7 @@ int time_setting(sc_symbolic *s, const sc_tune_table &t, bool rebuild, const dou
 
 extern "C" int sc_tune(sc_symbolic *s, const double *values, int values_on_device, int precision, int reps,
                        void *cuda_stream, sc_tune_table *best, int32_t *tried) {
+    sc::NvtxRange range("sc_tune");
     if (!s) return -1;
     if (!values) return -2;
     if (values_on_device != 0 && values_on_device != 1) return -3;
