@@ -52,6 +52,8 @@ extern "C" {
 #define SC_ERR_IN_USE (-105)        /* symbolic handle still referenced      */
 #define SC_ERR_INTERNAL (-106)      /* an internal consistency check failed  */
 #define SC_ERR_UNSUPPORTED (-107)   /* option not available in this library  */
+#define SC_ERR_IO (-108)            /* a file could not be written or read, or is
+                                       not a valid symbolic file of this library */
 
 /* --------------------------------------------------------------- options */
 /* SC_ORDER_GRID_ND: geometric nested dissection of an nx x ny x nz grid
@@ -183,6 +185,21 @@ int sc_symbolic_export(const sc_symbolic *s, sc_symbolic_view *v);
  * of relind(C,P) at that distance from its bottom. Errors: -1..-5 when a
  * pointer is NULL or a distance is outside relind(C,P). */
 int sc_relind_compose(const int32_t *rJC, int64_t lenJC, const int32_t *rCP, int64_t lenCP, int32_t *out);
+
+/* Writes s to the file at path (created or truncated): the options, the
+ * launch-plan settings and every host structure of the analysis, with a
+ * checksum, so that a later process can factor without analysing again.
+ * Errors: -1, -2 for NULL arguments, SC_ERR_IO, SC_ERR_OOM, SC_ERR_INTERNAL
+ * for a handle altered by a test hook. */
+int sc_symbolic_save(const sc_symbolic *s, const char *path);
+
+/* Reads a file written by sc_symbolic_save into a new handle (equal to the
+ * saved one in every array sc_symbolic_export shows; the device schedule is
+ * rebuilt and passes sc_check_schedule before the handle is returned). The
+ * file is portable between little-endian 64-bit hosts. Errors: -1, -2 for
+ * NULL arguments, SC_ERR_IO (unreadable, truncated, checksum or version
+ * mismatch, inconsistent sizes), SC_ERR_OOM. */
+int sc_symbolic_load(const char *path, sc_symbolic **out);
 
 /* Frees s. Returns SC_ERR_IN_USE (and frees nothing) while numeric handles
  * made from s are alive; SC_OK otherwise (also for NULL). */

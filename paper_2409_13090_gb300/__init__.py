@@ -29,7 +29,7 @@ _lib = None
 
 SC_OK = 0
 SC_ERR_CUDA, SC_ERR_TIMEOUT, SC_ERR_NOT_CONVERGED, SC_ERR_OOM = -101, -102, -103, -104
-SC_ERR_IN_USE, SC_ERR_INTERNAL, SC_ERR_UNSUPPORTED = -105, -106, -107
+SC_ERR_IN_USE, SC_ERR_INTERNAL, SC_ERR_UNSUPPORTED, SC_ERR_IO = -105, -106, -107, -108
 ORDERING = {"natural": 0, "grid_nd": 1, "user": 2, "graph_nd": 3}
 VARIANT = {"rlb": 0, "rl": 1}
 PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "tf32x3": 3}
@@ -123,6 +123,8 @@ def lib():
             "sc_factor_batch": ([C.c_int, P, P, C.c_int, C.c_int, P, C.POINTER(P), C.POINTER(P), P], C.c_int),
             "sc_tune": ([P, P, C.c_int, C.c_int, C.c_int, P, P, P], C.c_int),
             "sc_check_schedule": ([P, P, C.c_int], C.c_int),
+            "sc_symbolic_save": ([P, C.c_char_p], C.c_int),
+            "sc_symbolic_load": ([C.c_char_p, C.POINTER(P)], C.c_int),
             "sc_test_perturb_schedule": ([P, C.c_int], C.c_int),
             "sc_strerror": ([C.c_int], C.c_char_p),
             "sc_build_info": ([], C.c_char_p),
@@ -348,6 +350,21 @@ class Symbolic:
     CHECK_KINDS = {0: "ok", 1: "source range", 2: "target range", 3: "trapezoid", 4: "not an ancestor",
                    5: "level order", 6: "critical flag", 7: "run mapping", 8: "RL pool", 9: "RL relind",
                    10: "plain write outside the own panel", 11: "entry mapping"}
+
+    def save(self, path) -> None:
+        """sc_symbolic_save: the analysis on disk (factor later without analysing again)."""
+        rc = lib().sc_symbolic_save(self._h, os.fsencode(path))
+        if rc:
+            raise SCError(rc, "sc_symbolic_save")
+
+    @classmethod
+    def load(cls, path) -> "Symbolic":
+        """sc_symbolic_load: a handle from a file written by save()."""
+        h = C.c_void_p()
+        rc = lib().sc_symbolic_load(os.fsencode(path), C.byref(h))
+        if rc:
+            raise SCError(rc, "sc_symbolic_load")
+        return cls(_handle=h)
 
     def check_schedule(self) -> dict:
         """sc_check_schedule: host-side bounds / order check of the device schedule."""

@@ -10,7 +10,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["analyze.cpp", "schedule.cpp", "batch.cpp", "api.cpp", "factor.cu", "solve.cu", "probe.cu", "noalloc.cu", "tune.cpp", "check.cpp"]
+SOURCES = ["analyze.cpp", "schedule.cpp", "batch.cpp", "api.cpp", "factor.cu", "solve.cu", "probe.cu", "noalloc.cu", "tune.cpp", "check.cpp", "serialize.cpp"]
 HEADERS = ["sc_internal.h", "device_types.h", "kernels.cuh", "numeric.h", "tc_gemm.cuh"]
 
 

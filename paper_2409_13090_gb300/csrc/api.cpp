@@ -231,6 +231,7 @@ const char *sc_strerror(int code) {
         case SC_ERR_IN_USE: return "symbolic handle still referenced by numeric handles";
         case SC_ERR_INTERNAL: return "internal consistency check failed";
         case SC_ERR_UNSUPPORTED: return "option not supported by this library";
+        case SC_ERR_IO: return "file not written or read, or not a valid symbolic file";
         default: break;
     }
     if (code < 0 && code > -100) return "invalid argument (argument index = -code)";

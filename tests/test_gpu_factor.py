@@ -329,3 +329,23 @@ def test_tuner_keeps_the_fastest_setting(name, prec, tol):
     with pytest.raises(sc.SCError) as e:
         sym.tune(A.values, precision=prec, reps=1)
     assert e.value.code == sc.SC_ERR_IN_USE
+
+
+def test_loaded_symbolic_factors_like_the_original(tmp_path):
+    """Analyse, save, load in place of a new analysis: the loaded handle's FP64
+    factor matches the oracle's, and its TF32 factor the original handle's."""
+    A = _grid_case("diff7_24")
+    sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid, merge=0.125)
+    sym.save(tmp_path / "a.scs")
+    loaded = sc.Symbolic.load(tmp_path / "a.scs")
+    o = oracle.Oracle(A, oracle.nd_grid(*A.grid, 8), pr=True, merge=0.125)
+    assert o.factor() == 0
+    num = loaded.factor(A.values, precision="fp64")
+    assert num.rc == 0
+    _check_L(num.export_L(), o.L_supernodal(), 1e-10)
+    Lt = sym.factor(A.values, precision="tf32").export_L()
+    Ltl = loaded.factor(A.values, precision="tf32").export_L()
+    assert np.abs(Lt - Ltl).max() <= 1e-5 * np.abs(Lt).max()
+    B = inputs.rhs(A.n, 2, 4)
+    X, info = num.solve(B)
+    assert oracle.backward_error(A, B, X).max() <= 1e-14

@@ -318,3 +318,59 @@ def test_schedule_check_finds_planted_mistakes(kind, expect):
     with pytest.raises(sc.SCError) as e:
         sym.factor(A.values)
     assert e.value.code == sc.SC_ERR_INTERNAL
+
+
+def _same_handles(a, b, precisions=("fp64", "tf32")):
+    va, vb = a.view(), b.view()
+    for k in KEYS:
+        assert np.array_equal(va[k], vb[k]), k
+    for k in ("n", "nsuper", "nnzL", "flops"):
+        assert va[k] == vb[k], k
+    for p in precisions:
+        assert a.plan_stats(p) == b.plan_stats(p), p
+    assert b.check_schedule()["ok"]
+
+
+@pytest.mark.parametrize("case", ["grid_merge", "rl", "graph_nd", "tuned", "batch"])
+def test_symbolic_save_load_round_trip(tmp_path, case):
+    """A saved analysis loads into a handle equal to the original in every
+    exported array and in the launch plan it gives."""
+    A = inputs.workload(2, 0.3)[0]
+    if case == "grid_merge":
+        sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid, merge=0.125)
+    elif case == "rl":
+        sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid, variant="rl", chunk=24)
+    elif case == "graph_nd":
+        sym = sc.Symbolic(inputs.random_spd(400, 0.02, 4), ordering="graph_nd", pr=False)
+    elif case == "tuned":
+        sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid, tune=dict(tile_min_entries=64, thin_dim=4))
+    else:
+        mats, _ = inputs.workload(4, 0.05)
+        sym = sc.Symbolic.batch([sc.Symbolic(M, ordering="grid_nd", grid=M.grid) for M in mats])
+    path = tmp_path / "sym.scs"
+    sym.save(path)
+    _same_handles(sym, sc.Symbolic.load(path))
+
+
+def test_symbolic_load_rejects_damaged_files(tmp_path):
+    A = inputs.laplacian_2d(20, 20)
+    sym = sc.Symbolic(A, ordering="grid_nd", grid=(20, 20, 1))
+    path = tmp_path / "sym.scs"
+    sym.save(path)
+    data = path.read_bytes()
+    cases = {"truncated": data[:-20], "flipped": data[:100] + bytes([data[100] ^ 1]) + data[101:],
+             "empty": b"", "magic": b"X" + data[1:]}
+    for name, blob in cases.items():
+        bad = tmp_path / f"{name}.scs"
+        bad.write_bytes(blob)
+        with pytest.raises(sc.SCError) as e:
+            sc.Symbolic.load(bad)
+        assert e.value.code == sc.SC_ERR_IO, name
+    with pytest.raises(sc.SCError) as e:
+        sc.Symbolic.load(tmp_path / "missing.scs")
+    assert e.value.code == sc.SC_ERR_IO
+    # a handle altered by the test hook is not written
+    assert sym._perturb_schedule(4) == 0
+    with pytest.raises(sc.SCError) as e:
+        sym.save(tmp_path / "poisoned.scs")
+    assert e.value.code == sc.SC_ERR_INTERNAL
