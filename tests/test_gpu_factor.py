@@ -349,3 +349,43 @@ def test_loaded_symbolic_factors_like_the_original(tmp_path):
     B = inputs.rhs(A.n, 2, 4)
     X, info = num.solve(B)
     assert oracle.backward_error(A, B, X).max() <= 1e-14
+
+
+def _degenerate(name):
+    rng = np.random.default_rng(11)
+    if name == "n1":
+        A = inputs.from_lower_pattern(1, [])
+        A.values[:] = 4.0
+    elif name == "diagonal":
+        A = inputs.from_lower_pattern(50, [])
+        A.values[:] = rng.uniform(0.5, 2.0, 50)
+    elif name == "tridiagonal":
+        A = inputs.from_lower_pattern(100, [(i + 1, i) for i in range(99)], seed=2)
+    elif name == "dense":
+        A = inputs.from_lower_pattern(40, [(i, j) for j in range(40) for i in range(j + 1, 40)], seed=3)
+    elif name == "arrowhead":
+        A = inputs.from_lower_pattern(60, [(59, j) for j in range(59)], seed=4)
+    else:  # two independent dense blocks: a forest of two supernodes
+        ents = [(i, j) for j in range(15) for i in range(j + 1, 15)]
+        A = inputs.from_lower_pattern(30, ents + [(i + 15, j + 15) for i, j in ents], seed=5)
+    return A
+
+
+@pytest.mark.parametrize("name", ["n1", "diagonal", "tridiagonal", "dense", "arrowhead", "forest"])
+@pytest.mark.parametrize("variant", ["rlb", "rl"])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5), ("tf32x3", 1e-5)])
+def test_degenerate_structures(name, variant, prec, tol):
+    """The structures at the method's extremes: one unknown, no off-diagonal
+    entries (every supernode a root, no updates), a chain (one level per
+    column), one dense supernode, a star, and a forest. L against the oracle's,
+    then the solve to eta <= 1e-14."""
+    A = _degenerate(name)
+    sym = sc.Symbolic(A, variant=variant)
+    assert sym.check_schedule()["ok"]
+    o, Lo = _oracle_L(A, None)
+    num = sym.factor(A.values, precision=prec)
+    assert num.rc == 0
+    _check_L(num.export_L(), Lo, tol)
+    B = inputs.rhs(A.n, 3, 6)
+    X, info = num.solve(B)
+    assert oracle.backward_error(A, B, X).max() <= 1e-14, info
