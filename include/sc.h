@@ -59,8 +59,17 @@ extern "C" {
 /* SC_ORDER_GRID_ND: geometric nested dissection of an nx x ny x nz grid
  * (grid[] and nd_leaf); SC_ORDER_GRAPH_ND: nested dissection of the matrix
  * graph by breadth-first level structures (nd_leaf), for inputs without a
- * grid; both stand in for the paper's METIS ordering (Sec. 3.1). */
-enum sc_ordering { SC_ORDER_NATURAL = 0, SC_ORDER_GRID_ND = 1, SC_ORDER_USER = 2, SC_ORDER_GRAPH_ND = 3 };
+ * grid; SC_ORDER_GRAPH_ML: as SC_ORDER_GRAPH_ND, but each separator is the
+ * smaller of the level separator and that of a multilevel bisection (heavy-edge
+ * coarsening, FM refinement), which finds the plane separators of stencils with
+ * diagonal coupling. All stand in for the paper's METIS ordering (Sec. 3.1). */
+enum sc_ordering {
+    SC_ORDER_NATURAL = 0,
+    SC_ORDER_GRID_ND = 1,
+    SC_ORDER_USER = 2,
+    SC_ORDER_GRAPH_ND = 3,
+    SC_ORDER_GRAPH_ML = 4
+};
 enum sc_variant { SC_RLB = 0, SC_RL = 1 };
 /* Arithmetic of the numeric factorization:
  *   SC_FP64  every operation in FP64 (the paper's precision, Sec. 3.1);

@@ -6,8 +6,8 @@ never loads it, and the oracle shares no code with it.
 
 The arithmetic lives in `oracle.c` (plain C, FP64). This module only compiles
 it (`build()`) and marshals numpy arrays in and out through ctypes, except for
-`nd_graph`, the general-graph ordering, which is plain Python on sets (small
-cases only).
+the general-graph orderings (`ordering.py`: `nd_graph`, `nd_graph_ml`), which
+are plain Python on sets and dicts (small cases only).
 """
 from __future__ import annotations
 
@@ -66,6 +66,9 @@ def _p(a: np.ndarray):
     return a.ctypes.data_as(C.c_void_p)
 
 
+from .ordering import nd_graph, nd_graph_ml  # noqa: E402,F401  (plain Python; no library code)
+
+
 def nd_grid(nx: int, ny: int, nz: int, leaf: int = 8) -> np.ndarray:
     """Geometric nested-dissection ordering of an nx*ny*nz grid: perm[new] = old."""
     perm = np.empty(nx * ny * nz, dtype=np.int32)
@@ -73,87 +76,6 @@ def nd_grid(nx: int, ny: int, nz: int, leaf: int = 8) -> np.ndarray:
     if rc != 0:
         raise RuntimeError(f"or_nd_grid failed: {rc}")
     return perm
-
-
-def nd_graph(A, leaf: int = 8) -> np.ndarray:
-    """Nested dissection of the graph of A from breadth-first level structures,
-    perm[new] = old. It stands in for the METIS ordering of Sec. 3.1 on inputs
-    given without grid coordinates; the definition (a reading, the paper fixes
-    none) is:
-
-    ND(S), S a vertex set:
-      * |S| <= leaf: the vertices of S in increasing order;
-      * G[S] disconnected: ND of each connected component, the components taken
-        in order of their smallest vertex;
-      * otherwise: r = min S and L_0, L_1, ... the breadth-first levels of G[S]
-        from r; at most 8 times, let c be the vertex of the last level with the
-        fewest neighbours in S (ties: smaller index); if the levels from c are
-        more than those from r, take c as r, else stop. The separator is the
-        first level L_k with 2 |L_0 u ... u L_k| >= |S|, and
-        ND(S) = ND(L_0..L_{k-1}), ND(L_{k+1}..), then L_k in increasing order.
-
-    Pure Python on sets: meant for small test graphs.
-    """
-    n = A.n
-    nbr = [set() for _ in range(n)]
-    for j in range(n):
-        for p in range(int(A.colptr[j]), int(A.colptr[j + 1])):
-            i = int(A.rowind[p])
-            if i != j:
-                nbr[i].add(j)
-                nbr[j].add(i)
-
-    def bfs_levels(r, S):
-        seen = {r}
-        out = [{r}]
-        while True:
-            nxt = set()
-            for v in out[-1]:
-                nxt |= (nbr[v] & S) - seen
-            if not nxt:
-                return out
-            seen |= nxt
-            out.append(nxt)
-
-    def components(S):
-        left = set(S)
-        comps = []
-        while left:
-            comp = set().union(*bfs_levels(min(left), S))
-            comps.append(comp)
-            left -= comp
-        return comps
-
-    def nd(S):
-        if len(S) <= leaf:
-            return sorted(S)
-        comps = components(S)
-        if len(comps) > 1:
-            return [v for c in comps for v in nd(c)]
-        lv = bfs_levels(min(S), S)
-        for _ in range(8):
-            c = min(lv[-1], key=lambda v: (len(nbr[v] & S), v))
-            lc = bfs_levels(c, S)
-            if len(lc) <= len(lv):
-                break
-            lv = lc
-        total = 0
-        for k, level in enumerate(lv):
-            total += len(level)
-            if 2 * total >= len(S):
-                break
-        below = set().union(*lv[:k]) if k > 0 else set()
-        above = set().union(*lv[k + 1:]) if k + 1 < len(lv) else set()
-        return nd(below) + nd(above) + sorted(lv[k])
-
-    import sys
-    old = sys.getrecursionlimit()
-    sys.setrecursionlimit(max(old, 10000))
-    try:
-        perm = nd(set(range(n)))
-    finally:
-        sys.setrecursionlimit(old)
-    return np.asarray(perm, dtype=np.int32)
 
 
 @dataclass

@@ -30,7 +30,7 @@ _lib = None
 SC_OK = 0
 SC_ERR_CUDA, SC_ERR_TIMEOUT, SC_ERR_NOT_CONVERGED, SC_ERR_OOM = -101, -102, -103, -104
 SC_ERR_IN_USE, SC_ERR_INTERNAL, SC_ERR_UNSUPPORTED, SC_ERR_IO = -105, -106, -107, -108
-ORDERING = {"natural": 0, "grid_nd": 1, "user": 2, "graph_nd": 3}
+ORDERING = {"natural": 0, "grid_nd": 1, "user": 2, "graph_nd": 3, "graph_ml": 4}
 VARIANT = {"rlb": 0, "rl": 1}
 PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "tf32x3": 3}
 

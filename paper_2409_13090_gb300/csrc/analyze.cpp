@@ -12,6 +12,7 @@
 //   - partition refinement with an in-place, array-based partition;
 //   - relindB(J,P) by composition with relind(C,P), as Alg. 5 composes them.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <set>
@@ -75,6 +76,224 @@ void grid_nd(int nx, int ny, int nz, int leaf, std::vector<int32_t> &perm) {
 }
 
 // Full symmetric adjacency (no diagonal) of the lower-triangle CSC input.
+// Multilevel bisection of a small weighted graph (local ids 0..n-1, adjacency
+// lists sorted by neighbour id), every choice integer and tie-broken by id:
+//  * coarsening: heavy-edge matching, vertices visited in increasing id, each
+//    unmatched vertex takes the unmatched neighbour of largest edge weight
+//    (ties: smaller vertex weight, then smaller id); coarse ids in visiting
+//    order; repeated while more than 40 vertices remain (at most 30 times) and
+//    a step keeps at most 95 % of the vertices;
+//  * initial partition on the coarsest graph: from each of its first 32
+//    vertices, breadth-first growth (neighbours in increasing id) of part 0
+//    until it holds half the weight, then FM refinement; the smallest cut wins
+//    (ties: better balance, then the earlier seed);
+//  * uncoarsening: the partition is projected and refined again at every level;
+//  * FM refinement: up to 8 passes; a pass moves, one at a time, the unlocked
+//    boundary vertex of largest gain (cut decrease; ties smaller id) whose
+//    move keeps every part at most 55 % of the weight, locks it, and stops
+//    after 25 moves without a new best; it then returns to its best prefix.
+//    Passes end when one finds no improvement.
+namespace ml {
+
+struct WGraph {
+    std::vector<int64_t> vw;
+    std::vector<std::vector<std::pair<int32_t, int64_t>>> adj;  // (neighbour, edge weight), ascending
+    int32_t n() const { return (int32_t)vw.size(); }
+};
+
+constexpr int kCoarseMin = 40, kMaxLevels = 30, kSeeds = 32, kPasses = 8, kStall = 25;
+
+WGraph coarsen(const WGraph &g, std::vector<int32_t> &cmap) {
+    const int32_t n = g.n();
+    std::vector<int32_t> match(n, -1);
+    cmap.assign(n, -1);
+    int32_t nc = 0;
+    for (int32_t v = 0; v < n; v++) {
+        if (match[v] >= 0) continue;
+        int32_t best = -1;
+        int64_t bw = 0;
+        for (const auto &[u, w] : g.adj[v]) {
+            if (match[u] >= 0 || u == v) continue;
+            if (best < 0 || w > bw || (w == bw && g.vw[u] < g.vw[best])) {
+                best = u;
+                bw = w;
+            }
+        }
+        if (best >= 0) {
+            match[v] = best;
+            match[best] = v;
+            cmap[v] = cmap[best] = nc;
+        } else {
+            match[v] = v;
+            cmap[v] = nc;
+        }
+        nc++;
+    }
+    WGraph c;
+    c.vw.assign(nc, 0);
+    c.adj.resize(nc);
+    std::vector<std::vector<int32_t>> members(nc);
+    for (int32_t v = 0; v < n; v++) {
+        c.vw[cmap[v]] += g.vw[v];
+        members[cmap[v]].push_back(v);
+    }
+    std::vector<int64_t> acc(nc, 0);
+    std::vector<int32_t> touched;
+    for (int32_t a = 0; a < nc; a++) {
+        touched.clear();
+        for (int32_t v : members[a])
+            for (const auto &[u, w] : g.adj[v]) {
+                const int32_t b = cmap[u];
+                if (b == a) continue;
+                if (acc[b] == 0) touched.push_back(b);
+                acc[b] += w;
+            }
+        std::sort(touched.begin(), touched.end());
+        for (int32_t b : touched) {
+            c.adj[a].emplace_back(b, acc[b]);
+            acc[b] = 0;
+        }
+    }
+    return c;
+}
+
+int64_t cut_of(const WGraph &g, const std::vector<int8_t> &part) {
+    int64_t c = 0;
+    for (int32_t v = 0; v < g.n(); v++)
+        for (const auto &[u, w] : g.adj[v])
+            if (part[u] != part[v]) c += w;
+    return c / 2;
+}
+
+void fm_refine(const WGraph &g, std::vector<int8_t> &part, int64_t maxw) {
+    const int32_t n = g.n();
+    int64_t W[2] = {0, 0};
+    for (int32_t v = 0; v < n; v++) W[part[v]] += g.vw[v];
+    std::vector<int64_t> gain(n), ext(n);
+    std::vector<char> locked(n);
+    for (int pass = 0; pass < kPasses; pass++) {
+        std::set<std::pair<int64_t, int32_t>> cand;  // (-gain, id) of unlocked boundary vertices
+        for (int32_t v = 0; v < n; v++) {
+            int64_t e = 0, i = 0;
+            for (const auto &[u, w] : g.adj[v]) (part[u] != part[v] ? e : i) += w;
+            ext[v] = e;
+            gain[v] = e - i;
+            locked[v] = 0;
+            if (e > 0) cand.emplace(-gain[v], v);
+        }
+        std::vector<int32_t> moves;
+        int64_t cum = 0, best = 0;
+        size_t best_len = 0;
+        int stall = 0;
+        while (stall < kStall) {
+            int32_t v = -1;
+            for (const auto &[ng, id] : cand)
+                if (W[1 - part[id]] + g.vw[id] <= maxw) {
+                    v = id;
+                    break;
+                }
+            if (v < 0) break;
+            cand.erase({-gain[v], v});
+            const int8_t src = part[v], dst = 1 - src;
+            cum += gain[v];
+            part[v] = dst;
+            W[src] -= g.vw[v];
+            W[dst] += g.vw[v];
+            locked[v] = 1;
+            moves.push_back(v);
+            gain[v] = -gain[v];
+            for (const auto &[u, w] : g.adj[v]) {
+                if (!locked[u] && ext[u] > 0) cand.erase({-gain[u], u});
+                if (part[u] == dst) {
+                    gain[u] -= 2 * w;
+                    ext[u] -= w;
+                } else {
+                    gain[u] += 2 * w;
+                    ext[u] += w;
+                }
+                if (!locked[u] && ext[u] > 0) cand.emplace(-gain[u], u);
+            }
+            if (cum > best) {
+                best = cum;
+                best_len = moves.size();
+                stall = 0;
+            } else {
+                stall++;
+            }
+        }
+        for (size_t q = moves.size(); q > best_len; q--) {
+            const int32_t v = moves[q - 1];
+            const int8_t src = part[v];
+            part[v] = 1 - src;
+            W[src] -= g.vw[v];
+            W[1 - src] += g.vw[v];
+        }
+        if (best <= 0) break;
+    }
+}
+
+std::vector<int8_t> bfs_grow(const WGraph &g, int32_t seed, int64_t half) {
+    const int32_t n = g.n();
+    std::vector<int8_t> part(n, 1);
+    std::vector<char> seen(n, 0);
+    std::vector<int32_t> queue{seed};
+    seen[seed] = 1;
+    int64_t got = 0;
+    for (size_t h = 0; h < queue.size() && got < half; h++) {
+        const int32_t v = queue[h];
+        part[v] = 0;
+        got += g.vw[v];
+        for (const auto &[u, w] : g.adj[v])
+            if (!seen[u]) {
+                seen[u] = 1;
+                queue.push_back(u);
+            }
+    }
+    return part;
+}
+
+std::vector<int8_t> bisect(const WGraph &g0) {
+    std::vector<WGraph> graphs;
+    std::vector<std::vector<int32_t>> cmaps;
+    graphs.push_back(g0);
+    while (graphs.back().n() > kCoarseMin && (int)cmaps.size() < kMaxLevels) {
+        std::vector<int32_t> cmap;
+        WGraph c = coarsen(graphs.back(), cmap);
+        if ((double)c.n() > 0.95 * (double)graphs.back().n()) break;
+        cmaps.push_back(std::move(cmap));
+        graphs.push_back(std::move(c));
+    }
+    int64_t total = 0;
+    for (int64_t w : g0.vw) total += w;
+    const int64_t maxw = (11 * total + 19) / 20;
+    const WGraph &gc = graphs.back();
+    std::vector<int8_t> part;
+    int64_t best_cut = 0, best_bal = 0;
+    for (int32_t seed = 0; seed < std::min<int32_t>(gc.n(), kSeeds); seed++) {
+        std::vector<int8_t> p = bfs_grow(gc, seed, (total + 1) / 2);
+        fm_refine(gc, p, maxw);
+        int64_t w0 = 0;
+        for (int32_t v = 0; v < gc.n(); v++)
+            if (p[v] == 0) w0 += gc.vw[v];
+        const int64_t cut = cut_of(gc, p), bal = std::llabs(total - 2 * w0);
+        if (part.empty() || cut < best_cut || (cut == best_cut && bal < best_bal)) {
+            part = std::move(p);
+            best_cut = cut;
+            best_bal = bal;
+        }
+    }
+    for (size_t l = cmaps.size(); l > 0; l--) {
+        const std::vector<int32_t> &cmap = cmaps[l - 1];
+        std::vector<int8_t> fine(cmap.size());
+        for (size_t v = 0; v < cmap.size(); v++) fine[v] = part[cmap[v]];
+        part = std::move(fine);
+        fm_refine(graphs[l - 1], part, maxw);
+    }
+    return part;
+}
+
+}  // namespace ml
+
 // Nested dissection of a general graph (no coordinates), a stand-in for the
 // paper's METIS ordering on inputs without a grid. For a vertex set S (sorted):
 // |S| <= leaf: emit S ascending. Otherwise split S into the connected
@@ -85,11 +304,16 @@ void grid_nd(int nx, int ny, int nz, int leaf, std::vector<int32_t> &perm) {
 // index, while that raises the eccentricity): the first level k with
 // 2 |L_0 .. L_k| >= |S| is the separator, and the order is ND(levels < k),
 // ND(levels > k), then level k ascending. Neighbours are visited ascending.
+// With `multilevel`, a connected S is also bisected by ml::bisect (unit
+// weights) and its vertex separator taken as the smaller of the two boundary
+// layers (ties: part 0's); that split is used when both remaining parts are
+// non-empty and its separator is smaller than the level separator.
 class GraphND {
   public:
     GraphND(int64_t n, const std::vector<int64_t> &ptr, const std::vector<int32_t> &adj, int leaf,
-            std::vector<int32_t> &out)
-        : ptr_(ptr), adj_(adj), leaf_(leaf), out_(out), inset_(n, 0), seen_(n, 0) {}
+            std::vector<int32_t> &out, bool multilevel = false)
+        : ptr_(ptr), adj_(adj), leaf_(leaf), out_(out), inset_(n, 0), seen_(n, 0), loc_(n, -1),
+          multilevel_(multilevel) {}
 
     void order(std::vector<int32_t> S) {
         if ((int64_t)S.size() <= leaf_) {
@@ -145,9 +369,10 @@ class GraphND {
             if (2 * cum >= (int64_t)S.size()) break;
         }
         std::vector<int32_t> left, right, sep = L[k];
-        for (size_t q = 0; q < L.size(); q++)
-            if (q < k) left.insert(left.end(), L[q].begin(), L[q].end());
-            else if (q > k) right.insert(right.end(), L[q].begin(), L[q].end());
+        if (!multilevel_ || !ml_split(S, st, sep.size(), left, right, sep))
+            for (size_t q = 0; q < L.size(); q++)
+                if (q < k) left.insert(left.end(), L[q].begin(), L[q].end());
+                else if (q > k) right.insert(right.end(), L[q].begin(), L[q].end());
         std::sort(left.begin(), left.end());
         std::sort(right.begin(), right.end());
         std::sort(sep.begin(), sep.end());
@@ -157,6 +382,40 @@ class GraphND {
     }
 
   private:
+    // The multilevel split of the connected set S (sorted, stamped st): fills
+    // left / right / sep and returns true when its separator is smaller than
+    // level_sep vertices and both parts are non-empty.
+    bool ml_split(const std::vector<int32_t> &S, int32_t st, size_t level_sep, std::vector<int32_t> &left,
+                  std::vector<int32_t> &right, std::vector<int32_t> &sep) {
+        const int32_t m = (int32_t)S.size();
+        ml::WGraph g;
+        g.vw.assign(m, 1);
+        g.adj.resize(m);
+        for (int32_t i = 0; i < m; i++) loc_[S[i]] = i;
+        for (int32_t i = 0; i < m; i++)
+            for (int64_t p = ptr_[S[i]]; p < ptr_[S[i] + 1]; p++)
+                if (inset_[adj_[p]] == st) g.adj[i].emplace_back(loc_[adj_[p]], 1);
+        const std::vector<int8_t> part = ml::bisect(g);
+        std::vector<int32_t> b[2];
+        for (int32_t i = 0; i < m; i++)
+            for (const auto &[u, w] : g.adj[i])
+                if (part[u] != part[i]) {
+                    b[part[i]].push_back(i);
+                    break;
+                }
+        const int side = b[0].size() <= b[1].size() ? 0 : 1;
+        std::vector<char> in_sep(m, 0);
+        for (int32_t i : b[side]) in_sep[i] = 1;
+        std::vector<int32_t> p0, p1, sp;
+        for (int32_t i = 0; i < m; i++)
+            (in_sep[i] ? sp : part[i] == 0 ? p0 : p1).push_back(S[i]);
+        if (sp.empty() || p0.empty() || p1.empty() || level_sep <= sp.size()) return false;
+        left = std::move(p0);
+        right = std::move(p1);
+        sep = std::move(sp);
+        return true;
+    }
+
     // breadth-first levels of G[S] (S = vertices stamped st) from root
     std::vector<std::vector<int32_t>> levels(int32_t root, int32_t st) {
         const int32_t bs = ++seen_stamp_;
@@ -182,7 +441,8 @@ class GraphND {
     const std::vector<int32_t> &adj_;
     int64_t leaf_;
     std::vector<int32_t> &out_;
-    std::vector<int32_t> inset_, seen_;
+    std::vector<int32_t> inset_, seen_, loc_;
+    bool multilevel_;
     int32_t set_stamp_ = 0, seen_stamp_ = 0;
 };
 
@@ -455,19 +715,19 @@ int analyze_impl(int64_t n, const int64_t *colptr, const int32_t *rowind, const 
     } else if (o.ordering == SC_ORDER_NATURAL) {
         p0.resize(n);
         std::iota(p0.begin(), p0.end(), 0);
-    } else if (o.ordering != SC_ORDER_GRAPH_ND) {
+    } else if (o.ordering != SC_ORDER_GRAPH_ND && o.ordering != SC_ORDER_GRAPH_ML) {
         return -4;
     }
     std::vector<int64_t> aptr;
     std::vector<int32_t> adj;
     build_adjacency(n, colptr, rowind, aptr, adj);
-    if (o.ordering == SC_ORDER_GRAPH_ND) {
+    if (o.ordering == SC_ORDER_GRAPH_ND || o.ordering == SC_ORDER_GRAPH_ML) {
         if (o.nd_leaf < 1) return -4;
         p0.clear();
         p0.reserve(n);
         std::vector<int32_t> all(n);
         std::iota(all.begin(), all.end(), 0);
-        GraphND(n, aptr, adj, o.nd_leaf, p0).order(std::move(all));
+        GraphND(n, aptr, adj, o.nd_leaf, p0, o.ordering == SC_ORDER_GRAPH_ML).order(std::move(all));
         if ((int64_t)p0.size() != n) return SC_ERR_INTERNAL;
     }
     std::vector<int32_t> ip0(n);

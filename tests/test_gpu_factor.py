@@ -264,19 +264,22 @@ def test_factor_batch_entry_point(prec):
         r0 += A.n
 
 
-@pytest.mark.parametrize("case", ["rand", "diff7_14_no_grid"])
+@pytest.mark.parametrize("ordering", ["graph_nd", "graph_ml"])
+@pytest.mark.parametrize("case", ["rand", "diff7_14_no_grid", "st27_10_no_grid"])
 @pytest.mark.parametrize("variant", ["rlb", "rl"])
-def test_graph_nd_ordering_factor(case, variant):
+def test_graph_nd_ordering_factor(case, variant, ordering):
     """Inputs without grid coordinates ordered by the general-graph nested
-    dissection: the FP64 factor matches the oracle's under the oracle's own
+    dissections: the FP64 factor matches the oracle's under the oracle's own
     restatement of that ordering, and the solve reaches eta <= 1e-14."""
     if case == "rand":
         A = inputs.random_spd(2000, 0.003, 21)
-    else:
+    elif case == "diff7_14_no_grid":
         A = inputs.diffusion_3d_7pt(14, 14, 14, seed=2)
+    else:
+        A = inputs.stencil_3d_27pt(10, 10, 10, seed=2)
     A.grid = None
-    sym = sc.Symbolic(A, ordering="graph_nd", variant=variant)
-    o, Lo = _oracle_L(A, oracle.nd_graph(A, 8))
+    sym = sc.Symbolic(A, ordering=ordering, variant=variant)
+    o, Lo = _oracle_L(A, (oracle.nd_graph_ml if ordering == "graph_ml" else oracle.nd_graph)(A, 8))
     num = sym.factor(A.values, precision="fp64")
     assert num.rc == 0
     _check_L(num.export_L(), Lo, 1e-10)

@@ -405,3 +405,51 @@ def test_llt_probe_on_the_oracle_factor(case):
     k = int(np.argmax(np.abs(bad)))
     bad[k] *= 1.01
     assert llt_probe(A, view, bad) > 1e-4
+
+
+def test_nd_graph_ml_hand_orders():
+    """Two 10-cliques joined by the edge 9-10, leaf 10. The multilevel bisection
+    (20 vertices: no coarsening) grows part 0 from vertex 0 over its clique
+    {0..9} (cut 1, nothing for FM to gain); the boundary layers are {9} and
+    {10}, so the separator is {9}, smaller than the level separator {1..9}
+    (levels from 0 are {0}, {1..9}, {10}, {11..19}; from 11 no deeper). The
+    level-structure order keeps {1..9}."""
+    K = lambda off: [(i + off, j + off) for j in range(10) for i in range(j + 1, 10)]
+    bar = inputs.from_lower_pattern(20, K(0) + K(10) + [(10, 9)])
+    assert oracle.nd_graph_ml(bar, 10).tolist() == list(range(9)) + list(range(10, 20)) + [9]
+    assert oracle.nd_graph(bar, 10).tolist() == [0] + list(range(10, 20)) + list(range(1, 10))
+
+
+def test_multilevel_building_blocks_by_hand():
+    from oracle import ordering as od
+    # heavy-edge matching: 0 takes 2 (weight 5 over 1); 1 stays alone; the two
+    # unit edges 0-1 and 2-1 merge into one coarse edge of weight 2
+    assert od._coarsen([1, 1, 1], [{1: 1, 2: 5}, {0: 1, 2: 1}, {0: 5, 1: 1}]) == ([0, 1, 0], [2, 1], [{1: 2}, {0: 2}])
+    # path 0-1-2-3 cut 3 ways by [0,1,0,1], parts bounded by 3: vertex 1 (gain 2,
+    # the smaller of the two best) moves first; the next moves bring nothing and
+    # are undone; the second pass finds no gain
+    path4 = [{1: 1}, {0: 1, 2: 1}, {1: 1, 3: 1}, {2: 1}]
+    assert od._fm([1] * 4, path4, [0, 1, 0, 1], 3) == [0, 0, 0, 1]
+    # growth from vertex 2 of a 6-path until 3 vertices: 2, then 1 and 3
+    path6 = [{1: 1}, {0: 1, 2: 1}, {1: 1, 3: 1}, {2: 1, 4: 1}, {3: 1, 5: 1}, {4: 1}]
+    assert od._grow([1] * 6, path6, 2, 3) == [1, 0, 0, 0, 1, 1]
+
+
+def test_nd_graph_ml_finds_the_plane_of_a_27_point_cube():
+    """On a 27-point 12^3 cube (no coordinates) the top separator is the axis
+    plane z = 6 (144 vertices, the smallest balanced separator), where the
+    level structure gives a cube shell; the fill is within 10 % of the
+    geometric ND's."""
+    from oracle import ordering as od
+    A = inputs.stencil_3d_27pt(12, 12, 12, seed=3)
+    nbr = od._neighbours(A)
+    adj = [{u: 1 for u in nbr[g]} for g in range(A.n)]
+    part = od._bisect([1] * A.n, adj)
+    b0 = [i for i in range(A.n) if part[i] == 0 and any(part[u] == 1 for u in adj[i])]
+    b1 = [i for i in range(A.n) if part[i] == 1 and any(part[u] == 0 for u in adj[i])]
+    sep = np.array(b0 if len(b0) <= len(b1) else b1)
+    assert len(sep) == 144 and len(np.unique(sep // 144)) == 1
+    f_ml = oracle.Oracle(A, oracle.nd_graph_ml(A, 8), pr=False).symbolic().flops
+    f_geo = oracle.Oracle(A, oracle.nd_grid(12, 12, 12, 8), pr=False).symbolic().flops
+    f_bfs = oracle.Oracle(A, oracle.nd_graph(A, 8), pr=False).symbolic().flops
+    assert f_ml <= 1.1 * f_geo and f_ml < 0.5 * f_bfs, (f_ml, f_geo, f_bfs)

@@ -24,10 +24,10 @@ def built():
     sc.build()
 
 
-def _compare(A, *, grid=None, user_perm=None, pr=True, leaf=8, merge=0.0, graph_nd=False):
-    if graph_nd:
-        perm0 = oracle.nd_graph(A, leaf)
-        lib_sym = sc.Symbolic(A, ordering="graph_nd", nd_leaf=leaf, pr=pr, merge=merge)
+def _compare(A, *, grid=None, user_perm=None, pr=True, leaf=8, merge=0.0, graph_nd=False, graph_ml=False):
+    if graph_nd or graph_ml:
+        perm0 = (oracle.nd_graph_ml if graph_ml else oracle.nd_graph)(A, leaf)
+        lib_sym = sc.Symbolic(A, ordering="graph_ml" if graph_ml else "graph_nd", nd_leaf=leaf, pr=pr, merge=merge)
     elif grid is not None:
         perm0 = oracle.nd_grid(*grid, leaf)
         lib_sym = sc.Symbolic(A, ordering="grid_nd", grid=grid, nd_leaf=leaf, pr=pr, merge=merge)
@@ -177,9 +177,10 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(L, nm), nm
 
 
+@pytest.mark.parametrize("ordering", ["graph_nd", "graph_ml"])
 @pytest.mark.parametrize("case", ["rand", "grid2d", "grid3d", "st27", "disconnected", "path"])
 @pytest.mark.parametrize("leaf", [1, 8, 32])
-def test_graph_nd_ordering_bit_exact(case, leaf):
+def test_graph_nd_ordering_bit_exact(case, leaf, ordering):
     """The general-graph nested dissection (no grid coordinates) gives the same
     permutation as the oracle's set-based restatement, and every symbolic array
     that follows from it agrees bit for bit."""
@@ -209,7 +210,7 @@ def test_graph_nd_ordering_bit_exact(case, leaf):
         ents = [(max(lab[a], lab[b]), min(lab[a], lab[b])) for a, b in ents]
         A = inputs.from_lower_pattern(150, ents, seed=3)
     A.grid = None
-    v = _compare(A, graph_nd=True, leaf=leaf, pr=True)
+    v = _compare(A, graph_nd=ordering == "graph_nd", graph_ml=ordering == "graph_ml", leaf=leaf, pr=True)
     assert np.array_equal(v["perm"][np.argsort(v["perm"])], np.arange(A.n))
 
 
@@ -219,10 +220,16 @@ def test_graph_nd_fill_close_to_geometric_nd():
     A = inputs.diffusion_3d_7pt(16, 16, 16, seed=1)
     nnz = {}
     for name, kw in [("graph", dict(ordering="graph_nd")), ("grid", dict(ordering="grid_nd", grid=(16, 16, 16))),
-                     ("natural", dict(ordering="natural"))]:
+                     ("natural", dict(ordering="natural")), ("ml", dict(ordering="graph_ml"))]:
         nnz[name] = sc.Symbolic(A, pr=False, **kw).view()["nnzL"]
     assert nnz["graph"] < 2.0 * nnz["grid"], nnz
     assert nnz["graph"] < 0.5 * nnz["natural"], nnz
+    assert nnz["ml"] <= nnz["graph"] * 1.05, nnz
+    # 27-point coupling: the level separators are cube shells, the multilevel ones planes
+    A = inputs.stencil_3d_27pt(16, 16, 16, seed=3)
+    fl = {o: sc.Symbolic(A, pr=False, ordering=o, **({"grid": (16, 16, 16)} if o == "grid_nd" else {})).view()["flops"]
+          for o in ("graph_nd", "graph_ml", "grid_nd")}
+    assert fl["graph_ml"] < 1.15 * fl["grid_nd"] and fl["graph_ml"] < 0.4 * fl["graph_nd"], fl
 
 
 def test_tune_table_changes_only_the_launch_plan():
