@@ -15,8 +15,8 @@ nd_graph(A, leaf): ND(S), S a vertex set of the graph of A:
     is the first level L_k with 2 |L_0 u ... u L_k| >= |S|, and
     ND(S) = ND(L_0..L_{k-1}), ND(L_{k+1}..), then L_k in increasing order.
 
-nd_graph_ml(A, leaf): as nd_graph, but a connected S is also bisected by the
-multilevel scheme below (unit weights on G[S], vertices renumbered 0.. in
+nd_graph_ml(A, leaf): as nd_graph, but a connected S of at least 64 vertices
+is also bisected by the multilevel scheme below (unit weights on G[S], vertices renumbered 0.. in
 increasing order); its separator is the smaller boundary layer (the vertices
 of one part with a neighbour in the other; ties: part 0's). That split,
 ND(part 0 minus sep), ND(part 1 minus sep), sep, is used when both parts keep
@@ -51,6 +51,7 @@ import sys
 import numpy as np
 
 COARSE_MIN, MAX_LEVELS, SEEDS, PASSES, STALL = 40, 30, 32, 8, 25
+ML_MIN_SET = 64
 
 
 def _neighbours(A):
@@ -194,7 +195,7 @@ def _bisect(vw, adj):
 
 # ----------------------------------------------------------------- recursion
 
-def _nested_dissection(A, leaf, multilevel):
+def _nested_dissection(A, leaf, multilevel, ml_min=ML_MIN_SET):
     nbr = _neighbours(A)
 
     def levels(r, S):
@@ -254,7 +255,7 @@ def _nested_dissection(A, leaf, multilevel):
         if len(comps) > 1:
             return [v for c in comps for v in nd(c)]
         first, second, sep = level_split(S)
-        if multilevel:
+        if multilevel and len(S) >= ml_min:
             p0, p1, msep = multilevel_split(S)
             if msep and p0 and p1 and len(msep) < len(sep):
                 first, second, sep = p0, p1, msep

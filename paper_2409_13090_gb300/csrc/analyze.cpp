@@ -102,6 +102,7 @@ struct WGraph {
 };
 
 constexpr int kCoarseMin = 40, kMaxLevels = 30, kSeeds = 32, kPasses = 8, kStall = 25;
+constexpr int64_t kMinSet = 64;  // smaller sets take the level split only
 
 WGraph coarsen(const WGraph &g, std::vector<int32_t> &cmap) {
     const int32_t n = g.n();
@@ -167,6 +168,7 @@ int64_t cut_of(const WGraph &g, const std::vector<int8_t> &part) {
 
 void fm_refine(const WGraph &g, std::vector<int8_t> &part, int64_t maxw) {
     const int32_t n = g.n();
+    const bool small = n <= 128;  // candidates found by a scan instead of an ordered set
     int64_t W[2] = {0, 0};
     for (int32_t v = 0; v < n; v++) W[part[v]] += g.vw[v];
     std::vector<int64_t> gain(n), ext(n);
@@ -179,7 +181,7 @@ void fm_refine(const WGraph &g, std::vector<int8_t> &part, int64_t maxw) {
             ext[v] = e;
             gain[v] = e - i;
             locked[v] = 0;
-            if (e > 0) cand.emplace(-gain[v], v);
+            if (e > 0 && !small) cand.emplace(-gain[v], v);
         }
         std::vector<int32_t> moves;
         int64_t cum = 0, best = 0;
@@ -187,13 +189,20 @@ void fm_refine(const WGraph &g, std::vector<int8_t> &part, int64_t maxw) {
         int stall = 0;
         while (stall < kStall) {
             int32_t v = -1;
-            for (const auto &[ng, id] : cand)
-                if (W[1 - part[id]] + g.vw[id] <= maxw) {
-                    v = id;
-                    break;
-                }
+            if (small) {  // the same choice by a scan: largest gain, then smallest id
+                for (int32_t u = 0; u < n; u++)
+                    if (!locked[u] && ext[u] > 0 && W[1 - part[u]] + g.vw[u] <= maxw &&
+                        (v < 0 || gain[u] > gain[v]))
+                        v = u;
+            } else {
+                for (const auto &[ng, id] : cand)
+                    if (W[1 - part[id]] + g.vw[id] <= maxw) {
+                        v = id;
+                        break;
+                    }
+            }
             if (v < 0) break;
-            cand.erase({-gain[v], v});
+            if (!small) cand.erase({-gain[v], v});
             const int8_t src = part[v], dst = 1 - src;
             cum += gain[v];
             part[v] = dst;
@@ -203,7 +212,7 @@ void fm_refine(const WGraph &g, std::vector<int8_t> &part, int64_t maxw) {
             moves.push_back(v);
             gain[v] = -gain[v];
             for (const auto &[u, w] : g.adj[v]) {
-                if (!locked[u] && ext[u] > 0) cand.erase({-gain[u], u});
+                if (!small && !locked[u] && ext[u] > 0) cand.erase({-gain[u], u});
                 if (part[u] == dst) {
                     gain[u] -= 2 * w;
                     ext[u] -= w;
@@ -211,7 +220,7 @@ void fm_refine(const WGraph &g, std::vector<int8_t> &part, int64_t maxw) {
                     gain[u] += 2 * w;
                     ext[u] += w;
                 }
-                if (!locked[u] && ext[u] > 0) cand.emplace(-gain[u], u);
+                if (!small && !locked[u] && ext[u] > 0) cand.emplace(-gain[u], u);
             }
             if (cum > best) {
                 best = cum;
@@ -304,10 +313,11 @@ std::vector<int8_t> bisect(const WGraph &g0) {
 // index, while that raises the eccentricity): the first level k with
 // 2 |L_0 .. L_k| >= |S| is the separator, and the order is ND(levels < k),
 // ND(levels > k), then level k ascending. Neighbours are visited ascending.
-// With `multilevel`, a connected S is also bisected by ml::bisect (unit
-// weights) and its vertex separator taken as the smaller of the two boundary
-// layers (ties: part 0's); that split is used when both remaining parts are
-// non-empty and its separator is smaller than the level separator.
+// With `multilevel`, a connected S of at least 64 vertices is also bisected
+// by ml::bisect (unit weights) and its vertex separator taken as the smaller
+// of the two boundary layers (ties: part 0's); that split is used when both
+// remaining parts are non-empty and its separator is smaller than the level
+// separator.
 class GraphND {
   public:
     GraphND(int64_t n, const std::vector<int64_t> &ptr, const std::vector<int32_t> &adj, int leaf,
@@ -369,7 +379,7 @@ class GraphND {
             if (2 * cum >= (int64_t)S.size()) break;
         }
         std::vector<int32_t> left, right, sep = L[k];
-        if (!multilevel_ || !ml_split(S, st, sep.size(), left, right, sep))
+        if (!multilevel_ || (int64_t)S.size() < ml::kMinSet || !ml_split(S, st, sep.size(), left, right, sep))
             for (size_t q = 0; q < L.size(); q++)
                 if (q < k) left.insert(left.end(), L[q].begin(), L[q].end());
                 else if (q > k) right.insert(right.end(), L[q].begin(), L[q].end());
