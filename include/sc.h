@@ -120,7 +120,8 @@ typedef struct sc_tune_table {
 typedef struct sc_options {
     int32_t ordering;          /* enum sc_ordering                                  */
     int32_t grid[3];           /* nx, ny, nz for SC_ORDER_GRID_ND (id = x+nx*(y+ny*z)) */
-    int32_t nd_leaf;           /* ND: a box of at most this many points is a leaf   */
+    int32_t nd_leaf;           /* ND: a box or vertex set of at most this many
+                                  points is a leaf (grid and graph orderings)      */
     const int32_t *user_perm;  /* SC_ORDER_USER: perm[new] = old, length n          */
     int32_t pr;                /* 1 = partition-refinement reordering within supernodes */
     int32_t variant;           /* enum sc_variant                                   */

@@ -5,7 +5,9 @@
 // factor-storage layout and the map from A's entries into it.
 //
 // Algorithms (chosen for O(nnz(L)) or better cost on multi-million-row inputs):
-//   - nested dissection on a grid with an explicit work stack;
+//   - nested dissection on a grid with an explicit work stack, or on the
+//     matrix graph by level structures, optionally with multilevel bisection
+//     (heavy-edge coarsening, seeded growth, FM refinement);
 //   - elimination tree by Liu's algorithm with path compression;
 //   - column counts by marking the row subtrees of the elimination tree;
 //   - supernode structures by a union over child supernodes only;
