@@ -381,3 +381,27 @@ def test_symbolic_load_rejects_damaged_files(tmp_path):
     with pytest.raises(sc.SCError) as e:
         sym.save(tmp_path / "poisoned.scs")
     assert e.value.code == sc.SC_ERR_INTERNAL
+
+
+def test_c_abi_from_plain_c(tmp_path):
+    """include/sc.h compiles as C99 with warnings as errors, and a C program
+    drives the host half of the ABI (analysis with three orderings, export,
+    schedule check, plan, save / load) against the built library; its numbers
+    match the Python binding's."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lib_dir = os.path.dirname(sc._LIB_PATH)
+    exe = tmp_path / "abi_check"
+    subprocess.check_call([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                           os.path.join(ROOT, "tests", "c_abi", "abi_check.c"), "-o", str(exe), "-L", lib_dir,
+                           "-lsc", "-Wl,-rpath," + lib_dir])
+    out = subprocess.check_output([str(exe), "24", str(tmp_path / "a.scs")], text=True).splitlines()
+    assert len(out) == 3
+    A = inputs.laplacian_2d(24, 24)
+    for line, (ordering, kw) in zip(out, [("grid_nd", dict(grid=(24, 24, 1))), ("graph_nd", {}), ("graph_ml", {})]):
+        f = line.split()
+        v = sc.Symbolic(A, ordering=ordering, **kw).view()
+        assert int(f[5]) == v["nsuper"] and int(f[7]) == v["nnzL"], (line, ordering)
