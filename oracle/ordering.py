@@ -16,11 +16,13 @@ nd_graph(A, leaf): ND(S), S a vertex set of the graph of A:
     ND(S) = ND(L_0..L_{k-1}), ND(L_{k+1}..), then L_k in increasing order.
 
 nd_graph_ml(A, leaf): as nd_graph, but a connected S of at least 64 vertices
-is also bisected by the multilevel scheme below (unit weights on G[S], vertices renumbered 0.. in
-increasing order); its separator is the smaller boundary layer (the vertices
-of one part with a neighbour in the other; ties: part 0's). That split,
-ND(part 0 minus sep), ND(part 1 minus sep), sep, is used when both parts keep
-a vertex and its separator is smaller than the level separator.
+is also bisected by the multilevel scheme below (unit weights on G[S],
+vertices renumbered 0.. in increasing order); its separator is the minimum
+vertex cover of the cut edges (see _min_cover) when that is smaller than the
+smaller boundary layer (the vertices of one part with a neighbour in the
+other; ties: part 0's), else that layer. That split, ND(part 0 minus sep),
+ND(part 1 minus sep), sep, is used when both parts keep a vertex and its
+separator is smaller than the level separator.
 
 Multilevel bisection of a weighted graph (vertex weights vw, edge weights):
   * coarsening, while more than 40 vertices remain and fewer than 30 levels
@@ -193,6 +195,40 @@ def _bisect(vw, adj):
     return part
 
 
+def _min_cover(adj, part, b0):
+    """Minimum vertex cover of the cut edges (Konig's theorem): a maximum
+    matching between the part-0 boundary b0 and part 1 by augmenting paths
+    (each v of b0 in increasing order starts a depth-first search over its
+    part-1 neighbours in increasing order, every part-1 vertex entered at most
+    once per search); Z = the vertices reachable from the unmatched vertices
+    of b0 by alternating paths; the cover is (b0 - Z) with (part 1 in Z)."""
+    mate = {}
+
+    def augment(v, seen):
+        for u in sorted(adj[v]):
+            if part[u] != 1 or u in seen:
+                continue
+            seen.add(u)
+            if u not in mate or augment(mate[u], seen):
+                mate[u], mate[v] = v, u
+                return True
+        return False
+
+    for v in b0:
+        augment(v, set())
+    z = {v for v in b0 if v not in mate}
+    todo = list(z)
+    while todo:
+        v = todo.pop()
+        for u in adj[v]:
+            if part[u] == 1 and u not in z:
+                z.add(u)
+                if u in mate and mate[u] not in z:
+                    z.add(mate[u])
+                    todo.append(mate[u])
+    return {v for v in b0 if v not in z} | {u for u in z if part[u] == 1}
+
+
 # ----------------------------------------------------------------- recursion
 
 def _nested_dissection(A, leaf, multilevel, ml_min=ML_MIN_SET):
@@ -244,6 +280,9 @@ def _nested_dissection(A, leaf, multilevel, ml_min=ML_MIN_SET):
         bnd = [[i for i in range(len(verts)) if part[i] == side and any(part[u] != side for u in adj[i])]
                for side in (0, 1)]
         sep = set(bnd[0] if len(bnd[0]) <= len(bnd[1]) else bnd[1])
+        cover = _min_cover(adj, part, bnd[0])
+        if len(cover) < len(sep):
+            sep = cover
         p0 = {verts[i] for i in range(len(verts)) if part[i] == 0 and i not in sep}
         p1 = {verts[i] for i in range(len(verts)) if part[i] == 1 and i not in sep}
         return p0, p1, {verts[i] for i in sep}

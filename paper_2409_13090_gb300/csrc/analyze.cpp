@@ -303,6 +303,82 @@ std::vector<int8_t> bisect(const WGraph &g0) {
     return part;
 }
 
+// Minimum vertex cover of the cut edges (König): a maximum matching between
+// the boundary layers b0 (part 0, ascending) and b1, found by augmenting paths
+// (Kuhn: each vertex of b0 in increasing order starts a depth-first search
+// over its part-1 neighbours in increasing order, each part-1 vertex visited
+// at most once per search); then Z = the vertices reachable from the
+// unmatched vertices of b0 by alternating paths (any cut edge from part 0,
+// matching edges from part 1), and the cover is (b0 minus Z) with (b1 in Z).
+std::vector<int32_t> min_cover(const WGraph &g, const std::vector<int8_t> &part, const std::vector<int32_t> &b0) {
+    const int32_t n = g.n();
+    std::vector<int32_t> mate(n, -1), seen(n, -1);
+    struct Frame {
+        int32_t v;
+        size_t next;
+    };
+    std::vector<Frame> stack;
+    for (int32_t root : b0) {
+        stack.assign(1, Frame{root, 0});
+        bool found = false;
+        while (!stack.empty() && !found) {
+            Frame &f = stack.back();
+            const auto &adj = g.adj[f.v];
+            bool descended = false;
+            while (f.next < adj.size()) {
+                const int32_t u = adj[f.next].first;
+                if (part[u] != 1 || seen[u] == root) {
+                    f.next++;
+                    continue;
+                }
+                seen[u] = root;
+                if (mate[u] < 0) {
+                    found = true;  // augment along the stack: each frame takes its current neighbour
+                    break;
+                }
+                stack.push_back(Frame{mate[u], 0});
+                descended = true;
+                break;
+            }
+            if (found || descended) continue;
+            stack.pop_back();
+            if (!stack.empty()) stack.back().next++;
+        }
+        if (found)
+            for (const Frame &f : stack) {
+                const int32_t u = g.adj[f.v][f.next].first;
+                mate[u] = f.v;
+                mate[f.v] = u;
+            }
+    }
+    std::vector<char> z(n, 0);
+    std::vector<int32_t> todo;
+    for (int32_t v : b0)
+        if (mate[v] < 0) {
+            z[v] = 1;
+            todo.push_back(v);
+        }
+    while (!todo.empty()) {
+        const int32_t v = todo.back();
+        todo.pop_back();
+        for (const auto &[u, w] : g.adj[v]) {
+            if (part[u] != 1 || z[u]) continue;
+            z[u] = 1;
+            const int32_t x = mate[u];
+            if (x >= 0 && !z[x]) {
+                z[x] = 1;
+                todo.push_back(x);
+            }
+        }
+    }
+    std::vector<int32_t> cover;
+    for (int32_t v = 0; v < n; v++) {
+        const bool boundary0 = part[v] == 0 && mate[v] >= 0;  // matched b0 vertices: the unmatched are in Z
+        if ((boundary0 && !z[v]) || (part[v] == 1 && z[v])) cover.push_back(v);
+    }
+    return cover;
+}
+
 }  // namespace ml
 
 // Nested dissection of a general graph (no coordinates), a stand-in for the
@@ -417,7 +493,8 @@ class GraphND {
                 }
         const int side = b[0].size() <= b[1].size() ? 0 : 1;
         std::vector<char> in_sep(m, 0);
-        for (int32_t i : b[side]) in_sep[i] = 1;
+        const std::vector<int32_t> cover = ml::min_cover(g, part, b[0]);
+        for (int32_t i : cover.size() < b[side].size() ? cover : b[side]) in_sep[i] = 1;
         std::vector<int32_t> p0, p1, sp;
         for (int32_t i = 0; i < m; i++)
             (in_sep[i] ? sp : part[i] == 0 ? p0 : p1).push_back(S[i]);

@@ -435,6 +435,12 @@ def test_multilevel_building_blocks_by_hand():
     # are undone; the second pass finds no gain
     path4 = [{1: 1}, {0: 1, 2: 1}, {1: 1, 3: 1}, {2: 1}]
     assert od._fm([1] * 4, path4, [0, 1, 0, 1], 3) == [0, 0, 0, 1]
+    # cut edges a-c, a-r, a-s, p-c, q-c with a, p, q = 0, 1, 2 (part 0) and
+    # c, r, s = 3, 4, 5: Kuhn matches 0-3, then 1 re-routes 0 to 4 and takes 3,
+    # 2 finds nothing; alternating paths from 2 reach 3 and 1; the cover
+    # {0, 3} is smaller than either boundary layer (3 vertices each)
+    adj6 = [{3: 1, 4: 1, 5: 1}, {3: 1}, {3: 1}, {0: 1, 1: 1, 2: 1}, {0: 1}, {0: 1}]
+    assert od._min_cover(adj6, [0, 0, 0, 1, 1, 1], [0, 1, 2]) == {0, 3}
     # growth from vertex 2 of a 6-path until 3 vertices: 2, then 1 and 3
     path6 = [{1: 1}, {0: 1, 2: 1}, {1: 1, 3: 1}, {2: 1, 4: 1}, {3: 1, 5: 1}, {4: 1}]
     assert od._grow([1] * 6, path6, 2, 3) == [1, 0, 0, 0, 1, 1]
