@@ -671,8 +671,11 @@ void refine(int32_t size, const std::vector<std::vector<int32_t>> &sets, std::ve
 // re-keyed when a merge changes them. The merged supernode keeps P's rows
 // below its last column (S_X lies inside P's columns and S_P).
 void merge_supernodes(int64_t n, double frac, std::vector<int32_t> &sup_ptr, std::vector<int32_t> &sup_of,
-                      std::vector<int64_t> &sptr, std::vector<int32_t> &srows, std::vector<int32_t> &spar,
-                      std::vector<int32_t> &chead, std::vector<int32_t> &cnext, std::vector<int32_t> &ctail) {
+                      const std::vector<int64_t> &cc, const std::vector<int32_t> &parent) {
+    // A fundamental supernode X with last column l has |S_X| = cc[l] - 1 rows
+    // below it, the first of them parent[l] (the etree parent of l); merging a
+    // child into P changes neither P's last column nor its structure, so the
+    // sizes and the parent column are all the merging needs.
     const int64_t ns = (int64_t)sup_ptr.size() - 1;
     auto trap = [](int64_t w, int64_t m) { return w * m - w * (w - 1) / 2; };
     std::vector<int32_t> f(ns), l(ns), own(sup_of);
@@ -683,12 +686,11 @@ void merge_supernodes(int64_t n, double frac, std::vector<int32_t> &sup_ptr, std
         f[X] = sup_ptr[X];
         l[X] = sup_ptr[X + 1] - 1;
         w[X] = l[X] - f[X] + 1;
-        m[X] = w[X] + (sptr[X + 1] - sptr[X]);
+        m[X] = w[X] + (cc[l[X]] - 1);
         S0 += trap(w[X], m[X]);
     }
-    auto minS = [&](int64_t X) -> int32_t { return sptr[X + 1] > sptr[X] ? srows[sptr[X]] : -1; };
     auto parent_now = [&](int64_t X) -> int32_t {
-        int32_t r = minS(X);
+        const int32_t r = parent[l[X]];
         return r < 0 ? -1 : own[r];
     };
     typedef std::pair<int64_t, int32_t> Key;  // (fill, first column)
@@ -726,36 +728,15 @@ void merge_supernodes(int64_t n, double frac, std::vector<int32_t> &sup_ptr, std
             if (alive[C] && parent_now(C) == P) refresh(C);
         }
     }
-    // renumber the surviving supernodes in column order
-    std::vector<int32_t> newid(ns, -1);
+    // the surviving supernodes in column order
     std::vector<int32_t> nptr;
-    std::vector<int64_t> nsptr{0};
-    std::vector<int32_t> nsrows;
-    for (int32_t X = 0; X < ns; X++) {
-        if (!alive[X]) continue;
-        newid[X] = (int32_t)nptr.size();
-        nptr.push_back(f[X]);
-        nsrows.insert(nsrows.end(), srows.begin() + sptr[X], srows.begin() + sptr[X + 1]);
-        nsptr.push_back((int64_t)nsrows.size());
-    }
+    for (int32_t X = 0; X < ns; X++)
+        if (alive[X]) nptr.push_back(f[X]);
     nptr.push_back((int32_t)n);
     const int64_t nn = (int64_t)nptr.size() - 1;
     for (int64_t J = 0; J < nn; J++)
         for (int32_t j = nptr[J]; j < nptr[J + 1]; j++) sup_of[j] = (int32_t)J;
     sup_ptr.swap(nptr);
-    sptr.swap(nsptr);
-    srows.swap(nsrows);
-    spar.assign(nn, -1);
-    chead.assign(nn, -1);
-    cnext.assign(nn, -1);
-    ctail.assign(nn, -1);
-    for (int64_t J = 0; J < nn; J++) {
-        if (sptr[J + 1] == sptr[J]) continue;
-        int32_t P = sup_of[srows[sptr[J]]];
-        spar[J] = P;
-        if (chead[P] == -1) chead[P] = (int32_t)J; else cnext[ctail[P]] = (int32_t)J;
-        ctail[P] = (int32_t)J;
-    }
 }
 
 }  // namespace
@@ -836,23 +817,55 @@ int analyze_impl(int64_t n, const int64_t *colptr, const int32_t *rowind, const 
     std::vector<int32_t> parent(n);
     for (int64_t k = 0; k < n; k++) parent[k] = par0[post[k]] < 0 ? -1 : newof[par0[post[k]]];
 
-    // ---- column counts (row-subtree marking)
-    std::vector<int64_t> cc(n, 1);
+    // ---- column counts in O(nnz(A) alpha) by the row-subtree leaf method of
+    // Gilbert, Ng and Peyton (1994). cc[j] counts the rows i >= j whose row
+    // subtree T_r(i) (the union of the etree paths from each j' < i with
+    // A_ij' != 0, up to i) contains j. For a subtree T rooted at i with leaves
+    // l_1 < ... < l_k in postorder, the weights +1 at every leaf, -1 at
+    // lca(l_t-1, l_t) and -1 at parent(i) sum to [j in T] over the etree
+    // subtree of any j; so cc[j] is the subtree sum of the weights of all rows.
+    // With the columns visited in postorder, j is a leaf of T_r(i) when no
+    // earlier neighbour of row i lies in j's subtree [first[j], j]; the lca of
+    // the previous leaf and j is the lowest unfinished ancestor of the previous
+    // leaf (a disjoint-set forest that links each finished column to its parent).
+    std::vector<int64_t> cc(n, 0);
     {
-        std::vector<int32_t> mark(n, -1);
-        for (int64_t i = 0; i < n; i++) {
-            mark[i] = (int32_t)i;
-            int32_t io = p1[i];
-            for (int64_t p = aptr[io]; p < aptr[io + 1]; p++) {
-                int32_t j = ip1[adj[p]];
-                if (j >= i) continue;
-                while (mark[j] != i) {
-                    mark[j] = (int32_t)i;
-                    cc[j]++;
-                    j = parent[j];
-                }
+        std::vector<int32_t> first(n, -1), prevnbr(n, -1), prevleaf(n, -1), anc(n);
+        for (int64_t j = 0; j < n; j++)
+            for (int64_t k = j; k >= 0 && first[k] < 0; k = parent[k]) first[k] = (int32_t)j;
+        for (int64_t j = 0; j < n; j++) anc[j] = (int32_t)j;
+        auto find = [&](int32_t x) {
+            int32_t r = x;
+            while (anc[r] != r) r = anc[r];
+            while (anc[x] != r) {
+                const int32_t nx = anc[x];
+                anc[x] = r;
+                x = nx;
+            }
+            return r;
+        };
+        auto visit = [&](int32_t i, int32_t j) {  // entry (i, j), i >= j, of the postordered A
+            if (first[j] > prevnbr[i]) {          // j is a leaf of T_r(i)
+                cc[j]++;
+                if (prevleaf[i] >= 0) cc[find(prevleaf[i])]--;
+                prevleaf[i] = j;
+            }
+            prevnbr[i] = j;
+        };
+        for (int64_t j = 0; j < n; j++) {
+            visit((int32_t)j, (int32_t)j);
+            const int32_t jo = p1[j];
+            for (int64_t p = aptr[jo]; p < aptr[jo + 1]; p++) {
+                const int32_t i = ip1[adj[p]];
+                if (i > j) visit(i, (int32_t)j);
+            }
+            if (parent[j] >= 0) {
+                cc[parent[j]]--;
+                anc[j] = parent[j];
             }
         }
+        for (int64_t j = 0; j < n; j++)
+            if (parent[j] >= 0) cc[parent[j]] += cc[j];
     }
 
     // ---- fundamental supernodes
@@ -873,6 +886,14 @@ int analyze_impl(int64_t n, const int64_t *colptr, const int32_t *rowind, const 
     for (int64_t J = 0; J < ns; J++)
         for (int32_t j = sup_ptr[J]; j < sup_ptr[J + 1]; j++) sup_of[j] = (int32_t)J;
 
+    // ---- optional supernode merging (Sec. 3.1), before the structures and the
+    // reordering within supernodes
+    if (o.merge_frac > 0.0) {
+        merge_supernodes(n, o.merge_frac, sup_ptr, sup_of, cc, parent);
+        ns = (int64_t)sup_ptr.size() - 1;
+        s->nsuper = ns;
+    }
+
     // ---- supernode structures S_J (pre-PR labels), union over child supernodes
     std::vector<int64_t> sptr(ns + 1, 0);
     std::vector<int32_t> srows;
@@ -880,10 +901,15 @@ int analyze_impl(int64_t n, const int64_t *colptr, const int32_t *rowind, const 
     std::vector<int32_t> spar(ns, -1);
     std::vector<int32_t> chead(ns, -1), cnext(ns, -1), ctail(ns, -1);
     {
+        // S_J = (rows of A in J's columns, and the S_C of J's child supernodes) below J's
+        // last column. The children's lists are sorted, so with few children they are
+        // merged into the sorted entries of A; with many, marked and sorted at once.
         std::vector<int32_t> mark(n, -1);
-        std::vector<int32_t> lst;
+        std::vector<int32_t> lst, tmp;
         for (int64_t J = 0; J < ns; J++) {
             int32_t f = sup_ptr[J], l = sup_ptr[J + 1] - 1;
+            int nchildren = 0;
+            for (int32_t C = chead[J]; C != -1; C = cnext[C]) nchildren++;
             lst.clear();
             for (int32_t j = f; j <= l; j++) {
                 int32_t jo = p1[j];
@@ -895,21 +921,45 @@ int analyze_impl(int64_t n, const int64_t *colptr, const int32_t *rowind, const 
                     }
                 }
             }
-            for (int32_t C = chead[J]; C != -1; C = cnext[C])
-                for (int64_t p = sptr[C]; p < sptr[C + 1]; p++) {
-                    int32_t i = srows[p];
-                    if (i > l && mark[i] != J) {
-                        mark[i] = (int32_t)J;
-                        lst.push_back(i);
+            if (nchildren <= 4) {
+                std::sort(lst.begin(), lst.end());
+                for (int32_t C = chead[J]; C != -1; C = cnext[C]) {
+                    const int32_t *a = srows.data() + sptr[C], *ae = srows.data() + sptr[C + 1];
+                    a = std::upper_bound(a, ae, l);
+                    tmp.clear();
+                    size_t q = 0;
+                    while (a < ae || q < lst.size()) {
+                        int32_t v;
+                        if (q == lst.size() || (a < ae && *a < lst[q])) v = *a++;
+                        else if (a == ae || lst[q] < *a) v = lst[q++];
+                        else {
+                            v = *a++;
+                            q++;
+                        }
+                        tmp.push_back(v);
                     }
+                    lst.swap(tmp);
                 }
-            std::sort(lst.begin(), lst.end());
+            } else {
+                for (int32_t C = chead[J]; C != -1; C = cnext[C])
+                    for (int64_t p = sptr[C]; p < sptr[C + 1]; p++) {
+                        int32_t i = srows[p];
+                        if (i > l && mark[i] != J) {
+                            mark[i] = (int32_t)J;
+                            lst.push_back(i);
+                        }
+                    }
+                std::sort(lst.begin(), lst.end());
+            }
             srows.insert(srows.end(), lst.begin(), lst.end());
             sptr[J + 1] = (int64_t)srows.size();
-            // consistency with the column counts
+            // consistency with the column counts: S_J is the structure of J's last
+            // column; the other columns' structures lie inside J's (equal for
+            // fundamental supernodes, smaller where merging added zeros)
             int64_t m = (l - f + 1) + (int64_t)lst.size();
-            for (int32_t j = f; j <= l; j++)
-                if (cc[j] != m - (j - f)) return SC_ERR_INTERNAL;
+            if (cc[l] != m - (l - f)) return SC_ERR_INTERNAL;
+            for (int32_t j = f; j < l; j++)
+                if (cc[j] > m - (j - f) || (o.merge_frac <= 0.0 && cc[j] != m - (j - f))) return SC_ERR_INTERNAL;
             if (!lst.empty()) {
                 int32_t P = sup_of[lst[0]];
                 spar[J] = P;
@@ -922,13 +972,6 @@ int analyze_impl(int64_t n, const int64_t *colptr, const int32_t *rowind, const 
     // sum over columns of |L_{*,j}|^2 of the true (fundamental) structure
     s->flops = 0.0;
     for (int64_t j = 0; j < n; j++) s->flops += (double)cc[j] * (double)cc[j];
-
-    // ---- optional supernode merging (Sec. 3.1), before the reordering within supernodes
-    if (o.merge_frac > 0.0) {
-        merge_supernodes(n, o.merge_frac, sup_ptr, sup_of, sptr, srows, spar, chead, cnext, ctail);
-        ns = (int64_t)sup_ptr.size() - 1;
-        s->nsuper = ns;
-    }
 
     // ---- partition refinement within supernodes (on the pre-PR structure)
     std::vector<int32_t> p3 = p1;
