@@ -256,7 +256,9 @@ typedef struct sc_solve_info {
     double eta_max;        /* max over right-hand sides of the backward error    */
     double solve_ms;       /* device time of the whole solve incl. refinement    */
     double *eta;           /* optional [nrhs] output, caller-owned host memory   */
-    int32_t refine;        /* in: 1 = refine even for an FP64 factor (-1 = by precision) */
+    int32_t refine;        /* in: -1 = by precision (refine low-precision factors),
+                              1 = refine, 0 = no refinement. Without info (NULL)
+                              the solve refines by precision.                */
     int32_t kernel_launches; /* out: kernels launched by this solve                */
     int32_t method;        /* in: 0 = classical refinement x += solve(b - A x);
                               1 = conjugate gradients on A x = b preconditioned by
