@@ -405,3 +405,41 @@ def test_c_abi_from_plain_c(tmp_path):
         f = line.split()
         v = sc.Symbolic(A, ordering=ordering, **kw).view()
         assert int(f[5]) == v["nsuper"] and int(f[7]) == v["nnzL"], (line, ordering)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_patterns_all_options(seed):
+    """Random sparse patterns (varied size and density, sometimes disconnected)
+    under every ordering, both variants, merging on/off, PR on/off and several
+    chunk widths: the library's symbolic arrays bit-exact with the oracle's and
+    the device schedule passing the host-side check."""
+    rng = np.random.default_rng(1000 + seed)
+    n = int(rng.integers(5, 160))
+    density = float(rng.choice([0.01, 0.03, 0.08, 0.2]))
+    ents = set()
+    for j in range(n):
+        for i in range(j + 1, n):
+            if rng.random() < density:
+                ents.add((i, j))
+    A = inputs.from_lower_pattern(n, sorted(ents), seed=seed)
+    A.grid = None
+    merge = float(rng.choice([0.0, 0.125, 0.5]))
+    pr = bool(rng.integers(0, 2))
+    variant = str(rng.choice(["rlb", "rl"]))
+    chunk = int(rng.choice([4, 16, 64]))
+    for ordering in ("natural", "graph_nd", "graph_ml", "user"):
+        if ordering == "user":
+            perm0 = rng.permutation(n).astype(np.int32)
+            sym = sc.Symbolic(A, ordering="user", user_perm=perm0, pr=pr, merge=merge, variant=variant, chunk=chunk)
+        elif ordering == "natural":
+            perm0 = None
+            sym = sc.Symbolic(A, pr=pr, merge=merge, variant=variant, chunk=chunk)
+        else:
+            perm0 = (oracle.nd_graph_ml if ordering == "graph_ml" else oracle.nd_graph)(A, 8)
+            sym = sc.Symbolic(A, ordering=ordering, pr=pr, merge=merge, variant=variant, chunk=chunk)
+        o = oracle.Oracle(A, perm0, pr=pr, merge=merge).symbolic()
+        v = sym.view()
+        for k in KEYS:
+            assert np.array_equal(v[k], getattr(o, k)), (ordering, k)
+        chk = sym.check_schedule()
+        assert chk["ok"], (ordering, chk)
