@@ -327,6 +327,33 @@ int sc_factor_batch(int count, sc_symbolic *const *syms, const double *const *va
  * sum_J m_J |J| doubles. Synchronises the handle's last stream. */
 int sc_numeric_export_L(const sc_numeric *h, double *out);
 
+/* Read-only view of the factor where it lives, in device memory: for callers
+ * that check or use L on the GPU without copying it to the host (at the
+ * largest sizes the host copy of sc_numeric_export_L is tens of GB). Storage
+ * layout (Sec. 2.1.1's Lnz, one panel per supernode): supernode J is a
+ * row-major m_J x panel_ld[J] panel at element offset panel_off[J] of lnz;
+ * row r is global row glbind(J)[r] (sc_symbolic_view), column c < |J| is
+ * column f_J + c of the final ordering. Entries with c > r (above the
+ * diagonal of the panel's top block) and columns c >= |J| (row padding) are
+ * not part of L. Entries are FP64 (elt 8) or FP32 (elt 4, every low-precision
+ * factor).
+ *   lnz        device pointer, valid until the handle is refactored or freed;
+ *              the caller must not write through it
+ *   panel_off, panel_ld  host arrays [nsuper], valid while the symbolic
+ *              handle lives
+ * Synchronises the handle's last stream (the factor is complete on return).
+ * Errors: -1, -2 for NULL arguments, SC_ERR_CUDA. */
+typedef struct sc_factor_view {
+    const void *lnz;
+    int32_t elt;
+    int32_t precision;
+    int64_t size;       /* entries of the storage (panels and their padding) */
+    int64_t nsuper;
+    const int64_t *panel_off;
+    const int32_t *panel_ld;
+} sc_factor_view;
+int sc_numeric_view(const sc_numeric *h, sc_factor_view *v);
+
 /* Per-kernel-class profile of one factorization, for roofline reporting: the
  * factorization runs once outside the CUDA graph with CUDA events around every
  * launch on cuda_stream. Each output array has SC_PROF_CLASSES entries, in the
@@ -372,14 +399,18 @@ int sc_plan_stats(const sc_symbolic *s, int precision, int64_t *out, int nout);
  *   1 source range, 2 target range, 3 trapezoid, 4 not an ancestor, 5 level
  *   order, 6 critical flag, 7 run mapping, 8 RL pool, 9 RL relind, 10 plain
  *   write outside the own panel, 11 an entry not landing at its row's and
- *   column's positions in glbind(P)).
+ *   column's positions in glbind(P), 12 a product that the tensor-core
+ *   precisions route to tcgen05 tiles would multiply panel columns past its
+ *   inner dimension: its K is not a whole number of 8-column MMA steps and
+ *   real columns of the source panel follow it).
  * Returns SC_OK, SC_ERR_INTERNAL when a violation is found, -1 / -2 for NULL
  * arguments. */
 int sc_check_schedule(const sc_symbolic *s, int64_t *out, int nout);
 
 /* Test hook: plants one mistake of the given kind (1 a GEMM target one row
  * too high, 2 a critical product marked as other, 3 an in-panel update reading
- * one column too many, 4 a loop item reaching past its blocks) in s's schedule
+ * one column too many, 4 a loop item reaching past its blocks, 5 tensor-core
+ * routing that ignores the K-tail rule) in s's schedule
  * so that a test can see sc_check_schedule find it. s can no longer be factored
  * (sc_factor returns SC_ERR_INTERNAL). Returns SC_OK, -1, -2 for a bad kind,
  * or SC_ERR_UNSUPPORTED when the schedule has no entry of that kind. */
@@ -421,16 +452,24 @@ int sc_tune(sc_symbolic *s, const double *values, int values_on_device, int prec
  *                     int64, col int32, val FP64 -- device memory
  *   nrhs              columns of B, X, R: 1..SC_NOALLOC_MAX_RHS
  *   B, ldb / X, ldx   column-major FP64 inputs (device memory), ld >= n
- *   R, ldr            column-major FP64 output (device memory), ld >= n
- *   eta               nrhs FP64 outputs (device memory)
+ *   R, ldr            column-major FP64 output (device memory), ld >= n. R may
+ *                     be B itself (R == B with ldr == ldb: each row reads its
+ *                     B entry before writing R) but must not overlap X, which
+ *                     other rows are still reading.
+ *   eta               nrhs FP64 outputs (device memory); NaN for a column whose
+ *                     residual, X, B or ||A|| holds a NaN or an infinity, so a
+ *                     test eta <= tol never passes on such a column
  *   cuda_stream       stream for the work; the call returns without waiting
  * Working memory is one fixed array of 3 * SC_NOALLOC_MAX_RHS + 1 doubles
  * (about 24 KB) built into the library; every GPU that loads the library
- * holds it until the process exits. The first call on a device looks up that
- * array's device address (with the device current) and keeps it; make that
- * first call before any stream capture. All calls share the array and each
- * call clears it first, so calls whose work overlaps on the GPU (other
- * streams, other threads) race and must be serialised by the caller.
+ * holds it until the process exits. Each call looks up that array's device
+ * address on the current device (so it is current again after a device reset),
+ * except while cuda_stream is being captured, when the address found by the
+ * last call on that device is reused: the first call on a device therefore
+ * has to come before any stream capture (a first call during a capture returns
+ * SC_ERR_CUDA). All calls share the array and each call clears it
+ * first, so calls whose work overlaps on the GPU (other streams, other
+ * threads) race and must be serialised by the caller.
  * Errors: -1..-12 for the arguments in order (-5: nrhs outside 1..max),
  * SC_ERR_CUDA. */
 #define SC_NOALLOC_MAX_RHS 1024

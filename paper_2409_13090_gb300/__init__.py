@@ -78,6 +78,11 @@ class FactorInfo(C.Structure):
                 ("kernel_launches", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
+class FactorView(C.Structure):
+    _fields_ = [("lnz", C.c_void_p), ("elt", C.c_int32), ("precision", C.c_int32), ("size", C.c_int64),
+                ("nsuper", C.c_int64), ("panel_off", C.c_void_p), ("panel_ld", C.c_void_p)]
+
+
 class SolveInfo(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("eta_max", C.c_double),
                 ("solve_ms", C.c_double), ("eta", C.c_void_p), ("refine", C.c_int32),
@@ -115,6 +120,7 @@ def lib():
             "sc_refactor": ([P, P, C.c_int, P, P], C.c_int),
             "sc_solve": ([P, i64, P, i64, P, i64, C.c_int, P, P], C.c_int),
             "sc_numeric_export_L": ([P, P], C.c_int),
+            "sc_numeric_view": ([P, P], C.c_int),
             "sc_numeric_free": ([P], None),
             "sc_factor_profile": ([P, P, C.c_int, P, P, P, P], C.c_int),
             "sc_probe_fma_peak": ([C.c_int, P, P], C.c_int),
@@ -349,7 +355,8 @@ class Symbolic:
 
     CHECK_KINDS = {0: "ok", 1: "source range", 2: "target range", 3: "trapezoid", 4: "not an ancestor",
                    5: "level order", 6: "critical flag", 7: "run mapping", 8: "RL pool", 9: "RL relind",
-                   10: "plain write outside the own panel", 11: "entry mapping"}
+                   10: "plain write outside the own panel", 11: "entry mapping",
+                   12: "tensor-core K range"}
 
     def save(self, path) -> None:
         """sc_symbolic_save: the analysis on disk (factor later without analysing again)."""
@@ -512,6 +519,25 @@ class Numeric:
             raise SCError(rc, "sc_factor_profile")
         return {k: {"ms": float(ms[i]), "flops": float(fl[i]), "launches": int(ln[i])}
                 for i, k in enumerate(self.PROFILE_CLASSES)}
+
+    def device_view(self) -> dict:
+        """sc_numeric_view: the factor storage where it lives. Returns the panel
+        offsets and leading dimensions (numpy) and `lnz`, a read-only torch
+        tensor over the library's device memory (no copy; valid until the
+        handle is refactored or freed)."""
+        import torch
+        v = FactorView()
+        rc = lib().sc_numeric_view(self._h, C.byref(v))
+        if rc:
+            raise SCError(rc, "sc_numeric_view")
+
+        class _Mem:  # __cuda_array_interface__ (version 2) over the library's buffer
+            __cuda_array_interface__ = {"shape": (int(v.size),), "typestr": "<f8" if v.elt == 8 else "<f4",
+                                        "data": (int(v.lnz), True), "version": 2, "strides": None}
+
+        return {"lnz": torch.as_tensor(_Mem(), device="cuda"), "elt": v.elt,
+                "panel_off": _view_array(v.panel_off, np.int64, int(v.nsuper)),
+                "panel_ld": _view_array(v.panel_ld, np.int32, int(v.nsuper))}
 
     def export_L(self) -> np.ndarray:
         v = self.sym.view()

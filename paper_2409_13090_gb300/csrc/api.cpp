@@ -193,6 +193,21 @@ int sc_numeric_export_L(const sc_numeric *h, double *out) {
     return sc::numeric_export_L(h, out);
 }
 
+int sc_numeric_view(const sc_numeric *h, sc_factor_view *v) {
+    if (!h) return -1;
+    if (!v) return -2;
+    if (h->last_stream && cudaStreamSynchronize(h->last_stream) != cudaSuccess) return SC_ERR_CUDA;
+    const sc_symbolic *s = h->sym;
+    v->lnz = h->d_lnz;
+    v->elt = (int32_t)h->elt;
+    v->precision = h->precision;
+    v->size = s->lnz_size;
+    v->nsuper = s->nsuper;
+    v->panel_off = s->lnz_off.data();
+    v->panel_ld = s->lnz_ld.data();
+    return SC_OK;
+}
+
 int sc_factor_profile(sc_numeric *h, const double *values, int values_on_device, void *cuda_stream, double *ms,
                       double *flops, int32_t *launches) {
     if (!h) return -1;

@@ -27,6 +27,9 @@ enum Violation : int64_t {
     kRelind = 9,        // RL assembly entry outside Lnz(P) or above its diagonal
     kExclusive = 10,    // a plain (non-atomic) update outside the source's own panel
     kMap = 11,          // a target row / column is not the position in glbind(P) of the source's row
+    kTcK = 12,          // a product the tensor-core precisions route to tcgen05 would multiply
+                        // panel columns past its inner dimension (its K is not a whole number of
+                        // MMA steps and real columns of the panel follow it)
 };
 
 struct Checker {
@@ -35,8 +38,9 @@ struct Checker {
     std::vector<int32_t> first_lv;    // supernode -> level of its first chunk
     std::vector<int32_t> last_lv;     // supernode -> level of its last chunk
     std::vector<int32_t> by_off;      // supernodes sorted by Lnz offset
+    Knobs kn;                         // the handle's launch-plan settings
 
-    explicit Checker(const sc_symbolic *s_) : s(s_) {
+    explicit Checker(const sc_symbolic *s_) : s(s_), kn(knobs_of(s_->tune)) {
         clevel.assign(s->chunks.size(), -1);
         for (size_t lv = 0; lv < s->levels.size(); lv++)
             for (int32_t c : s->levels[lv].chunks) clevel[c] = (int32_t)lv;
@@ -87,6 +91,12 @@ struct Checker {
             return kSrcRange;
         // the columns read are factored at this level or before
         if (col_level(s->sup_ptr[J] + t.kx0 + t.k - 1) > lv) return kOrder;
+        // tensor-core tiles (TF32 / TF32x3 plans) multiply K in whole MMA steps:
+        // the columns consumed past kx0 + k must be the panel's zero padding
+        if (tc_route_width(t, nJ, kn.tc_min_k, kn.tc_wide_n, s->test_tc_ignore_tail)) {
+            const int64_t consumed = (int64_t)t.kx0 + (t.k + kTcKStep - 1) / kTcKStep * kTcKStep;
+            if (consumed > t.kx0 + t.k && t.kx0 + t.k < nJ) return kTcK;
+        }
         const bool lower = t.flags & kTaskLower;
         if (t.flags & kTaskStoreU) {
             if (!rl || t.ldc < t.n || t.c_off < 0 || t.c_off + (int64_t)(t.m - 1) * t.ldc + t.n > pool) return kPool;
@@ -247,7 +257,20 @@ extern "C" int sc_check_schedule(const sc_symbolic *s, int64_t *out, int nout) {
 // sc_tune refuse it.
 extern "C" int sc_test_perturb_schedule(sc_symbolic *s, int kind) {
     if (!s) return -1;
-    if (kind < 1 || kind > 4) return -2;
+    if (kind < 1 || kind > 5) return -2;
+    if (kind == 5) {  // tensor-core routing without the K-tail rule: only matters where a K tail exists
+        const Knobs kn = knobs_of(s->tune);
+        for (auto &L : s->levels)
+            for (const Task &t : L.tasks) {
+                const int32_t nJ = s->sup_ptr[t.src + 1] - s->sup_ptr[t.src];
+                if (t.k % kTcKStep != 0 && t.kx0 + t.k < nJ && tc_route_width(t, nJ, kn.tc_min_k, kn.tc_wide_n, true)) {
+                    s->test_tc_ignore_tail = true;
+                    s->poisoned = true;
+                    return SC_OK;
+                }
+            }
+        return SC_ERR_UNSUPPORTED;
+    }
     for (auto &L : s->levels) {
         for (Task &t : L.tasks) {
             const bool inpanel = t.flags & kTaskExclusive;

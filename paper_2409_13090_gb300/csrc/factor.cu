@@ -339,7 +339,9 @@ void build_plan(const sc_symbolic *s, int precision, Plan &P, bool lookahead) {
             int32_t id = (int32_t)P.tasks.size();
             const int cls = split && !(t.flags & kTaskCrit) ? 1 : 0;  // 0 crit, 1 rest
             P.tasks.push_back(t);
-            const int bn = tc ? tc_width(t, tmap_of_sn, kn.tc_min_k, kn.tc_wide_n) : 0;
+            const int bn = tc ? tc_width(t, tmap_of_sn, s->sup_ptr[t.src + 1] - s->sup_ptr[t.src], kn.tc_min_k,
+                                          kn.tc_wide_n, s->test_tc_ignore_tail)
+                             : 0;
             if (is_small(t)) {
                 ids_small.push_back(id);
                 P.class_flops[kProfSmall] += task_flops(t);

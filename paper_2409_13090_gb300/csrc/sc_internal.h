@@ -62,6 +62,28 @@ inline Knobs knobs_of(const sc_tune_table &t) {
     if (t.thin_dim) k.thin_dim = t.thin_dim < 0 ? 0 : t.thin_dim;
     return k;
 }
+// Inner-dimension granularity of one tcgen05.mma of kind::tf32 (K = 8): the
+// tensor-core tile consumes the columns [kx0, kx0 + round_up(k, kTcKStep)) of
+// its source panel.
+constexpr int kTcKStep = 8;
+
+// Tile width of a product on the tensor cores: 128 or 64 columns, or 0 when the
+// product stays on the SIMT units. Needs a tensor map of the source panel
+// (src_width = |J| >= 16: 16-byte row stride), K >= 32 and m >= 64; min_k
+// (>= 32) and wide_n (>= 16) are the plan's thresholds. The tile consumes K in
+// steps of kTcKStep columns, so a K that is not a multiple of it is allowed
+// only where the product's columns end at the panel's last real column (the
+// columns after it are zero padding or outside the tensor map, read as zero):
+// elsewhere the step would multiply the next columns of the panel in.
+// ignore_tail (a test hook only) drops that condition.
+inline int tc_route_width(const Task &t, int src_width, int min_k, int wide_n, bool ignore_tail = false) {
+    if (src_width < 16 || t.k < 32 || t.k < min_k || t.m < 64 || (t.flags & kTaskStoreU)) return 0;
+    if (!ignore_tail && t.k % kTcKStep != 0 && t.kx0 + t.k < src_width) return 0;
+    if (t.n >= wide_n && t.n >= 16) return 128;
+    if (t.n >= 16) return 64;
+    return 0;
+}
+
 // Field ranges of sc_tune_table (0 = default everywhere).
 inline bool tune_valid(const sc_tune_table &t) {
     auto in = [](int32_t v, int32_t lo, int32_t hi) { return v == 0 || (v >= lo && v <= hi); };
@@ -157,6 +179,7 @@ struct sc_symbolic {
     double anorm_inf_pattern = 0;  // unused placeholder
     std::atomic<int> refs{0};
     bool poisoned = false;  // a test hook altered the schedule: never factored
+    bool test_tc_ignore_tail = false;  // test hook: tensor-core routing without the K-tail rule
 };
 
 namespace sc {

@@ -567,9 +567,14 @@ __global__ void k_gather_vals(double *__restrict__ out, const double *__restrict
     if (i < nnz) out[i] = values[map[i]];
 }
 
+// atomic maximum of non-negative doubles by their bit patterns, which order
+// like the values; a NaN with the sign bit clear orders above +inf, so it wins
 __device__ inline void atomic_max_nonneg(double *addr, double v) {
     atomicMax((unsigned long long *)addr, (unsigned long long)__double_as_longlong(v));
 }
+
+// max of two non-negative values or NaNs (a NaN wins: fmax would drop it)
+__device__ inline double nan_max(double a, double b) { return (a != a || a > b) ? a : b; }
 
 // ||A||_inf of the full symmetric matrix from its CSR
 __global__ void k_anorm(const int64_t *__restrict__ ptr, const double *__restrict__ val, int64_t n, double *out) {
@@ -600,9 +605,9 @@ __global__ void k_residual(const int64_t *__restrict__ ptr, const int32_t *__res
     }
     // warp-level maxima first: one atomic per warp instead of one per row
     for (int o = 16; o > 0; o >>= 1) {
-        m0 = fmax(m0, __shfl_xor_sync(0xffffffffu, m0, o));
-        m1 = fmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
-        m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+        m0 = nan_max(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+        m1 = nan_max(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+        m2 = nan_max(m2, __shfl_xor_sync(0xffffffffu, m2, o));
     }
     if ((threadIdx.x & 31) == 0) {
         atomic_max_nonneg(red + 3 * c, m0);
@@ -664,9 +669,9 @@ __global__ void k_cg_step(double *__restrict__ X, double *__restrict__ R, const 
         m2 = fabs(B[g]);
     }
     for (int o = 16; o > 0; o >>= 1) {
-        m0 = fmax(m0, __shfl_xor_sync(0xffffffffu, m0, o));
-        m1 = fmax(m1, __shfl_xor_sync(0xffffffffu, m1, o));
-        m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+        m0 = nan_max(m0, __shfl_xor_sync(0xffffffffu, m0, o));
+        m1 = nan_max(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+        m2 = nan_max(m2, __shfl_xor_sync(0xffffffffu, m2, o));
     }
     if ((threadIdx.x & 31) == 0) {
         atomic_max_nonneg(red + 3 * c, m0);
@@ -941,10 +946,24 @@ int read_eta(sc_numeric *h, int64_t nrhs, cudaStream_t st, std::vector<double> &
     if (werr) return SC_ERR_TIMEOUT;
     eta.resize(nrhs);
     for (int64_t c = 0; c < nrhs; c++) {
-        double den = h->anorm * red[3 * c + 1] + red[3 * c + 2];
-        eta[c] = den > 0 ? red[3 * c] / den : 0.0;
+        const double r = red[3 * c], den = h->anorm * red[3 * c + 1] + red[3 * c + 2];
+        // a NaN or infinity in the residual, the iterate or the right-hand side
+        // gives eta = NaN, never a value that passes the tolerance
+        if (!std::isfinite(r) || !std::isfinite(den)) eta[c] = NAN;
+        else eta[c] = den > 0 ? r / den : (r == 0.0 ? 0.0 : INFINITY);
     }
     return SC_OK;
+}
+
+// largest eta over the columns; +inf when some column's eta is NaN, so the
+// refinement loops treat it as not converged
+double max_eta(const std::vector<double> &eta) {
+    double m = 0.0;
+    for (double e : eta) {
+        if (std::isnan(e)) return INFINITY;
+        m = std::max(m, e);
+    }
+    return m;
 }
 
 }  // namespace
@@ -1020,12 +1039,12 @@ int pcg(sc_numeric *h, int64_t nrhs, cudaStream_t st, double tol, int maxit, dou
         launches += 2;
         it++;
         if ((rc = read_eta(h, nrhs, st, eta))) return rc;
-        emax = *std::max_element(eta.begin(), eta.end());
+        emax = max_eta(eta);
         if (emax <= tol) {
             // the true residual decides
             if ((rc = enqueue_residual(h, nrhs, st, launches))) return rc;
             if ((rc = read_eta(h, nrhs, st, eta))) return rc;
-            emax = *std::max_element(eta.begin(), eta.end());
+            emax = max_eta(eta);
             if (emax < best) {
                 best = emax;
                 best_eta = eta;
@@ -1047,7 +1066,7 @@ int pcg(sc_numeric *h, int64_t nrhs, cudaStream_t st, double tol, int maxit, dou
         // cap reached: keep the better of the last iterate and the best so far, by the true residual
         if ((rc = enqueue_residual(h, nrhs, st, launches))) return rc;
         if ((rc = read_eta(h, nrhs, st, eta))) return rc;
-        emax = *std::max_element(eta.begin(), eta.end());
+        emax = max_eta(eta);
         if (emax < best) {
             best = emax;
             best_eta = eta;
@@ -1098,7 +1117,7 @@ int numeric_solve(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, dou
     std::vector<double> eta, best_eta;
     std::vector<double> hist;
     if ((rc = read_eta(h, nrhs, st, eta))) return rc;
-    double emax = *std::max_element(eta.begin(), eta.end());
+    double emax = max_eta(eta);
     double best = emax;
     best_eta = eta;
     SC_CUDA(cudaMemcpyAsync(h->d_xbest, h->d_x, (size_t)n * nrhs * 8, cudaMemcpyDeviceToDevice, st));
@@ -1115,7 +1134,7 @@ int numeric_solve(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, dou
             if ((rc = run_step(h, nrhs, 1, st, launches))) return rc;
             it++;
             if ((rc = read_eta(h, nrhs, st, eta))) return rc;
-            emax = *std::max_element(eta.begin(), eta.end());
+            emax = max_eta(eta);
             hist.push_back(emax);
             if (emax < best) {
                 best = emax;

@@ -263,8 +263,12 @@ __global__ void __launch_bounds__(kThreads, (Cfg<BN, X3>::CTAS_PER_SM))
                     }
                     fence_after();
                     const uint32_t a0 = a_tile<BN, X3>(smem, s, 0), b0 = b_tile<BN, X3>(smem, s, 0);
+                    // the box holds BK columns; only the 8-column steps inside K are
+                    // multiplied (the columns after K in the box belong to other work)
+                    const int ksteps = min(BK / kTcKStep, (tk.k - kb * BK + kTcKStep - 1) / kTcKStep);
 #pragma unroll
                     for (int kk = 0; kk < BK / 8; kk++) {  // 8 tf32 = 32 bytes along K inside the swizzle row
+                        if (kk >= ksteps) break;
                         if constexpr (X3) {
                             // small terms first: lo*hi, hi*lo, then hi*hi
                             const uint32_t a1 = a_tile<BN, X3>(smem, s, 1), b1 = b_tile<BN, X3>(smem, s, 1);
@@ -341,15 +345,12 @@ inline bool tc_gemm_init() {
                                 Cfg<64, true>::SMEM) == cudaSuccess;
 }
 
-// Tile width for a product on the tensor cores: 128 or 64 columns, or 0 when the
-// product stays on the SIMT units. Needs a tensor map for the source panel
-// (|J| >= 16: 16-byte row stride, 128-byte aligned base), K >= 32 and m >= 64;
-// min_k (>= 32) and wide_n (>= 16) are the plan's thresholds.
-inline int tc_width(const Task &t, const std::vector<int32_t> &tmap_of_sn, int min_k, int wide_n) {
-    if (tmap_of_sn[t.src] < 0 || t.k < 32 || t.k < min_k || t.m < 64 || (t.flags & kTaskStoreU)) return 0;
-    if (t.n >= wide_n && t.n >= 16) return 128;
-    if (t.n >= 16) return 64;
-    return 0;
+// Tile width for a product on the tensor cores (tc_route_width): a source panel
+// without a tensor map stays on the SIMT units.
+inline int tc_width(const Task &t, const std::vector<int32_t> &tmap_of_sn, int src_width, int min_k, int wide_n,
+                    bool ignore_tail) {
+    if (tmap_of_sn[t.src] < 0) return 0;
+    return tc_route_width(t, src_width, min_k, wide_n, ignore_tail);
 }
 
 inline void tc_tiles_of(const Task &t, int32_t id, int bn, std::vector<GemmTile> &out) {

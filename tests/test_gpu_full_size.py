@@ -4,7 +4,10 @@ hold at any size (needs a GB300).
 The oracle cannot factor these in seconds, so the factor is checked by what
 defines it, L L^T = P A P^T, on random probe vectors (tests/factor_props.py,
 pinned on the oracle's factor in test_oracle.py), and the solve by the
-backward error the oracle computes in FP64 on the CPU. Launch configuration
+backward error the oracle computes in FP64 on the CPU (for the anisotropic
+128^3 matrix, whose factor holds 3.2e9 entries, the probe reads the factor in
+place on the GPU with torch; no kernel of the library is involved in the
+check). Launch configuration
 as the benchmark times it: grid ND (leaf 8), PR, supernode merging 0.125, RLB,
 CUDA graph replay.
 
@@ -20,7 +23,7 @@ import pytest
 import oracle
 import paper_2409_13090_gb300 as sc
 from paper_2409_13090_gb300 import inputs
-from tests.factor_props import llt_probe
+from tests.factor_props import llt_probe, llt_probe_device
 
 pytestmark = pytest.mark.gpu
 
@@ -82,3 +85,30 @@ def test_full_batch_of_256_laplacians():
         worst = max(worst, float(oracle.backward_error(M, B[row:row + M.n], X[row:row + M.n]).max()))
         row += M.n
     assert worst <= 1e-14, worst
+
+
+def test_full_anisotropic_128_factor_and_solve():
+    """The anisotropic 7-point matrix on the full 128^3 grid (n = 2,097,152,
+    shift 1e-8, condition number near 1e11), 64 right-hand sides, in the
+    benchmark's launch configuration: the TF32x3 factor with conjugate
+    gradients preconditioned by it, and the FP64 factor with a plain solve.
+    The factor is probed in place on the GPU (L L^T = P A P^T), the solution
+    by the oracle's FP64 backward error of every right-hand side."""
+    A, nrhs = inputs.workload(5)
+    assert A.n == 128 ** 3 and nrhs == 64
+    sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid, nd_leaf=8, pr=True, variant="rlb", merge=0.125)
+    view = sym.view()
+    B = inputs.rhs(A.n, nrhs, inputs.SEED_BASE + 5)
+    for prec, bound in (("tf32x3", 1e-4), ("fp64", 1e-12)):
+        num = sym.factor(A.values, precision=prec)
+        assert num.rc == 0, prec
+        r = llt_probe_device(A, view, num.device_view(), nprobe=1)
+        assert r <= bound, (prec, r)
+        if prec == "fp64":
+            X, info = num.solve(B)
+        else:
+            X, info = num.solve(B, method="cg", max_iterations=1000)
+            assert info["converged"], info
+        eta = oracle.backward_error(A, B, X).max()
+        assert eta <= 1e-14, (prec, eta, info)
+        num.free()

@@ -104,3 +104,34 @@ def test_tf32x3_split_products_reach_fp32_accuracy(case):
         assert oracle.backward_error(A, B, X).max() <= 1e-14
         its[prec] = info["iterations"]
     assert its["tf32x3"] <= its["tf32"], its
+
+
+@pytest.mark.parametrize("prec,tol", [("tf32", 2e-2), ("tf32x3", 1e-3)])
+@pytest.mark.parametrize("chunk", [24, 36, 40, 48])
+@pytest.mark.parametrize("case", ["dense_700", "st27_16"])
+def test_tensor_core_tiles_at_chunk_widths_with_a_k_tail(case, chunk, prec, tol):
+    """Chunk widths other than 32 and 64: the in-panel updates have K = chunk
+    (40, 48: whole 8-column MMA steps but not whole 32-column boxes; 36: not a
+    whole step, kept on the SIMT units unless the product ends at the panel's
+    last column) and macro panels of 240 or 252 columns. The tensor-core tile
+    must multiply exactly K columns: L is compared with the oracle's FP64 L
+    element by element and refinement must reach eta <= 1e-14."""
+    if case == "dense_700":
+        A, perm0, kw = _dense(700, 1), None, dict(ordering="natural")
+    else:
+        A = inputs.stencil_3d_27pt(16, 16, 16, seed=3)
+        perm0, kw = oracle.nd_grid(16, 16, 16, 8), dict(ordering="grid_nd", grid=A.grid)
+    sym = sc.Symbolic(A, chunk=chunk, **kw)
+    assert sym.check_schedule()["ok"]
+    assert sym.plan_stats(prec)["tc_tiles"] > 0
+    o = oracle.Oracle(A, perm0, pr=True)
+    assert o.factor() == 0
+    Lo = o.L_supernodal()
+    num = sym.factor(A.values, precision=prec)
+    assert num.rc == 0
+    err = np.abs(num.export_L() - Lo).max() / np.abs(Lo).max()
+    assert err <= tol, err
+    B = inputs.rhs(A.n, 2, 7)
+    X, info = num.solve(B)
+    assert info["converged"], info
+    assert oracle.backward_error(A, B, X).max() <= 1e-14

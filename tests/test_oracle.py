@@ -55,6 +55,31 @@ def test_worked_example_symbolic(golden):
     assert pat == want
 
 
+def test_levels_are_heights_in_the_supernodal_tree(golden):
+    """level(J) = height of J in the supernodal elimination tree (leaves 0, a
+    parent one above its highest child), by hand: the worked example (J1, J2
+    are leaves below J3), a chain, an arrowhead (leaves under one root), and a
+    tree whose branches differ in length, where height and depth disagree."""
+    s = oracle.Oracle(_example(golden), None, pr=False).symbolic()
+    assert s.level.tolist() == [0, 0, 1]
+    # tridiagonal, natural order: supernodes {0}, ..., {n-3}, {n-2, n-1}, a chain
+    n = 10
+    s = oracle.Oracle(inputs.from_lower_pattern(n, [(j + 1, j) for j in range(n - 1)], seed=1), None,
+                      pr=False).symbolic()
+    assert s.nsuper == n - 1 and s.level.tolist() == list(range(n - 1))
+    # arrowhead (dense last row): every other column is a leaf under the last one
+    s = oracle.Oracle(inputs.from_lower_pattern(n, [(n - 1, j) for j in range(n - 1)], seed=1), None,
+                      pr=False).symbolic()
+    assert s.level.tolist() == [0] * (n - 1) + [1]
+    # columns 0 - 1 - 2 - 4 and 3 - 4, then 4 - 5: etree 0->1->2->4, 3->4, 4->5;
+    # supernodes {0} {1} {2} {3} {4, 5}; heights 0 1 2 0 3 (depths would be 3 2 1 1 0)
+    s = oracle.Oracle(inputs.from_lower_pattern(6, [(1, 0), (2, 1), (4, 2), (4, 3), (5, 4)], seed=1), None,
+                      pr=False).symbolic()
+    assert s.sup_ptr.tolist() == [0, 1, 2, 3, 4, 6]
+    assert [int(p) for p in s.sup_parent] == [1, 2, 4, 4, -1]
+    assert s.level.tolist() == [0, 1, 2, 0, 3]
+
+
 def test_worked_example_pr(golden):
     A = _example(golden)
     s = oracle.Oracle(A, None, pr=True).symbolic()
@@ -405,6 +430,56 @@ def test_llt_probe_on_the_oracle_factor(case):
     k = int(np.argmax(np.abs(bad)))
     bad[k] *= 1.01
     assert llt_probe(A, view, bad) > 1e-4
+
+
+@pytest.mark.parametrize("case", ["grid3d", "rand"])
+def test_llt_probe_device_agrees_with_host_probe(case):
+    """The in-place probe used on factors too large for the host (torch gather /
+    index_add over the storage layout, here on a CPU tensor in the library's
+    padded panel layout built from the oracle's factor): the same residual as
+    the host probe, rounding-level on the oracle's factor, and a planted wrong
+    entry seen."""
+    torch = pytest.importorskip("torch")
+    from tests.factor_props import llt_probe, llt_probe_device
+    if case == "grid3d":
+        A = inputs.diffusion_3d_7pt(12, 11, 10, seed=4)
+        perm0 = oracle.nd_grid(12, 11, 10, 8)
+    else:
+        A = inputs.random_spd(400, 0.02, 8)
+        perm0 = None
+    o = oracle.Oracle(A, perm0, pr=True, merge=0.125)
+    assert o.factor() == 0
+    s = o.symbolic()
+    view = {"perm": s.perm, "sup_ptr": s.sup_ptr, "gl_ptr": s.gl_ptr, "glbind": s.glbind}
+    L = o.L_supernodal()
+    # padded storage: each panel's rows 3 entries longer than its width, junk in
+    # the padding and above the diagonal (neither is part of L)
+    ns = len(s.sup_ptr) - 1
+    w = np.diff(s.sup_ptr).astype(np.int64)
+    m = np.diff(s.gl_ptr).astype(np.int64)
+    ld = w + 3
+    off = np.zeros(ns, np.int64)
+    off[1:] = np.cumsum(m * ld)[:-1]
+    store = np.full(int((m * ld).sum()), 7.0)
+    q = 0
+    for J in range(ns):
+        blk = L[q:q + m[J] * w[J]].reshape(m[J], w[J]).copy()
+        q += m[J] * w[J]
+        blk[np.triu_indices(w[J], 1)] = 5.0
+        store[off[J]:off[J] + m[J] * ld[J]].reshape(m[J], ld[J])[:, :w[J]] = blk
+    dview = {"lnz": torch.tensor(store), "panel_off": off, "panel_ld": ld.astype(np.int32)}
+    r_dev = llt_probe_device(A, view, dview, nprobe=2, group_entries=997)
+    assert r_dev <= 1e-14
+    assert abs(r_dev - llt_probe(A, view, L, nprobe=2)) <= 1e-15
+    k = int(np.argmax(np.abs(L)))
+    bad = L.copy()
+    bad[k] *= 1.01
+    # the same entry in the padded storage
+    J = int(np.searchsorted(np.cumsum(m * w), k, side="right"))
+    kk = k - int((m * w)[:J].sum())
+    dview["lnz"][int(off[J] + (kk // w[J]) * ld[J] + kk % w[J])] *= 1.01
+    assert llt_probe_device(A, view, dview, nprobe=2) > 1e-4
+    assert abs(llt_probe_device(A, view, dview, nprobe=2) - llt_probe(A, view, bad, nprobe=2)) <= 1e-12
 
 
 def test_nd_graph_ml_hand_orders():

@@ -327,6 +327,31 @@ def test_schedule_check_finds_planted_mistakes(kind, expect):
     assert e.value.code == sc.SC_ERR_INTERNAL
 
 
+def test_schedule_check_finds_tensor_core_k_tail():
+    """Chunk widths whose in-panel updates have a K that is not a whole number
+    of 8-column MMA steps (36: K = 36 and macro panels of 252 columns): the
+    library keeps those products off the tensor cores (the check passes), and a
+    plan that routes them there anyway (test hook 5) is found."""
+    A = _dense_spd(300, 5)
+    for chunk in (24, 36, 40, 48, 64):
+        chk = sc.Symbolic(A, ordering="natural", chunk=chunk).check_schedule()
+        assert chk["ok"], (chunk, chk)
+    sym = sc.Symbolic(A, ordering="natural", chunk=36)
+    assert sym._perturb_schedule(5) == 0
+    chk = sym.check_schedule()
+    assert not chk["ok"] and chk["kind"] == "tensor-core K range", chk
+    with pytest.raises(sc.SCError) as e:
+        sym.factor(A.values)
+    assert e.value.code == sc.SC_ERR_INTERNAL
+    # no K tail with chunks of 64: nothing to plant
+    assert sc.Symbolic(A, ordering="natural", chunk=64)._perturb_schedule(5) == sc.SC_ERR_UNSUPPORTED
+
+
+def _dense_spd(n, seed):
+    ents = [(i, j) for j in range(n) for i in range(j + 1, n)]
+    return inputs.from_lower_pattern(n, ents, seed=seed)
+
+
 def _same_handles(a, b, precisions=("fp64", "tf32")):
     va, vb = a.view(), b.view()
     for k in KEYS:

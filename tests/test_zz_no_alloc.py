@@ -10,7 +10,9 @@ The test calls it through the C ABI and checks it against the backward error
 that sc_solve reports for the same solution, on consecutive calls: the first
 two calls on the solution, then a call on a perturbed iterate (larger residual,
 checked against numpy), then the solution again -- which must not see anything
-left over in the shared array from the previous call.
+left over in the shared array from the previous call. Further calls must leave
+the device's free memory and torch's allocations unchanged; a NaN in X gives a
+NaN eta for its column; R may be B itself.
 """
 import ctypes as C
 
@@ -100,6 +102,39 @@ def test_noalloc_residual_eta_matches_solve():
 
     eta3, _ = call(X)  # nothing left over from the previous call
     assert np.allclose(eta3, eta_solve, rtol=1e-12, atol=0.0)
+
+    # the property the entry point exists for: after the calls above, further
+    # calls change neither the device's free memory nor torch's allocations
+    d_X = torch.tensor(np.ascontiguousarray(X.T), device=dev)
+    torch.cuda.synchronize()
+    free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    for _ in range(5):
+        rc = f(n, d_ptr.data_ptr(), d_col.data_ptr(), d_val.data_ptr(), nrhs, d_B.data_ptr(), n, d_X.data_ptr(), n,
+               d_R.data_ptr(), n, d_eta.data_ptr(), stream)
+        assert rc == 0
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == alloc0
+
+    # a NaN in one column of X: that column's eta is NaN (never "converged"),
+    # the other columns keep their values
+    Xn = X.copy()
+    Xn[n // 2, 1] = np.nan
+    eta_n, _ = call(Xn)
+    assert np.isnan(eta_n[1]), eta_n
+    assert np.allclose(eta_n[[0, 2]], eta_solve[[0, 2]], rtol=1e-12, atol=0.0)
+    eta4, _ = call(X)  # and the next call is clean again
+    assert np.allclose(eta4, eta_solve, rtol=1e-12, atol=0.0)
+
+    # R may be B itself
+    d_B2 = d_B.clone()
+    rc = f(n, d_ptr.data_ptr(), d_col.data_ptr(), d_val.data_ptr(), nrhs, d_B2.data_ptr(), n, d_X.data_ptr(), n,
+           d_B2.data_ptr(), n, d_eta.data_ptr(), stream)
+    assert rc == 0
+    torch.cuda.synchronize()
+    _, Rref, an = reference(X)
+    assert np.abs(d_B2.cpu().numpy().T - Rref).max() <= 1e-13 * (an * np.abs(X).max() + np.abs(B).max())
+    assert np.allclose(d_eta.cpu().numpy(), eta_solve, rtol=1e-12, atol=0.0)
 
 
 def test_noalloc_rejects_too_many_right_hand_sides():
