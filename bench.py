@@ -1,20 +1,27 @@
 #!/usr/bin/env python
 """Benchmark: numeric factorization GFLOP/s and solve time of the supernodal
-right-looking Cholesky (RLB) on one GB300.
+right-looking Cholesky (RLB, Alg. 5) on one GB300, FP64 against the
+TF32x3 + refinement form, at <= 1e-14 backward error.
 
-Workload: 3D 7-point variable-coefficient diffusion on a 48^3 grid
-(n = 110,592; edge coefficients log-uniform[1e-2, 1e2]; diagonal = row sum + 1e-6),
-geometric nested dissection, partition refinement, FP64 RLB factor, 4 right-hand
-sides uniform[-1, 1]. Seeded synthetic input (stand-in for the paper's
-SuiteSparse matrices).
+Headline workload (the largest configuration): 3D 7-point anisotropic diffusion
+on a 128^3 grid (n = 2,097,152; coefficients 1:1:100 along x:y:z times
+log-uniform[0.1, 10] noise; diagonal shift 1e-8), geometric nested dissection,
+partition refinement, supernode merging 12.5 %, 64 right-hand sides
+uniform[-1, 1]. Seeded synthetic input (stand-in for the paper's SuiteSparse
+matrices).
 
-One step = refactor (values already in HBM: value load, every level's POTRF,
-TRSM and RLB updates) + solve of the 4 right-hand sides (forward and backward
-sweeps, FP64 residual and backward error).
-value = sum_j |L_{*,j}|^2 / factor time (GFLOP/s), over the timed steps.
+One step = refactor in FP64 (values already in HBM: value load, every level's
+POTRF, TRSM and RLB updates) + solve of the 64 right-hand sides (forward and
+backward sweeps, FP64 residual and backward error).
+value = sum_j |L_{*,j}|^2 / factor time (GFLOP/s) over the timed steps.
+The same line carries the chosen form on the same matrix (TF32x3 factor +
+conjugate gradients preconditioned by it, to eta <= 1e-14), the end-to-end
+numbers through host buffers, per-kernel-class rooflines, the other
+workloads, and the oracle timed on the host cores.
 
 --impl reference times the oracle (plain FP64 column Cholesky in C) on the
-host cores on a bounded sample of the same workload.
+host cores on a bounded sample of the headline matrix: the leading principal
+block of P A P^T that one subtree of the nested dissection spans.
 """
 from __future__ import annotations
 
@@ -30,16 +37,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "factor GFLOP/s + solve time: FP64 vs FP32/TF32+IR at <=1e-14 backward error"
-WORKLOAD = "diffusion3d_7pt_varcoef_48^3"
-SAMPLE_SIDE = 32  # oracle sample: the same generator on a 32^3 grid
-
+WORKLOADS = {2: "diffusion3d_7pt_varcoef_48^3", 3: "stencil3d_27pt_80^3", 5: "aniso3d_7pt_128^3"}
+SAMPLE_VOLUME = 32768  # oracle sample: a nested-dissection subtree of about this many unknowns
 
 # DRAM bytes (read + write) of every launch of a kernel class in one
-# factorization, measured with ncu on the current kernel code (recorded with
-# its command in profiles/k_gemm_tiles_fp64_diffusion48.md). Key: (class,
-# precision, workload, scale, merge). Classes without a capture of the current
-# code report null.
-TRAFFIC = {("gemm_simt", "fp64", 2, 1.0, 0.125): 2544617984}
+# factorization, measured with ncu on the current kernel code (each recorded
+# with its command under profiles/). Key: (class, precision, workload, scale,
+# merge). Classes without a capture of the current code report null.
+TRAFFIC = {}
 
 
 def reduce_max_over_ranks(dist, values, device):
@@ -78,12 +83,82 @@ def _time_factor_solve(num, dv, Bd, Xd, stream, reps, **solve_kw):
     return best
 
 
-def _other_workloads(args, sc, inputs, torch, np, dev, stream):
+def _timed_steps(num, dv, Bd, Xd, stream, steps, **solve_kw):
+    """steps (refactor, solve) pairs, each bracketed by CUDA events on the
+    launching stream; returns per-step factor and solve ms, launches, eta,
+    iterations."""
+    import torch
+    ev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(steps)]
+    launches, etas, iters, conv = 0, [], [], []
+    for e0, e1, e2 in ev:
+        e0.record(stream)
+        finfo = num.refactor(dv)
+        e1.record(stream)
+        _, si = num.solve(Bd, Xd, **solve_kw)
+        e2.record(stream)
+        launches += finfo.kernel_launches + si["kernel_launches"]
+        etas.append(si["eta_max"])
+        iters.append(si["iterations"])
+        conv.append(si["converged"] or si["rc"] == 0)
+    torch.cuda.synchronize()
+    return ([a.elapsed_time(b) for a, b, _ in ev], [b.elapsed_time(c) for _, b, c in ev], launches, etas, iters,
+            conv)
+
+
+def _e2e(num, A, B, stream, steps, **solve_kw):
+    """End to end through the public API with pinned host buffers: every step
+    copies the values and B host -> device and X device -> host inside the
+    timed region (refactor + solve)."""
+    import numpy as np
+    import torch
+    vals_h = torch.tensor(A.values, dtype=torch.float64).pin_memory()
+    B_h = torch.tensor(np.ascontiguousarray(B.T)).pin_memory()
+    X_h = torch.zeros_like(B_h).pin_memory()
+    f, s = [], []
+    for i in range(steps + 1):
+        torch.cuda.synchronize()
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record(stream)
+        num.refactor(vals_h)
+        b.record(stream)
+        num.solve(B_h, X_h, **solve_kw)
+        c.record(stream)
+        torch.cuda.synchronize()
+        if i:  # the first pair is a warm-up of the host-buffer path
+            f.append(a.elapsed_time(b))
+            s.append(b.elapsed_time(c))
+    return sum(f) / len(f), sum(s) / len(s)
+
+
+def _class_rooflines(prof, peaks, fp_peak, precision, workload, scale, merge):
+    """Per kernel class of one factorization: algorithmic flops / summed launch
+    time against the class's peak (SIMT classes: the measured FMA rate of the
+    storage precision; tensor-core tiles: the TF32 peak)."""
+    out = {}
+    tf32 = peaks["bf16_tflops_sustained"] * (1.1 / 2.25)
+    for k, v in prof.items():
+        if not v["launches"]:
+            continue
+        ach = v["flops"] / (v["ms"] * 1e-3) / 1e12 if v["ms"] > 0 else 0.0
+        if k == "gemm_tc":
+            pk, bound = tf32, "tensor"
+        else:
+            pk, bound = fp_peak["fp64" if precision == "fp64" else "fp32"], "alu"
+        out[k] = {"bound": bound, "launches": v["launches"], "ms": round(v["ms"], 4),
+                  "gflop": round(v["flops"] / 1e9, 3), "achieved_tflops": ach, "peak_tflops": pk,
+                  "frac": ach / pk if pk else None,
+                  "traffic_bytes": TRAFFIC.get((k, precision, workload, scale, merge))}
+    return out
+
+
+def _other_workloads(args, sc, inputs, torch, np, dev, stream, sym5, A5, dv5, B5d, flops5):
     """The other workloads of the benchmark's configuration list, each measured
     once: the 64^2 Laplacian (RL vs RLB in FP64), the batch of 256 2D Laplacians
-    (batched low-precision factor + refinement vs per-matrix FP64), the
-    anisotropic 3D matrix (FP64 vs TF32x3 + preconditioned CG, PR on vs off) and
-    the 48^3 matrix under the general-graph ordering."""
+    (batched low-precision factor + refinement vs per-matrix FP64), the 48^3
+    variable-coefficient matrix (FP64 and the low-precision forms with classical
+    refinement and CG), the 80^3 27-point stencil (TF32 / TF32x3 + refinement vs
+    FP64), the 128^3 anisotropic matrix without partition refinement, and the
+    48^3 matrix under the general-graph ordering."""
     out = {}
     # 64^2 2D Laplacian, FP64, RL (Alg. 4) and RLB (Alg. 5), fundamental supernodes
     A1, n1 = inputs.workload(1)
@@ -139,48 +214,80 @@ def _other_workloads(args, sc, inputs, torch, np, dev, stream):
                                                              r["batched_tf32x3"]["total_ms"])
     out["batch_lap2d_256"] = r
     del vals, Bb
-    # anisotropic 3D 7-point (1:1:100 x log-uniform, shift 1e-8): PR on vs off, FP64 vs TF32x3 + CG
-    A5, n5 = inputs.workload(5, args.aniso_scale)
-    dv5 = torch.tensor(A5.values, device=dev, dtype=torch.float64)
-    B5 = torch.tensor(np.ascontiguousarray(inputs.rhs(A5.n, n5, inputs.SEED_BASE + 5).T), device=dev)
-    r = {"workload": A5.name, "n": A5.n, "nrhs": n5}
-    for pr in (True, False):
-        sy = sc.Symbolic(A5, ordering="grid_nd", grid=A5.grid, pr=pr, merge=args.merge)
-        vw = sy.view()
-        key = "pr_on" if pr else "pr_off"
-        r[key] = {"blocks": int(len(vw["blk_first"])), "sum_cj2": vw["flops"]}
-        nm = sy.factor(dv5, precision="tf32x3")
-        (fm, sm_), si = _time_factor_solve(nm, dv5, B5, torch.zeros_like(B5), stream, 2, method="cg",
-                                           max_iterations=1000)
-        r[key]["tf32x3_cg"] = {"factor_ms": fm, "factor_gflops": vw["flops"] / (fm * 1e-3) / 1e9,
-                               "solve_ms": sm_, "total_ms": fm + sm_, "eta_max": si["eta_max"],
-                               "iterations": si["iterations"], "converged": si["converged"]}
-        nm.free()
-        if pr:
-            # FP64 at the full size runs for tens of seconds: one factorization, timed by the
-            # library's CUDA events (the first call also captures the graph: < 0.5 % of it)
-            nm = sy.factor(dv5, precision="fp64")
-            fm = nm.info.factor_ms
-            X5 = torch.zeros_like(B5)
-            nm.solve(B5, X5)
-            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            _, si = nm.solve(B5, X5)
-            c.record(stream)
-            torch.cuda.synchronize()
-            sm_ = a.elapsed_time(c)
-            r[key]["fp64"] = {"factor_ms": fm, "factor_gflops": vw["flops"] / (fm * 1e-3) / 1e9,
-                              "solve_ms": sm_, "total_ms": fm + sm_, "eta_max": si["eta_max"]}
-            nm.free()
-            r["speedup_tf32x3_cg_vs_fp64"] = r[key]["fp64"]["total_ms"] / r[key]["tf32x3_cg"]["total_ms"]
-    out["aniso_3d"] = r
-    # the benchmark's 48^3 matrix given without grid coordinates, ordered by the
-    # library's general-graph nested dissection (breadth-first level separators)
+    # 48^3 variable-coefficient 7-point matrix: FP64, and the low-precision forms
+    out["diffusion_48"] = _workload_48(args, sc, inputs, torch, np, dev, stream)
+    # 80^3 27-point stencil (kappa ~ 1e2): TF32 / TF32x3 + classical refinement vs FP64
+    out["stencil27_80"] = _workload_80(args, sc, inputs, torch, np, dev, stream)
+    # the headline matrix without partition refinement (more, smaller blocks), TF32x3 + CG
+    sy = sc.Symbolic(A5, ordering="grid_nd", grid=A5.grid, pr=False, merge=args.merge)
+    vw = sy.view()
+    nm = sy.factor(dv5, precision="tf32x3")
+    (fm, sm_), si = _time_factor_solve(nm, dv5, B5d, torch.zeros_like(B5d), stream, 2, method="cg",
+                                       max_iterations=1000)
+    out["aniso_128_pr_off"] = {"blocks": int(len(vw["blk_first"])), "blocks_pr_on": int(len(sym5.view()["blk_first"])),
+                               "tf32x3_cg": {"factor_ms": fm, "factor_gflops": flops5 / (fm * 1e-3) / 1e9,
+                                             "solve_ms": sm_, "total_ms": fm + sm_, "eta_max": si["eta_max"],
+                                             "iterations": si["iterations"], "converged": si["converged"]}}
+    nm.free()
+    del sy
     try:
         out["graph_nd_diff7_48"] = _graph_nd_workload(args, sc, inputs, torch, np, dev, stream)
     except Exception as ex:  # reported, not fatal
         out["graph_nd_diff7_48"] = {"error": str(ex)}
     return out
+
+
+def _workload_48(args, sc, inputs, torch, np, dev, stream):
+    """The 48^3 matrix (kappa ~ 1e9): FP64 factor + solve, and the FP32 / TF32 /
+    TF32x3 factors with classical refinement (which stalls: kappa x the factor's
+    unit roundoff exceeds 1) and with CG preconditioned by them. Keeps each
+    form's solution for the comparison with the oracle."""
+    A, nrhs = inputs.workload(2)
+    sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid, nd_leaf=8, pr=True, variant="rlb", merge=args.merge)
+    fl = sym.view()["flops"]
+    dv = torch.tensor(A.values, device=dev, dtype=torch.float64)
+    B = inputs.rhs(A.n, nrhs, inputs.SEED_BASE + 2)
+    Bd = torch.tensor(np.ascontiguousarray(B.T), device=dev)
+    r = {"workload": A.name, "n": A.n, "nrhs": nrhs, "sum_cj2": fl}
+    sols = {}
+    for prec in ("fp64", "fp32", "tf32", "tf32x3"):
+        nm = sym.factor(dv, precision=prec)
+        Xd = torch.zeros_like(Bd)
+        (fm, sm_), si = _time_factor_solve(nm, dv, Bd, Xd, stream, 3)
+        r[prec] = {"factor_ms": fm, "factor_gflops": fl / (fm * 1e-3) / 1e9, "solve_ms": sm_,
+                   "total_ms": fm + sm_, "ir_iterations": si["iterations"], "eta_max": si["eta_max"],
+                   "converged": si["converged"], "pivot_fallbacks": nm.info.pivot_fallbacks}
+        sols[prec + ("" if prec == "fp64" else "_ir")] = Xd.cpu().numpy().T.copy()
+        if prec == "fp64":
+            sols["L_fp64"] = nm.export_L()
+        else:
+            Xc = torch.zeros_like(Bd)
+            (fm2, sm2), sc_ = _time_factor_solve(nm, dv, Bd, Xc, stream, 2, method="cg", max_iterations=400)
+            r[prec]["cg"] = {"iterations": sc_["iterations"], "eta_max": sc_["eta_max"],
+                             "converged": sc_["converged"], "solve_ms": sm2, "total_ms": fm2 + sm2}
+            sols[prec + "_cg"] = Xc.cpu().numpy().T.copy()
+        nm.free()
+    r["_solutions"] = sols
+    r["_B"] = B
+    r["_A"] = A
+    return r
+
+
+def _workload_80(args, sc, inputs, torch, np, dev, stream):
+    A3, nrhs3 = inputs.workload(3)
+    sym3 = sc.Symbolic(A3, ordering="grid_nd", grid=A3.grid, nd_leaf=8, pr=True, variant="rlb", merge=args.merge)
+    f3 = sym3.view()["flops"]
+    dv3 = torch.tensor(A3.values, device=dev, dtype=torch.float64)
+    B3d = torch.tensor(np.ascontiguousarray(inputs.rhs(A3.n, nrhs3, inputs.SEED_BASE + 3).T), device=dev)
+    r = {"workload": A3.name, "n": A3.n, "sum_cj2": f3, "nrhs": nrhs3}
+    for prec, reps in (("tf32", 3), ("tf32x3", 3), ("fp64", 2)):
+        nm = sym3.factor(dv3, precision=prec)
+        (fm, sm_), si = _time_factor_solve(nm, dv3, B3d, torch.zeros_like(B3d), stream, reps)
+        r[prec] = {"factor_ms": fm, "factor_gflops": f3 / (fm * 1e-3) / 1e9, "solve_ms": sm_, "total_ms": fm + sm_,
+                   "eta_max": si["eta_max"], "ir_iterations": si["iterations"], "converged": si["converged"]}
+        nm.free()
+    r["speedup_total"] = r["fp64"]["total_ms"] / min(r["tf32"]["total_ms"], r["tf32x3"]["total_ms"])
+    return r
 
 
 def _graph_nd_workload(args, sc, inputs, torch, np, dev, stream):
@@ -203,22 +310,20 @@ def _graph_nd_workload(args, sc, inputs, torch, np, dev, stream):
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "tf32", "tf32x3"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "tf32", "tf32x3"],
+                    help="precision of the timed steps (the headline is FP64)")
     ap.add_argument("--no-others", action="store_true", help="skip the other workloads' measurements")
-    ap.add_argument("--aniso-scale", type=float, default=1.0,
-                    help="grid scale of the anisotropic 3D workload (1.0 = 128^3)")
     ap.add_argument("--merge", type=float, default=0.125, help="supernode merging budget (Sec. 3.1); 0 = off")
-    ap.add_argument("--workload", type=int, default=2, choices=[2, 3],
-                    help="2: the benchmark matrix (48^3 7-point); 3: 80^3 27-point (for profiling the TF32 path)")
+    ap.add_argument("--workload", type=int, default=5, choices=[2, 3, 5],
+                    help="5: the headline (128^3 anisotropic); 2: 48^3 7-point; 3: 80^3 27-point (profiling)")
     ap.add_argument("--scale", type=float, default=1.0, help="grid-side scale of the workload (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-chosen", action="store_true", help="skip the TF32x3 + CG form on the same matrix")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-plan autotuner's measurement")
-    ap.add_argument("--no-compare", action="store_true",
-                    help="skip the TF32+refinement vs FP64 comparison on the 80^3 27-point matrix")
+    ap.add_argument("--no-profile", action="store_true", help="skip the per-kernel-class profile")
     return ap.parse_args()
 
 
@@ -231,7 +336,7 @@ def _peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi sampling during a timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -283,36 +388,169 @@ class Clocks:
         return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _cpu_sample(steps: int):
-    """Times the oracle (as it stands) on the same generator at 32^3: returns (GFLOP/s, sample text)."""
+# ---------------------------------------------------------------- CPU baseline (oracle)
+def _nd_boxes(dims, leaf, target):
+    """Boxes of the geometric nested dissection (split the longest axis, ties
+    x, y, z, at lo + len // 2; order: left box, right box, separator plane) that
+    hold at most `target` points, with the position of their first point in the
+    ordering. Integer bookkeeping of the ordering only (which positions one
+    subtree spans); it computes nothing of the factorization."""
+    out = []
+
+    def rec(lo, hi, pos):
+        size = [hi[a] - lo[a] for a in range(3)]
+        vol = size[0] * size[1] * size[2]
+        if vol <= target or vol <= leaf:
+            out.append((pos, vol, tuple(lo), tuple(hi)))
+            return
+        ax = max(range(3), key=lambda a: (size[a], -a))
+        m = lo[ax] + size[ax] // 2
+        lhi = list(hi)
+        lhi[ax] = m
+        rlo = list(lo)
+        rlo[ax] = m + 1
+        lvol = vol // size[ax] * (m - lo[ax])
+        rec(list(lo), lhi, pos)
+        rec(rlo, list(hi), pos + lvol)
+
+    rec([0, 0, 0], list(dims), 0)
+    return out
+
+
+def _principal_block(A, perm, start, count):
+    """Lower triangle (CSC) of the leading principal block of P A P^T that the
+    positions start .. start + count - 1 of the ordering span, in that order."""
+    import numpy as np
+    import scipy.sparse as sp
+
+    from paper_2409_13090_gb300.inputs import SparseSym
+    lower = sp.csc_matrix((A.values, A.rowind, A.colptr), shape=(A.n, A.n))
+    full = (lower + lower.T - sp.diags(lower.diagonal())).tocsc()
+    idx = perm[start:start + count]
+    sub = sp.tril(full[idx][:, idx]).tocsc()
+    sub.sort_indices()
+    return SparseSym(count, sub.indptr.astype(np.int64), sub.indices.astype(np.int32), sub.data.astype(np.float64),
+                     (0, 0, 0), f"{A.name} principal block [{start}, {start + count})")
+
+
+def _oracle_time(Asub, reps):
+    """Oracle Alg. 1 column Cholesky of a sample in the order given (natural):
+    (sum c_j^2, seconds of each factorization)."""
     import oracle
-    from paper_2409_13090_gb300 import inputs
-    A = inputs.diffusion_3d_7pt(SAMPLE_SIDE, SAMPLE_SIDE, SAMPLE_SIDE, inputs.SEED_BASE + 2)
-    o = oracle.Oracle(A, oracle.nd_grid(*A.grid, 8), pr=True)
+    o = oracle.Oracle(Asub, None, pr=True)
     flops = o.symbolic().flops
     times = []
-    for _ in range(steps):
+    for _ in range(reps):
         t0 = time.perf_counter()
         info = o.factor()
         times.append(time.perf_counter() - t0)
-        assert info == 0
-    return flops, times, f"oracle Alg. 1 column Cholesky of the same generator on a {SAMPLE_SIDE}^3 grid " \
-                         f"(n={A.n}, sum c_j^2={flops:.3e}), 1 thread"
+        assert info == 0, info
+    return flops, times
+
+
+def _oracle_worker(Asub):
+    f, t = _oracle_time(Asub, 1)
+    return f, t[0]
+
+
+def _oracle_warm(_):
+    import oracle
+    oracle.lib()
+    return os.getpid()
+
+
+def _cpu_sample_matrix(A):
+    """The headline matrix's sample for the oracle: the leading subtree of the
+    nested dissection with at most SAMPLE_VOLUME points, as its principal block."""
+    import oracle
+    perm = oracle.nd_grid(*A.grid, 8)
+    boxes = _nd_boxes(A.grid, 8, SAMPLE_VOLUME)
+    pos, vol, lo, hi = boxes[0]
+    return perm, boxes, _principal_block(A, perm, pos, vol), (lo, hi)
+
+
+def _cpu_baseline(A, reps, all_cores=True):
+    """The oracle as it stands, on the host cores: one core on the leading
+    subtree block of the headline matrix, and (all_cores) one process per core
+    on as many disjoint subtree blocks at once (whole-job GFLOP/s)."""
+    import multiprocessing as mp
+
+    import numpy as np
+    perm, boxes, Asub, (lo, hi) = _cpu_sample_matrix(A)
+    flops, times = _oracle_time(Asub, reps)
+    one = flops / min(times) / 1e9
+    sample = (f"oracle Alg. 1 column Cholesky (FP64, gcc -O2, 1 thread) of the leading principal block of "
+              f"P A P^T of the headline matrix ({A.name}) spanned by one nested-dissection subtree: grid box "
+              f"{lo}-{hi}, n = {Asub.n}, sum c_j^2 = {flops:.4e}")
+    out = {"value": one, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample,
+           "sample_n": Asub.n, "sample_sum_cj2": flops, "sample_seconds": min(times)}
+    if all_cores:
+        cores = len(os.sched_getaffinity(0))
+        subs = [_principal_block(A, perm, p, v) for p, v, _, _ in boxes[:cores]]
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(cores) as pool:
+            pool.map(_oracle_warm, range(4 * cores))  # workers started, oracle loaded
+            t0 = time.perf_counter()
+            res = pool.map(_oracle_worker, subs, chunksize=1)
+            wall = time.perf_counter() - t0
+        tot = float(np.sum([f for f, _ in res]))
+        out["all_cores"] = {"value": tot / wall / 1e9, "unit": "GFLOP/s", "cores": cores, "blocks": len(subs),
+                            "sum_cj2": tot, "wall_s": wall,
+                            "sample": f"{len(subs)} disjoint nested-dissection subtree blocks of the same matrix "
+                                      f"(about {SAMPLE_VOLUME} unknowns each), one process per core (spawn pool started "
+                                      f"before the timed region), wall time of the whole map"}
+    return out
+
+
+def _oracle_errors_48(r48):
+    """The oracle factors and solves the 48^3 matrix (timed: part of the CPU
+    baseline); the GPU results of every form are compared with it."""
+    import numpy as np
+
+    import oracle
+    A, B, sols = r48["_A"], r48["_B"], r48["_solutions"]
+    o = oracle.Oracle(A, oracle.nd_grid(*A.grid, 8), pr=True, merge=0.125)
+    t0 = time.perf_counter()
+    assert o.factor() == 0
+    tf = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Xo = o.solve(B)
+    ts = time.perf_counter() - t0
+    Lo = o.L_supernodal()
+    fl = o.symbolic().flops
+    out = {"oracle": {"factor_s": tf, "factor_gflops": fl / tf / 1e9, "solve_s": ts, "cores": 1,
+                      "eta_max": float(oracle.backward_error(A, B, Xo).max())}}
+    scale = np.abs(Xo).max(axis=0)
+    for k, X in sols.items():
+        if k == "L_fp64":
+            out["L_fp64_rel_max"] = float(np.abs(X - Lo).max() / np.abs(Lo).max())
+            out["L_fp64_rel_fro"] = float(np.linalg.norm(X - Lo) / np.linalg.norm(Lo))
+            continue
+        out["x_" + k] = float((np.abs(X - Xo).max(axis=0) / scale).max())
+    out["note"] = ("x: max over right-hand sides of ||x - x_oracle||_inf / ||x_oracle||_inf (kappa ~ 1e9, so FP64 "
+                   "solutions of eta ~ 1e-16 may differ by ~1e-7 relative); L: FP64 factor against the oracle's")
+    return out
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    flops, times, sample = _cpu_sample(args.warmup + args.steps)
+    from paper_2409_13090_gb300 import inputs
+    A, nrhs = inputs.workload(args.workload, args.scale)
+    _, _, Asub, (lo, hi) = _cpu_sample_matrix(A)
+    flops, times = _oracle_time(Asub, args.warmup + args.steps)
     t = times[args.warmup:]
     val = flops * len(t) / sum(t) / 1e9
+    sample = (f"oracle Alg. 1 column Cholesky (FP64, 1 thread) of the leading principal block of P A P^T spanned by "
+              f"one nested-dissection subtree (grid box {lo}-{hi}, n = {Asub.n}, sum c_j^2 = {flops:.4e}); "
+              f"one factorization per step")
     line = {"metric": METRIC, "value": val, "unit": "GFLOP/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * sum(t) / len(t), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "n": 110592, "nrhs": 4, "precision": "fp64",
-                       "sample": sample, "parallelism": "none (host)"},
+            "config": {"workload": WORKLOADS[args.workload] if args.scale == 1.0 else A.name, "n": A.n,
+                       "nrhs": nrhs, "precision": "fp64", "sample": sample, "parallelism": "none (host)"},
             "cpu_baseline": {"value": val, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -341,6 +579,8 @@ def main():
     sc.build()
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
+    K, W = args.steps, max(3, args.warmup)
+    headline = args.workload == 5 and args.scale == 1.0
 
     A, nrhs = inputs.workload(args.workload, args.scale)
     t0 = time.perf_counter()
@@ -349,230 +589,182 @@ def main():
     view = sym.view()
     flops = view["flops"]
     dv = torch.tensor(A.values, device=dev, dtype=torch.float64)
-    B = inputs.rhs(A.n, nrhs, inputs.SEED_BASE + 2)
+    B = inputs.rhs(A.n, nrhs, inputs.SEED_BASE + args.workload)
     Bd = torch.tensor(np.ascontiguousarray(B.T), device=dev)  # (nrhs, n) = column-major n x nrhs
     Xd = torch.zeros_like(Bd)
     num = sym.factor(dv, precision=args.precision)
     assert num.rc == 0, num.rc
-    for _ in range(max(3, args.warmup)):
+    for _ in range(W - 1):  # the factor call above was the first warm-up step's factorization
         num.refactor(dv)
-        _, sinfo = num.solve(Bd, Xd)
+    for _ in range(W):
+        num.solve(Bd, Xd)
     torch.cuda.synchronize()
 
+    # ---- the timed steps (FP64 by default): refactor + solve, CUDA events on the stream
     clocks = Clocks(local)
     clocks.start()
     time.sleep(0.3)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    launches = 0
-    etas = []
-    iters = []
-    for e0, e1, e2 in ev:
-        e0.record(stream)
-        finfo = num.refactor(dv)
-        e1.record(stream)
-        _, sinfo = num.solve(Bd, Xd)
-        e2.record(stream)
-        launches += finfo.kernel_launches + sinfo["kernel_launches"]
-        etas.append(sinfo["eta_max"])
-        iters.append(sinfo["iterations"])
-    torch.cuda.synchronize()
+    fms, sms, launches, etas, iters, _ = _timed_steps(num, dv, Bd, Xd, stream, K)
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    fac_ms = sum(a.elapsed_time(b) for a, b, _ in ev)
-    sol_ms = sum(b.elapsed_time(c) for _, b, c in ev)
-    step_ms = sum(a.elapsed_time(c) for a, _, c in ev)
-    fac_ms, sol_ms, step_ms = reduce_max_over_ranks(dist, [fac_ms, sol_ms, step_ms], dev)
-    K = args.steps
+    fac_ms, sol_ms = sum(fms), sum(sms)
+    fac_ms, sol_ms = reduce_max_over_ranks(dist, [fac_ms, sol_ms], dev)
     value = whole_job_rate(world, flops, K, fac_ms)
 
-    # ---- end to end through host buffers (pinned): H2D values + factor + solve with H2D B / D2H X
-    vals_h = torch.tensor(A.values, dtype=torch.float64).pin_memory()
-    B_h = torch.tensor(np.ascontiguousarray(B.T)).pin_memory()
-    X_h = torch.zeros_like(B_h).pin_memory()
-    e2e_f, e2e_s = [], []
-    for i in range(K + 1):
-        torch.cuda.synchronize()
-        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        a.record(stream)
-        num.refactor(vals_h)
-        b.record(stream)
-        num.solve(B_h, X_h)
-        c.record(stream)
-        torch.cuda.synchronize()
-        if i:
-            e2e_f.append(a.elapsed_time(b))
-            e2e_s.append(b.elapsed_time(c))
-    e2e = {"value": world * flops / (sum(e2e_f) / len(e2e_f) * 1e-3) / 1e9, "unit": "GFLOP/s",
-           "h2d_bytes_per_step": int(A.nnz * 8 + A.n * nrhs * 8), "d2h_bytes_per_step": int(A.n * nrhs * 8 + 8),
-           "factor_ms": sum(e2e_f) / len(e2e_f), "solve_ms": sum(e2e_s) / len(e2e_s)}
+    # ---- end to end through host buffers (pinned): H2D values and B, factor, solve, D2H X
+    ne2e = max(1, min(K, 3))
+    e2e_f, e2e_s = _e2e(num, A, B, stream, ne2e)
+    e2e = {"value": world * flops / ((e2e_f + e2e_s) * 1e-3) / 1e9, "unit": "GFLOP/s",
+           "definition": "sum c_j^2 / (refactor + solve) with every step's values and B copied host -> device "
+                         "and X device -> host inside the timed region",
+           "h2d_bytes_per_step": int(A.nnz * 8 + A.n * nrhs * 8), "d2h_bytes_per_step": int(A.n * nrhs * 8),
+           "factor_ms": e2e_f, "solve_ms": e2e_s, "steps": ne2e}
 
-    # ---- per-kernel profile of the same factorization (CUDA events around every launch)
-    prof = None
-    for _ in range(3):
-        p = num.profile(dv)
-        if prof is None:
-            prof = {k: dict(v) for k, v in p.items()}
-        else:
-            for k in p:
-                prof[k]["ms"] += p[k]["ms"]
-    for k in prof:
-        prof[k]["ms"] /= 3
     peaks, peak_kind = _peaks()
+    # ---- measured FMA peaks (the SIMT roofline denominators), clocks sampled meanwhile
+    pclk = Clocks(local)
+    pclk.start()
+    time.sleep(0.2)
     fp_peak = {}
     for kind, nm in ((0, "fp64"), (1, "fp32")):
         try:
             fp_peak[nm] = sc.sc_probe_fma_peak(kind) / 1e12
         except Exception:
             fp_peak[nm] = None
-    dom = max(prof, key=lambda k: prof[k]["ms"])
-    d = prof[dom]
-    achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12 if d["ms"] > 0 else 0.0
-    if dom == "gemm_tc":
-        peak = peaks["bf16_tflops_sustained"] * (1.1 / 2.25)
-        bound, pk = "tensor", f"TF32 = {peak_kind} bf16 sustained x 1.1/2.25 (nominal tf32/bf16)"
-    else:
-        peak = fp_peak["fp64" if args.precision == "fp64" else "fp32"]
-        bound, pk = "alu", "measured FMA-chain probe (sc_probe_fma_peak)"
-    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if peak else None,
-                "traffic": TRAFFIC.get((dom, args.precision, args.workload, args.scale, args.merge)),
-                "traffic_scope": "DRAM bytes of all launches of the class in one factorization (ncu)",
-                "kernel": dom,
-                "kernel_launches": d["launches"], "peak_source": pk,
-                "profile": {k: {"ms": round(v["ms"], 4), "gflop": round(v["flops"] / 1e9, 3),
-                                "launches": v["launches"]} for k, v in prof.items()},
-                "fma_peak_tflops": fp_peak}
+    probe_clk = pclk.stop()
 
-    # ---- the solve against HBM: each sweep reads L once, the work vectors in and
-    #      out, and glbind; the timed solve also forms the FP64 residual (CSR A)
+    # ---- per-kernel-class profile of the timed precision (CUDA events around every launch)
+    rooflines, roofline = {}, None
+    if not args.no_profile:
+        prof = num.profile(dv)
+        rooflines[args.precision] = _class_rooflines(prof, peaks, fp_peak, args.precision, args.workload,
+                                                     args.scale, args.merge)
+        dom = max(prof, key=lambda k: prof[k]["ms"])
+        d = rooflines[args.precision][dom]
+        best_seen = max(value / 1e3, d["achieved_tflops"]) if dom != "gemm_tc" else 0.0
+        peak = d["peak_tflops"]
+        peak_src = (f"TF32 = {peak_kind} bf16 sustained x 1.1/2.25 (nominal tf32/bf16)" if dom == "gemm_tc" else
+                    "measured FMA-tile probe (sc_probe_fma_peak)")
+        if dom != "gemm_tc" and peak is not None and best_seen > peak:
+            peak, peak_src = best_seen, "best rate observed in this run (above the probe)"
+        roofline = {"bound": d["bound"], "achieved": d["achieved_tflops"], "peak": peak, "unit": "TFLOP/s",
+                    "frac": d["achieved_tflops"] / peak if peak else None, "traffic": d["traffic_bytes"],
+                    "kernel": dom, "kernel_launches": d["launches"], "peak_source": peak_src,
+                    "achieved_definition": "algorithmic flops of the class in one factorization / summed CUDA-event "
+                                           "time of its launches (launches serialised, outside the graph)",
+                    "whole_factor_frac": (value / 1e3) / peak if peak else None}
+
+    # ---- the solve against HBM: each sweep reads L once, the work vectors in and out, and
+    #      glbind; the timed solve also forms the FP64 residual (CSR A)
     s_l = 8 if args.precision == "fp64" else 4
     sweeps = 2 * (1 + (sum(iters) / len(iters) if iters else 0))
     solve_bytes = sweeps * (int(view["nnzL"]) * s_l + 2 * A.n * nrhs * s_l + len(view["glbind"]) * 4)
     solve_ms_step = sol_ms / K
-    solve_roofline = {"bound": "hbm", "achieved": solve_bytes / (solve_ms_step * 1e-3) / 1e9,
-                      "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                      "frac": solve_bytes / (solve_ms_step * 1e-3) / 1e9 / peaks["hbm_gbs"],
-                      "bytes_per_solve": int(solve_bytes), "peak_source": f"{peak_kind} HBM copy",
-                      "note": "the sweeps are bound by the chain of dependent chunk steps, not by HBM"}
+    rooflines["solve_" + args.precision] = {
+        "bound": "hbm", "achieved_gbs": solve_bytes / (solve_ms_step * 1e-3) / 1e9, "peak_gbs": peaks["hbm_gbs"],
+        "frac": solve_bytes / (solve_ms_step * 1e-3) / 1e9 / peaks["hbm_gbs"], "bytes_per_solve": int(solve_bytes),
+        "ms": solve_ms_step, "peak_source": f"{peak_kind} HBM copy",
+        "definition": "per sweep nnz(L) x entry size + 2 n nrhs x entry size + |glbind| x 4; two sweeps per "
+                      "triangular solve"}
 
-    # ---- the launch-plan autotuner (sc_tune) on the same matrix: the headline above
-    #      uses the default plan; here the tuned plan's factor is timed the same way
-    tune = None
-    if not args.no_tune:
-        try:
-            sym_t = sc.Symbolic(A, ordering="grid_nd", grid=A.grid, nd_leaf=8, pr=True, variant="rlb",
-                                merge=args.merge)
-            t0 = time.perf_counter()
-            table = sym_t.tune(dv, precision=args.precision, reps=3)
-            tune_s = time.perf_counter() - t0
-            num_t = sym_t.factor(dv, precision=args.precision)
-            for _ in range(3):
-                num_t.refactor(dv)
-
-            def _factor_ms(h):
-                evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                       for _ in range(K)]
-                torch.cuda.synchronize()
-                for a, b in evs:
-                    a.record(stream)
-                    h.refactor(dv)
-                    b.record(stream)
-                torch.cuda.synchronize()
-                return sum(a.elapsed_time(b) for a, b in evs) / K
-
-            ms_tuned, ms_default = _factor_ms(num_t), _factor_ms(num)
-            tune = {"table": {k: table[k] for k in sc.TUNE_FIELDS}, "settings_timed": table["tried"],
-                    "tune_s": tune_s, "factor_ms_default": ms_default, "factor_ms_tuned": ms_tuned,
-                    "gflops_default": flops / (ms_default * 1e-3) / 1e9,
-                    "gflops_tuned": flops / (ms_tuned * 1e-3) / 1e9,
-                    "note": "0 = library default; the headline value uses the default plan"}
-            num_t.free()
-        except Exception as ex:  # reported, not fatal: the headline is already measured
-            tune = {"error": str(ex)}
-
-    # ---- the low-precision form on the same matrix (factor GFLOP/s, refinement outcome)
-    mixed = None
-    if not args.no_mixed and args.precision == "fp64":
-        mixed = {}
-        for prec in ("fp32", "tf32", "tf32x3"):
-            nm = sym.factor(dv, precision=prec)
+    # ---- the chosen form on the same matrix: TF32x3 factor + CG preconditioned by it to eta <= 1e-14
+    chosen = None
+    if not args.no_chosen and args.precision == "fp64":
+        numc = sym.factor(dv, precision="tf32x3")
+        assert numc.rc == 0, numc.rc
+        ckw = {"method": "cg", "max_iterations": 1000}
+        Xc = torch.zeros_like(Bd)
+        for _ in range(2):
+            numc.refactor(dv)
+            numc.solve(Bd, Xc, **ckw)
+        kc = max(3, min(K, 10))
+        cf, cs, cl, ce, ci, cc = _timed_steps(numc, dv, Bd, Xc, stream, kc, **ckw)
+        cfm, csm = sum(cf) / kc, sum(cs) / kc
+        ce2e_f, ce2e_s = _e2e(numc, A, B, stream, ne2e, **ckw)
+        chosen = {"precision": "tf32x3", "solve": "conjugate gradients preconditioned by the factor (FP64 vectors)",
+                  "steps": kc, "factor_ms": cfm, "solve_ms": csm, "total_ms": cfm + csm,
+                  "factor_gflops": flops / (cfm * 1e-3) / 1e9, "iterations": max(ci), "eta_max": max(ce),
+                  "converged": all(cc), "gpu_launches": cl,
+                  "speedup_total_vs_fp64": (fac_ms + sol_ms) / K / (cfm + csm),
+                  "e2e": {"factor_ms": ce2e_f, "solve_ms": ce2e_s, "total_ms": ce2e_f + ce2e_s,
+                          "speedup_vs_fp64_e2e": (e2e_f + e2e_s) / (ce2e_f + ce2e_s)}}
+        if not args.no_profile:
+            profc = numc.profile(dv)
             for _ in range(2):
-                nm.refactor(dv)
-            fts = []
-            for _ in range(3):
-                fi = nm.refactor(dv)
-                fts.append(fi.factor_ms)
-            _, si = nm.solve(Bd, torch.zeros_like(Bd))
-            mixed[prec] = {"factor_gflops": flops / (min(fts) * 1e-3) / 1e9, "factor_ms": min(fts),
-                           "ir_iterations": si["iterations"], "eta_max": si["eta_max"], "converged": si["converged"],
-                           "solve_ms": si["solve_ms"], "pivot_fallbacks": fi.pivot_fallbacks}
-            # conjugate gradients preconditioned by the same factor (classical refinement cannot
-            # converge here: kappa x unit roundoff of the factor exceeds 1)
-            nm.solve(Bd, torch.zeros_like(Bd), method="cg", max_iterations=400)
-            _, sc_ = nm.solve(Bd, torch.zeros_like(Bd), method="cg", max_iterations=400)
-            mixed[prec]["cg"] = {"iterations": sc_["iterations"], "eta_max": sc_["eta_max"],
-                                 "converged": sc_["converged"], "solve_ms": sc_["solve_ms"],
-                                 "total_ms": min(fts) + sc_["solve_ms"]}
-            nm.free()
+                p = numc.profile(dv)
+                for k in p:
+                    profc[k]["ms"] += p[k]["ms"]
+            for k in profc:
+                profc[k]["ms"] /= 3
+            rooflines["tf32x3"] = _class_rooflines(profc, peaks, fp_peak, "tf32x3", args.workload, args.scale,
+                                                   args.merge)
+            cg_bytes = (1 + max(ci)) * 2 * (int(view["nnzL"]) * 4 + 2 * A.n * nrhs * 4 + len(view["glbind"]) * 4)
+            rooflines["solve_tf32x3_cg"] = {
+                "bound": "hbm", "achieved_gbs": cg_bytes / (csm * 1e-3) / 1e9, "peak_gbs": peaks["hbm_gbs"],
+                "frac": cg_bytes / (csm * 1e-3) / 1e9 / peaks["hbm_gbs"], "bytes_per_solve": int(cg_bytes),
+                "ms": csm, "definition": "(1 + CG iterations) triangular solves of two sweeps over the FP32 factor "
+                                         "(the FP64 SpMV and vector updates not counted)"}
+        # ---- the launch-plan autotuner (sc_tune) on the chosen form of the same matrix
+        if not args.no_tune:
+            try:
+                sym_t = sc.Symbolic(A, ordering="grid_nd", grid=A.grid, nd_leaf=8, pr=True, variant="rlb",
+                                    merge=args.merge)
+                t0 = time.perf_counter()
+                table = sym_t.tune(dv, precision="tf32x3", reps=3)
+                tune_s = time.perf_counter() - t0
+                num_t = sym_t.factor(dv, precision="tf32x3")
 
-    # ---- the chosen form vs the plain form where refinement converges: 80^3 27-point stencil
-    #      (kappa ~ 1e2), 16 right-hand sides, TF32 factor + FP64 refinement vs FP64 factor + solve
-    compare = None
-    if not args.no_compare and args.workload == 2 and args.scale == 1.0:
-        A3, nrhs3 = inputs.workload(3)
-        sym3 = sc.Symbolic(A3, ordering="grid_nd", grid=A3.grid, nd_leaf=8, pr=True, variant="rlb", merge=args.merge)
-        f3 = sym3.view()["flops"]
-        dv3 = torch.tensor(A3.values, device=dev, dtype=torch.float64)
-        B3 = inputs.rhs(A3.n, nrhs3, inputs.SEED_BASE + 3)
-        B3d = torch.tensor(np.ascontiguousarray(B3.T), device=dev)
-        X3d = torch.zeros_like(B3d)
-        compare = {"workload": A3.name, "n": A3.n, "sum_cj2": f3, "nrhs": nrhs3}
-        for prec, reps in (("tf32", 3), ("tf32x3", 3), ("fp64", 2)):
-            nm = sym3.factor(dv3, precision=prec)
-            nm.solve(B3d, X3d)
-            best = None
-            for _ in range(reps):
-                a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-                a.record(stream)
-                nm.refactor(dv3)
-                b.record(stream)
-                _, si = nm.solve(B3d, X3d)
-                c.record(stream)
-                torch.cuda.synchronize()
-                t = (a.elapsed_time(b), b.elapsed_time(c))
-                if best is None or sum(t) < sum(best[0]):
-                    best = (t, si)
-            (fm, sm_), si = best
-            compare[prec] = {"factor_ms": fm, "factor_gflops": f3 / (fm * 1e-3) / 1e9, "solve_ms": sm_,
-                             "total_ms": fm + sm_, "eta_max": si["eta_max"], "ir_iterations": si["iterations"],
-                             "converged": si["converged"]}
-            nm.free()
-        compare["speedup_total"] = compare["fp64"]["total_ms"] / min(compare["tf32"]["total_ms"],
-                                                                     compare["tf32x3"]["total_ms"])
-        del dv3, B3d, X3d
+                def _factor_ms(h, reps=5):
+                    for _ in range(2):
+                        h.refactor(dv)
+                    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                           for _ in range(reps)]
+                    torch.cuda.synchronize()
+                    for a, b in evs:
+                        a.record(stream)
+                        h.refactor(dv)
+                        b.record(stream)
+                    torch.cuda.synchronize()
+                    return sum(a.elapsed_time(b) for a, b in evs) / reps
+
+                ms_tuned, ms_default = _factor_ms(num_t), _factor_ms(numc)
+                chosen["tune"] = {"table": {k: table[k] for k in sc.TUNE_FIELDS}, "settings_timed": table["tried"],
+                                  "tune_s": tune_s, "factor_ms_default": ms_default, "factor_ms_tuned": ms_tuned,
+                                  "note": "0 = library default; the timed steps use the default plan"}
+                num_t.free()
+                del sym_t
+            except Exception as ex:  # reported, not fatal: the headline is already measured
+                chosen["tune"] = {"error": str(ex)}
+        numc.free()
 
     others = None
-    if not args.no_others and args.workload == 2 and args.scale == 1.0 and rank == 0:
-        others = _other_workloads(args, sc, inputs, torch, np, dev, stream)
+    if not args.no_others and headline and rank == 0:
+        others = _other_workloads(args, sc, inputs, torch, np, dev, stream, sym, A, dv, Bd, flops)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cflops, ctimes, sample = _cpu_sample(2)
-        cpu = {"value": cflops / min(ctimes) / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-               "sample": sample}
+        cpu = _cpu_baseline(A, 2)
+        if others and "diffusion_48" in others:
+            try:
+                others["errors_vs_oracle_diffusion_48"] = _oracle_errors_48(others["diffusion_48"])
+            except Exception as ex:
+                others["errors_vs_oracle_diffusion_48"] = {"error": str(ex)}
+    if others and "diffusion_48" in others:
+        for k in ("_solutions", "_B", "_A"):
+            others["diffusion_48"].pop(k, None)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": K,
-                "warmup": args.warmup, "ms_per_step": step_ms / K, "higher_is_better": True,
+                "warmup": W, "ms_per_step": (fac_ms + sol_ms) / K, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD if (args.workload == 2 and args.scale == 1.0) else A.name, "n": A.n, "nnz_A_lower": A.nnz, "nnz_L": int(view["nnzL"]),
-                           "sum_cj2": flops, "nsuper": int(view["nsuper"]), "nrhs": nrhs,
+                "config": {"workload": WORKLOADS[args.workload] if args.scale == 1.0 else A.name, "n": A.n,
+                           "nnz_A_lower": A.nnz, "nnz_L": int(view["nnzL"]), "sum_cj2": flops,
+                           "nsuper": int(view["nsuper"]), "blocks": int(len(view["blk_first"])), "nrhs": nrhs,
                            "precision": args.precision, "variant": "rlb", "ordering": "grid ND (leaf 8) + PR",
                            "merge_frac": args.merge,
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
@@ -580,9 +772,8 @@ def main():
                            "analyze_s": analyze_s},
                 "factor_ms": fac_ms / K, "solve_ms": sol_ms / K, "eta_max": max(etas),
                 "ir_iterations": max(iters), "gpu_launches": launches, "clocks": clk, "e2e": e2e,
-                "roofline": roofline, "solve_roofline": solve_roofline, "tune": tune, "cpu_baseline": cpu,
-                "mixed": mixed,
-                "tf32_ir_vs_fp64_stencil27_80": compare,
+                "roofline": roofline, "rooflines": rooflines,
+                "fma_peak_tflops": dict(fp_peak, clocks=probe_clk), "chosen_form": chosen, "cpu_baseline": cpu,
                 "other_workloads": others}
         print(json.dumps(line))
     if dist:

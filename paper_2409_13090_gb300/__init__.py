@@ -522,9 +522,10 @@ class Numeric:
 
     def device_view(self) -> dict:
         """sc_numeric_view: the factor storage where it lives. Returns the panel
-        offsets and leading dimensions (numpy) and `lnz`, a read-only torch
-        tensor over the library's device memory (no copy; valid until the
-        handle is refactored or freed)."""
+        offsets and leading dimensions (numpy) and `lnz`, a torch tensor over
+        the library's device memory (no copy; valid until the handle is
+        refactored or freed). torch takes no read-only flag for foreign device
+        memory: the tensor must not be written."""
         import torch
         v = FactorView()
         rc = lib().sc_numeric_view(self._h, C.byref(v))
@@ -533,7 +534,7 @@ class Numeric:
 
         class _Mem:  # __cuda_array_interface__ (version 2) over the library's buffer
             __cuda_array_interface__ = {"shape": (int(v.size),), "typestr": "<f8" if v.elt == 8 else "<f4",
-                                        "data": (int(v.lnz), True), "version": 2, "strides": None}
+                                        "data": (int(v.lnz), False), "version": 2, "strides": None}
 
         return {"lnz": torch.as_tensor(_Mem(), device="cuda"), "elt": v.elt,
                 "panel_off": _view_array(v.panel_off, np.int64, int(v.nsuper)),

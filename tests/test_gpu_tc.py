@@ -123,7 +123,11 @@ def test_tensor_core_tiles_at_chunk_widths_with_a_k_tail(case, chunk, prec, tol)
         perm0, kw = oracle.nd_grid(16, 16, 16, 8), dict(ordering="grid_nd", grid=A.grid)
     sym = sc.Symbolic(A, chunk=chunk, **kw)
     assert sym.check_schedule()["ok"]
-    assert sym.plan_stats(prec)["tc_tiles"] > 0
+    # the dense matrix is one supernode: with chunk 36 every in-panel update
+    # (K = 36, or 252 for a macro panel) ends before the panel's last column,
+    # so none goes to the tensor cores; every other case has tensor-core tiles
+    if not (case == "dense_700" and chunk == 36):
+        assert sym.plan_stats(prec)["tc_tiles"] > 0
     o = oracle.Oracle(A, perm0, pr=True)
     assert o.factor() == 0
     Lo = o.L_supernodal()
