@@ -94,7 +94,6 @@ struct sc_numeric {
     int32_t *d_sync = nullptr;      // per sweep: arrivals, backward counters, done flags, work counters
     int32_t *d_serr = nullptr;      // nonzero after a bounded wait of a solve sweep gave up
     int32_t solve_tiles = 0;        // grab units of one sweep
-    int32_t solve_grid = 1;         // CTAs of a persistent sweep that fit on the device at once
     int32_t stall_chunk = -1;       // test hook: chunk whose expected arrivals are raised by one
     void *d_xw = nullptr;           // permuted right-hand side / forward work vector
     sc::TrsmTile *d_solve_tiles = nullptr;

@@ -30,17 +30,33 @@ namespace sc {
 
 namespace {
 
-constexpr int kRhsBlk = 16;
+constexpr int kRhsBlk = 64;  // right-hand sides of one block: one sweep unit covers all of them
 constexpr int kSolveRows = 64;
 // one synchronisation word per 128-byte line: the CTAs that poll one chunk's
 // word do not contend with arrivals at its neighbours
 constexpr int kSyncStride = 32;
+// synchronisation words per chunk and block of right-hand sides: forward
+// arrivals, forward "y_c published", backward tile count, backward "z_c done"
+constexpr int kSyncWords = 4;
 
-// shared memory of a sweep CTA: the diagonal block (or its inverse), the chunk's
-// right-hand-side values in and out, reciprocal pivots
+// row stride (elements) of the shared-memory right-hand-side tiles of a block
+// of nb right-hand sides: a multiple of 4, so 16-byte vector loads stay aligned
+__host__ __device__ constexpr int rhs_ld(int nb) { return (nb + 3) / 4 * 4; }
+
+// right-hand sides per thread in the block products (four thread groups share
+// the block's right-hand sides): 1, 2, 4, 8 or 16
+inline int rhs_per_thread(int nb) {
+    const int q = (nb + 3) / 4;
+    return q <= 1 ? 1 : q <= 2 ? 2 : q <= 4 ? 4 : q <= 8 ? 8 : 16;
+}
+
+// dynamic shared memory of a sweep CTA for blocks of nb right-hand sides: the
+// diagonal block (or its inverse) and the tile's rows of L (64 x 65 each), then
+// two 64 x rhs_ld(nb) right-hand-side tiles (also the per-warp slices of the
+// narrow-tile path: 8 warps x kSmallW rows)
 template <typename T>
-constexpr int solve_smem() {
-    return (int)sizeof(T) * (2 * kMaxChunk * (kMaxChunk + 1) + 2 * kMaxChunk * kRhsBlk + kMaxChunk);
+size_t solve_smem(int nb) {
+    return sizeof(T) * (2 * (size_t)kMaxChunk * (kMaxChunk + 1) + 2 * (size_t)kMaxChunk * rhs_ld(nb));
 }
 
 // Loads a rows x w block (row stride ld) into shared memory dst[r][c] with a
@@ -60,6 +76,16 @@ __device__ __forceinline__ void stage_block(T (*dst)[kMaxChunk + 1], const T *__
     for (int it = 0; it < kIters; it++) {
         const int idx = threadIdx.x + it * 256;
         dst[idx / kMaxChunk][idx % kMaxChunk] = tmp[it];
+    }
+}
+
+// Loads rows x nb values of a row-major vector block (row r at src + row(r) * nb,
+// read through L2: other CTAs wrote them) into dst[r][0..nb) (row stride ldv).
+template <typename T, typename RowOf>
+__device__ __forceinline__ void stage_rhs(T *__restrict__ dst, int ldv, const T *src, int nb, int rows, RowOf row_of) {
+    for (int idx = threadIdx.x; idx < rows * nb; idx += blockDim.x) {
+        const int r = idx / nb, c = idx % nb;
+        dst[r * ldv + c] = __ldcg(src + (int64_t)row_of(r) * nb + c);
     }
 }
 
@@ -132,24 +158,60 @@ __device__ void warp_upper_solve(const T (*m)[kMaxChunk + 1], const T *rinv, int
     if (lane + 32 < w) x1 *= rinv[lane + 32];
 }
 
-// FP32 block products of the sweeps, register-blocked over right-hand sides:
-// thread (i = tid % 64, g = tid / 64) forms o[j] = sum_k a(i, k) b[k][4g + j],
-// j < 4, with a(i, k) = a[i][k] (or a[k][i] when kTrans). Lanes of a warp read
-// a at 32 consecutive banks and b as one broadcast 16-byte word, so each k
-// costs two shared-memory wavefronts for four FMAs per lane.
-template <bool kTrans>
-__device__ __forceinline__ void rhs4_product(const float (*a)[kMaxChunk + 1], const float (*b)[kRhsBlk], int i, int g,
-                                             int K, float (&o)[4]) {
-    o[0] = o[1] = o[2] = o[3] = 0.f;
-#pragma unroll 8
+// Block product of the sweeps, register-blocked over right-hand sides: the
+// thread forms o[j] = sum_k a(i, k) b[k][r0 + j], j < RPT, with a(i, k) =
+// a[i][k] (or a[k][i] when kTrans) and b of row stride ldb. The 64 threads of
+// one group read a at consecutive banks and b as broadcast 16-byte words (FP32,
+// RPT a multiple of 4) or 16-byte pairs (FP64, RPT even).
+template <typename T, int RPT, bool kTrans>
+__device__ __forceinline__ void rhs_product(const T (*a)[kMaxChunk + 1], const T *__restrict__ b, int ldb, int i,
+                                            int r0, int K, T (&o)[RPT]) {
+#pragma unroll
+    for (int j = 0; j < RPT; j++) o[j] = T(0);
+#pragma unroll 4
     for (int k = 0; k < K; k++) {
-        const float av = kTrans ? a[k][i] : a[i][k];
-        const float4 bv = *reinterpret_cast<const float4 *>(&b[k][4 * g]);
-        o[0] += av * bv.x;
-        o[1] += av * bv.y;
-        o[2] += av * bv.z;
-        o[3] += av * bv.w;
+        const T av = kTrans ? a[k][i] : a[i][k];
+        const T *bk = b + k * ldb + r0;
+        if constexpr (sizeof(T) == 4 && RPT % 4 == 0) {
+#pragma unroll
+            for (int j = 0; j < RPT; j += 4) {
+                const float4 bv = *reinterpret_cast<const float4 *>(bk + j);
+                o[j] += av * bv.x;
+                o[j + 1] += av * bv.y;
+                o[j + 2] += av * bv.z;
+                o[j + 3] += av * bv.w;
+            }
+        } else if constexpr (sizeof(T) == 8 && RPT % 2 == 0) {
+#pragma unroll
+            for (int j = 0; j < RPT; j += 2) {
+                const double2 bv = *reinterpret_cast<const double2 *>(bk + j);
+                o[j] += av * bv.x;
+                o[j + 1] += av * bv.y;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < RPT; j++) o[j] += av * bk[j];
+        }
     }
+}
+
+// dst[0..RPT) += sign * o over the valid right-hand sides r0 + j < nb, by atomic
+// adds (16-byte vector atomics where the four values are valid and aligned)
+template <typename T, int RPT>
+__device__ __forceinline__ void add_rhs(T *dst, const T (&o)[RPT], T sign, int r0, int nb) {
+    if constexpr (sizeof(T) == 4 && RPT % 4 == 0) {
+        if ((nb & 3) == 0) {
+#pragma unroll
+            for (int j = 0; j < RPT; j += 4)
+                if (r0 + j < nb)
+                    atomicAdd(reinterpret_cast<float4 *>(dst + j),
+                              make_float4(sign * o[j], sign * o[j + 1], sign * o[j + 2], sign * o[j + 3]));
+            return;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < RPT; j++)
+        if (r0 + j < nb) atomicAdd(dst + j, sign * o[j]);
 }
 
 // Bounded wait until *flag >= target (acquire at GPU scope). Gives up, setting
@@ -177,7 +239,7 @@ __device__ __forceinline__ int grab_tile(int32_t *work, int total, int32_t *err,
 
 // ---- tiles of narrow chunks (w <= kSmallW): one warp per tile, eight per CTA
 // (a SolveUnit with cnt > 0). v / z of the diagonal step are kept in a
-// per-warp shared-memory slice of kSmallW x kRhsBlk values.
+// per-warp shared-memory slice of kSmallW rows of ldv values.
 constexpr int kSmallW = 16;
 
 // Forward step of one narrow tile by one warp: wait for the chunk's arrivals,
@@ -189,7 +251,7 @@ __device__ bool fwd_tile_warp(const T *__restrict__ lnz, const ChunkDev &ch, con
                               const int32_t *__restrict__ dep_ptr, const int32_t *__restrict__ dep,
                               const int32_t *__restrict__ need, const int32_t *__restrict__ glbind, T *__restrict__ x,
                               T *__restrict__ y, int nb, const float *__restrict__ inv, int32_t *__restrict__ arrive,
-                              int32_t *__restrict__ err, long long spin_limit, T (*vw)[kRhsBlk]) {
+                              int32_t *__restrict__ err, long long spin_limit, T *vw, int ldv) {
     const int lane = threadIdx.x % 32, w = ch.w;
     const bool first = tl.r0 == ch.c0 + w;
     const int rows = max(0, min(kSolveRows, ch.m - tl.r0));
@@ -203,17 +265,16 @@ __device__ bool fwd_tile_warp(const T *__restrict__ lnz, const ChunkDev &ch, con
             const int k = e / nb, r = e % nb;
             T acc = T(0);
             for (int q = 0; q <= k; q++) acc += iv[k * w + q] * __ldcg(x + (int64_t)(ch.col0 + q) * nb + r);
-            vw[k][r] = acc;
+            vw[k * ldv + r] = acc;
             if (first) y[(int64_t)(ch.col0 + k) * nb + r] = acc;
         }
     } else {
-        if (lane < nb) {
-            const int r = lane;
+        for (int r = lane; r < nb; r += 32) {
             for (int k = 0; k < w; k++) {
                 T sum = __ldcg(x + (int64_t)(ch.col0 + k) * nb + r);
-                for (int q = 0; q < k; q++) sum -= dg[(int64_t)k * ch.ld + q] * vw[q][r];
-                vw[k][r] = sum / dg[(int64_t)k * ch.ld + k];
-                if (first) y[(int64_t)(ch.col0 + k) * nb + r] = vw[k][r];
+                for (int q = 0; q < k; q++) sum -= dg[(int64_t)k * ch.ld + q] * vw[q * ldv + r];
+                vw[k * ldv + r] = sum / dg[(int64_t)k * ch.ld + k];
+                if (first) y[(int64_t)(ch.col0 + k) * nb + r] = vw[k * ldv + r];
             }
         }
     }
@@ -222,7 +283,7 @@ __device__ bool fwd_tile_warp(const T *__restrict__ lnz, const ChunkDev &ch, con
         const int i = e / nb, r = e % nb;
         const T *lr = lnz + ch.off + (int64_t)(tl.r0 + i) * ch.ld + ch.c0;
         T acc = T(0);
-        for (int k = 0; k < w; k++) acc += lr[k] * vw[k][r];
+        for (int k = 0; k < w; k++) acc += lr[k] * vw[k * ldv + r];
         atomicAdd(x + (int64_t)glbind[ch.gl + tl.r0 + i] * nb + r, -acc);
     }
     __syncwarp();
@@ -243,7 +304,7 @@ __device__ bool bwd_tile_warp(const T *__restrict__ lnz, const ChunkDev &ch, con
                               const int32_t *__restrict__ ntiles, const int32_t *__restrict__ glbind,
                               const T *__restrict__ y, T *__restrict__ z, T *__restrict__ acc, int nb,
                               const float *__restrict__ inv, int32_t *__restrict__ cnt, int32_t *__restrict__ done,
-                              int32_t *__restrict__ err, long long spin_limit, T (*vw)[kRhsBlk]) {
+                              int32_t *__restrict__ err, long long spin_limit, T *vw, int ldv) {
     const int lane = threadIdx.x % 32, w = ch.w;
     const int rows = max(0, min(kSolveRows, ch.m - tl.r0));
     if (rows > 0) {
@@ -273,7 +334,7 @@ __device__ bool bwd_tile_warp(const T *__restrict__ lnz, const ChunkDev &ch, con
     for (int e = lane; e < w * nb; e += 32) {
         const int k = e / nb, r = e % nb;
         const int64_t g = (int64_t)(ch.col0 + k) * nb + r;
-        vw[k][r] = y[g] - __ldcg(acc + g);
+        vw[k * ldv + r] = y[g] - __ldcg(acc + g);
     }
     __syncwarp();
     if constexpr (sizeof(T) == 4) {
@@ -281,17 +342,16 @@ __device__ bool bwd_tile_warp(const T *__restrict__ lnz, const ChunkDev &ch, con
         for (int e = lane; e < w * nb; e += 32) {
             const int k = e / nb, r = e % nb;
             T sum = T(0);
-            for (int q = k; q < w; q++) sum += iv[q * w + k] * vw[q][r];
+            for (int q = k; q < w; q++) sum += iv[q * w + k] * vw[q * ldv + r];
             z[(int64_t)(ch.col0 + k) * nb + r] = sum;
         }
     } else {
-        if (lane < nb) {
-            const int r = lane;
+        for (int r = lane; r < nb; r += 32) {
             for (int k = w - 1; k >= 0; k--) {
-                T sum = vw[k][r];
-                for (int q = k + 1; q < w; q++) sum -= dg[(int64_t)q * ch.ld + k] * vw[q][r];
-                vw[k][r] = sum / dg[(int64_t)k * ch.ld + k];
-                z[(int64_t)(ch.col0 + k) * nb + r] = vw[k][r];
+                T sum = vw[k * ldv + r];
+                for (int q = k + 1; q < w; q++) sum -= dg[(int64_t)q * ch.ld + k] * vw[q * ldv + r];
+                vw[k * ldv + r] = sum / dg[(int64_t)k * ch.ld + k];
+                z[(int64_t)(ch.col0 + k) * nb + r] = vw[k * ldv + r];
             }
         }
     }
@@ -304,39 +364,56 @@ __device__ bool bwd_tile_warp(const T *__restrict__ lnz, const ChunkDev &ch, con
     return true;
 }
 
-// Forward sweep: one persistent launch over all tiles in level order. A CTA
-// takes the next tile, stages its rows of L and the chunk's diagonal block (or
-// its inverse), waits until every tile that updates the chunk's rows of x has
-// arrived, solves y_c = L_cc^{-1} x_c and subtracts L_{rows,c} y_c from x. Then
-// it counts one arrival at every chunk its rows fall in. A tile only waits for
-// tiles of lower levels, which were taken earlier by running CTAs, so the
-// sweep needs no co-residency guarantee.
+// Pointers of one sweep CTA's dynamic shared memory.
 template <typename T>
-__global__ void __launch_bounds__(256, 4) k_fwd(const T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
+struct SweepSmem {
+    T (*l)[kMaxChunk + 1];   // diagonal block L_cc (or its FP32 inverse)
+    T (*lr)[kMaxChunk + 1];  // the tile's rows of L
+    T *v;                    // 64 x ldv: y_c (forward), z of the tile's rows (backward)
+    T *xin;                  // 64 x ldv: x_c (forward), y_c - acc_c (backward)
+    __device__ SweepSmem(unsigned char *raw, int ldv) {
+        l = reinterpret_cast<T (*)[kMaxChunk + 1]>(raw);
+        lr = l + kMaxChunk;
+        v = reinterpret_cast<T *>(lr + kMaxChunk);
+        xin = v + kMaxChunk * ldv;
+    }
+};
+
+// Forward sweep: one persistent launch over all tiles in level order, every
+// unit all right-hand sides of one block (up to kRhsBlk). A wide chunk's first
+// tile waits until every tile that updates the chunk's rows of x has arrived,
+// solves y_c = L_cc^{-1} x_c once (the stored FP32 inverse as a product, or
+// FP64 substitution), writes y_c and publishes it (ready flag); the chunk's
+// other tiles wait for that flag and read y_c. Every tile stages its rows of L
+// before waiting, subtracts L_{rows,c} y_c from x (atomic adds: tiles of
+// several chunks update the same rows) and counts one arrival at every chunk
+// its rows fall in. A tile only waits for tiles taken earlier (lower levels,
+// or its own chunk's first tile), so the sweep needs no co-residency.
+template <typename T, int RPT>
+__global__ void __launch_bounds__(256) k_fwd(const T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
                                              const TrsmTile *__restrict__ tiles, const SolveUnit *__restrict__ units,
                                              int total, const int32_t *__restrict__ dep_ptr,
                                              const int32_t *__restrict__ dep, const int32_t *__restrict__ need,
-                                             const int32_t *__restrict__ glbind,
-                                             T *__restrict__ x0, T *__restrict__ y0, int nrhs, int64_t vstride,
+                                             const int32_t *__restrict__ glbind, T *__restrict__ x0,
+                                             T *__restrict__ y0, int nrhs, int64_t vstride,
                                              const float *__restrict__ inv, int32_t *__restrict__ arrive0,
-                                             int64_t sstride, int32_t *__restrict__ work, int32_t *__restrict__ err,
-                                             long long spin_limit) {
+                                             int32_t *__restrict__ ready0, int64_t sstride, int32_t *__restrict__ work,
+                                             int32_t *__restrict__ err, long long spin_limit) {
     extern __shared__ __align__(16) unsigned char smem_fwd[];
-    auto l = reinterpret_cast<T (*)[kMaxChunk + 1]>(smem_fwd);
-    auto v = reinterpret_cast<T (*)[kRhsBlk]>(smem_fwd + sizeof(T) * kMaxChunk * (kMaxChunk + 1));
-    auto xin = reinterpret_cast<T (*)[kRhsBlk]>(smem_fwd + sizeof(T) * (kMaxChunk * (kMaxChunk + 1) + kMaxChunk * kRhsBlk));
-    T *rinv = reinterpret_cast<T *>(smem_fwd + sizeof(T) * (kMaxChunk * (kMaxChunk + 1) + 2 * kMaxChunk * kRhsBlk));
-    auto lr = reinterpret_cast<T (*)[kMaxChunk + 1]>(smem_fwd + sizeof(T) * (kMaxChunk * (kMaxChunk + 1) + 2 * kMaxChunk * kRhsBlk + kMaxChunk));
+    const int ldv = rhs_ld(min(nrhs, kRhsBlk));
+    SweepSmem<T> sm(smem_fwd, ldv);
+    __shared__ T rinv[kMaxChunk];
     __shared__ int s_t, s_ok;
+    const int nblk = (nrhs + kRhsBlk - 1) / kRhsBlk;
     for (;;) {
         const int ug = grab_tile(work, total, err, &s_t);
         if (ug >= total) break;
         // unit-major over the right-hand-side blocks: each block keeps its own order
-        const int nblk = (nrhs + kRhsBlk - 1) / kRhsBlk, bk = ug % nblk;
+        const int bk = ug % nblk;
         const SolveUnit su = units[ug / nblk];
         const int nb = min(kRhsBlk, nrhs - bk * kRhsBlk);
         T *x = x0 + bk * vstride, *y = y0 + bk * vstride;
-        int32_t *arrive = arrive0 + bk * sstride;
+        int32_t *arrive = arrive0 + bk * sstride, *ready = ready0 + bk * sstride;
         if (su.cnt > 0) {  // narrow tiles, one per warp
             const int wp = threadIdx.x / 32;
             if (wp < su.cnt) {
@@ -344,7 +421,7 @@ __global__ void __launch_bounds__(256, 4) k_fwd(const T *__restrict__ lnz, const
                 const TrsmTile tl = tiles[t];
                 const ChunkDev ch = chunks[tl.chunk];
                 fwd_tile_warp(lnz, ch, tl, t, dep_ptr, dep, need, glbind, x, y, nb, inv, arrive, err, spin_limit,
-                              reinterpret_cast<T (*)[kRhsBlk]>(smem_fwd) + wp * kSmallW);
+                              sm.v + wp * kSmallW * ldv, ldv);
             }
             __syncthreads();
             continue;
@@ -353,69 +430,67 @@ __global__ void __launch_bounds__(256, 4) k_fwd(const T *__restrict__ lnz, const
         const TrsmTile tl = tiles[t];
         const ChunkDev ch = chunks[tl.chunk];
         const int w = ch.w;
-        const bool first = tl.r0 == ch.c0 + w;  // the chunk's first tile writes y_c
+        const bool first = tl.r0 == ch.c0 + w;  // the chunk's first tile solves and publishes y_c
         const int rows = max(0, min(kSolveRows, ch.m - tl.r0));
-        // loads that need no other tile: the tile's rows of L and the diagonal block
-        stage_block(lr, lnz + ch.off + (int64_t)tl.r0 * ch.ld + ch.c0, ch.ld, rows, w);
-        if constexpr (sizeof(T) == 4) stage_block(l, (const T *)(inv + ch.inv), w, w, w);
-        else load_diag(l, rinv, lnz, ch, true);
-        if (threadIdx.x == 0) s_ok = wait_flag(arrive + (int64_t)tl.chunk * kSyncStride, need[tl.chunk], err, spin_limit, 5);
-        __syncthreads();
-        if (!s_ok) break;
-        if constexpr (sizeof(T) == 4) {
-            // y_c = inv(L_cc) x_c: the block's stored inverse, a parallel product
-#pragma unroll
-            for (int it = 0; it < kMaxChunk * kRhsBlk / 256; it++) {
-                const int idx = threadIdx.x + it * 256, k = idx / nb, r = idx % nb;
-                if (idx < w * nb) xin[k][r] = __ldcg(x + (int64_t)(ch.col0 + k) * nb + r);
-            }
+        // loads that need no other tile: the tile's rows of L (and the diagonal block)
+        stage_block(sm.lr, lnz + ch.off + (int64_t)tl.r0 * ch.ld + ch.c0, ch.ld, rows, w);
+        if (first) {
+            if constexpr (sizeof(T) == 4) stage_block(sm.l, (const T *)(inv + ch.inv), w, w, w);
+            else load_diag(sm.l, rinv, lnz, ch, true);
+            if (threadIdx.x == 0)
+                s_ok = wait_flag(arrive + (int64_t)tl.chunk * kSyncStride, need[tl.chunk], err, spin_limit, 5);
             __syncthreads();
-            // the stored inverse is zero above its diagonal: full-width rows
-            const int k = threadIdx.x % kMaxChunk, g = threadIdx.x / kMaxChunk;
-            if (k < w && 4 * g < nb) {
-                float o[4];
-                rhs4_product<false>(l, xin, k, g, w, o);
+            if (!s_ok) break;
+            stage_rhs(sm.xin, ldv, x, nb, w, [&](int r) { return ch.col0 + r; });
+            __syncthreads();
+            if constexpr (sizeof(T) == 4) {
+                // y_c = inv(L_cc) x_c: the block's stored inverse (zero above its diagonal)
+                const int k = threadIdx.x % kMaxChunk, r0 = (threadIdx.x / kMaxChunk) * RPT;
+                if (k < w && r0 < nb) {
+                    T o[RPT];
+                    rhs_product<T, RPT, false>(sm.l, sm.xin, ldv, k, r0, w, o);
 #pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    const int r = 4 * g + j;
-                    if (r < nb) {
-                        v[k][r] = o[j];
-                        if (first) y[(int64_t)(ch.col0 + k) * nb + r] = o[j];
+                    for (int j = 0; j < RPT; j++)
+                        if (r0 + j < nb) {
+                            sm.v[k * ldv + r0 + j] = o[j];
+                            y[(int64_t)(ch.col0 + k) * nb + r0 + j] = o[j];
+                        }
+                }
+            } else {
+                const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+                for (int r = warp; r < nb; r += blockDim.x / 32) {
+                    T u0 = lane < w ? sm.xin[lane * ldv + r] : T(0);
+                    T u1 = lane + 32 < w ? sm.xin[(lane + 32) * ldv + r] : T(0);
+                    warp_lower_solve(sm.l, rinv, w, u0, u1);
+                    if (lane < w) {
+                        sm.v[lane * ldv + r] = u0;
+                        y[(int64_t)(ch.col0 + lane) * nb + r] = u0;
+                    }
+                    if (lane + 32 < w) {
+                        sm.v[(lane + 32) * ldv + r] = u1;
+                        y[(int64_t)(ch.col0 + lane + 32) * nb + r] = u1;
                     }
                 }
             }
-        } else {
-            const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
-            for (int r = warp; r < nb; r += blockDim.x / 32) {
-                T x0 = lane < w ? __ldcg(x + (int64_t)(ch.col0 + lane) * nb + r) : T(0);
-                T x1 = lane + 32 < w ? __ldcg(x + (int64_t)(ch.col0 + lane + 32) * nb + r) : T(0);
-                warp_lower_solve(l, rinv, w, x0, x1);
-                if (lane < w) v[lane][r] = x0;
-                if (lane + 32 < w) v[lane + 32][r] = x1;
-                if (first) {
-                    if (lane < w) y[(int64_t)(ch.col0 + lane) * nb + r] = x0;
-                    if (lane + 32 < w) y[(int64_t)(ch.col0 + lane + 32) * nb + r] = x1;
-                }
+            __syncthreads();
+            if (threadIdx.x == 0) {  // release y_c to the chunk's other tiles
+                __threadfence();
+                atomicExch(ready + (int64_t)tl.chunk * kSyncStride, 1);
             }
+        } else {
+            if (threadIdx.x == 0) s_ok = wait_flag(ready + (int64_t)tl.chunk * kSyncStride, 1, err, spin_limit, 7);
+            __syncthreads();
+            if (!s_ok) break;
+            stage_rhs(sm.v, ldv, (const T *)y, nb, w, [&](int r) { return ch.col0 + r; });
+            __syncthreads();
         }
-        __syncthreads();
-        if constexpr (sizeof(T) == 4) {
-            const int i = threadIdx.x % kSolveRows, g = threadIdx.x / kSolveRows;
-            if (i < rows && 4 * g < nb) {
-                float o[4];
-                rhs4_product<false>(lr, v, i, g, w, o);
-                T *xr = x + (int64_t)glbind[ch.gl + tl.r0 + i] * nb;
-#pragma unroll
-                for (int j = 0; j < 4; j++)
-                    if (4 * g + j < nb) atomicAdd(xr + 4 * g + j, -o[j]);
-            }
-        } else {
-            for (int idx = threadIdx.x; idx < rows * nb; idx += blockDim.x) {
-                int i = idx / nb, r = idx % nb;
-                T acc = T(0);
-                for (int k = 0; k < w; k++) acc += lr[i][k] * v[k][r];
-                int g = glbind[ch.gl + tl.r0 + i];
-                atomicAdd(x + (int64_t)g * nb + r, -acc);
+        // x_rows -= L_{rows,c} y_c
+        {
+            const int i = threadIdx.x % kSolveRows, r0 = (threadIdx.x / kSolveRows) * RPT;
+            if (i < rows && r0 < nb) {
+                T o[RPT];
+                rhs_product<T, RPT, false>(sm.lr, sm.v, ldv, i, r0, w, o);
+                add_rhs<T, RPT>(x + (int64_t)glbind[ch.gl + tl.r0 + i] * nb + r0, o, T(-1), r0, nb);
             }
         }
         // release: the barrier orders every thread's updates before thread 0's fence
@@ -427,34 +502,33 @@ __global__ void __launch_bounds__(256, 4) k_fwd(const T *__restrict__ lnz, const
     }
 }
 
-// Backward sweep: one persistent launch over all tiles in reverse level order.
-// A tile stages its rows of L, waits until z is final in every chunk its rows
-// fall in, and adds L_{rows,c}^T z_rows into acc_c; the chunk's last tile to
-// finish solves z_c = L_cc^{-T} (y_c - acc_c) and marks the chunk done.
-template <typename T>
-__global__ void __launch_bounds__(256, 4) k_bwd(const T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
+// Backward sweep: one persistent launch over all tiles in reverse level order,
+// every unit all right-hand sides of one block. A tile stages its rows of L,
+// waits until z is final in every chunk its rows fall in, and adds
+// L_{rows,c}^T z_rows into acc_c; the chunk's last tile to finish solves
+// z_c = L_cc^{-T} (y_c - acc_c) and marks the chunk done.
+template <typename T, int RPT>
+__global__ void __launch_bounds__(256) k_bwd(const T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
                                              const TrsmTile *__restrict__ tiles, const SolveUnit *__restrict__ units,
                                              int total, const int32_t *__restrict__ dep_ptr,
                                              const int32_t *__restrict__ dep, const int32_t *__restrict__ ntiles,
-                                             const int32_t *__restrict__ glbind,
-                                             const T *__restrict__ y0, T *__restrict__ z0, T *__restrict__ acc0,
-                                             int nrhs, int64_t vstride, const float *__restrict__ inv,
-                                             int32_t *__restrict__ cnt0, int32_t *__restrict__ done0, int64_t sstride,
-                                             int32_t *__restrict__ work, int32_t *__restrict__ err,
-                                             long long spin_limit) {
+                                             const int32_t *__restrict__ glbind, const T *__restrict__ y0,
+                                             T *__restrict__ z0, T *__restrict__ acc0, int nrhs, int64_t vstride,
+                                             const float *__restrict__ inv, int32_t *__restrict__ cnt0,
+                                             int32_t *__restrict__ done0, int64_t sstride, int32_t *__restrict__ work,
+                                             int32_t *__restrict__ err, long long spin_limit) {
     extern __shared__ __align__(16) unsigned char smem_bwd[];
-    auto l = reinterpret_cast<T (*)[kMaxChunk + 1]>(smem_bwd);
-    auto vin = reinterpret_cast<T (*)[kRhsBlk]>(smem_bwd + sizeof(T) * kMaxChunk * (kMaxChunk + 1));
-    T *rinv = reinterpret_cast<T *>(smem_bwd + sizeof(T) * (kMaxChunk * (kMaxChunk + 1) + 2 * kMaxChunk * kRhsBlk));
-    auto lt = reinterpret_cast<T (*)[kMaxChunk + 1]>(smem_bwd);  // [rows][w]
-    auto zt = reinterpret_cast<T (*)[kRhsBlk]>(smem_bwd + sizeof(T) * kMaxChunk * (kMaxChunk + 1));
+    const int ldv = rhs_ld(min(nrhs, kRhsBlk));
+    SweepSmem<T> sm(smem_bwd, ldv);
+    __shared__ T rinv[kMaxChunk];
     __shared__ int32_t grow[kSolveRows];
     __shared__ int s_t, s_ok, s_last;
+    const int nblk = (nrhs + kRhsBlk - 1) / kRhsBlk;
     for (;;) {
         const int tr = grab_tile(work, total, err, &s_t);
         if (tr >= total) break;
         const int ug = total - 1 - tr;
-        const int nblk = (nrhs + kRhsBlk - 1) / kRhsBlk, bk = ug % nblk;
+        const int bk = ug % nblk;
         const SolveUnit su = units[ug / nblk];
         const int nb = min(kRhsBlk, nrhs - bk * kRhsBlk);
         const T *y = y0 + bk * vstride;
@@ -467,7 +541,7 @@ __global__ void __launch_bounds__(256, 4) k_bwd(const T *__restrict__ lnz, const
                 const TrsmTile tl = tiles[t];
                 const ChunkDev ch = chunks[tl.chunk];
                 bwd_tile_warp(lnz, ch, tl, t, dep_ptr, dep, ntiles, glbind, y, z, acc, nb, inv, cnt, done, err,
-                              spin_limit, reinterpret_cast<T (*)[kRhsBlk]>(smem_bwd) + wp * kSmallW);
+                              spin_limit, sm.v + wp * kSmallW * ldv, ldv);
             }
             __syncthreads();
             continue;
@@ -479,37 +553,23 @@ __global__ void __launch_bounds__(256, 4) k_bwd(const T *__restrict__ lnz, const
         const int rows = max(0, min(kSolveRows, ch.m - tl.r0));
         if (rows > 0) {
             if (threadIdx.x < rows) grow[threadIdx.x] = glbind[ch.gl + tl.r0 + threadIdx.x];
-            stage_block(lt, lnz + ch.off + (int64_t)tl.r0 * ch.ld + ch.c0, ch.ld, rows, w);
+            stage_block(sm.lr, lnz + ch.off + (int64_t)tl.r0 * ch.ld + ch.c0, ch.ld, rows, w);
             if (threadIdx.x == 0) {
                 bool ok = true;
-                for (int p = dep_ptr[t]; p < dep_ptr[t + 1] && ok; p++) ok = wait_flag(done + (int64_t)dep[p] * kSyncStride, 1, err, spin_limit, 6);
+                for (int p = dep_ptr[t]; p < dep_ptr[t + 1] && ok; p++)
+                    ok = wait_flag(done + (int64_t)dep[p] * kSyncStride, 1, err, spin_limit, 6);
                 s_ok = ok;
             }
             __syncthreads();
             if (!s_ok) break;
-#pragma unroll
-            for (int it = 0; it < kSolveRows * kRhsBlk / 256; it++) {
-                const int idx = threadIdx.x + it * 256, i = idx / nb, r = idx % nb;
-                if (idx < rows * nb) zt[i][r] = __ldcg(z + (int64_t)grow[i] * nb + r);
-            }
+            stage_rhs(sm.v, ldv, (const T *)z, nb, rows, [&](int r) { return grow[r]; });
             __syncthreads();
-            if constexpr (sizeof(T) == 4) {
-                const int k = threadIdx.x % kMaxChunk, g = threadIdx.x / kMaxChunk;
-                if (k < w && 4 * g < nb) {
-                    float o[4];
-                    rhs4_product<true>(lt, zt, k, g, rows, o);
-                    T *ar = acc + (int64_t)(ch.col0 + k) * nb;
-#pragma unroll
-                    for (int j = 0; j < 4; j++)
-                        if (4 * g + j < nb) atomicAdd(ar + 4 * g + j, o[j]);
-                }
-            } else {
-                for (int idx = threadIdx.x; idx < w * nb; idx += blockDim.x) {
-                    int k = idx / nb, r = idx % nb;
-                    T s = T(0);
-                    for (int i = 0; i < rows; i++) s += lt[i][k] * zt[i][r];
-                    atomicAdd(acc + (int64_t)(ch.col0 + k) * nb + r, s);
-                }
+            // acc_c += L_{rows,c}^T z_rows
+            const int k = threadIdx.x % kMaxChunk, r0 = (threadIdx.x / kMaxChunk) * RPT;
+            if (k < w && r0 < nb) {
+                T o[RPT];
+                rhs_product<T, RPT, true>(sm.lr, sm.v, ldv, k, r0, rows, o);
+                add_rhs<T, RPT>(acc + (int64_t)(ch.col0 + k) * nb + r0, o, T(1), r0, nb);
             }
         }
         __syncthreads();
@@ -522,35 +582,31 @@ __global__ void __launch_bounds__(256, 4) k_bwd(const T *__restrict__ lnz, const
         if (!s_last) continue;
         if constexpr (sizeof(T) == 4) {
             // z_c = inv(L_cc)^T (y_c - acc_c) with the block's stored inverse
-            stage_block(l, (const T *)(inv + ch.inv), w, w, w);
-#pragma unroll
-            for (int it = 0; it < kMaxChunk * kRhsBlk / 256; it++) {
-                const int idx = threadIdx.x + it * 256, k = idx / nb, r = idx % nb;
-                if (idx < w * nb) {
-                    int64_t g = (int64_t)(ch.col0 + k) * nb + r;
-                    vin[k][r] = y[g] - __ldcg(acc + g);
-                }
+            stage_block(sm.l, (const T *)(inv + ch.inv), w, w, w);
+            for (int idx = threadIdx.x; idx < w * nb; idx += blockDim.x) {
+                const int kk = idx / nb, r = idx % nb;
+                const int64_t g = (int64_t)(ch.col0 + kk) * nb + r;
+                sm.xin[kk * ldv + r] = y[g] - __ldcg(acc + g);
             }
             __syncthreads();
-            // inv(L_cc)^T: column k of the inverse, zero above the diagonal
-            const int k = threadIdx.x % kMaxChunk, g = threadIdx.x / kMaxChunk;
-            if (k < w && 4 * g < nb) {
-                float o[4];
-                rhs4_product<true>(l, vin, k, g, w, o);
+            const int k = threadIdx.x % kMaxChunk, r0 = (threadIdx.x / kMaxChunk) * RPT;
+            if (k < w && r0 < nb) {
+                T o[RPT];
+                rhs_product<T, RPT, true>(sm.l, sm.xin, ldv, k, r0, w, o);
 #pragma unroll
-                for (int j = 0; j < 4; j++)
-                    if (4 * g + j < nb) z[(int64_t)(ch.col0 + k) * nb + 4 * g + j] = o[j];
+                for (int j = 0; j < RPT; j++)
+                    if (r0 + j < nb) z[(int64_t)(ch.col0 + k) * nb + r0 + j] = o[j];
             }
         } else {
-            load_diag(l, rinv, lnz, ch, false);
+            load_diag(sm.l, rinv, lnz, ch, false);
             const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
             for (int r = warp; r < nb; r += blockDim.x / 32) {
                 const int64_t g0 = (int64_t)(ch.col0 + lane) * nb + r, g1 = (int64_t)(ch.col0 + lane + 32) * nb + r;
-                T x0 = lane < w ? y[g0] - __ldcg(acc + g0) : T(0);
-                T x1 = lane + 32 < w ? y[g1] - __ldcg(acc + g1) : T(0);
-                warp_upper_solve(l, rinv, w, x0, x1);
-                if (lane < w) z[g0] = x0;
-                if (lane + 32 < w) z[g1] = x1;
+                T u0 = lane < w ? y[g0] - __ldcg(acc + g0) : T(0);
+                T u1 = lane + 32 < w ? y[g1] - __ldcg(acc + g1) : T(0);
+                warp_upper_solve(sm.l, rinv, w, u0, u1);
+                if (lane < w) z[g0] = u0;
+                if (lane + 32 < w) z[g1] = u1;
             }
         }
         __syncthreads();
@@ -691,6 +747,9 @@ __global__ void k_cg_dir(double *__restrict__ P, const double *__restrict__ Z, c
     P[g] = Z[g] + b * P[g];
 }
 
+template <typename T>
+int set_sweep_attrs();
+
 int ensure_solve(sc_numeric *h, int64_t nrhs) {
     const sc_symbolic *s = h->sym;
     int64_t n = s->n;
@@ -786,25 +845,7 @@ int ensure_solve(sc_numeric *h, int64_t nrhs) {
         // the two work counters
         if (cudaMalloc((void **)&h->d_serr, sizeof(int32_t)) != cudaSuccess) return SC_ERR_OOM;
         if (cudaMalloc((void **)&h->d_red, 4096 * sizeof(double)) != cudaSuccess) return SC_ERR_OOM;
-        if (cudaFuncSetAttribute(k_fwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, solve_smem<double>()) ||
-            cudaFuncSetAttribute(k_bwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, solve_smem<double>()) ||
-            cudaFuncSetAttribute(k_fwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, solve_smem<float>()) ||
-            cudaFuncSetAttribute(k_bwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, solve_smem<float>()))
-            return SC_ERR_CUDA;
-        // persistent sweeps: as many CTAs as fit on the device at once
-        int per_sm = 1;
-        if (h->elt == 8) {
-            int a = 1, b = 1;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_fwd<double>, 256, solve_smem<double>());
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bwd<double>, 256, solve_smem<double>());
-            per_sm = std::max(1, std::min(a, b));
-        } else {
-            int a = 1, b = 1;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_fwd<float>, 256, solve_smem<float>());
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bwd<float>, 256, solve_smem<float>());
-            per_sm = std::max(1, std::min(a, b));
-        }
-        h->solve_grid = std::max(1, per_sm * h->num_sms);  // CTAs resident at once; a launch takes fewer if it has less work
+        if (set_sweep_attrs<double>() || set_sweep_attrs<float>()) return SC_ERR_CUDA;
         h->solve_ready = true;
     }
     if (nrhs > h->solve_cap) {
@@ -823,11 +864,12 @@ int ensure_solve(sc_numeric *h, int64_t nrhs) {
         void **dw[] = {&h->d_y, &h->d_z, &h->d_acc, &h->d_xw};
         for (void **p : dw) {
             if (*p) cudaFree(*p);
-            if (cudaMalloc(p, (size_t)n * kRhsBlk * nblk * h->elt) != cudaSuccess) return SC_ERR_OOM;
+            if (cudaMalloc(p, (size_t)n * std::min<int64_t>(nrhs, kRhsBlk) * nblk * h->elt) != cudaSuccess)
+                return SC_ERR_OOM;
         }
         if (h->d_sync) cudaFree(h->d_sync);
-        if (cudaMalloc((void **)&h->d_sync, (3 * s->chunks.size() * kSyncStride * nblk + 2) * sizeof(int32_t)) !=
-            cudaSuccess)
+        if (cudaMalloc((void **)&h->d_sync,
+                       (kSyncWords * s->chunks.size() * kSyncStride * nblk + 2) * sizeof(int32_t)) != cudaSuccess)
             return SC_ERR_OOM;
         h->solve_cap = nrhs;
     }
@@ -836,18 +878,58 @@ int ensure_solve(sc_numeric *h, int64_t nrhs) {
 
 // One triangular solve with the factor: X = A^{-1} B (or X += A^{-1} B), B and X
 // column-major n x nrhs FP64 device arrays.
+template <typename T, int RPT>
+void launch_sweeps(sc_numeric *h, int nrhs, int64_t vs, int64_t ss, T *xw, T *y, T *z, T *acc, int32_t *sync,
+                   int nblk, cudaStream_t st) {
+    const sc_symbolic *s = h->sym;
+    const T *lnz = (const T *)h->d_lnz;
+    const size_t nch = s->chunks.size();
+    const int nbmax = std::min(nrhs, kRhsBlk);
+    const size_t smem = solve_smem<T>(nbmax);
+    int per_sm = 1, a = 1, b = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_fwd<T, RPT>, 256, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bwd<T, RPT>, 256, smem);
+    per_sm = std::max(1, std::min(a, b));
+    const long long spin = (long long)s->opt.spin_limit;
+    const int total = h->solve_tiles * nblk;
+    // persistent sweeps: as many CTAs as fit on the device at once (fewer if there is less work)
+    const int grid = std::max(1, std::min(total, per_sm * h->num_sms));
+    int32_t *arrive = sync, *ready = sync + nch * kSyncStride, *cnt = sync + 2 * nch * kSyncStride,
+            *done = sync + 3 * nch * kSyncStride, *work = sync + nblk * ss;
+    k_fwd<T, RPT><<<grid, 256, smem, st>>>(lnz, h->d_chunks, h->d_solve_tiles, h->d_solve_units, total, h->d_dep_ptr,
+                                           h->d_dep, h->d_counters + nch, h->d_glbind, xw, y, nrhs, vs,
+                                           (const float *)h->d_inv, arrive, ready, ss, work, h->d_serr, spin);
+    k_bwd<T, RPT><<<grid, 256, smem, st>>>(lnz, h->d_chunks, h->d_solve_tiles, h->d_solve_units, total, h->d_dep_ptr,
+                                           h->d_dep, h->d_counters, h->d_glbind, y, z, acc, nrhs, vs,
+                                           (const float *)h->d_inv, cnt, done, ss, work + 1, h->d_serr, spin);
+}
+
+template <typename T>
+int set_sweep_attrs() {
+    const int smem = (int)solve_smem<T>(kRhsBlk);
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void *k) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    };
+    set((const void *)k_fwd<T, 1>), set((const void *)k_bwd<T, 1>);
+    set((const void *)k_fwd<T, 2>), set((const void *)k_bwd<T, 2>);
+    set((const void *)k_fwd<T, 4>), set((const void *)k_bwd<T, 4>);
+    set((const void *)k_fwd<T, 8>), set((const void *)k_bwd<T, 8>);
+    set((const void *)k_fwd<T, 16>), set((const void *)k_bwd<T, 16>);
+    return e == cudaSuccess ? 0 : 1;
+}
+
 template <typename T>
 int tri_solve(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, double *X, int64_t ldx, int add,
               cudaStream_t st, int &launches) {
     const sc_symbolic *s = h->sym;
     const int64_t n = s->n;
-    const T *lnz = (const T *)h->d_lnz;
     T *xw = (T *)h->d_xw, *y = (T *)h->d_y, *z = (T *)h->d_z, *acc = (T *)h->d_acc;
     const size_t nch = s->chunks.size();
     // every block of kRhsBlk right-hand sides has its own work vectors and
     // synchronisation words; one persistent launch per sweep serves them all
     const int nblk = (int)((nrhs + kRhsBlk - 1) / kRhsBlk);
-    const int64_t vs = n * kRhsBlk, ss = 3 * (int64_t)nch * kSyncStride;
+    const int64_t vs = n * std::min<int64_t>(nrhs, kRhsBlk), ss = kSyncWords * (int64_t)nch * kSyncStride;
     for (int bk = 0; bk < nblk; bk++) {
         const int nb = (int)std::min<int64_t>(kRhsBlk, nrhs - bk * kRhsBlk);
         const unsigned g = (unsigned)((n * nb + 255) / 256);
@@ -856,19 +938,13 @@ int tri_solve(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, double 
     }
     SC_CUDA(cudaMemsetAsync(h->d_sync, 0, (nblk * ss + 2) * sizeof(int32_t), st));
     SC_CUDA(cudaMemsetAsync(acc, 0, (size_t)nblk * vs * sizeof(T), st));
-    int32_t *arrive = h->d_sync, *cnt = h->d_sync + nch * kSyncStride, *done = h->d_sync + 2 * nch * kSyncStride,
-            *work = h->d_sync + nblk * ss;
-    const long long spin = (long long)s->opt.spin_limit;
-    const int total = h->solve_tiles * nblk;
-    const int grid = std::max(1, std::min(total, h->solve_grid));
-    k_fwd<T><<<grid, 256, solve_smem<T>(), st>>>(lnz, h->d_chunks, h->d_solve_tiles, h->d_solve_units, total,
-                                                 h->d_dep_ptr, h->d_dep, h->d_counters + nch, h->d_glbind, xw, y,
-                                                 (int)nrhs, vs, (const float *)h->d_inv, arrive, ss, work, h->d_serr,
-                                                 spin);
-    k_bwd<T><<<grid, 256, solve_smem<T>(), st>>>(lnz, h->d_chunks, h->d_solve_tiles, h->d_solve_units, total,
-                                                 h->d_dep_ptr, h->d_dep, h->d_counters, h->d_glbind, y, z, acc,
-                                                 (int)nrhs, vs, (const float *)h->d_inv, cnt, done, ss, work + 1,
-                                                 h->d_serr, spin);
+    switch (rhs_per_thread((int)std::min<int64_t>(nrhs, kRhsBlk))) {
+        case 1: launch_sweeps<T, 1>(h, (int)nrhs, vs, ss, xw, y, z, acc, h->d_sync, nblk, st); break;
+        case 2: launch_sweeps<T, 2>(h, (int)nrhs, vs, ss, xw, y, z, acc, h->d_sync, nblk, st); break;
+        case 4: launch_sweeps<T, 4>(h, (int)nrhs, vs, ss, xw, y, z, acc, h->d_sync, nblk, st); break;
+        case 8: launch_sweeps<T, 8>(h, (int)nrhs, vs, ss, xw, y, z, acc, h->d_sync, nblk, st); break;
+        default: launch_sweeps<T, 16>(h, (int)nrhs, vs, ss, xw, y, z, acc, h->d_sync, nblk, st); break;
+    }
     launches += 2;
     for (int bk = 0; bk < nblk; bk++) {
         const int nb = (int)std::min<int64_t>(kRhsBlk, nrhs - bk * kRhsBlk);

@@ -47,15 +47,26 @@ def test_stalled_chunk_times_out_and_handle_recovers(prec, where):
     assert np.abs(X1 - X0).max() <= 1e-10 * np.abs(X0).max()
 
 
-def test_many_right_hand_sides_several_blocks():
-    """40 right-hand sides: three blocks of the sweep (16 + 16 + 8), each with
-    freshly zeroed counters."""
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("nrhs", [1, 5, 12, 33, 64, 70, 130])
+def test_many_right_hand_sides(prec, nrhs):
+    """Blocks of up to 64 right-hand sides, one sweep unit covering a whole
+    block: 1..4, 5..8, 9..16, 17..32 and 33..64 right-hand sides per block take
+    the five register-blocking variants; 70 and 130 make two and three blocks
+    (the last one ragged: 6 and 2), each with freshly zeroed counters; counts
+    that are not multiples of 4 take the scalar atomic adds. X is compared
+    with the oracle's solve and eta <= 1e-14 (FP32: after refinement)."""
     A = inputs.workload(2, 0.25)[0]
     sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid)
-    num = sym.factor(A.values, precision="fp64")
-    B = inputs.rhs(A.n, 40, 12)
+    num = sym.factor(A.values, precision=prec)
+    assert num.rc == 0
+    B = inputs.rhs(A.n, nrhs, 12)
     X, info = num.solve(B)
-    assert oracle.backward_error(A, B, X).max() <= 1e-14
+    assert oracle.backward_error(A, B, X).max() <= 1e-14, info
+    o = oracle.Oracle(A, oracle.nd_grid(*A.grid, 8), pr=True)
+    assert o.factor() == 0
+    Xo = o.solve(B)
+    assert np.abs(X - Xo).max() <= 1e-8 * np.abs(Xo).max()
 
 
 @pytest.mark.parametrize("prec", ["fp32", "tf32", "tf32x3"])
