@@ -80,12 +80,58 @@ __device__ __forceinline__ void stage_block(T (*dst)[kMaxChunk + 1], const T *__
 }
 
 // Loads rows x nb values of a row-major vector block (row r at src + row(r) * nb,
-// read through L2: other CTAs wrote them) into dst[r][0..nb) (row stride ldv).
+// read through L2: other CTAs wrote them) into dst[r][0..nb) (row stride ldv),
+// rows <= 64, nb <= 64, 256 threads: a fixed trip count per thread with every
+// load in flight before the stores (16-byte vectors when nb allows).
 template <typename T, typename RowOf>
-__device__ __forceinline__ void stage_rhs(T *__restrict__ dst, int ldv, const T *src, int nb, int rows, RowOf row_of) {
-    for (int idx = threadIdx.x; idx < rows * nb; idx += blockDim.x) {
-        const int r = idx / nb, c = idx % nb;
-        dst[r * ldv + c] = __ldcg(src + (int64_t)row_of(r) * nb + c);
+__device__ __forceinline__ void stage_rhs(T *__restrict__ dst, int ldv, const T *src, int nb, int rows,
+                                          RowOf row_of) {
+    if constexpr (sizeof(T) == 4) {
+        if ((nb & 3) == 0) {  // float4: at most 64 x 64 / 4 / 256 = 4 per thread
+            const int nv = nb >> 2, total = rows * nv;
+            float4 tmp[4];
+#pragma unroll
+            for (int it = 0; it < 4; it++) {
+                const int idx = threadIdx.x + it * 256;
+                if (idx < total)
+                    tmp[it] = __ldcg(reinterpret_cast<const float4 *>(src + (int64_t)row_of(idx / nv) * nb) + idx % nv);
+            }
+#pragma unroll
+            for (int it = 0; it < 4; it++) {
+                const int idx = threadIdx.x + it * 256;
+                if (idx < total) *reinterpret_cast<float4 *>(dst + (idx / nv) * ldv + 4 * (idx % nv)) = tmp[it];
+            }
+            return;
+        }
+    } else {
+        if ((nb & 1) == 0) {  // double2: at most 8 per thread
+            const int nv = nb >> 1, total = rows * nv;
+            double2 tmp[8];
+#pragma unroll
+            for (int it = 0; it < 8; it++) {
+                const int idx = threadIdx.x + it * 256;
+                if (idx < total)
+                    tmp[it] = __ldcg(reinterpret_cast<const double2 *>(src + (int64_t)row_of(idx / nv) * nb) + idx % nv);
+            }
+#pragma unroll
+            for (int it = 0; it < 8; it++) {
+                const int idx = threadIdx.x + it * 256;
+                if (idx < total) *reinterpret_cast<double2 *>(dst + (idx / nv) * ldv + 2 * (idx % nv)) = tmp[it];
+            }
+            return;
+        }
+    }
+    const int total = rows * nb;  // scalar: at most 16 per thread
+    T tmp[16];
+#pragma unroll
+    for (int it = 0; it < 16; it++) {
+        const int idx = threadIdx.x + it * 256;
+        if (idx < total) tmp[it] = __ldcg(src + (int64_t)row_of(idx / nb) * nb + idx % nb);
+    }
+#pragma unroll
+    for (int it = 0; it < 16; it++) {
+        const int idx = threadIdx.x + it * 256;
+        if (idx < total) dst[(idx / nb) * ldv + idx % nb] = tmp[it];
     }
 }
 
@@ -583,11 +629,10 @@ __global__ void __launch_bounds__(256) k_bwd(const T *__restrict__ lnz, const Ch
         if constexpr (sizeof(T) == 4) {
             // z_c = inv(L_cc)^T (y_c - acc_c) with the block's stored inverse
             stage_block(sm.l, (const T *)(inv + ch.inv), w, w, w);
-            for (int idx = threadIdx.x; idx < w * nb; idx += blockDim.x) {
-                const int kk = idx / nb, r = idx % nb;
-                const int64_t g = (int64_t)(ch.col0 + kk) * nb + r;
-                sm.xin[kk * ldv + r] = y[g] - __ldcg(acc + g);
-            }
+            stage_rhs(sm.xin, ldv, y, nb, w, [&](int r) { return ch.col0 + r; });
+            stage_rhs(sm.v, ldv, (const T *)acc, nb, w, [&](int r) { return ch.col0 + r; });
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < w * ldv; idx += blockDim.x) sm.xin[idx] -= sm.v[idx];
             __syncthreads();
             const int k = threadIdx.x % kMaxChunk, r0 = (threadIdx.x / kMaxChunk) * RPT;
             if (k < w && r0 < nb) {
@@ -632,119 +677,151 @@ __device__ inline void atomic_max_nonneg(double *addr, double v) {
 // max of two non-negative values or NaNs (a NaN wins: fmax would drop it)
 __device__ inline double nan_max(double a, double b) { return (a != a || a > b) ? a : b; }
 
+// Reductions of the vector kernels below: every kernel is grid-stride over the
+// rows of one column (blockIdx.y), reduces its values over the block (warp
+// shuffles, then the eight warp results through shared memory) and thread 0
+// adds or maxes the block's value into the column's word, so a column's words
+// take one atomic per block (a few dozen) instead of one per warp.
+__device__ inline double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ inline double warp_max(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = nan_max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+// block (256 threads) reduction of NV values; the result is valid in thread 0
+template <int NV, bool kMax>
+__device__ __forceinline__ void block_reduce(double (&v)[NV]) {
+    __shared__ double part[8][NV];
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+#pragma unroll
+    for (int q = 0; q < NV; q++) v[q] = kMax ? warp_max(v[q]) : warp_sum(v[q]);
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < NV; q++) part[warp][q] = v[q];
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int q = 0; q < NV; q++) {
+            double r = part[0][q];
+            for (int w = 1; w < 8; w++) r = kMax ? nan_max(r, part[w][q]) : r + part[w][q];
+            v[q] = r;
+        }
+}
+
 // ||A||_inf of the full symmetric matrix from its CSR
-__global__ void k_anorm(const int64_t *__restrict__ ptr, const double *__restrict__ val, int64_t n, double *out) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double s = 0.0;
-    for (int64_t p = ptr[i]; p < ptr[i + 1]; p++) s += fabs(val[p]);
-    atomic_max_nonneg(out, s);
+__global__ void __launch_bounds__(256) k_anorm(const int64_t *__restrict__ ptr, const double *__restrict__ val,
+                                               int64_t n, double *out) {
+    double m[1] = {0.0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int64_t p = ptr[i]; p < ptr[i + 1]; p++) s += fabs(val[p]);
+        m[0] = nan_max(m[0], s);
+    }
+    block_reduce<1, true>(m);
+    if (threadIdx.x == 0) atomic_max_nonneg(out, m[0]);
 }
 
 // r = b - A x (FP64), and per column: red[3c] = max|r|, red[3c+1] = max|x|, red[3c+2] = max|b|
-__global__ void k_residual(const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
-                           const double *__restrict__ val, const double *__restrict__ X, const double *__restrict__ B,
-                           double *__restrict__ R, int64_t n, int nrhs, double *__restrict__ red) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    int c = blockIdx.y;
-    const bool live = i < n;  // every lane stays for the warp-wide reduction below
+__global__ void __launch_bounds__(256) k_residual(const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                                                  const double *__restrict__ val, const double *__restrict__ X,
+                                                  const double *__restrict__ B, double *__restrict__ R, int64_t n,
+                                                  int nrhs, double *__restrict__ red) {
+    const int c = blockIdx.y;
     const double *x = X + (int64_t)c * n;
-    double m0 = 0.0, m1 = 0.0, m2 = 0.0;
-    if (live) {
+    double m[3] = {0.0, 0.0, 0.0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double b = B[(int64_t)c * n + i];
         double s = b;
         for (int64_t p = ptr[i]; p < ptr[i + 1]; p++) s -= val[p] * x[col[p]];
         R[(int64_t)c * n + i] = s;
-        m0 = fabs(s);
-        m1 = fabs(x[i]);
-        m2 = fabs(b);
+        m[0] = nan_max(m[0], fabs(s));
+        m[1] = nan_max(m[1], fabs(x[i]));
+        m[2] = nan_max(m[2], fabs(b));
     }
-    // warp-level maxima first: one atomic per warp instead of one per row
-    for (int o = 16; o > 0; o >>= 1) {
-        m0 = nan_max(m0, __shfl_xor_sync(0xffffffffu, m0, o));
-        m1 = nan_max(m1, __shfl_xor_sync(0xffffffffu, m1, o));
-        m2 = nan_max(m2, __shfl_xor_sync(0xffffffffu, m2, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomic_max_nonneg(red + 3 * c, m0);
-        atomic_max_nonneg(red + 3 * c + 1, m1);
-        atomic_max_nonneg(red + 3 * c + 2, m2);
+    block_reduce<3, true>(m);
+    if (threadIdx.x == 0) {
+        atomic_max_nonneg(red + 3 * c, m[0]);
+        atomic_max_nonneg(red + 3 * c + 1, m[1]);
+        atomic_max_nonneg(red + 3 * c + 2, m[2]);
     }
 }
 
 // ---- conjugate gradients preconditioned by the factor (M = L L^T in the
 // factor's precision, FP64 vectors), all right-hand sides at once; per-column
 // scalars live on the device.
-__device__ inline double warp_sum(double v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 
 // Q = A P and pq[c] += P(:,c) . Q(:,c)
-__global__ void k_spmv_dot(const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
-                           const double *__restrict__ val, const double *__restrict__ P, double *__restrict__ Q,
-                           int64_t n, double *__restrict__ pq) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_spmv_dot(const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
+                                                  const double *__restrict__ val, const double *__restrict__ P,
+                                                  double *__restrict__ Q, int64_t n, double *__restrict__ pq) {
     const int c = blockIdx.y;
-    double d = 0.0;
-    if (i < n) {
-        const double *p = P + (int64_t)c * n;
+    const double *p = P + (int64_t)c * n;
+    double d[1] = {0.0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         double s = 0.0;
         for (int64_t e = ptr[i]; e < ptr[i + 1]; e++) s += val[e] * p[col[e]];
         Q[(int64_t)c * n + i] = s;
-        d = p[i] * s;
+        d[0] += p[i] * s;
     }
-    d = warp_sum(d);
-    if ((threadIdx.x & 31) == 0) atomicAdd(pq + c, d);
+    block_reduce<1, false>(d);
+    if (threadIdx.x == 0) atomicAdd(pq + c, d[0]);
 }
 
 // out[c] += X(:,c) . Y(:,c)
-__global__ void k_dot(const double *__restrict__ X, const double *__restrict__ Y, int64_t n, double *__restrict__ out) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_dot(const double *__restrict__ X, const double *__restrict__ Y, int64_t n,
+                                             double *__restrict__ out) {
     const int c = blockIdx.y;
-    double d = i < n ? X[(int64_t)c * n + i] * Y[(int64_t)c * n + i] : 0.0;
-    d = warp_sum(d);
-    if ((threadIdx.x & 31) == 0) atomicAdd(out + c, d);
+    double d[1] = {0.0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        d[0] += X[(int64_t)c * n + i] * Y[(int64_t)c * n + i];
+    block_reduce<1, false>(d);
+    if (threadIdx.x == 0) atomicAdd(out + c, d[0]);
 }
 
 // alpha = rz / pq; x += alpha p; r -= alpha q; maxima of |r|, |x|, |b| for eta
-__global__ void k_cg_step(double *__restrict__ X, double *__restrict__ R, const double *__restrict__ P,
-                          const double *__restrict__ Q, const double *__restrict__ B, const double *__restrict__ rz,
-                          const double *__restrict__ pq, int64_t n, double *__restrict__ red) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_cg_step(double *__restrict__ X, double *__restrict__ R,
+                                                 const double *__restrict__ P, const double *__restrict__ Q,
+                                                 const double *__restrict__ B, const double *__restrict__ rz,
+                                                 const double *__restrict__ pq, int64_t n, double *__restrict__ red) {
     const int c = blockIdx.y;
-    double m0 = 0.0, m1 = 0.0, m2 = 0.0;
-    if (i < n) {
-        const double a = pq[c] != 0.0 ? rz[c] / pq[c] : 0.0;
+    const double a = pq[c] != 0.0 ? rz[c] / pq[c] : 0.0;
+    double m[3] = {0.0, 0.0, 0.0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t g = (int64_t)c * n + i;
         const double x = X[g] + a * P[g], r = R[g] - a * Q[g];
         X[g] = x;
         R[g] = r;
-        m0 = fabs(r);
-        m1 = fabs(x);
-        m2 = fabs(B[g]);
+        m[0] = nan_max(m[0], fabs(r));
+        m[1] = nan_max(m[1], fabs(x));
+        m[2] = nan_max(m[2], fabs(B[g]));
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        m0 = nan_max(m0, __shfl_xor_sync(0xffffffffu, m0, o));
-        m1 = nan_max(m1, __shfl_xor_sync(0xffffffffu, m1, o));
-        m2 = nan_max(m2, __shfl_xor_sync(0xffffffffu, m2, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomic_max_nonneg(red + 3 * c, m0);
-        atomic_max_nonneg(red + 3 * c + 1, m1);
-        atomic_max_nonneg(red + 3 * c + 2, m2);
+    block_reduce<3, true>(m);
+    if (threadIdx.x == 0) {
+        atomic_max_nonneg(red + 3 * c, m[0]);
+        atomic_max_nonneg(red + 3 * c + 1, m[1]);
+        atomic_max_nonneg(red + 3 * c + 2, m[2]);
     }
 }
 
 // p = z + (rz_new / rz_old) p  (p = z when rz_old is 0)
-__global__ void k_cg_dir(double *__restrict__ P, const double *__restrict__ Z, const double *__restrict__ rz_new,
-                         const double *__restrict__ rz_old, int64_t n) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) k_cg_dir(double *__restrict__ P, const double *__restrict__ Z,
+                                                const double *__restrict__ rz_new, const double *__restrict__ rz_old,
+                                                int64_t n) {
     const int c = blockIdx.y;
-    if (i >= n) return;
     const double b = rz_old[c] != 0.0 ? rz_new[c] / rz_old[c] : 0.0;
-    const int64_t g = (int64_t)c * n + i;
-    P[g] = Z[g] + b * P[g];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = (int64_t)c * n + i;
+        P[g] = Z[g] + b * P[g];
+    }
+}
+
+// grid of the column-wise vector kernels: about eight CTAs of 256 threads per
+// SM over all columns, at most one CTA per 256 rows of a column
+dim3 vec_grid(const sc_numeric *h, int64_t n, int64_t ncols) {
+    const int64_t per_col = std::max<int64_t>(1, (int64_t)h->num_sms * 8 / std::max<int64_t>(1, ncols));
+    return dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, per_col)), (unsigned)ncols);
 }
 
 template <typename T>
@@ -967,8 +1044,7 @@ int tri_solve_any(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, dou
 int enqueue_residual(sc_numeric *h, int64_t nrhs, cudaStream_t st, int &launches) {
     const int64_t n = h->sym->n;
     SC_CUDA(cudaMemsetAsync(h->d_red, 0, 3 * nrhs * sizeof(double), st));
-    dim3 g((unsigned)((n + 255) / 256), (unsigned)nrhs);
-    k_residual<<<g, 256, 0, st>>>(h->d_csr_ptr, h->d_csr_col, h->d_csr_val, h->d_x, h->d_b, h->d_r, n, (int)nrhs,
+    k_residual<<<vec_grid(h, n, nrhs), 256, 0, st>>>(h->d_csr_ptr, h->d_csr_col, h->d_csr_val, h->d_x, h->d_b, h->d_r, n, (int)nrhs,
                                   h->d_red);
     launches++;
     return SC_OK;
@@ -1091,7 +1167,7 @@ int pcg(sc_numeric *h, int64_t nrhs, cudaStream_t st, double tol, int maxit, dou
         if (cudaMalloc((void **)&h->d_cgs, 3 * nrhs * sizeof(double)) != cudaSuccess) return SC_ERR_OOM;
         h->cg_cap = nrhs;
     }
-    const dim3 g((unsigned)((n + 255) / 256), (unsigned)nrhs);
+    const dim3 g = vec_grid(h, n, nrhs);
     double *rz = h->d_cgs, *rz2 = h->d_cgs + nrhs, *pq = h->d_cgs + 2 * nrhs;
     int rc;
     // z = M^-1 r, p = z, rz = r . z
@@ -1181,7 +1257,7 @@ int numeric_solve(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, dou
     int64_t nnzc = (int64_t)s->csr_col.size();
     k_gather_vals<<<(unsigned)((nnzc + 255) / 256), 256, 0, st>>>(h->d_csr_val, h->d_values, h->d_csr_map, nnzc);
     SC_CUDA(cudaMemsetAsync(h->d_red + 4095, 0, sizeof(double), st));
-    k_anorm<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(h->d_csr_ptr, h->d_csr_val, n, h->d_red + 4095);
+    k_anorm<<<vec_grid(h, n, 1), 256, 0, st>>>(h->d_csr_ptr, h->d_csr_val, n, h->d_red + 4095);
     SC_CUDA(cudaMemcpyAsync(&h->anorm, h->d_red + 4095, sizeof(double), cudaMemcpyDeviceToHost, st));
     SC_CUDA(cudaMemsetAsync(h->d_serr, 0, sizeof(int32_t), st));
     int launches = 2;

@@ -55,8 +55,10 @@ def test_many_right_hand_sides(prec, nrhs):
     the five register-blocking variants; 70 and 130 make two and three blocks
     (the last one ragged: 6 and 2), each with freshly zeroed counters; counts
     that are not multiples of 4 take the scalar atomic adds. X is compared
-    with the oracle's solve and eta <= 1e-14 (FP32: after refinement)."""
-    A = inputs.workload(2, 0.25)[0]
+    with the oracle's solve and eta <= 1e-14 (FP32: after refinement; the
+    7-point matrix with a diagonal shift of 1e-2, whose condition number lets
+    classical refinement of an FP32 factor converge)."""
+    A = inputs.diffusion_3d_7pt(12, 12, 12, seed=12, shift=1e-2)
     sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid)
     num = sym.factor(A.values, precision=prec)
     assert num.rc == 0
