@@ -80,58 +80,34 @@ __device__ __forceinline__ void stage_block(T (*dst)[kMaxChunk + 1], const T *__
 }
 
 // Loads rows x nb values of a row-major vector block (row r at src + row(r) * nb,
-// read through L2: other CTAs wrote them) into dst[r][0..nb) (row stride ldv),
-// rows <= 64, nb <= 64, 256 threads: a fixed trip count per thread with every
-// load in flight before the stores (16-byte vectors when nb allows).
+// read through L2: other CTAs wrote them) into dst[r][0..nb) (row stride ldv).
+// Rows of a whole number of 16-byte pieces go through cp.async.cg (L2 only,
+// every copy in flight at once, no registers); each thread waits for its own
+// copies and the caller's __syncthreads() makes them visible to the CTA. Other
+// widths are loaded directly.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void stage_rhs_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 template <typename T, typename RowOf>
 __device__ __forceinline__ void stage_rhs(T *__restrict__ dst, int ldv, const T *src, int nb, int rows,
                                           RowOf row_of) {
-    if constexpr (sizeof(T) == 4) {
-        if ((nb & 3) == 0) {  // float4: at most 64 x 64 / 4 / 256 = 4 per thread
-            const int nv = nb >> 2, total = rows * nv;
-            float4 tmp[4];
-#pragma unroll
-            for (int it = 0; it < 4; it++) {
-                const int idx = threadIdx.x + it * 256;
-                if (idx < total)
-                    tmp[it] = __ldcg(reinterpret_cast<const float4 *>(src + (int64_t)row_of(idx / nv) * nb) + idx % nv);
-            }
-#pragma unroll
-            for (int it = 0; it < 4; it++) {
-                const int idx = threadIdx.x + it * 256;
-                if (idx < total) *reinterpret_cast<float4 *>(dst + (idx / nv) * ldv + 4 * (idx % nv)) = tmp[it];
-            }
-            return;
+    if ((nb * (int)sizeof(T)) % 16 == 0) {
+        const int per_row = nb * (int)sizeof(T) / 16, total = rows * per_row;
+        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            const int r = idx / per_row, q = idx % per_row;
+            cp_async16(reinterpret_cast<unsigned char *>(dst + r * ldv) + 16 * q,
+                       reinterpret_cast<const unsigned char *>(src + (int64_t)row_of(r) * nb) + 16 * q);
         }
-    } else {
-        if ((nb & 1) == 0) {  // double2: at most 8 per thread
-            const int nv = nb >> 1, total = rows * nv;
-            double2 tmp[8];
-#pragma unroll
-            for (int it = 0; it < 8; it++) {
-                const int idx = threadIdx.x + it * 256;
-                if (idx < total)
-                    tmp[it] = __ldcg(reinterpret_cast<const double2 *>(src + (int64_t)row_of(idx / nv) * nb) + idx % nv);
-            }
-#pragma unroll
-            for (int it = 0; it < 8; it++) {
-                const int idx = threadIdx.x + it * 256;
-                if (idx < total) *reinterpret_cast<double2 *>(dst + (idx / nv) * ldv + 2 * (idx % nv)) = tmp[it];
-            }
-            return;
-        }
+        stage_rhs_wait();
+        return;
     }
-    const int total = rows * nb;  // scalar: at most 16 per thread
-    T tmp[16];
-#pragma unroll
-    for (int it = 0; it < 16; it++) {
-        const int idx = threadIdx.x + it * 256;
-        if (idx < total) tmp[it] = __ldcg(src + (int64_t)row_of(idx / nb) * nb + idx % nb);
-    }
-#pragma unroll
-    for (int it = 0; it < 16; it++) {
-        const int idx = threadIdx.x + it * 256;
-        if (idx < total) dst[(idx / nb) * ldv + idx % nb] = tmp[it];
+    for (int idx = threadIdx.x; idx < rows * nb; idx += blockDim.x) {
+        const int r = idx / nb, c = idx % nb;
+        dst[r * ldv + c] = __ldcg(src + (int64_t)row_of(r) * nb + c);
     }
 }
 
@@ -519,10 +495,6 @@ __global__ void __launch_bounds__(256) k_fwd(const T *__restrict__ lnz, const Ch
                 }
             }
             __syncthreads();
-            if (threadIdx.x == 0) {  // release y_c to the chunk's other tiles
-                __threadfence();
-                atomicExch(ready + (int64_t)tl.chunk * kSyncStride, 1);
-            }
         } else {
             if (threadIdx.x == 0) s_ok = wait_flag(ready + (int64_t)tl.chunk * kSyncStride, 1, err, spin_limit, 7);
             __syncthreads();
@@ -539,10 +511,14 @@ __global__ void __launch_bounds__(256) k_fwd(const T *__restrict__ lnz, const Ch
                 add_rhs<T, RPT>(x + (int64_t)glbind[ch.gl + tl.r0 + i] * nb + r0, o, T(-1), r0, nb);
             }
         }
-        // release: the barrier orders every thread's updates before thread 0's fence
+        // release: the barrier orders every thread's updates (and the first tile's
+        // y_c) before thread 0's fence; the first tile publishes y_c only now, so
+        // its own rows -- the next chunk's, the one contribution on the chain --
+        // are updated before the chunk's other tiles compete for the SMs
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
+            if (first) atomicExch(ready + (int64_t)tl.chunk * kSyncStride, 1);
             for (int p = dep_ptr[t]; p < dep_ptr[t + 1]; p++) atomicAdd(arrive + (int64_t)dep[p] * kSyncStride, 1);
         }
     }
@@ -550,9 +526,12 @@ __global__ void __launch_bounds__(256) k_fwd(const T *__restrict__ lnz, const Ch
 
 // Backward sweep: one persistent launch over all tiles in reverse level order,
 // every unit all right-hand sides of one block. A tile stages its rows of L,
-// waits until z is final in every chunk its rows fall in, and adds
-// L_{rows,c}^T z_rows into acc_c; the chunk's last tile to finish solves
-// z_c = L_cc^{-T} (y_c - acc_c) and marks the chunk done.
+// waits until z is final in every chunk its rows fall in, and forms
+// L_{rows,c}^T z_rows. For a wide chunk, every tile but the first adds it into
+// acc_c and counts itself; the first tile (taken last: reverse order) keeps its
+// own part, waits for the count, solves z_c = L_cc^{-T} (y_c - acc_c - own)
+// and marks the chunk done. Narrow chunks' warp tiles add and count, and the
+// last to finish solves.
 template <typename T, int RPT>
 __global__ void __launch_bounds__(256) k_bwd(const T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
                                              const TrsmTile *__restrict__ tiles, const SolveUnit *__restrict__ units,
@@ -568,7 +547,7 @@ __global__ void __launch_bounds__(256) k_bwd(const T *__restrict__ lnz, const Ch
     SweepSmem<T> sm(smem_bwd, ldv);
     __shared__ T rinv[kMaxChunk];
     __shared__ int32_t grow[kSolveRows];
-    __shared__ int s_t, s_ok, s_last;
+    __shared__ int s_t, s_ok;
     const int nblk = (nrhs + kRhsBlk - 1) / kRhsBlk;
     for (;;) {
         const int tr = grab_tile(work, total, err, &s_t);
@@ -596,7 +575,19 @@ __global__ void __launch_bounds__(256) k_bwd(const T *__restrict__ lnz, const Ch
         const TrsmTile tl = tiles[t];
         const ChunkDev ch = chunks[tl.chunk];
         const int w = ch.w;
+        // the chunk's first tile (rows just below the chunk) is taken after its other
+        // tiles (reverse order) and solves for z_c; it stages the diagonal block
+        // before it waits and keeps its own contribution in registers
+        const bool first = tl.r0 == ch.c0 + w;
         const int rows = max(0, min(kSolveRows, ch.m - tl.r0));
+        const int k = threadIdx.x % kMaxChunk, r0 = (threadIdx.x / kMaxChunk) * RPT;
+        T o[RPT];
+#pragma unroll
+        for (int j = 0; j < RPT; j++) o[j] = T(0);
+        if (first) {
+            if constexpr (sizeof(T) == 4) stage_block(sm.l, (const T *)(inv + ch.inv), w, w, w);
+            else load_diag(sm.l, rinv, lnz, ch, false);
+        }
         if (rows > 0) {
             if (threadIdx.x < rows) grow[threadIdx.x] = glbind[ch.gl + tl.r0 + threadIdx.x];
             stage_block(sm.lr, lnz + ch.off + (int64_t)tl.r0 * ch.ld + ch.c0, ch.ld, rows, w);
@@ -610,48 +601,53 @@ __global__ void __launch_bounds__(256) k_bwd(const T *__restrict__ lnz, const Ch
             if (!s_ok) break;
             stage_rhs(sm.v, ldv, (const T *)z, nb, rows, [&](int r) { return grow[r]; });
             __syncthreads();
-            // acc_c += L_{rows,c}^T z_rows
-            const int k = threadIdx.x % kMaxChunk, r0 = (threadIdx.x / kMaxChunk) * RPT;
+            // this tile's part of L_{S,c}^T z_S
             if (k < w && r0 < nb) {
-                T o[RPT];
                 rhs_product<T, RPT, true>(sm.lr, sm.v, ldv, k, r0, rows, o);
-                add_rhs<T, RPT>(acc + (int64_t)(ch.col0 + k) * nb + r0, o, T(1), r0, nb);
+                if (!first) add_rhs<T, RPT>(acc + (int64_t)(ch.col0 + k) * nb + r0, o, T(1), r0, nb);
             }
         }
+        if (!first) {
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();  // release this tile's contributions
+                atomicAdd(cnt + (int64_t)tl.chunk * kSyncStride, 1);
+            }
+            continue;
+        }
+        // the chunk's other tiles have added theirs into acc_c
+        if (threadIdx.x == 0)
+            s_ok = ntiles[tl.chunk] <= 1 ||
+                   wait_flag(cnt + (int64_t)tl.chunk * kSyncStride, ntiles[tl.chunk] - 1, err, spin_limit, 8);
         __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();  // release this tile's contributions
-            s_last = (atomicAdd(cnt + (int64_t)tl.chunk * kSyncStride, 1) == ntiles[tl.chunk] - 1);
-            if (s_last) __threadfence();  // acquire the other tiles' contributions
+        if (!s_ok) break;
+        // xin = y_c - acc_c - (own contribution)
+        stage_rhs(sm.xin, ldv, y, nb, w, [&](int r) { return ch.col0 + r; });
+        stage_rhs(sm.v, ldv, (const T *)acc, nb, w, [&](int r) { return ch.col0 + r; });
+        __syncthreads();
+        if (k < w && r0 < nb) {
+#pragma unroll
+            for (int j = 0; j < RPT; j++)
+                if (r0 + j < nb) sm.xin[k * ldv + r0 + j] -= sm.v[k * ldv + r0 + j] + o[j];
         }
         __syncthreads();
-        if (!s_last) continue;
         if constexpr (sizeof(T) == 4) {
             // z_c = inv(L_cc)^T (y_c - acc_c) with the block's stored inverse
-            stage_block(sm.l, (const T *)(inv + ch.inv), w, w, w);
-            stage_rhs(sm.xin, ldv, y, nb, w, [&](int r) { return ch.col0 + r; });
-            stage_rhs(sm.v, ldv, (const T *)acc, nb, w, [&](int r) { return ch.col0 + r; });
-            __syncthreads();
-            for (int idx = threadIdx.x; idx < w * ldv; idx += blockDim.x) sm.xin[idx] -= sm.v[idx];
-            __syncthreads();
-            const int k = threadIdx.x % kMaxChunk, r0 = (threadIdx.x / kMaxChunk) * RPT;
             if (k < w && r0 < nb) {
-                T o[RPT];
-                rhs_product<T, RPT, true>(sm.l, sm.xin, ldv, k, r0, w, o);
+                T zo[RPT];
+                rhs_product<T, RPT, true>(sm.l, sm.xin, ldv, k, r0, w, zo);
 #pragma unroll
                 for (int j = 0; j < RPT; j++)
-                    if (r0 + j < nb) z[(int64_t)(ch.col0 + k) * nb + r0 + j] = o[j];
+                    if (r0 + j < nb) z[(int64_t)(ch.col0 + k) * nb + r0 + j] = zo[j];
             }
         } else {
-            load_diag(sm.l, rinv, lnz, ch, false);
             const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
             for (int r = warp; r < nb; r += blockDim.x / 32) {
-                const int64_t g0 = (int64_t)(ch.col0 + lane) * nb + r, g1 = (int64_t)(ch.col0 + lane + 32) * nb + r;
-                T u0 = lane < w ? y[g0] - __ldcg(acc + g0) : T(0);
-                T u1 = lane + 32 < w ? y[g1] - __ldcg(acc + g1) : T(0);
+                T u0 = lane < w ? sm.xin[lane * ldv + r] : T(0);
+                T u1 = lane + 32 < w ? sm.xin[(lane + 32) * ldv + r] : T(0);
                 warp_upper_solve(sm.l, rinv, w, u0, u1);
-                if (lane < w) z[g0] = u0;
-                if (lane + 32 < w) z[g1] = u1;
+                if (lane < w) z[(int64_t)(ch.col0 + lane) * nb + r] = u0;
+                if (lane + 32 < w) z[(int64_t)(ch.col0 + lane + 32) * nb + r] = u1;
             }
         }
         __syncthreads();
