@@ -185,11 +185,10 @@ __device__ void warp_upper_solve(const T (*m)[kMaxChunk + 1], const T *rinv, int
 // a[i][k] (or a[k][i] when kTrans) and b of row stride ldb. The 64 threads of
 // one group read a at consecutive banks and b as broadcast 16-byte words (FP32,
 // RPT a multiple of 4) or 16-byte pairs (FP64, RPT even).
+// rhs_product_acc adds the product into o; rhs_product overwrites it.
 template <typename T, int RPT, bool kTrans>
-__device__ __forceinline__ void rhs_product(const T (*a)[kMaxChunk + 1], const T *__restrict__ b, int ldb, int i,
-                                            int r0, int K, T (&o)[RPT]) {
-#pragma unroll
-    for (int j = 0; j < RPT; j++) o[j] = T(0);
+__device__ __forceinline__ void rhs_product_acc(const T (*a)[kMaxChunk + 1], const T *__restrict__ b, int ldb, int i,
+                                                int r0, int K, T (&o)[RPT]) {
 #pragma unroll 4
     for (int k = 0; k < K; k++) {
         const T av = kTrans ? a[k][i] : a[i][k];
@@ -215,6 +214,14 @@ __device__ __forceinline__ void rhs_product(const T (*a)[kMaxChunk + 1], const T
             for (int j = 0; j < RPT; j++) o[j] += av * bk[j];
         }
     }
+}
+
+template <typename T, int RPT, bool kTrans>
+__device__ __forceinline__ void rhs_product(const T (*a)[kMaxChunk + 1], const T *__restrict__ b, int ldb, int i,
+                                            int r0, int K, T (&o)[RPT]) {
+#pragma unroll
+    for (int j = 0; j < RPT; j++) o[j] = T(0);
+    rhs_product_acc<T, RPT, kTrans>(a, b, ldb, i, r0, K, o);
 }
 
 // dst[0..RPT) += sign * o over the valid right-hand sides r0 + j < nb, by atomic
@@ -412,7 +419,7 @@ struct SweepSmem {
 // its rows fall in. A tile only waits for tiles taken earlier (lower levels,
 // or its own chunk's first tile), so the sweep needs no co-residency.
 template <typename T, int RPT>
-__global__ void __launch_bounds__(256) k_fwd(const T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_fwd(const T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
                                              const TrsmTile *__restrict__ tiles, const SolveUnit *__restrict__ units,
                                              int total, const int32_t *__restrict__ dep_ptr,
                                              const int32_t *__restrict__ dep, const int32_t *__restrict__ need,
@@ -446,6 +453,44 @@ __global__ void __launch_bounds__(256) k_fwd(const T *__restrict__ lnz, const Ch
                               sm.v + wp * kSmallW * ldv, ldv);
             }
             __syncthreads();
+            continue;
+        }
+        if (su.cnt < 0) {  // further tiles of one wide chunk: y_c staged once, tiles one after another
+            const int g = -su.cnt;
+            const ChunkDev ch = chunks[tiles[su.t0].chunk];
+            const int w = ch.w;
+            const int c = tiles[su.t0].chunk;
+            {
+                const TrsmTile tl = tiles[su.t0];
+                stage_block(sm.lr, lnz + ch.off + (int64_t)tl.r0 * ch.ld + ch.c0, ch.ld,
+                            max(0, min(kSolveRows, ch.m - tl.r0)), w);
+            }
+            if (threadIdx.x == 0) s_ok = wait_flag(ready + (int64_t)c * kSyncStride, 1, err, spin_limit, 7);
+            __syncthreads();
+            if (!s_ok) break;
+            stage_rhs(sm.v, ldv, (const T *)y, nb, w, [&](int r) { return ch.col0 + r; });
+            __syncthreads();
+            const int i = threadIdx.x % kSolveRows, r0 = (threadIdx.x / kSolveRows) * RPT;
+            for (int q = 0; q < g; q++) {
+                const TrsmTile tl = tiles[su.t0 + q];
+                const int rows = max(0, min(kSolveRows, ch.m - tl.r0));
+                if (q > 0) {
+                    __syncthreads();  // the previous tile's rows of L are no longer read
+                    stage_block(sm.lr, lnz + ch.off + (int64_t)tl.r0 * ch.ld + ch.c0, ch.ld, rows, w);
+                    __syncthreads();
+                }
+                if (i < rows && r0 < nb) {
+                    T o[RPT];
+                    rhs_product<T, RPT, false>(sm.lr, sm.v, ldv, i, r0, w, o);
+                    add_rhs<T, RPT>(x + (int64_t)glbind[ch.gl + tl.r0 + i] * nb + r0, o, T(-1), r0, nb);
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                for (int p = dep_ptr[su.t0]; p < dep_ptr[su.t0 + g]; p++)
+                    atomicAdd(arrive + (int64_t)dep[p] * kSyncStride, 1);
+            }
             continue;
         }
         const int t = su.t0;
@@ -533,7 +578,7 @@ __global__ void __launch_bounds__(256) k_fwd(const T *__restrict__ lnz, const Ch
 // and marks the chunk done. Narrow chunks' warp tiles add and count, and the
 // last to finish solves.
 template <typename T, int RPT>
-__global__ void __launch_bounds__(256) k_bwd(const T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_bwd(const T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
                                              const TrsmTile *__restrict__ tiles, const SolveUnit *__restrict__ units,
                                              int total, const int32_t *__restrict__ dep_ptr,
                                              const int32_t *__restrict__ dep, const int32_t *__restrict__ ntiles,
@@ -569,6 +614,42 @@ __global__ void __launch_bounds__(256) k_bwd(const T *__restrict__ lnz, const Ch
                               spin_limit, sm.v + wp * kSmallW * ldv, ldv);
             }
             __syncthreads();
+            continue;
+        }
+        if (su.cnt < 0) {  // further tiles of one wide chunk: their parts summed in registers
+            const int g = -su.cnt;
+            const int c = tiles[su.t0].chunk;
+            const ChunkDev ch = chunks[c];
+            const int w = ch.w;
+            if (threadIdx.x == 0) {
+                bool ok = true;
+                for (int p = dep_ptr[su.t0]; p < dep_ptr[su.t0 + g] && ok; p++)
+                    ok = wait_flag(done + (int64_t)dep[p] * kSyncStride, 1, err, spin_limit, 6);
+                s_ok = ok;
+            }
+            __syncthreads();
+            if (!s_ok) break;
+            const int k = threadIdx.x % kMaxChunk, r0 = (threadIdx.x / kMaxChunk) * RPT;
+            T o[RPT];
+#pragma unroll
+            for (int j = 0; j < RPT; j++) o[j] = T(0);
+            for (int q = 0; q < g; q++) {
+                const TrsmTile tl = tiles[su.t0 + q];
+                const int rows = max(0, min(kSolveRows, ch.m - tl.r0));
+                if (q > 0) __syncthreads();  // the previous tile's L rows and z rows are no longer read
+                if (threadIdx.x < rows) grow[threadIdx.x] = glbind[ch.gl + tl.r0 + threadIdx.x];
+                stage_block(sm.lr, lnz + ch.off + (int64_t)tl.r0 * ch.ld + ch.c0, ch.ld, rows, w);
+                __syncthreads();
+                stage_rhs(sm.v, ldv, (const T *)z, nb, rows, [&](int r) { return grow[r]; });
+                __syncthreads();
+                if (k < w && r0 < nb) rhs_product_acc<T, RPT, true>(sm.lr, sm.v, ldv, k, r0, rows, o);
+            }
+            if (k < w && r0 < nb) add_rhs<T, RPT>(acc + (int64_t)(ch.col0 + k) * nb + r0, o, T(1), r0, nb);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();  // release this unit's contributions
+                atomicAdd(cnt + (int64_t)c * kSyncStride, g);
+            }
             continue;
         }
         const int t = su.t0;
@@ -881,8 +962,10 @@ int ensure_solve(sc_numeric *h, int64_t nrhs) {
             }
             dep_ptr[t + 1] = (int32_t)dep.size();
         }
-        // grab units in level order: a tile of a chunk wider than kSmallW alone (one
-        // CTA), else up to eight consecutive narrow tiles of one level (a warp each)
+        // grab units in level order: the first tile of a chunk wider than kSmallW
+        // alone (one CTA; the chunk's step on the chain), its other tiles in runs of
+        // up to kSolveGroup (one CTA, one after another), else up to eight
+        // consecutive narrow tiles of one level (a warp each)
         std::vector<SolveUnit> units;
         {
             size_t t = 0;
@@ -890,9 +973,19 @@ int ensure_solve(sc_numeric *h, int64_t nrhs) {
                 size_t tend = t;
                 for (int32_t c : s->levels[lv].chunks) tend += ntiles[c];
                 while (t < tend) {
-                    if (s->chunks[tiles[t].chunk].w > kSmallW) {
-                        units.push_back(SolveUnit{(int32_t)t, 0});
-                        t++;
+                    const Chunk &cw = s->chunks[tiles[t].chunk];
+                    if (cw.w > kSmallW) {
+                        if (tiles[t].r0 == cw.c0 + cw.w) {
+                            units.push_back(SolveUnit{(int32_t)t, 0});
+                            t++;
+                            continue;
+                        }
+                        size_t e = t;
+                        while (e < tend && e - t < (size_t)kSolveGroup && tiles[e].chunk == tiles[t].chunk &&
+                               tiles[e].r0 != cw.c0 + cw.w)
+                            e++;
+                        units.push_back(SolveUnit{(int32_t)t, -(int32_t)(e - t)});
+                        t = e;
                         continue;
                     }
                     size_t e = t;
