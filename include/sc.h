@@ -104,6 +104,14 @@ enum sc_precision { SC_FP64 = 0, SC_FP32 = 1, SC_TF32 = 2, SC_TF32X3 = 3 };
  *                     wide, 64-column tiles below (>= 16) [96]
  *   thin_dim          products with min(m, n) <= thin_dim (1..8) go to the
  *                     warp-block kernel, -1 = none [8]
+ *   defer_width       trailing updates inside a supernode are deferred in
+ *                     levels: a chunk updates the rest of its 256-column macro
+ *                     panel (K = chunk width), a macro panel's last chunk the
+ *                     rest of its defer_width-column block (K = 256), and that
+ *                     block's last chunk every later column (K = defer_width).
+ *                     256..2^20, rounded down to a multiple of the macro panel;
+ *                     256 = two levels only [256]. Wider outer blocks mean fewer
+ *                     read-modify-write passes over each target with longer K.
  *   factor_ms         out (sc_tune): median factor time of this setting */
 typedef struct sc_tune_table {
     int32_t tile_min_entries;
@@ -113,7 +121,8 @@ typedef struct sc_tune_table {
     int32_t tc_min_k;
     int32_t tc_wide_n;
     int32_t thin_dim;
-    int32_t reserved[7];
+    int32_t defer_width;
+    int32_t reserved[6];
     double factor_ms;
 } sc_tune_table;
 

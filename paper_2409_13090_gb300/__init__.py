@@ -44,12 +44,13 @@ class Options(C.Structure):
                 ("reserved", C.c_int32 * 4)]
 
 
-TUNE_FIELDS = ["tile_min_entries", "tile_min_k", "loop_budget", "lookahead", "tc_min_k", "tc_wide_n", "thin_dim"]
+TUNE_FIELDS = ["tile_min_entries", "tile_min_k", "loop_budget", "lookahead", "tc_min_k", "tc_wide_n", "thin_dim",
+               "defer_width"]
 
 
 class TuneTable(C.Structure):
     """sc_tune_table: launch-plan settings (0 = library default)."""
-    _fields_ = [(f, C.c_int32) for f in TUNE_FIELDS] + [("reserved", C.c_int32 * 7), ("factor_ms", C.c_double)]
+    _fields_ = [(f, C.c_int32) for f in TUNE_FIELDS] + [("reserved", C.c_int32 * 6), ("factor_ms", C.c_double)]
 
     def to_dict(self) -> dict:
         d = {f: getattr(self, f) for f in TUNE_FIELDS}

@@ -8,9 +8,11 @@
 // Per level:
 //   - cdiv of each chunk: POTRF of its diagonal block, TRSM of the rows below;
 //   - for a chunk that is not the last of J: trailing updates inside J,
-//     deferred to macro panels of 256 columns (a chunk updates the rest of its
-//     macro panel, K = chunk width; the macro panel's last chunk updates all
-//     later columns at once, K = 256);
+//     deferred in levels (a chunk updates the rest of its 256-column macro
+//     panel, K = chunk width; a macro panel's last chunk updates the rest of its
+//     outer block, K = 256, and an outer block's last chunk every later column,
+//     K = the outer width; with the default outer width of 256 the macro panel's
+//     last chunk updates all later columns at once);
 //   - for J's last chunk (all of L_{*,J} is final):
 //       RLB (Alg. 5): for every ancestor P, every block B of J inside P:
 //         SYRK  L_{B,B}  -= L_{B,J} L_{B,J}^T
@@ -75,13 +77,14 @@ int build_schedule(sc_symbolic *s) {
             int32_t ldJ = s->lnz_ld[J];
             int64_t offJ = s->lnz_off[J];
             if (!ch.last) {
-                // trailing updates inside J, deferred to macro panels of Wm columns:
-                // a chunk updates the rest of its macro panel (K = chunk width); the
-                // macro panel's last chunk updates every column after the macro
-                // panel at once (K = macro width). Targets lie in Lnz(J) only.
+                // trailing updates inside J, deferred in levels of width W (the chunk),
+                // Wm (macro panel) and Wd (outer block, Wd = Wm: two levels only): the
+                // chunk ending at column e updates, with K = the width of the largest
+                // level block ending at e, the columns from e to the end of the next
+                // level's block (to nJ after an outer block). Every column before a
+                // chunk is then applied to it before its POTRF. Targets lie in Lnz(J).
                 const int32_t Wm = W * std::max(1, 256 / W);
-                const int32_t mstart = ch.c0 / Wm * Wm;
-                const int32_t mend = std::min(mstart + Wm, nJ);
+                const int32_t Wd = Wm * std::max(1, kn.defer_width / Wm);
                 const int32_t r0 = ch.c0 + ch.w;
                 // the update of the next chunk's columns is split off, so the next
                 // level's POTRF waits only for it (kTaskCrit, set below)
@@ -107,8 +110,9 @@ int build_schedule(sc_symbolic *s) {
                         L.tasks.push_back(t);
                     }
                 };
-                if (r0 < mend) lower_update(r0, mend, ch.c0, ch.w);
-                else lower_update(mend, nJ, mstart, mend - mstart);
+                if (r0 % Wm != 0) lower_update(r0, std::min(nJ, (r0 / Wm + 1) * Wm), ch.c0, ch.w);
+                else if (Wd > Wm && r0 % Wd != 0) lower_update(r0, std::min(nJ, (r0 / Wd + 1) * Wd), r0 - Wm, Wm);
+                else lower_update(r0, nJ, r0 - (Wd > Wm ? Wd : Wm), Wd > Wm ? Wd : Wm);
                 continue;
             }
             int64_t b0 = s->blk_ptr[J], b1 = s->blk_ptr[J + 1];

@@ -1,6 +1,8 @@
 // Launch-plan autotuner (sc_tune in include/sc.h). The level schedule and the
 // routing of Alg. 4/5's products follow from the structure; what is tuned are
-// the thresholds that cut those products into tiled tasks, device-loop items,
+// the depth of the trailing-update deferral inside supernodes (how many
+// read-modify-write passes each target takes, and with which K), the
+// thresholds that cut products into tiled tasks, device-loop items,
 // tensor-core tiles or warp blocks, and the lookahead split. Each setting is
 // timed by factoring the caller's matrix; coordinate descent over the fields
 // of sc_tune_table, one pass, keeping a value only when it is clearly faster.
@@ -26,7 +28,7 @@ bool same_knobs(const sc_tune_table &a, const sc_tune_table &b) {
     const sc::Knobs x = sc::knobs_of(a), y = sc::knobs_of(b);
     return x.tile_min_entries == y.tile_min_entries && x.tile_min_k == y.tile_min_k &&
            x.loop_budget == y.loop_budget && x.lookahead == y.lookahead && x.tc_min_k == y.tc_min_k &&
-           x.tc_wide_n == y.tc_wide_n && x.thin_dim == y.thin_dim;
+           x.tc_wide_n == y.tc_wide_n && x.thin_dim == y.thin_dim && x.defer_width == y.defer_width;
 }
 
 double median(std::vector<double> v) {
@@ -95,6 +97,7 @@ extern "C" int sc_tune(sc_symbolic *s, const double *values, int values_on_devic
     int rc = time_setting(s, cur, false, dv, precision, reps, st, &best_ms);
     count++;
     const std::vector<Field> fields = {
+        {&sc_tune_table::defer_width, {256, 512, 1024, 4096}, true, false, false},
         {&sc_tune_table::lookahead, {1, -1}, false, false, true},
         {&sc_tune_table::tile_min_entries, {512, 1024, 2048}, true, false, true},
         {&sc_tune_table::tile_min_k, {8, 16, 32}, true, false, true},

@@ -139,3 +139,25 @@ def test_tensor_core_tiles_at_chunk_widths_with_a_k_tail(case, chunk, prec, tol)
     X, info = num.solve(B)
     assert info["converged"], info
     assert oracle.backward_error(A, B, X).max() <= 1e-14
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("tf32", 2e-2), ("tf32x3", 1e-3)])
+@pytest.mark.parametrize("defer", [512, 1024])
+def test_deeper_trailing_update_deferral(defer, prec, tol):
+    """Outer deferral blocks of 512 and 1024 columns inside a 1300-column
+    supernode (a dense matrix): in-panel products with K = 256 and K = the
+    outer width, some of them critical (split along K in FP64), against the
+    oracle's L element by element and refinement to eta <= 1e-14."""
+    A = _dense(1300, 2)
+    sym = sc.Symbolic(A, ordering="natural", tune=dict(defer_width=defer))
+    assert sym.check_schedule()["ok"]
+    o = oracle.Oracle(A, None, pr=True)
+    assert o.factor() == 0
+    Lo = o.L_supernodal()
+    num = sym.factor(A.values, precision=prec)
+    assert num.rc == 0
+    err = np.abs(num.export_L() - Lo).max() / np.abs(Lo).max()
+    assert err <= tol, err
+    B = inputs.rhs(A.n, 2, 9)
+    X, info = num.solve(B)
+    assert oracle.backward_error(A, B, X).max() <= 1e-14

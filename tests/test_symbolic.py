@@ -266,8 +266,36 @@ def test_tune_table_changes_only_the_launch_plan():
     assert 0 < wtf["tc_tiles"] <= btf["tc_tiles"]
 
 
+def test_deferral_depth_changes_only_the_in_panel_products():
+    """A third level of trailing-update deferral (outer blocks of 1024 or 4096
+    columns) regroups the in-supernode products: the same flops in fewer
+    read-modify-write passes (each target column takes at most three updates of
+    K = chunk width, three of K = 256, and one of K = the outer width per outer
+    block), while every symbolic array stays bit-exact and the schedule check
+    passes. One dense supernode of 2100 columns shows it."""
+    A = _dense_spd(2100, 3)
+    o = oracle.Oracle(A, None, pr=True).symbolic()
+
+    def passes(defer):
+        """128-row tensor-core target tiles of the TF32 plan: one read-modify-write pass each"""
+        sym = sc.Symbolic(A, ordering="natural", tune=None if defer is None else dict(defer_width=defer))
+        assert sym.check_schedule()["ok"]
+        v = sym.view()
+        for k in KEYS:
+            assert np.array_equal(v[k], getattr(o, k)), (defer, k)
+        return sym.plan_stats("tf32")["tc_tiles"]
+
+    base = passes(None)
+    assert passes(256) == base
+    # an outer block boundary replaces the macro panels' updates of all later columns
+    assert passes(512) < base and passes(1024) < base
+    # an outer block wider than the supernode is the two-level schedule
+    assert passes(4096) == base
+
+
 @pytest.mark.parametrize("bad", [dict(lookahead=2), dict(tc_min_k=16), dict(tc_wide_n=8), dict(thin_dim=9),
-                                 dict(thin_dim=-2), dict(loop_budget=100), dict(tile_min_entries=-1)])
+                                 dict(thin_dim=-2), dict(loop_budget=100), dict(tile_min_entries=-1),
+                                 dict(defer_width=128), dict(defer_width=1 << 21)])
 def test_tune_table_ranges(bad):
     A = inputs.laplacian_2d(8, 8)
     with pytest.raises(sc.SCError) as e:
@@ -303,7 +331,8 @@ def test_schedule_check_on_workloads(variant, chunk, merge):
 
 def test_schedule_check_under_plan_settings_and_batches():
     A = inputs.diffusion_3d_7pt(12, 12, 12, seed=2)
-    for t in (dict(tile_min_entries=64, tile_min_k=1), dict(tile_min_entries=1 << 20, loop_budget=256)):
+    for t in (dict(tile_min_entries=64, tile_min_k=1), dict(tile_min_entries=1 << 20, loop_budget=256),
+              dict(defer_width=1024), dict(defer_width=4096, lookahead=-1)):
         chk = sc.Symbolic(A, ordering="grid_nd", grid=A.grid, tune=t).check_schedule()
         assert chk["ok"], (t, chk)
     mats, _ = inputs.workload(4, 0.06)
