@@ -224,23 +224,34 @@ __device__ __forceinline__ void rhs_product(const T (*a)[kMaxChunk + 1], const T
     rhs_product_acc<T, RPT, kTrans>(a, b, ldb, i, r0, K, o);
 }
 
-// dst[0..RPT) += sign * o over the valid right-hand sides r0 + j < nb, by atomic
-// adds (16-byte vector atomics where the four values are valid and aligned)
+// Reductions into global memory that return nothing (red): the issuing thread
+// does not wait for them; the fence before a release orders them.
+__device__ __forceinline__ void red_add(float *p, float a) {
+    asm volatile("red.relaxed.gpu.global.add.f32 [%0], %1;" ::"l"(p), "f"(a) : "memory");
+}
+__device__ __forceinline__ void red_add(double *p, double a) {
+    asm volatile("red.relaxed.gpu.global.add.f64 [%0], %1;" ::"l"(p), "d"(a) : "memory");
+}
+__device__ __forceinline__ void red_add4(float *p, float a, float b, float c, float d) {
+    asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+
+// dst[0..RPT) += sign * o over the valid right-hand sides r0 + j < nb, by
+// reductions (16-byte vector reductions where the four values are valid and aligned)
 template <typename T, int RPT>
 __device__ __forceinline__ void add_rhs(T *dst, const T (&o)[RPT], T sign, int r0, int nb) {
     if constexpr (sizeof(T) == 4 && RPT % 4 == 0) {
         if ((nb & 3) == 0) {
 #pragma unroll
             for (int j = 0; j < RPT; j += 4)
-                if (r0 + j < nb)
-                    atomicAdd(reinterpret_cast<float4 *>(dst + j),
-                              make_float4(sign * o[j], sign * o[j + 1], sign * o[j + 2], sign * o[j + 3]));
+                if (r0 + j < nb) red_add4(dst + j, sign * o[j], sign * o[j + 1], sign * o[j + 2], sign * o[j + 3]);
             return;
         }
     }
 #pragma unroll
     for (int j = 0; j < RPT; j++)
-        if (r0 + j < nb) atomicAdd(dst + j, sign * o[j]);
+        if (r0 + j < nb) red_add(dst + j, sign * o[j]);
 }
 
 // Bounded wait until *flag >= target (acquire at GPU scope). Gives up, setting
@@ -313,7 +324,7 @@ __device__ bool fwd_tile_warp(const T *__restrict__ lnz, const ChunkDev &ch, con
         const T *lr = lnz + ch.off + (int64_t)(tl.r0 + i) * ch.ld + ch.c0;
         T acc = T(0);
         for (int k = 0; k < w; k++) acc += lr[k] * vw[k * ldv + r];
-        atomicAdd(x + (int64_t)glbind[ch.gl + tl.r0 + i] * nb + r, -acc);
+        red_add(x + (int64_t)glbind[ch.gl + tl.r0 + i] * nb + r, -acc);
     }
     __syncwarp();
     if (lane == 0) {
@@ -348,7 +359,7 @@ __device__ bool bwd_tile_warp(const T *__restrict__ lnz, const ChunkDev &ch, con
             for (int i = 0; i < rows; i++)
                 sum += lnz[ch.off + (int64_t)(tl.r0 + i) * ch.ld + ch.c0 + k] *
                        __ldcg(z + (int64_t)glbind[ch.gl + tl.r0 + i] * nb + r);
-            atomicAdd(acc + (int64_t)(ch.col0 + k) * nb + r, sum);
+            red_add(acc + (int64_t)(ch.col0 + k) * nb + r, sum);
         }
     }
     __syncwarp();
@@ -419,7 +430,7 @@ struct SweepSmem {
 // its rows fall in. A tile only waits for tiles taken earlier (lower levels,
 // or its own chunk's first tile), so the sweep needs no co-residency.
 template <typename T, int RPT>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_fwd(const T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fwd(const T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
                                              const TrsmTile *__restrict__ tiles, const SolveUnit *__restrict__ units,
                                              int total, const int32_t *__restrict__ dep_ptr,
                                              const int32_t *__restrict__ dep, const int32_t *__restrict__ need,
@@ -472,10 +483,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_fwd(const T *__
             __syncthreads();
             const int i = threadIdx.x % kSolveRows, r0 = (threadIdx.x / kSolveRows) * RPT;
             for (int q = 0; q < g; q++) {
-                const TrsmTile tl = tiles[su.t0 + q];
+                const int tq = su.t0 + q;
+                const TrsmTile tl = tiles[tq];
                 const int rows = max(0, min(kSolveRows, ch.m - tl.r0));
                 if (q > 0) {
-                    __syncthreads();  // the previous tile's rows of L are no longer read
                     stage_block(sm.lr, lnz + ch.off + (int64_t)tl.r0 * ch.ld + ch.c0, ch.ld, rows, w);
                     __syncthreads();
                 }
@@ -484,12 +495,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_fwd(const T *__
                     rhs_product<T, RPT, false>(sm.lr, sm.v, ldv, i, r0, w, o);
                     add_rhs<T, RPT>(x + (int64_t)glbind[ch.gl + tl.r0 + i] * nb + r0, o, T(-1), r0, nb);
                 }
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                __threadfence();
-                for (int p = dep_ptr[su.t0]; p < dep_ptr[su.t0 + g]; p++)
-                    atomicAdd(arrive + (int64_t)dep[p] * kSyncStride, 1);
+                // each tile's arrivals go out as soon as its rows are updated: a later
+                // chunk's step must not wait for the rest of the unit
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    __threadfence();
+                    for (int p = dep_ptr[tq]; p < dep_ptr[tq + 1]; p++) atomicAdd(arrive + (int64_t)dep[p] * kSyncStride, 1);
+                }
             }
             continue;
         }
@@ -578,7 +590,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_fwd(const T *__
 // and marks the chunk done. Narrow chunks' warp tiles add and count, and the
 // last to finish solves.
 template <typename T, int RPT>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_bwd(const T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_bwd(const T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
                                              const TrsmTile *__restrict__ tiles, const SolveUnit *__restrict__ units,
                                              int total, const int32_t *__restrict__ dep_ptr,
                                              const int32_t *__restrict__ dep, const int32_t *__restrict__ ntiles,
