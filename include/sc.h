@@ -112,6 +112,11 @@ enum sc_precision { SC_FP64 = 0, SC_FP32 = 1, SC_TF32 = 2, SC_TF32X3 = 3 };
  *                     256..2^20, rounded down to a multiple of the macro panel;
  *                     256 = two levels only [256]. Wider outer blocks mean fewer
  *                     read-modify-write passes over each target with longer K.
+ *   fused             1 = every level of an FP64 / FP32 RLB factorization runs as
+ *                     one persistent launch (POTRF, TRSM, products, device loops
+ *                     and the previous level's lookahead products, ordered by
+ *                     device-side counters), -1 = one launch per kernel class
+ *                     (each class at its own occupancy) [-1]
  *   factor_ms         out (sc_tune): median factor time of this setting */
 typedef struct sc_tune_table {
     int32_t tile_min_entries;
@@ -122,7 +127,8 @@ typedef struct sc_tune_table {
     int32_t tc_wide_n;
     int32_t thin_dim;
     int32_t defer_width;
-    int32_t reserved[6];
+    int32_t fused;
+    int32_t reserved[5];
     double factor_ms;
 } sc_tune_table;
 
@@ -497,6 +503,17 @@ int sc_residual_eta_noalloc(int64_t n, const int64_t *row_ptr, const int32_t *co
  * Errors: -1 (h NULL), -2 (chunk < 0; a chunk beyond the last makes the next
  * sc_solve return -1). */
 int sc_test_stall_solve(sc_numeric *h, int64_t chunk);
+
+/* Test hook for the failure path of the per-level persistent kernel's bounded
+ * waits (fused plans; no counterpart in the paper). The next sc_refactor on h
+ * runs with the units that read chunk `chunk` (0-based, in the order of the
+ * level schedule) waiting for one more POTRF / TRSM completion than the chunk
+ * delivers: their waits give up after spin_limit polls, every other wait sees
+ * the error and stops, and sc_refactor returns SC_ERR_TIMEOUT. The target is
+ * restored afterwards, so later factorizations run normally. Nothing faults.
+ * Errors: -1 (h NULL), -2 (chunk < 0); the next factorization returns
+ * SC_ERR_UNSUPPORTED if h has no per-level kernel or chunk is out of range. */
+int sc_test_stall_factor(sc_numeric *h, int64_t chunk);
 
 /* Frees h and its device memory. NULL is accepted. */
 void sc_numeric_free(sc_numeric *h);

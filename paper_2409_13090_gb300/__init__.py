@@ -45,12 +45,12 @@ class Options(C.Structure):
 
 
 TUNE_FIELDS = ["tile_min_entries", "tile_min_k", "loop_budget", "lookahead", "tc_min_k", "tc_wide_n", "thin_dim",
-               "defer_width"]
+               "defer_width", "fused"]
 
 
 class TuneTable(C.Structure):
     """sc_tune_table: launch-plan settings (0 = library default)."""
-    _fields_ = [(f, C.c_int32) for f in TUNE_FIELDS] + [("reserved", C.c_int32 * 6), ("factor_ms", C.c_double)]
+    _fields_ = [(f, C.c_int32) for f in TUNE_FIELDS] + [("reserved", C.c_int32 * 5), ("factor_ms", C.c_double)]
 
     def to_dict(self) -> dict:
         d = {f: getattr(self, f) for f in TUNE_FIELDS}
@@ -127,6 +127,7 @@ def lib():
             "sc_probe_fma_peak": ([C.c_int, P, P], C.c_int),
             "sc_plan_stats": ([P, C.c_int, P, C.c_int], C.c_int),
             "sc_test_stall_solve": ([P, i64], C.c_int),
+            "sc_test_stall_factor": ([P, i64], C.c_int),
             "sc_factor_batch": ([C.c_int, P, P, C.c_int, C.c_int, P, C.POINTER(P), C.POINTER(P), P], C.c_int),
             "sc_tune": ([P, P, C.c_int, C.c_int, C.c_int, P, P, P], C.c_int),
             "sc_check_schedule": ([P, P, C.c_int], C.c_int),
@@ -495,6 +496,13 @@ class Numeric:
             raise SCError(rc, "sc_solve")
         return X, {"iterations": info.iterations, "converged": bool(info.converged), "eta_max": info.eta_max,
                    "eta": eta, "solve_ms": info.solve_ms, "rc": rc, "kernel_launches": info.kernel_launches}
+
+    def stall_next_factor(self, chunk: int):
+        """Test hook (sc_test_stall_factor): the next refactor's units that read
+        `chunk` wait for one completion too many; their bounded waits give up."""
+        rc = lib().sc_test_stall_factor(self._h, int(chunk))
+        if rc:
+            raise SCError(rc, "sc_test_stall_factor")
 
     def stall_next_solve(self, chunk: int):
         """Test hook (sc_test_stall_solve): the next solve's forward sweep waits at

@@ -233,6 +233,13 @@ int sc_test_stall_solve(sc_numeric *h, int64_t chunk) {
     return SC_OK;
 }
 
+int sc_test_stall_factor(sc_numeric *h, int64_t chunk) {
+    if (!h) return -1;
+    if (chunk < 0 || chunk > INT32_MAX) return -2;
+    h->stall_factor_chunk = (int32_t)chunk;
+    return SC_OK;
+}
+
 void sc_numeric_free(sc_numeric *h) { sc::numeric_free(h); }
 
 const char *sc_strerror(int code) {

@@ -91,4 +91,15 @@ struct BlkDev {
 
 constexpr int kLoopSmemBytes = 48 * 1024;
 
+// One unit of the per-level persistent kernel (k_level): a POTRF of a chunk, a
+// TRSM tile, a product tile, one or two thin units, up to eight small tasks, a
+// device-loop item or up to eight narrow loop items. idx indexes the list of
+// its kind (for small tasks and narrow loop items: the first of cnt entries).
+struct FlowUnit {
+    int32_t kind, idx, cnt, pad;
+};
+enum : int32_t { kFlowPotrf = 0, kFlowTrsm, kFlowGemm, kFlowThin, kFlowSmall, kFlowLoop, kFlowLoopW };
+// one counter word per 128-byte line in the per-chunk arrays of k_level
+constexpr int kFlowStride = 32;
+
 }  // namespace sc

@@ -81,6 +81,121 @@ __global__ void __launch_bounds__(256) k_inverse(const float *__restrict__ lnz, 
 }
 
 
+// ---- one persistent launch per level (SIMT precisions, RLB)
+// Bounded wait until *flag >= target (acquire at GPU scope); gives up, setting
+// *err, after spin_limit polls or once another CTA has given up.
+__device__ bool flow_wait(const int32_t *flag, int32_t target, int32_t *err, long long spin_limit, int code) {
+    for (long long i = 0; i < spin_limit; i++) {
+        int32_t v;
+        asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
+        if (v >= target) return true;
+        if (*(volatile int32_t *)err) return false;
+        if (i > 64) __nanosleep(64);
+    }
+    atomicCAS(err, 0, code);
+    return false;
+}
+
+template <typename T>
+struct LevelArgs {
+    T *lnz, *pool;
+    const ChunkDev *chunks;
+    const TrsmTile *trsm;
+    const GemmTile *gemm;
+    const Task *tasks;
+    const ThinUnit *thin;
+    const int32_t *small;
+    const LoopItem *loops;
+    const SnDev *sn;
+    const BlkDev *blk;
+    const int32_t *rbval;
+    const double *adiag;
+    int32_t *info, *low_pivots;
+    double tau;
+    const FlowUnit *units;
+    int32_t nunits;
+    int32_t *ctr;             // per chunk (kFlowStride apart): POTRF and TRSM units done
+    const int32_t *need;      // per chunk: 1 + its TRSM tiles
+    const int32_t *task_chunk;
+    const int32_t *sn_chunk;
+    int32_t *work;            // this launch's unit counter
+    int32_t *err;
+    long long spin_limit;
+};
+
+// All work of one level in one launch: CTAs take units in list order (POTRF of
+// the level's chunks, their TRSM tiles, the previous level's lookahead
+// products, this level's products, small tasks and device loops). A TRSM tile
+// waits for its chunk's POTRF; a product, small task or loop item waits until
+// the chunk it reads is factored (POTRF and every TRSM tile). Every wait is
+// for a unit earlier in the list, taken by a running CTA, so the launch needs
+// no co-residency; every wait is bounded (then *err is set and the CTAs stop).
+// Product writes are atomic: units of one launch may update the same target.
+template <typename T>
+__global__ void __launch_bounds__(256, 2) k_level(LevelArgs<T> a) {
+    __shared__ int s_u, s_ok;
+    for (;;) {
+        if (threadIdx.x == 0) s_u = *(volatile int32_t *)a.err ? a.nunits : atomicAdd(a.work, 1);
+        __syncthreads();
+        const int u = s_u;
+        if (u >= a.nunits) break;
+        const FlowUnit fu = a.units[u];
+        // dependencies, checked by thread 0
+        if (threadIdx.x == 0) {
+            bool ok = true;
+            auto src = [&](int32_t c) {
+                if (ok) ok = flow_wait(a.ctr + (int64_t)c * kFlowStride, a.need[c], a.err, a.spin_limit, 9);
+            };
+            switch (fu.kind) {
+                case kFlowTrsm:
+                    ok = flow_wait(a.ctr + (int64_t)a.trsm[fu.idx].chunk * kFlowStride, 1, a.err, a.spin_limit, 9);
+                    break;
+                case kFlowGemm: src(a.task_chunk[a.gemm[fu.idx].task]); break;
+                case kFlowThin:
+                    for (int q = 0; q < fu.cnt; q++) src(a.task_chunk[a.thin[fu.idx + q].task]);
+                    break;
+                case kFlowSmall:
+                    for (int q = 0; q < fu.cnt; q++) src(a.task_chunk[a.small[fu.idx + q]]);
+                    break;
+                case kFlowLoop: src(a.sn_chunk[a.loops[fu.idx].sn]); break;
+                case kFlowLoopW:
+                    for (int q = 0; q < fu.cnt; q++) src(a.sn_chunk[a.loops[fu.idx + q].sn]);
+                    break;
+                default: break;
+            }
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        switch (fu.kind) {
+            case kFlowPotrf:
+                potrf_chunk<T>(a.lnz, a.chunks, fu.idx, a.adiag, a.info, a.low_pivots, a.tau, nullptr, nullptr);
+                break;
+            case kFlowTrsm: trsm_tile<T>(a.lnz, a.chunks, a.trsm[fu.idx], nullptr, nullptr); break;
+            case kFlowGemm: gemm_tile<T, 64, 64, 16>(a.lnz, a.pool, a.tasks, a.gemm[fu.idx], true); break;
+            case kFlowThin: {
+                const int wq = threadIdx.x / 32 / kThinWarps;
+                if (wq < fu.cnt) thin_warp<T>(a.lnz, a.tasks, a.thin[fu.idx + wq], (threadIdx.x / 32) % kThinWarps);
+                break;
+            }
+            case kFlowSmall: small_tasks<T>(a.lnz, a.pool, a.tasks, a.small + fu.idx, fu.cnt, 0); break;
+            case kFlowLoop: loop_item<T>(a.lnz, a.loops[fu.idx], a.sn, a.blk, a.rbval); break;
+            case kFlowLoopW: loop_items_warp<T>(a.lnz, a.loops + fu.idx, fu.cnt, 0, a.sn, a.blk, a.rbval); break;
+            default: break;
+        }
+        if (fu.kind == kFlowPotrf || fu.kind == kFlowTrsm) {
+            // release: the barrier orders the CTA's stores before thread 0's fence
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                const int32_t c = fu.kind == kFlowPotrf ? fu.idx : a.trsm[fu.idx].chunk;
+                atomicAdd(a.ctr + (int64_t)c * kFlowStride, 1);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Optional per-kernel-class timing of one factorization (CUDA events around
 // every launch; only used outside graph capture).
 struct Prof {
@@ -124,6 +239,37 @@ int run_levels(sc_numeric *h, cudaStream_t st, Prof *prof = nullptr, cudaStream_
     E();
     launches += 2;
     const double tau = s->opt.pivot_tau;
+    if (h->fused && !prof) {
+        // one persistent launch per level, then the tail of lookahead products
+        const size_t nch = s->chunks.size(), nlev = h->plans.size();
+        SC_CUDA(cudaMemsetAsync(h->d_flow_ctr, 0, (nch * kFlowStride + nlev + 1) * sizeof(int32_t), st));
+        LevelArgs<T> a{lnz, pool, h->d_chunks, h->d_trsm, h->d_gemm, h->d_tasks, h->d_thin, h->d_small, h->d_loops,
+                       h->d_sn, h->d_blk, h->d_rbval, h->d_adiag, h->d_info, h->d_info + 1, tau, nullptr, 0,
+                       h->d_flow_ctr, h->d_flow_need, h->d_task_chunk, h->d_sn_chunk, nullptr, h->d_err,
+                       (long long)s->opt.spin_limit};
+        int32_t *work = h->d_flow_ctr + nch * kFlowStride;
+        for (size_t lv = 0; lv <= nlev; lv++) {
+            const int32_t off = lv < nlev ? h->plans[lv].flow_off : h->flow_tail_off;
+            const int32_t cnt = lv < nlev ? h->plans[lv].flow_cnt : h->flow_tail_cnt;
+            if (!cnt) continue;
+            a.units = h->d_flow + off;
+            a.nunits = cnt;
+            a.work = work + lv;
+            const int grid = std::max(1, std::min(cnt, 2 * h->num_sms));
+            k_level<T><<<grid, 256, kPotrfSmem, st>>>(a);
+            launches++;
+        }
+        if constexpr (sizeof(T) == 4) {
+            const int32_t nchk = (int32_t)s->chunks.size();
+            if (nchk) {
+                k_inverse<<<nchk, 256, kPotrfSmem, st>>>((const float *)lnz, h->d_chunks, h->d_potrf, (float *)h->d_inv);
+                launches++;
+            }
+        }
+        SC_CUDA(cudaGetLastError());
+        h->kernel_launches = launches;
+        return SC_OK;
+    }
     // tiled products of one dependency class on stream ps
     auto products = [&](const ProdLists &pl, cudaStream_t ps) -> int {
         if (pl.gemm_cnt) {
@@ -269,6 +415,8 @@ int set_smem_attrs() {
     SC_CUDA(cudaFuncSetAttribute(k_potrf<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPotrfSmem));
     SC_CUDA(cudaFuncSetAttribute(k_potrf<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPotrfSmem));
     SC_CUDA(cudaFuncSetAttribute(k_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, kPotrfSmem));
+    SC_CUDA(cudaFuncSetAttribute(k_level<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPotrfSmem));
+    SC_CUDA(cudaFuncSetAttribute(k_level<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPotrfSmem));
     if (!tc_gemm_init()) return SC_ERR_CUDA;
     done = true;
     return SC_OK;
@@ -288,7 +436,43 @@ struct Plan {
     std::vector<LevelPlan> levels;
     int64_t inv_size = 0;  // elements of the diagonal-block inverses
     double class_flops[kProfClasses] = {};
+    // fused plans: the units of every level's k_level launch, then the tail launch's
+    std::vector<FlowUnit> flow;
+    int32_t flow_tail_off = 0, flow_tail_cnt = 0;
 };
+
+// Units of the per-level launches (fused plans): per level its POTRFs, TRSM
+// tiles, the previous level's lookahead products (lookahead), its own products
+// (with the rest as well when there is no lookahead), small tasks in eights,
+// loop items, narrow loop items in eights; the last level's lookahead products
+// form a tail launch.
+void build_flow(Plan &P, bool lookahead) {
+    P.flow.clear();
+    auto products = [&](const ProdLists &pl) {
+        for (int32_t i = 0; i < pl.gemm_cnt; i++) P.flow.push_back(FlowUnit{kFlowGemm, pl.gemm_off + i, 1, 0});
+        for (int32_t i = 0; i < pl.thin_cnt; i += 2)
+            P.flow.push_back(FlowUnit{kFlowThin, pl.thin_off + i, std::min<int32_t>(2, pl.thin_cnt - i), 0});
+    };
+    const size_t nlev = P.levels.size();
+    for (size_t lv = 0; lv < nlev; lv++) {
+        LevelPlan &p = P.levels[lv];
+        p.flow_off = (int32_t)P.flow.size();
+        for (int32_t i = 0; i < p.potrf_cnt; i++) P.flow.push_back(FlowUnit{kFlowPotrf, P.potrf[p.potrf_off + i], 1, 0});
+        for (int32_t i = 0; i < p.trsm_cnt; i++) P.flow.push_back(FlowUnit{kFlowTrsm, p.trsm_off + i, 1, 0});
+        if (lookahead && lv > 0) products(P.levels[lv - 1].rest);
+        products(p.crit);
+        if (!lookahead) products(p.rest);
+        for (int32_t i = 0; i < p.small_cnt; i += 8)
+            P.flow.push_back(FlowUnit{kFlowSmall, p.small_off + i, std::min<int32_t>(8, p.small_cnt - i), 0});
+        for (int32_t i = 0; i < p.loop_cnt; i++) P.flow.push_back(FlowUnit{kFlowLoop, p.loop_off + i, 1, 0});
+        for (int32_t i = 0; i < p.loopw_cnt; i += 8)
+            P.flow.push_back(FlowUnit{kFlowLoopW, p.loopw_off + i, std::min<int32_t>(8, p.loopw_cnt - i), 0});
+        p.flow_cnt = (int32_t)P.flow.size() - p.flow_off;
+    }
+    P.flow_tail_off = (int32_t)P.flow.size();
+    if (lookahead && nlev) products(P.levels[nlev - 1].rest);
+    P.flow_tail_cnt = (int32_t)P.flow.size() - P.flow_tail_off;
+}
 
 // lookahead: split each level's tiled products into those that target chunks
 // of the next level (crit) and the rest (targets two or more levels up).
@@ -495,9 +679,32 @@ int numeric_create(sc_symbolic *s, int precision, sc_numeric **out) {
         if ((rc = upload(h->d_tmap_of_sn, tmap_of_sn, bytes))) return fail(rc);
     }
     Plan P;
-    // lookahead needs the captured graph's concurrent branches (RLB schedule)
-    h->lookahead = h->use_graph && s->opt.variant == SC_RLB && knobs_of(s->tune).lookahead;
+    // one persistent launch per level: SIMT precisions, RLB schedule
+    const Knobs kn = knobs_of(s->tune);
+    h->fused = kn.fused && s->opt.variant == SC_RLB && (precision == SC_FP64 || precision == SC_FP32);
+    // lookahead needs concurrent work: the captured graph's branches, or the fused launches
+    h->lookahead = (h->use_graph || h->fused) && s->opt.variant == SC_RLB && kn.lookahead;
     build_plan(s, precision, P, h->lookahead);
+    if (h->fused) {
+        build_flow(P, h->lookahead);
+        h->flow_tail_off = P.flow_tail_off;
+        h->flow_tail_cnt = P.flow_tail_cnt;
+        const size_t nch = s->chunks.size();
+        std::vector<int32_t> need(nch, 1), task_chunk(P.tasks.size()), sn_chunk(s->nsuper);
+        for (const TrsmTile &t : P.trsm) need[t.chunk]++;
+        for (size_t i = 0; i < P.tasks.size(); i++) {
+            const Task &t = P.tasks[i];
+            task_chunk[i] = s->chunk_of_col[s->sup_ptr[t.src] + t.kx0 + t.k - 1];
+        }
+        for (int64_t J = 0; J < s->nsuper; J++) sn_chunk[J] = s->chunk_of_col[s->sup_ptr[J + 1] - 1];
+        if ((rc = upload(h->d_flow, P.flow, bytes))) return fail(rc);
+        if ((rc = upload(h->d_flow_need, need, bytes))) return fail(rc);
+        if ((rc = upload(h->d_task_chunk, task_chunk, bytes))) return fail(rc);
+        if ((rc = upload(h->d_sn_chunk, sn_chunk, bytes))) return fail(rc);
+        const size_t words = nch * kFlowStride + P.levels.size() + 1;
+        if (cudaMalloc((void **)&h->d_flow_ctr, words * sizeof(int32_t)) != cudaSuccess) return fail(SC_ERR_OOM);
+        bytes += (int64_t)(words * sizeof(int32_t));
+    }
     if (precision != SC_FP64) {
         if (cudaMalloc(&h->d_inv, (size_t)std::max<int64_t>(1, P.inv_size) * sizeof(float)) != cudaSuccess)
             return fail(SC_ERR_OOM);
@@ -550,6 +757,21 @@ int numeric_factor(sc_numeric *h, const double *values, int on_device, cudaStrea
     const sc_symbolic *s = h->sym;
     int64_t nnz = (int64_t)s->valmap.size();
     h->last_stream = st;
+    if (h->stall_factor_chunk >= 0) {
+        // test hook: this factorization's units that read the chunk wait for one
+        // more POTRF / TRSM completion than will come; their bounded waits give up
+        const int32_t c = h->stall_factor_chunk;
+        h->stall_factor_chunk = -1;
+        if (!h->fused || c >= (int32_t)s->chunks.size()) return SC_ERR_UNSUPPORTED;
+        int32_t need = 0;
+        SC_CUDA(cudaMemcpy(&need, h->d_flow_need + c, sizeof(need), cudaMemcpyDeviceToHost));
+        const int32_t raised = need + 1;
+        SC_CUDA(cudaMemcpy(h->d_flow_need + c, &raised, sizeof(raised), cudaMemcpyHostToDevice));
+        const int rc = numeric_factor(h, values, on_device, st, info);
+        cudaStreamSynchronize(st);
+        SC_CUDA(cudaMemcpy(h->d_flow_need + c, &need, sizeof(need), cudaMemcpyHostToDevice));
+        return rc;
+    }
     SC_CUDA(cudaMemcpyAsync(h->d_values, values, nnz * sizeof(double),
                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
     cudaEvent_t e0, e1;
@@ -674,7 +896,8 @@ void numeric_free(sc_numeric *h) {
                     h->d_csr_map, h->d_counters, h->d_xw, h->d_solve_tiles, h->d_sn, h->d_blk, h->d_rbval,
                     h->d_loops, h->d_tmaps, h->d_tmap_of_sn, h->d_err, h->d_inv, h->d_x, h->d_r, h->d_b, h->d_xbest, h->d_y, h->d_z, h->d_acc, h->d_red,
                     h->d_dep_ptr, h->d_dep, h->d_sync, h->d_serr, h->d_hi, h->d_lo, h->d_thin,
-                    h->d_cgz, h->d_cgp, h->d_cgq, h->d_cgs, h->d_solve_units};
+                    h->d_cgz, h->d_cgp, h->d_cgq, h->d_cgs, h->d_solve_units, h->d_flow, h->d_flow_ctr,
+                    h->d_flow_need, h->d_task_chunk, h->d_sn_chunk};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->sym) h->sym->refs--;

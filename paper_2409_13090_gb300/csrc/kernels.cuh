@@ -181,15 +181,17 @@ __device__ void tri_inverse(const S (*a)[kMaxChunk + 1], int w, float (*iv)[kMax
     for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) out[idx] = iv[idx / w][idx % w];
 }
 
+// POTRF of chunk c by one CTA of 256 threads (the body of k_potrf and of the
+// per-level kernel's POTRF units); kPotrfSmem bytes of dynamic shared memory.
 template <typename T>
-__global__ void __launch_bounds__(256) k_potrf(T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
-                                               const int32_t *__restrict__ list, const double *__restrict__ adiag,
-                                               int32_t *__restrict__ info, int32_t *__restrict__ low_pivots,
-                                               double tau, float *__restrict__ hi, float *__restrict__ lo) {
+__device__ void potrf_chunk(T *__restrict__ lnz, const ChunkDev *__restrict__ chunks, int32_t c,
+                            const double *__restrict__ adiag, int32_t *__restrict__ info,
+                            int32_t *__restrict__ low_pivots, double tau, float *__restrict__ hi,
+                            float *__restrict__ lo) {
     extern __shared__ double smem_potrf[];
     __shared__ int flag;
     __shared__ double thr[kMaxChunk];
-    const ChunkDev ch = chunks[list[blockIdx.x]];
+    const ChunkDev ch = chunks[c];
     const int w = ch.w;
     T *base = lnz + ch.off + (int64_t)ch.c0 * ch.ld + ch.c0;
     if (threadIdx.x == 0) flag = 0;
@@ -223,6 +225,14 @@ __global__ void __launch_bounds__(256) k_potrf(T *__restrict__ lnz, const ChunkD
             if (sizeof(T) == 4 && hi) store_split(hi, lo, (base - lnz) + (int64_t)r * ch.ld + c, (float)a[r][c]);
         }
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_potrf(T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
+                                               const int32_t *__restrict__ list, const double *__restrict__ adiag,
+                                               int32_t *__restrict__ info, int32_t *__restrict__ low_pivots,
+                                               double tau, float *__restrict__ hi, float *__restrict__ lo) {
+    potrf_chunk<T>(lnz, chunks, list[blockIdx.x], adiag, info, low_pivots, tau, hi, lo);
 }
 
 // --------------------------------------------------------------------- K2
@@ -276,19 +286,20 @@ __device__ __forceinline__ void trsm_row(const T (*l)[kMaxChunk + 1], const T *r
     }
 }
 
+// TRSM of one tile (trsm_rows<T>() rows, four threads each) by the first
+// trsm_rows<T>() * 4 threads of the CTA; every thread of the CTA takes part in
+// the barriers (the body of k_trsm and of the per-level kernel's TRSM units).
 template <typename T>
-__global__ void __launch_bounds__(trsm_rows<T>() * 4) k_trsm(T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
-                                                       const TrsmTile *__restrict__ tiles, float *__restrict__ hi,
-                                                       float *__restrict__ lo) {
+__device__ void trsm_tile(T *__restrict__ lnz, const ChunkDev *__restrict__ chunks, const TrsmTile &tl,
+                          float *__restrict__ hi, float *__restrict__ lo) {
     __shared__ T l[kMaxChunk][kMaxChunk + 1];
     __shared__ T rinv[kMaxChunk];
-    const TrsmTile tl = tiles[blockIdx.x];
+    constexpr int kThreads = trsm_rows<T>() * 4;
     const ChunkDev ch = chunks[tl.chunk];
     const int w = ch.w;
     const T *diag = lnz + ch.off + (int64_t)ch.c0 * ch.ld + ch.c0;
-    {
+    if (threadIdx.x < kThreads) {
         // fixed-trip staging through registers, 16 loads in flight per thread
-        constexpr int kThreads = trsm_rows<T>() * 4;
         constexpr int kIters = kMaxChunk * kMaxChunk / kThreads;
         for (int it0 = 0; it0 < kIters; it0 += 16) {
             T tmp[16];
@@ -307,6 +318,7 @@ __global__ void __launch_bounds__(trsm_rows<T>() * 4) k_trsm(T *__restrict__ lnz
     __syncthreads();
     for (int k = threadIdx.x; k < kMaxChunk; k += blockDim.x) rinv[k] = k < w ? T(1) / l[k][k] : T(0);
     __syncthreads();
+    if (threadIdx.x >= kThreads) return;  // whole warps: the shuffles below stay within a warp
     const int q = threadIdx.x % 4;
     const int row = tl.r0 + threadIdx.x / 4;
     const bool live = row < ch.m;
@@ -315,6 +327,13 @@ __global__ void __launch_bounds__(trsm_rows<T>() * 4) k_trsm(T *__restrict__ lnz
     else if (w <= 16) trsm_row<T, 16>(l, rinv, xr, live, w, q, lnz, hi, lo);
     else if (w <= 32) trsm_row<T, 32>(l, rinv, xr, live, w, q, lnz, hi, lo);
     else trsm_row<T, 64>(l, rinv, xr, live, w, q, lnz, hi, lo);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(trsm_rows<T>() * 4) k_trsm(T *__restrict__ lnz, const ChunkDev *__restrict__ chunks,
+                                                       const TrsmTile *__restrict__ tiles, float *__restrict__ hi,
+                                                       float *__restrict__ lo) {
+    trsm_tile<T>(lnz, chunks, tiles[blockIdx.x], hi, lo);
 }
 
 // --------------------------------------------------------------------- K3
@@ -350,14 +369,16 @@ __device__ __forceinline__ void tile_fma(const T (*As)[64 + 1], const T (*Bs)[64
 // padding. The scatter into Lnz(P) is an atomic add
 // unless the task is the only writer of its target: supernodes of one level
 // may update the same ancestor entries.
+// One tile by one CTA of 256 threads (the body of k_gemm_tiles and of the
+// per-level kernel's product units). atomic_only: every target entry is added
+// atomically, also for an exclusive target (other units of the same launch may
+// update it concurrently).
 template <typename T, int BM, int BN, int BK>
-__global__ void __launch_bounds__(256) k_gemm_tiles(T *__restrict__ lnz, T *__restrict__ pool,
-                                                    const Task *__restrict__ tasks,
-                                                    const GemmTile *__restrict__ tiles) {
+__device__ void gemm_tile(T *__restrict__ lnz, T *__restrict__ pool, const Task *__restrict__ tasks,
+                          const GemmTile &tl, bool atomic_only) {
     static_assert(BM == 64 && BN == 64, "8 warps of 16 x 32 sub-tiles");
     __shared__ T As[BK][BM + 1];
     __shared__ T Bs[BK][BN + 1];
-    const GemmTile tl = tiles[blockIdx.x];
     const Task tk = tasks[tl.task];
     const int row0 = tl.tm * BM, col0 = tl.tn * BN;
     const T *A = lnz + tk.a_off;
@@ -419,7 +440,7 @@ __global__ void __launch_bounds__(256) k_gemm_tiles(T *__restrict__ lnz, T *__re
     }
     if (!active) return;
     const bool store = tk.flags & kTaskStoreU;
-    const bool excl = (tk.flags & kTaskExclusive) && !split;
+    const bool excl = (tk.flags & kTaskExclusive) && !split && !atomic_only;
     T *C = (store ? pool : lnz) + tk.c_off;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
@@ -437,12 +458,19 @@ __global__ void __launch_bounds__(256) k_gemm_tiles(T *__restrict__ lnz, T *__re
     }
 }
 
+template <typename T, int BM, int BN, int BK>
+__global__ void __launch_bounds__(256) k_gemm_tiles(T *__restrict__ lnz, T *__restrict__ pool,
+                                                    const Task *__restrict__ tasks,
+                                                    const GemmTile *__restrict__ tiles) {
+    gemm_tile<T, BM, BN, BK>(lnz, pool, tasks, tiles[blockIdx.x], false);
+}
+
 // Tiny product tasks: one warp per task, one output entry per lane step.
+// Tasks unit * 8 .. unit * 8 + 7 of the list, one per warp of a 256-thread CTA.
 template <typename T>
-__global__ void __launch_bounds__(256) k_small_tasks(T *__restrict__ lnz, T *__restrict__ pool,
-                                                     const Task *__restrict__ tasks,
-                                                     const int32_t *__restrict__ list, int32_t count) {
-    int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32;
+__device__ void small_tasks(T *__restrict__ lnz, T *__restrict__ pool, const Task *__restrict__ tasks,
+                            const int32_t *__restrict__ list, int32_t count, int unit) {
+    int warp = unit * 8 + threadIdx.x / 32;
     int lane = threadIdx.x % 32;
     if (warp >= count) return;
     const Task tk = tasks[list[warp]];
@@ -460,6 +488,13 @@ __global__ void __launch_bounds__(256) k_small_tasks(T *__restrict__ lnz, T *__r
         if (store) C[(int64_t)i * tk.ldc + j] = -acc;
         else atomicAdd(C + (int64_t)i * tk.ldc + j, -acc);
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_small_tasks(T *__restrict__ lnz, T *__restrict__ pool,
+                                                     const Task *__restrict__ tasks,
+                                                     const int32_t *__restrict__ list, int32_t count) {
+    small_tasks<T>(lnz, pool, tasks, list, count, blockIdx.x);
 }
 
 // --------------------------------------------------------------------- K3 (device loops)
@@ -560,16 +595,15 @@ __device__ __forceinline__ void product_blocks(const T *A, const T *Bm, int64_t 
 // blocks of one task (ThinUnit), one per warp, so a long thin product spreads
 // over many SMs.
 constexpr int kThinDim = 8;
+// Warp `wu` (0..kThinWarps-1) of thin unit u: one warp block of u's task.
 template <typename T>
-__global__ void __launch_bounds__(kThinWarps * 32) k_thin_tasks(T *__restrict__ lnz, const Task *__restrict__ tasks,
-                                                                const ThinUnit *__restrict__ units) {
-    const ThinUnit u = units[blockIdx.x];
+__device__ void thin_warp(T *__restrict__ lnz, const Task *__restrict__ tasks, const ThinUnit &u, int wu) {
     const Task tk = tasks[u.task];
     const bool lower = (tk.flags & kTaskLower) != 0;
     const int ni_min = sizeof(T) == 8 ? 2 : 1;
     const int NI = block_rows(tk.m, tk.n, ni_min, lower), NJ = 32 / NI;
     const int nbj = (tk.n + NJ - 1) / NJ, nblk = ((tk.m + NI - 1) / NI) * nbj;
-    const int b = u.blk0 + threadIdx.x / 32;
+    const int b = u.blk0 + wu;
     if (b >= nblk) return;
     const int i0 = (b / nbj) * NI, j0 = (b % nbj) * NJ;
     if (lower && j0 > i0 + NI - 1) return;  // wholly above the diagonal
@@ -584,6 +618,12 @@ __global__ void __launch_bounds__(kThinWarps * 32) k_thin_tasks(T *__restrict__ 
         case 4: warp_block<T, 4>(A, Bm, tk.lds, tk.k, ni, nj, C, tk.ldc, lower, i0, j0); break;
         default: warp_block<T, 8>(A, Bm, tk.lds, tk.k, ni, nj, C, tk.ldc, lower, i0, j0); break;
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThinWarps * 32) k_thin_tasks(T *__restrict__ lnz, const Task *__restrict__ tasks,
+                                                                const ThinUnit *__restrict__ units) {
+    thin_warp<T>(lnz, tasks, units[blockIdx.x], threadIdx.x / 32);
 }
 
 // Alg. 5's inner loops for a range of J's blocks, in one CTA: for each block B
@@ -625,27 +665,35 @@ __device__ __forceinline__ void item_products(T *lnz, const LoopItem &it, const 
     }
 }
 
+// One device-loop item by one CTA (the body of k_rlb_loop and of the per-level
+// kernel's loop units).
+template <typename T>
+__device__ void loop_item(T *__restrict__ lnz, const LoopItem &it, const SnDev *__restrict__ sn,
+                          const BlkDev *__restrict__ blk, const int32_t *__restrict__ rb_val) {
+    int task = 0;
+    item_products(lnz, it, sn, blk, rb_val,
+                  [&](const T *A, const T *Bm, int64_t ld, int K, int rows, int nb, T *C, int64_t ldc, bool lower) {
+                      product_blocks(A, Bm, ld, K, rows, nb, C, ldc, lower, task);
+                  });
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 2 : 1)) k_rlb_loop(T *__restrict__ lnz,
                                                                          const LoopItem *__restrict__ items,
                                                                          const SnDev *__restrict__ sn,
                                                                          const BlkDev *__restrict__ blk,
                                                                          const int32_t *__restrict__ rb_val) {
-    int task = 0;
-    item_products(lnz, items[blockIdx.x], sn, blk, rb_val,
-                  [&](const T *A, const T *Bm, int64_t ld, int K, int rows, int nb, T *C, int64_t ldc, bool lower) {
-                      product_blocks(A, Bm, ld, K, rows, nb, C, ldc, lower, task);
-                  });
+    loop_item<T>(lnz, items[blockIdx.x], sn, blk, rb_val);
 }
 
 // Loop items of a supernode narrower than 32 columns: one warp per item (eight
 // per CTA), one output per lane with the K-loop in registers.
+// Items unit * 8 .. unit * 8 + 7 of a list of narrow supernodes' items, one per warp.
 template <typename T>
-__global__ void __launch_bounds__(256) k_rlb_loop_warp(T *__restrict__ lnz, const LoopItem *__restrict__ items,
-                                                       int count, const SnDev *__restrict__ sn,
-                                                       const BlkDev *__restrict__ blk,
-                                                       const int32_t *__restrict__ rb_val) {
-    const int idx = blockIdx.x * 8 + threadIdx.x / 32, lane = threadIdx.x % 32;
+__device__ void loop_items_warp(T *__restrict__ lnz, const LoopItem *__restrict__ items, int count, int unit,
+                                const SnDev *__restrict__ sn, const BlkDev *__restrict__ blk,
+                                const int32_t *__restrict__ rb_val) {
+    const int idx = unit * 8 + threadIdx.x / 32, lane = threadIdx.x % 32;
     if (idx >= count) return;
     item_products(lnz, items[idx], sn, blk, rb_val,
                   [&](const T *A, const T *Bm, int64_t ld, int K, int rows, int nb, T *C, int64_t ldc, bool lower) {
@@ -658,6 +706,14 @@ __global__ void __launch_bounds__(256) k_rlb_loop_warp(T *__restrict__ lnz, cons
                           atomicAdd(C + (int64_t)i * ldc + j, -acc);
                       }
                   });
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_rlb_loop_warp(T *__restrict__ lnz, const LoopItem *__restrict__ items,
+                                                       int count, const SnDev *__restrict__ sn,
+                                                       const BlkDev *__restrict__ blk,
+                                                       const int32_t *__restrict__ rb_val) {
+    loop_items_warp<T>(lnz, items, count, blockIdx.x, sn, blk, rb_val);
 }
 
 // --------------------------------------------------------------------- K4b

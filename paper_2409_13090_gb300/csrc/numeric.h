@@ -34,7 +34,7 @@ struct LevelPlan {
     int32_t loopw_off = 0, loopw_cnt = 0;   // LoopItem of supernodes narrower than 32 columns, one warp per item
     int32_t rlp_off = 0, rlp_cnt = 0;       // RLPair
     int64_t rlp_max = 0;                    // largest assembly work item (elements)
-    // solve
+    int32_t flow_off = 0, flow_cnt = 0;     // FlowUnit of this level's k_level launch (fused plans)
 };
 
 // kernel classes of the per-kernel profile
@@ -95,6 +95,7 @@ struct sc_numeric {
     int32_t *d_serr = nullptr;      // nonzero after a bounded wait of a solve sweep gave up
     int32_t solve_tiles = 0;        // grab units of one sweep
     int32_t stall_chunk = -1;       // test hook: chunk whose expected arrivals are raised by one
+    int32_t stall_factor_chunk = -1;  // test hook: chunk whose k_level count target is raised by one
     void *d_xw = nullptr;           // permuted right-hand side / forward work vector
     sc::TrsmTile *d_solve_tiles = nullptr;
     sc::SolveUnit *d_solve_units = nullptr;
@@ -126,6 +127,13 @@ struct sc_numeric {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaEvent_t ev_trsm = nullptr, ev_rest[2] = {nullptr, nullptr};
     bool lookahead = false;              // plan split into crit / rest products
+    bool fused = false;                  // one k_level launch per level (SIMT precisions, RLB)
+    sc::FlowUnit *d_flow = nullptr;      // units of every level's launch, then the tail launch's
+    int32_t flow_tail_off = 0, flow_tail_cnt = 0;  // the products that follow the last level
+    int32_t *d_flow_ctr = nullptr;       // per chunk: POTRF + TRSM units done (kFlowStride apart); then work counters
+    int32_t *d_flow_need = nullptr;      // per chunk: 1 + its TRSM tiles
+    int32_t *d_task_chunk = nullptr;     // per task: the chunk whose columns it reads last (its source)
+    int32_t *d_sn_chunk = nullptr;       // per supernode: its last chunk
     bool use_graph = true;
     int num_sms = 152;
 };

@@ -51,6 +51,7 @@ struct Knobs {
     bool lookahead = true;
     int tc_min_k = 32, tc_wide_n = 96, thin_dim = 8;
     int defer_width = 256;
+    bool fused = false;
 };
 inline Knobs knobs_of(const sc_tune_table &t) {
     Knobs k;
@@ -62,6 +63,7 @@ inline Knobs knobs_of(const sc_tune_table &t) {
     if (t.tc_wide_n) k.tc_wide_n = t.tc_wide_n;
     if (t.thin_dim) k.thin_dim = t.thin_dim < 0 ? 0 : t.thin_dim;
     if (t.defer_width) k.defer_width = t.defer_width;
+    if (t.fused) k.fused = t.fused > 0;
     return k;
 }
 // Inner-dimension granularity of one tcgen05.mma of kind::tf32 (K = 8): the
@@ -91,7 +93,8 @@ inline bool tune_valid(const sc_tune_table &t) {
     auto in = [](int32_t v, int32_t lo, int32_t hi) { return v == 0 || (v >= lo && v <= hi); };
     return in(t.tile_min_entries, 1, 1 << 24) && in(t.tile_min_k, 1, 1 << 16) && in(t.loop_budget, 256, 1 << 28) &&
            (t.lookahead >= -1 && t.lookahead <= 1) && in(t.tc_min_k, 32, 1 << 16) && in(t.tc_wide_n, 16, 1 << 16) &&
-           (t.thin_dim == -1 || in(t.thin_dim, 1, 8)) && in(t.defer_width, 256, 1 << 20);
+           (t.thin_dim == -1 || in(t.thin_dim, 1, 8)) && in(t.defer_width, 256, 1 << 20) &&
+           (t.fused >= -1 && t.fused <= 1);
 }
 
 // Part of Alg. 5's inner loops for one block B of supernode J, run on the

@@ -28,7 +28,7 @@ bool same_knobs(const sc_tune_table &a, const sc_tune_table &b) {
     const sc::Knobs x = sc::knobs_of(a), y = sc::knobs_of(b);
     return x.tile_min_entries == y.tile_min_entries && x.tile_min_k == y.tile_min_k &&
            x.loop_budget == y.loop_budget && x.lookahead == y.lookahead && x.tc_min_k == y.tc_min_k &&
-           x.tc_wide_n == y.tc_wide_n && x.thin_dim == y.thin_dim && x.defer_width == y.defer_width;
+           x.tc_wide_n == y.tc_wide_n && x.thin_dim == y.thin_dim && x.defer_width == y.defer_width && x.fused == y.fused;
 }
 
 double median(std::vector<double> v) {
@@ -98,6 +98,7 @@ extern "C" int sc_tune(sc_symbolic *s, const double *values, int values_on_devic
     count++;
     const std::vector<Field> fields = {
         {&sc_tune_table::defer_width, {256, 512, 1024, 4096}, true, false, false},
+        {&sc_tune_table::fused, {1, -1}, false, false, true},
         {&sc_tune_table::lookahead, {1, -1}, false, false, true},
         {&sc_tune_table::tile_min_entries, {512, 1024, 2048}, true, false, true},
         {&sc_tune_table::tile_min_k, {8, 16, 32}, true, false, true},
@@ -111,6 +112,7 @@ extern "C" int sc_tune(sc_symbolic *s, const double *values, int values_on_devic
         if (rc) break;
         if ((f.tc_only && !tc) || (f.rlb_only && !rlb)) continue;
         if (f.member == &sc_tune_table::lookahead && !s->opt.use_graph) continue;
+        if (f.member == &sc_tune_table::fused && tc) continue;  // tensor-core precisions keep per-class launches
         for (int32_t v : f.values) {
             sc_tune_table cand = cur;
             cand.*f.member = v;

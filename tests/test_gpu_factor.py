@@ -392,3 +392,56 @@ def test_degenerate_structures(name, variant, prec, tol):
     B = inputs.rhs(A.n, 3, 6)
     X, info = num.solve(B)
     assert oracle.backward_error(A, B, X).max() <= 1e-14, info
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-3)])
+@pytest.mark.parametrize("name", ["diff7_24s", "st27_14", "lap2d_ragged", "aniso_16"])
+@pytest.mark.parametrize("lookahead", [1, -1])
+def test_one_persistent_launch_per_level(name, lookahead, prec, tol):
+    """The per-level persistent kernel (fused plan, a launch-plan setting for
+    FP64 / FP32 RLB): POTRF, TRSM, products, small tasks and device loops of a level, and
+    the previous level's lookahead products, in one launch ordered by device
+    counters. L against the oracle's, the same as the per-class launches
+    (fused = -1), and at most one launch per level plus the value load, the
+    tail launch and (FP32) the inverses."""
+    # diff7_24s: the 7-point 24^3 matrix with a diagonal shift of 1e-2, so that an
+    # FP32 factor is comparable with the FP64 oracle's at the FP32 bound
+    A = inputs.diffusion_3d_7pt(24, 24, 24, seed=7, shift=1e-2) if name == "diff7_24s" else _grid_case(name)
+    kw = dict(ordering="grid_nd", grid=A.grid, merge=0.125)
+    sym = sc.Symbolic(A, tune=dict(lookahead=lookahead, fused=1), **kw)
+    o = oracle.Oracle(A, oracle.nd_grid(*A.grid, 8), pr=True, merge=0.125)
+    assert o.factor() == 0
+    Lo = o.L_supernodal()
+    num = sym.factor(A.values, precision=prec)
+    assert num.rc == 0
+    _check_L(num.export_L(), Lo, tol)
+    levels = sym.plan_stats(prec)["levels"]
+    assert num.info.kernel_launches <= levels + 4, (num.info.kernel_launches, levels)
+    sym2 = sc.Symbolic(A, tune=dict(lookahead=lookahead, fused=-1), **kw)
+    num2 = sym2.factor(A.values, precision=prec)
+    assert num2.rc == 0
+    assert num2.info.kernel_launches > num.info.kernel_launches
+    _check_L(num2.export_L(), Lo, tol)
+    B = inputs.rhs(A.n, 2, 5)
+    X, info = num.solve(B)
+    assert oracle.backward_error(A, B, X).max() <= 1e-14, info
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_per_level_kernel_wait_times_out_and_handle_recovers(prec):
+    """A chunk whose POTRF / TRSM count target is raised by one (test hook):
+    the units that read it give up after spin_limit polls, the factorization
+    returns SC_ERR_TIMEOUT, and the same handle then factors correctly."""
+    A = _grid_case("diff7_13")
+    sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid, spin_limit=1 << 16, tune=dict(fused=1))
+    num = sym.factor(A.values, precision=prec)
+    assert num.rc == 0
+    L0 = num.export_L()
+    nchunks = sym.plan_stats(prec)["chunks"]
+    for chunk in (0, nchunks // 2, nchunks - 2):
+        num.stall_next_factor(chunk)
+        with pytest.raises(sc.SCError) as e:
+            num.refactor(A.values)
+        assert e.value.code == sc.SC_ERR_TIMEOUT
+        num.refactor(A.values)
+        assert np.abs(num.export_L() - L0).max() <= 1e-5 * np.abs(L0).max()
