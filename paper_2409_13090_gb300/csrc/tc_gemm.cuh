@@ -10,7 +10,7 @@
 //           stages and hands finished accumulators to the epilogue;
 //   warps 2-9 epilogue: tcgen05.ld of 32 lanes x half the columns each, subtract into the target
 //           block of Lnz(P) (plain read-modify-write for an exclusive target,
-//           atomic add otherwise; 16-byte vectors when aligned), then release
+//           a no-return reduction otherwise; 16-byte vectors when aligned), then release
 //           the accumulator -- so one tile's epilogue overlaps the next tile's
 //           loads and MMAs.
 // Operands are K-major: a panel row is contiguous along the supernode's
@@ -128,6 +128,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
 }
 
+// no-return reductions into the target (the epilogue never needs the old value)
+__device__ __forceinline__ void red_sub4(float *p, float a, float b, float c, float d) {
+    asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(-a), "f"(-b), "f"(-c),
+                 "f"(-d)
+                 : "memory");
+}
+__device__ __forceinline__ void red_sub(float *p, float a) {
+    asm volatile("red.relaxed.gpu.global.add.f32 [%0], %1;" ::"l"(p), "f"(-a) : "memory");
+}
+
 // C row segment -= v[0..32) for columns gj0..gj0+31 of row gi (masked at n, and
 // to j <= gi for a lower task). For an exclusive target with an aligned full
 // segment, the caller has already loaded the old values into c (prefetch).
@@ -144,7 +154,7 @@ __device__ __forceinline__ void epilogue_row(float *__restrict__ crow, const flo
                 c4[q] = make_float4(c[q].x - v[4 * q], c[q].y - v[4 * q + 1], c[q].z - v[4 * q + 2],
                                     c[q].w - v[4 * q + 3]);
             } else {
-                atomicAdd(c4 + q, make_float4(-v[4 * q], -v[4 * q + 1], -v[4 * q + 2], -v[4 * q + 3]));
+                red_sub4(reinterpret_cast<float *>(c4 + q), v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
             }
         }
         return;
@@ -154,7 +164,7 @@ __device__ __forceinline__ void epilogue_row(float *__restrict__ crow, const flo
         const int gj = gj0 + j;
         if (gj < n && (!lower || gj <= gi)) {
             if (excl) crow[gj] -= v[j];
-            else atomicAdd(crow + gj, -v[j]);
+            else red_sub(crow + gj, v[j]);
         }
     }
 }
