@@ -151,12 +151,20 @@ typedef struct sc_options {
                                   pairs by least new fill while the added storage stays
                                   <= merge_frac x the fundamental storage; 0 = off */
     const sc_tune_table *tune; /* launch-plan settings (copied), NULL = defaults     */
-    int32_t reserved[4];
+    int32_t deterministic;     /* 1 = bit-reproducible factor: every entry of L gets its
+                                  updates in one fixed order, so two factorizations of
+                                  the same values give the same bits. Needs variant
+                                  SC_RL: the U_J products are stored, never accumulated
+                                  (no inner-dimension splitting), and each level's
+                                  assembly is owned by the targets (a CTA per row slab
+                                  of Lnz(P) adds P's update matrices in source order).
+                                  The solve's reductions stay unordered. 0 = off. */
+    int32_t reserved[3];
 } sc_options;
 
 /* Fills o with the defaults: SC_ORDER_NATURAL, nd_leaf 8, pr 1, SC_RLB, SC_FP64,
  * chunk 64, ir_tol 1e-14, ir_maxit 30, pivot_tau 2^-10, spin_limit 1<<22,
- * use_graph 1, merge_frac 0 (fundamental supernodes), tune NULL. Returns
+ * use_graph 1, merge_frac 0 (fundamental supernodes), tune NULL, deterministic 0. Returns
  * SC_OK, or -1 if o is NULL. */
 int sc_options_default(sc_options *o);
 
@@ -174,7 +182,8 @@ typedef struct sc_symbolic sc_symbolic;
  *   o        options (host); NULL = defaults
  *   out      receives the new handle
  * Errors: -1..-5 for invalid arguments (unsorted or duplicate indices,
- * entries above the diagonal or a missing diagonal give -3), SC_ERR_OOM. */
+ * entries above the diagonal or a missing diagonal give -3; an option out of
+ * range, or deterministic with a variant other than SC_RL, gives -4), SC_ERR_OOM. */
 int sc_analyze(int64_t n, const int64_t *colptr, const int32_t *rowind, const sc_options *o,
                sc_symbolic **out);
 
@@ -308,7 +317,8 @@ int sc_solve(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, double *
  *   out      receives the combined handle; its unknowns are the matrices'
  *            unknowns concatenated in order, and its values array is the
  *            matrices' values arrays concatenated in order.
- * Errors: -1..-3, SC_ERR_OOM. */
+ * Errors: -1..-3 (-2 also when the handles differ in variant or
+ * deterministic), SC_ERR_OOM. */
 int sc_analyze_batch(int count, sc_symbolic *const *syms, sc_symbolic **out);
 
 /* Batched numeric factorization of many independent matrices in one launch
@@ -393,8 +403,9 @@ int sc_probe_fma_peak(int kind, void *cuda_stream, double *flops_per_s);
 /* Size of the launch plan a factorization in `precision` would use (host only,
  * no device memory): out[0..nout) receives, in order, the chunk levels, chunks,
  * product tasks, warp-sized tasks, tiled tasks, SIMT tiles, tensor-core tiles,
- * TRSM tiles, RL assembly pairs, device-loop items and warp-block units.
- * Errors: -1, -2, -3. */
+ * TRSM tiles, RL assembly pairs, device-loop items, warp-block units, SIMT
+ * tiles split along the inner dimension (added atomically) and target-owned RL
+ * assembly slabs (deterministic plans). Errors: -1, -2, -3. */
 int sc_plan_stats(const sc_symbolic *s, int precision, int64_t *out, int nout);
 
 /* Host-side check of the device schedule of s (no device work): recomputes,
@@ -417,7 +428,11 @@ int sc_plan_stats(const sc_symbolic *s, int precision, int64_t *out, int nout);
  *   column's positions in glbind(P), 12 a product that the tensor-core
  *   precisions route to tcgen05 tiles would multiply panel columns past its
  *   inner dimension: its K is not a whole number of 8-column MMA steps and
- *   real columns of the source panel follow it).
+ *   real columns of the source panel follow it; 13 in a deterministic
+ *   schedule, a launch plan (FP64 or tensor-core) with a product tile split
+ *   along the inner dimension, or a target row of an RL assembly pair that no
+ *   slab of its target owns, or a slab whose pairs are not one target's in
+ *   source order).
  * Returns SC_OK, SC_ERR_INTERNAL when a violation is found, -1 / -2 for NULL
  * arguments. */
 int sc_check_schedule(const sc_symbolic *s, int64_t *out, int nout);
@@ -425,7 +440,8 @@ int sc_check_schedule(const sc_symbolic *s, int64_t *out, int nout);
 /* Test hook: plants one mistake of the given kind (1 a GEMM target one row
  * too high, 2 a critical product marked as other, 3 an in-panel update reading
  * one column too many, 4 a loop item reaching past its blocks, 5 tensor-core
- * routing that ignores the K-tail rule) in s's schedule
+ * routing that ignores the K-tail rule, 6 a deterministic plan whose first
+ * level of assembly slabs misses a target row) in s's schedule
  * so that a test can see sc_check_schedule find it. s can no longer be factored
  * (sc_factor returns SC_ERR_INTERNAL). Returns SC_OK, -1, -2 for a bad kind,
  * or SC_ERR_UNSUPPORTED when the schedule has no entry of that kind. */

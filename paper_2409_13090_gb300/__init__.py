@@ -41,7 +41,7 @@ class Options(C.Structure):
                 ("precision", C.c_int32), ("chunk", C.c_int32), ("ir_tol", C.c_double),
                 ("ir_maxit", C.c_int32), ("pivot_tau", C.c_double), ("spin_limit", C.c_int64),
                 ("use_graph", C.c_int32), ("merge_frac", C.c_double), ("tune", C.c_void_p),
-                ("reserved", C.c_int32 * 4)]
+                ("deterministic", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 TUNE_FIELDS = ["tile_min_entries", "tile_min_k", "loop_budget", "lookahead", "tc_min_k", "tc_wide_n", "thin_dim",
@@ -267,7 +267,8 @@ class Symbolic:
 
     def __init__(self, A=None, *, ordering="natural", grid=None, nd_leaf=8, user_perm=None, pr=True,
                  variant="rlb", precision="fp64", chunk=64, ir_tol=1e-14, ir_maxit=30, use_graph=True,
-                 merge=0.0, spin_limit=None, pivot_tau=None, tune=None, _handle=None, _parts=None):
+                 merge=0.0, spin_limit=None, pivot_tau=None, tune=None, deterministic=False, _handle=None,
+                 _parts=None):
         self._parts = _parts
         if _handle is not None:
             self._h = _handle
@@ -291,6 +292,7 @@ class Symbolic:
         o.ir_maxit = ir_maxit
         o.use_graph = 1 if use_graph else 0
         o.merge_frac = float(merge)
+        o.deterministic = 1 if deterministic else 0
         if spin_limit is not None:
             o.spin_limit = int(spin_limit)
         if pivot_tau is not None:
@@ -353,12 +355,12 @@ class Symbolic:
         return out
 
     PLAN_KEYS = ["levels", "chunks", "tasks", "warp_tasks", "tiled_tasks", "simt_tiles", "tc_tiles", "trsm_tiles",
-                 "rl_pairs", "loop_items", "thin_units"]
+                 "rl_pairs", "loop_items", "thin_units", "split_tiles", "rl_slabs"]
 
     CHECK_KINDS = {0: "ok", 1: "source range", 2: "target range", 3: "trapezoid", 4: "not an ancestor",
                    5: "level order", 6: "critical flag", 7: "run mapping", 8: "RL pool", 9: "RL relind",
                    10: "plain write outside the own panel", 11: "entry mapping",
-                   12: "tensor-core K range"}
+                   12: "tensor-core K range", 13: "deterministic plan"}
 
     def save(self, path) -> None:
         """sc_symbolic_save: the analysis on disk (factor later without analysing again)."""

@@ -37,7 +37,7 @@ extern "C" int sc_analyze_batch(int count, sc_symbolic *const *syms, sc_symbolic
         b->rb_val_ptr.push_back(0);
         for (int i = 0; i < count; i++) {
             const sc_symbolic *s = syms[i];
-            if (s->opt.variant != b->opt.variant) {
+            if (s->opt.variant != b->opt.variant || s->opt.deterministic != b->opt.deterministic) {
                 delete b;
                 return -2;
             }

@@ -244,6 +244,7 @@ extern "C" int sc_check_schedule(const sc_symbolic *s, int64_t *out, int nout) {
             }
             if (bad_kind) bad_level = (int64_t)lv;
         }
+        if (!bad_kind && s->opt.deterministic) bad_kind = det_plan_check(s, &bad_level);
         int64_t v[] = {tasks, products, entries, bad_level, bad_kind};
         for (int i = 0; i < nout && i < 5; i++) out[i] = v[i];
         return bad_kind ? SC_ERR_INTERNAL : SC_OK;
@@ -257,7 +258,16 @@ extern "C" int sc_check_schedule(const sc_symbolic *s, int64_t *out, int nout) {
 // sc_tune refuse it.
 extern "C" int sc_test_perturb_schedule(sc_symbolic *s, int kind) {
     if (!s) return -1;
-    if (kind < 1 || kind > 5) return -2;
+    if (kind < 1 || kind > 6) return -2;
+    if (kind == 6) {  // a deterministic plan whose first assembly slab misses a touched row
+        for (const auto &L : s->levels)
+            if (!L.rl_pairs.empty() && s->opt.deterministic) {
+                s->test_det_short_slab = true;
+                s->poisoned = true;
+                return SC_OK;
+            }
+        return SC_ERR_UNSUPPORTED;
+    }
     if (kind == 5) {  // tensor-core routing without the K-tail rule: only matters where a K tail exists
         const Knobs kn = knobs_of(s->tune);
         for (auto &L : s->levels)

@@ -91,6 +91,14 @@ struct BlkDev {
 
 constexpr int kLoopSmemBytes = 48 * 1024;
 
+// Target-owned RL assembly (deterministic plans): rows [row0, row1) of Lnz(P)
+// receive the update matrices of pairs pair0 .. pair0 + npairs - 1 (all with
+// target P, in the order of their source supernodes) from one CTA.
+struct RLSlab {
+    int32_t pair0, npairs, row0, row1;
+};
+constexpr int kRLSlabRows = 64;
+
 // One unit of the per-level persistent kernel (k_level): a POTRF of a chunk, a
 // TRSM tile, a product tile, one or two thin units, up to eight small tasks, a
 // device-loop item or up to eight narrow loop items. idx indexes the list of

@@ -47,14 +47,15 @@ double task_flops(const Task &t) {
     return 2.0 * e * t.k;
 }
 
-void tiles_of(const Task &t, int32_t id, std::vector<GemmTile> &out) {
+void tiles_of(const Task &t, int32_t id, std::vector<GemmTile> &out, bool no_split) {
     int tm = (t.m + kBM - 1) / kBM, tn = (t.n + kBN - 1) / kBN;
     // a task of few tiles with a long inner dimension is split along it, so its
     // tiles do not serialise a level; a critical task (the next level waits for
     // it) is split into slices of kSplitKCrit so its latency is short (an RL
-    // update matrix is stored, not added: never split)
+    // update matrix is stored, not added: never split; nor is anything in a
+    // deterministic plan, where the slices' atomic adds would land in any order)
     int slices = 0;
-    if (!(t.flags & kTaskStoreU)) {
+    if (!(t.flags & kTaskStoreU) && !no_split) {
         if ((t.flags & kTaskCrit) && t.k >= 2 * kSplitKCrit) slices = (t.k + kSplitKCrit - 1) / kSplitKCrit;
         else if (tm * tn <= 8 && t.k > 2 * kSplitK) slices = (t.k + kSplitK - 1) / kSplitK;
     }
@@ -384,7 +385,14 @@ int run_levels(sc_numeric *h, cudaStream_t st, Prof *prof = nullptr, cudaStream_
             launches++;
         }
         if (join) SC_CUDA(cudaStreamWaitEvent(st, h->ev_join, 0));
-        for (int32_t q0 = 0; q0 < p.rlp_cnt; q0 += 65535) {  // grid.y holds at most 65535 pairs
+        if (p.rlo_cnt) {
+            B(kProfRlAsm);
+            k_rl_assemble_ordered<T><<<p.rlo_cnt, 256, 0, st>>>(lnz, pool, h->d_rlpairs, h->d_rlslabs + p.rlo_off,
+                                                                h->d_rlrelind);
+            E();
+            launches++;
+        }
+        for (int32_t q0 = 0; q0 < p.rlp_cnt && !p.rlo_cnt; q0 += 65535) {  // grid.y holds at most 65535 pairs
             unsigned gx = (unsigned)std::min<int64_t>((p.rlp_max + 255) / 256, 64);
             unsigned gy = (unsigned)std::min<int32_t>(65535, p.rlp_cnt - q0);
             B(kProfRlAsm);
@@ -432,6 +440,7 @@ struct Plan {
     std::vector<GemmTile> gemm;
     std::vector<Task> tasks;
     std::vector<RLPair> rlpairs;
+    std::vector<RLSlab> rlslabs;
     std::vector<LoopItem> loops;
     std::vector<LevelPlan> levels;
     int64_t inv_size = 0;  // elements of the diagonal-block inverses
@@ -478,6 +487,7 @@ void build_flow(Plan &P, bool lookahead) {
 // of the next level (crit) and the rest (targets two or more levels up).
 void build_plan(const sc_symbolic *s, int precision, Plan &P, bool lookahead) {
     const Knobs kn = knobs_of(s->tune);
+    const bool det = s->opt.deterministic != 0;
     P.cd.resize(s->chunks.size());
     int64_t inv = 0;
     for (size_t c = 0; c < s->chunks.size(); c++) {
@@ -539,7 +549,7 @@ void build_plan(const sc_symbolic *s, int precision, Plan &P, bool lookahead) {
                 for (int b0 = 0; b0 < nblk; b0 += kThinWarps) units_thin[cls].push_back(ThinUnit{id, b0});
                 P.class_flops[kProfGemm] += task_flops(t);
             } else {
-                tiles_of(t, id, g_simt[cls]);
+                tiles_of(t, id, g_simt[cls], det);
                 P.class_flops[kProfGemm] += task_flops(t);
             }
         }
@@ -579,7 +589,7 @@ void build_plan(const sc_symbolic *s, int precision, Plan &P, bool lookahead) {
             int32_t id = (int32_t)P.tasks.size();
             P.tasks.push_back(t);
             if (is_small(t)) rl_small.push_back(id);
-            else tiles_of(t, id, rl_g);
+            else tiles_of(t, id, rl_g, det);
             P.class_flops[kProfRlUpd] += task_flops(t);
         }
         p.rlg_off = (int32_t)P.gemm.size();
@@ -595,10 +605,92 @@ void build_plan(const sc_symbolic *s, int precision, Plan &P, bool lookahead) {
             P.class_flops[kProfRlAsm] += (double)(pr.c_end - pr.c_begin) * (pr.s - pr.c_begin);
         }
         p.rlp_cnt = (int32_t)L.rl_pairs.size();
+        if (det) {
+            // target-owned assembly: the level's pairs grouped by target P, each
+            // group in the order of its source supernodes (the order the level
+            // lists them in), P's touched rows cut into slabs of kRLSlabRows
+            auto first = P.rlpairs.begin() + p.rlp_off;
+            std::stable_sort(first, P.rlpairs.end(),
+                             [](const RLPair &a, const RLPair &b) { return a.p_off < b.p_off; });
+            p.rlo_off = (int32_t)P.rlslabs.size();
+            for (int32_t g0 = p.rlp_off, g1; g0 < (int32_t)P.rlpairs.size(); g0 = g1) {
+                int32_t lo = INT32_MAX, hi = -1;
+                for (g1 = g0; g1 < (int32_t)P.rlpairs.size() && P.rlpairs[g1].p_off == P.rlpairs[g0].p_off; g1++) {
+                    const RLPair &pr = P.rlpairs[g1];
+                    const int32_t *ri = s->rl_relind.data() + pr.ri_off;
+                    // target rows mP - 1 - relind[r] of the pair's rows, ascending in r
+                    lo = std::min(lo, pr.mP - 1 - ri[0]);
+                    hi = std::max(hi, pr.mP - 1 - ri[pr.s - pr.c_begin - 1]);
+                }
+                for (int32_t r = lo; r <= hi; r += kRLSlabRows)
+                    P.rlslabs.push_back(RLSlab{g0, g1 - g0, r, std::min(hi + 1, r + kRLSlabRows)});
+            }
+            p.rlo_cnt = (int32_t)P.rlslabs.size() - p.rlo_off;
+            if (s->test_det_short_slab && p.rlo_cnt && !P.rlslabs.empty()) {
+                RLSlab &last = P.rlslabs.back();  // its last row is a touched row (the group's hi)
+                if (last.row1 - last.row0 > 1 && P.rlslabs.size() == (size_t)p.rlo_cnt) last.row1--;
+            }
+        }
     }
 }
 
 }  // namespace
+
+int det_plan_check(const sc_symbolic *s, int64_t *bad_level) {
+    for (int precision : {SC_FP64, SC_TF32}) {
+        Plan P;
+        build_plan(s, precision, P, false);
+        for (size_t lv = 0; lv < P.levels.size(); lv++) {
+            const LevelPlan &p = P.levels[lv];
+            *bad_level = (int64_t)lv;
+            auto split_in = [&](int32_t off, int32_t cnt) {
+                for (int32_t i = off; i < off + cnt; i++)
+                    if (P.gemm[i].ks >= 0) return true;
+                return false;
+            };
+            for (const ProdLists *pl : {&p.crit, &p.rest})
+                if (split_in(pl->gemm_off, pl->gemm_cnt) || split_in(pl->tc_off, pl->tc_cnt) ||
+                    split_in(pl->tc64_off, pl->tc64_cnt))
+                    return 13;
+            if (split_in(p.rlg_off, p.rlg_cnt)) return 13;
+            if (!p.rlp_cnt) continue;
+            // slabs: inside the level's pairs, one target each, sources ascending (pool offsets
+            // follow the level's source order), groups disjoint and ascending, a group's row
+            // ranges non-empty, ascending and disjoint
+            const int32_t pe = p.rlp_off + p.rlp_cnt;
+            for (int32_t q = p.rlo_off; q < p.rlo_off + p.rlo_cnt; q++) {
+                const RLSlab &sl = P.rlslabs[q];
+                if (sl.npairs < 1 || sl.pair0 < p.rlp_off || sl.pair0 + sl.npairs > pe || sl.row0 >= sl.row1) return 13;
+                for (int32_t i = sl.pair0 + 1; i < sl.pair0 + sl.npairs; i++)
+                    if (P.rlpairs[i].p_off != P.rlpairs[sl.pair0].p_off || P.rlpairs[i].u_off <= P.rlpairs[i - 1].u_off)
+                        return 13;
+                if (q > p.rlo_off) {
+                    const RLSlab &pv = P.rlslabs[q - 1];
+                    if (pv.pair0 == sl.pair0 ? (pv.npairs != sl.npairs || pv.row1 > sl.row0)
+                                             : pv.pair0 + pv.npairs > sl.pair0)
+                        return 13;
+                }
+            }
+            // every target row of every pair lies in a slab of the pair's group
+            int32_t q = p.rlo_off;
+            for (int32_t i = p.rlp_off; i < pe; i++) {
+                while (q < p.rlo_off + p.rlo_cnt && P.rlslabs[q].pair0 + P.rlslabs[q].npairs <= i) q++;
+                if (q == p.rlo_off + p.rlo_cnt || P.rlslabs[q].pair0 > i) return 13;
+                int32_t qe = q;
+                while (qe < p.rlo_off + p.rlo_cnt && P.rlslabs[qe].pair0 == P.rlslabs[q].pair0) qe++;
+                const RLPair &pr = P.rlpairs[i];
+                const int32_t *ri = s->rl_relind.data() + pr.ri_off;
+                for (int32_t r = 0, k = q; r < pr.s - pr.c_begin; r++) {
+                    const int32_t row = pr.mP - 1 - ri[r];
+                    while (k < qe && P.rlslabs[k].row1 <= row) k++;
+                    if (k == qe || P.rlslabs[k].row0 > row) return 13;
+                }
+            }
+        }
+    }
+    *bad_level = -1;
+    return 0;
+}
 
 int plan_stats(const sc_symbolic *s, int precision, int64_t *out, int nout) {
     Plan P;
@@ -606,14 +698,15 @@ int plan_stats(const sc_symbolic *s, int precision, int64_t *out, int nout) {
     int64_t small_tasks = 0, tile_tasks = 0;
     for (const LevelPlan &l : P.levels) small_tasks += l.small_cnt + l.rls_cnt;
     tile_tasks = (int64_t)P.tasks.size() - small_tasks;
-    int64_t tc_tiles = 0, simt_tiles = 0;
+    int64_t tc_tiles = 0, simt_tiles = 0, split_tiles = 0;
     for (const LevelPlan &l : P.levels) {
         tc_tiles += l.crit.tc_cnt + l.crit.tc64_cnt + l.rest.tc_cnt + l.rest.tc64_cnt;
         simt_tiles += l.crit.gemm_cnt + l.rest.gemm_cnt + l.rlg_cnt;
     }
+    for (const GemmTile &g : P.gemm) split_tiles += g.ks >= 0;
     int64_t v[] = {(int64_t)P.levels.size(), (int64_t)P.cd.size(), (int64_t)P.tasks.size(), small_tasks, tile_tasks,
                    simt_tiles, tc_tiles, (int64_t)P.trsm.size(), (int64_t)P.rlpairs.size(), (int64_t)P.loops.size(),
-                   (int64_t)P.thin.size()};
+                   (int64_t)P.thin.size(), split_tiles, (int64_t)P.rlslabs.size()};
     for (int i = 0; i < nout && i < (int)(sizeof(v) / sizeof(v[0])); i++) out[i] = v[i];
     return SC_OK;
 }
@@ -721,6 +814,7 @@ int numeric_create(sc_symbolic *s, int precision, sc_numeric **out) {
     if ((rc = upload(h->d_thin, P.thin, bytes))) return fail(rc);
     if ((rc = upload(h->d_tasks, P.tasks, bytes))) return fail(rc);
     if ((rc = upload(h->d_rlpairs, P.rlpairs, bytes))) return fail(rc);
+    if ((rc = upload(h->d_rlslabs, P.rlslabs, bytes))) return fail(rc);
     if ((rc = upload(h->d_rlrelind, s->rl_relind, bytes))) return fail(rc);
     if ((rc = upload(h->d_loops, P.loops, bytes))) return fail(rc);
     {
@@ -892,7 +986,7 @@ void numeric_free(sc_numeric *h) {
         if (e) cudaEventDestroy(e);
     void *ptrs[] = {h->d_lnz, h->d_pool, h->d_valmap, h->d_values, h->d_diagpos, h->d_adiag, h->d_info,
                     h->d_chunks, h->d_potrf, h->d_trsm, h->d_gemm, h->d_small, h->d_tasks, h->d_rlpairs,
-                    h->d_rlrelind, h->d_glbind, h->d_perm, h->d_csr_ptr, h->d_csr_col, h->d_csr_val,
+                    h->d_rlslabs, h->d_rlrelind, h->d_glbind, h->d_perm, h->d_csr_ptr, h->d_csr_col, h->d_csr_val,
                     h->d_csr_map, h->d_counters, h->d_xw, h->d_solve_tiles, h->d_sn, h->d_blk, h->d_rbval,
                     h->d_loops, h->d_tmaps, h->d_tmap_of_sn, h->d_err, h->d_inv, h->d_x, h->d_r, h->d_b, h->d_xbest, h->d_y, h->d_z, h->d_acc, h->d_red,
                     h->d_dep_ptr, h->d_dep, h->d_sync, h->d_serr, h->d_hi, h->d_lo, h->d_thin,

@@ -737,4 +737,46 @@ __global__ void k_rl_assemble(T *__restrict__ lnz, const T *__restrict__ pool, c
     }
 }
 
+// Target-owned RL assembly (deterministic plans): the CTA owns rows [row0, row1)
+// of Lnz(P) and adds into them the update matrices of P's pairs one pair after
+// another, in the order of their source supernodes, with plain read-modify-
+// writes; a barrier between two pairs orders the adds to an entry. The target
+// row m_P-1-relind[rr] grows with rr, so the rows of a pair that land in the
+// slab are one range [ra, rb), found by binary search.
+template <typename T>
+__global__ void __launch_bounds__(256) k_rl_assemble_ordered(T *__restrict__ lnz, const T *__restrict__ pool,
+                                                             const RLPair *__restrict__ pairs,
+                                                             const RLSlab *__restrict__ slabs,
+                                                             const int32_t *__restrict__ relind) {
+    const RLSlab sl = slabs[blockIdx.x];
+    for (int32_t q = 0; q < sl.npairs; q++) {
+        const RLPair pr = pairs[sl.pair0 + q];
+        const int32_t *ri = relind + pr.ri_off;  // entries for rows c_begin..s-1
+        const int ncols = pr.c_end - pr.c_begin;
+        const int nrows = pr.s - pr.c_begin;
+        // first rr whose target row is >= v: target row >= v <=> relind <= m_P-1-v
+        auto first_at = [&](int32_t v) {
+            int lo = 0, hi = nrows;
+            while (lo < hi) {
+                const int mid = (lo + hi) / 2;
+                if (pr.mP - 1 - ri[mid] >= v) hi = mid;
+                else lo = mid + 1;
+            }
+            return lo;
+        };
+        const int ra = first_at(sl.row0), rb = first_at(sl.row1);
+        if (ra >= rb) continue;  // uniform over the CTA: no barrier needed
+        const int64_t total = (int64_t)(rb - ra) * ncols;
+        for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+            const int rr = ra + (int)(e / ncols), cc = (int)(e % ncols);
+            if (cc > rr) continue;
+            const int64_t prow = pr.mP - 1 - ri[rr];
+            const int64_t pcol = pr.mP - 1 - ri[cc];
+            lnz[pr.p_off + prow * pr.ldp + pcol] +=
+                pool[pr.u_off + (int64_t)(pr.c_begin + rr) * pr.s + pr.c_begin + cc];
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace sc

@@ -34,6 +34,7 @@ struct LevelPlan {
     int32_t loopw_off = 0, loopw_cnt = 0;   // LoopItem of supernodes narrower than 32 columns, one warp per item
     int32_t rlp_off = 0, rlp_cnt = 0;       // RLPair
     int64_t rlp_max = 0;                    // largest assembly work item (elements)
+    int32_t rlo_off = 0, rlo_cnt = 0;       // RLSlab (deterministic plans: target-owned assembly)
     int32_t flow_off = 0, flow_cnt = 0;     // FlowUnit of this level's k_level launch (fused plans)
 };
 
@@ -69,6 +70,7 @@ struct sc_numeric {
     sc::ThinUnit *d_thin = nullptr;
     sc::Task *d_tasks = nullptr;
     sc::RLPair *d_rlpairs = nullptr;
+    sc::RLSlab *d_rlslabs = nullptr;
     sc::SnDev *d_sn = nullptr;
     sc::BlkDev *d_blk = nullptr;
     int32_t *d_rbval = nullptr;

@@ -185,6 +185,7 @@ struct sc_symbolic {
     std::atomic<int> refs{0};
     bool poisoned = false;  // a test hook altered the schedule: never factored
     bool test_tc_ignore_tail = false;  // test hook: tensor-core routing without the K-tail rule
+    bool test_det_short_slab = false;  // test hook: a deterministic plan's first level of slabs misses a row
 };
 
 namespace sc {
@@ -199,5 +200,10 @@ struct NvtxRange {
 int analyze_impl(int64_t n, const int64_t *colptr, const int32_t *rowind, const sc_options &o,
                  sc_symbolic **out);
 int build_schedule(sc_symbolic *s);
+// Violation kind of the launch plans of a deterministic schedule (0 if none;
+// the level in *bad_level): a product tile split along the inner dimension, or
+// a target row of an RL assembly pair not owned by exactly one slab of its
+// target, or a slab whose pairs are not one target's in source order.
+int det_plan_check(const sc_symbolic *s, int64_t *bad_level);
 int compose_relind(const int32_t *rJC, int64_t lenJC, const int32_t *rCP, int64_t lenCP, int32_t *out);
 }  // namespace sc

@@ -85,7 +85,8 @@ bool consistent(const sc_symbolic &s) {
     if (n < 1 || ns < 1 || ns > n) return false;
     const sc_options &o = s.opt;
     if ((o.variant != SC_RLB && o.variant != SC_RL) || o.precision < SC_FP64 || o.precision > SC_TF32X3 ||
-        o.chunk < 1 || o.chunk > 64 || o.spin_limit < 1)
+        o.chunk < 1 || o.chunk > 64 || o.spin_limit < 1 ||
+        (o.deterministic != 0 && !(o.deterministic == 1 && o.variant == SC_RL)))
         return false;
     auto sz = [](const auto &v, int64_t want) { return (int64_t)v.size() == want; };
     if (!sz(s.colptr, n + 1) || !sz(s.perm, n) || !sz(s.iperm, n) || !sz(s.cparent, n) || !sz(s.sup_of, n) ||

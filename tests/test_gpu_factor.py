@@ -445,3 +445,35 @@ def test_per_level_kernel_wait_times_out_and_handle_recovers(prec):
         assert e.value.code == sc.SC_ERR_TIMEOUT
         num.refactor(A.values)
         assert np.abs(num.export_L() - L0).max() <= 1e-5 * np.abs(L0).max()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-3), ("tf32x3", 1e-3)])
+@pytest.mark.parametrize("name,chunk", [("diff7_24s", 64), ("st27_14", 64), ("lap2d_ragged", 64),
+                                        ("st27_14", 40)])
+def test_deterministic_factor_is_bitwise_reproducible(name, chunk, prec, tol):
+    """Deterministic plans (RL, no inner-dimension splitting, target-owned
+    assembly in source order): three factorizations of the same values give
+    the same bits, and L agrees with the oracle's at the usual bound. The same
+    matrix has split tiles and unordered assembly without the option."""
+    A = inputs.diffusion_3d_7pt(24, 24, 24, seed=7, shift=1e-2) if name == "diff7_24s" else _grid_case(name)
+    kw = dict(ordering="grid_nd", grid=A.grid, merge=0.125, variant="rl", chunk=chunk)
+    sym = sc.Symbolic(A, deterministic=True, **kw)
+    st = sym.plan_stats(prec)
+    assert st["split_tiles"] == 0 and st["rl_slabs"] > 0
+    base = sc.Symbolic(A, **kw).plan_stats(prec)
+    assert base["rl_slabs"] == 0 and base["rl_pairs"] == st["rl_pairs"]
+    Ls = []
+    for _ in range(3):
+        num = sym.factor(A.values, precision=prec)
+        assert num.rc == 0
+        Ls.append(num.export_L())
+        last = num
+    for L in Ls[1:]:
+        assert np.array_equal(L.view(np.uint64), Ls[0].view(np.uint64))
+    o = oracle.Oracle(A, oracle.nd_grid(*A.grid, 8), pr=True, merge=0.125)
+    assert o.factor() == 0
+    _check_L(Ls[0], o.L_supernodal(), tol)
+    B = inputs.rhs(A.n, 2, 21)
+    X, info = last.solve(B)
+    assert info["converged"], info
+    assert oracle.backward_error(A, B, X).max() <= 1e-14

@@ -376,6 +376,72 @@ def test_schedule_check_finds_tensor_core_k_tail():
     assert sc.Symbolic(A, ordering="natural", chunk=64)._perturb_schedule(5) == sc.SC_ERR_UNSUPPORTED
 
 
+@pytest.mark.parametrize("case", ["st27", "aniso", "random", "batch"])
+@pytest.mark.parametrize("chunk", [64, 24])
+def test_deterministic_plan(case, chunk):
+    """A deterministic schedule (RL): the same pairs as without the option, no
+    product tile split along the inner dimension, every target row of every
+    RL assembly pair owned by a slab of its target with the pairs in source
+    order (the schedule check, kind 13, on the FP64 and tensor-core plans); and
+    the option needs the RL variant and matches across a batch."""
+    if case == "st27":
+        A = inputs.workload(3, 0.2)[0]
+        kw = dict(ordering="grid_nd", grid=A.grid, merge=0.125)
+    elif case == "aniso":
+        A = inputs.anisotropic_3d_7pt(20, 14, 11, seed=3, shift=1e-2)
+        kw = dict(ordering="grid_nd", grid=A.grid)
+    elif case == "random":
+        A = inputs.random_spd(500, 0.02, 9)
+        kw = dict(ordering="graph_nd", pr=False)
+    else:
+        mats, _ = inputs.workload(4, 0.05)
+        syms = [sc.Symbolic(M, ordering="grid_nd", grid=M.grid, variant="rl", chunk=chunk, deterministic=True)
+                for M in mats]
+        b = sc.Symbolic.batch(syms)
+        assert b.check_schedule()["ok"]
+        assert b.plan_stats("fp64")["split_tiles"] == 0 and b.plan_stats("fp64")["rl_slabs"] > 0
+        mixed = syms[:1] + [sc.Symbolic(mats[1], ordering="grid_nd", grid=mats[1].grid, variant="rl", chunk=chunk)]
+        with pytest.raises(sc.SCError) as e:
+            sc.Symbolic.batch(mixed)
+        assert e.value.code == -2
+        return
+    det = sc.Symbolic(A, variant="rl", chunk=chunk, deterministic=True, **kw)
+    chk = det.check_schedule()
+    assert chk["ok"], chk
+    plain = sc.Symbolic(A, variant="rl", chunk=chunk, **kw)
+    for prec in ("fp64", "fp32", "tf32"):
+        d, p = det.plan_stats(prec), plain.plan_stats(prec)
+        assert d["split_tiles"] == 0 and p["rl_slabs"] == 0 and d["rl_slabs"] >= 1
+        assert d["rl_pairs"] == p["rl_pairs"] and d["tasks"] == p["tasks"]
+    with pytest.raises(sc.SCError) as e:
+        sc.Symbolic(A, variant="rlb", deterministic=True, **kw)
+    assert e.value.code == -4
+
+
+def test_deterministic_plan_split_tiles_exist_without_it():
+    """The matrices above do split tiles without the option (the critical
+    in-panel updates with K = 64), so the zero counts are not vacuous."""
+    A = inputs.workload(3, 0.2)[0]
+    sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid, merge=0.125, variant="rl")
+    assert sym.plan_stats("fp64")["split_tiles"] > 0
+
+
+def test_schedule_check_finds_unowned_assembly_row():
+    """Test hook 6: the first level of assembly slabs misses a target row; the
+    deterministic-plan check (kind 13) finds it and the handle refuses to
+    factor. Without the option there is nothing to plant."""
+    A = inputs.workload(2, 0.3)[0]
+    kw = dict(ordering="grid_nd", grid=A.grid, variant="rl")
+    sym = sc.Symbolic(A, deterministic=True, **kw)
+    assert sym._perturb_schedule(6) == 0
+    chk = sym.check_schedule()
+    assert not chk["ok"] and chk["kind"] == "deterministic plan", chk
+    with pytest.raises(sc.SCError) as e:
+        sym.factor(A.values)
+    assert e.value.code == sc.SC_ERR_INTERNAL
+    assert sc.Symbolic(A, **kw)._perturb_schedule(6) == sc.SC_ERR_UNSUPPORTED
+
+
 def _dense_spd(n, seed):
     ents = [(i, j) for j in range(n) for i in range(j + 1, n)]
     return inputs.from_lower_pattern(n, ents, seed=seed)
@@ -392,7 +458,7 @@ def _same_handles(a, b, precisions=("fp64", "tf32")):
     assert b.check_schedule()["ok"]
 
 
-@pytest.mark.parametrize("case", ["grid_merge", "rl", "graph_nd", "tuned", "batch"])
+@pytest.mark.parametrize("case", ["grid_merge", "rl", "graph_nd", "tuned", "deterministic", "batch"])
 def test_symbolic_save_load_round_trip(tmp_path, case):
     """A saved analysis loads into a handle equal to the original in every
     exported array and in the launch plan it gives."""
@@ -405,6 +471,8 @@ def test_symbolic_save_load_round_trip(tmp_path, case):
         sym = sc.Symbolic(inputs.random_spd(400, 0.02, 4), ordering="graph_nd", pr=False)
     elif case == "tuned":
         sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid, tune=dict(tile_min_entries=64, thin_dim=4))
+    elif case == "deterministic":
+        sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid, variant="rl", deterministic=True)
     else:
         mats, _ = inputs.workload(4, 0.05)
         sym = sc.Symbolic.batch([sc.Symbolic(M, ordering="grid_nd", grid=M.grid) for M in mats])
