@@ -117,6 +117,10 @@ enum sc_precision { SC_FP64 = 0, SC_FP32 = 1, SC_TF32 = 2, SC_TF32X3 = 3 };
  *                     and the previous level's lookahead products, ordered by
  *                     device-side counters), -1 = one launch per kernel class
  *                     (each class at its own occupancy) [-1]
+ *   tc_wide256        products at least this wide (that would take 128-column
+ *                     tiles) take 256-column tensor-core tiles, which read
+ *                     each A row from shared memory once per 256 outputs
+ *                     (16..2^20; above every product's width = off) [256]
  *   factor_ms         out (sc_tune): median factor time of this setting */
 typedef struct sc_tune_table {
     int32_t tile_min_entries;
@@ -128,7 +132,8 @@ typedef struct sc_tune_table {
     int32_t thin_dim;
     int32_t defer_width;
     int32_t fused;
-    int32_t reserved[5];
+    int32_t tc_wide256;
+    int32_t reserved[4];
     double factor_ms;
 } sc_tune_table;
 
@@ -404,8 +409,9 @@ int sc_probe_fma_peak(int kind, void *cuda_stream, double *flops_per_s);
  * no device memory): out[0..nout) receives, in order, the chunk levels, chunks,
  * product tasks, warp-sized tasks, tiled tasks, SIMT tiles, tensor-core tiles,
  * TRSM tiles, RL assembly pairs, device-loop items, warp-block units, SIMT
- * tiles split along the inner dimension (added atomically) and target-owned RL
- * assembly slabs (deterministic plans). Errors: -1, -2, -3. */
+ * tiles split along the inner dimension (added atomically), target-owned RL
+ * assembly slabs (deterministic plans) and the tensor-core tiles that are 256
+ * columns wide. Errors: -1, -2, -3. */
 int sc_plan_stats(const sc_symbolic *s, int precision, int64_t *out, int nout);
 
 /* Host-side check of the device schedule of s (no device work): recomputes,

@@ -45,12 +45,12 @@ class Options(C.Structure):
 
 
 TUNE_FIELDS = ["tile_min_entries", "tile_min_k", "loop_budget", "lookahead", "tc_min_k", "tc_wide_n", "thin_dim",
-               "defer_width", "fused"]
+               "defer_width", "fused", "tc_wide256"]
 
 
 class TuneTable(C.Structure):
     """sc_tune_table: launch-plan settings (0 = library default)."""
-    _fields_ = [(f, C.c_int32) for f in TUNE_FIELDS] + [("reserved", C.c_int32 * 5), ("factor_ms", C.c_double)]
+    _fields_ = [(f, C.c_int32) for f in TUNE_FIELDS] + [("reserved", C.c_int32 * 4), ("factor_ms", C.c_double)]
 
     def to_dict(self) -> dict:
         d = {f: getattr(self, f) for f in TUNE_FIELDS}
@@ -355,7 +355,7 @@ class Symbolic:
         return out
 
     PLAN_KEYS = ["levels", "chunks", "tasks", "warp_tasks", "tiled_tasks", "simt_tiles", "tc_tiles", "trsm_tiles",
-                 "rl_pairs", "loop_items", "thin_units", "split_tiles", "rl_slabs"]
+                 "rl_pairs", "loop_items", "thin_units", "split_tiles", "rl_slabs", "tc256_tiles"]
 
     CHECK_KINDS = {0: "ok", 1: "source range", 2: "target range", 3: "trapezoid", 4: "not an ancestor",
                    5: "level order", 6: "critical flag", 7: "run mapping", 8: "RL pool", 9: "RL relind",

@@ -289,6 +289,14 @@ int run_levels(sc_numeric *h, cudaStream_t st, Prof *prof = nullptr, cudaStream_
                 E();
                 launches++;
             }
+            if (pl.tc256_cnt) {
+                B(kProfTc);
+                launch_tc_gemm(256, h->precision == SC_TF32X3, (float *)lnz, h->d_tasks, h->d_gemm + pl.tc256_off,
+                               pl.tc256_cnt, h->d_tmaps, h->nmaps, h->d_tmap_of_sn, h->d_err,
+                               (long long)s->opt.spin_limit, h->num_sms, ps);
+                E();
+                launches++;
+            }
             if (pl.tc64_cnt) {
                 B(kProfTc);
                 launch_tc_gemm(64, h->precision == SC_TF32X3, (float *)lnz, h->d_tasks, h->d_gemm + pl.tc64_off,
@@ -527,20 +535,21 @@ void build_plan(const sc_symbolic *s, int precision, Plan &P, bool lookahead) {
         // product tasks: tensor-core tiles (TF32), SIMT tiles, warp tasks
         std::vector<int32_t> ids_small;
         std::vector<ThinUnit> units_thin[2];
-        std::vector<GemmTile> g_simt[2], g_tc[2], g_tc64[2];
+        std::vector<GemmTile> g_simt[2], g_tc[2], g_tc64[2], g_tc256[2];
         const bool split = lookahead;
         for (Task t : L.tasks) {
             int32_t id = (int32_t)P.tasks.size();
             const int cls = split && !(t.flags & kTaskCrit) ? 1 : 0;  // 0 crit, 1 rest
             P.tasks.push_back(t);
-            const int bn = tc ? tc_width(t, tmap_of_sn, s->sup_ptr[t.src + 1] - s->sup_ptr[t.src], kn.tc_min_k,
-                                          kn.tc_wide_n, s->test_tc_ignore_tail)
-                             : 0;
+            int bn = tc ? tc_width(t, tmap_of_sn, s->sup_ptr[t.src + 1] - s->sup_ptr[t.src], kn.tc_min_k,
+                                    kn.tc_wide_n, s->test_tc_ignore_tail)
+                        : 0;
+            if (bn == 128 && t.n >= kn.tc_wide256) bn = 256;
             if (is_small(t)) {
                 ids_small.push_back(id);
                 P.class_flops[kProfSmall] += task_flops(t);
             } else if (bn) {
-                tc_tiles_of(t, id, bn, bn == 128 ? g_tc[cls] : g_tc64[cls]);
+                tc_tiles_of(t, id, bn, bn == 256 ? g_tc256[cls] : bn == 128 ? g_tc[cls] : g_tc64[cls]);
                 P.class_flops[kProfTc] += task_flops(t);
             } else if (std::min(t.m, t.n) <= std::min(kn.thin_dim, kThinDim) && !(t.flags & kTaskStoreU)) {
                 // a 64 x 64 tile would be mostly padding: warp blocks, kThinWarps per CTA
@@ -564,6 +573,9 @@ void build_plan(const sc_symbolic *s, int precision, Plan &P, bool lookahead) {
             pl.tc64_off = (int32_t)P.gemm.size();
             P.gemm.insert(P.gemm.end(), g_tc64[cls].begin(), g_tc64[cls].end());
             pl.tc64_cnt = (int32_t)g_tc64[cls].size();
+            pl.tc256_off = (int32_t)P.gemm.size();
+            P.gemm.insert(P.gemm.end(), g_tc256[cls].begin(), g_tc256[cls].end());
+            pl.tc256_cnt = (int32_t)g_tc256[cls].size();
             pl.thin_off = (int32_t)P.thin.size();
             P.thin.insert(P.thin.end(), units_thin[cls].begin(), units_thin[cls].end());
             pl.thin_cnt = (int32_t)units_thin[cls].size();
@@ -650,7 +662,7 @@ int det_plan_check(const sc_symbolic *s, int64_t *bad_level) {
             };
             for (const ProdLists *pl : {&p.crit, &p.rest})
                 if (split_in(pl->gemm_off, pl->gemm_cnt) || split_in(pl->tc_off, pl->tc_cnt) ||
-                    split_in(pl->tc64_off, pl->tc64_cnt))
+                    split_in(pl->tc64_off, pl->tc64_cnt) || split_in(pl->tc256_off, pl->tc256_cnt))
                     return 13;
             if (split_in(p.rlg_off, p.rlg_cnt)) return 13;
             if (!p.rlp_cnt) continue;
@@ -698,15 +710,17 @@ int plan_stats(const sc_symbolic *s, int precision, int64_t *out, int nout) {
     int64_t small_tasks = 0, tile_tasks = 0;
     for (const LevelPlan &l : P.levels) small_tasks += l.small_cnt + l.rls_cnt;
     tile_tasks = (int64_t)P.tasks.size() - small_tasks;
-    int64_t tc_tiles = 0, simt_tiles = 0, split_tiles = 0;
+    int64_t tc_tiles = 0, simt_tiles = 0, split_tiles = 0, tc256_tiles = 0;
     for (const LevelPlan &l : P.levels) {
-        tc_tiles += l.crit.tc_cnt + l.crit.tc64_cnt + l.rest.tc_cnt + l.rest.tc64_cnt;
+        tc256_tiles += l.crit.tc256_cnt + l.rest.tc256_cnt;
+        tc_tiles += l.crit.tc_cnt + l.crit.tc64_cnt + l.crit.tc256_cnt + l.rest.tc_cnt + l.rest.tc64_cnt +
+                    l.rest.tc256_cnt;
         simt_tiles += l.crit.gemm_cnt + l.rest.gemm_cnt + l.rlg_cnt;
     }
     for (const GemmTile &g : P.gemm) split_tiles += g.ks >= 0;
     int64_t v[] = {(int64_t)P.levels.size(), (int64_t)P.cd.size(), (int64_t)P.tasks.size(), small_tasks, tile_tasks,
                    simt_tiles, tc_tiles, (int64_t)P.trsm.size(), (int64_t)P.rlpairs.size(), (int64_t)P.loops.size(),
-                   (int64_t)P.thin.size(), split_tiles, (int64_t)P.rlslabs.size()};
+                   (int64_t)P.thin.size(), split_tiles, (int64_t)P.rlslabs.size(), tc256_tiles};
     for (int i = 0; i < nout && i < (int)(sizeof(v) / sizeof(v[0])); i++) out[i] = v[i];
     return SC_OK;
 }

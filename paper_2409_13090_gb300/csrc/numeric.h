@@ -16,8 +16,9 @@ struct ProdLists {
     int32_t gemm_off = 0, gemm_cnt = 0;     // GemmTile (SIMT)
     int32_t tc_off = 0, tc_cnt = 0;         // GemmTile (tensor cores, 128-column tiles)
     int32_t tc64_off = 0, tc64_cnt = 0;     // GemmTile (tensor cores, 64-column tiles)
+    int32_t tc256_off = 0, tc256_cnt = 0;   // GemmTile (tensor cores, 256-column tiles)
     int32_t thin_off = 0, thin_cnt = 0;     // ThinUnits of tasks with min(m, n) <= 8 (warp-block kernel)
-    bool any() const { return gemm_cnt || tc_cnt || tc64_cnt || thin_cnt; }
+    bool any() const { return gemm_cnt || tc_cnt || tc64_cnt || tc256_cnt || thin_cnt; }
 };
 
 // Launch plan of one level: offsets/counts into the flat device work lists.

@@ -52,6 +52,7 @@ struct Knobs {
     int tc_min_k = 32, tc_wide_n = 96, thin_dim = 8;
     int defer_width = 256;
     bool fused = false;
+    int tc_wide256 = 256;
 };
 inline Knobs knobs_of(const sc_tune_table &t) {
     Knobs k;
@@ -64,6 +65,7 @@ inline Knobs knobs_of(const sc_tune_table &t) {
     if (t.thin_dim) k.thin_dim = t.thin_dim < 0 ? 0 : t.thin_dim;
     if (t.defer_width) k.defer_width = t.defer_width;
     if (t.fused) k.fused = t.fused > 0;
+    if (t.tc_wide256) k.tc_wide256 = t.tc_wide256;
     return k;
 }
 // Inner-dimension granularity of one tcgen05.mma of kind::tf32 (K = 8): the
@@ -71,7 +73,8 @@ inline Knobs knobs_of(const sc_tune_table &t) {
 // its source panel.
 constexpr int kTcKStep = 8;
 
-// Tile width of a product on the tensor cores: 128 or 64 columns, or 0 when the
+// Tile width of a product on the tensor cores: 128 or 64 columns (the launch
+// plan widens a 128 to 256 for n >= the tc_wide256 setting), or 0 when the
 // product stays on the SIMT units. Needs a tensor map of the source panel
 // (src_width = |J| >= 16: 16-byte row stride), K >= 32 and m >= 64; min_k
 // (>= 32) and wide_n (>= 16) are the plan's thresholds. The tile consumes K in
@@ -79,9 +82,13 @@ constexpr int kTcKStep = 8;
 // only where the product's columns end at the panel's last real column (the
 // columns after it are zero padding or outside the tensor map, read as zero):
 // elsewhere the step would multiply the next columns of the panel in.
-// ignore_tail (a test hook only) drops that condition.
+// ignore_tail (a test hook only) drops that condition. The tile's TMA loads
+// start at column kx0, which must be 16-byte aligned (kx0 % 4 == 0); the
+// schedule gives every K >= 32 product a kx0 that is a multiple of its K or 0,
+// so this holds for every routed product, and the rule keeps it so.
 inline int tc_route_width(const Task &t, int src_width, int min_k, int wide_n, bool ignore_tail = false) {
     if (src_width < 16 || t.k < 32 || t.k < min_k || t.m < 64 || (t.flags & kTaskStoreU)) return 0;
+    if (t.kx0 % 4 != 0) return 0;
     if (!ignore_tail && t.k % kTcKStep != 0 && t.kx0 + t.k < src_width) return 0;
     if (t.n >= wide_n && t.n >= 16) return 128;
     if (t.n >= 16) return 64;
@@ -94,7 +101,7 @@ inline bool tune_valid(const sc_tune_table &t) {
     return in(t.tile_min_entries, 1, 1 << 24) && in(t.tile_min_k, 1, 1 << 16) && in(t.loop_budget, 256, 1 << 28) &&
            (t.lookahead >= -1 && t.lookahead <= 1) && in(t.tc_min_k, 32, 1 << 16) && in(t.tc_wide_n, 16, 1 << 16) &&
            (t.thin_dim == -1 || in(t.thin_dim, 1, 8)) && in(t.defer_width, 256, 1 << 20) &&
-           (t.fused >= -1 && t.fused <= 1);
+           (t.fused >= -1 && t.fused <= 1) && in(t.tc_wide256, 16, 1 << 20);
 }
 
 // Part of Alg. 5's inner loops for one block B of supernode J, run on the

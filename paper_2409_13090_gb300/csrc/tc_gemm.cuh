@@ -37,14 +37,21 @@ constexpr int kThreads = 32 * (2 + kEpiWarps);  // producer warp, MMA warp, epil
 // X3: the three-product split form (SC_TF32X3): a stage holds hi and lo tiles
 // of A and B (A_hi, A_lo, B_hi, B_lo), and each K step issues hi*hi, hi*lo,
 // lo*hi into the same accumulator.
+// BN = 256: half the shared-memory operand reads per flop of A (each A row
+// meets 256 B rows per MMA); a stage is 48 KB (96 KB for X3), so X3 keeps two
+// stages, and the two accumulators fill the SM's 512 TMEM columns.
 template <int BN, bool X3>
 struct Cfg {
     static constexpr int B_BYTES = BN * BK * 4;
     static constexpr int NSPLIT = X3 ? 2 : 1;
-    static constexpr int STAGES = X3 ? 3 : 4;
+    static constexpr int STAGES = X3 ? (BN == 256 ? 2 : 3) : 4;
     static constexpr int STAGE_BYTES = NSPLIT * (A_BYTES + B_BYTES);
     static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*alignment*/ + 256 /*barriers*/;
     static constexpr int TMEM_COLS = 2 * BN;  // two accumulators
+    static_assert(SMEM <= 227 * 1024, "shared memory per CTA");
+    // 512 columns: no other tensor-core CTA fits beside this one's shared memory, so the
+    // allocation never waits for another CTA's columns
+    static_assert(TMEM_COLS <= 512, "TMEM columns per SM");
     static constexpr int CTAS_PER_SM = (BN == 64 && !X3) ? 2 : 1;
     // instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major, M = 128, N = BN
     static constexpr uint32_t IDESC =
@@ -227,7 +234,7 @@ __global__ void __launch_bounds__(kThreads, (Cfg<BN, X3>::CTAS_PER_SM))
                 const Task tk = tasks[tl.task];
                 const int mi = tmap_of_sn[tk.src];
                 const CUtensorMap *amap = tmaps + 2 * mi;
-                const CUtensorMap *bmap = tmaps + 2 * mi + (BN == BM ? 0 : 1);
+                const CUtensorMap *bmap = tmaps + 2 * mi + (BN == 64 ? 1 : 0);  // 128-row boxes (two for BN = 256)
                 const int nk = (tk.k + BK - 1) / BK;
                 const int ay = tk.a_row + tl.tm * BM, by = tk.b_row + tl.tn * BN;
                 for (int kb = 0; kb < nk; kb++, g++) {
@@ -240,11 +247,14 @@ __global__ void __launch_bounds__(kThreads, (Cfg<BN, X3>::CTAS_PER_SM))
                     const uint32_t fb = smem_u32(full + s);
                     mbar_expect_tx(fb, C::STAGE_BYTES);
                     const int x = tk.kx0 + kb * BK;
-                    tma_load_2d(a_tile<BN, X3>(smem, s, 0), amap, x, ay, fb);
-                    tma_load_2d(b_tile<BN, X3>(smem, s, 0), bmap, x, by, fb);
-                    if constexpr (X3) {
-                        tma_load_2d(a_tile<BN, X3>(smem, s, 1), amap + 2 * lo_maps, x, ay, fb);
-                        tma_load_2d(b_tile<BN, X3>(smem, s, 1), bmap + 2 * lo_maps, x, by, fb);
+                    // a 256-row B tile is two 128-row boxes: with the 128-byte swizzle, rows
+                    // sit in 1024-byte groups of 8, so the second box continues the first's layout
+                    for (int part = 0; part < C::NSPLIT; part++) {
+                        const CUtensorMap *ap = amap + 2 * lo_maps * part, *bp = bmap + 2 * lo_maps * part;
+                        tma_load_2d(a_tile<BN, X3>(smem, s, part), ap, x, ay, fb);
+                        tma_load_2d(b_tile<BN, X3>(smem, s, part), bp, x, by, fb);
+                        if constexpr (BN == 256)
+                            tma_load_2d(b_tile<BN, X3>(smem, s, part) + 128 * BK * 4, bp, x, by + 128, fb);
                     }
                 }
             }
@@ -345,7 +355,11 @@ __global__ void __launch_bounds__(kThreads, (Cfg<BN, X3>::CTAS_PER_SM))
 // ---------------------------------------------------------------- host side
 inline bool tc_gemm_init() {
     using namespace tc;
-    return cudaFuncSetAttribute(k_tc_gemm<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_tc_gemm<256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                Cfg<256, false>::SMEM) == cudaSuccess &&
+           cudaFuncSetAttribute(k_tc_gemm<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                Cfg<256, true>::SMEM) == cudaSuccess &&
+           cudaFuncSetAttribute(k_tc_gemm<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 Cfg<128, false>::SMEM) == cudaSuccess &&
            cudaFuncSetAttribute(k_tc_gemm<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 Cfg<64, false>::SMEM) == cudaSuccess &&
@@ -424,7 +438,10 @@ inline void launch_tc(float *lnz, const Task *tasks, const GemmTile *tiles, int3
 inline void launch_tc_gemm(int bn, bool x3, float *lnz, const Task *tasks, const GemmTile *tiles, int32_t count,
                            const CUtensorMap *maps, int nmaps, const int32_t *tmap_of_sn, int32_t *err,
                            long long spin_limit, int num_sms, cudaStream_t st) {
-    if (bn == 128) {
+    if (bn == 256) {
+        if (x3) launch_tc<256, true>(lnz, tasks, tiles, count, maps, nmaps, tmap_of_sn, err, spin_limit, num_sms, st);
+        else launch_tc<256, false>(lnz, tasks, tiles, count, maps, nmaps, tmap_of_sn, err, spin_limit, num_sms, st);
+    } else if (bn == 128) {
         if (x3) launch_tc<128, true>(lnz, tasks, tiles, count, maps, nmaps, tmap_of_sn, err, spin_limit, num_sms, st);
         else launch_tc<128, false>(lnz, tasks, tiles, count, maps, nmaps, tmap_of_sn, err, spin_limit, num_sms, st);
     } else {

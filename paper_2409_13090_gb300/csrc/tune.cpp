@@ -28,7 +28,8 @@ bool same_knobs(const sc_tune_table &a, const sc_tune_table &b) {
     const sc::Knobs x = sc::knobs_of(a), y = sc::knobs_of(b);
     return x.tile_min_entries == y.tile_min_entries && x.tile_min_k == y.tile_min_k &&
            x.loop_budget == y.loop_budget && x.lookahead == y.lookahead && x.tc_min_k == y.tc_min_k &&
-           x.tc_wide_n == y.tc_wide_n && x.thin_dim == y.thin_dim && x.defer_width == y.defer_width && x.fused == y.fused;
+           x.tc_wide_n == y.tc_wide_n && x.thin_dim == y.thin_dim && x.defer_width == y.defer_width && x.fused == y.fused &&
+           x.tc_wide256 == y.tc_wide256;
 }
 
 double median(std::vector<double> v) {
@@ -106,6 +107,7 @@ extern "C" int sc_tune(sc_symbolic *s, const double *values, int values_on_devic
         {&sc_tune_table::thin_dim, {8, 4, -1}, false, false, false},
         {&sc_tune_table::tc_min_k, {32, 64, 128}, false, true, false},
         {&sc_tune_table::tc_wide_n, {64, 96, 128}, false, true, false},
+        {&sc_tune_table::tc_wide256, {384, 1 << 20}, false, true, false},
     };
     bool dirty = false;  // the schedule in s is not the one of `cur`
     for (const Field &f : fields) {

@@ -266,6 +266,24 @@ def test_tune_table_changes_only_the_launch_plan():
     assert 0 < wtf["tc_tiles"] <= btf["tc_tiles"]
 
 
+def test_256_column_tiles_only_in_tensor_core_plans():
+    """The 256-column tensor-core tiles take the products at least tc_wide256
+    wide that would take 128-column tiles: the tensor-core plans have them
+    (fewer tiles in all), the FP64 / FP32 plans none, and with the setting
+    above every width the plan is the 128-column one."""
+    A = _dense_spd(1100, 4)
+    sym = sc.Symbolic(A, ordering="natural")
+    off = sc.Symbolic(A, ordering="natural", tune=dict(tc_wide256=1 << 20))
+    for prec in ("tf32", "tf32x3"):
+        s, o = sym.plan_stats(prec), off.plan_stats(prec)
+        assert s["tc256_tiles"] > 0 and o["tc256_tiles"] == 0
+        assert 0 < s["tc_tiles"] < o["tc_tiles"]
+        assert s["tasks"] == o["tasks"] and s["simt_tiles"] == o["simt_tiles"]
+    for prec in ("fp64", "fp32"):
+        assert sym.plan_stats(prec)["tc256_tiles"] == 0 and sym.plan_stats(prec)["tc_tiles"] == 0
+    assert sym.check_schedule()["ok"]
+
+
 def test_deferral_depth_changes_only_the_in_panel_products():
     """A third level of trailing-update deferral (outer blocks of 1024 or 4096
     columns) regroups the in-supernode products: the same flops in fewer
@@ -293,7 +311,8 @@ def test_deferral_depth_changes_only_the_in_panel_products():
     assert passes(4096) == base
 
 
-@pytest.mark.parametrize("bad", [dict(lookahead=2), dict(tc_min_k=16), dict(tc_wide_n=8), dict(thin_dim=9),
+@pytest.mark.parametrize("bad", [dict(lookahead=2), dict(tc_min_k=16), dict(tc_wide_n=8), dict(tc_wide256=8),
+                                 dict(thin_dim=9),
                                  dict(thin_dim=-2), dict(loop_budget=100), dict(tile_min_entries=-1),
                                  dict(defer_width=128), dict(defer_width=1 << 21)])
 def test_tune_table_ranges(bad):
