@@ -121,6 +121,10 @@ enum sc_precision { SC_FP64 = 0, SC_FP32 = 1, SC_TF32 = 2, SC_TF32X3 = 3 };
  *                     tiles) take 256-column tensor-core tiles, which read
  *                     each A row from shared memory once per 256 outputs
  *                     (16..2^20; above every product's width = off) [256]
+ *   solve_group       the solve sweeps' units: a wide chunk's row tiles after
+ *                     its first, taken by one CTA in runs of up to this many
+ *                     (1..1024): fewer CTAs wait for one chunk's solution, at
+ *                     the price of later arrivals from a run's last tiles [4]
  *   factor_ms         out (sc_tune): median factor time of this setting */
 typedef struct sc_tune_table {
     int32_t tile_min_entries;
@@ -133,7 +137,8 @@ typedef struct sc_tune_table {
     int32_t defer_width;
     int32_t fused;
     int32_t tc_wide256;
-    int32_t reserved[4];
+    int32_t solve_group;
+    int32_t reserved[3];
     double factor_ms;
 } sc_tune_table;
 

@@ -457,10 +457,12 @@ class GraphND {
             if (2 * cum >= (int64_t)S.size()) break;
         }
         std::vector<int32_t> left, right, sep = L[k];
-        if (!multilevel_ || (int64_t)S.size() < ml::kMinSet || !ml_split(S, st, sep.size(), left, right, sep))
-            for (size_t q = 0; q < L.size(); q++)
+        if (!multilevel_ || (int64_t)S.size() < ml::kMinSet || !ml_split(S, st, sep.size(), left, right, sep)) {
+            for (size_t q = 0; q < L.size(); q++) {
                 if (q < k) left.insert(left.end(), L[q].begin(), L[q].end());
                 else if (q > k) right.insert(right.end(), L[q].begin(), L[q].end());
+            }
+        }
         std::sort(left.begin(), left.end());
         std::sort(right.begin(), right.end());
         std::sort(sep.begin(), sep.end());

@@ -218,7 +218,6 @@ extern "C" int sc_check_schedule(const sc_symbolic *s, int64_t *out, int nout) {
     if (nout > 0 && !out) return -2;
     try {
         Checker ck(s);
-        const bool rl = s->opt.variant == SC_RL;
         int64_t tasks = 0, products = 0, entries = 0, bad_level = -1, bad_kind = 0;
         for (size_t lv = 0; lv < s->levels.size() && !bad_kind; lv++) {
             const Level &L = s->levels[lv];

@@ -27,11 +27,10 @@ struct TrsmTile {
 // What a CTA of a persistent solve sweep takes at once: tile t0 alone (cnt 0:
 // the first tile of a wide chunk), narrow tiles t0 .. t0 + cnt - 1, one per
 // warp (cnt 1..8), or -cnt further tiles t0 .. t0 - cnt - 1 of one wide chunk,
-// one after another (cnt -1..-kSolveGroup).
+// one after another (cnt -1..-solve_group, a launch-plan setting).
 struct SolveUnit {
     int32_t t0, cnt;
 };
-constexpr int kSolveGroup = 4;
 
 // One output tile of a product task. ks < 0: the whole inner dimension;
 // ks >= 0: only its slice [ks * S, (ks + 1) * S), added atomically, with

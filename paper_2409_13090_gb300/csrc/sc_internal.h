@@ -53,6 +53,7 @@ struct Knobs {
     int defer_width = 256;
     bool fused = false;
     int tc_wide256 = 256;
+    int solve_group = 4;
 };
 inline Knobs knobs_of(const sc_tune_table &t) {
     Knobs k;
@@ -66,6 +67,7 @@ inline Knobs knobs_of(const sc_tune_table &t) {
     if (t.defer_width) k.defer_width = t.defer_width;
     if (t.fused) k.fused = t.fused > 0;
     if (t.tc_wide256) k.tc_wide256 = t.tc_wide256;
+    if (t.solve_group) k.solve_group = t.solve_group;
     return k;
 }
 // Inner-dimension granularity of one tcgen05.mma of kind::tf32 (K = 8): the
@@ -101,7 +103,8 @@ inline bool tune_valid(const sc_tune_table &t) {
     return in(t.tile_min_entries, 1, 1 << 24) && in(t.tile_min_k, 1, 1 << 16) && in(t.loop_budget, 256, 1 << 28) &&
            (t.lookahead >= -1 && t.lookahead <= 1) && in(t.tc_min_k, 32, 1 << 16) && in(t.tc_wide_n, 16, 1 << 16) &&
            (t.thin_dim == -1 || in(t.thin_dim, 1, 8)) && in(t.defer_width, 256, 1 << 20) &&
-           (t.fused >= -1 && t.fused <= 1) && in(t.tc_wide256, 16, 1 << 20);
+           (t.fused >= -1 && t.fused <= 1) && in(t.tc_wide256, 16, 1 << 20) &&
+           in(t.solve_group, 1, 1024);
 }
 
 // Part of Alg. 5's inner loops for one block B of supernode J, run on the

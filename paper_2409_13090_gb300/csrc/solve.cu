@@ -976,10 +976,11 @@ int ensure_solve(sc_numeric *h, int64_t nrhs) {
         }
         // grab units in level order: the first tile of a chunk wider than kSmallW
         // alone (one CTA; the chunk's step on the chain), its other tiles in runs of
-        // up to kSolveGroup (one CTA, one after another), else up to eight
+        // up to solve_group (one CTA, one after another), else up to eight
         // consecutive narrow tiles of one level (a warp each)
         std::vector<SolveUnit> units;
         {
+            const size_t group = (size_t)knobs_of(s->tune).solve_group;
             size_t t = 0;
             for (size_t lv = 0; lv < s->levels.size(); lv++) {
                 size_t tend = t;
@@ -993,7 +994,7 @@ int ensure_solve(sc_numeric *h, int64_t nrhs) {
                             continue;
                         }
                         size_t e = t;
-                        while (e < tend && e - t < (size_t)kSolveGroup && tiles[e].chunk == tiles[t].chunk &&
+                        while (e < tend && e - t < group && tiles[e].chunk == tiles[t].chunk &&
                                tiles[e].r0 != cw.c0 + cw.w)
                             e++;
                         units.push_back(SolveUnit{(int32_t)t, -(int32_t)(e - t)});

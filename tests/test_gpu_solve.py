@@ -84,3 +84,22 @@ def test_cg_with_low_precision_factor_reaches_fp64_backward_error(prec):
     X, info = num.solve(B, method="cg", max_iterations=400)
     assert info["converged"], info
     assert oracle.backward_error(A, B, X).max() <= 1e-14
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("group", [1, 3, 7, 16])
+def test_solve_group_sizes(prec, group):
+    """Runs of 1, 3, 7 and 16 row tiles per sweep unit (the solve_group
+    setting; 4 by default): the same solution as the oracle's, ragged last
+    runs included, for 5 right-hand sides."""
+    A = inputs.diffusion_3d_7pt(14, 12, 10, seed=21, shift=1e-2)
+    sym = sc.Symbolic(A, ordering="grid_nd", grid=A.grid, tune=dict(solve_group=group))
+    num = sym.factor(A.values, precision=prec)
+    assert num.rc == 0
+    B = inputs.rhs(A.n, 5, 22)
+    X, info = num.solve(B)
+    assert oracle.backward_error(A, B, X).max() <= 1e-14, info
+    o = oracle.Oracle(A, oracle.nd_grid(*A.grid, 8), pr=True)
+    assert o.factor() == 0
+    Xo = o.solve(B)
+    assert np.abs(X - Xo).max() <= 1e-8 * np.abs(Xo).max()

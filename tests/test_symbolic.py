@@ -312,6 +312,7 @@ def test_deferral_depth_changes_only_the_in_panel_products():
 
 
 @pytest.mark.parametrize("bad", [dict(lookahead=2), dict(tc_min_k=16), dict(tc_wide_n=8), dict(tc_wide256=8),
+                                 dict(solve_group=2000),
                                  dict(thin_dim=9),
                                  dict(thin_dim=-2), dict(loop_budget=100), dict(tile_min_entries=-1),
                                  dict(defer_width=128), dict(defer_width=1 << 21)])
