@@ -124,7 +124,8 @@ enum sc_precision { SC_FP64 = 0, SC_FP32 = 1, SC_TF32 = 2, SC_TF32X3 = 3 };
  *   solve_group       the solve sweeps' units: a wide chunk's row tiles after
  *                     its first, taken by one CTA in runs of up to this many
  *                     (1..1024): fewer CTAs wait for one chunk's solution, at
- *                     the price of later arrivals from a run's last tiles [4]
+ *                     the price of later arrivals from a run's last tiles
+ *                     [2 for FP64 factors, 4 for FP32 / TF32 / TF32x3]
  *   factor_ms         out (sc_tune): median factor time of this setting */
 typedef struct sc_tune_table {
     int32_t tile_min_entries;

@@ -101,7 +101,7 @@ struct sc_numeric {
     int32_t stall_factor_chunk = -1;  // test hook: chunk whose k_level count target is raised by one
     void *d_xw = nullptr;           // permuted right-hand side / forward work vector
     sc::TrsmTile *d_solve_tiles = nullptr;
-    sc::SolveUnit *d_solve_units = nullptr;
+    sc::SolveUnit *d_solve_units = nullptr;  // per level its first tiles, then the rest (backward: reversed)
     int64_t solve_cap = 0;          // rhs capacity of the work vectors
     double *d_x = nullptr, *d_r = nullptr, *d_b = nullptr, *d_xbest = nullptr;
     void *d_y = nullptr, *d_z = nullptr, *d_acc = nullptr;  // permuted work vectors (storage precision)

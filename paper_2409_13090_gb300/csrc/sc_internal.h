@@ -53,7 +53,7 @@ struct Knobs {
     int defer_width = 256;
     bool fused = false;
     int tc_wide256 = 256;
-    int solve_group = 4;
+    int solve_group = 0;  // 0: by the factor's precision (2 FP64, 4 FP32)
 };
 inline Knobs knobs_of(const sc_tune_table &t) {
     Knobs k;

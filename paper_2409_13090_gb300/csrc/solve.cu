@@ -980,7 +980,9 @@ int ensure_solve(sc_numeric *h, int64_t nrhs) {
         // consecutive narrow tiles of one level (a warp each)
         std::vector<SolveUnit> units;
         {
-            const size_t group = (size_t)knobs_of(s->tune).solve_group;
+            // runs of 2 tiles for FP64 factors (two sweep CTAs per SM), 4 for FP32
+            const int kg = knobs_of(s->tune).solve_group;
+            const size_t group = (size_t)(kg > 0 ? kg : h->elt == 8 ? 2 : 4);
             size_t t = 0;
             for (size_t lv = 0; lv < s->levels.size(); lv++) {
                 size_t tend = t;
@@ -1008,9 +1010,34 @@ int ensure_solve(sc_numeric *h, int64_t nrhs) {
                 }
             }
         }
+        // per level its first tiles, then its other units: the forward sweep
+        // starts every chunk's diagonal step of a level at once and its runs,
+        // taken after them, find y_c published sooner; the backward sweep (the
+        // reverse order) takes a level's runs of every chunk before its first
+        // tiles, which wait for them
+        std::vector<SolveUnit> funits;
+        funits.reserve(units.size());
+        {
+            size_t u = 0;
+            for (size_t lv = 0; lv < s->levels.size(); lv++) {
+                size_t tend = 0;
+                for (int32_t c : s->levels[lv].chunks) tend += ntiles[c];
+                const size_t u0 = u;
+                size_t seen = 0;
+                while (u < units.size() && seen < tend) {
+                    const SolveUnit su = units[u++];
+                    seen += su.cnt > 0 ? su.cnt : su.cnt < 0 ? -su.cnt : 1;
+                }
+                for (size_t q = u0; q < u; q++)
+                    if (units[q].cnt == 0) funits.push_back(units[q]);
+                for (size_t q = u0; q < u; q++)
+                    if (units[q].cnt != 0) funits.push_back(units[q]);
+            }
+        }
+        if (funits.size() != units.size()) return SC_ERR_INTERNAL;
         h->solve_tiles = (int32_t)units.size();
         if ((rc = up(h->d_solve_tiles, tiles))) return rc;
-        if ((rc = up(h->d_solve_units, units))) return rc;
+        if ((rc = up(h->d_solve_units, funits))) return rc;
         if ((rc = up(h->d_dep_ptr, dep_ptr))) return rc;
         if ((rc = up(h->d_dep, dep))) return rc;
         // constants: tile counts [nchunks], then expected forward arrivals [nchunks]
