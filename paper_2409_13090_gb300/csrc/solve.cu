@@ -56,7 +56,9 @@ inline int rhs_per_thread(int nb) {
 // narrow-tile path: 8 warps x kSmallW rows)
 template <typename T>
 size_t solve_smem(int nb) {
-    return sizeof(T) * (2 * (size_t)kMaxChunk * (kMaxChunk + 1) + 2 * (size_t)kMaxChunk * rhs_ld(nb));
+    // + 16 elements: a product thread's 16-byte loads of b may run up to 15
+    // elements past its row's last right-hand side (those values are not used)
+    return sizeof(T) * (2 * (size_t)kMaxChunk * (kMaxChunk + 1) + 2 * (size_t)kMaxChunk * rhs_ld(nb) + 16);
 }
 
 // Loads a rows x w block (row stride ld) into shared memory dst[r][c] with a
@@ -180,48 +182,82 @@ __device__ void warp_upper_solve(const T (*m)[kMaxChunk + 1], const T *rinv, int
     if (lane + 32 < w) x1 *= rinv[lane + 32];
 }
 
-// Block product of the sweeps, register-blocked over right-hand sides: the
-// thread forms o[j] = sum_k a(i, k) b[k][r0 + j], j < RPT, with a(i, k) =
-// a[i][k] (or a[k][i] when kTrans) and b of row stride ldb. The 64 threads of
-// one group read a at consecutive banks and b as broadcast 16-byte words (FP32,
-// RPT a multiple of 4) or 16-byte pairs (FP64, RPT even).
-// rhs_product_acc adds the product into o; rhs_product overwrites it.
+// Thread mapping of the sweeps' block products (256 threads over a 64-row
+// block and up to 64 right-hand sides): NR rows per thread, from i, R
+// right-hand sides per row from r0. FP32 blocks of more than 16 right-hand
+// sides take two rows (i and i + 32) of 8 or 4 right-hand sides: the rows share
+// the thread's loads of b, 4 shared-memory wavefronts per 16 multiply-adds
+// instead of 5; otherwise one row i of RPT right-hand sides.
+template <typename T, int RPT>
+struct RhsMap {
+    static constexpr int NR = (sizeof(T) == 4 && RPT >= 8) ? 2 : 1;
+    static constexpr int R = RPT / NR;
+    static constexpr int kStep = kMaxChunk / NR;
+    int i, r0;
+    __device__ __forceinline__ RhsMap() : i((int)threadIdx.x % kStep), r0(((int)threadIdx.x / kStep) * R) {}
+    __device__ __forceinline__ int row(int h) const { return i + h * kStep; }
+};
+
+// Block product of the sweeps, register-blocked over rows and right-hand
+// sides: o[h][j] = sum_{k < K} a(row(h), k) b[k][r0 + j], with a(r, k) = a[r][k]
+// (or a[k][r] when kTrans) and b of row stride ldb. A warp reads a at
+// consecutive banks and b as broadcast 16-byte words (FP32, R a multiple of 4)
+// or 16-byte pairs (FP64, R even). Rows past the caller's range are formed from
+// whatever the buffer holds and not used. rhs_product_acc adds into o;
+// rhs_product overwrites it.
 template <typename T, int RPT, bool kTrans>
-__device__ __forceinline__ void rhs_product_acc(const T (*a)[kMaxChunk + 1], const T *__restrict__ b, int ldb, int i,
-                                                int r0, int K, T (&o)[RPT]) {
+__device__ __forceinline__ void rhs_product_acc(const T (*a)[kMaxChunk + 1], const T *__restrict__ b, int ldb,
+                                                const RhsMap<T, RPT> &m, int K,
+                                                T (&o)[RhsMap<T, RPT>::NR][RhsMap<T, RPT>::R]) {
+    constexpr int NR = RhsMap<T, RPT>::NR, R = RhsMap<T, RPT>::R;
 #pragma unroll 4
     for (int k = 0; k < K; k++) {
-        const T av = kTrans ? a[k][i] : a[i][k];
-        const T *bk = b + k * ldb + r0;
-        if constexpr (sizeof(T) == 4 && RPT % 4 == 0) {
+        T av[NR];
 #pragma unroll
-            for (int j = 0; j < RPT; j += 4) {
+        for (int h = 0; h < NR; h++) av[h] = kTrans ? a[k][m.row(h)] : a[m.row(h)][k];
+        const T *bk = b + k * ldb + m.r0;
+        if constexpr (sizeof(T) == 4 && R % 4 == 0) {
+#pragma unroll
+            for (int j = 0; j < R; j += 4) {
                 const float4 bv = *reinterpret_cast<const float4 *>(bk + j);
-                o[j] += av * bv.x;
-                o[j + 1] += av * bv.y;
-                o[j + 2] += av * bv.z;
-                o[j + 3] += av * bv.w;
-            }
-        } else if constexpr (sizeof(T) == 8 && RPT % 2 == 0) {
 #pragma unroll
-            for (int j = 0; j < RPT; j += 2) {
+                for (int h = 0; h < NR; h++) {
+                    o[h][j] += av[h] * bv.x;
+                    o[h][j + 1] += av[h] * bv.y;
+                    o[h][j + 2] += av[h] * bv.z;
+                    o[h][j + 3] += av[h] * bv.w;
+                }
+            }
+        } else if constexpr (sizeof(T) == 8 && R % 2 == 0) {
+#pragma unroll
+            for (int j = 0; j < R; j += 2) {
                 const double2 bv = *reinterpret_cast<const double2 *>(bk + j);
-                o[j] += av * bv.x;
-                o[j + 1] += av * bv.y;
+#pragma unroll
+                for (int h = 0; h < NR; h++) {
+                    o[h][j] += av[h] * bv.x;
+                    o[h][j + 1] += av[h] * bv.y;
+                }
             }
         } else {
 #pragma unroll
-            for (int j = 0; j < RPT; j++) o[j] += av * bk[j];
+            for (int j = 0; j < R; j++) {
+                const T bj = bk[j];
+#pragma unroll
+                for (int h = 0; h < NR; h++) o[h][j] += av[h] * bj;
+            }
         }
     }
 }
 
 template <typename T, int RPT, bool kTrans>
-__device__ __forceinline__ void rhs_product(const T (*a)[kMaxChunk + 1], const T *__restrict__ b, int ldb, int i,
-                                            int r0, int K, T (&o)[RPT]) {
+__device__ __forceinline__ void rhs_product(const T (*a)[kMaxChunk + 1], const T *__restrict__ b, int ldb,
+                                            const RhsMap<T, RPT> &m, int K,
+                                            T (&o)[RhsMap<T, RPT>::NR][RhsMap<T, RPT>::R]) {
 #pragma unroll
-    for (int j = 0; j < RPT; j++) o[j] = T(0);
-    rhs_product_acc<T, RPT, kTrans>(a, b, ldb, i, r0, K, o);
+    for (int h = 0; h < RhsMap<T, RPT>::NR; h++)
+#pragma unroll
+        for (int j = 0; j < RhsMap<T, RPT>::R; j++) o[h][j] = T(0);
+    rhs_product_acc<T, RPT, kTrans>(a, b, ldb, m, K, o);
 }
 
 // Reductions into global memory that return nothing (red): the issuing thread
@@ -439,6 +475,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fwd(const T *__
                                              const float *__restrict__ inv, int32_t *__restrict__ arrive0,
                                              int32_t *__restrict__ ready0, int64_t sstride, int32_t *__restrict__ work,
                                              int32_t *__restrict__ err, long long spin_limit) {
+    using Map = RhsMap<T, RPT>;
     extern __shared__ __align__(16) unsigned char smem_fwd[];
     const int ldv = rhs_ld(min(nrhs, kRhsBlk));
     SweepSmem<T> sm(smem_fwd, ldv);
@@ -481,7 +518,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fwd(const T *__
             if (!s_ok) break;
             stage_rhs(sm.v, ldv, (const T *)y, nb, w, [&](int r) { return ch.col0 + r; });
             __syncthreads();
-            const int i = threadIdx.x % kSolveRows, r0 = (threadIdx.x / kSolveRows) * RPT;
+            const Map m;
             for (int q = 0; q < g; q++) {
                 const int tq = su.t0 + q;
                 const TrsmTile tl = tiles[tq];
@@ -490,10 +527,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fwd(const T *__
                     stage_block(sm.lr, lnz + ch.off + (int64_t)tl.r0 * ch.ld + ch.c0, ch.ld, rows, w);
                     __syncthreads();
                 }
-                if (i < rows && r0 < nb) {
-                    T o[RPT];
-                    rhs_product<T, RPT, false>(sm.lr, sm.v, ldv, i, r0, w, o);
-                    add_rhs<T, RPT>(x + (int64_t)glbind[ch.gl + tl.r0 + i] * nb + r0, o, T(-1), r0, nb);
+                if (m.row(0) < rows && m.r0 < nb) {
+                    T o[Map::NR][Map::R];
+                    rhs_product<T, RPT, false>(sm.lr, sm.v, ldv, m, w, o);
+#pragma unroll
+                    for (int h = 0; h < Map::NR; h++)
+                        if (m.row(h) < rows)
+                            add_rhs<T, Map::R>(x + (int64_t)glbind[ch.gl + tl.r0 + m.row(h)] * nb + m.r0, o[h], T(-1),
+                                               m.r0, nb);
                 }
                 // each tile's arrivals go out as soon as its rows are updated: a later
                 // chunk's step must not wait for the rest of the unit
@@ -524,16 +565,20 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fwd(const T *__
             __syncthreads();
             if constexpr (sizeof(T) == 4) {
                 // y_c = inv(L_cc) x_c: the block's stored inverse (zero above its diagonal)
-                const int k = threadIdx.x % kMaxChunk, r0 = (threadIdx.x / kMaxChunk) * RPT;
-                if (k < w && r0 < nb) {
-                    T o[RPT];
-                    rhs_product<T, RPT, false>(sm.l, sm.xin, ldv, k, r0, w, o);
+                const Map m;
+                if (m.row(0) < w && m.r0 < nb) {
+                    T o[Map::NR][Map::R];
+                    rhs_product<T, RPT, false>(sm.l, sm.xin, ldv, m, w, o);
 #pragma unroll
-                    for (int j = 0; j < RPT; j++)
-                        if (r0 + j < nb) {
-                            sm.v[k * ldv + r0 + j] = o[j];
-                            y[(int64_t)(ch.col0 + k) * nb + r0 + j] = o[j];
-                        }
+                    for (int h = 0; h < Map::NR; h++) {
+                        const int k = m.row(h);
+#pragma unroll
+                        for (int j = 0; j < Map::R; j++)
+                            if (k < w && m.r0 + j < nb) {
+                                sm.v[k * ldv + m.r0 + j] = o[h][j];
+                                y[(int64_t)(ch.col0 + k) * nb + m.r0 + j] = o[h][j];
+                            }
+                    }
                 }
             } else {
                 const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
@@ -561,11 +606,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fwd(const T *__
         }
         // x_rows -= L_{rows,c} y_c
         {
-            const int i = threadIdx.x % kSolveRows, r0 = (threadIdx.x / kSolveRows) * RPT;
-            if (i < rows && r0 < nb) {
-                T o[RPT];
-                rhs_product<T, RPT, false>(sm.lr, sm.v, ldv, i, r0, w, o);
-                add_rhs<T, RPT>(x + (int64_t)glbind[ch.gl + tl.r0 + i] * nb + r0, o, T(-1), r0, nb);
+            const Map m;
+            if (m.row(0) < rows && m.r0 < nb) {
+                T o[Map::NR][Map::R];
+                rhs_product<T, RPT, false>(sm.lr, sm.v, ldv, m, w, o);
+#pragma unroll
+                for (int h = 0; h < Map::NR; h++)
+                    if (m.row(h) < rows)
+                        add_rhs<T, Map::R>(x + (int64_t)glbind[ch.gl + tl.r0 + m.row(h)] * nb + m.r0, o[h], T(-1),
+                                           m.r0, nb);
             }
         }
         // release: the barrier orders every thread's updates (and the first tile's
@@ -599,6 +648,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_bwd(const T *__
                                              const float *__restrict__ inv, int32_t *__restrict__ cnt0,
                                              int32_t *__restrict__ done0, int64_t sstride, int32_t *__restrict__ work,
                                              int32_t *__restrict__ err, long long spin_limit) {
+    using Map = RhsMap<T, RPT>;
     extern __shared__ __align__(16) unsigned char smem_bwd[];
     const int ldv = rhs_ld(min(nrhs, kRhsBlk));
     SweepSmem<T> sm(smem_bwd, ldv);
@@ -641,10 +691,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_bwd(const T *__
             }
             __syncthreads();
             if (!s_ok) break;
-            const int k = threadIdx.x % kMaxChunk, r0 = (threadIdx.x / kMaxChunk) * RPT;
-            T o[RPT];
+            const Map m;
+            T o[Map::NR][Map::R];
 #pragma unroll
-            for (int j = 0; j < RPT; j++) o[j] = T(0);
+            for (int h = 0; h < Map::NR; h++)
+#pragma unroll
+                for (int j = 0; j < Map::R; j++) o[h][j] = T(0);
             for (int q = 0; q < g; q++) {
                 const TrsmTile tl = tiles[su.t0 + q];
                 const int rows = max(0, min(kSolveRows, ch.m - tl.r0));
@@ -654,9 +706,14 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_bwd(const T *__
                 __syncthreads();
                 stage_rhs(sm.v, ldv, (const T *)z, nb, rows, [&](int r) { return grow[r]; });
                 __syncthreads();
-                if (k < w && r0 < nb) rhs_product_acc<T, RPT, true>(sm.lr, sm.v, ldv, k, r0, rows, o);
+                if (m.row(0) < w && m.r0 < nb) rhs_product_acc<T, RPT, true>(sm.lr, sm.v, ldv, m, rows, o);
             }
-            if (k < w && r0 < nb) add_rhs<T, RPT>(acc + (int64_t)(ch.col0 + k) * nb + r0, o, T(1), r0, nb);
+            if (m.r0 < nb) {
+#pragma unroll
+                for (int h = 0; h < Map::NR; h++)
+                    if (m.row(h) < w)
+                        add_rhs<T, Map::R>(acc + (int64_t)(ch.col0 + m.row(h)) * nb + m.r0, o[h], T(1), m.r0, nb);
+            }
             __syncthreads();
             if (threadIdx.x == 0) {
                 __threadfence();  // release this unit's contributions
@@ -673,10 +730,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_bwd(const T *__
         // before it waits and keeps its own contribution in registers
         const bool first = tl.r0 == ch.c0 + w;
         const int rows = max(0, min(kSolveRows, ch.m - tl.r0));
-        const int k = threadIdx.x % kMaxChunk, r0 = (threadIdx.x / kMaxChunk) * RPT;
-        T o[RPT];
+        const Map m;
+        T o[Map::NR][Map::R];
 #pragma unroll
-        for (int j = 0; j < RPT; j++) o[j] = T(0);
+        for (int h = 0; h < Map::NR; h++)
+#pragma unroll
+            for (int j = 0; j < Map::R; j++) o[h][j] = T(0);
         if (first) {
             if constexpr (sizeof(T) == 4) stage_block(sm.l, (const T *)(inv + ch.inv), w, w, w);
             else load_diag(sm.l, rinv, lnz, ch, false);
@@ -695,9 +754,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_bwd(const T *__
             stage_rhs(sm.v, ldv, (const T *)z, nb, rows, [&](int r) { return grow[r]; });
             __syncthreads();
             // this tile's part of L_{S,c}^T z_S
-            if (k < w && r0 < nb) {
-                rhs_product<T, RPT, true>(sm.lr, sm.v, ldv, k, r0, rows, o);
-                if (!first) add_rhs<T, RPT>(acc + (int64_t)(ch.col0 + k) * nb + r0, o, T(1), r0, nb);
+            if (m.row(0) < w && m.r0 < nb) {
+                rhs_product<T, RPT, true>(sm.lr, sm.v, ldv, m, rows, o);
+                if (!first) {
+#pragma unroll
+                    for (int h = 0; h < Map::NR; h++)
+                        if (m.row(h) < w)
+                            add_rhs<T, Map::R>(acc + (int64_t)(ch.col0 + m.row(h)) * nb + m.r0, o[h], T(1), m.r0,
+                                               nb);
+                }
             }
         }
         if (!first) {
@@ -718,20 +783,28 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_bwd(const T *__
         stage_rhs(sm.xin, ldv, y, nb, w, [&](int r) { return ch.col0 + r; });
         stage_rhs(sm.v, ldv, (const T *)acc, nb, w, [&](int r) { return ch.col0 + r; });
         __syncthreads();
-        if (k < w && r0 < nb) {
+        if (m.r0 < nb) {
 #pragma unroll
-            for (int j = 0; j < RPT; j++)
-                if (r0 + j < nb) sm.xin[k * ldv + r0 + j] -= sm.v[k * ldv + r0 + j] + o[j];
+            for (int h = 0; h < Map::NR; h++) {
+                const int k = m.row(h);
+#pragma unroll
+                for (int j = 0; j < Map::R; j++)
+                    if (k < w && m.r0 + j < nb) sm.xin[k * ldv + m.r0 + j] -= sm.v[k * ldv + m.r0 + j] + o[h][j];
+            }
         }
         __syncthreads();
         if constexpr (sizeof(T) == 4) {
             // z_c = inv(L_cc)^T (y_c - acc_c) with the block's stored inverse
-            if (k < w && r0 < nb) {
-                T zo[RPT];
-                rhs_product<T, RPT, true>(sm.l, sm.xin, ldv, k, r0, w, zo);
+            if (m.row(0) < w && m.r0 < nb) {
+                T zo[Map::NR][Map::R];
+                rhs_product<T, RPT, true>(sm.l, sm.xin, ldv, m, w, zo);
 #pragma unroll
-                for (int j = 0; j < RPT; j++)
-                    if (r0 + j < nb) z[(int64_t)(ch.col0 + k) * nb + r0 + j] = zo[j];
+                for (int h = 0; h < Map::NR; h++) {
+                    const int k = m.row(h);
+#pragma unroll
+                    for (int j = 0; j < Map::R; j++)
+                        if (k < w && m.r0 + j < nb) z[(int64_t)(ch.col0 + k) * nb + m.r0 + j] = zo[h][j];
+                }
             }
         } else {
             const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
