@@ -126,6 +126,10 @@ enum sc_precision { SC_FP64 = 0, SC_FP32 = 1, SC_TF32 = 2, SC_TF32X3 = 3 };
  *                     (1..1024): fewer CTAs wait for one chunk's solution, at
  *                     the price of later arrivals from a run's last tiles
  *                     [2 for FP64 factors, 4 for FP32 / TF32 / TF32x3]
+ *   tc_multicast      1 = the 256-column tensor-core tiles run in clusters of
+ *                     two CTAs that take vertically adjacent tiles and share
+ *                     the B tiles by TMA multicast (each loads half), -1 = one
+ *                     CTA per tile [1]
  *   factor_ms         out (sc_tune): median factor time of this setting */
 typedef struct sc_tune_table {
     int32_t tile_min_entries;
@@ -139,7 +143,8 @@ typedef struct sc_tune_table {
     int32_t fused;
     int32_t tc_wide256;
     int32_t solve_group;
-    int32_t reserved[3];
+    int32_t tc_multicast;
+    int32_t reserved[2];
     double factor_ms;
 } sc_tune_table;
 

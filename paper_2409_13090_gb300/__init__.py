@@ -45,12 +45,12 @@ class Options(C.Structure):
 
 
 TUNE_FIELDS = ["tile_min_entries", "tile_min_k", "loop_budget", "lookahead", "tc_min_k", "tc_wide_n", "thin_dim",
-               "defer_width", "fused", "tc_wide256", "solve_group"]
+               "defer_width", "fused", "tc_wide256", "solve_group", "tc_multicast"]
 
 
 class TuneTable(C.Structure):
     """sc_tune_table: launch-plan settings (0 = library default)."""
-    _fields_ = [(f, C.c_int32) for f in TUNE_FIELDS] + [("reserved", C.c_int32 * 3), ("factor_ms", C.c_double)]
+    _fields_ = [(f, C.c_int32) for f in TUNE_FIELDS] + [("reserved", C.c_int32 * 2), ("factor_ms", C.c_double)]
 
     def to_dict(self) -> dict:
         d = {f: getattr(self, f) for f in TUNE_FIELDS}

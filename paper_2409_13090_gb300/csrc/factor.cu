@@ -293,7 +293,7 @@ int run_levels(sc_numeric *h, cudaStream_t st, Prof *prof = nullptr, cudaStream_
                 B(kProfTc);
                 launch_tc_gemm(256, h->precision == SC_TF32X3, (float *)lnz, h->d_tasks, h->d_gemm + pl.tc256_off,
                                pl.tc256_cnt, h->d_tmaps, h->nmaps, h->d_tmap_of_sn, h->d_err,
-                               (long long)s->opt.spin_limit, h->num_sms, ps);
+                               (long long)s->opt.spin_limit, h->num_sms, ps, knobs_of(s->tune).tc_multicast);
                 E();
                 launches++;
             }
@@ -549,7 +549,8 @@ void build_plan(const sc_symbolic *s, int precision, Plan &P, bool lookahead) {
                 ids_small.push_back(id);
                 P.class_flops[kProfSmall] += task_flops(t);
             } else if (bn) {
-                tc_tiles_of(t, id, bn, bn == 256 ? g_tc256[cls] : bn == 128 ? g_tc[cls] : g_tc64[cls]);
+                if (bn == 256 && kn.tc_multicast) tc_tile_pairs_of(t, id, g_tc256[cls]);
+                else tc_tiles_of(t, id, bn, bn == 256 ? g_tc256[cls] : bn == 128 ? g_tc[cls] : g_tc64[cls]);
                 P.class_flops[kProfTc] += task_flops(t);
             } else if (std::min(t.m, t.n) <= std::min(kn.thin_dim, kThinDim) && !(t.flags & kTaskStoreU)) {
                 // a 64 x 64 tile would be mostly padding: warp blocks, kThinWarps per CTA

@@ -54,6 +54,7 @@ struct Knobs {
     bool fused = false;
     int tc_wide256 = 256;
     int solve_group = 0;  // 0: by the factor's precision (2 FP64, 4 FP32)
+    bool tc_multicast = true;
 };
 inline Knobs knobs_of(const sc_tune_table &t) {
     Knobs k;
@@ -68,6 +69,7 @@ inline Knobs knobs_of(const sc_tune_table &t) {
     if (t.fused) k.fused = t.fused > 0;
     if (t.tc_wide256) k.tc_wide256 = t.tc_wide256;
     if (t.solve_group) k.solve_group = t.solve_group;
+    if (t.tc_multicast) k.tc_multicast = t.tc_multicast > 0;
     return k;
 }
 // Inner-dimension granularity of one tcgen05.mma of kind::tf32 (K = 8): the
@@ -104,7 +106,7 @@ inline bool tune_valid(const sc_tune_table &t) {
            (t.lookahead >= -1 && t.lookahead <= 1) && in(t.tc_min_k, 32, 1 << 16) && in(t.tc_wide_n, 16, 1 << 16) &&
            (t.thin_dim == -1 || in(t.thin_dim, 1, 8)) && in(t.defer_width, 256, 1 << 20) &&
            (t.fused >= -1 && t.fused <= 1) && in(t.tc_wide256, 16, 1 << 20) &&
-           in(t.solve_group, 1, 1024);
+           in(t.solve_group, 1, 1024) && (t.tc_multicast >= -1 && t.tc_multicast <= 1);
 }
 
 // Part of Alg. 5's inner loops for one block B of supernode J, run on the

@@ -95,6 +95,26 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         "l"(map), "r"(bar), "r"(x), "r"(y)
         : "memory");
 }
+// the same load delivered to the same shared-memory offset, and its bytes counted
+// on the barrier at the same offset, in every CTA of the cluster in `mask`
+__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar,
+                                               uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(dst),
+        "l"(map), "r"(bar), "r"(x), "r"(y), "h"(mask)
+        : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// every thread of every CTA of the cluster (release / acquire)
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 // shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
 __device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t addr) {
     uint64_t d = 0;
@@ -116,6 +136,14 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t adesc, uint64_t
 }
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+// one arrival, when this CTA's MMAs issued so far complete, on the barrier at
+// offset `bar` of every CTA of the cluster in `mask`
+__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::
+                     "r"(bar),
+                 "h"(mask)
+                 : "memory");
 }
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -188,13 +216,27 @@ __device__ __forceinline__ uint32_t b_tile(const unsigned char *smem, int s, int
     return smem_u32(smem + C::STAGES * C::NSPLIT * A_BYTES + (s * C::NSPLIT + part) * C::B_BYTES);
 }
 
-template <int BN, bool X3>
+// CL = 2 (BN = 256 only): clusters of two CTAs take the two tiles of a pair
+// (vertically adjacent tiles of one product and column block; the plan lists
+// them in pairs, the second possibly one that writes nothing). Each CTA loads
+// its own A tiles and one 128-row half of the B tiles, multicast to both CTAs,
+// so a stage costs each SM 64 KB of loads instead of 96 KB (X3). A stage is
+// refilled only when the MMAs of both CTAs are done with it (its empty barrier
+// counts both CTAs' commits); the CTAs start after a cluster barrier that
+// follows the barrier set-up, and leave after every commit of the partner has
+// reached them and a second cluster barrier.
+template <int BN, bool X3, int CL = 1>
 __global__ void __launch_bounds__(kThreads, (Cfg<BN, X3>::CTAS_PER_SM))
     k_tc_gemm(float *__restrict__ lnz, const Task *__restrict__ tasks, const GemmTile *__restrict__ tiles, int ntiles,
               const CUtensorMap *__restrict__ tmaps, int lo_maps, const int32_t *__restrict__ tmap_of_sn,
               int32_t *__restrict__ err, long long spin_limit) {
     using C = Cfg<BN, X3>;
     constexpr int STAGES = C::STAGES;
+    static_assert(CL == 1 || (CL == 2 && BN == 256), "clusters of two take 256-column tiles");
+    const int rank = CL == 2 ? (int)cluster_rank() : 0;
+    // this CTA's first tile and its stride: pairs go to clusters, tile 2p + rank to rank
+    const int t_first = CL == 2 ? 2 * ((int)blockIdx.x / 2) + rank : (int)blockIdx.x;
+    const int t_step = (int)gridDim.x;
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * C::STAGE_BYTES);
@@ -205,7 +247,8 @@ __global__ void __launch_bounds__(kThreads, (Cfg<BN, X3>::CTAS_PER_SM))
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     if (threadIdx.x == 0) {
         abort_flag = 0;
-        for (int s = 0; s < 2 * STAGES; s++) mbar_init(smem_u32(bars + s), 1);
+        for (int s = 0; s < STAGES; s++) mbar_init(smem_u32(full + s), 1);
+        for (int s = 0; s < STAGES; s++) mbar_init(smem_u32(empty + s), CL);  // one commit per CTA of the cluster
         for (int a = 0; a < 2; a++) {
             mbar_init(smem_u32(accf + a), 1);  // one tcgen05.commit per tile
             mbar_init(smem_u32(acce + a), kEpiWarps);  // one arrival per epilogue warp
@@ -222,6 +265,7 @@ __global__ void __launch_bounds__(kThreads, (Cfg<BN, X3>::CTAS_PER_SM))
     }
     fence_before();
     __syncthreads();
+    if constexpr (CL == 2) cluster_sync();  // the partner's barriers exist before any multicast
     fence_after();
     const uint32_t tmem = *tmem_holder;
 
@@ -229,7 +273,7 @@ __global__ void __launch_bounds__(kThreads, (Cfg<BN, X3>::CTAS_PER_SM))
         if (lane == 0) {
             // producer
             uint32_t g = 0;
-            for (int t = blockIdx.x; t < ntiles && !abort_flag; t += gridDim.x) {
+            for (int t = t_first; t < ntiles && !abort_flag; t += t_step) {
                 const GemmTile tl = tiles[t];
                 const Task tk = tasks[tl.task];
                 const int mi = tmap_of_sn[tk.src];
@@ -252,11 +296,24 @@ __global__ void __launch_bounds__(kThreads, (Cfg<BN, X3>::CTAS_PER_SM))
                     for (int part = 0; part < C::NSPLIT; part++) {
                         const CUtensorMap *ap = amap + 2 * lo_maps * part, *bp = bmap + 2 * lo_maps * part;
                         tma_load_2d(a_tile<BN, X3>(smem, s, part), ap, x, ay, fb);
-                        tma_load_2d(b_tile<BN, X3>(smem, s, part), bp, x, by, fb);
-                        if constexpr (BN == 256)
-                            tma_load_2d(b_tile<BN, X3>(smem, s, part) + 128 * BK * 4, bp, x, by + 128, fb);
+                        if constexpr (CL == 2) {
+                            // this CTA's half of B, into both CTAs
+                            tma_load_2d_mc(b_tile<BN, X3>(smem, s, part) + rank * 128 * BK * 4, bp, x, by + 128 * rank,
+                                           fb, (uint16_t)0x3);
+                        } else {
+                            tma_load_2d(b_tile<BN, X3>(smem, s, part), bp, x, by, fb);
+                            if constexpr (BN == 256)
+                                tma_load_2d(b_tile<BN, X3>(smem, s, part) + 128 * BK * 4, bp, x, by + 128, fb);
+                        }
                     }
                 }
+            }
+            if constexpr (CL == 2) {
+                // the last use of every stage released by both CTAs: the partner's
+                // commits have all reached this CTA's barriers, and its MMAs have read
+                // every multicast piece
+                for (uint32_t u = g > (uint32_t)STAGES ? g - STAGES : 0; u < g; u++)
+                    if (!mbar_wait(smem_u32(empty + u % STAGES), (u / STAGES) & 1u, spin_limit, err, 5)) break;
             }
         }
     } else if (warp == 1) {
@@ -264,7 +321,7 @@ __global__ void __launch_bounds__(kThreads, (Cfg<BN, X3>::CTAS_PER_SM))
             // MMA issuer
             uint32_t g = 0;
             int i = 0;
-            for (int t = blockIdx.x; t < ntiles && !abort_flag; t += gridDim.x, i++) {
+            for (int t = t_first; t < ntiles && !abort_flag; t += t_step, i++) {
                 const Task tk = tasks[tiles[t].task];
                 const int nk = (tk.k + BK - 1) / BK;
                 const int a = i & 1, u = i >> 1;
@@ -301,7 +358,9 @@ __global__ void __launch_bounds__(kThreads, (Cfg<BN, X3>::CTAS_PER_SM))
                                      (kb > 0 || kk > 0) ? 1u : 0u);
                         }
                     }
-                    mma_commit(smem_u32(empty + s));  // frees ring stage s when these MMAs finish
+                    // frees ring stage s (in both CTAs of a cluster) when these MMAs finish
+                    if constexpr (CL == 2) mma_commit_mc(smem_u32(empty + s), (uint16_t)0x3);
+                    else mma_commit(smem_u32(empty + s));
                 }
                 mma_commit(smem_u32(accf + a));  // accumulator a complete
             }
@@ -310,7 +369,7 @@ __global__ void __launch_bounds__(kThreads, (Cfg<BN, X3>::CTAS_PER_SM))
         // epilogue warps 2..9: TMEM lanes 32*(warp % 4) .. +31, column half (warp - 2) / 4
         const int quarter = warp % 4, half = (warp - 2) / 4;
         int i = 0;
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, i++) {
+        for (int t = t_first; t < ntiles; t += t_step, i++) {
             const GemmTile tl = tiles[t];
             const Task tk = tasks[tl.task];
             const int gi = tl.tm * BM + quarter * 32 + lane;
@@ -345,6 +404,7 @@ __global__ void __launch_bounds__(kThreads, (Cfg<BN, X3>::CTAS_PER_SM))
     __syncwarp();
     fence_before();
     __syncthreads();
+    if constexpr (CL == 2) cluster_sync();  // no multicast or commit is still on its way to this CTA
     fence_after();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
@@ -355,7 +415,11 @@ __global__ void __launch_bounds__(kThreads, (Cfg<BN, X3>::CTAS_PER_SM))
 // ---------------------------------------------------------------- host side
 inline bool tc_gemm_init() {
     using namespace tc;
-    return cudaFuncSetAttribute(k_tc_gemm<256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(k_tc_gemm<256, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                Cfg<256, false>::SMEM) == cudaSuccess &&
+           cudaFuncSetAttribute(k_tc_gemm<256, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                Cfg<256, true>::SMEM) == cudaSuccess &&
+           cudaFuncSetAttribute(k_tc_gemm<256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 Cfg<256, false>::SMEM) == cudaSuccess &&
            cudaFuncSetAttribute(k_tc_gemm<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 Cfg<256, true>::SMEM) == cudaSuccess &&
@@ -375,6 +439,21 @@ inline int tc_width(const Task &t, const std::vector<int32_t> &tmap_of_sn, int s
                     bool ignore_tail) {
     if (tmap_of_sn[t.src] < 0) return 0;
     return tc_route_width(t, src_width, min_k, wide_n, ignore_tail);
+}
+
+// 256-column tiles for clusters of two: per column block, the row tiles in
+// pairs (2p, 2p + 1); a pair whose second (or first) tile does not exist gets
+// it anyway -- past the product's rows, or above the diagonal of a lower
+// product -- and that tile's epilogue writes nothing.
+inline void tc_tile_pairs_of(const Task &t, int32_t id, std::vector<GemmTile> &out) {
+    const int tm = (t.m + tc::BM - 1) / tc::BM, tn = (t.n + 255) / 256;
+    auto live = [&](int i, int j) { return i < tm && !((t.flags & kTaskLower) && (i * tc::BM + tc::BM - 1) < j * 256); };
+    for (int j = 0; j < tn; j++)
+        for (int i = 0; i < tm; i += 2)
+            if (live(i, j) || live(i + 1, j)) {
+                out.push_back(GemmTile{id, i, j, -1});
+                out.push_back(GemmTile{id, i + 1, j, -1});
+            }
 }
 
 inline void tc_tiles_of(const Task &t, int32_t id, int bn, std::vector<GemmTile> &out) {
@@ -435,10 +514,43 @@ inline void launch_tc(float *lnz, const Task *tasks, const GemmTile *tiles, int3
     tc::k_tc_gemm<BN, X3><<<grid, tc::kThreads, C::SMEM, st>>>(lnz, tasks, tiles, count, maps, nmaps, tmap_of_sn, err,
                                                                spin_limit);
 }
+// Clusters of two over `count` paired tiles (count even): as many clusters as
+// fit on the device at once (fewer if there are fewer pairs).
+template <bool X3>
+inline void launch_tc_pairs(float *lnz, const Task *tasks, const GemmTile *tiles, int32_t count,
+                            const CUtensorMap *maps, int nmaps, const int32_t *tmap_of_sn, int32_t *err,
+                            long long spin_limit, int num_sms, cudaStream_t st) {
+    using C = tc::Cfg<256, X3>;
+    static int max_clusters_of[64] = {};  // per device ordinal
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int &max_clusters = max_clusters_of[dev & 63];
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2, at[0].val.clusterDim.y = 1, at[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(tc::kThreads);
+    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (!max_clusters) {
+        cfg.gridDim = dim3((unsigned)(num_sms / 2 * 2));
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, tc::k_tc_gemm<256, X3, 2>, &cfg) != cudaSuccess || n < 1) n = num_sms / 2;
+        max_clusters = n;
+    }
+    cfg.gridDim = dim3((unsigned)(2 * std::min<int>(count / 2, max_clusters)));
+    cudaLaunchKernelEx(&cfg, tc::k_tc_gemm<256, X3, 2>, lnz, tasks, tiles, (int)count, maps, nmaps, tmap_of_sn, err,
+                       spin_limit);
+}
 inline void launch_tc_gemm(int bn, bool x3, float *lnz, const Task *tasks, const GemmTile *tiles, int32_t count,
                            const CUtensorMap *maps, int nmaps, const int32_t *tmap_of_sn, int32_t *err,
-                           long long spin_limit, int num_sms, cudaStream_t st) {
-    if (bn == 256) {
+                           long long spin_limit, int num_sms, cudaStream_t st, bool pairs = false) {
+    if (bn == 256 && pairs) {
+        if (x3) launch_tc_pairs<true>(lnz, tasks, tiles, count, maps, nmaps, tmap_of_sn, err, spin_limit, num_sms, st);
+        else launch_tc_pairs<false>(lnz, tasks, tiles, count, maps, nmaps, tmap_of_sn, err, spin_limit, num_sms, st);
+    } else if (bn == 256) {
         if (x3) launch_tc<256, true>(lnz, tasks, tiles, count, maps, nmaps, tmap_of_sn, err, spin_limit, num_sms, st);
         else launch_tc<256, false>(lnz, tasks, tiles, count, maps, nmaps, tmap_of_sn, err, spin_limit, num_sms, st);
     } else if (bn == 128) {

@@ -29,7 +29,8 @@ bool same_knobs(const sc_tune_table &a, const sc_tune_table &b) {
     return x.tile_min_entries == y.tile_min_entries && x.tile_min_k == y.tile_min_k &&
            x.loop_budget == y.loop_budget && x.lookahead == y.lookahead && x.tc_min_k == y.tc_min_k &&
            x.tc_wide_n == y.tc_wide_n && x.thin_dim == y.thin_dim && x.defer_width == y.defer_width && x.fused == y.fused &&
-           x.tc_wide256 == y.tc_wide256 && x.solve_group == y.solve_group;
+           x.tc_wide256 == y.tc_wide256 && x.solve_group == y.solve_group &&
+           x.tc_multicast == y.tc_multicast;
 }
 
 double median(std::vector<double> v) {

@@ -168,10 +168,11 @@ def test_deeper_trailing_update_deferral(defer, prec, tol):
 def test_256_column_tensor_core_tiles(case, prec, tol):
     """Products at least 256 columns wide on 128 x 256 tensor-core tiles (the
     B tile loaded as two 128-row boxes, both TMEM accumulators 256 columns):
-    L against the oracle's element by element, with the 256-column tiles on
-    (the default) and off (every such product on 128-column tiles), ragged
-    widths and lower products that cross the diagonal included; refinement
-    reaches eta <= 1e-14."""
+    L against the oracle's element by element with the 256-column tiles in
+    clusters of two sharing B by multicast (the default, pairs completed by
+    tiles that write nothing), one CTA per tile, and off (every such product
+    on 128-column tiles); ragged widths and lower products that cross the
+    diagonal included; refinement reaches eta <= 1e-14."""
     if case.startswith("dense"):
         n = 1300 if case == "dense_1300" else 700
         A, perm0, kw = _dense(n, 3), None, dict(ordering="natural", chunk=40 if case.endswith("c40") else 64)
@@ -181,14 +182,15 @@ def test_256_column_tensor_core_tiles(case, prec, tol):
     o = oracle.Oracle(A, perm0, pr=True)
     assert o.factor() == 0
     Lo = o.L_supernodal()
-    for wide in (0, 1 << 20):
-        sym = sc.Symbolic(A, tune=dict(tc_wide256=wide) if wide else None, **kw)
+    for wide, mc in ((0, 0), (0, -1), (1 << 20, 0)):
+        tune = {k: v for k, v in (("tc_wide256", wide), ("tc_multicast", mc)) if v}
+        sym = sc.Symbolic(A, tune=tune or None, **kw)
         st = sym.plan_stats(prec)
         assert (st["tc256_tiles"] > 0) == (wide == 0), st
         num = sym.factor(A.values, precision=prec)
         assert num.rc == 0
         err = np.abs(num.export_L() - Lo).max() / np.abs(Lo).max()
-        assert err <= tol, (wide, err)
+        assert err <= tol, (wide, mc, err)
         B = inputs.rhs(A.n, 2, 13)
         X, info = num.solve(B)
         assert info["converged"], info

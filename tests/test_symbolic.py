@@ -282,6 +282,13 @@ def test_256_column_tiles_only_in_tensor_core_plans():
     for prec in ("fp64", "fp32"):
         assert sym.plan_stats(prec)["tc256_tiles"] == 0 and sym.plan_stats(prec)["tc_tiles"] == 0
     assert sym.check_schedule()["ok"]
+    # clusters of two (the default): the 256-column tiles come in pairs, completed
+    # where a product has an odd number of row tiles or a lower product's pair
+    # straddles the diagonal; one CTA per tile lists only the real ones
+    one = sc.Symbolic(A, ordering="natural", tune=dict(tc_multicast=-1)).plan_stats("tf32")
+    pairs = sym.plan_stats("tf32")
+    assert pairs["tc256_tiles"] % 2 == 0 and pairs["tc256_tiles"] >= one["tc256_tiles"] > 0
+    assert pairs["tc256_tiles"] <= 2 * one["tc256_tiles"]
 
 
 def test_deferral_depth_changes_only_the_in_panel_products():
@@ -312,7 +319,7 @@ def test_deferral_depth_changes_only_the_in_panel_products():
 
 
 @pytest.mark.parametrize("bad", [dict(lookahead=2), dict(tc_min_k=16), dict(tc_wide_n=8), dict(tc_wide256=8),
-                                 dict(solve_group=2000),
+                                 dict(solve_group=2000), dict(tc_multicast=2),
                                  dict(thin_dim=9),
                                  dict(thin_dim=-2), dict(loop_budget=100), dict(tile_min_entries=-1),
                                  dict(defer_width=128), dict(defer_width=1 << 21)])
