@@ -110,7 +110,7 @@ enum sc_precision { SC_FP64 = 0, SC_FP32 = 1, SC_TF32 = 2, SC_TF32X3 = 3 };
  *                     rest of its defer_width-column block (K = 256), and that
  *                     block's last chunk every later column (K = defer_width).
  *                     256..2^20, rounded down to a multiple of the macro panel;
- *                     256 = two levels only [256]. Wider outer blocks mean fewer
+ *                     256 = two levels only [512]. Wider outer blocks mean fewer
  *                     read-modify-write passes over each target with longer K.
  *   fused             1 = every level of an FP64 / FP32 RLB factorization runs as
  *                     one persistent launch (POTRF, TRSM, products, device loops

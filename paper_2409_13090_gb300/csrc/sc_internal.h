@@ -50,7 +50,7 @@ struct Knobs {
     int tile_min_entries = 1024, tile_min_k = 16, loop_budget = 1 << 15;
     bool lookahead = true;
     int tc_min_k = 32, tc_wide_n = 96, thin_dim = 8;
-    int defer_width = 256;
+    int defer_width = 512;
     bool fused = false;
     int tc_wide256 = 256;
     int solve_group = 0;  // 0: by the factor's precision (2 FP64, 4 FP32)

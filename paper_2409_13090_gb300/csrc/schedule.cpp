@@ -11,8 +11,8 @@
 //     deferred in levels (a chunk updates the rest of its 256-column macro
 //     panel, K = chunk width; a macro panel's last chunk updates the rest of its
 //     outer block, K = 256, and an outer block's last chunk every later column,
-//     K = the outer width; with the default outer width of 256 the macro panel's
-//     last chunk updates all later columns at once);
+//     K = the outer width; with an outer width of 256 the macro panel's last
+//     chunk updates all later columns at once; the default is 512);
 //   - for J's last chunk (all of L_{*,J} is final):
 //       RLB (Alg. 5): for every ancestor P, every block B of J inside P:
 //         SYRK  L_{B,B}  -= L_{B,J} L_{B,J}^T
@@ -78,7 +78,7 @@ int build_schedule(sc_symbolic *s) {
             int64_t offJ = s->lnz_off[J];
             if (!ch.last) {
                 // trailing updates inside J, deferred in levels of width W (the chunk),
-                // Wm (macro panel) and Wd (outer block, Wd = Wm: two levels only): the
+                // Wm (macro panel) and Wd (outer block; Wd = Wm: two levels only): the
                 // chunk ending at column e updates, with K = the width of the largest
                 // level block ending at e, the columns from e to the end of the next
                 // level's block (to nJ after an outer block). Every column before a

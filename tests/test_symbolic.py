@@ -310,12 +310,12 @@ def test_deferral_depth_changes_only_the_in_panel_products():
             assert np.array_equal(v[k], getattr(o, k)), (defer, k)
         return sym.plan_stats("tf32")["tc_tiles"]
 
-    base = passes(None)
-    assert passes(256) == base
+    two = passes(256)  # two levels: macro panels only
+    assert passes(None) == passes(512)  # the default outer width
     # an outer block boundary replaces the macro panels' updates of all later columns
-    assert passes(512) < base and passes(1024) < base
+    assert passes(512) < two and passes(1024) < two
     # an outer block wider than the supernode is the two-level schedule
-    assert passes(4096) == base
+    assert passes(4096) == two
 
 
 @pytest.mark.parametrize("bad", [dict(lookahead=2), dict(tc_min_k=16), dict(tc_wide_n=8), dict(tc_wide256=8),
