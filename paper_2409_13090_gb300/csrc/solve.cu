@@ -597,6 +597,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fwd(const T *__
                 }
             }
             __syncthreads();
+            // y_c is published as soon as it is written: the chunk's other tiles start
+            // while this one updates its own rows (the next chunk's, on the chain)
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicExch(ready + (int64_t)tl.chunk * kSyncStride, 1);
+            }
         } else {
             if (threadIdx.x == 0) s_ok = wait_flag(ready + (int64_t)tl.chunk * kSyncStride, 1, err, spin_limit, 7);
             __syncthreads();
@@ -617,14 +623,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_fwd(const T *__
                                            m.r0, nb);
             }
         }
-        // release: the barrier orders every thread's updates (and the first tile's
-        // y_c) before thread 0's fence; the first tile publishes y_c only now, so
-        // its own rows -- the next chunk's, the one contribution on the chain --
-        // are updated before the chunk's other tiles compete for the SMs
+        // release: the barrier orders every thread's updates before thread 0's fence
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
-            if (first) atomicExch(ready + (int64_t)tl.chunk * kSyncStride, 1);
             for (int p = dep_ptr[t]; p < dep_ptr[t + 1]; p++) atomicAdd(arrive + (int64_t)dep[p] * kSyncStride, 1);
         }
     }
