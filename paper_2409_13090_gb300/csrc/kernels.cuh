@@ -39,8 +39,9 @@ __global__ void k_scatter_values(T *__restrict__ lnz, const int64_t *__restrict_
 // --------------------------------------------------------------------- K1
 // POTRF of each chunk's w x w diagonal block (lower) in shared memory,
 // right-looking by panels of 8 columns. Per panel:
-//   1. warp 0 factors the panel's 8 x 8 diagonal block in registers (lane i
-//      holds row i; pivots and column entries are broadcast by shuffles);
+//   1. the panel's 8 x 8 diagonal block is factored in registers: FP32 by one
+//      thread (no shuffles on the serial chain of pivots), FP64 by warp 0 (lane
+//      i holds row i; pivots and column entries are broadcast by shuffles);
 //   2. every row below it is solved against that block, one thread per row
 //      (x <- x L_d^{-T}, reciprocal pivots);
 //   3. all 256 threads apply the panel's rank-8 update to the trailing triangle.
@@ -57,35 +58,25 @@ __device__ bool potrf_pass(S (*a)[kMaxChunk + 1], int w, const double *thr, int 
                            int32_t *__restrict__ info, int *flag) {
     constexpr int PW = 8;  // panel width
     __shared__ S rpiv[PW];
-    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // 16 x 16 threads
     for (int p0 = 0; p0 < w; p0 += PW) {
         const int pw = min(PW, w - p0), p1 = p0 + pw;
-        if (warp == 0) {
+        if (sizeof(S) == 8 && threadIdx.x < 32) {
+            // FP64: warp 0, lane i holding row i, pivots and column entries broadcast
+            // by shuffles (one thread's FP64 chain would be slower)
+            const int lane = threadIdx.x;
             S r[PW];
 #pragma unroll
             for (int j = 0; j < PW; j++) r[j] = (lane < pw && j <= lane) ? a[p0 + lane][p0 + j] : S(0);
-            bool low = false;
 #pragma unroll
             for (int k = 0; k < PW; k++) {
                 if (k < pw) {
                     S d = __shfl_sync(0xffffffffu, r[k], k);  // the same value in every lane
-                    if (check_low) {
-                        if (!((double)d > thr[p0 + k])) low = true;
-                    } else if (!(d > S(0))) {
+                    if (!(d > S(0))) {
                         if (lane == 0) atomicMin(info, col0 + p0 + k + 1);
+                        d = S(1);
                     }
-                    if (!(d > S(0))) d = S(1);
-                    // FP64: one reciprocal square root (the FP64 pipe is narrow and this chain is
-                    // serial); FP32: IEEE square root and division
-                    S sq, rk;
-                    if constexpr (sizeof(S) == 8) {
-                        rk = rsqrt(d);
-                        sq = d * rk;
-                    } else {
-                        sq = sqrt(d);
-                        rk = S(1) / sq;
-                    }
+                    const S rk = rsqrt(d), sq = d * rk;
                     if (lane == k) r[k] = sq;
                     else if (lane > k) r[k] *= rk;
                     if (lane == 0) rpiv[k] = rk;
@@ -101,7 +92,43 @@ __device__ bool potrf_pass(S (*a)[kMaxChunk + 1], int w, const double *thr, int 
                 for (int j = 0; j < PW; j++)
                     if (j <= lane) a[p0 + lane][p0 + j] = r[j];
             }
-            if (lane == 0 && low) *flag = 1;
+        } else if (sizeof(S) == 4 && threadIdx.x == 0) {
+            // FP32: the panel's diagonal block in one thread's registers, no shuffles
+            // on the serial chain of pivots (rows past pw hold the identity)
+            S r[PW][PW];
+#pragma unroll
+            for (int i = 0; i < PW; i++)
+#pragma unroll
+                for (int j = 0; j <= i; j++) r[i][j] = i < pw ? a[p0 + i][p0 + j] : S(i == j ? 1 : 0);
+            bool low = false;
+#pragma unroll
+            for (int k = 0; k < PW; k++) {
+                if (k < pw) {
+                    S d = r[k][k];
+                    if (check_low) {
+                        // the pivot threshold tau |A_jj| in the block's precision
+                        if (!(d > (S)thr[p0 + k])) low = true;
+                    } else if (!(d > S(0))) {
+                        atomicMin(info, col0 + p0 + k + 1);
+                    }
+                    if (!(d > S(0))) d = S(1);
+                    const S rk = rsqrt(d);
+                    r[k][k] = d * rk;
+                    rpiv[k] = rk;
+#pragma unroll
+                    for (int i = k + 1; i < PW; i++) r[i][k] *= rk;
+#pragma unroll
+                    for (int i = k + 1; i < PW; i++)
+#pragma unroll
+                        for (int j = k + 1; j <= i; j++) r[i][j] -= r[i][k] * r[j][k];
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < PW; i++)
+#pragma unroll
+                for (int j = 0; j <= i; j++)
+                    if (i < pw) a[p0 + i][p0 + j] = r[i][j];
+            if (low) *flag = 1;
         }
         __syncthreads();
         if (check_low && *flag) return false;
