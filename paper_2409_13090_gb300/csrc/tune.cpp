@@ -109,6 +109,7 @@ extern "C" int sc_tune(sc_symbolic *s, const double *values, int values_on_devic
         {&sc_tune_table::tc_min_k, {32, 64, 128}, false, true, false},
         {&sc_tune_table::tc_wide_n, {64, 96, 128}, false, true, false},
         {&sc_tune_table::tc_wide256, {384, 1 << 20}, false, true, false},
+        {&sc_tune_table::tc_multicast, {-1}, false, true, false},
     };
     bool dirty = false;  // the schedule in s is not the one of `cur`
     for (const Field &f : fields) {
