@@ -1,7 +1,8 @@
 /* Host-only use of the C ABI from plain C99 (no device work): analyse a 2D
  * 5-point Laplacian on an n x n grid with the geometric and the two graph
  * orderings, read the symbolic view, check the device schedule, query the
- * launch plan, save and reload the analysis. Prints one line per ordering;
+ * launch plan, save and reload the analysis; a deterministic RL analysis with
+ * a launch-plan table. Prints one line per ordering and one for the last;
  * exits non-zero on the first failed call. Build: cc -std=c99 -I include
  * abi_check.c -L <lib dir> -lsc. */
 #include <stdio.h>
@@ -61,6 +62,39 @@ int main(int argc, char **argv) {
                (long long)plan[0]);
         CHECK(sc_symbolic_free(t));
         CHECK(sc_symbolic_free(s));
+    }
+    {
+        /* a deterministic RL analysis with a launch-plan table: the schedule check
+         * covers its plans (kind 13), the plan has target-owned slabs and no tile
+         * split along K; the same option with RLB is refused */
+        sc_options opt;
+        CHECK(sc_options_default(&opt));
+        opt.ordering = SC_ORDER_GRID_ND;
+        opt.grid[0] = k;
+        opt.grid[1] = k;
+        opt.grid[2] = 1;
+        opt.variant = SC_RL;
+        opt.deterministic = 1;
+        sc_tune_table tt;
+        memset(&tt, 0, sizeof(tt));
+        tt.defer_width = 1024;
+        tt.solve_group = 3;
+        tt.tc_multicast = -1;
+        opt.tune = &tt;
+        sc_symbolic *s = NULL;
+        CHECK(sc_analyze(n, colptr, rowind, &opt, &s));
+        int64_t chk[5], plan[14];
+        CHECK(sc_check_schedule(s, chk, 5));
+        CHECK(sc_plan_stats(s, SC_FP64, plan, 14));
+        if (plan[11] != 0 || plan[12] <= 0) {
+            fprintf(stderr, "deterministic plan: %lld split tiles, %lld slabs\n", (long long)plan[11],
+                    (long long)plan[12]);
+            return 1;
+        }
+        printf("deterministic rl pairs %lld slabs %lld\n", (long long)plan[8], (long long)plan[12]);
+        CHECK(sc_symbolic_free(s));
+        opt.variant = SC_RLB;
+        if (sc_analyze(n, colptr, rowind, &opt, &s) != -4) return 1;
     }
     if (sc_analyze(0, colptr, rowind, NULL, NULL) >= 0) return 1; /* invalid arguments are refused */
     remove(path);

@@ -548,12 +548,17 @@ def test_c_abi_from_plain_c(tmp_path):
                            os.path.join(ROOT, "tests", "c_abi", "abi_check.c"), "-o", str(exe), "-L", lib_dir,
                            "-lsc", "-Wl,-rpath," + lib_dir])
     out = subprocess.check_output([str(exe), "24", str(tmp_path / "a.scs")], text=True).splitlines()
-    assert len(out) == 3
+    assert len(out) == 4
     A = inputs.laplacian_2d(24, 24)
     for line, (ordering, kw) in zip(out, [("grid_nd", dict(grid=(24, 24, 1))), ("graph_nd", {}), ("graph_ml", {})]):
         f = line.split()
         v = sc.Symbolic(A, ordering=ordering, **kw).view()
         assert int(f[5]) == v["nsuper"] and int(f[7]) == v["nnzL"], (line, ordering)
+    # the deterministic RL analysis from C: the same pairs and slabs as through the binding
+    st = sc.Symbolic(A, ordering="grid_nd", grid=(24, 24, 1), variant="rl", deterministic=True,
+                     tune=dict(defer_width=1024, solve_group=3, tc_multicast=-1)).plan_stats("fp64")
+    f = out[3].split()
+    assert f[:2] == ["deterministic", "rl"] and int(f[3]) == st["rl_pairs"] and int(f[5]) == st["rl_slabs"], out[3]
 
 
 @pytest.mark.parametrize("seed", range(12))
