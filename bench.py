@@ -114,20 +114,38 @@ def _e2e(num, A, B, stream, steps, **solve_kw):
     vals_h = torch.tensor(A.values, dtype=torch.float64).pin_memory()
     B_h = torch.tensor(np.ascontiguousarray(B.T)).pin_memory()
     X_h = torch.zeros_like(B_h).pin_memory()
-    f, s = [], []
+    f, s, lib, its, cin, cout = [], [], [], [], [], []
     for i in range(steps + 1):
         torch.cuda.synchronize()
         a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         a.record(stream)
         num.refactor(vals_h)
         b.record(stream)
-        num.solve(B_h, X_h, **solve_kw)
+        _, si = num.solve(B_h, X_h, **solve_kw)
         c.record(stream)
         torch.cuda.synchronize()
         if i:  # the first pair is a warm-up of the host-buffer path
             f.append(a.elapsed_time(b))
             s.append(b.elapsed_time(c))
-    return sum(f) / len(f), sum(s) / len(s)
+            lib.append(si["solve_ms"])
+            its.append(si["iterations"])
+            cin.append(si["copy_in_ms"])
+            cout.append(si["copy_out_ms"])
+    # the copy rates of these pinned buffers on their own (B in, X out)
+    Bt = torch.empty(B_h.shape, dtype=B_h.dtype, device="cuda")
+    rates = {}
+    for key, dst, src in (("h2d_gbs", Bt, B_h), ("d2h_gbs", X_h, Bt)):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        dst.copy_(src, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        rates[key] = B_h.numel() * 8 / (a.elapsed_time(b) * 1e6)
+    del Bt
+    return sum(f) / len(f), sum(s) / len(s), {"lib_solve_ms": sum(lib) / len(lib), "iterations": max(its),
+                                               "lib_copy_in_ms": sum(cin) / len(cin),
+                                               "lib_copy_out_ms": sum(cout) / len(cout), **rates}
 
 
 def _class_rooflines(prof, peaks, fp_peak, precision, workload, scale, merge):
@@ -642,12 +660,12 @@ def main():
 
     # ---- end to end through host buffers (pinned): H2D values and B, factor, solve, D2H X
     ne2e = max(1, min(K, 3))
-    e2e_f, e2e_s = _e2e(num, A, B, stream, ne2e)
+    e2e_f, e2e_s, e2e_x = _e2e(num, A, B, stream, ne2e)
     e2e = {"value": world * flops / ((e2e_f + e2e_s) * 1e-3) / 1e9, "unit": "GFLOP/s",
            "definition": "sum c_j^2 / (refactor + solve) with every step's values and B copied host -> device "
                          "and X device -> host inside the timed region",
            "h2d_bytes_per_step": int(A.nnz * 8 + A.n * nrhs * 8), "d2h_bytes_per_step": int(A.n * nrhs * 8),
-           "factor_ms": e2e_f, "solve_ms": e2e_s, "steps": ne2e}
+           "factor_ms": e2e_f, "solve_ms": e2e_s, "steps": ne2e, **e2e_x}
 
     peaks, peak_kind = _peaks()
     # ---- measured FMA peaks (the SIMT roofline denominators), clocks sampled meanwhile
@@ -704,14 +722,14 @@ def main():
         kc = max(3, min(K, 10))
         cf, cs, cl, ce, ci, cc = _timed_steps(numc, dv, Bd, Xc, stream, kc, **ckw)
         cfm, csm = sum(cf) / kc, sum(cs) / kc
-        ce2e_f, ce2e_s = _e2e(numc, A, B, stream, ne2e, **ckw)
+        ce2e_f, ce2e_s, ce2e_x = _e2e(numc, A, B, stream, ne2e, **ckw)
         chosen = {"precision": "tf32x3", "solve": "conjugate gradients preconditioned by the factor (FP64 vectors)",
                   "steps": kc, "factor_ms": cfm, "solve_ms": csm, "total_ms": cfm + csm,
                   "factor_gflops": flops / (cfm * 1e-3) / 1e9, "iterations": max(ci), "eta_max": max(ce),
                   "converged": all(cc), "gpu_launches": cl,
                   "speedup_total_vs_fp64": (fac_ms + sol_ms) / K / (cfm + csm),
                   "e2e": {"factor_ms": ce2e_f, "solve_ms": ce2e_s, "total_ms": ce2e_f + ce2e_s,
-                          "speedup_vs_fp64_e2e": (e2e_f + e2e_s) / (ce2e_f + ce2e_s)}}
+                          "speedup_vs_fp64_e2e": (e2e_f + e2e_s) / (ce2e_f + ce2e_s), **ce2e_x}}
         if not args.no_profile:
             profc = numc.profile(dv)
             for _ in range(2):

@@ -306,7 +306,9 @@ typedef struct sc_solve_info {
                               condition number times the factor's unit roundoff
                               is too large for classical refinement to converge */
     int32_t max_iterations; /* in: iteration cap of this solve (0 = ir_maxit)    */
-    int32_t reserved[2];
+    float copy_in_ms;      /* out: device time of copying B in (host -> device
+                              when on_device = 0), part of solve_ms           */
+    float copy_out_ms;     /* out: device time of copying X out, part of solve_ms */
 } sc_solve_info;
 
 /* Solves A X = B (Sec. 1 step 4): permute, forward solve with L, backward

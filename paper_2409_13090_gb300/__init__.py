@@ -88,7 +88,7 @@ class SolveInfo(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("eta_max", C.c_double),
                 ("solve_ms", C.c_double), ("eta", C.c_void_p), ("refine", C.c_int32),
                 ("kernel_launches", C.c_int32), ("method", C.c_int32), ("max_iterations", C.c_int32),
-                ("reserved", C.c_int32 * 2)]
+                ("copy_in_ms", C.c_float), ("copy_out_ms", C.c_float)]
 
 
 class SCError(RuntimeError):
@@ -497,7 +497,8 @@ class Numeric:
         if rc not in (0, SC_ERR_NOT_CONVERGED):
             raise SCError(rc, "sc_solve")
         return X, {"iterations": info.iterations, "converged": bool(info.converged), "eta_max": info.eta_max,
-                   "eta": eta, "solve_ms": info.solve_ms, "rc": rc, "kernel_launches": info.kernel_launches}
+                   "eta": eta, "solve_ms": info.solve_ms, "rc": rc, "kernel_launches": info.kernel_launches,
+                "copy_in_ms": info.copy_in_ms, "copy_out_ms": info.copy_out_ms}
 
     def stall_next_factor(self, chunk: int):
         """Test hook (sc_test_stall_factor): the next refactor's units that read

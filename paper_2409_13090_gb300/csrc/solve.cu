@@ -1443,20 +1443,25 @@ int numeric_solve(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, dou
     if (nrhs > 1365) return -2;  // the reduction buffer holds 3 values per column (+ ||A||)
     if (h->stall_chunk >= 0) return solve_with_stall(h, nrhs, B, ldb, X, ldx, on_device, st, info);
     struct Events {  // destroyed on every return path
-        cudaEvent_t e[2] = {nullptr, nullptr};
+        cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
         ~Events() {
             for (cudaEvent_t x : e)
                 if (x) cudaEventDestroy(x);
         }
     } ev;
-    SC_CUDA(cudaEventCreate(&ev.e[0]));
-    SC_CUDA(cudaEventCreate(&ev.e[1]));
-    cudaEvent_t e0 = ev.e[0], e1 = ev.e[1];
+    for (cudaEvent_t &x : ev.e) SC_CUDA(cudaEventCreate(&x));
+    // e0 .. e_in: B in; e_out .. e1: X out
+    cudaEvent_t e0 = ev.e[0], e_in = ev.e[1], e_out = ev.e[2], e1 = ev.e[3];
     SC_CUDA(cudaEventRecord(e0, st));
-    // b (column-major, ld = n) on the device
-    for (int64_t c = 0; c < nrhs; c++)
-        SC_CUDA(cudaMemcpyAsync(h->d_b + c * n, B + c * ldb, n * sizeof(double),
-                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    // b (column-major, ld = n) on the device: one copy when the columns are contiguous
+    const cudaMemcpyKind kin = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (ldb == n) {
+        SC_CUDA(cudaMemcpyAsync(h->d_b, B, (size_t)n * nrhs * sizeof(double), kin, st));
+    } else {
+        for (int64_t c = 0; c < nrhs; c++)
+            SC_CUDA(cudaMemcpyAsync(h->d_b + c * n, B + c * ldb, n * sizeof(double), kin, st));
+    }
+    SC_CUDA(cudaEventRecord(e_in, st));
     // matrix values in CSR order and ||A||_inf (values may change with every refactor)
     int64_t nnzc = (int64_t)s->csr_col.size();
     k_gather_vals<<<(unsigned)((nnzc + 255) / 256), 256, 0, st>>>(h->d_csr_val, h->d_values, h->d_csr_map, nnzc);
@@ -1501,15 +1506,24 @@ int numeric_solve(sc_numeric *h, int64_t nrhs, const double *B, int64_t ldb, dou
             if (hist.size() > 3 && emax > 0.5 * hist[hist.size() - 4]) break;
         }
     }
-    for (int64_t c = 0; c < nrhs; c++)
-        SC_CUDA(cudaMemcpyAsync(X + c * ldx, h->d_xbest + c * n, n * sizeof(double),
-                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    SC_CUDA(cudaEventRecord(e_out, st));
+    const cudaMemcpyKind kout = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (ldx == n) {
+        SC_CUDA(cudaMemcpyAsync(X, h->d_xbest, (size_t)n * nrhs * sizeof(double), kout, st));
+    } else {
+        for (int64_t c = 0; c < nrhs; c++)
+            SC_CUDA(cudaMemcpyAsync(X + c * ldx, h->d_xbest + c * n, n * sizeof(double), kout, st));
+    }
     SC_CUDA(cudaEventRecord(e1, st));
     SC_CUDA(cudaStreamSynchronize(st));
-    float ms = 0.f;
+    float ms = 0.f, ms_in = 0.f, ms_out = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventElapsedTime(&ms_in, e0, e_in);
+    cudaEventElapsedTime(&ms_out, e_out, e1);
     bool conv = best <= tol;
     if (info) {
+        info->copy_in_ms = ms_in;
+        info->copy_out_ms = ms_out;
         info->iterations = it;
         info->converged = conv ? 1 : 0;
         info->eta_max = best;
