@@ -175,12 +175,18 @@ typedef struct sc_options {
                                   assembly is owned by the targets (a CTA per row slab
                                   of Lnz(P) adds P's update matrices in source order).
                                   The solve's reductions stay unordered. 0 = off. */
-    int32_t reserved[3];
+    int32_t threads;           /* host threads of the graph orderings (SC_ORDER_GRAPH_ND,
+                                  SC_ORDER_GRAPH_ML): the two halves of each of the top
+                                  nested-dissection splits are ordered concurrently.
+                                  The ordering is the same for every value.
+                                  0 = the host's hardware threads (at most 64); 1 = serial;
+                                  < 0 or > 1024 is an argument error (-4). */
+    int32_t reserved[2];
 } sc_options;
 
 /* Fills o with the defaults: SC_ORDER_NATURAL, nd_leaf 8, pr 1, SC_RLB, SC_FP64,
  * chunk 64, ir_tol 1e-14, ir_maxit 30, pivot_tau 2^-10, spin_limit 1<<22,
- * use_graph 1, merge_frac 0 (fundamental supernodes), tune NULL, deterministic 0. Returns
+ * use_graph 1, merge_frac 0 (fundamental supernodes), tune NULL, deterministic 0, threads 0. Returns
  * SC_OK, or -1 if o is NULL. */
 int sc_options_default(sc_options *o);
 

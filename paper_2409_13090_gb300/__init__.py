@@ -41,7 +41,7 @@ class Options(C.Structure):
                 ("precision", C.c_int32), ("chunk", C.c_int32), ("ir_tol", C.c_double),
                 ("ir_maxit", C.c_int32), ("pivot_tau", C.c_double), ("spin_limit", C.c_int64),
                 ("use_graph", C.c_int32), ("merge_frac", C.c_double), ("tune", C.c_void_p),
-                ("deterministic", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("deterministic", C.c_int32), ("threads", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 TUNE_FIELDS = ["tile_min_entries", "tile_min_k", "loop_budget", "lookahead", "tc_min_k", "tc_wide_n", "thin_dim",
@@ -267,8 +267,8 @@ class Symbolic:
 
     def __init__(self, A=None, *, ordering="natural", grid=None, nd_leaf=8, user_perm=None, pr=True,
                  variant="rlb", precision="fp64", chunk=64, ir_tol=1e-14, ir_maxit=30, use_graph=True,
-                 merge=0.0, spin_limit=None, pivot_tau=None, tune=None, deterministic=False, _handle=None,
-                 _parts=None):
+                 merge=0.0, spin_limit=None, pivot_tau=None, tune=None, deterministic=False, threads=0,
+                 _handle=None, _parts=None):
         self._parts = _parts
         if _handle is not None:
             self._h = _handle
@@ -293,6 +293,7 @@ class Symbolic:
         o.use_graph = 1 if use_graph else 0
         o.merge_frac = float(merge)
         o.deterministic = 1 if deterministic else 0
+        o.threads = int(threads)
         if spin_limit is not None:
             o.spin_limit = int(spin_limit)
         if pivot_tau is not None:

@@ -14,10 +14,15 @@
 //   - partition refinement with an in-place, array-based partition;
 //   - relindB(J,P) by composition with relind(C,P), as Alg. 5 composes them.
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
+#include <exception>
+#include <memory>
 #include <numeric>
 #include <set>
+#include <system_error>
+#include <thread>
 
 #include "sc_internal.h"
 
@@ -398,21 +403,46 @@ std::vector<int32_t> min_cover(const WGraph &g, const std::vector<int8_t> &part,
 // separator.
 class GraphND {
   public:
+    // threads: the top ceil(log2(threads)) levels of splits order their two
+    // halves on two threads (halves of at least kForkMin vertices). Every
+    // subproblem depends only on its own vertex set, so the order is the same
+    // for any thread count.
     GraphND(int64_t n, const std::vector<int64_t> &ptr, const std::vector<int32_t> &adj, int leaf,
-            std::vector<int32_t> &out, bool multilevel = false)
-        : ptr_(ptr), adj_(adj), leaf_(leaf), out_(out), inset_(n, 0), seen_(n, 0), loc_(n, -1),
-          multilevel_(multilevel) {}
+            std::vector<int32_t> &out, bool multilevel, int threads)
+        : n_(n), ptr_(ptr), adj_(adj), leaf_(leaf), out_(out), inset_(new std::atomic<int32_t>[n]), seen_(n, 0),
+          loc_(n, -1), multilevel_(multilevel) {
+        for (int64_t v = 0; v < n; v++) inset_[v].store(0, std::memory_order_relaxed);
+        while ((1 << fork_depth_) < threads) fork_depth_++;
+    }
 
-    void order(std::vector<int32_t> S) {
+    // The order of all n vertices, written to out (resized to n).
+    void run() {
+        std::vector<int32_t> all(n_);
+        std::iota(all.begin(), all.end(), 0);
+        out_.assign(n_, -1);
+        order(std::move(all), 0, 0);
+    }
+
+  private:
+    static constexpr int64_t kForkMin = 2048;
+
+    // A subproblem stamps its own vertices in inset_ and reads the stamps of
+    // their neighbours, which a concurrent subproblem may be writing: relaxed
+    // atomics (stamps are unique, so another set's stamp never matches).
+    // seen_ and loc_ are read and written only at the subproblem's own vertices.
+    bool in_set(int32_t u, int32_t st) const { return inset_[u].load(std::memory_order_relaxed) == st; }
+
+    // Orders the vertex set S (sorted) into out_[off, off + |S|).
+    void order(std::vector<int32_t> S, int64_t off, int depth) {
         if ((int64_t)S.size() <= leaf_) {
-            out_.insert(out_.end(), S.begin(), S.end());
+            std::copy(S.begin(), S.end(), out_.begin() + off);
             return;
         }
-        const int32_t st = ++set_stamp_;
-        for (int32_t v : S) inset_[v] = st;
+        const int32_t st = set_stamp_.fetch_add(1) + 1;
+        for (int32_t v : S) inset_[v].store(st, std::memory_order_relaxed);
         // connected components of G[S]
         std::vector<std::vector<int32_t>> comps;
-        const int32_t cs = ++seen_stamp_;
+        const int32_t cs = seen_stamp_.fetch_add(1) + 1;
         for (int32_t v : S) {
             if (seen_[v] == cs) continue;
             std::vector<int32_t> comp{v};
@@ -420,7 +450,7 @@ class GraphND {
             for (size_t h = 0; h < comp.size(); h++)
                 for (int64_t p = ptr_[comp[h]]; p < ptr_[comp[h] + 1]; p++) {
                     const int32_t u = adj_[p];
-                    if (inset_[u] == st && seen_[u] != cs) {
+                    if (in_set(u, st) && seen_[u] != cs) {
                         seen_[u] = cs;
                         comp.push_back(u);
                     }
@@ -429,7 +459,11 @@ class GraphND {
             comps.push_back(std::move(comp));
         }
         if (comps.size() > 1) {
-            for (auto &c : comps) order(std::move(c));
+            for (auto &c : comps) {
+                const int64_t size = (int64_t)c.size();
+                order(std::move(c), off, depth);
+                off += size;
+            }
             return;
         }
         // pseudo-peripheral root and its level structure
@@ -439,7 +473,7 @@ class GraphND {
             int32_t cand = -1, cdeg = 0;
             for (int32_t v : L.back()) {
                 int32_t d = 0;
-                for (int64_t p = ptr_[v]; p < ptr_[v + 1]; p++) d += inset_[adj_[p]] == st;
+                for (int64_t p = ptr_[v]; p < ptr_[v + 1]; p++) d += in_set(adj_[p], st);
                 if (cand < 0 || d < cdeg || (d == cdeg && v < cand)) {
                     cand = v;
                     cdeg = d;
@@ -466,12 +500,40 @@ class GraphND {
         std::sort(left.begin(), left.end());
         std::sort(right.begin(), right.end());
         std::sort(sep.begin(), sep.end());
-        order(std::move(left));
-        order(std::move(right));
-        out_.insert(out_.end(), sep.begin(), sep.end());
+        const int64_t nl = (int64_t)left.size(), nr = (int64_t)right.size();
+        std::copy(sep.begin(), sep.end(), out_.begin() + off + nl + nr);
+        S.clear();
+        S.shrink_to_fit();
+        if (depth < fork_depth_ && nl >= kForkMin && nr >= kForkMin) {
+            std::exception_ptr err;
+            std::thread t;
+            try {
+                t = std::thread([&] {
+                    try {
+                        order(std::move(left), off, depth + 1);
+                    } catch (...) {
+                        err = std::current_exception();
+                    }
+                });
+            } catch (const std::system_error &) {  // no thread to be had: this one does both halves
+                order(std::move(left), off, depth + 1);
+                order(std::move(right), off + nl, depth + 1);
+                return;
+            }
+            try {
+                order(std::move(right), off + nl, depth + 1);
+            } catch (...) {
+                t.join();
+                throw;
+            }
+            t.join();
+            if (err) std::rethrow_exception(err);
+            return;
+        }
+        order(std::move(left), off, depth + 1);
+        order(std::move(right), off + nl, depth + 1);
     }
 
-  private:
     // The multilevel split of the connected set S (sorted, stamped st): fills
     // left / right / sep and returns true when its separator is smaller than
     // level_sep vertices and both parts are non-empty.
@@ -484,7 +546,7 @@ class GraphND {
         for (int32_t i = 0; i < m; i++) loc_[S[i]] = i;
         for (int32_t i = 0; i < m; i++)
             for (int64_t p = ptr_[S[i]]; p < ptr_[S[i] + 1]; p++)
-                if (inset_[adj_[p]] == st) g.adj[i].emplace_back(loc_[adj_[p]], 1);
+                if (in_set(adj_[p], st)) g.adj[i].emplace_back(loc_[adj_[p]], 1);
         const std::vector<int8_t> part = ml::bisect(g);
         std::vector<int32_t> b[2];
         for (int32_t i = 0; i < m; i++)
@@ -509,7 +571,7 @@ class GraphND {
 
     // breadth-first levels of G[S] (S = vertices stamped st) from root
     std::vector<std::vector<int32_t>> levels(int32_t root, int32_t st) {
-        const int32_t bs = ++seen_stamp_;
+        const int32_t bs = seen_stamp_.fetch_add(1) + 1;
         std::vector<std::vector<int32_t>> L{{root}};
         seen_[root] = bs;
         while (true) {
@@ -517,7 +579,7 @@ class GraphND {
             for (int32_t v : L.back())
                 for (int64_t p = ptr_[v]; p < ptr_[v + 1]; p++) {
                     const int32_t u = adj_[p];
-                    if (inset_[u] == st && seen_[u] != bs) {
+                    if (in_set(u, st) && seen_[u] != bs) {
                         seen_[u] = bs;
                         next.push_back(u);
                     }
@@ -528,13 +590,16 @@ class GraphND {
         return L;
     }
 
+    const int64_t n_;
     const std::vector<int64_t> &ptr_;
     const std::vector<int32_t> &adj_;
     int64_t leaf_;
     std::vector<int32_t> &out_;
-    std::vector<int32_t> inset_, seen_, loc_;
+    std::unique_ptr<std::atomic<int32_t>[]> inset_;
+    std::vector<int32_t> seen_, loc_;
     bool multilevel_;
-    int32_t set_stamp_ = 0, seen_stamp_ = 0;
+    int fork_depth_ = 0;
+    std::atomic<int32_t> set_stamp_{0}, seen_stamp_{0};
 };
 
 void build_adjacency(int64_t n, const int64_t *colptr, const int32_t *rowind, std::vector<int64_t> &ptr,
@@ -795,12 +860,11 @@ int analyze_impl(int64_t n, const int64_t *colptr, const int32_t *rowind, const 
     build_adjacency(n, colptr, rowind, aptr, adj);
     if (o.ordering == SC_ORDER_GRAPH_ND || o.ordering == SC_ORDER_GRAPH_ML) {
         if (o.nd_leaf < 1) return -4;
-        p0.clear();
-        p0.reserve(n);
-        std::vector<int32_t> all(n);
-        std::iota(all.begin(), all.end(), 0);
-        GraphND(n, aptr, adj, o.nd_leaf, p0, o.ordering == SC_ORDER_GRAPH_ML).order(std::move(all));
-        if ((int64_t)p0.size() != n) return SC_ERR_INTERNAL;
+        int threads = o.threads;
+        if (threads == 0) threads = (int)std::min(64u, std::max(1u, std::thread::hardware_concurrency()));
+        GraphND(n, aptr, adj, o.nd_leaf, p0, o.ordering == SC_ORDER_GRAPH_ML, threads).run();
+        for (int64_t k = 0; k < n; k++)
+            if (p0[k] < 0) return SC_ERR_INTERNAL;
     }
     std::vector<int32_t> ip0(n);
     for (int64_t k = 0; k < n; k++) ip0[p0[k]] = (int32_t)k;

@@ -43,6 +43,7 @@ int sc_analyze(int64_t n, const int64_t *colptr, const int32_t *rowind, const sc
     if (!(opt.merge_frac >= 0.0)) return -4;
     if (opt.tune && !sc::tune_valid(*opt.tune)) return -4;
     if (opt.deterministic != 0 && !(opt.deterministic == 1 && opt.variant == SC_RL)) return -4;
+    if (opt.threads < 0 || opt.threads > 1024) return -4;
     try {
         return sc::analyze_impl(n, colptr, rowind, opt, out);
     } catch (const std::bad_alloc &) {

@@ -214,6 +214,49 @@ def test_graph_nd_ordering_bit_exact(case, leaf, ordering):
     assert np.array_equal(v["perm"][np.argsort(v["perm"])], np.arange(A.n))
 
 
+@pytest.mark.parametrize("ordering", ["graph_nd", "graph_ml"])
+@pytest.mark.parametrize("case", ["grid2d", "two_components"])
+def test_graph_orderings_with_threads(case, ordering):
+    """Graphs large enough that the top nested-dissection splits order their
+    halves on separate threads (halves of at least 2048 vertices): the default
+    thread count gives the oracle's permutation and symbolic arrays, and 1, 2,
+    3 and 8 threads give the same permutation."""
+    if case == "grid2d":
+        A = inputs.laplacian_2d(100, 90)
+    else:
+        # a 2D grid and a 3D grid, labels interleaved: the components are ordered one by one
+        rng = np.random.default_rng(4)
+        n2, n3 = 80 * 64, 16 * 15 * 14
+        lab = rng.permutation(n2 + n3)
+        ents = []
+        for y in range(64):
+            for x in range(80):
+                v = x + 80 * y
+                if x + 1 < 80:
+                    ents.append((v, v + 1))
+                if y + 1 < 64:
+                    ents.append((v, v + 80))
+        for z in range(14):
+            for y in range(15):
+                for x in range(16):
+                    v = n2 + x + 16 * (y + 15 * z)
+                    if x + 1 < 16:
+                        ents.append((v, v + 1))
+                    if y + 1 < 15:
+                        ents.append((v, v + 16))
+                    if z + 1 < 14:
+                        ents.append((v, v + 240))
+        ents = [(max(lab[a], lab[b]), min(lab[a], lab[b])) for a, b in ents]
+        A = inputs.from_lower_pattern(n2 + n3, ents, seed=5)
+    A.grid = None
+    v = _compare(A, graph_nd=ordering == "graph_nd", graph_ml=ordering == "graph_ml", leaf=8, pr=False)
+    for th in (1, 2, 3, 8):
+        w = sc.Symbolic(A, ordering=ordering, nd_leaf=8, pr=False, threads=th).view()
+        assert np.array_equal(w["perm"], v["perm"]), th
+    with pytest.raises(sc.SCError):
+        sc.Symbolic(A, ordering=ordering, threads=-1)
+
+
 def test_graph_nd_fill_close_to_geometric_nd():
     """On a 3D grid given without coordinates the graph ordering's fill stays
     within a small factor of the geometric ND and well below the natural order."""
