@@ -20,6 +20,7 @@
 #include <exception>
 #include <memory>
 #include <numeric>
+#include <queue>
 #include <set>
 #include <system_error>
 #include <thread>
@@ -745,7 +746,18 @@ void merge_supernodes(int64_t n, double frac, std::vector<int32_t> &sup_ptr, std
     // sizes and the parent column are all the merging needs.
     const int64_t ns = (int64_t)sup_ptr.size() - 1;
     auto trap = [](int64_t w, int64_t m) { return w * m - w * (w - 1) / 2; };
-    std::vector<int32_t> f(ns), l(ns), own(sup_of);
+    // owner of a column: find() over the merges from its fundamental supernode
+    // (rep[X] = the supernode X was merged into, path-halved)
+    std::vector<int32_t> f(ns), l(ns), rep(ns);
+    std::iota(rep.begin(), rep.end(), 0);
+    auto find = [&](int32_t X) {
+        while (rep[X] != X) {
+            rep[X] = rep[rep[X]];
+            X = rep[X];
+        }
+        return X;
+    };
+    auto own = [&](int32_t j) { return find(sup_of[j]); };
     std::vector<int64_t> w(ns), m(ns);
     std::vector<char> alive(ns, 1);
     int64_t S0 = 0;
@@ -758,40 +770,48 @@ void merge_supernodes(int64_t n, double frac, std::vector<int32_t> &sup_ptr, std
     }
     auto parent_now = [&](int64_t X) -> int32_t {
         const int32_t r = parent[l[X]];
-        return r < 0 ? -1 : own[r];
+        return r < 0 ? -1 : own(r);
     };
+    // Candidates in a binary min-heap of (fill, first column, X) with lazy
+    // deletion: an entry whose key is no longer X's current key is skipped when
+    // it reaches the top, so the top valid entry is always the least (fill,
+    // first column) among the current candidates.
     typedef std::pair<int64_t, int32_t> Key;  // (fill, first column)
-    std::set<std::pair<Key, int32_t>> cand;
+    typedef std::pair<Key, int32_t> Entry;
+    std::priority_queue<Entry, std::vector<Entry>, std::greater<Entry>> cand;
     std::vector<Key> key(ns, Key(-1, -1));
     auto refresh = [&](int32_t X) {
-        if (key[X].first >= 0) cand.erase({key[X], X});
         key[X] = Key(-1, -1);
         if (!alive[X]) return;
         int32_t P = parent_now(X);
         if (P < 0 || l[X] + 1 != f[P]) return;
         int64_t fill = trap(w[X] + w[P], w[X] + m[P]) - trap(w[X], m[X]) - trap(w[P], m[P]);
         key[X] = Key(fill, f[X]);
-        cand.insert({key[X], X});
+        cand.push({key[X], X});
     };
     for (int32_t X = 0; X < ns; X++) refresh(X);
     int64_t added = 0;
     while (!cand.empty()) {
-        auto it = cand.begin();
-        int64_t fill = it->first.first;
-        int32_t X = it->second;
+        const Entry top = cand.top();
+        const int32_t X = top.second;
+        if (!alive[X] || key[X] != top.first) {  // stale
+            cand.pop();
+            continue;
+        }
+        int64_t fill = top.first.first;
         if ((double)(added + fill) > frac * (double)S0) break;
         int32_t P = parent_now(X);
-        cand.erase(it);
+        cand.pop();
         key[X] = Key(-1, -1);
         added += fill;
         alive[X] = 0;
-        for (int32_t j = f[X]; j <= l[X]; j++) own[j] = P;
+        rep[X] = P;
         m[P] += w[X];
         w[P] += w[X];
         f[P] = f[X];
         refresh(P);
         if (f[P] > 0) {
-            int32_t C = own[f[P] - 1];
+            int32_t C = own(f[P] - 1);
             if (alive[C] && parent_now(C) == P) refresh(C);
         }
     }
