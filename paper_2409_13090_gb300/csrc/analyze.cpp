@@ -772,13 +772,20 @@ void merge_supernodes(int64_t n, double frac, std::vector<int32_t> &sup_ptr, std
         const int32_t r = parent[l[X]];
         return r < 0 ? -1 : own(r);
     };
-    // Candidates in a binary min-heap of (fill, first column, X) with lazy
-    // deletion: an entry whose key is no longer X's current key is skipped when
-    // it reaches the top, so the top valid entry is always the least (fill,
-    // first column) among the current candidates.
+    // Candidates ordered by (fill, first column), with lazy deletion: an entry
+    // whose key is no longer X's current key is dropped when it comes to the
+    // top. Fills below kSmall (most merges) sit in one bucket per fill, each a
+    // min-heap of (first column, X); larger fills in one heap of (fill, first
+    // column, X). The first valid entry of the lowest non-empty bucket, else
+    // of the large heap, is the least current candidate. (fill >= 0: the
+    // merged trapezoid holds X's columns padded to P's rows plus P itself.)
     typedef std::pair<int64_t, int32_t> Key;  // (fill, first column)
     typedef std::pair<Key, int32_t> Entry;
-    std::priority_queue<Entry, std::vector<Entry>, std::greater<Entry>> cand;
+    typedef std::pair<int32_t, int32_t> Small;  // (first column, X)
+    constexpr int64_t kSmall = 64;
+    std::vector<std::vector<Small>> bucket(kSmall);
+    int64_t lo = kSmall;  // buckets below lo are empty
+    std::priority_queue<Entry, std::vector<Entry>, std::greater<Entry>> large;
     std::vector<Key> key(ns, Key(-1, -1));
     auto refresh = [&](int32_t X) {
         key[X] = Key(-1, -1);
@@ -787,21 +794,57 @@ void merge_supernodes(int64_t n, double frac, std::vector<int32_t> &sup_ptr, std
         if (P < 0 || l[X] + 1 != f[P]) return;
         int64_t fill = trap(w[X] + w[P], w[X] + m[P]) - trap(w[X], m[X]) - trap(w[P], m[P]);
         key[X] = Key(fill, f[X]);
-        cand.push({key[X], X});
+        if (fill >= 0 && fill < kSmall) {
+            bucket[fill].emplace_back(f[X], X);
+            std::push_heap(bucket[fill].begin(), bucket[fill].end(), std::greater<Small>());
+            lo = std::min(lo, fill);
+        } else {
+            large.push({key[X], X});
+        }
+    };
+    // the least current candidate (X = -1: none); stale entries on the way are dropped
+    auto least = [&](Key &k) -> int32_t {
+        for (; lo < kSmall; lo++) {
+            std::vector<Small> &h = bucket[lo];
+            while (!h.empty()) {
+                const int32_t X = h.front().second;
+                if (alive[X] && key[X] == Key(lo, h.front().first)) {
+                    k = key[X];
+                    return X;
+                }
+                std::pop_heap(h.begin(), h.end(), std::greater<Small>());
+                h.pop_back();
+            }
+        }
+        while (!large.empty()) {
+            const int32_t X = large.top().second;
+            if (alive[X] && key[X] == large.top().first) {
+                k = key[X];
+                return X;
+            }
+            large.pop();
+        }
+        return -1;
+    };
+    auto drop = [&](const Key &k) {  // removes the entry least() returned
+        if (k.first >= 0 && k.first < kSmall) {
+            std::vector<Small> &h = bucket[k.first];
+            std::pop_heap(h.begin(), h.end(), std::greater<Small>());
+            h.pop_back();
+        } else {
+            large.pop();
+        }
     };
     for (int32_t X = 0; X < ns; X++) refresh(X);
     int64_t added = 0;
-    while (!cand.empty()) {
-        const Entry top = cand.top();
-        const int32_t X = top.second;
-        if (!alive[X] || key[X] != top.first) {  // stale
-            cand.pop();
-            continue;
-        }
-        int64_t fill = top.first.first;
+    while (true) {
+        Key k;
+        const int32_t X = least(k);
+        if (X < 0) break;
+        int64_t fill = k.first;
         if ((double)(added + fill) > frac * (double)S0) break;
         int32_t P = parent_now(X);
-        cand.pop();
+        drop(k);
         key[X] = Key(-1, -1);
         added += fill;
         alive[X] = 0;
