@@ -1,8 +1,9 @@
 /* Host-only use of the C ABI from plain C99 (no device work): analyse a 2D
  * 5-point Laplacian on an n x n grid with the geometric and the two graph
- * orderings, read the symbolic view, check the device schedule, query the
- * launch plan, save and reload the analysis; a deterministic RL analysis with
- * a launch-plan table. Prints one line per ordering and one for the last;
+ * orderings (the graph orderings also on 1 and 5 threads: the same order),
+ * read the symbolic view, check the device schedule, query the launch plan,
+ * save and reload the analysis; a deterministic RL analysis with a
+ * launch-plan table. Prints one line per ordering and one for the last;
  * exits non-zero on the first failed call. Build: cc -std=c99 -I include
  * abi_check.c -L <lib dir> -lsc. */
 #include <stdio.h>
@@ -56,6 +57,24 @@ int main(int argc, char **argv) {
             memcmp(w.perm, v.perm, (size_t)n * sizeof(int32_t)) != 0) {
             fprintf(stderr, "reloaded analysis differs\n");
             return 1;
+        }
+        if (orderings[o] != SC_ORDER_GRID_ND) { /* the graph orderings: the same order on 1 and 5 threads */
+            for (int th = 1; th <= 5; th += 4) {
+                sc_symbolic *u = NULL;
+                sc_symbolic_view x;
+                opt.threads = th;
+                CHECK(sc_analyze(n, colptr, rowind, &opt, &u));
+                CHECK(sc_symbolic_export(u, &x));
+                if (memcmp(x.perm, v.perm, (size_t)n * sizeof(int32_t)) != 0) {
+                    fprintf(stderr, "ordering %d on %d threads differs\n", orderings[o], th);
+                    return 1;
+                }
+                CHECK(sc_symbolic_free(u));
+            }
+            sc_symbolic *r = NULL;
+            opt.threads = -1;
+            if (sc_analyze(n, colptr, rowind, &opt, &r) != -4 || r != NULL) return 1;
+            opt.threads = 0;
         }
         printf("ordering %d n %lld nsuper %lld nnzL %lld flops %.6g products %lld levels %lld\n", orderings[o],
                (long long)v.n, (long long)v.nsuper, (long long)v.nnzL, v.flops, (long long)chk[0],

@@ -577,9 +577,9 @@ def test_symbolic_load_rejects_damaged_files(tmp_path):
 
 def test_c_abi_from_plain_c(tmp_path):
     """include/sc.h compiles as C99 with warnings as errors, and a C program
-    drives the host half of the ABI (analysis with three orderings, export,
-    schedule check, plan, save / load) against the built library; its numbers
-    match the Python binding's."""
+    drives the host half of the ABI (analysis with three orderings, the graph
+    orderings also on 1 and 5 threads, export, schedule check, plan, save /
+    load) against the built library; its numbers match the Python binding's."""
     import shutil
     import subprocess
     cc = shutil.which("gcc") or shutil.which("cc")
@@ -602,6 +602,9 @@ def test_c_abi_from_plain_c(tmp_path):
                      tune=dict(defer_width=1024, solve_group=3, tc_multicast=-1)).plan_stats("fp64")
     f = out[3].split()
     assert f[:2] == ["deterministic", "rl"] and int(f[3]) == st["rl_pairs"] and int(f[5]) == st["rl_slabs"], out[3]
+    # an 80 x 80 grid: the top splits of the graph orderings run on two threads
+    out = subprocess.check_output([str(exe), "80", str(tmp_path / "b.scs")], text=True).splitlines()
+    assert len(out) == 4
 
 
 @pytest.mark.parametrize("seed", range(12))
