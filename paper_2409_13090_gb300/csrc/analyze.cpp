@@ -31,6 +31,29 @@ namespace sc {
 
 namespace {
 
+// Runs body(lo, hi) over [0, n) in blocks of `block`, taken from a shared
+// counter by up to `threads` threads (the caller is one of them). body must
+// not throw; its blocks must write disjoint data. Without a thread to be had
+// the caller does the remaining blocks alone.
+template <class F>
+void parallel_blocks(int64_t n, int64_t block, int threads, const F &body) {
+    std::atomic<int64_t> next{0};
+    auto work = [&] {
+        for (int64_t lo = next.fetch_add(block); lo < n; lo = next.fetch_add(block)) body(lo, std::min(n, lo + block));
+    };
+    std::vector<std::thread> pool;
+    const int64_t extra = std::min<int64_t>(threads, (n + block - 1) / block) - 1;
+    for (int64_t t = 0; t < extra; t++) {
+        try {
+            pool.emplace_back(work);
+        } catch (const std::system_error &) {
+            break;
+        }
+    }
+    work();
+    for (auto &t : pool) t.join();
+}
+
 int validate(int64_t n, const int64_t *colptr, const int32_t *rowind) {
     if (n <= 0 || n > INT32_MAX - 1) return -1;
     if (!colptr) return -2;
@@ -894,6 +917,8 @@ int analyze_impl(int64_t n, const int64_t *colptr, const int32_t *rowind, const 
     s->opt.tune = nullptr;
     if (o.tune) s->tune = *o.tune;
     int64_t nnzA = colptr[n];
+    const int threads =
+        o.threads > 0 ? o.threads : (int)std::min(64u, std::max(1u, std::thread::hardware_concurrency()));
     s->colptr.assign(colptr, colptr + n + 1);
     s->rowind.assign(rowind, rowind + nnzA);
 
@@ -923,8 +948,6 @@ int analyze_impl(int64_t n, const int64_t *colptr, const int32_t *rowind, const 
     build_adjacency(n, colptr, rowind, aptr, adj);
     if (o.ordering == SC_ORDER_GRAPH_ND || o.ordering == SC_ORDER_GRAPH_ML) {
         if (o.nd_leaf < 1) return -4;
-        int threads = o.threads;
-        if (threads == 0) threads = (int)std::min(64u, std::max(1u, std::thread::hardware_concurrency()));
         GraphND(n, aptr, adj, o.nd_leaf, p0, o.ordering == SC_ORDER_GRAPH_ML, threads).run();
         for (int64_t k = 0; k < n; k++)
             if (p0[k] < 0) return SC_ERR_INTERNAL;
@@ -1159,13 +1182,15 @@ int analyze_impl(int64_t n, const int64_t *colptr, const int32_t *rowind, const 
     for (int64_t J = 0; J < ns; J++)
         s->gl_ptr[J + 1] = s->gl_ptr[J] + (sup_ptr[J + 1] - sup_ptr[J]) + (sptr[J + 1] - sptr[J]);
     s->glbind.resize(s->gl_ptr[ns]);
-    for (int64_t J = 0; J < ns; J++) {
-        int64_t w = s->gl_ptr[J];
-        for (int32_t j = sup_ptr[J]; j < sup_ptr[J + 1]; j++) s->glbind[w++] = j;
-        int64_t b = w;
-        for (int64_t p = sptr[J]; p < sptr[J + 1]; p++) s->glbind[w++] = lab[srows[p]];
-        std::sort(s->glbind.begin() + b, s->glbind.begin() + w);
-    }
+    parallel_blocks(ns, 256, threads, [&](int64_t J0, int64_t J1) {
+        for (int64_t J = J0; J < J1; J++) {
+            int64_t w = s->gl_ptr[J];
+            for (int32_t j = sup_ptr[J]; j < sup_ptr[J + 1]; j++) s->glbind[w++] = j;
+            int64_t b = w;
+            for (int64_t p = sptr[J]; p < sptr[J + 1]; p++) s->glbind[w++] = lab[srows[p]];
+            std::sort(s->glbind.begin() + b, s->glbind.begin() + w);
+        }
+    });
     s->sup_parent = spar;
     s->nnzL = 0;
     for (int64_t J = 0; J < ns; J++) {
@@ -1288,18 +1313,25 @@ int analyze_impl(int64_t n, const int64_t *colptr, const int32_t *rowind, const 
 
     // ---- map of A's entries into Lnz
     s->valmap.resize(nnzA);
-    for (int64_t c = 0; c < n; c++)
-        for (int64_t p = colptr[c]; p < colptr[c + 1]; p++) {
-            int32_t a = s->iperm[rowind[p]], b = s->iperm[c];
-            int32_t col = std::min(a, b), row = std::max(a, b);
-            int32_t J = sup_of[col];
-            int32_t f = sup_ptr[J];
-            int64_t m = s->gl_ptr[J + 1] - s->gl_ptr[J];
-            const int32_t *g = s->glbind.data() + s->gl_ptr[J];
-            int64_t pos = std::lower_bound(g, g + m, row) - g;
-            if (pos >= m || g[pos] != row) return SC_ERR_INTERNAL;
-            s->valmap[p] = s->lnz_off[J] + pos * s->lnz_ld[J] + (col - f);
-        }
+    std::atomic<bool> missing{false};
+    parallel_blocks(n, 4096, threads, [&](int64_t c0, int64_t c1) {
+        for (int64_t c = c0; c < c1; c++)
+            for (int64_t p = colptr[c]; p < colptr[c + 1]; p++) {
+                int32_t a = s->iperm[rowind[p]], b = s->iperm[c];
+                int32_t col = std::min(a, b), row = std::max(a, b);
+                int32_t J = sup_of[col];
+                int32_t f = sup_ptr[J];
+                int64_t m = s->gl_ptr[J + 1] - s->gl_ptr[J];
+                const int32_t *g = s->glbind.data() + s->gl_ptr[J];
+                int64_t pos = std::lower_bound(g, g + m, row) - g;
+                if (pos >= m || g[pos] != row) {
+                    missing.store(true, std::memory_order_relaxed);
+                    return;
+                }
+                s->valmap[p] = s->lnz_off[J] + pos * s->lnz_ld[J] + (col - f);
+            }
+    });
+    if (missing.load()) return SC_ERR_INTERNAL;
 
     // ---- full symmetric CSR of A (caller's ordering) for the FP64 residual
     s->csr_ptr.assign(n + 1, 0);
