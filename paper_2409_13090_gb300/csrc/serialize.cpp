@@ -134,6 +134,7 @@ extern "C" int sc_symbolic_save(const sc_symbolic *s, const char *path) {
         sc_options o = s->opt;
         o.user_perm = nullptr;
         o.tune = nullptr;
+        o.threads = 0;  // how the analysis ran, not what it produced
         w.val(o);
         w.val(s->tune);
         w.val(s->n);
