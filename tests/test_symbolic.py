@@ -257,7 +257,7 @@ def test_graph_orderings_with_threads(case, ordering):
         sc.Symbolic(A, ordering=ordering, threads=-1)
 
 
-@pytest.mark.parametrize("case", ["grid_merge", "graph_ml"])
+@pytest.mark.parametrize("case", ["grid_merge", "graph_ml", "graph_nd_shortcuts"])
 def test_analysis_same_for_every_thread_count(tmp_path, case):
     """The saved analysis (every array: structures, relind(B), the map of A's
     entries into Lnz, the residual's CSR, the launch plan inputs) is byte for
@@ -266,10 +266,19 @@ def test_analysis_same_for_every_thread_count(tmp_path, case):
     if case == "grid_merge":
         A = inputs.diffusion_3d_7pt(32, 32, 30, seed=7)
         kw = dict(ordering="grid_nd", grid=A.grid, merge=0.125)
-    else:
+    elif case == "graph_ml":
         A = inputs.laplacian_2d(120, 100)
         A.grid = None
         kw = dict(ordering="graph_ml")
+    else:
+        # a 2D grid with 600 random long-range edges: irregular separators
+        rng = np.random.default_rng(8)
+        k = 110
+        ents = [(v + 1, v) for v in range(k * k) if (v % k) + 1 < k] + [(v + k, v) for v in range(k * k - k)]
+        a, b = rng.integers(0, k * k, 600), rng.integers(0, k * k, 600)
+        ents += [(int(max(x, y)), int(min(x, y))) for x, y in zip(a, b) if x != y]
+        A = inputs.from_lower_pattern(k * k, sorted(set(ents)), seed=9)
+        kw = dict(ordering="graph_nd", merge=0.125)
     blobs = []
     for th in (1, 2, 8):
         path = tmp_path / f"a{th}.scs"
