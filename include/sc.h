@@ -178,9 +178,9 @@ typedef struct sc_options {
     int32_t threads;           /* host threads of sc_analyze: the graph orderings
                                   (SC_ORDER_GRAPH_ND, SC_ORDER_GRAPH_ML) order the two
                                   halves of each of the top nested-dissection splits
-                                  concurrently, and the per-supernode glbind sort and
-                                  the map of A's entries into Lnz run in blocks on
-                                  these threads. The analysis is the same for every
+                                  concurrently, and the partition refinement, the
+                                  per-supernode glbind sort and the map of A's entries
+                                  into Lnz run in blocks on these threads. The analysis is the same for every
                                   value. 0 = the host's hardware threads (at most 64);
                                   1 = serial; < 0 or > 1024 is an argument error (-4). */
     int32_t reserved[2];

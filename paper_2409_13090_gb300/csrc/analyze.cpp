@@ -32,14 +32,23 @@ namespace sc {
 namespace {
 
 // Runs body(lo, hi) over [0, n) in blocks of `block`, taken from a shared
-// counter by up to `threads` threads (the caller is one of them). body must
-// not throw; its blocks must write disjoint data. Without a thread to be had
-// the caller does the remaining blocks alone.
+// counter by up to `threads` threads (the caller is one of them); the blocks
+// must write disjoint data. Without a thread to be had the caller does the
+// remaining blocks alone. An exception in a block stops the taking of new
+// blocks and is rethrown to the caller once every thread has ended.
 template <class F>
 void parallel_blocks(int64_t n, int64_t block, int threads, const F &body) {
     std::atomic<int64_t> next{0};
+    std::atomic<bool> failed{false};
+    std::exception_ptr first;  // written once, by the thread that sets failed
     auto work = [&] {
-        for (int64_t lo = next.fetch_add(block); lo < n; lo = next.fetch_add(block)) body(lo, std::min(n, lo + block));
+        for (int64_t lo = next.fetch_add(block); lo < n && !failed.load(); lo = next.fetch_add(block)) {
+            try {
+                body(lo, std::min(n, lo + block));
+            } catch (...) {
+                if (!failed.exchange(true)) first = std::current_exception();
+            }
+        }
     };
     std::vector<std::thread> pool;
     const int64_t extra = std::min<int64_t>(threads, (n + block - 1) / block) - 1;
@@ -52,6 +61,7 @@ void parallel_blocks(int64_t n, int64_t block, int threads, const F &body) {
     }
     work();
     for (auto &t : pool) t.join();
+    if (first) std::rethrow_exception(first);
 }
 
 int validate(int64_t n, const int64_t *colptr, const int32_t *rowind) {
@@ -1152,19 +1162,22 @@ int analyze_impl(int64_t n, const int64_t *colptr, const int32_t *rowind, const 
                 p = q;
             }
         }
-        std::vector<std::vector<int32_t>> sets;
-        std::vector<int32_t> order;
-        for (int64_t P = 0; P < ns; P++) {
-            int32_t f = sup_ptr[P], size = sup_ptr[P + 1] - f;
-            if (size < 2 || nsets[P + 1] == nsets[P]) continue;
-            sets.clear();
-            for (int64_t q = nsets[P]; q < nsets[P + 1]; q++) {
-                sets.emplace_back();
-                for (int64_t p = set_lo[q]; p < set_hi[q]; p++) sets.back().push_back(srows[p] - f);
+        // each P reorders only its own columns: blocks of supernodes on the host threads
+        parallel_blocks(ns, 64, threads, [&](int64_t P0, int64_t P1) {
+            std::vector<std::vector<int32_t>> sets;
+            std::vector<int32_t> order;
+            for (int64_t P = P0; P < P1; P++) {
+                int32_t f = sup_ptr[P], size = sup_ptr[P + 1] - f;
+                if (size < 2 || nsets[P + 1] == nsets[P]) continue;
+                sets.clear();
+                for (int64_t q = nsets[P]; q < nsets[P + 1]; q++) {
+                    sets.emplace_back();
+                    for (int64_t p = set_lo[q]; p < set_hi[q]; p++) sets.back().push_back(srows[p] - f);
+                }
+                refine(size, sets, order);
+                for (int32_t k = 0; k < size; k++) p3[f + k] = p1[f + order[k]];
             }
-            refine(size, sets, order);
-            for (int32_t k = 0; k < size; k++) p3[f + k] = p1[f + order[k]];
-        }
+        });
     }
     // labels after PR
     std::vector<int32_t> lab(n);  // lab[pre-PR label] = final label
