@@ -469,7 +469,10 @@ class Numeric:
         (CUDA, or pinned/host CPU): shape (nrhs, n) contiguous, i.e. column-major
         n x nrhs; X likewise (allocated when None). method "ir": classical
         refinement; "cg": conjugate gradients preconditioned by the factor.
-        max_iterations caps the iterations of this solve (0: the options' cap)."""
+        max_iterations caps the iterations of this solve (0: the options' cap).
+        Returns (X, info); info holds the iterations, convergence, eta per
+        right-hand side, the device time of the solve and of its B / X copies
+        (solve_ms, copy_in_ms, copy_out_ms) and the kernel launches."""
         if isinstance(B, np.ndarray):
             dev = False
             B = np.asfortranarray(B, np.float64)
